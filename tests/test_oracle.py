@@ -1,0 +1,397 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle is checked against things other than itself: codec vectors from
+the LEB128 definition, closed forms, hand-derived layouts of small CPMAs
+(derivations in the comments, from the readings of Sec. 3-5 listed in
+``oracle/cpma_oracle.c``), Python's own set semantics by brute force, and the
+structural invariants of Sec. 3 and Sec. 5.
+"""
+import os
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_05055_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+M64 = (1 << 64) - 1
+CFG = dict(tau_leaf=900, tau_root=700, rho_leaf=100, rho_root=300)
+
+
+# --------------------------------------------------------------------------
+# codec (Sec. 5 "Data compression techniques")
+# --------------------------------------------------------------------------
+
+def _golden_leb():
+    out = []
+    with open(os.path.join(GOLDEN, "leb128.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                v, h = line.split()
+                out.append((int(v), bytes.fromhex(h)))
+    return out
+
+
+@pytest.mark.parametrize("value,enc", _golden_leb())
+def test_leb128_vectors(value, enc):
+    assert oracle.leb_put(value) == enc
+    assert oracle.leb_get(enc) == (value, len(enc))
+    assert oracle.leb_len(value) == len(enc)
+
+
+def test_leb128_length_closed_form_bruteforce():
+    # len(d) = max(1, ceil(bitlen(d) / 7)) for every d < 2^16 and at every
+    # group boundary up to 2^64 - 1.
+    vals = list(range(1 << 16))
+    for i in range(1, 10):
+        vals += [(1 << (7 * i)) - 1, 1 << (7 * i), (1 << (7 * i)) + 1]
+    vals += [M64, M64 - 1, 1 << 63]
+    for d in vals:
+        want = max(1, -(-d.bit_length() // 7))
+        assert oracle.leb_len(d) == want, d
+
+
+def test_leb128_roundtrip_and_minimal():
+    rng = random.Random(7)
+    for _ in range(3000):
+        d = rng.getrandbits(rng.randint(1, 64))
+        b = oracle.leb_put(d)
+        assert oracle.leb_get(b) == (d, len(b))
+        # continue bit on every byte but the last; no redundant zero group
+        assert all(x & 0x80 for x in b[:-1]) and not (b[-1] & 0x80)
+        assert len(b) == 1 or b[-1] != 0
+
+
+def test_leaf_encode_hand_example():
+    # e = [5, 6, 306]: head 5 as 8 little-endian bytes, delta 1 -> 01,
+    # delta 300 -> ac 02; 11 bytes used, the rest zero (packed left).
+    buf, used = oracle.leaf_encode([5, 6, 306], 64)
+    assert used == 11
+    assert bytes(buf[:11]) == bytes([5, 0, 0, 0, 0, 0, 0, 0, 0x01, 0xAC, 0x02])
+    assert not buf[11:].any()
+    assert list(oracle.leaf_decode(buf, used)) == [5, 6, 306]
+    # head of 2^64-1 and a single element
+    buf, used = oracle.leaf_encode([M64], 64)
+    assert used == 8 and bytes(buf[:8]) == b"\xff" * 8
+    buf, used = oracle.leaf_encode([], 64)
+    assert used == 0 and not buf.any()
+
+
+def test_leaf_roundtrip_random():
+    rng = np.random.default_rng(3)
+    for bits in (8, 20, 40, 64):
+        for m in (1, 2, 17, 60):
+            e = np.unique(rng.integers(0, 2 ** min(bits, 63), size=m, dtype=np.uint64))
+            if bits == 64:
+                e = np.unique(np.concatenate([e, np.array([M64], np.uint64)]))
+            nbytes = oracle.leaf_bytes(e)
+            assert nbytes == 8 + sum(oracle.leb_len(int(b) - int(a)) for a, b in zip(e[:-1], e[1:]))
+            buf, used = oracle.leaf_encode(e, 1024)
+            assert used == nbytes
+            assert np.array_equal(oracle.leaf_decode(buf, used), e)
+
+
+# --------------------------------------------------------------------------
+# density bounds (Sec. 3; byte density Sec. 5)
+# --------------------------------------------------------------------------
+
+def V(H, h, leaves, b, LB=512):
+    return oracle.violates(LB, CFG["tau_leaf"], CFG["tau_root"], CFG["rho_leaf"],
+                           CFG["rho_root"], H, h, leaves, b)
+
+
+def test_bounds_hand_values():
+    # H = 3, LB = 512.  Leaf (h=0): upper 0.9*512 = 460.8, lower 0.1*512 = 51.2
+    assert not V(3, 0, 1, 460) and V(3, 0, 1, 461)
+    assert V(3, 0, 1, 51) and not V(3, 0, 1, 52)
+    # h = 1, two leaves (cap 1024): tau = 0.9 - 0.2/3 -> 853.33; rho = 0.1 + 0.2/3 -> 170.67
+    assert not V(3, 1, 2, 853) and V(3, 1, 2, 854)
+    assert V(3, 1, 2, 170) and not V(3, 1, 2, 171)
+    # h = 2 clipped to three leaves (L = 7): cap 1536, tau = 0.9 - 0.4/3 -> 1177.6
+    # rho = 0.1 + 0.4/3 -> 358.4
+    assert not V(3, 2, 3, 1177) and V(3, 2, 3, 1178)
+    assert V(3, 2, 3, 358) and not V(3, 2, 3, 359)
+    # root h = H = 3, eight leaves (cap 4096): tau_root 2867.2, rho_root 1228.8
+    assert not V(3, 3, 8, 2867) and V(3, 3, 8, 2868)
+    assert V(3, 3, 8, 1228) and not V(3, 3, 8, 1229)
+    # a single leaf is the root: upper 0.7*512 = 358.4, no lower bound
+    assert not V(0, 0, 1, 358) and V(0, 0, 1, 359)
+    assert not V(0, 0, 1, 0)
+    # overflowed leaves (more than LB bytes) always violate
+    assert V(5, 0, 1, 600)
+
+
+def test_build_and_resize_leaf_counts():
+    # build: L = max(1, ceil(1000 S / (500*512 - 8000))) = ceil(S / 248)
+    assert oracle.build_leaves(0, 512, 500) == 1
+    assert oracle.build_leaves(248, 512, 500) == 1
+    assert oracle.build_leaves(249, 512, 500) == 2
+    assert oracle.build_leaves(248 * 1000, 512, 500) == 1000
+    assert oracle.build_leaves(248 * 1000 + 1, 512, 500) == 1001
+    # grow (x6/5 rounded up) until 1000 T <= 700 L' 512
+    assert oracle.resize_leaves(3585, 10, 512, 700, 300) == 12
+    assert oracle.resize_leaves(5000, 10, 512, 700, 300) == 15   # 10 -> 12 -> 15
+    assert oracle.resize_leaves(400, 1, 512, 700, 300) == 2
+    # shrink (x5/6 rounded down) while 1000 T < 300 L' 512 and L' > 1
+    assert oracle.resize_leaves(1000, 10, 512, 700, 300) == 6    # 10 -> 8 -> 6
+    assert oracle.resize_leaves(10, 10, 512, 700, 300) == 1
+
+
+def test_cut_points_hand_values():
+    e = list(range(10))  # costs 8,1,1,...,1 -> C = 0,8,9,...,17; S = 17
+    # W = 2: theta_1 = floor(17/2) = 8 -> first C_i >= 8 is i = 1
+    assert list(oracle.cut_points(e, 2)) == [0, 1, 10]
+    # W = 3: thetas 0, 5, 11 -> starts 0, 1, 4
+    assert list(oracle.cut_points(e, 3)) == [0, 1, 4, 10]
+    # one element over three leaves: C = 0, 8; thetas 0, 2, 5 -> 0, 1, 1
+    assert list(oracle.cut_points([42], 3)) == [0, 1, 1, 1]
+    # no elements
+    assert list(oracle.cut_points([], 4)) == [0, 0, 0, 0, 0]
+    # a 3-byte delta: e = [0, 1, 2^14 + 1, 2^14 + 2]: costs 8, 1, 3, 1 -> C = 0, 8, 9, 12, 13
+    # W = 2: theta_1 = 6 -> i = 1.  W = 4: thetas 0, 3, 6, 9 -> 0, 1, 1, 2
+    e = [0, 1, (1 << 14) + 1, (1 << 14) + 2]
+    assert list(oracle.cut_points(e, 2)) == [0, 1, 4]
+    assert list(oracle.cut_points(e, 4)) == [0, 1, 1, 2, 4]
+
+
+# --------------------------------------------------------------------------
+# hand-derived sequential CPMA scenarios (LB = 256)
+# --------------------------------------------------------------------------
+#
+# Keys 4i for i < 600: every delta is 4 (one byte), so the stream costs
+# S = 8 + 599 = 607 bytes.  Build: L = ceil(607000 / (500*256 - 8000)) =
+# ceil(5.06) = 6 leaves, H = 3.  Cut points: C_i = i + 7 for i >= 1 and
+# theta_w = floor(607 w / 6) = 0, 101, 202, 303, 404, 505, so s_w = theta_w - 7
+# = 0, 94, 195, 296, 397, 498 (s_6 = 600).  Leaf j holds 4i for i in
+# [s_j, s_{j+1}) and uses 8 + (count - 1) bytes.
+
+def _base():
+    return oracle.SeqCPMA([4 * i for i in range(600)][::-1] + [8, 8, 12],
+                          leaf_bytes=256, **CFG)
+
+
+def test_scenario_build():
+    o = _base()
+    data, used, head = o.layout()
+    assert o.leaves() == 6 and o.size() == 600
+    assert list(used) == [101, 108, 108, 108, 108, 109]
+    assert list(head) == [0, 376, 780, 1184, 1588, 1992]
+    assert o.bytes() == 6 * (256 + 16)
+    assert o.check() == 0
+
+
+def test_scenario_window_at_level_one():
+    # Insert 4i+1 and 4i+2 for i in [195, 270): 150 keys, all routed to leaf 2
+    # (heads 780 <= key < 1184).  Each splits a 4-delta into 1+1+2... all
+    # one-byte codes, so leaf 2 grows from 108 to 258 bytes (> 0.9*256 = 230.4).
+    # Level 1, leaves [2, 4): 258 + 108 = 366 bytes against
+    # 512 * (0.9 - 0.2/3) = 426.7 and 512 * (0.1 + 0.2/3) = 85.3: within
+    # bounds, so the window is leaves [2, 4).  It holds 251 + 101 = 352
+    # elements, all deltas one byte: S = 359, theta_1 = floor(359/2) = 179,
+    # s_1 = 179 - 7 = 172.  Leaf 2: 172 elements -> 179 bytes; leaf 3: 180
+    # elements -> 187 bytes.  Element 172 is the second of triplet 57 of leaf
+    # 2's (4i, 4i+1, 4i+2) run: i = 195 + 57 = 252, key 4*252 + 1 = 1009.
+    o = _base()
+    ins = [4 * i + 1 for i in range(195, 270)] + [4 * i + 2 for i in range(195, 270)]
+    assert o.insert_batch(ins) == 150
+    lb = o.last_batch()
+    assert lb == dict(resized=0, nwindows=1, touched=1)
+    assert o.last_windows().tolist() == [[2, 2]]
+    data, used, head = o.layout()
+    assert list(used) == [101, 108, 179, 187, 108, 109]
+    assert list(head) == [0, 376, 780, 1009, 1588, 1992]
+    assert o.check() == 0
+
+
+def test_scenario_in_place():
+    # 100 keys 4i+1 for i in [195, 295) into leaf 2: 108 + 100 = 208 bytes,
+    # within 230.4, so only leaf 2 is rewritten in place.
+    o = _base()
+    assert o.insert_batch([4 * i + 1 for i in range(195, 295)]) == 100
+    assert o.last_batch() == dict(resized=0, nwindows=0, touched=1)
+    _, used, head = o.layout()
+    assert list(used) == [101, 108, 208, 108, 108, 109]
+    assert list(head) == [0, 376, 780, 1184, 1588, 1992]
+
+
+def test_scenario_grow():
+    # Insert 4i+1, 4i+2, 4i+3 for every i < 599: 1797 keys, every delta
+    # becomes 1.  Per leaf after the merge: leaf 0 has 94*4 = 376 elements
+    # (383 bytes), leaves 1-4 have 404 (411 bytes), leaf 5 has 102 + 101*3 =
+    # 405 (412 bytes): T = 383 + 4*411 + 412 = 2439.  Every walk passes the
+    # root, so resize: 1000 T = 2,439,000 > 700 * L' * 256 for L' = 6, 8, 10,
+    # 12 and <= for L' = 15 (6 -> 8 -> 10 -> 12 -> 15).  2397 elements,
+    # S = 8 + 2396 = 2404, all costs after the first are 1, so
+    # s_w = floor(2404 w / 15) - 7 and leaf w uses s_{w+1} - s_w + 7 bytes.
+    o = _base()
+    ins = [4 * i + r for i in range(599) for r in (1, 2, 3)]
+    assert o.insert_batch(ins) == 1797
+    assert o.last_batch()["resized"] == 1
+    assert o.leaves() == 15
+    s = [0] + [2404 * w // 15 - 7 for w in range(1, 15)] + [2397]
+    _, used, head = o.layout()
+    assert list(used) == [s[w + 1] - s[w] + 7 for w in range(15)]
+    elems = sorted([4 * i for i in range(600)] + ins)
+    assert list(head) == [elems[s[w]] for w in range(15)]
+    assert o.check() == 0
+
+
+def test_scenario_shrink():
+    # Delete 4i for i in [50, 550): leaves 1-4 become empty (0 bytes), leaves
+    # 0 and 5 keep 50 elements (57 bytes).  Leaf 0 is within [25.6, 230.4]:
+    # rewritten in place.  Leaf 1: 0 < 25.6 -> walk: [0,2) 57 < 85.3,
+    # [0,4) 57 < 1024 * (0.1 + 0.4/3) = 238.9, root [0,6) 114 < 0.3*1536 =
+    # 460.8 -> resize.  T = 114: shrink 6 -> 5 -> 4 -> 3 -> 2 -> 1 (at every
+    # step 114000 < 300 * L' * 256).  One leaf: 100 elements, deltas 4 (1 byte)
+    # except 4*550 - 4*49 = 2004 (2 bytes): 8 + 98 + 2 = 108 bytes.
+    o = _base()
+    assert o.delete_batch([4 * i for i in range(50, 550)] + [3, 5, 7]) == 500
+    assert o.last_batch()["resized"] == 1
+    assert o.leaves() == 1
+    _, used, head = o.layout()
+    assert list(used) == [108] and list(head) == [0]
+    assert o.check() == 0
+
+
+def test_scenario_empty_and_extremes():
+    o = oracle.SeqCPMA([], leaf_bytes=256, **CFG)
+    assert o.leaves() == 1 and o.size() == 0
+    _, used, head = o.layout()
+    assert list(used) == [0] and list(head) == [M64]   # empty leaf: 2^64-1
+    assert o.insert_batch([M64, 0, M64]) == 2
+    _, used, head = o.layout()
+    # head 0 (8 bytes) + delta 2^64-1 (10 bytes)
+    assert list(used) == [18] and list(head) == [0]
+    assert list(o.has_batch([0, 1, M64, M64 - 1])) == [1, 0, 1, 0]
+    s, c = o.range_map([0, 1, 0], [M64, M64, 1])
+    assert list(c) == [1, 0, 1] and list(s) == [0, 0, 0]
+    assert o.sum() == M64
+    assert o.delete_batch([0, M64, 5]) == 2
+    _, used, head = o.layout()
+    assert list(used) == [0] and list(head) == [M64]
+    assert o.check() == 0
+
+
+def test_scenario_empty_leaf_in_the_middle():
+    # With zero lower bounds (rho = 0) a leaf may stay empty.  Deleting all of
+    # leaf 2 (4i for i in [195, 296)) leaves it empty and within bounds, so it
+    # is rewritten in place with used 0; its head-index entry becomes the head
+    # of the next non-empty leaf (1184).  Key 1000 then routes to leaf 1 (the
+    # last entry <= 1000 is 376), whose last element 776 gives a delta of 224
+    # (two bytes): leaf 1 grows from 108 to 110 bytes.
+    o = oracle.SeqCPMA([4 * i for i in range(600)], leaf_bytes=256,
+                       tau_leaf=900, tau_root=700, rho_leaf=0, rho_root=0)
+    assert o.delete_batch([4 * i for i in range(195, 296)]) == 101
+    assert o.last_batch() == dict(resized=0, nwindows=0, touched=1)
+    _, used, head = o.layout()
+    assert list(used) == [101, 108, 0, 108, 108, 109]
+    assert list(head) == [0, 376, 1184, 1184, 1588, 1992]
+    assert o.insert_batch([1000]) == 1
+    _, used, head = o.layout()
+    assert list(used) == [101, 110, 0, 108, 108, 109]
+    assert list(head) == [0, 376, 1184, 1184, 1588, 1992]
+    assert o.check() == 0
+
+
+# --------------------------------------------------------------------------
+# set semantics by brute force against Python sets
+# --------------------------------------------------------------------------
+
+def _brute_range(S, lo, hi):
+    sel = [x for x in S if lo <= x < hi]
+    return sum(sel) & M64, len(sel)
+
+
+@pytest.mark.parametrize("LB", [256, 512, 1024, 2048])
+def test_plainset_and_seqcpma_vs_python_sets(LB):
+    rng = random.Random(LB)
+    pyset = set()
+    base = [rng.getrandbits(20) for _ in range(3000)] + [0, M64]
+    pyset.update(base)
+    plain = oracle.PlainSet(base)
+    seq = oracle.SeqCPMA(base, leaf_bytes=LB, **CFG)
+    for step in range(40):
+        k = rng.choice([1, 5, 100, 1500, 6000])
+        if rng.random() < 0.55:
+            keys = [rng.getrandbits(rng.choice([20, 22, 64])) for _ in range(k)]
+            keys += keys[: k // 4]  # repeats
+            want = len(set(keys) - pyset)
+            pyset.update(keys)
+            assert plain.insert_batch(keys) == want
+            assert seq.insert_batch(keys) == want
+        else:
+            present = sorted(pyset)
+            keys = [present[rng.randrange(len(present))] for _ in range(min(k, len(present)))] \
+                if present else []
+            keys += [rng.getrandbits(20) for _ in range(k // 3)]
+            want = len(set(keys) & pyset)
+            pyset.difference_update(keys)
+            assert plain.delete_batch(keys) == want
+            assert seq.delete_batch(keys) == want
+        S = sorted(pyset)
+        assert plain.S.tolist() == S
+        assert seq.elements().tolist() == S
+        assert seq.size() == len(S)
+        assert seq.check() == 0
+        if step % 8 == 0:
+            q = [rng.getrandbits(20) for _ in range(50)] + S[:5] + [M64, 0]
+            want_has = [int(x in pyset) for x in q]
+            assert plain.has_batch(q).tolist() == want_has
+            assert seq.has_batch(q).tolist() == want_has
+            lo = [rng.getrandbits(20) for _ in range(30)] + [0, 5, M64]
+            hi = [x + rng.getrandbits(rng.choice([4, 12, 19])) for x in lo[:30]] + [M64, 5, M64]
+            hi = [min(h, M64) for h in hi]
+            ws = [_brute_range(S, a, b) for a, b in zip(lo, hi)]
+            for impl in (plain, seq):
+                s, c = impl.range_map(lo, hi)
+                assert [(int(x), int(y)) for x, y in zip(s, c)] == ws
+            assert seq.sum() == sum(S) & M64
+
+
+def test_seqcpma_delete_everything_and_rebuild():
+    keys = list(range(0, 40000, 3))
+    o = oracle.SeqCPMA(keys, leaf_bytes=256, **CFG)
+    assert o.delete_batch(keys) == len(keys)
+    assert o.size() == 0 and o.leaves() == 1 and o.check() == 0
+    assert o.insert_batch(keys) == len(keys)
+    assert o.elements().tolist() == keys and o.check() == 0
+
+
+def test_seqcpma_windows_are_maximal_dyadic_nodes():
+    # Skewed inserts force many windows; every reported window must be a node
+    # of the implicit tree (aligned, power-of-two or clipped at L) and no
+    # window may contain another.
+    rng = np.random.default_rng(11)
+    base = W.uniform_keys(5, 200000, bits=40)
+    o = oracle.SeqCPMA(base, leaf_bytes=256, **CFG)
+    seen = 0
+    for r in range(6):
+        keys = W.zipf_keys(100 + r, 20000, bits=34)
+        L = o.leaves()
+        o.insert_batch(keys)
+        assert o.check() == 0
+        if o.last_batch()["resized"]:
+            continue
+        wins = o.last_windows()
+        seen += len(wins)
+        for a, w in wins:
+            a, w = int(a), int(w)
+            h = max(0, (w - 1).bit_length())
+            assert a % (1 << h) == 0
+            assert w == (1 << h) or a + w == L
+        iv = sorted((int(a), int(a + w)) for a, w in wins)
+        for (a0, a1), (b0, b1) in zip(iv, iv[1:]):
+            assert a1 <= b0
+    assert seen > 0
+
+
+def test_bytes_per_key_sanity_band():
+    # Not a pin: Table size-micro reports 4.77 bytes/element for the CPMA at
+    # 1e6 uniform 40-bit keys; a fresh build at density 0.5 with 512-byte
+    # leaves lands in the same few-bytes band.
+    o = oracle.SeqCPMA(W.uniform_keys(9, 10 ** 6), leaf_bytes=512, **CFG)
+    bpk = o.bytes() / o.size()
+    assert 3.0 < bpk < 8.0
