@@ -1,0 +1,160 @@
+/*
+ * cpma.h -- C ABI of a GPU (sm_103a) batch-parallel compressed set: the
+ * Compressed Packed Memory Array (CPMA) of Wheatman, Burns, Bulu\c{c} and Xu,
+ * "CPMA: An Efficient Batch-Parallel Compressed Set Without Pointers"
+ * (PPoPP '24).
+ *
+ * A CPMA stores a set of distinct 64-bit keys in one flat array of L leaves
+ * of LB bytes.  Each non-empty leaf holds its first key (the head) as 8
+ * little-endian bytes followed by the deltas to the following keys in
+ * unsigned LEB128 byte codes, packed to the left (Sec. 5 "CPMA structure",
+ * "Data compression techniques").  An implicit binary tree over the leaves
+ * carries byte-density bounds per height (Sec. 3 "Design and operations",
+ * Sec. 5 byte density); batch updates merge, count and redistribute
+ * (Sec. 4); the array grows by 6/5 when the root bound fails (Sec. 3
+ * "Resizing a PMA"; growing factor in App. B).
+ *
+ * Conventions shared by every call:
+ *  - All key, query and result pointers are DEVICE pointers owned by the
+ *    caller.  They must stay valid until the work queued on `stream`
+ *    completes.  The library never keeps them and never writes to inputs.
+ *  - Every uint64 value 0 .. 2^64-1 is a valid key.  Batches may be unsorted
+ *    and may repeat keys; repeats are counted once.
+ *  - Updates on one handle are single-writer: issue them on one stream (or
+ *    order the streams).  Queries may run concurrently with other queries,
+ *    never with an update unless the caller orders them.
+ *  - Every call returns CPMA_OK (0) or a negative error code (below).  An
+ *    update that fails before it starts changing the structure leaves the set
+ *    unchanged; CPMA_ECUDA and CPMA_EINTERNAL after that point leave the
+ *    handle unusable (destroy it).
+ *  - Calls that take a stream enqueue device work on it; the update calls and
+ *    cpma_create also wait on it once or twice for small control values
+ *    (batch sizes, whether to resize), so they return with the update
+ *    complete on the device.
+ */
+#ifndef CPMA_H
+#define CPMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cpma_stream_t; /* a cudaStream_t; NULL = legacy default */
+typedef struct cpma cpma_t;                /* opaque handle */
+
+enum {
+  CPMA_OK = 0,
+  CPMA_EINVAL = -1,    /* bad argument or configuration */
+  CPMA_ENOMEM = -2,    /* device or host allocation failed */
+  CPMA_ECUDA = -3,     /* a CUDA call failed */
+  CPMA_EINTERNAL = -4, /* a device-side consistency check failed */
+};
+
+/* Tunables.  The density bounds follow Sec. 3 ("the density bound of a node
+ * depends on its height"; leaf bound 0.9 in the figure captions) read as a
+ * linear interpolation from leaf to root:
+ *   upper(h) = tau_leaf - (tau_leaf - tau_root) * h / H,
+ *   lower(h) = rho_leaf + (rho_root - rho_leaf) * h / H   (permille),
+ * H = ceil(log2 L).  With L == 1 only the upper root bound applies.
+ * Requirements: 256 <= leaf_bytes <= 2048, leaf_bytes % 16 == 0,
+ * rho_leaf <= rho_root < tau_root <= tau_leaf < 1000,
+ * (1000 - tau_leaf) * leaf_bytes >= 20000 (a redistributed leaf then always
+ * fits), grow_num > grow_den > 0, 8000 < build_pm * leaf_bytes,
+ * build_pm <= tau_root. */
+typedef struct {
+  uint32_t leaf_bytes; /* LB; default 512 */
+  uint32_t tau_leaf;   /* default 900 */
+  uint32_t tau_root;   /* default 700 */
+  uint32_t rho_leaf;   /* default 100 */
+  uint32_t rho_root;   /* default 300 */
+  uint32_t grow_num;   /* growing factor grow_num / grow_den; default 6/5 */
+  uint32_t grow_den;
+  uint32_t build_pm;   /* fill density of cpma_create; default 500 */
+} cpma_config;
+
+/* Fill *cfg with the defaults above. */
+void cpma_default_config(cpma_config* cfg);
+
+/* App. A constructor "CPMA(key_type *start, key_type *end)": build a CPMA
+ * holding the distinct keys of d_keys[0..n).  d_keys: device, any order,
+ * repeats allowed (n == 0 gives an empty set; d_keys may then be NULL).
+ * cfg: NULL for defaults.  The new handle is written to *out and owns all the
+ * device memory it allocates (cudaMalloc on the current device). */
+int cpma_create(cpma_t** out, const cpma_config* cfg, const uint64_t* d_keys,
+                uint64_t n, cpma_stream_t stream);
+
+/* Free the handle and all its device memory (synchronises its last stream). */
+int cpma_destroy(cpma_t* h);
+
+/* A deep copy of src (device to device) on `stream`: *out gets a new handle. */
+int cpma_clone(const cpma_t* src, cpma_t** out, cpma_stream_t stream);
+
+/* App. A insert_batch: insert the keys d_keys[0..k) (Sec. 4 batch insert:
+ * sort, batch merge, counting, redistribute, resize).  sorted != 0 promises
+ * that the keys are non-decreasing (repeats still allowed) and skips the
+ * sort; a batch that breaks the promise is rejected with CPMA_EINVAL and the
+ * set is unchanged.  If d_added is not NULL, the number of keys that were not
+ * already present is written to the device uint64 *d_added. */
+int cpma_insert_batch(cpma_t* h, const uint64_t* d_keys, uint64_t k,
+                      int sorted, uint64_t* d_added, cpma_stream_t stream);
+
+/* App. A remove_batch: delete the keys of d_keys[0..k) that are present
+ * (Sec. 3 "deletes x ... if it exists"; Sec. 4 "batch deletes are
+ * symmetric").  d_removed (nullable, device) receives the number removed. */
+int cpma_delete_batch(cpma_t* h, const uint64_t* d_keys, uint64_t k,
+                      int sorted, uint64_t* d_removed, cpma_stream_t stream);
+
+/* App. A has, batched: d_out[i] = 1 if d_keys[i] is in the set, else 0
+ * (Sec. 5 "Point queries": binary search on the heads, then one pass over
+ * the leaf).  d_keys: q device uint64 in any order; d_out: q device bytes. */
+int cpma_has_batch(const cpma_t* h, const uint64_t* d_keys, uint64_t q,
+                   uint8_t* d_out, cpma_stream_t stream);
+
+/* Sec. 3 range_map(start, end, f) with f = (sum, count), batched: for every
+ * i < q, d_sum[i] = sum of the keys x with d_lo[i] <= x < d_hi[i], modulo
+ * 2^64, and d_count[i] = how many there are (both device uint64 arrays of q
+ * entries).  lo >= hi gives 0 and 0.  All q queries run in one load-balanced
+ * launch over (query, leaf) work items. */
+int cpma_range_map(const cpma_t* h, const uint64_t* d_lo, const uint64_t* d_hi,
+                   uint64_t q, uint64_t* d_sum, uint64_t* d_count,
+                   cpma_stream_t stream);
+
+/* App. A sum(): sum of all keys modulo 2^64 into the device uint64 *d_sum
+ * (and, if d_count is not NULL, the number of keys into *d_count). */
+int cpma_sum(const cpma_t* h, uint64_t* d_sum, uint64_t* d_count,
+             cpma_stream_t stream);
+
+/* App. A size(): number of keys, as a host value.  Exact after every update
+ * call has returned (the update calls keep a host copy). */
+int cpma_size(const cpma_t* h, uint64_t* out);
+
+/* App. A get_size(): bytes of the structure: L * (leaf_bytes + 16), i.e. the
+ * leaf array plus an 8-byte head-index entry, a 4-byte used-byte count and a
+ * 4-byte element count per leaf.  Per-batch scratch is not included. */
+int cpma_bytes(const cpma_t* h, uint64_t* out);
+
+/* Number of leaves L (host value). */
+int cpma_leaves(const cpma_t* h, uint64_t* out);
+
+/* Copy the layout into caller device buffers: d_data (L * leaf_bytes bytes),
+ * d_used (L uint32), d_heads (L uint64; for an empty leaf the head of the next
+ * non-empty leaf, or 2^64-1).  Any pointer may be NULL to skip it. */
+int cpma_export_layout(const cpma_t* h, uint8_t* d_data, uint32_t* d_used,
+                       uint64_t* d_heads, cpma_stream_t stream);
+
+/* Device time and kernel-launch counters of the calls on this handle since the
+ * last reset, for profiling: *launches = kernels launched by the library. */
+int cpma_stats(const cpma_t* h, uint64_t* launches);
+int cpma_reset_stats(cpma_t* h);
+
+/* Text for an error code. */
+const char* cpma_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPMA_H */

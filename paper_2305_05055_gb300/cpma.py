@@ -1,0 +1,279 @@
+"""Python binding of the CPMA C ABI (``include/cpma.h``).
+
+Argument marshalling only: every step of every call runs in the CUDA library
+``_build/libcpma.so``.  PyTorch supplies device memory and streams.  Keys are
+64-bit unsigned integers; on the torch side they live in int64 (or uint64)
+CUDA tensors holding the same bit patterns.
+
+If the library is missing or fails to load, every call raises
+:class:`CPMAError`: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+CPMA_OK, CPMA_EINVAL, CPMA_ENOMEM, CPMA_ECUDA, CPMA_EINTERNAL = 0, -1, -2, -3, -4
+
+
+class CPMAError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = lib().cpma_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__("%s: %s (%d)" % (what, msg, code))
+
+
+class cpma_config(C.Structure):
+    _fields_ = [(n, C.c_uint32) for n in (
+        "leaf_bytes", "tau_leaf", "tau_root", "rho_leaf", "rho_root", "grow_num",
+        "grow_den", "build_pm")]
+
+
+def lib():
+    """Load libcpma.so (building it first when the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path) or os.environ.get("CPMA_REBUILD"):
+                path = _build.build()
+            try:
+                L = C.CDLL(path)
+            except OSError as e:  # pragma: no cover - depends on the box
+                raise RuntimeError("cannot load the CPMA CUDA library %s: %s" % (path, e))
+            V, U64, I = C.c_void_p, C.c_uint64, C.c_int
+            P64 = C.POINTER(U64)
+            sig = {
+                "cpma_default_config": (None, [C.POINTER(cpma_config)]),
+                "cpma_create": (I, [C.POINTER(V), C.POINTER(cpma_config), V, U64, V]),
+                "cpma_destroy": (I, [V]),
+                "cpma_clone": (I, [V, C.POINTER(V), V]),
+                "cpma_insert_batch": (I, [V, V, U64, I, V, V]),
+                "cpma_delete_batch": (I, [V, V, U64, I, V, V]),
+                "cpma_has_batch": (I, [V, V, U64, V, V]),
+                "cpma_range_map": (I, [V, V, V, U64, V, V, V]),
+                "cpma_sum": (I, [V, V, V, V]),
+                "cpma_size": (I, [V, P64]),
+                "cpma_bytes": (I, [V, P64]),
+                "cpma_leaves": (I, [V, P64]),
+                "cpma_export_layout": (I, [V, V, V, V, V]),
+                "cpma_stats": (I, [V, P64]),
+                "cpma_reset_stats": (I, [V]),
+                "cpma_strerror": (C.c_char_p, [I]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype, f.argtypes = res, args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != CPMA_OK:
+        raise CPMAError(rc, what)
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _keys(t, name="keys") -> torch.Tensor:
+    if isinstance(t, np.ndarray):
+        t = torch.from_numpy(np.ascontiguousarray(t).view(np.int64)).cuda()
+    if not (t.is_cuda and t.element_size() == 8):
+        raise TypeError("%s: expected a CUDA tensor of 64-bit integers" % name)
+    return t.contiguous()
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() else None
+
+
+def to_u64(t: torch.Tensor) -> np.ndarray:
+    """Device int64/uint64 tensor -> host numpy uint64 (same bits)."""
+    return t.detach().cpu().contiguous().view(torch.int64).numpy().view(np.uint64)
+
+
+def default_config(**overrides) -> cpma_config:
+    c = cpma_config()
+    lib().cpma_default_config(C.byref(c))
+    for k, v in overrides.items():
+        setattr(c, k, int(v))
+    return c
+
+
+# ---------------------------------------------------------------------------
+# functions with the names of the C ABI
+# ---------------------------------------------------------------------------
+
+def cpma_create(keys, config: cpma_config | None = None, stream=None):
+    k = _keys(keys) if keys is not None and len(keys) else None
+    h = C.c_void_p()
+    _check(lib().cpma_create(C.byref(h), C.byref(config) if config is not None else None,
+                             _ptr(k), 0 if k is None else k.numel(), C.c_void_p(_stream(stream))),
+           "cpma_create")
+    return h
+
+
+def cpma_destroy(h):
+    _check(lib().cpma_destroy(h), "cpma_destroy")
+
+
+def cpma_clone(h, stream=None):
+    out = C.c_void_p()
+    _check(lib().cpma_clone(h, C.byref(out), C.c_void_p(_stream(stream))), "cpma_clone")
+    return out
+
+
+def cpma_insert_batch(h, keys, sorted=False, out=None, stream=None):
+    k = _keys(keys)
+    _check(lib().cpma_insert_batch(h, _ptr(k), k.numel(), int(bool(sorted)), _ptr(out),
+                                   C.c_void_p(_stream(stream))), "cpma_insert_batch")
+    return out
+
+
+def cpma_delete_batch(h, keys, sorted=False, out=None, stream=None):
+    k = _keys(keys)
+    _check(lib().cpma_delete_batch(h, _ptr(k), k.numel(), int(bool(sorted)), _ptr(out),
+                                   C.c_void_p(_stream(stream))), "cpma_delete_batch")
+    return out
+
+
+def cpma_has_batch(h, keys, out=None, stream=None):
+    k = _keys(keys)
+    if out is None:
+        out = torch.empty(k.numel(), dtype=torch.uint8, device=k.device)
+    _check(lib().cpma_has_batch(h, _ptr(k), k.numel(), _ptr(out), C.c_void_p(_stream(stream))),
+           "cpma_has_batch")
+    return out
+
+
+def cpma_range_map(h, lo, hi, out_sum=None, out_count=None, stream=None):
+    lo, hi = _keys(lo, "lo"), _keys(hi, "hi")
+    if lo.numel() != hi.numel():
+        raise ValueError("lo and hi differ in length")
+    q = lo.numel()
+    if out_sum is None:
+        out_sum = torch.empty(q, dtype=torch.int64, device=lo.device)
+    if out_count is None:
+        out_count = torch.empty(q, dtype=torch.int64, device=lo.device)
+    _check(lib().cpma_range_map(h, _ptr(lo), _ptr(hi), q, _ptr(out_sum), _ptr(out_count),
+                                C.c_void_p(_stream(stream))), "cpma_range_map")
+    return out_sum, out_count
+
+
+def cpma_sum(h, stream=None, device="cuda"):
+    s = torch.empty(1, dtype=torch.int64, device=device)
+    c = torch.empty(1, dtype=torch.int64, device=device)
+    _check(lib().cpma_sum(h, _ptr(s), _ptr(c), C.c_void_p(_stream(stream))), "cpma_sum")
+    return s, c
+
+
+def _u64_out(fn, h, what):
+    v = C.c_uint64()
+    _check(fn(h, C.byref(v)), what)
+    return int(v.value)
+
+
+def cpma_size(h) -> int:
+    return _u64_out(lib().cpma_size, h, "cpma_size")
+
+
+def cpma_bytes(h) -> int:
+    return _u64_out(lib().cpma_bytes, h, "cpma_bytes")
+
+
+def cpma_leaves(h) -> int:
+    return _u64_out(lib().cpma_leaves, h, "cpma_leaves")
+
+
+def cpma_stats(h) -> int:
+    return _u64_out(lib().cpma_stats, h, "cpma_stats")
+
+
+def cpma_reset_stats(h):
+    _check(lib().cpma_reset_stats(h), "cpma_reset_stats")
+
+
+def cpma_export_layout(h, leaf_bytes: int, stream=None, device="cuda"):
+    L = cpma_leaves(h)
+    data = torch.empty(L * leaf_bytes, dtype=torch.uint8, device=device)
+    used = torch.empty(L, dtype=torch.int32, device=device)
+    heads = torch.empty(L, dtype=torch.int64, device=device)
+    _check(lib().cpma_export_layout(h, _ptr(data), _ptr(used), _ptr(heads),
+                                    C.c_void_p(_stream(stream))), "cpma_export_layout")
+    return data, used, heads
+
+
+# ---------------------------------------------------------------------------
+# object wrapper
+# ---------------------------------------------------------------------------
+
+class CPMA:
+    """A CPMA on the current CUDA device.  Updates and queries run on the
+    current torch stream unless one is given."""
+
+    def __init__(self, keys=None, stream=None, _handle=None, **config):
+        self.config = default_config(**config)
+        self._h = _handle if _handle is not None else cpma_create(keys, self.config, stream)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.cpma_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def clone(self, stream=None) -> "CPMA":
+        c = CPMA.__new__(CPMA)
+        c.config = self.config
+        c._h = cpma_clone(self._h, stream)
+        return c
+
+    def insert_batch(self, keys, sorted=False, stream=None) -> torch.Tensor:
+        k = _keys(keys)
+        out = torch.empty(1, dtype=torch.int64, device=k.device)
+        return cpma_insert_batch(self._h, k, sorted, out, stream)
+
+    def delete_batch(self, keys, sorted=False, stream=None) -> torch.Tensor:
+        k = _keys(keys)
+        out = torch.empty(1, dtype=torch.int64, device=k.device)
+        return cpma_delete_batch(self._h, k, sorted, out, stream)
+
+    def has_batch(self, keys, stream=None) -> torch.Tensor:
+        return cpma_has_batch(self._h, keys, None, stream)
+
+    def range_map(self, lo, hi, stream=None):
+        return cpma_range_map(self._h, lo, hi, None, None, stream)
+
+    def sum(self, stream=None):
+        return cpma_sum(self._h, stream)
+
+    def size(self) -> int:
+        return cpma_size(self._h)
+
+    def bytes(self) -> int:
+        return cpma_bytes(self._h)
+
+    def leaves(self) -> int:
+        return cpma_leaves(self._h)
+
+    def layout(self, stream=None):
+        return cpma_export_layout(self._h, self.config.leaf_bytes, stream)
+
+    def launches(self) -> int:
+        return cpma_stats(self._h)

@@ -1,0 +1,296 @@
+// C ABI of the CPMA library (declared in include/cpma.h): handle lifecycle,
+// argument checks and the dispatch to the update and query launchers.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using namespace cpmaimpl;
+
+namespace cpmaimpl {
+
+int check_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return CPMA_OK;
+  if (e == cudaErrorMemoryAllocation) return CPMA_ENOMEM;
+  return CPMA_ECUDA;
+}
+
+int ensure(Buf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.cap >= bytes) return CPMA_OK;
+  size_t want = std::max(bytes, b.cap + b.cap / 2);
+  want = (want + 255) & ~(size_t)255;
+  if (b.p) {
+    // growth only: the old contents are dead, but queued kernels may still
+    // read them
+    if (cudaDeviceSynchronize() != cudaSuccess) return CPMA_ECUDA;
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return CPMA_ENOMEM;
+  }
+  b.cap = want;
+  return CPMA_OK;
+}
+
+void release(Buf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+int sync_status(cpma* h, cudaStream_t st) {
+  CPMA_CUDA(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(Status), cudaMemcpyDeviceToHost, st));
+  CPMA_CUDA(cudaStreamSynchronize(st));
+  return CPMA_OK;
+}
+
+}  // namespace cpmaimpl
+
+namespace {
+
+int validate(const cpma_config& c) {
+  if (c.leaf_bytes < 256 || c.leaf_bytes > 2048 || c.leaf_bytes % 16) return CPMA_EINVAL;
+  if (!(c.rho_leaf <= c.rho_root && c.rho_root < c.tau_root && c.tau_root <= c.tau_leaf &&
+        c.tau_leaf < 1000))
+    return CPMA_EINVAL;
+  if ((uint64_t)(1000 - c.tau_leaf) * c.leaf_bytes < 20000) return CPMA_EINVAL;
+  if (c.grow_den == 0 || c.grow_num <= c.grow_den) return CPMA_EINVAL;
+  if ((uint64_t)c.build_pm * c.leaf_bytes <= 8000 || c.build_pm > c.tau_root) return CPMA_EINVAL;
+  return CPMA_OK;
+}
+
+void release_all(cpma* h) {
+  Scratch& s = h->s;
+  for (Buf* b : {&s.keysA, &s.keysB, &s.hist, &s.hoff, &s.flags, &s.flags_scan, &s.leaf_of,
+                 &s.chunk_begin, &s.chunk_leaf, &s.chunk_tid, &s.chunk_cnt, &s.chunk_off,
+                 &s.T_leaf, &s.T_begin, &s.T_first_chunk, &s.T_oldcnt, &s.T_oldused, &s.T_newcnt,
+                 &s.T_newbytes, &s.T_state, &s.viol, &s.cand, &s.wins, &s.bits, &s.prefix, &s.ovf,
+                 &s.E, &s.cost, &s.C, &s.srccnt, &s.srcoff, &s.dstart, &s.win_src, &s.win_dst,
+                 &s.win_leaf_off, &s.win_elem_off, &s.win_dst_off, &s.partials, &s.q_first,
+                 &s.q_items, &s.q_off})
+    release(*b);
+  cudaFree(h->data);
+  cudaFree(h->used);
+  cudaFree(h->cnt);
+  cudaFree(h->heads);
+  cudaFree(h->d_status);
+  if (h->h_status) cudaFreeHost(h->h_status);
+  h->data = nullptr;
+  h->used = nullptr;
+  h->cnt = nullptr;
+  h->heads = nullptr;
+  h->d_status = nullptr;
+  h->h_status = nullptr;
+}
+
+int new_handle(const cpma_config* cfg, cpma** out) {
+  cpma_config c;
+  cpma_default_config(&c);
+  if (cfg) c = *cfg;
+  CPMA_TRY(validate(c));
+  cpma* h = new (std::nothrow) cpma();
+  if (!h) return CPMA_ENOMEM;
+  h->cfg = c;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { delete h; return CPMA_ECUDA; }
+  h->device = dev;
+  if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete h;
+    return CPMA_ECUDA;
+  }
+  if (cudaMalloc(&h->d_status, sizeof(Status)) != cudaSuccess ||
+      cudaMallocHost(&h->h_status, sizeof(Status)) != cudaSuccess) {
+    cudaGetLastError();
+    release_all(h);
+    delete h;
+    return CPMA_ENOMEM;
+  }
+  if (cudaMemset(h->d_status, 0, sizeof(Status)) != cudaSuccess) {
+    release_all(h);
+    delete h;
+    return CPMA_ECUDA;
+  }
+  *out = h;
+  return CPMA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cpma_default_config(cpma_config* c) {
+  c->leaf_bytes = 512;
+  c->tau_leaf = 900;
+  c->tau_root = 700;
+  c->rho_leaf = 100;
+  c->rho_root = 300;
+  c->grow_num = 6;
+  c->grow_den = 5;
+  c->build_pm = 500;
+}
+
+int cpma_create(cpma_t** out, const cpma_config* cfg, const uint64_t* d_keys, uint64_t n,
+                cpma_stream_t stream) {
+  if (!out || (n && !d_keys)) return CPMA_EINVAL;
+  *out = nullptr;
+  cpma* h = nullptr;
+  CPMA_TRY(new_handle(cfg, &h));
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = CPMA_OK;
+  do {
+    rc = ensure(h->s.E, (n + 1) * 8);
+    if (rc) break;
+    uint64_t nu = 0;
+    if (n) {
+      const uint64_t* sorted = nullptr;
+      rc = sort_keys(h, d_keys, n, &sorted, st);
+      if (rc) break;
+      rc = unique_keys(h, sorted, n, (uint64_t*)h->s.E.p, st);
+      if (rc) break;
+      rc = sync_status(h, st);
+      if (rc) break;
+      nu = h->h_status->nunique;
+    }
+    rc = build_from_sorted_unique(h, (const uint64_t*)h->s.E.p, nu, st);
+  } while (0);
+  if (rc != CPMA_OK) {
+    cudaStreamSynchronize(st);
+    release_all(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return CPMA_OK;
+}
+
+int cpma_destroy(cpma_t* h) {
+  if (!h) return CPMA_EINVAL;
+  cudaDeviceSynchronize();
+  release_all(h);
+  delete h;
+  return CPMA_OK;
+}
+
+int cpma_clone(const cpma_t* src, cpma_t** out, cpma_stream_t stream) {
+  if (!src || !out) return CPMA_EINVAL;
+  *out = nullptr;
+  cpma* h = nullptr;
+  CPMA_TRY(new_handle(&src->cfg, &h));
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint64_t L = src->L, LB = src->cfg.leaf_bytes;
+  if (cudaMalloc(&h->data, L * LB) != cudaSuccess || cudaMalloc(&h->used, L * 4) != cudaSuccess ||
+      cudaMalloc(&h->cnt, L * 4) != cudaSuccess || cudaMalloc(&h->heads, L * 8) != cudaSuccess) {
+    cudaGetLastError();
+    release_all(h);
+    delete h;
+    return CPMA_ENOMEM;
+  }
+  int rc = CPMA_OK;
+  rc |= check_cuda(cudaMemcpyAsync(h->data, src->data, L * LB, cudaMemcpyDeviceToDevice, st));
+  rc |= check_cuda(cudaMemcpyAsync(h->used, src->used, L * 4, cudaMemcpyDeviceToDevice, st));
+  rc |= check_cuda(cudaMemcpyAsync(h->cnt, src->cnt, L * 4, cudaMemcpyDeviceToDevice, st));
+  rc |= check_cuda(cudaMemcpyAsync(h->heads, src->heads, L * 8, cudaMemcpyDeviceToDevice, st));
+  rc |= check_cuda(cudaMemcpyAsync(&h->d_status->empties, &src->d_status->empties, 8,
+                                   cudaMemcpyDeviceToDevice, st));
+  if (rc != CPMA_OK) {
+    cudaStreamSynchronize(st);
+    release_all(h);
+    delete h;
+    return CPMA_ECUDA;
+  }
+  h->L = L;
+  h->n = src->n;
+  h->may_have_empty = src->may_have_empty;
+  *out = h;
+  return CPMA_OK;
+}
+
+int cpma_insert_batch(cpma_t* h, const uint64_t* d_keys, uint64_t k, int sorted,
+                      uint64_t* d_added, cpma_stream_t stream) {
+  if (!h || (k && !d_keys)) return CPMA_EINVAL;
+  return run_update(h, d_keys, k, sorted, 0, d_added, (cudaStream_t)stream);
+}
+
+int cpma_delete_batch(cpma_t* h, const uint64_t* d_keys, uint64_t k, int sorted,
+                      uint64_t* d_removed, cpma_stream_t stream) {
+  if (!h || (k && !d_keys)) return CPMA_EINVAL;
+  return run_update(h, d_keys, k, sorted, 1, d_removed, (cudaStream_t)stream);
+}
+
+int cpma_has_batch(const cpma_t* h, const uint64_t* d_keys, uint64_t q, uint8_t* d_out,
+                   cpma_stream_t stream) {
+  if (!h || (q && (!d_keys || !d_out))) return CPMA_EINVAL;
+  return run_has(h, d_keys, q, d_out, (cudaStream_t)stream);
+}
+
+int cpma_range_map(const cpma_t* h, const uint64_t* d_lo, const uint64_t* d_hi, uint64_t q,
+                   uint64_t* d_sum, uint64_t* d_count, cpma_stream_t stream) {
+  if (!h || (q && (!d_lo || !d_hi || !d_sum || !d_count))) return CPMA_EINVAL;
+  return run_range(h, d_lo, d_hi, q, d_sum, d_count, (cudaStream_t)stream);
+}
+
+int cpma_sum(const cpma_t* h, uint64_t* d_sum, uint64_t* d_count, cpma_stream_t stream) {
+  if (!h || !d_sum) return CPMA_EINVAL;
+  return run_sum(h, d_sum, d_count, (cudaStream_t)stream);
+}
+
+int cpma_size(const cpma_t* h, uint64_t* out) {
+  if (!h || !out) return CPMA_EINVAL;
+  *out = h->n;
+  return CPMA_OK;
+}
+
+int cpma_bytes(const cpma_t* h, uint64_t* out) {
+  if (!h || !out) return CPMA_EINVAL;
+  *out = h->L * ((uint64_t)h->cfg.leaf_bytes + 16);
+  return CPMA_OK;
+}
+
+int cpma_leaves(const cpma_t* h, uint64_t* out) {
+  if (!h || !out) return CPMA_EINVAL;
+  *out = h->L;
+  return CPMA_OK;
+}
+
+int cpma_export_layout(const cpma_t* h, uint8_t* d_data, uint32_t* d_used, uint64_t* d_heads,
+                       cpma_stream_t stream) {
+  if (!h) return CPMA_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint64_t L = h->L;
+  if (d_data)
+    CPMA_CUDA(cudaMemcpyAsync(d_data, h->data, L * h->cfg.leaf_bytes, cudaMemcpyDeviceToDevice, st));
+  if (d_used) CPMA_CUDA(cudaMemcpyAsync(d_used, h->used, L * 4, cudaMemcpyDeviceToDevice, st));
+  if (d_heads) CPMA_CUDA(cudaMemcpyAsync(d_heads, h->heads, L * 8, cudaMemcpyDeviceToDevice, st));
+  return CPMA_OK;
+}
+
+int cpma_stats(const cpma_t* h, uint64_t* launches) {
+  if (!h || !launches) return CPMA_EINVAL;
+  *launches = h->launches;
+  return CPMA_OK;
+}
+
+int cpma_reset_stats(cpma_t* h) {
+  if (!h) return CPMA_EINVAL;
+  h->launches = 0;
+  return CPMA_OK;
+}
+
+const char* cpma_strerror(int code) {
+  switch (code) {
+    case CPMA_OK: return "ok";
+    case CPMA_EINVAL: return "invalid argument or configuration";
+    case CPMA_ENOMEM: return "out of device or host memory";
+    case CPMA_ECUDA: return "CUDA error";
+    case CPMA_EINTERNAL: return "device-side consistency check failed";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Host-side internals of the CPMA library: the handle, its scratch buffers and
+// the kernel launchers of each translation unit.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/cpma.h"
+
+namespace cpmaimpl {
+
+typedef unsigned long long ull;
+
+// Device-side control block of one batch.  The host reads it back once or
+// twice per update to size the later phases.
+struct Status {
+  ull nT;          // routed leaves (runs of the sorted batch)
+  ull nchunks;     // merge work items (runs split every kChunk keys)
+  ull delta;       // keys added (insert) or removed (delete)
+  ull npend;       // leaves whose merged content waits in the overflow buffer
+  ull novf;        // overflow elements
+  ull nviol;       // touched leaves that violate their own bound
+  ull ncand;       // window candidates (distinct tree nodes)
+  ull resize;      // some walk passed the root
+  ull nwin;        // maximal windows
+  ull win_leaves;  // leaves over all maximal windows
+  ull total_bytes; // bytes over all leaves after the merge
+  ull nempty;      // empty leaves written by this batch
+  ull err;         // device-side error flags (kErr*)
+  ull mask_or;     // OR / AND of the batch keys (radix pass selection)
+  ull mask_and;
+  ull nelem;       // elements moved by the current redistribution
+  ull nunique;     // distinct keys after sort+dedup (create)
+  ull stream_bytes;// bytes of the build stream (create)
+  ull pad[13];
+  ull empties;     // empty leaves in the structure (written by the head
+                   // fix-up; not cleared at the start of a batch)
+};
+
+constexpr ull kErrUnsorted = 1;   // a batch promised sorted was not
+constexpr ull kErrFit = 2;        // a redistributed leaf did not fit
+constexpr ull kErrState = 4;      // inconsistent leaf state
+
+constexpr uint32_t kChunk = 256;  // keys per merge work item
+constexpr int kMaxLevels = 48;
+
+// T-entry states after the merge
+constexpr uint32_t kUnchanged = 0, kInPlace = 1, kPending = 2;
+
+// A grow-only device buffer.
+struct Buf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+struct Scratch {
+  Buf keysA, keysB;       // sort ping-pong (u64)
+  Buf hist;               // radix histograms (u32)
+  Buf hoff;               // scanned histograms (u64)
+  Buf flags;              // route / unique flags (u64)
+  Buf flags_scan;         // scanned flags (u64)
+  Buf leaf_of;            // leaf per sorted key (u32)
+  Buf chunk_begin, chunk_leaf, chunk_tid, chunk_cnt, chunk_off;
+  Buf T_leaf, T_begin, T_first_chunk, T_oldcnt, T_oldused, T_newcnt, T_newbytes, T_state;
+  Buf viol, cand, wins;   // violating leaves, window candidates, windows
+  Buf bits;               // per-level window bitsets (u32 words)
+  Buf prefix;             // prefix sums of used bytes (u64, L+1)
+  Buf ovf;                // overflow elements (u64)
+  Buf E, cost, C;         // redistribution: elements, costs, cost prefix
+  Buf srccnt, srcoff, dstart;
+  Buf win_src, win_dst, win_leaf_off, win_elem_off, win_dst_off;
+  Buf partials;           // scan partials
+  Buf q_first, q_items, q_off; // range queries
+};
+
+}  // namespace cpmaimpl
+
+struct cpma {
+  cpma_config cfg;
+  int device = 0;
+  int num_sms = 0;
+  uint64_t L = 0;        // leaves
+  uint64_t n = 0;        // keys
+  uint8_t* data = nullptr;
+  uint32_t* used = nullptr;
+  uint32_t* cnt = nullptr;
+  uint64_t* heads = nullptr;
+  uint64_t bits_words = 0;          // words of the window bitsets now zeroed
+  bool may_have_empty = false;      // some leaf may be empty (head fix-up)
+  cpmaimpl::Status* d_status = nullptr;
+  cpmaimpl::Status* h_status = nullptr;  // pinned
+  cpmaimpl::Scratch s;
+  uint64_t launches = 0;
+};
+
+namespace cpmaimpl {
+
+// memory
+int ensure(Buf& b, size_t bytes);
+void release(Buf& b);
+
+// scan.cu: exclusive prefix sums.  out has n+1 entries (out[n] = total).
+// The element count is n_host, or *n_dev when n_dev != nullptr (n_host is
+// then an upper bound used to size the launch).
+int scan_u32_to_u64(cpma* h, const uint32_t* in, uint64_t* out, uint64_t n_host,
+                    const ull* n_dev, cudaStream_t st);
+int scan_u8_to_u64(cpma* h, const uint8_t* in, uint64_t* out, uint64_t n_host,
+                   const ull* n_dev, cudaStream_t st);
+int scan_u64(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host, const ull* n_dev,
+             cudaStream_t st);
+
+// sort.cu: sort k keys ascending into *out (one of the scratch buffers).
+int sort_keys(cpma* h, const uint64_t* d_in, uint64_t k, const uint64_t** out,
+              cudaStream_t st);
+// sort.cu: drop adjacent repeats of sorted keys; result count into status->nunique.
+int unique_keys(cpma* h, const uint64_t* in, uint64_t k, uint64_t* out, cudaStream_t st);
+
+// update.cu
+int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_delete,
+               uint64_t* d_delta, cudaStream_t st);
+int build_from_sorted_unique(cpma* h, const uint64_t* E, uint64_t n, cudaStream_t st);
+
+// query.cu
+int run_has(const cpma* h, const uint64_t* d_keys, uint64_t q, uint8_t* d_out, cudaStream_t st);
+int run_range(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q, uint64_t* sum,
+              uint64_t* count, cudaStream_t st);
+int run_sum(const cpma* h, uint64_t* sum, uint64_t* count, cudaStream_t st);
+
+int check_cuda(cudaError_t e);
+int sync_status(cpma* h, cudaStream_t st);
+
+inline unsigned ceil_log2(uint64_t L) {
+  unsigned H = 0;
+  while ((1ull << H) < L) H++;
+  return H;
+}
+
+}  // namespace cpmaimpl
+
+#define CPMA_TRY(x)              \
+  do {                           \
+    int _rc = (x);               \
+    if (_rc != CPMA_OK) return _rc; \
+  } while (0)
+#define CPMA_CUDA(x) CPMA_TRY(::cpmaimpl::check_cuda(x))
+#define CPMA_LAUNCHED(h) (const_cast<cpma*>(h)->launches++)

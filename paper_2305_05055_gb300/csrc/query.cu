@@ -1,0 +1,202 @@
+// Queries over the compressed leaves.
+//  has (Sec. 5 "Point queries"): binary search on the uncompressed heads, then
+//    one warp-cooperative pass over the leaf.
+//  range_map (Sec. 3: a search for the first element, then a scan to the end
+//    of the range) with f = (sum mod 2^64, count): every query is routed to
+//    its first and last leaf; the (query, leaf) pairs of all queries are
+//    numbered by a prefix sum and split into equal contiguous shares, one per
+//    warp of a persistent grid, so long and short ranges balance.  Leaves
+//    strictly inside a range need no filter.  A warp keeps per-lane partial
+//    sums while it stays on one query and adds them atomically when it
+//    leaves it (addition mod 2^64 is associative, so the order is free).
+//  sum (App. A sum()): every leaf once.
+#include <algorithm>
+
+#include "dev_common.cuh"
+#include "internal.h"
+
+using namespace cpmadev;
+
+namespace cpmaimpl {
+namespace {
+
+constexpr int kT = 256;
+
+__device__ __forceinline__ uint64_t gtid() {
+  return (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+}
+__device__ __forceinline__ uint64_t gstride() { return (uint64_t)gridDim.x * blockDim.x; }
+
+__global__ void __launch_bounds__(kT) k_has(const uint64_t* __restrict__ keys, uint64_t q,
+                                            const uint8_t* __restrict__ data,
+                                            const uint32_t* __restrict__ used,
+                                            const uint64_t* __restrict__ heads, uint64_t L,
+                                            uint32_t LB, uint8_t* __restrict__ out) {
+  const unsigned lane = lane_id();
+  const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
+  for (uint64_t i = gw; i < q; i += nw) {
+    const uint64_t x = keys[i];
+    const uint64_t j = route_leaf(heads, L, x);
+    bool found = false;
+    warp_decode(data + j * LB, min(used[j], LB), [&](uint32_t, uint64_t v) { found |= (v == x); });
+    found = __any_sync(FULL, found);
+    if (lane == 0) out[i] = found ? 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(kT) k_range_prep(const uint64_t* __restrict__ lo,
+                                                   const uint64_t* __restrict__ hi, uint64_t q,
+                                                   const uint64_t* __restrict__ heads, uint64_t L,
+                                                   uint64_t* __restrict__ first,
+                                                   uint64_t* __restrict__ items,
+                                                   uint64_t* __restrict__ sum,
+                                                   uint64_t* __restrict__ count) {
+  for (uint64_t i = gtid(); i < q; i += gstride()) {
+    const uint64_t a = lo[i], b = hi[i];
+    uint64_t fl = 0, n = 0;
+    if (a < b) {
+      fl = route_leaf(heads, L, a);
+      n = route_leaf(heads, L, b - 1) - fl + 1;
+    }
+    first[i] = fl;
+    items[i] = n;
+    sum[i] = 0;
+    count[i] = 0;
+  }
+}
+
+struct RangeArgs {
+  const uint64_t* lo;
+  const uint64_t* hi;
+  uint64_t q;
+  const uint64_t* first;
+  const uint64_t* off;  // q + 1 entries
+  const uint8_t* data;
+  const uint32_t* used;
+  const uint32_t* cnt;
+  uint32_t LB;
+  uint64_t* sum;
+  uint64_t* count;
+};
+
+__global__ void __launch_bounds__(kT) k_range(RangeArgs a) {
+  const unsigned lane = lane_id();
+  const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
+  const uint64_t N = a.off[a.q];
+  const uint64_t g0 = N * gw / nw, g1 = N * (gw + 1) / nw;
+  if (g0 >= g1) return;
+  uint64_t qi = upper_count(a.off, a.q + 1, g0) - 1;
+  uint64_t s = 0, c = 0;
+  uint64_t qend = a.off[qi + 1];
+  uint64_t lo = a.lo[qi], hi = a.hi[qi], fl = a.first[qi], qoff = a.off[qi];
+  for (uint64_t g = g0; g < g1; g++) {
+    while (g >= qend) {
+      s = warp_sum(s);
+      c = warp_sum(c);
+      if (lane == 0 && (s | c)) {
+        atomicAdd((ull*)&a.sum[qi], (ull)s);
+        atomicAdd((ull*)&a.count[qi], (ull)c);
+      }
+      s = 0;
+      c = 0;
+      qi++;
+      qend = a.off[qi + 1];
+      lo = a.lo[qi]; hi = a.hi[qi]; fl = a.first[qi]; qoff = a.off[qi];
+    }
+    const uint64_t li = g - qoff;
+    const uint64_t j = fl + li;
+    const uint8_t* leaf = a.data + j * a.LB;
+    const bool interior = li > 0 && g + 1 < qend;
+    if (interior) {
+      warp_decode(leaf, min(a.used[j], a.LB), [&](uint32_t, uint64_t v) { s += v; });
+      if (lane == 0) c += a.cnt[j];
+    } else {
+      warp_decode(leaf, min(a.used[j], a.LB), [&](uint32_t, uint64_t v) {
+        if (v >= lo && v < hi) { s += v; c++; }
+      });
+    }
+  }
+  s = warp_sum(s);
+  c = warp_sum(c);
+  if (lane == 0 && (s | c)) {
+    atomicAdd((ull*)&a.sum[qi], (ull)s);
+    atomicAdd((ull*)&a.count[qi], (ull)c);
+  }
+}
+
+__global__ void __launch_bounds__(kT) k_sum(const uint8_t* __restrict__ data,
+                                            const uint32_t* __restrict__ used,
+                                            const uint32_t* __restrict__ cnt, uint64_t L,
+                                            uint32_t LB, uint64_t* sum, uint64_t* count) {
+  const unsigned lane = lane_id();
+  const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
+  const uint64_t j0 = L * gw / nw, j1 = L * (gw + 1) / nw;
+  uint64_t s = 0, c = 0;
+  for (uint64_t j = j0; j < j1; j++) {
+    warp_decode(data + j * LB, min(used[j], LB), [&](uint32_t, uint64_t v) { s += v; });
+    if (lane == 0) c += cnt[j];
+  }
+  s = warp_sum(s);
+  c = warp_sum(c);
+  if (lane == 0 && (s | c)) {
+    atomicAdd((ull*)sum, (ull)s);
+    if (count) atomicAdd((ull*)count, (ull)c);
+  }
+}
+
+int persistent_grid(const cpma* h) { return h->num_sms * 8; }
+
+}  // namespace
+
+int run_has(const cpma* h, const uint64_t* d_keys, uint64_t q, uint8_t* d_out, cudaStream_t st) {
+  if (q == 0) return CPMA_OK;
+  const int grid = (int)std::max<uint64_t>(
+      1, std::min<uint64_t>((q * 32 + kT - 1) / kT, (uint64_t)persistent_grid(h)));
+  k_has<<<grid, kT, 0, st>>>(d_keys, q, h->data, h->used, h->heads, h->L, h->cfg.leaf_bytes,
+                             d_out);
+  CPMA_LAUNCHED(h);
+  return check_cuda(cudaGetLastError());
+}
+
+int run_range(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q, uint64_t* sum,
+              uint64_t* count, cudaStream_t st) {
+  if (q == 0) return CPMA_OK;
+  cpma* hm = const_cast<cpma*>(h);
+  CPMA_TRY(ensure(hm->s.q_first, q * 8));
+  CPMA_TRY(ensure(hm->s.q_items, q * 8));
+  CPMA_TRY(ensure(hm->s.q_off, (q + 1) * 8));
+  uint64_t* first = (uint64_t*)hm->s.q_first.p;
+  uint64_t* items = (uint64_t*)hm->s.q_items.p;
+  uint64_t* off = (uint64_t*)hm->s.q_off.p;
+  const int g1 = (int)std::max<uint64_t>(
+      1, std::min<uint64_t>((q + kT - 1) / kT, (uint64_t)h->num_sms * 8));
+  k_range_prep<<<g1, kT, 0, st>>>(lo, hi, q, h->heads, h->L, first, items, sum, count);
+  CPMA_LAUNCHED(h);
+  CPMA_TRY(scan_u64(hm, items, off, q, nullptr, st));
+  RangeArgs a;
+  a.lo = lo;
+  a.hi = hi;
+  a.q = q;
+  a.first = first;
+  a.off = off;
+  a.data = h->data;
+  a.used = h->used;
+  a.cnt = h->cnt;
+  a.LB = h->cfg.leaf_bytes;
+  a.sum = sum;
+  a.count = count;
+  k_range<<<persistent_grid(h), kT, 0, st>>>(a);
+  CPMA_LAUNCHED(h);
+  return check_cuda(cudaGetLastError());
+}
+
+int run_sum(const cpma* h, uint64_t* sum, uint64_t* count, cudaStream_t st) {
+  CPMA_CUDA(cudaMemsetAsync(sum, 0, 8, st));
+  if (count) CPMA_CUDA(cudaMemsetAsync(count, 0, 8, st));
+  k_sum<<<persistent_grid(h), kT, 0, st>>>(h->data, h->used, h->cnt, h->L, h->cfg.leaf_bytes, sum,
+                                           count);
+  CPMA_LAUNCHED(h);
+  return check_cuda(cudaGetLastError());
+}
+
+}  // namespace cpmaimpl

@@ -1,0 +1,147 @@
+// Exclusive prefix sums over device arrays (reduce, scan of block partials,
+// rescan).  A fixed grid of 2 blocks per SM splits the input into equal
+// ranges, so the element count may live in device memory: the launch is sized
+// by a host upper bound and every block reads the true count.  Tiles of 2048
+// elements are staged through shared memory so global loads and stores stay
+// coalesced.
+#include <algorithm>
+
+#include "dev_common.cuh"
+#include "internal.h"
+
+using namespace cpmadev;
+
+namespace cpmaimpl {
+namespace {
+
+constexpr int kT = 256;
+constexpr int kItems = 8;
+constexpr int kTile = kT * kItems;
+
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* warp_tot,
+                                                    uint64_t* total) {
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  uint64_t inc = warp_incl_scan(v);
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t w = lane < (kT / 32) ? warp_tot[lane] : 0;
+    uint64_t wi = warp_incl_scan(w);
+    if (lane < (kT / 32)) warp_tot[lane] = wi - w;
+    if (lane == 31) *total = wi;
+  }
+  __syncthreads();
+  uint64_t r = warp_tot[warp] + inc - v;
+  __syncthreads();
+  return r;
+}
+
+template <typename Tin>
+__global__ void __launch_bounds__(kT) k_reduce(const Tin* __restrict__ in, uint64_t n_host,
+                                               const ull* n_dev, uint64_t* partials) {
+  const uint64_t n = n_dev ? *n_dev : n_host;
+  const uint64_t G = gridDim.x;
+  const uint64_t b0 = n * blockIdx.x / G, b1 = n * (blockIdx.x + 1) / G;
+  uint64_t s = 0;
+  for (uint64_t i = b0 + threadIdx.x; i < b1; i += kT) s += (uint64_t)in[i];
+  s = warp_sum(s);
+  __shared__ uint64_t ws[kT / 32];
+  if (lane_id() == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint64_t v = threadIdx.x < kT / 32 ? ws[threadIdx.x] : 0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+  }
+}
+
+// One block: exclusive scan of G partials in place, partials[G] = total.
+__global__ void __launch_bounds__(1024) k_partials(uint64_t* partials, int G) {
+  __shared__ uint64_t wt[32];
+  __shared__ uint64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < G; base += 1024) {
+    const int i = base + threadIdx.x;
+    uint64_t v = i < G ? partials[i] : 0;
+    uint64_t inc = warp_incl_scan(v);
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    if (lane == 31) wt[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      uint64_t w = wt[lane];
+      uint64_t wi = warp_incl_scan(w);
+      wt[lane] = wi - w;
+    }
+    __syncthreads();
+    uint64_t ex = carry + wt[warp] + inc - v;
+    if (i < G) partials[i] = ex;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = ex + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[G] = carry;
+}
+
+template <typename Tin>
+__global__ void __launch_bounds__(kT) k_down(const Tin* __restrict__ in, uint64_t* __restrict__ out,
+                                             uint64_t n_host, const ull* n_dev,
+                                             const uint64_t* __restrict__ partials) {
+  __shared__ uint64_t tile[kTile];
+  __shared__ uint64_t warp_tot[kT / 32];
+  __shared__ uint64_t tile_total;
+  const uint64_t n = n_dev ? *n_dev : n_host;
+  const uint64_t G = gridDim.x;
+  const uint64_t b0 = n * blockIdx.x / G, b1 = n * (blockIdx.x + 1) / G;
+  uint64_t carry = partials[blockIdx.x];
+  for (uint64_t t0 = b0; t0 < b1; t0 += kTile) {
+    const uint64_t cnt = min((uint64_t)kTile, b1 - t0);
+    for (uint32_t i = threadIdx.x; i < kTile; i += kT)
+      tile[i] = i < cnt ? (uint64_t)in[t0 + i] : 0;
+    __syncthreads();
+    uint64_t v[kItems];
+    uint64_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kItems; q++) { v[q] = tile[threadIdx.x * kItems + q]; s += v[q]; }
+    uint64_t ex = block_excl_scan(s, warp_tot, &tile_total);
+    uint64_t run = carry + ex;
+#pragma unroll
+    for (int q = 0; q < kItems; q++) { tile[threadIdx.x * kItems + q] = run; run += v[q]; }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < cnt; i += kT) out[t0 + i] = tile[i];
+    carry += tile_total;
+    __syncthreads();
+  }
+  if (blockIdx.x == G - 1 && threadIdx.x == 0) out[n] = partials[G];
+}
+
+template <typename Tin>
+int scan_impl(cpma* h, const Tin* in, uint64_t* out, uint64_t n_host, const ull* n_dev,
+              cudaStream_t st) {
+  uint64_t tiles = (n_host + kTile - 1) / kTile;
+  int G = (int)std::min<uint64_t>((uint64_t)2 * h->num_sms, std::max<uint64_t>(tiles, 1));
+  CPMA_TRY(ensure(h->s.partials, (size_t)(G + 1) * 8));
+  uint64_t* part = (uint64_t*)h->s.partials.p;
+  k_reduce<Tin><<<G, kT, 0, st>>>(in, n_host, n_dev, part);
+  k_partials<<<1, 1024, 0, st>>>(part, G);
+  k_down<Tin><<<G, kT, 0, st>>>(in, out, n_host, n_dev, part);
+  h->launches += 3;
+  return check_cuda(cudaGetLastError());
+}
+
+}  // namespace
+
+int scan_u32_to_u64(cpma* h, const uint32_t* in, uint64_t* out, uint64_t n_host,
+                    const ull* n_dev, cudaStream_t st) {
+  return scan_impl<uint32_t>(h, in, out, n_host, n_dev, st);
+}
+int scan_u8_to_u64(cpma* h, const uint8_t* in, uint64_t* out, uint64_t n_host,
+                   const ull* n_dev, cudaStream_t st) {
+  return scan_impl<uint8_t>(h, in, out, n_host, n_dev, st);
+}
+int scan_u64(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host, const ull* n_dev,
+             cudaStream_t st) {
+  return scan_impl<uint64_t>(h, in, out, n_host, n_dev, st);
+}
+
+}  // namespace cpmaimpl

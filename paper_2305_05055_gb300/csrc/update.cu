@@ -1,0 +1,1113 @@
+// Batch updates of the CPMA (Sec. 4 "Parallel Batch Updates in a PMA",
+// applied to compressed leaves as Sec. 5 prescribes), resize (Sec. 3
+// "Resizing a PMA") and the constructor (App. A).
+//
+// Phases of one batch, all on the caller's stream:
+//  1. sort the batch (sort.cu);
+//  2. route: every sorted key goes to the last leaf whose head-index entry is
+//     <= key; runs of equal leaf ids are the touched leaves, further split
+//     every kChunk keys into merge work items (one scan over packed flags);
+//  3. merge (warp per work item): decode the leaf, merge (insert: union with
+//     the repeat-free slice; delete: difference), count the new bytes.  A
+//     single-item leaf whose result fits is rewritten in place; otherwise the
+//     leaf is "pending" and its merged elements go to an overflow buffer
+//     (Sec. 4: "copies all elements into separate memory");
+//  4. counting (Sec. 4 "Counting phase"): every changed leaf that violates
+//     its own bound walks up the implicit tree over a prefix sum of the byte
+//     counts to the first node within bounds; distinct nodes are recorded in
+//     per-level bitsets and only nodes without a recorded ancestor are kept
+//     (maximal windows); a walk past the root requests a resize;
+//  5. redistribute (Sec. 4 "Redistribution phase"): pack the windows'
+//     elements into a buffer, compute byte costs and their prefix, place the
+//     byte-balanced cut points and re-encode every destination leaf.
+//     A resize is the same with the whole array as one window and L' leaves.
+#include <algorithm>
+
+#include "dev_common.cuh"
+#include "internal.h"
+
+using namespace cpmadev;
+
+namespace cpmaimpl {
+namespace {
+
+constexpr int kT = 256;
+
+struct Levels {
+  uint64_t off[kMaxLevels + 1];  // word offset of each level's bitset
+};
+
+__host__ __device__ __forceinline__ size_t merge_warp_bytes(uint32_t LB) {
+  // old[LB] + z[LB + kChunk] + sl[kChunk] + nk[kChunk] (u64) + buf[LB] bytes
+  return (size_t)8 * (2 * LB + 3 * kChunk) + LB;
+}
+
+__device__ __forceinline__ uint64_t gtid() {
+  return (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+}
+__device__ __forceinline__ uint64_t gstride() { return (uint64_t)gridDim.x * blockDim.x; }
+
+__device__ __forceinline__ bool bsearch_sm(const uint64_t* a, uint32_t n, uint64_t x) {
+  uint32_t i = (uint32_t)lower_bound(a, n, x);
+  return i < n && a[i] == x;
+}
+
+// ---------------------------------------------------------------------------
+// 2. routing
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kT) k_route_flags(const uint64_t* __restrict__ u, uint64_t k,
+                                                    const uint64_t* __restrict__ heads, uint64_t L,
+                                                    uint32_t* __restrict__ leaf_of,
+                                                    uint64_t* __restrict__ flags, Status* st) {
+  const unsigned lane = lane_id();
+  const uint64_t nthreads = gstride();
+  for (uint64_t base = gtid() - lane; base < k; base += nthreads) {
+    const uint64_t i = base + lane;
+    const bool valid = i < k;
+    const uint64_t x = valid ? u[i] : 0;
+    const uint32_t leaf = valid ? (uint32_t)route_leaf(heads, L, x) : 0u;
+    uint32_t prev = __shfl_up_sync(FULL, leaf, 1);
+    uint64_t px = __shfl_up_sync(FULL, x, 1);
+    if (lane == 0 && i > 0 && valid) {
+      px = u[i - 1];
+      prev = (uint32_t)route_leaf(heads, L, px);
+    }
+    if (valid) {
+      if (i > 0 && px > x) atomicOr(&st->err, kErrUnsorted);
+      const uint64_t run = (i == 0 || leaf != prev) ? 1u : 0u;
+      const uint64_t chunk = (run || (i % kChunk) == 0) ? 1u : 0u;
+      leaf_of[i] = leaf;
+      flags[i] = (run << 32) | chunk;
+    }
+  }
+}
+
+struct RouteOut {
+  uint32_t *chunk_begin, *chunk_leaf, *chunk_tid;
+  uint32_t *T_leaf, *T_begin, *T_first_chunk, *T_oldcnt, *T_oldused, *T_newcnt, *T_state;
+  ull* T_newbytes;
+};
+
+__global__ void __launch_bounds__(kT) k_route_scatter(uint64_t k, const uint32_t* __restrict__ leaf_of,
+                                                      const uint64_t* __restrict__ flags,
+                                                      const uint64_t* __restrict__ fscan,
+                                                      const uint32_t* __restrict__ cnt,
+                                                      const uint32_t* __restrict__ used, RouteOut o,
+                                                      Status* st) {
+  for (uint64_t i = gtid(); i < k; i += gstride()) {
+    const uint64_t f = flags[i], ex = fscan[i];
+    const uint32_t run = (uint32_t)(f >> 32), ch = (uint32_t)(f & 1u);
+    const uint32_t runs_before = (uint32_t)(ex >> 32), chunks_before = (uint32_t)ex;
+    const uint32_t t = runs_before + run - 1;
+    const uint32_t leaf = leaf_of[i];
+    if (ch) {
+      o.chunk_begin[chunks_before] = (uint32_t)i;
+      o.chunk_leaf[chunks_before] = leaf;
+      o.chunk_tid[chunks_before] = t;
+    }
+    if (run) {
+      o.T_leaf[t] = leaf;
+      o.T_begin[t] = (uint32_t)i;
+      o.T_first_chunk[t] = chunks_before;
+      o.T_oldcnt[t] = cnt[leaf];
+      o.T_oldused[t] = used[leaf];
+      o.T_newcnt[t] = 0;
+      o.T_newbytes[t] = 0;
+      o.T_state[t] = kUnchanged;
+    }
+    if (i == k - 1) {
+      const uint64_t tot = fscan[k];
+      const uint32_t nT = (uint32_t)(tot >> 32), nC = (uint32_t)tot;
+      st->nT = nT;
+      st->nchunks = nC;
+      o.T_begin[nT] = (uint32_t)k;
+      o.T_first_chunk[nT] = nC;
+      o.chunk_begin[nC] = (uint32_t)k;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. merge
+// ---------------------------------------------------------------------------
+struct MergeArgs {
+  const uint64_t* u;
+  uint8_t* data;
+  uint32_t* used;
+  uint32_t* cnt;
+  uint64_t* heads;
+  uint32_t LB;
+  const uint32_t *chunk_begin, *chunk_leaf, *chunk_tid;
+  uint32_t* chunk_cnt;
+  const uint64_t* chunk_off;
+  const uint32_t *T_begin, *T_oldcnt, *T_oldused;
+  uint32_t *T_newcnt, *T_state;
+  ull* T_newbytes;
+  uint64_t* ovf;
+  int is_delete;
+  Status* st;
+};
+
+// WRITE == false: count every work item, rewrite single-item leaves in place
+// when they fit.  WRITE == true: recompute the items of pending leaves and
+// store their merged elements in the overflow buffer.
+template <bool WRITE>
+__global__ void __launch_bounds__(kT) k_merge(MergeArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  if (a.st->err) return;
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const unsigned wpb = blockDim.x >> 5;
+  const uint32_t LB = a.LB;
+  uint64_t* old = reinterpret_cast<uint64_t*>(smem + (size_t)warp * merge_warp_bytes(LB));
+  uint64_t* z = old + LB;
+  uint64_t* sl = z + LB + kChunk;
+  uint64_t* nk = sl + kChunk;
+  uint8_t* buf = reinterpret_cast<uint8_t*>(nk + kChunk);
+  const uint64_t nch = a.st->nchunks;
+  for (uint64_t c = (uint64_t)blockIdx.x * wpb + warp; c < nch; c += (uint64_t)gridDim.x * wpb) {
+    const uint32_t t = a.chunk_tid[c];
+    if (WRITE && a.T_state[t] != kPending) continue;
+    const uint32_t j = a.chunk_leaf[c];
+    const uint32_t b = a.chunk_begin[c], e = a.chunk_begin[c + 1];
+    const uint32_t tb = a.T_begin[t], te = a.T_begin[t + 1];
+    const bool first = (b == tb), last = (e == te);
+    const uint32_t s = e - b;
+    const uint32_t uold = a.T_oldused[t], m = a.T_oldcnt[t];
+    uint8_t* leafp = a.data + (size_t)j * LB;
+    warp_decode(leafp, min(uold, LB), [&](uint32_t idx, uint64_t v) { old[idx] = v; });
+    for (uint32_t i = lane; i < s; i += 32) sl[i] = a.u[b + i];
+    __syncwarp();
+    const bool has_hi = !last;
+    const uint64_t hiv = has_hi ? a.u[e] : 0;
+    const uint64_t lov = sl[0];
+    const uint32_t oa = first ? 0u : (uint32_t)lower_bound(old, m, lov);
+    const uint32_t ob = has_hi ? (uint32_t)lower_bound(old, m, hiv) : m;
+    uint32_t r = 0;
+    if (!a.is_delete) {
+      uint32_t nn = 0;
+      for (uint32_t i0 = 0; i0 < s; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        bool keep = false;
+        uint64_t x = 0;
+        if (i < s) {
+          x = sl[i];
+          keep = (!has_hi || x < hiv) && (i == 0 || x != sl[i - 1]) && !bsearch_sm(old, m, x);
+        }
+        const unsigned bal = __ballot_sync(FULL, keep);
+        if (keep) nk[nn + __popc(bal & lanemask_lt())] = x;
+        nn += __popc(bal);
+      }
+      __syncwarp();
+      for (uint32_t q = oa + lane; q < ob; q += 32) {
+        const uint64_t x = old[q];
+        z[(q - oa) + (uint32_t)lower_bound(nk, nn, x)] = x;
+      }
+      for (uint32_t i = lane; i < nn; i += 32) {
+        const uint64_t x = nk[i];
+        z[i + (uint32_t)lower_bound(old + oa, ob - oa, x)] = x;
+      }
+      r = (ob - oa) + nn;
+    } else {
+      for (uint32_t q0 = oa; q0 < ob; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        bool keep = false;
+        uint64_t x = 0;
+        if (q < ob) {
+          x = old[q];
+          keep = !bsearch_sm(sl, s, x);
+        }
+        const unsigned bal = __ballot_sync(FULL, keep);
+        if (keep) z[r + __popc(bal & lanemask_lt())] = x;
+        r += __popc(bal);
+      }
+    }
+    __syncwarp();
+    // predecessor of z[0] in the whole merged leaf (items after the first)
+    bool has_pred = false;
+    uint64_t pred = 0;
+    if (!first) {
+      if (!a.is_delete) {
+        if (oa > 0) { pred = old[oa - 1]; has_pred = true; }
+        const uint64_t idx = lower_bound(a.u + tb, b - tb, lov);
+        if (idx > 0) {
+          const uint64_t x = a.u[tb + idx - 1];
+          if (!has_pred || x > pred) pred = x;
+          has_pred = true;
+        }
+      } else {
+        for (int64_t q0 = (int64_t)oa - 1; q0 >= 0 && !has_pred; q0 -= 32) {
+          const int64_t q = q0 - (int64_t)lane;
+          bool alive = false;
+          uint64_t x = 0;
+          if (q >= 0) {
+            x = old[q];
+            const uint64_t p = lower_bound(a.u + tb, b - tb, x);
+            alive = !(p < b - tb && a.u[tb + p] == x);
+          }
+          const unsigned bal = __ballot_sync(FULL, alive);
+          if (bal) {
+            pred = __shfl_sync(FULL, x, __ffs(bal) - 1);
+            has_pred = true;
+          }
+        }
+      }
+    }
+    uint32_t bsum = 0;
+    for (uint32_t i = lane; i < r; i += 32)
+      bsum += (i == 0) ? (has_pred ? leb_len(z[0] - pred) : 8u) : leb_len(z[i] - z[i - 1]);
+    bsum = warp_sum(bsum);
+    if (WRITE) {
+      const uint64_t off = a.chunk_off[c];
+      for (uint32_t i = lane; i < r; i += 32) a.ovf[off + i] = z[i];
+      __syncwarp();
+      continue;
+    }
+    const bool single = first && last;
+    if (single) {
+      if (r == m) {
+        if (lane == 0) {
+          a.T_state[t] = kUnchanged;
+          a.T_newcnt[t] = m;
+          a.T_newbytes[t] = uold;
+          a.chunk_cnt[c] = 0;
+        }
+      } else if (bsum <= LB) {
+        for (uint32_t p = lane * 16; p < LB; p += 512)
+          *reinterpret_cast<uint4*>(buf + p) = make_uint4(0u, 0u, 0u, 0u);
+        __syncwarp();
+        const uint32_t nb = warp_encode(z, r, buf);
+        const uint32_t wend = (max(uold, nb) + 15u) & ~15u;
+        for (uint32_t p = lane * 16; p < wend; p += 512)
+          *reinterpret_cast<uint4*>(leafp + p) = *reinterpret_cast<const uint4*>(buf + p);
+        if (lane == 0) {
+          a.used[j] = nb;
+          a.cnt[j] = r;
+          a.heads[j] = r ? z[0] : KEY_MAX;
+          a.T_state[t] = kInPlace;
+          a.T_newcnt[t] = r;
+          a.T_newbytes[t] = nb;
+          a.chunk_cnt[c] = 0;
+          if (nb != bsum) atomicOr(&a.st->err, kErrState);
+          if (r == 0) atomicAdd(&a.st->nempty, 1ull);
+        }
+      } else if (lane == 0) {
+        a.T_state[t] = kPending;
+        a.T_newcnt[t] = r;
+        a.T_newbytes[t] = bsum;
+        a.chunk_cnt[c] = r;
+      }
+    } else if (lane == 0) {
+      atomicAdd(&a.T_newcnt[t], r);
+      atomicAdd(&a.T_newbytes[t], (ull)bsum);
+      a.T_state[t] = kPending;
+      a.chunk_cnt[c] = r;
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 4. counting
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mark_node(uint32_t* bits, const Levels& lv, unsigned h, uint64_t a,
+                                          uint64_t* cand, Status* st) {
+  const uint64_t idx = a >> h;
+  uint32_t* w = bits + lv.off[h] + (idx >> 5);
+  const uint32_t bit = 1u << (idx & 31);
+  const uint32_t old = atomicOr(w, bit);
+  if (!(old & bit)) {
+    const ull c = atomicAdd(&st->ncand, 1ull);
+    cand[c] = ((uint64_t)h << 56) | a;
+  }
+}
+
+struct FinArgs {
+  uint32_t* used;
+  uint32_t* cnt;
+  const uint32_t *T_leaf, *T_first_chunk, *T_oldcnt, *T_newcnt;
+  uint32_t* T_state;
+  const ull* T_newbytes;
+  uint32_t* chunk_cnt;
+  uint32_t* viol;
+  uint64_t* cand;
+  uint32_t* bits;
+  Levels lv;
+  Bounds B;
+  unsigned H;
+  int is_delete;
+  Status* st;
+};
+
+__global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
+  if (a.st->err) return;
+  const uint64_t nT = a.st->nT;
+  for (uint64_t t = gtid(); t < nT; t += gstride()) {
+    const uint32_t state = a.T_state[t];
+    const uint32_t oldc = a.T_oldcnt[t], newc = a.T_newcnt[t];
+    const uint32_t j = a.T_leaf[t];
+    if (newc == oldc) {
+      if (state == kPending) {
+        a.T_state[t] = kUnchanged;
+        for (uint32_t c = a.T_first_chunk[t]; c < a.T_first_chunk[t + 1]; c++) a.chunk_cnt[c] = 0;
+      }
+      continue;
+    }
+    atomicAdd(&a.st->delta, (ull)(a.is_delete ? oldc - newc : newc - oldc));
+    const uint64_t nb = a.T_newbytes[t];
+    if (state == kPending) {
+      a.used[j] = (uint32_t)nb;
+      a.cnt[j] = newc;
+      atomicAdd(&a.st->npend, 1ull);
+    }
+    if (node_violates(a.B, a.H, 0, 1, nb)) {
+      const ull v = atomicAdd(&a.st->nviol, 1ull);
+      a.viol[v] = j;
+    } else if (state == kPending) {
+      mark_node(a.bits, a.lv, 0, j, a.cand, a.st);
+    }
+  }
+}
+
+__global__ void k_copy_total(const uint64_t* arr, const ull* n, ull* dst) { *dst = arr[*n]; }
+
+struct WalkArgs {
+  const uint32_t* viol;
+  const uint64_t* P;
+  uint64_t L;
+  uint32_t* bits;
+  uint64_t* cand;
+  Levels lv;
+  Bounds B;
+  unsigned H;
+  Status* st;
+};
+
+__global__ void __launch_bounds__(kT) k_walk(WalkArgs a) {
+  if (gtid() == 0) a.st->total_bytes = a.P[a.L];
+  const uint64_t nv = a.st->nviol;
+  for (uint64_t v = gtid(); v < nv; v += gstride()) {
+    const uint64_t j = a.viol[v];
+    bool done = false;
+    for (unsigned h = 1; h <= a.H && !done; h++) {
+      const uint64_t s = (j >> h) << h;
+      const uint64_t e = min(s + ((uint64_t)1 << h), a.L);
+      if (!node_violates(a.B, a.H, h, e - s, a.P[e] - a.P[s])) {
+        mark_node(a.bits, a.lv, h, s, a.cand, a.st);
+        done = true;
+      }
+    }
+    if (!done) a.st->resize = 1;
+  }
+}
+
+__global__ void __launch_bounds__(kT) k_maximal(const uint64_t* __restrict__ cand,
+                                                const uint32_t* __restrict__ bits, Levels lv,
+                                                unsigned H, uint64_t L, uint64_t* wins,
+                                                Status* st) {
+  if (st->resize) return;
+  const uint64_t nc = st->ncand;
+  for (uint64_t c = gtid(); c < nc; c += gstride()) {
+    const uint64_t v = cand[c];
+    const unsigned h = (unsigned)(v >> 56);
+    const uint64_t a = v & ((1ull << 56) - 1);
+    bool maximal = true;
+    for (unsigned h2 = h + 1; h2 <= H && maximal; h2++) {
+      const uint64_t idx = a >> h2;
+      if (bits[lv.off[h2] + (idx >> 5)] & (1u << (idx & 31))) maximal = false;
+    }
+    if (maximal) {
+      const uint64_t W = min((uint64_t)1 << h, L - a);
+      const ull w = atomicAdd(&st->nwin, 1ull);
+      wins[2 * w] = a;
+      wins[2 * w + 1] = W;
+      atomicAdd(&st->win_leaves, (ull)W);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kT) k_clear_bits(const uint64_t* __restrict__ cand,
+                                                   uint32_t* bits, Levels lv, Status* st) {
+  const uint64_t nc = st->ncand;
+  for (uint64_t c = gtid(); c < nc; c += gstride()) {
+    const uint64_t v = cand[c];
+    const unsigned h = (unsigned)(v >> 56);
+    const uint64_t idx = (v & ((1ull << 56) - 1)) >> h;
+    atomicAnd(bits + lv.off[h] + (idx >> 5), ~(1u << (idx & 31)));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 5. redistribution
+// ---------------------------------------------------------------------------
+// Windows: src leaves [sa, sa + sW) of the source arrays, dst leaves
+// [da, da + dW) of the destination arrays.  win_src holds (sa, sW) pairs,
+// win_dst (da, dW) pairs; leaf_off / dst_off are their exclusive prefix sums
+// of sW / dW; elem_off the element offsets (filled after the source counts).
+struct WinArgs {
+  const uint64_t* win_src;
+  const uint64_t* win_dst;
+  const uint64_t* leaf_off;
+  const uint64_t* dst_off;
+  uint64_t* elem_off;
+  uint64_t nwin;
+};
+
+__device__ __forceinline__ uint64_t find_seg(const uint64_t* off, uint64_t nseg, uint64_t x) {
+  // last s with off[s] <= x
+  return upper_count(off, nseg + 1, x) - 1;
+}
+
+__global__ void __launch_bounds__(kT) k_win_sizes(const uint64_t* __restrict__ wins, uint64_t nwin,
+                                                  uint64_t* __restrict__ sizes) {
+  for (uint64_t w = gtid(); w < nwin; w += gstride()) sizes[w] = wins[2 * w + 1];
+}
+
+__global__ void __launch_bounds__(kT) k_src_counts(WinArgs w, const uint32_t* __restrict__ cnt,
+                                                   uint64_t nsrc, uint32_t* __restrict__ srccnt) {
+  for (uint64_t f = gtid(); f < nsrc; f += gstride()) {
+    const uint64_t s = find_seg(w.leaf_off, w.nwin, f);
+    srccnt[f] = cnt[w.win_src[2 * s] + (f - w.leaf_off[s])];
+  }
+}
+
+__global__ void k_elem_offsets(WinArgs w, const uint64_t* __restrict__ srcoff, Status* st) {
+  for (uint64_t s = gtid(); s <= w.nwin; s += gstride()) w.elem_off[s] = srcoff[w.leaf_off[s]];
+  if (gtid() == 0) st->nelem = srcoff[w.leaf_off[w.nwin]];
+}
+
+struct UnpackArgs {
+  WinArgs w;
+  uint64_t nsrc;
+  const uint8_t* data;
+  const uint32_t* used;
+  const uint32_t* cnt;
+  uint32_t LB;
+  const uint64_t* srcoff;
+  // pending leaves of the current batch (sorted by leaf)
+  const uint32_t* T_leaf;
+  const uint32_t* T_state;
+  const uint32_t* T_first_chunk;
+  const uint64_t* chunk_off;
+  uint64_t nT;
+  const uint64_t* ovf;
+  uint64_t* E;
+  Status* st;
+};
+
+__global__ void __launch_bounds__(kT) k_unpack(UnpackArgs a) {
+  const unsigned lane = lane_id();
+  const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
+  for (uint64_t f = gw; f < a.nsrc; f += nw) {
+    const uint64_t s = find_seg(a.w.leaf_off, a.w.nwin, f);
+    const uint64_t j = a.w.win_src[2 * s] + (f - a.w.leaf_off[s]);
+    uint64_t* dst = a.E + a.srcoff[f];
+    bool pend = false;
+    uint64_t t = 0;
+    if (a.nT) {
+      t = lower_bound(a.T_leaf, a.nT, j);
+      pend = t < a.nT && a.T_leaf[t] == j && a.T_state[t] == kPending;
+    }
+    if (pend) {
+      const uint64_t off = a.chunk_off[a.T_first_chunk[t]];
+      const uint32_t m = a.cnt[j];
+      for (uint32_t i = lane; i < m; i += 32) dst[i] = a.ovf[off + i];
+    } else {
+      const uint32_t m = a.cnt[j];
+      const uint32_t got = warp_decode(a.data + j * a.LB, min(a.used[j], a.LB),
+                                       [&](uint32_t idx, uint64_t v) { if (idx < m) dst[idx] = v; });
+      if (lane == 0 && got != m) atomicOr(&a.st->err, kErrState);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kT) k_costs(WinArgs w, const uint64_t* __restrict__ E,
+                                              const ull* nelem, uint8_t* __restrict__ cost) {
+  const uint64_t n = *nelem;
+  for (uint64_t i = gtid(); i < n; i += gstride()) {
+    const uint64_t s = find_seg(w.elem_off, w.nwin, i);
+    cost[i] = (i == w.elem_off[s]) ? (uint8_t)8 : (uint8_t)leb_len(E[i] - E[i - 1]);
+  }
+}
+
+__global__ void __launch_bounds__(kT) k_starts(WinArgs w, const uint64_t* __restrict__ C,
+                                               uint64_t ndst, uint64_t* __restrict__ dstart) {
+  typedef unsigned __int128 u128;
+  for (uint64_t g = gtid(); g < ndst; g += gstride()) {
+    const uint64_t s = find_seg(w.dst_off, w.nwin, g);
+    const uint64_t wl = g - w.dst_off[s];
+    const uint64_t Wd = w.win_dst[2 * s + 1];
+    const uint64_t e0 = w.elem_off[s], e1 = w.elem_off[s + 1];
+    const uint64_t B = C[e0], S = C[e1] - B;
+    const uint64_t theta = (uint64_t)((u128)wl * S / Wd);
+    dstart[g] = e0 + lower_bound(C + e0, e1 - e0 + 1, B + theta);
+  }
+}
+
+struct EncodeArgs {
+  WinArgs w;
+  uint64_t ndst;
+  const uint64_t* dstart;
+  const uint64_t* E;
+  const uint64_t* C;
+  uint8_t* data;
+  uint32_t* used;
+  uint32_t* cnt;
+  uint64_t* heads;
+  uint32_t LB;
+  Status* st;
+};
+
+__global__ void __launch_bounds__(kT) k_encode(EncodeArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  uint8_t* buf = smem + (size_t)warp * a.LB;
+  const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
+  for (uint64_t g = gw; g < a.ndst; g += nw) {
+    const uint64_t s = find_seg(a.w.dst_off, a.w.nwin, g);
+    const uint64_t wl = g - a.w.dst_off[s];
+    const uint64_t Wd = a.w.win_dst[2 * s + 1];
+    const uint64_t j = a.w.win_dst[2 * s] + wl;
+    const uint64_t b = a.dstart[g];
+    const uint64_t e = (wl + 1 < Wd) ? a.dstart[g + 1] : a.w.elem_off[s + 1];
+    const uint32_t r = (uint32_t)(e - b);
+    // bytes: the first element becomes an 8-byte head
+    uint64_t nb = 0;
+    if (r) nb = a.C[e] - a.C[b + 1] + 8;
+    uint8_t* leafp = a.data + j * a.LB;
+    if (nb > a.LB) {
+      if (lane == 0) atomicOr(&a.st->err, kErrFit);
+      continue;
+    }
+    for (uint32_t p = lane * 16; p < a.LB; p += 512)
+      *reinterpret_cast<uint4*>(buf + p) = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    const uint32_t got = warp_encode(a.E + b, r, buf);
+    for (uint32_t p = lane * 16; p < a.LB; p += 512)
+      *reinterpret_cast<uint4*>(leafp + p) = *reinterpret_cast<const uint4*>(buf + p);
+    if (lane == 0) {
+      a.used[j] = got;
+      a.cnt[j] = r;
+      a.heads[j] = r ? a.E[b] : KEY_MAX;
+      if (got != nb) atomicOr(&a.st->err, kErrState);
+      if (r == 0) atomicAdd(&a.st->nempty, 1ull);
+    }
+    __syncwarp();
+  }
+}
+
+// Head index of empty leaves: the head of the next non-empty leaf, or
+// 2^64-1.  One block; each thread owns a contiguous segment.
+__global__ void __launch_bounds__(1024) k_fix_heads(const uint32_t* __restrict__ used,
+                                                    uint64_t* __restrict__ heads, uint64_t L,
+                                                    Status* st) {
+  __shared__ uint64_t segmin[1024];
+  __shared__ ull empties;
+  if (threadIdx.x == 0) empties = 0;
+  const uint64_t seg = (L + 1023) / 1024;
+  const uint64_t s0 = min(L, threadIdx.x * seg), s1 = min(L, s0 + seg);
+  uint64_t first = KEY_MAX;
+  ull ne = 0;
+  for (uint64_t j = s0; j < s1; j++) {
+    if (used[j]) { if (first == KEY_MAX) first = heads[j]; }
+    else ne++;
+  }
+  segmin[threadIdx.x] = first;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t nxt = KEY_MAX;
+    for (int t = 1023; t >= 0; t--) {
+      const uint64_t v = segmin[t];
+      segmin[t] = nxt;  // first non-empty head after segment t
+      if (v != KEY_MAX) nxt = v;
+    }
+  }
+  __syncthreads();
+  // a segment whose only non-empty heads equal KEY_MAX is handled by the
+  // backward walk below, which reads real heads
+  uint64_t nxt = segmin[threadIdx.x];
+  for (uint64_t j = s1; j-- > s0;) {
+    if (used[j]) nxt = heads[j];
+    else heads[j] = nxt;
+  }
+  atomicAdd(&empties, ne);
+  __syncthreads();
+  if (threadIdx.x == 0) st->empties = empties;
+}
+
+__global__ void k_set_window(uint64_t* win_src, uint64_t* win_dst, uint64_t* leaf_off,
+                             uint64_t* dst_off, uint64_t sa, uint64_t sW, uint64_t da,
+                             uint64_t dW) {
+  win_src[0] = sa; win_src[1] = sW;
+  win_dst[0] = da; win_dst[1] = dW;
+  leaf_off[0] = 0; leaf_off[1] = sW;
+  dst_off[0] = 0; dst_off[1] = dW;
+}
+
+template <typename T>
+T* P(Buf& b) { return reinterpret_cast<T*>(b.p); }
+
+int grid_for(const cpma* h, uint64_t work, int per_block = kT) {
+  uint64_t g = (work + per_block - 1) / per_block;
+  g = std::max<uint64_t>(1, std::min<uint64_t>(g, (uint64_t)h->num_sms * 8));
+  return (int)g;
+}
+
+Bounds bounds_of(const cpma* h) {
+  Bounds B;
+  B.LB = h->cfg.leaf_bytes;
+  B.tau_leaf = h->cfg.tau_leaf;
+  B.tau_root = h->cfg.tau_root;
+  B.rho_leaf = h->cfg.rho_leaf;
+  B.rho_root = h->cfg.rho_root;
+  return B;
+}
+
+Levels levels_of(uint64_t L, unsigned H, uint64_t* words) {
+  Levels lv;
+  uint64_t off = 0;
+  for (unsigned h = 0; h <= (unsigned)kMaxLevels; h++) {
+    lv.off[h] = off;
+    if (h <= H) {
+      const uint64_t nodes = (L + (1ull << h) - 1) >> h;
+      off += (nodes + 31) / 32;
+    }
+  }
+  *words = off;
+  return lv;
+}
+
+int ensure_bits(cpma* h, cudaStream_t st, Levels* lv) {
+  const unsigned H = ceil_log2(h->L);
+  uint64_t words = 0;
+  *lv = levels_of(h->L, H, &words);
+  if (words != h->bits_words) {
+    CPMA_TRY(ensure(h->s.bits, words * 4));
+    CPMA_CUDA(cudaMemsetAsync(h->s.bits.p, 0, words * 4, st));
+    h->bits_words = words;
+  }
+  return CPMA_OK;
+}
+
+struct Arrays {
+  uint8_t* data;
+  uint32_t* used;
+  uint32_t* cnt;
+  uint64_t* heads;
+};
+
+int alloc_arrays(uint64_t L, uint32_t LB, Arrays* a) {
+  *a = Arrays{nullptr, nullptr, nullptr, nullptr};
+  if (cudaMalloc(&a->data, L * LB) != cudaSuccess || cudaMalloc(&a->used, L * 4) != cudaSuccess ||
+      cudaMalloc(&a->cnt, L * 4) != cudaSuccess || cudaMalloc(&a->heads, L * 8) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(a->data); cudaFree(a->used); cudaFree(a->cnt); cudaFree(a->heads);
+    *a = Arrays{nullptr, nullptr, nullptr, nullptr};
+    return CPMA_ENOMEM;
+  }
+  return CPMA_OK;
+}
+
+void free_arrays(Arrays a) {
+  cudaFree(a.data); cudaFree(a.used); cudaFree(a.cnt); cudaFree(a.heads);
+}
+
+// Shared tail of every redistribution: costs over E, their prefix, cut points
+// and the encode into `dst`.  The window arrays and elem_off must be set;
+// nelem_dev points at the element count.
+int spread(cpma* h, cudaStream_t st, WinArgs w, uint64_t nelem_bound, const ull* nelem_dev,
+           uint64_t ndst, Arrays dst) {
+  CPMA_TRY(ensure(h->s.cost, nelem_bound + 1));
+  CPMA_TRY(ensure(h->s.C, (nelem_bound + 2) * 8));
+  CPMA_TRY(ensure(h->s.dstart, (ndst + 1) * 8));
+  k_costs<<<grid_for(h, nelem_bound), kT, 0, st>>>(w, P<uint64_t>(h->s.E), nelem_dev,
+                                                   P<uint8_t>(h->s.cost));
+  h->launches++;
+  CPMA_TRY(scan_u8_to_u64(h, P<uint8_t>(h->s.cost), P<uint64_t>(h->s.C), nelem_bound, nelem_dev,
+                          st));
+  k_starts<<<grid_for(h, ndst), kT, 0, st>>>(w, P<uint64_t>(h->s.C), ndst,
+                                             P<uint64_t>(h->s.dstart));
+  h->launches++;
+  EncodeArgs ea;
+  ea.w = w;
+  ea.ndst = ndst;
+  ea.dstart = P<uint64_t>(h->s.dstart);
+  ea.E = P<uint64_t>(h->s.E);
+  ea.C = P<uint64_t>(h->s.C);
+  ea.data = dst.data;
+  ea.used = dst.used;
+  ea.cnt = dst.cnt;
+  ea.heads = dst.heads;
+  ea.LB = h->cfg.leaf_bytes;
+  ea.st = h->d_status;
+  const size_t smem = (size_t)(kT / 32) * h->cfg.leaf_bytes;
+  k_encode<<<grid_for(h, ndst * 32), kT, smem, st>>>(ea);
+  h->launches++;
+  return check_cuda(cudaGetLastError());
+}
+
+WinArgs win_args(cpma* h, uint64_t nwin) {
+  WinArgs w;
+  w.win_src = P<uint64_t>(h->s.win_src);
+  w.win_dst = P<uint64_t>(h->s.win_dst);
+  w.leaf_off = P<uint64_t>(h->s.win_leaf_off);
+  w.dst_off = P<uint64_t>(h->s.win_dst_off);
+  w.elem_off = P<uint64_t>(h->s.win_elem_off);
+  w.nwin = nwin;
+  return w;
+}
+
+int ensure_win(cpma* h, uint64_t nwin) {
+  CPMA_TRY(ensure(h->s.win_src, (nwin + 1) * 16));
+  CPMA_TRY(ensure(h->s.win_dst, (nwin + 1) * 16));
+  CPMA_TRY(ensure(h->s.win_leaf_off, (nwin + 2) * 8));
+  CPMA_TRY(ensure(h->s.win_dst_off, (nwin + 2) * 8));
+  CPMA_TRY(ensure(h->s.win_elem_off, (nwin + 2) * 8));
+  return CPMA_OK;
+}
+
+// Pack the source windows into E (sources are the live arrays plus the
+// pending leaves of the current batch), then spread into dst.
+int redistribute(cpma* h, cudaStream_t st, uint64_t nwin, uint64_t nsrc, uint64_t ndst,
+                 uint64_t nelem_bound, uint64_t nT, Arrays dst) {
+  WinArgs w = win_args(h, nwin);
+  CPMA_TRY(ensure(h->s.srccnt, (nsrc + 1) * 4));
+  CPMA_TRY(ensure(h->s.srcoff, (nsrc + 2) * 8));
+  CPMA_TRY(ensure(h->s.E, (nelem_bound + 1) * 8));
+  k_src_counts<<<grid_for(h, nsrc), kT, 0, st>>>(w, h->cnt, nsrc, P<uint32_t>(h->s.srccnt));
+  h->launches++;
+  CPMA_TRY(scan_u32_to_u64(h, P<uint32_t>(h->s.srccnt), P<uint64_t>(h->s.srcoff), nsrc, nullptr,
+                           st));
+  k_elem_offsets<<<1, kT, 0, st>>>(w, P<uint64_t>(h->s.srcoff), h->d_status);
+  h->launches++;
+  UnpackArgs ua;
+  ua.w = w;
+  ua.nsrc = nsrc;
+  ua.data = h->data;
+  ua.used = h->used;
+  ua.cnt = h->cnt;
+  ua.LB = h->cfg.leaf_bytes;
+  ua.srcoff = P<uint64_t>(h->s.srcoff);
+  ua.T_leaf = P<uint32_t>(h->s.T_leaf);
+  ua.T_state = P<uint32_t>(h->s.T_state);
+  ua.T_first_chunk = P<uint32_t>(h->s.T_first_chunk);
+  ua.chunk_off = P<uint64_t>(h->s.chunk_off);
+  ua.nT = nT;
+  ua.ovf = P<uint64_t>(h->s.ovf);
+  ua.E = P<uint64_t>(h->s.E);
+  ua.st = h->d_status;
+  k_unpack<<<grid_for(h, nsrc * 32), kT, 0, st>>>(ua);
+  h->launches++;
+  CPMA_CUDA(cudaGetLastError());
+  return spread(h, st, w, nelem_bound, &h->d_status->nelem, ndst, dst);
+}
+
+int fix_heads(cpma* h, cudaStream_t st) {
+  k_fix_heads<<<1, 1024, 0, st>>>(h->used, h->heads, h->L, h->d_status);
+  h->launches++;
+  return check_cuda(cudaGetLastError());
+}
+
+// R9 of the readings: grow by grow_num/grow_den (rounded up) while the root
+// upper bound fails, shrink by the inverse (rounded down) while the root
+// lower bound fails and more than one leaf remains.
+uint64_t resize_target(const cpma_config& c, uint64_t T, uint64_t L) {
+  typedef unsigned __int128 u128;
+  uint64_t Lp = L;
+  if ((u128)T * 1000 > (u128)c.tau_root * Lp * c.leaf_bytes) {
+    while ((u128)T * 1000 > (u128)c.tau_root * Lp * c.leaf_bytes)
+      Lp = (uint64_t)(((u128)Lp * c.grow_num + c.grow_den - 1) / c.grow_den);
+  } else {
+    while (Lp > 1 && (u128)T * 1000 < (u128)c.rho_root * Lp * c.leaf_bytes) {
+      uint64_t nx = (uint64_t)((u128)Lp * c.grow_den / c.grow_num);
+      Lp = nx < 1 ? 1 : nx;
+    }
+  }
+  return Lp;
+}
+
+int do_resize(cpma* h, cudaStream_t st, uint64_t T, uint64_t n_after, uint64_t nT) {
+  const uint64_t Lp = resize_target(h->cfg, T, h->L);
+  Arrays na;
+  CPMA_TRY(alloc_arrays(Lp, h->cfg.leaf_bytes, &na));
+  int rc = ensure_win(h, 1);
+  if (rc != CPMA_OK) { free_arrays(na); return rc; }
+  k_set_window<<<1, 1, 0, st>>>(P<uint64_t>(h->s.win_src), P<uint64_t>(h->s.win_dst),
+                                P<uint64_t>(h->s.win_leaf_off), P<uint64_t>(h->s.win_dst_off), 0,
+                                h->L, 0, Lp);
+  h->launches++;
+  rc = redistribute(h, st, 1, h->L, Lp, n_after, nT, na);
+  if (rc != CPMA_OK) { free_arrays(na); return rc; }
+  rc = check_cuda(cudaStreamSynchronize(st));
+  if (rc != CPMA_OK) return rc;
+  free_arrays(Arrays{h->data, h->used, h->cnt, h->heads});
+  h->data = na.data; h->used = na.used; h->cnt = na.cnt; h->heads = na.heads;
+  h->L = Lp;
+  return CPMA_OK;
+}
+
+}  // namespace
+
+int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_delete,
+               uint64_t* d_delta, cudaStream_t st) {
+  Status* ds = h->d_status;
+  if (k == 0) {
+    if (d_delta) CPMA_CUDA(cudaMemsetAsync(d_delta, 0, 8, st));
+    return CPMA_OK;
+  }
+  if (k >= (1ull << 31)) return CPMA_EINVAL;
+  CPMA_CUDA(cudaMemsetAsync(ds, 0, offsetof(Status, empties), st));
+  const uint64_t* u = d_keys;
+  if (!sorted) CPMA_TRY(sort_keys(h, d_keys, k, &u, st));
+  if (u == d_keys && !sorted) {
+    // k <= 1: nothing to sort
+  }
+  // ---- scratch (all before any change to the structure) ----
+  Scratch& s = h->s;
+  CPMA_TRY(ensure(s.leaf_of, k * 4));
+  CPMA_TRY(ensure(s.flags, k * 8));
+  CPMA_TRY(ensure(s.flags_scan, (k + 1) * 8));
+  for (Buf* b : {&s.chunk_begin, &s.chunk_leaf, &s.chunk_tid, &s.chunk_cnt, &s.T_leaf, &s.T_begin,
+                 &s.T_first_chunk, &s.T_oldcnt, &s.T_oldused, &s.T_newcnt, &s.T_state, &s.viol})
+    CPMA_TRY(ensure(*b, (k + 2) * 4));
+  CPMA_TRY(ensure(s.chunk_off, (k + 2) * 8));
+  CPMA_TRY(ensure(s.T_newbytes, (k + 2) * 8));
+  CPMA_TRY(ensure(s.cand, (2 * k + 2) * 8));
+  CPMA_TRY(ensure(s.wins, (2 * k + 2) * 16));
+  CPMA_TRY(ensure(s.prefix, (h->L + 2) * 8));
+  Levels lv;
+  CPMA_TRY(ensure_bits(h, st, &lv));
+  const unsigned H = ceil_log2(h->L);
+  const Bounds B = bounds_of(h);
+  const uint32_t LB = h->cfg.leaf_bytes;
+
+  // ---- route ----
+  k_route_flags<<<grid_for(h, k), kT, 0, st>>>(u, k, h->heads, h->L, P<uint32_t>(s.leaf_of),
+                                               P<uint64_t>(s.flags), ds);
+  h->launches++;
+  CPMA_TRY(scan_u64(h, P<uint64_t>(s.flags), P<uint64_t>(s.flags_scan), k, nullptr, st));
+  RouteOut ro;
+  ro.chunk_begin = P<uint32_t>(s.chunk_begin);
+  ro.chunk_leaf = P<uint32_t>(s.chunk_leaf);
+  ro.chunk_tid = P<uint32_t>(s.chunk_tid);
+  ro.T_leaf = P<uint32_t>(s.T_leaf);
+  ro.T_begin = P<uint32_t>(s.T_begin);
+  ro.T_first_chunk = P<uint32_t>(s.T_first_chunk);
+  ro.T_oldcnt = P<uint32_t>(s.T_oldcnt);
+  ro.T_oldused = P<uint32_t>(s.T_oldused);
+  ro.T_newcnt = P<uint32_t>(s.T_newcnt);
+  ro.T_state = P<uint32_t>(s.T_state);
+  ro.T_newbytes = P<ull>(s.T_newbytes);
+  k_route_scatter<<<grid_for(h, k), kT, 0, st>>>(k, P<uint32_t>(s.leaf_of), P<uint64_t>(s.flags),
+                                                 P<uint64_t>(s.flags_scan), h->cnt, h->used, ro,
+                                                 ds);
+  h->launches++;
+
+  // ---- merge (count; in-place rewrites) ----
+  MergeArgs ma;
+  ma.u = u;
+  ma.data = h->data;
+  ma.used = h->used;
+  ma.cnt = h->cnt;
+  ma.heads = h->heads;
+  ma.LB = LB;
+  ma.chunk_begin = ro.chunk_begin;
+  ma.chunk_leaf = ro.chunk_leaf;
+  ma.chunk_tid = ro.chunk_tid;
+  ma.chunk_cnt = P<uint32_t>(s.chunk_cnt);
+  ma.chunk_off = P<uint64_t>(s.chunk_off);
+  ma.T_begin = ro.T_begin;
+  ma.T_oldcnt = ro.T_oldcnt;
+  ma.T_oldused = ro.T_oldused;
+  ma.T_newcnt = ro.T_newcnt;
+  ma.T_state = ro.T_state;
+  ma.T_newbytes = ro.T_newbytes;
+  ma.ovf = nullptr;
+  ma.is_delete = is_delete;
+  ma.st = ds;
+  const size_t per = merge_warp_bytes(LB);
+  const int mwarps = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));
+  const size_t msmem = per * mwarps;
+  static bool attr_done = false;
+  if (!attr_done) {
+    CPMA_CUDA(cudaFuncSetAttribute(k_merge<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   200 * 1024));
+    CPMA_CUDA(cudaFuncSetAttribute(k_merge<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   200 * 1024));
+    attr_done = true;
+  }
+  const int mgrid = (int)std::max<uint64_t>(
+      1, std::min<uint64_t>((k + kChunk + mwarps - 1) / mwarps, (uint64_t)h->num_sms * 4));
+  k_merge<false><<<mgrid, mwarps * 32, msmem, st>>>(ma);
+  h->launches++;
+  CPMA_CUDA(cudaGetLastError());
+
+  FinArgs fa;
+  fa.used = h->used;
+  fa.cnt = h->cnt;
+  fa.T_leaf = ro.T_leaf;
+  fa.T_first_chunk = ro.T_first_chunk;
+  fa.T_oldcnt = ro.T_oldcnt;
+  fa.T_newcnt = ro.T_newcnt;
+  fa.T_state = ro.T_state;
+  fa.T_newbytes = ro.T_newbytes;
+  fa.chunk_cnt = ma.chunk_cnt;
+  fa.viol = P<uint32_t>(s.viol);
+  fa.cand = P<uint64_t>(s.cand);
+  fa.bits = P<uint32_t>(s.bits);
+  fa.lv = lv;
+  fa.B = B;
+  fa.H = H;
+  fa.is_delete = is_delete;
+  fa.st = ds;
+  k_finalize<<<grid_for(h, k), kT, 0, st>>>(fa);
+  h->launches++;
+  CPMA_TRY(scan_u32_to_u64(h, ma.chunk_cnt, P<uint64_t>(s.chunk_off), k + 1, &ds->nchunks, st));
+  k_copy_total<<<1, 1, 0, st>>>(P<uint64_t>(s.chunk_off), &ds->nchunks, &ds->novf);
+  h->launches++;
+  CPMA_CUDA(cudaGetLastError());
+  CPMA_TRY(sync_status(h, st));
+  Status hs = *h->h_status;
+  if (hs.err & kErrUnsorted) return CPMA_EINVAL;
+  if (hs.err) return CPMA_EINTERNAL;
+  const uint64_t delta = hs.delta;
+  const uint64_t n_after = is_delete ? h->n - delta : h->n + delta;
+  if (hs.nempty || hs.empties) h->may_have_empty = true;
+
+  // ---- pending leaves: materialise their merged elements ----
+  if (hs.npend) {
+    CPMA_TRY(ensure(s.ovf, (hs.novf + 1) * 8));
+    ma.ovf = P<uint64_t>(s.ovf);
+    k_merge<true><<<mgrid, mwarps * 32, msmem, st>>>(ma);
+    h->launches++;
+    CPMA_CUDA(cudaGetLastError());
+  }
+
+  // ---- counting ----
+  bool resized = false;
+  if (hs.nviol || hs.npend) {
+    if (hs.nviol) {
+      CPMA_TRY(scan_u32_to_u64(h, h->used, P<uint64_t>(s.prefix), h->L, nullptr, st));
+      WalkArgs wa;
+      wa.viol = fa.viol;
+      wa.P = P<uint64_t>(s.prefix);
+      wa.L = h->L;
+      wa.bits = fa.bits;
+      wa.cand = fa.cand;
+      wa.lv = lv;
+      wa.B = B;
+      wa.H = H;
+      wa.st = ds;
+      k_walk<<<grid_for(h, hs.nviol), kT, 0, st>>>(wa);
+      h->launches++;
+    }
+    const uint64_t ncand_bound = hs.nviol + hs.npend + 1;
+    k_maximal<<<grid_for(h, ncand_bound), kT, 0, st>>>(fa.cand, fa.bits, lv, H, h->L,
+                                                       P<uint64_t>(s.wins), ds);
+    k_clear_bits<<<grid_for(h, ncand_bound), kT, 0, st>>>(fa.cand, fa.bits, lv, ds);
+    h->launches += 2;
+    CPMA_CUDA(cudaGetLastError());
+    CPMA_TRY(sync_status(h, st));
+    hs = *h->h_status;
+    if (hs.err) return CPMA_EINTERNAL;
+    if (hs.resize) {
+      CPMA_TRY(do_resize(h, st, hs.total_bytes, n_after, hs.nT));
+      resized = true;
+    } else if (hs.nwin) {
+      const uint64_t nwin = hs.nwin;
+      CPMA_TRY(ensure_win(h, nwin));
+      // windows in place: destination = source
+      CPMA_CUDA(cudaMemcpyAsync(s.win_src.p, s.wins.p, nwin * 16, cudaMemcpyDeviceToDevice, st));
+      CPMA_CUDA(cudaMemcpyAsync(s.win_dst.p, s.wins.p, nwin * 16, cudaMemcpyDeviceToDevice, st));
+      k_win_sizes<<<grid_for(h, nwin), kT, 0, st>>>(P<uint64_t>(s.wins), nwin,
+                                                    P<uint64_t>(s.prefix));
+      h->launches++;
+      CPMA_TRY(scan_u64(h, P<uint64_t>(s.prefix), P<uint64_t>(s.win_leaf_off), nwin, nullptr, st));
+      CPMA_CUDA(cudaMemcpyAsync(s.win_dst_off.p, s.win_leaf_off.p, (nwin + 1) * 8,
+                                cudaMemcpyDeviceToDevice, st));
+      Arrays cur{h->data, h->used, h->cnt, h->heads};
+      CPMA_TRY(redistribute(h, st, nwin, hs.win_leaves, hs.win_leaves, n_after, hs.nT, cur));
+    }
+  }
+  if (resized) {
+    Levels lv2;
+    CPMA_TRY(ensure_bits(h, st, &lv2));
+    h->may_have_empty = true;
+  }
+  if (h->may_have_empty) CPMA_TRY(fix_heads(h, st));
+  h->n = n_after;
+  if (d_delta)
+    CPMA_CUDA(cudaMemcpyAsync(d_delta, &ds->delta, 8, cudaMemcpyDeviceToDevice, st));
+  CPMA_CUDA(cudaGetLastError());
+  return CPMA_OK;
+}
+
+// App. A constructor over sorted distinct keys E[0..n) (already in the E
+// scratch buffer): L = max(1, ceil(1000 S / (build_pm LB - 8000))) leaves for
+// a stream of S bytes, then one byte-balanced spread.
+int build_from_sorted_unique(cpma* h, const uint64_t* E, uint64_t n, cudaStream_t st) {
+  typedef unsigned __int128 u128;
+  const uint32_t LB = h->cfg.leaf_bytes;
+  Scratch& s = h->s;
+  CPMA_TRY(ensure_win(h, 1));
+  CPMA_TRY(ensure(s.cost, n + 1));
+  CPMA_TRY(ensure(s.C, (n + 2) * 8));
+  if (E != P<uint64_t>(s.E)) return CPMA_EINTERNAL;
+  // costs and stream bytes (one window, no source leaves)
+  k_set_window<<<1, 1, 0, st>>>(P<uint64_t>(s.win_src), P<uint64_t>(s.win_dst),
+                                P<uint64_t>(s.win_leaf_off), P<uint64_t>(s.win_dst_off), 0, 0, 0,
+                                1);
+  h->launches++;
+  uint64_t eo[2] = {0, n};
+  CPMA_CUDA(cudaMemcpyAsync(s.win_elem_off.p, eo, 16, cudaMemcpyHostToDevice, st));
+  CPMA_CUDA(cudaMemcpyAsync(&h->d_status->nelem, &n, 8, cudaMemcpyHostToDevice, st));
+  WinArgs w = win_args(h, 1);
+  k_costs<<<grid_for(h, n), kT, 0, st>>>(w, E, &h->d_status->nelem, P<uint8_t>(s.cost));
+  h->launches++;
+  CPMA_TRY(scan_u8_to_u64(h, P<uint8_t>(s.cost), P<uint64_t>(s.C), n, nullptr, st));
+  CPMA_CUDA(cudaMemcpyAsync(&h->d_status->stream_bytes, P<uint64_t>(s.C) + n, 8,
+                            cudaMemcpyDeviceToDevice, st));
+  CPMA_TRY(sync_status(h, st));
+  const uint64_t S = h->h_status->stream_bytes;
+  const u128 num = (u128)S * 1000, den = (u128)h->cfg.build_pm * LB - 8000;
+  uint64_t L = (uint64_t)((num + den - 1) / den);
+  if (L < 1) L = 1;
+  Arrays na;
+  CPMA_TRY(alloc_arrays(L, LB, &na));
+  k_set_window<<<1, 1, 0, st>>>(P<uint64_t>(s.win_src), P<uint64_t>(s.win_dst),
+                                P<uint64_t>(s.win_leaf_off), P<uint64_t>(s.win_dst_off), 0, 0, 0,
+                                L);
+  h->launches++;
+  CPMA_TRY(ensure(s.dstart, (L + 1) * 8));
+  k_starts<<<grid_for(h, L), kT, 0, st>>>(w, P<uint64_t>(s.C), L, P<uint64_t>(s.dstart));
+  h->launches++;
+  EncodeArgs ea;
+  ea.w = w;
+  ea.ndst = L;
+  ea.dstart = P<uint64_t>(s.dstart);
+  ea.E = E;
+  ea.C = P<uint64_t>(s.C);
+  ea.data = na.data;
+  ea.used = na.used;
+  ea.cnt = na.cnt;
+  ea.heads = na.heads;
+  ea.LB = LB;
+  ea.st = h->d_status;
+  k_encode<<<grid_for(h, L * 32), kT, (size_t)(kT / 32) * LB, st>>>(ea);
+  h->launches++;
+  CPMA_CUDA(cudaGetLastError());
+  CPMA_CUDA(cudaStreamSynchronize(st));
+  if (h->data) free_arrays(Arrays{h->data, h->used, h->cnt, h->heads});
+  h->data = na.data; h->used = na.used; h->cnt = na.cnt; h->heads = na.heads;
+  h->L = L;
+  h->n = n;
+  Levels lv;
+  CPMA_TRY(ensure_bits(h, st, &lv));
+  h->may_have_empty = true;
+  CPMA_TRY(fix_heads(h, st));
+  CPMA_TRY(sync_status(h, st));
+  if (h->h_status->err) return CPMA_EINTERNAL;
+  h->may_have_empty = h->h_status->empties > 0;
+  return CPMA_OK;
+}
+
+}  // namespace cpmaimpl

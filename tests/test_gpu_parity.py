@@ -1,0 +1,218 @@
+"""GPU parity: every C-ABI call against the CPU oracle on the same seeded
+inputs, bit for bit (all of this work is integer).  Set-level answers are
+compared with the plain definition (PlainSet); the byte layout (leaf bytes,
+used counts, head index, leaf count, get_size) with the sequential CPMA."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2305_05055_gb300 import cpma as cp
+from paper_2305_05055_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+M64 = (1 << 64) - 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    cp.lib()
+    yield
+    torch.cuda.synchronize()
+
+
+def T(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.uint64))
+    return torch.from_numpy(a.view(np.int64)).cuda()
+
+
+def same_layout(g, o):
+    assert g.leaves() == o.leaves()
+    data, used, heads = g.layout()
+    od, ou, oh = o.layout()
+    gu = used.cpu().numpy().view(np.uint32)
+    gh = cp.to_u64(heads)
+    if not np.array_equal(gu, ou):
+        bad = np.nonzero(gu != ou)[0][:10]
+        raise AssertionError("used differs at leaves %s: gpu %s oracle %s" % (bad, gu[bad], ou[bad]))
+    assert np.array_equal(gh, oh), np.nonzero(gh != oh)[0][:10]
+    gd = data.cpu().numpy()
+    if not np.array_equal(gd, od):
+        LB = g.config.leaf_bytes
+        bad = np.unique(np.nonzero(gd != od)[0] // LB)[:10]
+        raise AssertionError("leaf bytes differ in leaves %s" % bad)
+    assert g.size() == o.size()
+    assert g.bytes() == o.bytes()
+
+
+def same_queries(g, p, seed, nq=400):
+    S = p.S
+    q = np.concatenate([W.uniform_keys(seed, nq, bits=40), S[:: max(1, S.size // nq)][:nq],
+                        np.array([0, 1, M64, M64 - 1], np.uint64)])
+    assert np.array_equal(g.has_batch(T(q)).cpu().numpy(), p.has_batch(q))
+    lo, hi = W.range_queries_fixed_width(seed + 1, nq, 1 << 28)
+    if S.size:
+        lo2, hi2, _ = W.range_queries_by_rank(S, seed + 2, nq, 1, max(2, S.size // 3))
+        lo, hi = np.concatenate([lo, lo2]), np.concatenate([hi, hi2])
+    lo = np.concatenate([lo, np.array([0, 5, M64, 0, 7], np.uint64)])
+    hi = np.concatenate([hi, np.array([M64, 5, M64, 1, 3], np.uint64)])
+    s, c = g.range_map(T(lo), T(hi))
+    ws, wc = p.range_map(lo, hi)
+    assert np.array_equal(cp.to_u64(c), wc)
+    assert np.array_equal(cp.to_u64(s), ws)
+    s, c = g.sum()
+    assert int(cp.to_u64(s)[0]) == p.sum() and int(c.item()) == len(p)
+
+
+@pytest.mark.parametrize("LB", [256, 512, 1024, 2048])
+@pytest.mark.parametrize("n,bits", [(0, 40), (1, 40), (7, 64), (5000, 40), (70000, 40),
+                                    (70000, 64), (4096, 40), (4097, 40)])
+def test_build_layout(LB, n, bits):
+    keys = W.uniform_keys(11 + n, n, bits=bits) if bits < 64 else W.full_range_keys(11 + n, n)
+    keys = np.concatenate([keys, keys[: n // 5]])  # repeats
+    g = cp.CPMA(T(keys) if keys.size else None, leaf_bytes=LB)
+    o = oracle.SeqCPMA(keys, leaf_bytes=LB)
+    same_layout(g, o)
+    same_queries(g, oracle.PlainSet(keys), 5 + n)
+
+
+@pytest.mark.parametrize("LB", [256, 512, 2048])
+def test_update_sequence(LB):
+    rng = np.random.default_rng(LB)
+    base = W.uniform_keys(21, 30000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=LB)
+    o = oracle.SeqCPMA(base, leaf_bytes=LB)
+    p = oracle.PlainSet(base)
+    for r in range(24):
+        kind = r % 6
+        if kind == 0:
+            keys = W.uniform_keys(100 + r, int(rng.choice([1, 50, 3000, 20000])), bits=40)
+            keys = np.concatenate([keys, keys[: keys.size // 3]])
+        elif kind == 1:
+            keys = W.zipf_keys(200 + r, 20000, bits=34)          # hot leaves, huge slices
+        elif kind == 2:
+            keys = np.sort(W.uniform_keys(300 + r, 5000, bits=40))  # pre-sorted
+        elif kind == 3:
+            keys = np.concatenate([W.sample_present(p.S, 400 + r, 4000),
+                                   W.uniform_keys(500 + r, 1000, bits=40)])
+        elif kind == 4:
+            keys = W.sample_present(p.S, 600 + r, len(p) // 2)   # big delete: shrink
+        else:
+            keys = W.full_range_keys(700 + r, 3000)
+        is_del = kind in (3, 4)
+        srt = kind == 2
+        if is_del:
+            got = int(g.delete_batch(T(keys), sorted=srt).item())
+            assert got == o.delete_batch(keys) == p.delete_batch(keys)
+        else:
+            got = int(g.insert_batch(T(keys), sorted=srt).item())
+            assert got == o.insert_batch(keys) == p.insert_batch(keys)
+        assert o.check() == 0
+        same_layout(g, o)
+        if r % 4 == 3:
+            same_queries(g, p, 900 + r, 200)
+
+
+def test_grow_from_empty_and_delete_everything():
+    g = cp.CPMA(None, leaf_bytes=256)
+    o = oracle.SeqCPMA([], leaf_bytes=256)
+    p = oracle.PlainSet([])
+    same_layout(g, o)
+    for r in range(6):
+        keys = W.uniform_keys(40 + r, 3000 * (r + 1), bits=40)
+        assert int(g.insert_batch(T(keys)).item()) == o.insert_batch(keys) == p.insert_batch(keys)
+        same_layout(g, o)
+    same_queries(g, p, 77)
+    allk = p.S.copy()
+    assert int(g.delete_batch(T(allk)).item()) == o.delete_batch(allk) == p.delete_batch(allk)
+    same_layout(g, o)
+    assert g.size() == 0 and g.leaves() == 1
+    same_queries(g, p, 78)
+
+
+def test_extreme_keys():
+    g = cp.CPMA(None, leaf_bytes=256)
+    o = oracle.SeqCPMA([], leaf_bytes=256)
+    p = oracle.PlainSet([])
+    for keys in ([M64, 0, M64], [1, M64 - 1, 1 << 63], list(range(2, 600)),
+                 [M64 - i for i in range(2, 400)]):
+        assert int(g.insert_batch(T(keys)).item()) == o.insert_batch(keys) == p.insert_batch(keys)
+        same_layout(g, o)
+        same_queries(g, p, 3)
+    keys = [0, M64, 5, 7]
+    assert int(g.delete_batch(T(keys)).item()) == o.delete_batch(keys) == p.delete_batch(keys)
+    same_layout(g, o)
+    same_queries(g, p, 4)
+
+
+def test_single_key_batches_and_duplicates():
+    base = W.uniform_keys(31, 8000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=512)
+    o = oracle.SeqCPMA(base, leaf_bytes=512)
+    for i in range(20):
+        k = [int(W.uniform_keys(1000 + i, 1, bits=40)[0])]
+        assert int(g.insert_batch(T(k)).item()) == o.insert_batch(k)
+        k = [int(base[i * 7])] * 9000                  # one key repeated: sort copy path
+        assert int(g.delete_batch(T(k)).item()) == o.delete_batch(k)
+    same_layout(g, o)
+
+
+def test_sorted_flag_rejects_unsorted_batch():
+    base = W.uniform_keys(41, 5000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=512)
+    before = [t.cpu().clone() for t in g.layout()]
+    keys = W.uniform_keys(42, 3000, bits=40)             # not sorted
+    with pytest.raises(cp.CPMAError) as e:
+        g.insert_batch(T(keys), sorted=True)
+    assert e.value.code == cp.CPMA_EINVAL
+    after = [t.cpu() for t in g.layout()]
+    assert all(torch.equal(a, b) for a, b in zip(before, after))
+    assert g.size() == len(oracle.PlainSet(base))
+
+
+def test_clone_is_independent():
+    base = W.uniform_keys(51, 20000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=512)
+    h = g.clone()
+    o = oracle.SeqCPMA(base, leaf_bytes=512)
+    ins = W.uniform_keys(52, 5000, bits=40)
+    h.insert_batch(T(ins))
+    same_layout(g, o)
+    o.insert_batch(ins)
+    same_layout(h, o)
+
+
+def test_config_plain_cpma():
+    """uint64 keys uniform in [0, 2^40) from seed 1: build from 2^20 keys, one
+    batch insert of 10^4 keys, one batch delete of 10^3 existing keys, then
+    1000 range_map sums over [lo, lo + 2^24) with lo uniform."""
+    base = W.uniform_keys(1, 1 << 20, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=512)
+    o = oracle.SeqCPMA(base, leaf_bytes=512)
+    p = oracle.PlainSet(base)
+    same_layout(g, o)
+    ins = W.uniform_keys(2, 10 ** 4, bits=40)
+    assert int(g.insert_batch(T(ins)).item()) == o.insert_batch(ins) == p.insert_batch(ins)
+    same_layout(g, o)
+    dele = W.sample_present(p.S, 3, 10 ** 3)
+    assert int(g.delete_batch(T(dele)).item()) == o.delete_batch(dele) == p.delete_batch(dele)
+    same_layout(g, o)
+    lo, hi = W.range_queries_fixed_width(4, 1000, 1 << 24)
+    s, c = g.range_map(T(lo), T(hi))
+    ws, wc = p.range_map(lo, hi)
+    assert np.array_equal(cp.to_u64(s), ws) and np.array_equal(cp.to_u64(c), wc)
+    os_, oc = o.range_map(lo, hi)
+    assert np.array_equal(os_, ws) and np.array_equal(oc, wc)
+    same_queries(g, p, 9)
+
+
+def test_many_uneven_ranges_one_launch():
+    base = W.uniform_keys(61, 300000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=512)
+    p = oracle.PlainSet(base)
+    lo, hi, _ = W.range_queries_by_rank(p.S, 62, 20000, 1, 200000)
+    s, c = g.range_map(T(lo), T(hi))
+    ws, wc = p.range_map(lo, hi)
+    assert np.array_equal(cp.to_u64(c), wc)
+    assert np.array_equal(cp.to_u64(s), ws)
