@@ -1,0 +1,443 @@
+#!/usr/bin/env python
+"""Benchmark of the GPU CPMA hot path on GB300.
+
+Headline (the timed K steps): batch insert into a CPMA holding 1e8 uniform
+40-bit keys, one step = one cpma_insert_batch of 1e6 fresh uniform 40-bit keys
+(unsorted, repeats allowed), so the set grows by about 1e6 per step as in the
+paper's protocol (start at 1e8, add batches).  value = inserted keys / device
+time of the K steps (CUDA events on the stream, max over ranks).
+
+After the timed region the same run measures, with CUDA events, the other rows
+of the hot path on the same structure: batch delete of 1e6 present keys,
+has_batch of 1e6 keys, range_map of 1e5 queries whose widths are log-uniform
+between 10 and 1e6 elements (one launch), and a full-set scan sum; each with
+its algorithmic bytes and achieved fraction of the measured HBM bandwidth.
+
+--impl reference times the CPU oracle (oracle/, single thread) on a bounded
+sample of the same workload.  Several GPUs: independent replicas, one per
+rank, no collective on the data path (the timing uses a barrier and a max).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import platform
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "batch-insert keys/s, range-sum elems/s at n=1e8 (% HBM peak); serve p99 ms"
+PAPER_INSERT_1E6 = 1.1e8  # Table batch-ins-del, uniform, batch 1e6, 64-core Xeon (context)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=float, default=1e8)
+    ap.add_argument("--batch", type=float, default=1e6)
+    ap.add_argument("--leaf-bytes", type=int, default=512)
+    ap.add_argument("--queries", type=float, default=1e5)
+    ap.add_argument("--no-extra", action="store_true", help="headline only")
+    ap.add_argument("--sweep", action="store_true", help="insert/delete sweep 1e3..1e7")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_info():
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                model = line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return model, os.cpu_count()
+
+
+def oracle_insert_sample(seconds=12.0, n_sample=10 ** 7, k_sample=10 ** 5, steps=None):
+    """The sequential oracle CPMA (oracle/, one thread) on a bounded sample of
+    the workload: n = 1e7 uniform 40-bit keys, batches of 1e5 (the same 1%
+    batch-to-set ratio as 1e6 into 1e8)."""
+    import oracle
+    from paper_2305_05055_gb300 import workloads as W
+    o = oracle.SeqCPMA(W.uniform_keys(2, n_sample, bits=40), leaf_bytes=512)
+    done, t_tot, i = 0, 0.0, 0
+    while (steps is None and t_tot < seconds) or (steps is not None and i < steps):
+        b = W.uniform_keys(5000 + i, k_sample, bits=40)
+        t0 = time.perf_counter()
+        o.insert_batch(b)
+        t_tot += time.perf_counter() - t0
+        done += k_sample
+        i += 1
+    model, _ = cpu_info()
+    return {"value": done / t_tot, "unit": "keys/s", "cores": 1, "kind": "oracle",
+            "sample": "sequential oracle CPMA of 1e7 uniform 40-bit keys, %d batch inserts of "
+                      "1e5 keys (same 1%% batch/set ratio), LB=512; cpu %s" % (i, model),
+            "seconds": t_tot}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2305_05055_gb300 import workloads as W
+    oracle.build()
+    n_s, k_s = 10 ** 7, 10 ** 5
+    o = oracle.SeqCPMA(W.uniform_keys(2, n_s, bits=40), leaf_bytes=a.leaf_bytes)
+    for i in range(a.warmup):
+        o.insert_batch(W.uniform_keys(7000 + i, k_s, bits=40))
+    times = []
+    for i in range(a.steps):
+        b = W.uniform_keys(8000 + i, k_s, bits=40)
+        t0 = time.perf_counter()
+        o.insert_batch(b)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    v = a.steps * k_s / tot
+    model, ncpu = cpu_info()
+    sample = ("sequential oracle CPMA (one thread) of 1e7 uniform 40-bit keys, one batch insert "
+              "of 1e5 fresh keys per step (the 1%% batch/set ratio of 1e6 into 1e8); cpu %s" % model)
+    line = {"metric": METRIC, "value": v, "unit": "keys/s", "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": v / PAPER_INSERT_1E6, "dtype": "u64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "batch insert into a CPMA of uniform 40-bit keys "
+                                   "(bounded CPU sample: n=1e7, batch=1e5)",
+                       "n": n_s, "batch": k_s, "leaf_bytes": a.leaf_bytes},
+            "cpu_baseline": {"value": v, "unit": "keys/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "keys/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+
+    import torch
+    from paper_2305_05055_gb300 import cpma as cp
+    from paper_2305_05055_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    st = torch.cuda.current_stream()
+    hbm_peak, peak_kind = peaks()
+    n, k = int(a.n), int(a.batch)
+    nsteps, nwarm = a.steps, a.warmup
+
+    def T(x):
+        return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).to(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- build (inputs resident in HBM before anything is timed) ----
+    base = T(W.uniform_keys(2 + 1000 * rank, n, bits=40))
+    t0 = time.perf_counter()
+    g = cp.CPMA(base, leaf_bytes=a.leaf_bytes)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    batches = [T(W.uniform_keys(10 ** 6 + 1000 * rank + i, k, bits=40))
+               for i in range(nwarm + nsteps)]
+    for i in range(nwarm):
+        g.insert_batch(batches[i])
+    torch.cuda.synchronize()
+    ref = g.clone()          # same state, for the end-to-end pass
+    torch.cuda.synchronize()
+
+    # ---- timed region: K insert steps ----
+    g.profile(True)
+    l0 = g.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        e0.record(st)
+        for i in range(nsteps):
+            g.insert_batch(batches[nwarm + i])
+        e1.record(st)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    launches = g.launches() - l0
+    prof = g.profile_read()
+    g.profile(False)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nsteps * k / (ms / 1e3)
+
+    # roofline of the dominant kernel of the step
+    upd = ["sort", "route", "merge", "count", "redistribute", "finish"]
+    dom = max(upd, key=lambda p: prof[p]["ms"])
+    def roof(p, pk=hbm_peak):
+        msp, by, calls = prof[p]["ms"], prof[p]["bytes"], max(1, prof[p]["calls"])
+        ach = by / (msp / 1e3) / 1e9 if msp > 0 else 0.0
+        return {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
+                "frac": ach / pk, "traffic": None, "kernel": p,
+                "ms_per_launch": msp / calls, "bytes_per_launch": by / calls,
+                "peak_kind": peak_kind}
+    roofline = roof(dom)
+    phases = {p: {"ms_per_step": prof[p]["ms"] / nsteps,
+                  "gbs": (prof[p]["bytes"] / (prof[p]["ms"] / 1e3) / 1e9) if prof[p]["ms"] else None}
+              for p in upd}
+
+    # ---- end to end through the public API with host buffers ----
+    host_batches = [batches[nwarm + i].cpu().pin_memory() for i in range(nsteps)]
+    added_h = torch.empty(1, dtype=torch.int64).pin_memory()
+    dbuf = torch.empty(k, dtype=torch.int64, device=dev)
+    added_d = torch.empty(1, dtype=torch.int64, device=dev)
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(nsteps):
+        dbuf.copy_(host_batches[i], non_blocking=True)
+        cp.cpma_insert_batch(ref.handle, dbuf, False, added_d)
+        added_h.copy_(added_d, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * nsteps * k / e2e_s, "unit": "keys/s",
+           "h2d_bytes_per_step": 8 * k, "d2h_bytes_per_step": 8}
+    del ref
+
+    extra = {}
+    if not a.no_extra and rank == 0:
+        extra = measure_extra(a, g, batches[nwarm:], dev, st, hbm_peak, peak_kind, T)
+
+    cpu_base = None
+    if not a.no_cpu_baseline and rank == 0:
+        try:
+            cpu_base = oracle_insert_sample()
+        except Exception as ex:  # the oracle is optional for the GPU number
+            cpu_base = {"error": str(ex)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world, "steps": nsteps,
+        "warmup": nwarm, "ms_per_step": ms / nsteps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_INSERT_1E6, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "batch insert of 1e6 uniform 40-bit keys into a CPMA holding "
+                               "1e8 keys (grows by 1e6 per step)",
+                   "n": n, "batch": k, "leaf_bytes": a.leaf_bytes,
+                   "l2": "inputs larger than L2 (CPMA %.2f GB, fresh 8 MB batch per step)"
+                         % (g.bytes() / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roofline, "cpu_baseline": cpu_base, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk.summary(), "phases": phases,
+        "build_s": build_s, "bytes_per_key": g.bytes() / g.size(), "size": g.size(),
+    }
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
+    import torch
+    from paper_2305_05055_gb300 import cpma as cp
+    from paper_2305_05055_gb300 import workloads as W
+    out = {}
+
+    def timed(fn, reps=1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(reps):
+            r = fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, r
+
+    def roof(prof, p):
+        msp, by, calls = prof[p]["ms"], prof[p]["bytes"], max(1, prof[p]["calls"])
+        ach = by / (msp / 1e3) / 1e9 if msp > 0 else 0.0
+        return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "kernel": p, "ms_per_launch": msp / calls,
+                "bytes_per_launch": by / calls, "peak_kind": peak_kind}
+
+    # range_map: 1e5 queries by rank, widths log-uniform 10..1e6 elements
+    q = int(a.queries)
+    S = torch.empty(0)
+    n_now = g.size()
+    # sorted set on the device (torch) only to place query endpoints
+    lay_d, lay_u, lay_h = None, None, None
+    allk = torch.cat([T(W.uniform_keys(2, int(a.n), bits=40))] + list(ins_batches))
+    S = torch.unique(allk)
+    del allk
+    r = torch.from_numpy((W.splitmix64(33, q) % np.uint64(S.numel())).astype(np.int64)).to(dev)
+    u = W.uniform01(34, q)
+    c = torch.from_numpy(np.floor(10.0 ** (1 + 5 * u)).astype(np.int64)).to(dev)
+    lo = S[r]
+    j = r + c
+    hi = torch.where(j < S.numel(), S[torch.clamp(j, max=S.numel() - 1)],
+                     torch.full_like(lo, -1))
+    g.profile(True)
+    ms, (s, cnt) = timed(lambda: g.range_map(lo, hi), reps=3)
+    prof = g.profile_read()
+    g.profile(False)
+    elems = int(cnt.sum().item())
+    out["range_map"] = {"metric": "range-sum elems/s", "value": elems / (ms / 1e3),
+                        "unit": "elems/s", "queries": q, "elements": elems,
+                        "ms_per_call": ms, "roofline": roof(prof, "range"),
+                        "note": "widths log-uniform 10..1e6 elements; overlapping queries may "
+                                "hit in L2, so algorithmic GB/s can exceed HBM"}
+    # full-set scan
+    g.profile(True)
+    ms, (s, cnt) = timed(lambda: g.sum(), reps=5)
+    prof = g.profile_read()
+    g.profile(False)
+    out["full_scan"] = {"value": int(cnt.item()) / (ms / 1e3), "unit": "elems/s",
+                        "ms_per_call": ms, "roofline": roof(prof, "sum")}
+    # has_batch: half present keys
+    hq = torch.cat([S[torch.randint(0, S.numel(), (500000,), device=dev,
+                                    generator=torch.Generator(device=dev).manual_seed(5))],
+                    T(W.uniform_keys(35, 500000, bits=40))])
+    g.profile(True)
+    ms, found = timed(lambda: g.has_batch(hq), reps=3)
+    prof = g.profile_read()
+    g.profile(False)
+    out["has"] = {"value": hq.numel() / (ms / 1e3), "unit": "keys/s", "ms_per_call": ms,
+                  "found": int(found.sum().item()), "roofline": roof(prof, "has")}
+    del S
+    # delete of present keys (the batches inserted by the timed steps)
+    g.profile(True)
+    tot = 0.0
+    removed = 0
+    for b in ins_batches[: min(5, len(ins_batches))]:
+        ms, rm = timed(lambda: g.delete_batch(b))
+        tot += ms
+        removed += int(rm.item())
+    prof = g.profile_read()
+    g.profile(False)
+    upd = ["sort", "route", "merge", "count", "redistribute", "finish"]
+    dom = max(upd, key=lambda p: prof[p]["ms"])
+    out["delete"] = {"value": removed / (tot / 1e3), "unit": "keys/s",
+                     "batches": min(5, len(ins_batches)), "batch": int(a.batch),
+                     "roofline": roof(prof, dom),
+                     "phases_ms": {p: prof[p]["ms"] for p in upd}}
+    if a.sweep:
+        out["sweep"] = sweep(a, g, dev, T, timed)
+    return out
+
+
+def sweep(a, g, dev, T, timed):
+    import torch
+    from paper_2305_05055_gb300 import workloads as W
+    rows = []
+    for kk in (10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7):
+        ins_ms, del_ms = [], []
+        for trial in range(3):
+            c = g.clone()
+            b = T(W.uniform_keys(3 * 10 ** 7 + 100 * trial + kk % 97, kk, bits=40))
+            c.insert_batch(b)  # warm
+            c2 = g.clone()
+            torch.cuda.synchronize()
+            ms, added = timed(lambda: c2.insert_batch(b))
+            ins_ms.append(ms)
+            ms, rm = timed(lambda: c2.delete_batch(b))
+            del_ms.append(ms)
+            del c, c2
+        rows.append({"batch": kk, "insert_keys_per_s": kk / (statistics.median(ins_ms) / 1e3),
+                     "delete_keys_per_s": kk / (statistics.median(del_ms) / 1e3),
+                     "insert_ms": statistics.median(ins_ms), "delete_ms": statistics.median(del_ms)})
+    return rows
+
+
+if __name__ == "__main__":
+    sys.exit(main())

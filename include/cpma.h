@@ -150,6 +150,19 @@ int cpma_export_layout(const cpma_t* h, uint8_t* d_data, uint32_t* d_used,
 int cpma_stats(const cpma_t* h, uint64_t* launches);
 int cpma_reset_stats(cpma_t* h);
 
+/* Optional per-phase device timing for profiling.  cpma_profile(h, 1) resets
+ * and enables it (synchronising the device); the library then records CUDA
+ * events around each phase on the caller's stream, resolved at the host
+ * synchronisations the update calls already make, and counts each phase's
+ * algorithmic bytes (what the method must read and write).  Phases, in
+ * order: 0 sort, 1 route, 2 merge, 3 counting (incl. overflow write),
+ * 4 redistribute/resize, 5 finish (head fix-up), 6 has, 7 range routing +
+ * scan, 8 range scan of the leaves, 9 sum.  cpma_profile_read synchronises
+ * the device and copies up to nphases entries (any pointer may be NULL). */
+#define CPMA_NPHASES 10
+int cpma_profile(cpma_t* h, int enable);
+int cpma_profile_read(cpma_t* h, double* ms, uint64_t* bytes, uint64_t* calls, int nphases);
+
 /* Text for an error code. */
 const char* cpma_strerror(int code);
 

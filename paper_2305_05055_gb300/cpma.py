@@ -69,6 +69,8 @@ def lib():
                 "cpma_stats": (I, [V, P64]),
                 "cpma_reset_stats": (I, [V]),
                 "cpma_strerror": (C.c_char_p, [I]),
+                "cpma_profile": (I, [V, I]),
+                "cpma_profile_read": (I, [V, C.POINTER(C.c_double), P64, P64, I]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -206,6 +208,24 @@ def cpma_reset_stats(h):
     _check(lib().cpma_reset_stats(h), "cpma_reset_stats")
 
 
+PHASES = ("sort", "route", "merge", "count", "redistribute", "finish", "has",
+          "range_prep", "range", "sum")
+
+
+def cpma_profile(h, enable: bool = True):
+    _check(lib().cpma_profile(h, int(bool(enable))), "cpma_profile")
+
+
+def cpma_profile_read(h) -> dict:
+    n = len(PHASES)
+    ms = (C.c_double * n)()
+    by = (C.c_uint64 * n)()
+    ca = (C.c_uint64 * n)()
+    _check(lib().cpma_profile_read(h, ms, by, ca, n), "cpma_profile_read")
+    return {p: dict(ms=float(ms[i]), bytes=int(by[i]), calls=int(ca[i]))
+            for i, p in enumerate(PHASES)}
+
+
 def cpma_export_layout(h, leaf_bytes: int, stream=None, device="cuda"):
     L = cpma_leaves(h)
     data = torch.empty(L * leaf_bytes, dtype=torch.uint8, device=device)
@@ -277,3 +297,9 @@ class CPMA:
 
     def launches(self) -> int:
         return cpma_stats(self._h)
+
+    def profile(self, enable: bool = True):
+        cpma_profile(self._h, enable)
+
+    def profile_read(self) -> dict:
+        return cpma_profile_read(self._h)

@@ -47,7 +47,75 @@ void release(Buf& b) {
 int sync_status(cpma* h, cudaStream_t st) {
   CPMA_CUDA(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(Status), cudaMemcpyDeviceToHost, st));
   CPMA_CUDA(cudaStreamSynchronize(st));
+  prof_resolve(h);
   return CPMA_OK;
+}
+
+namespace {
+cudaEvent_t take_event(Prof& p) {
+  if (p.npool > 0) return p.pool[--p.npool];
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return e;
+}
+void give_event(Prof& p, cudaEvent_t e) {
+  if (!e) return;
+  if (p.npool == p.pool_cap) {
+    int nc = p.pool_cap ? 2 * p.pool_cap : 64;
+    cudaEvent_t* np = new cudaEvent_t[nc];
+    for (int i = 0; i < p.npool; i++) np[i] = p.pool[i];
+    delete[] p.pool;
+    p.pool = np;
+    p.pool_cap = nc;
+  }
+  p.pool[p.npool++] = e;
+}
+}  // namespace
+
+void prof_begin(const cpma* hc, int phase, cudaStream_t st) {
+  cpma* h = const_cast<cpma*>(hc);
+  Prof& p = h->prof;
+  if (!p.on) return;
+  if (p.open_rec.phase >= 0) prof_end(h, st);
+  p.open_rec.phase = phase;
+  p.open_rec.a = take_event(p);
+  p.open_rec.b = take_event(p);
+  if (p.open_rec.a) cudaEventRecord(p.open_rec.a, st);
+}
+
+void prof_end(const cpma* hc, cudaStream_t st) {
+  cpma* h = const_cast<cpma*>(hc);
+  Prof& p = h->prof;
+  if (!p.on || p.open_rec.phase < 0) return;
+  if (p.open_rec.b) cudaEventRecord(p.open_rec.b, st);
+  if (p.npending == p.cap) {
+    int nc = p.cap ? 2 * p.cap : 64;
+    Prof::Rec* np = new Prof::Rec[nc];
+    for (int i = 0; i < p.npending; i++) np[i] = p.pending[i];
+    delete[] p.pending;
+    p.pending = np;
+    p.cap = nc;
+  }
+  p.pending[p.npending++] = p.open_rec;
+  p.open_rec.phase = -1;
+}
+
+void prof_resolve(const cpma* hc) {
+  cpma* h = const_cast<cpma*>(hc);
+  Prof& p = h->prof;
+  for (int i = 0; i < p.npending; i++) {
+    Prof::Rec& r = p.pending[i];
+    float ms = 0.f;
+    if (r.a && r.b && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      p.ms[r.phase] += ms;
+      p.calls[r.phase]++;
+    } else {
+      cudaGetLastError();
+    }
+    give_event(p, r.a);
+    give_event(p, r.b);
+  }
+  p.npending = 0;
 }
 
 }  // namespace cpmaimpl
@@ -81,6 +149,15 @@ void release_all(cpma* h) {
   cudaFree(h->heads);
   cudaFree(h->d_status);
   if (h->h_status) cudaFreeHost(h->h_status);
+  prof_resolve(h);
+  for (int i = 0; i < h->prof.npool; i++) cudaEventDestroy(h->prof.pool[i]);
+  delete[] h->prof.pool;
+  delete[] h->prof.pending;
+  h->prof.pool = nullptr;
+  h->prof.pending = nullptr;
+  h->prof.npool = h->prof.pool_cap = h->prof.npending = h->prof.cap = 0;
+  if (h->prof.d_bytes) cudaFree(h->prof.d_bytes);
+  h->prof.d_bytes = nullptr;
   h->data = nullptr;
   h->used = nullptr;
   h->cnt = nullptr;
@@ -279,6 +356,39 @@ int cpma_stats(const cpma_t* h, uint64_t* launches) {
 int cpma_reset_stats(cpma_t* h) {
   if (!h) return CPMA_EINVAL;
   h->launches = 0;
+  return CPMA_OK;
+}
+
+int cpma_profile(cpma_t* h, int enable) {
+  if (!h) return CPMA_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return CPMA_ECUDA;
+  prof_resolve(h);
+  Prof& p = h->prof;
+  if (!p.d_bytes) {
+    if (cudaMalloc(&p.d_bytes, sizeof(unsigned long long) * PH_N) != cudaSuccess) {
+      cudaGetLastError();
+      p.d_bytes = nullptr;
+      return CPMA_ENOMEM;
+    }
+  }
+  CPMA_CUDA(cudaMemset(p.d_bytes, 0, sizeof(unsigned long long) * PH_N));
+  for (int i = 0; i < PH_N; i++) { p.ms[i] = 0; p.calls[i] = 0; p.host_bytes[i] = 0; }
+  p.on = enable != 0;
+  return CPMA_OK;
+}
+
+int cpma_profile_read(cpma_t* h, double* ms, uint64_t* bytes, uint64_t* calls, int nphases) {
+  if (!h || nphases < 0) return CPMA_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return CPMA_ECUDA;
+  prof_resolve(h);
+  unsigned long long db[PH_N] = {0};
+  if (h->prof.d_bytes)
+    CPMA_CUDA(cudaMemcpy(db, h->prof.d_bytes, sizeof(db), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < nphases && i < PH_N; i++) {
+    if (ms) ms[i] = h->prof.ms[i];
+    if (bytes) bytes[i] = db[i] + h->prof.host_bytes[i];
+    if (calls) calls[i] = h->prof.calls[i];
+  }
   return CPMA_OK;
 }
 

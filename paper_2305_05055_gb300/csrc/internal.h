@@ -72,6 +72,28 @@ struct Scratch {
   Buf q_first, q_items, q_off; // range queries
 };
 
+// Profiling phases (cpma_profile_read order).
+enum Phase {
+  PH_SORT = 0, PH_ROUTE, PH_MERGE, PH_COUNT, PH_REDIST, PH_FINISH,
+  PH_HAS, PH_RANGE_PREP, PH_RANGE, PH_SUM, PH_N
+};
+
+// Optional per-phase device timing: event pairs recorded around each phase
+// and resolved at the next host synchronisation, so profiling adds no waits.
+struct Prof {
+  bool on = false;
+  struct Rec { int phase; cudaEvent_t a, b; };
+  Rec open_rec{-1, nullptr, nullptr};
+  Rec* pending = nullptr;
+  int npending = 0, cap = 0;
+  cudaEvent_t* pool = nullptr;
+  int npool = 0, pool_cap = 0;
+  double ms[PH_N] = {0};
+  unsigned long long calls[PH_N] = {0};
+  unsigned long long* d_bytes = nullptr;  // device: algorithmic bytes per phase
+  unsigned long long host_bytes[PH_N] = {0};  // bytes known on the host
+};
+
 }  // namespace cpmaimpl
 
 struct cpma {
@@ -90,6 +112,7 @@ struct cpma {
   cpmaimpl::Status* h_status = nullptr;  // pinned
   cpmaimpl::Scratch s;
   uint64_t launches = 0;
+  cpmaimpl::Prof prof;
 };
 
 namespace cpmaimpl {
@@ -127,6 +150,17 @@ int run_sum(const cpma* h, uint64_t* sum, uint64_t* count, cudaStream_t st);
 
 int check_cuda(cudaError_t e);
 int sync_status(cpma* h, cudaStream_t st);
+
+// profiling (no-ops unless enabled)
+void prof_begin(const cpma* h, int phase, cudaStream_t st);
+void prof_end(const cpma* h, cudaStream_t st);
+void prof_resolve(const cpma* h);  // call only after the stream is idle
+inline void prof_add_bytes(const cpma* h, int phase, unsigned long long b) {
+  if (h->prof.on) const_cast<cpma*>(h)->prof.host_bytes[phase] += b;
+}
+inline unsigned long long* prof_bytes(const cpma* h, int phase) {
+  return h->prof.on ? h->prof.d_bytes + phase : nullptr;
+}
 
 inline unsigned ceil_log2(uint64_t L) {
   unsigned H = 0;

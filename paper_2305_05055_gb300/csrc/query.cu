@@ -31,17 +31,22 @@ __global__ void __launch_bounds__(kT) k_has(const uint64_t* __restrict__ keys, u
                                             const uint8_t* __restrict__ data,
                                             const uint32_t* __restrict__ used,
                                             const uint64_t* __restrict__ heads, uint64_t L,
-                                            uint32_t LB, uint8_t* __restrict__ out) {
+                                            uint32_t LB, uint8_t* __restrict__ out,
+                                            ull* prof) {
   const unsigned lane = lane_id();
   const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
+  ull nbytes = 0;
   for (uint64_t i = gw; i < q; i += nw) {
     const uint64_t x = keys[i];
     const uint64_t j = route_leaf(heads, L, x);
     bool found = false;
-    warp_decode(data + j * LB, min(used[j], LB), [&](uint32_t, uint64_t v) { found |= (v == x); });
+    const uint32_t u = min(used[j], LB);
+    warp_decode(data + j * LB, u, [&](uint32_t, uint64_t v) { found |= (v == x); });
     found = __any_sync(FULL, found);
     if (lane == 0) out[i] = found ? 1 : 0;
+    nbytes += u + 9;  // leaf bytes, key in, answer out
   }
+  if (prof && lane == 0 && nbytes) atomicAdd(prof, nbytes);
 }
 
 __global__ void __launch_bounds__(kT) k_range_prep(const uint64_t* __restrict__ lo,
@@ -77,6 +82,7 @@ struct RangeArgs {
   uint32_t LB;
   uint64_t* sum;
   uint64_t* count;
+  ull* prof;  // profiling: leaf bytes scanned (nullable)
 };
 
 __global__ void __launch_bounds__(kT) k_range(RangeArgs a) {
@@ -87,6 +93,7 @@ __global__ void __launch_bounds__(kT) k_range(RangeArgs a) {
   if (g0 >= g1) return;
   uint64_t qi = upper_count(a.off, a.q + 1, g0) - 1;
   uint64_t s = 0, c = 0;
+  ull nbytes = 0;
   uint64_t qend = a.off[qi + 1];
   uint64_t lo = a.lo[qi], hi = a.hi[qi], fl = a.first[qi], qoff = a.off[qi];
   for (uint64_t g = g0; g < g1; g++) {
@@ -107,11 +114,13 @@ __global__ void __launch_bounds__(kT) k_range(RangeArgs a) {
     const uint64_t j = fl + li;
     const uint8_t* leaf = a.data + j * a.LB;
     const bool interior = li > 0 && g + 1 < qend;
+    const uint32_t u = min(a.used[j], a.LB);
+    nbytes += u;
     if (interior) {
-      warp_decode(leaf, min(a.used[j], a.LB), [&](uint32_t, uint64_t v) { s += v; });
+      warp_decode(leaf, u, [&](uint32_t, uint64_t v) { s += v; });
       if (lane == 0) c += a.cnt[j];
     } else {
-      warp_decode(leaf, min(a.used[j], a.LB), [&](uint32_t, uint64_t v) {
+      warp_decode(leaf, u, [&](uint32_t, uint64_t v) {
         if (v >= lo && v < hi) { s += v; c++; }
       });
     }
@@ -122,20 +131,26 @@ __global__ void __launch_bounds__(kT) k_range(RangeArgs a) {
     atomicAdd((ull*)&a.sum[qi], (ull)s);
     atomicAdd((ull*)&a.count[qi], (ull)c);
   }
+  if (a.prof && lane == 0 && nbytes) atomicAdd(a.prof, nbytes);
 }
 
 __global__ void __launch_bounds__(kT) k_sum(const uint8_t* __restrict__ data,
                                             const uint32_t* __restrict__ used,
                                             const uint32_t* __restrict__ cnt, uint64_t L,
-                                            uint32_t LB, uint64_t* sum, uint64_t* count) {
+                                            uint32_t LB, uint64_t* sum, uint64_t* count,
+                                            ull* prof) {
   const unsigned lane = lane_id();
   const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
   const uint64_t j0 = L * gw / nw, j1 = L * (gw + 1) / nw;
   uint64_t s = 0, c = 0;
+  ull nbytes = 0;
   for (uint64_t j = j0; j < j1; j++) {
-    warp_decode(data + j * LB, min(used[j], LB), [&](uint32_t, uint64_t v) { s += v; });
+    const uint32_t u = min(used[j], LB);
+    warp_decode(data + j * LB, u, [&](uint32_t, uint64_t v) { s += v; });
     if (lane == 0) c += cnt[j];
+    nbytes += u + 8;  // leaf bytes + used/count entries
   }
+  if (prof && lane == 0 && nbytes) atomicAdd(prof, nbytes);
   s = warp_sum(s);
   c = warp_sum(c);
   if (lane == 0 && (s | c)) {
@@ -152,9 +167,11 @@ int run_has(const cpma* h, const uint64_t* d_keys, uint64_t q, uint8_t* d_out, c
   if (q == 0) return CPMA_OK;
   const int grid = (int)std::max<uint64_t>(
       1, std::min<uint64_t>((q * 32 + kT - 1) / kT, (uint64_t)persistent_grid(h)));
+  prof_begin(h, PH_HAS, st);
   k_has<<<grid, kT, 0, st>>>(d_keys, q, h->data, h->used, h->heads, h->L, h->cfg.leaf_bytes,
-                             d_out);
+                             d_out, prof_bytes(h, PH_HAS));
   CPMA_LAUNCHED(h);
+  prof_end(h, st);
   return check_cuda(cudaGetLastError());
 }
 
@@ -170,9 +187,12 @@ int run_range(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q,
   uint64_t* off = (uint64_t*)hm->s.q_off.p;
   const int g1 = (int)std::max<uint64_t>(
       1, std::min<uint64_t>((q + kT - 1) / kT, (uint64_t)h->num_sms * 8));
+  prof_begin(h, PH_RANGE_PREP, st);
+  prof_add_bytes(h, PH_RANGE_PREP, 72ull * q);  // lo, hi in; first, items, sums out; scan
   k_range_prep<<<g1, kT, 0, st>>>(lo, hi, q, h->heads, h->L, first, items, sum, count);
   CPMA_LAUNCHED(h);
   CPMA_TRY(scan_u64(hm, items, off, q, nullptr, st));
+  prof_end(h, st);
   RangeArgs a;
   a.lo = lo;
   a.hi = hi;
@@ -185,17 +205,22 @@ int run_range(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q,
   a.LB = h->cfg.leaf_bytes;
   a.sum = sum;
   a.count = count;
+  a.prof = prof_bytes(h, PH_RANGE);
+  prof_begin(h, PH_RANGE, st);
   k_range<<<persistent_grid(h), kT, 0, st>>>(a);
   CPMA_LAUNCHED(h);
+  prof_end(h, st);
   return check_cuda(cudaGetLastError());
 }
 
 int run_sum(const cpma* h, uint64_t* sum, uint64_t* count, cudaStream_t st) {
   CPMA_CUDA(cudaMemsetAsync(sum, 0, 8, st));
   if (count) CPMA_CUDA(cudaMemsetAsync(count, 0, 8, st));
+  prof_begin(h, PH_SUM, st);
   k_sum<<<persistent_grid(h), kT, 0, st>>>(h->data, h->used, h->cnt, h->L, h->cfg.leaf_bytes, sum,
-                                           count);
+                                           count, prof_bytes(h, PH_SUM));
   CPMA_LAUNCHED(h);
+  prof_end(h, st);
   return check_cuda(cudaGetLastError());
 }
 

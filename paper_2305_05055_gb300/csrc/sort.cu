@@ -228,6 +228,7 @@ int sort_keys(cpma* h, const uint64_t* d_in, uint64_t k, const uint64_t** out,
     attr_done = true;
   }
   if (k <= (uint64_t)kTile) {
+    prof_add_bytes(h, PH_SORT, 16ull * k);
     k_sort_small<<<1, kT, smem, st>>>(d_in, A, (uint32_t)k);
     h->launches++;
     *out = A;
@@ -249,8 +250,11 @@ int sort_keys(cpma* h, const uint64_t* d_in, uint64_t k, const uint64_t** out,
   uint64_t* hoff = (uint64_t*)h->s.hoff.p;
   const uint64_t* src = d_in;
   uint64_t* dst = A;
+  prof_add_bytes(h, PH_SORT, 8ull * k);  // the OR/AND pass
   for (int p = 0; p < 8; p++) {
     if (((vary >> (8 * p)) & 255u) == 0) continue;
+    // histogram reads the keys; the scatter reads and writes them
+    prof_add_bytes(h, PH_SORT, 24ull * k);
     k_hist<<<ntiles, kT, 0, st>>>(src, k, 8 * p, hist, ntiles);
     h->launches++;
     CPMA_TRY(scan_u32_to_u64(h, hist, hoff, (uint64_t)256 * ntiles, nullptr, st));

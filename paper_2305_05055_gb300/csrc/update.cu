@@ -324,7 +324,8 @@ __device__ __forceinline__ void mark_node(uint32_t* bits, const Levels& lv, unsi
 struct FinArgs {
   uint32_t* used;
   uint32_t* cnt;
-  const uint32_t *T_leaf, *T_first_chunk, *T_oldcnt, *T_newcnt;
+  const uint32_t *T_leaf, *T_first_chunk, *T_oldcnt, *T_newcnt, *T_begin, *T_oldused;
+  ull* merge_bytes;  // profiling: algorithmic bytes of the merge (nullable)
   uint32_t* T_state;
   const ull* T_newbytes;
   uint32_t* chunk_cnt;
@@ -341,10 +342,17 @@ struct FinArgs {
 __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
   if (a.st->err) return;
   const uint64_t nT = a.st->nT;
+  ull mb = 0;
   for (uint64_t t = gtid(); t < nT; t += gstride()) {
     const uint32_t state = a.T_state[t];
     const uint32_t oldc = a.T_oldcnt[t], newc = a.T_newcnt[t];
     const uint32_t j = a.T_leaf[t];
+    if (a.merge_bytes) {
+      // the merge reads the old leaf, the batch slice and ~24 bytes of
+      // per-leaf metadata, and writes the leaf when it rewrites it in place
+      mb += a.T_oldused[t] + 8ull * (a.T_begin[t + 1] - a.T_begin[t]) + 24;
+      if (state == kInPlace) mb += (max(a.T_oldused[t], (uint32_t)a.T_newbytes[t]) + 15u) & ~15u;
+    }
     if (newc == oldc) {
       if (state == kPending) {
         a.T_state[t] = kUnchanged;
@@ -365,6 +373,10 @@ __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
     } else if (state == kPending) {
       mark_node(a.bits, a.lv, 0, j, a.cand, a.st);
     }
+  }
+  if (a.merge_bytes) {
+    mb = warp_sum(mb);
+    if (lane_id() == 0 && mb) atomicAdd(a.merge_bytes, mb);
   }
 }
 
@@ -857,9 +869,10 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   if (k >= (1ull << 31)) return CPMA_EINVAL;
   CPMA_CUDA(cudaMemsetAsync(ds, 0, offsetof(Status, empties), st));
   const uint64_t* u = d_keys;
-  if (!sorted) CPMA_TRY(sort_keys(h, d_keys, k, &u, st));
-  if (u == d_keys && !sorted) {
-    // k <= 1: nothing to sort
+  if (!sorted) {
+    prof_begin(h, PH_SORT, st);
+    CPMA_TRY(sort_keys(h, d_keys, k, &u, st));
+    prof_end(h, st);
   }
   // ---- scratch (all before any change to the structure) ----
   Scratch& s = h->s;
@@ -881,6 +894,10 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   const uint32_t LB = h->cfg.leaf_bytes;
 
   // ---- route ----
+  prof_begin(h, PH_ROUTE, st);
+  // keys 8k, leaf ids 4k + 4k, flags 8k + 8k, flag scan 24k, T / chunk
+  // entries about 12 bytes per key on a uniform batch
+  prof_add_bytes(h, PH_ROUTE, 68ull * k);
   k_route_flags<<<grid_for(h, k), kT, 0, st>>>(u, k, h->heads, h->L, P<uint32_t>(s.leaf_of),
                                                P<uint64_t>(s.flags), ds);
   h->launches++;
@@ -937,9 +954,13 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   }
   const int mgrid = (int)std::max<uint64_t>(
       1, std::min<uint64_t>((k + kChunk + mwarps - 1) / mwarps, (uint64_t)h->num_sms * 4));
+  prof_end(h, st);
+  prof_begin(h, PH_MERGE, st);
   k_merge<false><<<mgrid, mwarps * 32, msmem, st>>>(ma);
   h->launches++;
   CPMA_CUDA(cudaGetLastError());
+  prof_end(h, st);
+  prof_begin(h, PH_COUNT, st);
 
   FinArgs fa;
   fa.used = h->used;
@@ -948,6 +969,9 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   fa.T_first_chunk = ro.T_first_chunk;
   fa.T_oldcnt = ro.T_oldcnt;
   fa.T_newcnt = ro.T_newcnt;
+  fa.T_begin = ro.T_begin;
+  fa.T_oldused = ro.T_oldused;
+  fa.merge_bytes = prof_bytes(h, PH_MERGE);
   fa.T_state = ro.T_state;
   fa.T_newbytes = ro.T_newbytes;
   fa.chunk_cnt = ma.chunk_cnt;
@@ -965,7 +989,9 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   k_copy_total<<<1, 1, 0, st>>>(P<uint64_t>(s.chunk_off), &ds->nchunks, &ds->novf);
   h->launches++;
   CPMA_CUDA(cudaGetLastError());
+  prof_end(h, st);
   CPMA_TRY(sync_status(h, st));
+  prof_begin(h, PH_COUNT, st);
   Status hs = *h->h_status;
   if (hs.err & kErrUnsorted) return CPMA_EINVAL;
   if (hs.err) return CPMA_EINTERNAL;
@@ -1006,9 +1032,11 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
     k_clear_bits<<<grid_for(h, ncand_bound), kT, 0, st>>>(fa.cand, fa.bits, lv, ds);
     h->launches += 2;
     CPMA_CUDA(cudaGetLastError());
+    prof_end(h, st);
     CPMA_TRY(sync_status(h, st));
     hs = *h->h_status;
     if (hs.err) return CPMA_EINTERNAL;
+    prof_begin(h, PH_REDIST, st);
     if (hs.resize) {
       CPMA_TRY(do_resize(h, st, hs.total_bytes, n_after, hs.nT));
       resized = true;
@@ -1028,6 +1056,8 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
       CPMA_TRY(redistribute(h, st, nwin, hs.win_leaves, hs.win_leaves, n_after, hs.nT, cur));
     }
   }
+  prof_end(h, st);
+  prof_begin(h, PH_FINISH, st);
   if (resized) {
     Levels lv2;
     CPMA_TRY(ensure_bits(h, st, &lv2));
@@ -1038,6 +1068,7 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   if (d_delta)
     CPMA_CUDA(cudaMemcpyAsync(d_delta, &ds->delta, 8, cudaMemcpyDeviceToDevice, st));
   CPMA_CUDA(cudaGetLastError());
+  prof_end(h, st);
   return CPMA_OK;
 }
 
