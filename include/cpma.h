@@ -122,6 +122,29 @@ int cpma_range_map(const cpma_t* h, const uint64_t* d_lo, const uint64_t* d_hi,
                    uint64_t q, uint64_t* d_sum, uint64_t* d_count,
                    cpma_stream_t stream);
 
+/* cpma_range_map without any device allocation (the paper has no counterpart:
+ * this is a deployment variant).  cpma_range_map grows private scratch with
+ * cudaMalloc/cudaFree when a larger batch of queries arrives; some callers
+ * cannot let that happen, e.g. a process whose device memory is all handed to
+ * another allocator up front, or a latency-bound serving thread that must not
+ * hit the device-wide synchronisation cudaFree implies.  This entry point
+ * takes its scratch from a fixed 2 MiB array inside the library's device
+ * image instead, so it allocates nothing.  Arguments and results are those of
+ * cpma_range_map.
+ *  - q <= CPMA_RANGE_NOALLOC_MAX_QUERIES (65536); larger q returns
+ *    CPMA_EINVAL without doing anything.
+ *  - The handle's device must be the current device (else CPMA_EINVAL).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture.
+ *  - Every call on a device shares the one array: calls whose work overlaps
+ *    on the GPU (different streams, not ordered) race and give wrong results.
+ *    Order them on one stream. */
+#define CPMA_RANGE_NOALLOC_MAX_QUERIES 65536
+int cpma_range_map_noalloc(const cpma_t* h, const uint64_t* d_lo,
+                           const uint64_t* d_hi, uint64_t q, uint64_t* d_sum,
+                           uint64_t* d_count, cpma_stream_t stream);
+
 /* App. A sum(): sum of all keys modulo 2^64 into the device uint64 *d_sum
  * (and, if d_count is not NULL, the number of keys into *d_count). */
 int cpma_sum(const cpma_t* h, uint64_t* d_sum, uint64_t* d_count,

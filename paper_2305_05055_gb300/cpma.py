@@ -69,6 +69,7 @@ def lib():
                 "cpma_stats": (I, [V, P64]),
                 "cpma_reset_stats": (I, [V]),
                 "cpma_strerror": (C.c_char_p, [I]),
+                "cpma_range_map_noalloc": (I, [V, V, V, U64, V, V, V]),
                 "cpma_profile": (I, [V, I]),
                 "cpma_profile_read": (I, [V, C.POINTER(C.c_double), P64, P64, I]),
             }
@@ -172,6 +173,21 @@ def cpma_range_map(h, lo, hi, out_sum=None, out_count=None, stream=None):
         out_count = torch.empty(q, dtype=torch.int64, device=lo.device)
     _check(lib().cpma_range_map(h, _ptr(lo), _ptr(hi), q, _ptr(out_sum), _ptr(out_count),
                                 C.c_void_p(_stream(stream))), "cpma_range_map")
+    return out_sum, out_count
+
+
+RANGE_NOALLOC_MAX_QUERIES = 65536
+
+
+def cpma_range_map_noalloc(h, lo, hi, out_sum, out_count, stream=None):
+    """cpma_range_map with no device allocation inside the call: the caller
+    passes the output buffers, the library uses its fixed scratch array."""
+    lo, hi = _keys(lo, "lo"), _keys(hi, "hi")
+    if lo.numel() != hi.numel():
+        raise ValueError("lo and hi differ in length")
+    _check(lib().cpma_range_map_noalloc(h, _ptr(lo), _ptr(hi), lo.numel(), _ptr(out_sum),
+                                        _ptr(out_count), C.c_void_p(_stream(stream))),
+           "cpma_range_map_noalloc")
     return out_sum, out_count
 
 

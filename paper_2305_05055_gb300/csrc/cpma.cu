@@ -312,6 +312,12 @@ int cpma_range_map(const cpma_t* h, const uint64_t* d_lo, const uint64_t* d_hi, 
   return run_range(h, d_lo, d_hi, q, d_sum, d_count, (cudaStream_t)stream);
 }
 
+int cpma_range_map_noalloc(const cpma_t* h, const uint64_t* d_lo, const uint64_t* d_hi,
+                           uint64_t q, uint64_t* d_sum, uint64_t* d_count, cpma_stream_t stream) {
+  if (!h || (q && (!d_lo || !d_hi || !d_sum || !d_count))) return CPMA_EINVAL;
+  return run_range_noalloc(h, d_lo, d_hi, q, d_sum, d_count, (cudaStream_t)stream);
+}
+
 int cpma_sum(const cpma_t* h, uint64_t* d_sum, uint64_t* d_count, cpma_stream_t stream) {
   if (!h || !d_sum) return CPMA_EINVAL;
   return run_sum(h, d_sum, d_count, (cudaStream_t)stream);

@@ -130,6 +130,10 @@ int scan_u8_to_u64(cpma* h, const uint8_t* in, uint64_t* out, uint64_t n_host,
                    const ull* n_dev, cudaStream_t st);
 int scan_u64(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host, const ull* n_dev,
              cudaStream_t st);
+// Same as scan_u64 for a host-known count, with caller-provided partials
+// (partials_cap entries); it never allocates.
+int scan_u64_given_partials(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host,
+                            uint64_t* partials, uint64_t partials_cap, cudaStream_t st);
 
 // sort.cu: sort k keys ascending into *out (one of the scratch buffers).
 int sort_keys(cpma* h, const uint64_t* d_in, uint64_t k, const uint64_t** out,
@@ -147,6 +151,8 @@ int run_has(const cpma* h, const uint64_t* d_keys, uint64_t q, uint8_t* d_out, c
 int run_range(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q, uint64_t* sum,
               uint64_t* count, cudaStream_t st);
 int run_sum(const cpma* h, uint64_t* sum, uint64_t* count, cudaStream_t st);
+int run_range_noalloc(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q,
+                      uint64_t* sum, uint64_t* count, cudaStream_t st);
 
 int check_cuda(cudaError_t e);
 int sync_status(cpma* h, cudaStream_t st);

@@ -11,6 +11,7 @@
 //    leaves it (addition mod 2^64 is associative, so the order is free).
 //  sum (App. A sum()): every leaf once.
 #include <algorithm>
+#include <mutex>
 
 #include "dev_common.cuh"
 #include "internal.h"
@@ -161,6 +162,40 @@ __global__ void __launch_bounds__(kT) k_sum(const uint8_t* __restrict__ data,
 
 int persistent_grid(const cpma* h) { return h->num_sms * 8; }
 
+// Scratch of the allocation-free range_map: per-query first leaf, item count
+// and item offsets, plus the partial sums of the offset scan.  It lives in the
+// library's own device image, so every GPU that loads the library holds these
+// 2 MiB until the process exits, and every call shares them.
+constexpr uint64_t kNoAllocMaxQueries = 1ull << 16;
+constexpr uint64_t kNoAllocPartials = 1024;
+constexpr size_t kNoAllocBytes = 2u << 20;
+static_assert((3 * kNoAllocMaxQueries + 1 + kNoAllocPartials) * 8 <= kNoAllocBytes,
+              "range scratch too small");
+static __device__ __align__(256) uint8_t g_range_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_range_scratch on device `dev` (which must be current).
+// The host-side name of the array is only a stand-in, so the address is
+// looked up once per device with cudaGetSymbolAddress and cached.
+int scratch_address(int dev, uint8_t** out) {
+  if (dev < 0 || dev >= kMaxDevices) return CPMA_EINVAL;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_range_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return CPMA_ECUDA;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = static_cast<uint8_t*>(g_scratch_addr[dev]);
+  return CPMA_OK;
+}
+
 }  // namespace
 
 int run_has(const cpma* h, const uint64_t* d_keys, uint64_t q, uint8_t* d_out, cudaStream_t st) {
@@ -210,6 +245,46 @@ int run_range(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q,
   k_range<<<persistent_grid(h), kT, 0, st>>>(a);
   CPMA_LAUNCHED(h);
   prof_end(h, st);
+  return check_cuda(cudaGetLastError());
+}
+
+int run_range_noalloc(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q,
+                      uint64_t* sum, uint64_t* count, cudaStream_t st) {
+  if (q > kNoAllocMaxQueries) return CPMA_EINVAL;
+  if (q == 0) return CPMA_OK;
+  int dev = -1;
+  CPMA_CUDA(cudaGetDevice(&dev));
+  if (dev != h->device) return CPMA_EINVAL;
+  uint8_t* base = nullptr;
+  CPMA_TRY(scratch_address(dev, &base));
+  uint64_t* first = reinterpret_cast<uint64_t*>(base);
+  uint64_t* items = first + kNoAllocMaxQueries;
+  uint64_t* off = items + kNoAllocMaxQueries;            // q + 1 entries
+  uint64_t* partials = off + kNoAllocMaxQueries + 1;     // kNoAllocPartials entries
+  const int g1 = (int)std::max<uint64_t>(
+      1, std::min<uint64_t>((q + kT - 1) / kT, (uint64_t)h->num_sms * 8));
+  // every scratch entry read below is written first on this stream: nothing
+  // carries over from an earlier call
+  k_range_prep<<<g1, kT, 0, st>>>(lo, hi, q, h->heads, h->L, first, items, sum, count);
+  CPMA_LAUNCHED(h);
+  CPMA_CUDA(cudaGetLastError());
+  CPMA_TRY(scan_u64_given_partials(const_cast<cpma*>(h), items, off, q, partials,
+                                   kNoAllocPartials, st));
+  RangeArgs a;
+  a.lo = lo;
+  a.hi = hi;
+  a.q = q;
+  a.first = first;
+  a.off = off;
+  a.data = h->data;
+  a.used = h->used;
+  a.cnt = h->cnt;
+  a.LB = h->cfg.leaf_bytes;
+  a.sum = sum;
+  a.count = count;
+  a.prof = nullptr;
+  k_range<<<persistent_grid(h), kT, 0, st>>>(a);
+  CPMA_LAUNCHED(h);
   return check_cuda(cudaGetLastError());
 }
 

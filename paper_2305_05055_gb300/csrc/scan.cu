@@ -144,4 +144,16 @@ int scan_u64(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host, const 
   return scan_impl<uint64_t>(h, in, out, n_host, n_dev, st);
 }
 
+int scan_u64_given_partials(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host,
+                            uint64_t* partials, uint64_t partials_cap, cudaStream_t st) {
+  uint64_t tiles = (n_host + kTile - 1) / kTile;
+  int G = (int)std::min<uint64_t>((uint64_t)2 * h->num_sms, std::max<uint64_t>(tiles, 1));
+  if ((uint64_t)G + 1 > partials_cap) return CPMA_EINVAL;
+  k_reduce<uint64_t><<<G, kT, 0, st>>>(in, n_host, nullptr, partials);
+  k_partials<<<1, 1024, 0, st>>>(partials, G);
+  k_down<uint64_t><<<G, kT, 0, st>>>(in, out, n_host, nullptr, partials);
+  h->launches += 3;
+  return check_cuda(cudaGetLastError());
+}
+
 }  // namespace cpmaimpl
