@@ -110,13 +110,18 @@ __device__ __host__ __forceinline__ bool node_violates(const Bounds& B, unsigned
 // f(index, value) is called once per element by the lane that owns it.
 // Returns the element count (warp-uniform).
 // ---------------------------------------------------------------------------
-template <class F>
-__device__ __forceinline__ uint32_t warp_decode(const uint8_t* __restrict__ leaf, uint32_t used,
-                                                F&& f) {
+// WITH_POS: f(index, value, byte position of the last byte of the element's
+// code) -- 7 for the head.
+template <bool WITH_POS, class F>
+__device__ __forceinline__ uint32_t warp_decode_impl(const uint8_t* __restrict__ leaf,
+                                                     uint32_t used, F&& f) {
   if (used == 0) return 0;
   const unsigned lane = lane_id();
   const uint64_t head = *reinterpret_cast<const uint64_t*>(leaf);
-  if (lane == 0) f(0u, head);
+  if (lane == 0) {
+    if constexpr (WITH_POS) f(0u, head, 7u);
+    else f(0u, head);
+  }
   uint32_t base_idx = 1;
   uint64_t base_val = head;
   uint64_t carry_val = 0;
@@ -170,7 +175,8 @@ __device__ __forceinline__ uint32_t warp_decode(const uint8_t* __restrict__ leaf
     for (int b = 0; b < 16; b++) {
       if ((term >> b) & 1u) {
         val += d[b];
-        f(idx, val);
+        if constexpr (WITH_POS) f(idx, val, p0 + (uint32_t)b);
+        else f(idx, val);
         idx++;
       }
     }
@@ -180,6 +186,18 @@ __device__ __forceinline__ uint32_t warp_decode(const uint8_t* __restrict__ leaf
     carry_sh = __shfl_sync(FULL, sh, 31);
   }
   return base_idx;
+}
+
+template <class F>
+__device__ __forceinline__ uint32_t warp_decode(const uint8_t* __restrict__ leaf, uint32_t used,
+                                                F&& f) {
+  return warp_decode_impl<false>(leaf, used, f);
+}
+
+template <class F>
+__device__ __forceinline__ uint32_t warp_decode_pos(const uint8_t* __restrict__ leaf,
+                                                    uint32_t used, F&& f) {
+  return warp_decode_impl<true>(leaf, used, f);
 }
 
 // Encodes z[0..r) (shared memory) into buf (shared, zeroed, 8-byte aligned):
@@ -206,6 +224,126 @@ __device__ __forceinline__ uint32_t warp_encode(const uint64_t* z, uint32_t r, u
 // Byte cost of z[i] in a stream: 8 for the first element, else its code.
 __device__ __forceinline__ uint32_t elem_cost(const uint64_t* z, uint32_t i) {
   return i == 0 ? 8u : leb_len(z[i] - z[i - 1]);
+}
+
+// ---------------------------------------------------------------------------
+// Sum (mod 2^64) and count of every element of the leaves [j0, j1), added to
+// the calling lane's partials (the caller reduces them over the warp).
+//
+// Leaves are taken 32 at a time.  Their used bytes are cut into 16-byte
+// chunks and the warp takes 32 chunks per step, so no lane idles on the zero
+// padding of a leaf.  The sum of a leaf with m elements, head h and deltas
+// d_1..d_{m-1} is m*h + sum_c (m - c) d_c; a chunk holding the codes c =
+// 1+B .. B+n (B = codes earlier in its leaf, a segmented warp scan) adds
+// (m - 1 - B) * D - W with D = sum of its deltas and W = sum of lidx * delta
+// (lidx = position among the chunk's codes).  The code a chunk starts in the
+// middle of is completed with the previous chunk's partial bits (one
+// shuffle).  Chunks decode with 32-bit arithmetic, valid while every code is
+// at most 4 bytes (deltas < 2^28); a window of leaves with a longer code is
+// summed again by the general decoder instead.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void warp_span_sum(const uint8_t* __restrict__ data,
+                                              const uint32_t* __restrict__ used,
+                                              const uint32_t* __restrict__ cnt, uint32_t LB,
+                                              uint64_t j0, uint64_t j1, uint64_t& acc,
+                                              uint64_t& cacc, ull& nbytes) {
+  const unsigned lane = lane_id();
+  for (uint64_t w0 = j0; w0 < j1; w0 += 32) {
+    const uint64_t jj = w0 + lane;
+    const bool lv = jj < j1;
+    const uint32_t u_i = lv ? min(__ldg(used + jj), LB) : 0u;
+    const uint32_t m_i = lv ? __ldg(cnt + jj) : 0u;
+    cacc += m_i;
+    nbytes += u_i;
+    const uint32_t nc_i = (u_i + 15u) >> 4;
+    const uint32_t cinc = warp_incl_scan(nc_i);
+    const uint32_t NC = __shfl_sync(FULL, cinc, 31);
+    uint64_t wacc = 0;
+    bool bad = false;
+    uint32_t cont_li = 0xFFFFFFFFu, cont_cnt = 0, cont_val = 0, cont_sh = 0;
+    for (uint32_t g0 = 0; g0 < NC; g0 += 32) {
+      const uint32_t ci = g0 + lane;
+      const bool act = ci < NC;
+      // leaf slot of chunk ci: the number of leaves whose chunks end at or
+      // before ci
+      uint32_t li = 0;
+#pragma unroll
+      for (int stp = 16; stp >= 1; stp >>= 1) {
+        const uint32_t v = __shfl_sync(FULL, cinc, li + stp - 1);
+        if (v <= ci) li += stp;
+      }
+      const uint32_t lis = min(li, 31u);
+      const uint32_t cstart = __shfl_sync(FULL, cinc, lis) - __shfl_sync(FULL, nc_i, lis);
+      const uint32_t u = __shfl_sync(FULL, u_i, lis);
+      const uint32_t m = __shfl_sync(FULL, m_i, lis);
+      const uint32_t cw = ci - cstart;
+      const uint32_t p0 = cw * 16u;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (act) v = __ldg(reinterpret_cast<const uint4*>(data + (w0 + lis) * LB + p0));
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+      const int b_lo = (cw == 0) ? 8 : 0;
+      const int b_hi = act ? (int)min(16u, u - p0) : 0;
+      uint32_t range = 0;
+      if (b_hi > b_lo)
+        range = ((b_hi == 16) ? 0xFFFFu : ((1u << b_hi) - 1u)) & ~((1u << b_lo) - 1u);
+      uint32_t cur = 0, sh = 0, D = 0, W = 0, lidx = 0, first_own = 0, term = 0;
+#pragma unroll
+      for (int b = 0; b < 16; b++) {
+        const uint32_t byte = (w[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+        const bool inr = (range >> b) & 1u;
+        const bool t = inr && !(byte & 0x80u);
+        bad |= inr && (byte & 0x80u) && sh >= 21u;
+        if (inr) { cur |= (byte & 0x7Fu) << sh; sh += 7u; }
+        if (t) {
+          if (term == 0) first_own = cur;
+          D += cur;
+          W += lidx * cur;
+          lidx++;
+          term |= 1u << b;
+          cur = 0;
+          sh = 0;
+        }
+      }
+      if (range && !term) bad = true;
+      // the partial code left by the previous chunk of the same leaf
+      const uint32_t prev_li = __shfl_up_sync(FULL, li, 1);
+      uint32_t pv = __shfl_up_sync(FULL, cur, 1);
+      uint32_t ps = __shfl_up_sync(FULL, sh, 1);
+      if (lane == 0 || prev_li != li) {
+        if (lane == 0 && cont_li == li && cw > 0) { pv = cont_val; ps = cont_sh; }
+        else { pv = 0; ps = 0; }
+      }
+      if (term) {
+        const uint32_t own = (uint32_t)__ffs(term) - (uint32_t)b_lo;
+        if (ps / 7u + own > 4u) bad = true;
+        D = D - first_own + pv + (first_own << ps);
+      }
+      // codes of this leaf in earlier chunks (segmented scan)
+      const uint32_t c = __popc(term);
+      const uint32_t incl = warp_incl_scan(c);
+      const uint32_t excl = incl - c;
+      const bool started_before = cstart < g0;
+      const uint32_t seg_lane = started_before ? 0u : cstart - g0;
+      const uint32_t B = excl - __shfl_sync(FULL, excl, seg_lane & 31u) +
+                         (started_before ? cont_cnt : 0u);
+      if (act) {
+        uint64_t contrib = (uint64_t)(m - 1u - B) * D - W;
+        if (cw == 0) contrib += (uint64_t)m * ((uint64_t)w[0] | ((uint64_t)w[1] << 32));
+        wacc += contrib;
+      }
+      cont_li = __shfl_sync(FULL, li, 31);
+      cont_cnt = __shfl_sync(FULL, B + c, 31);
+      cont_val = __shfl_sync(FULL, cur, 31);
+      cont_sh = __shfl_sync(FULL, sh, 31);
+    }
+    if (__any_sync(FULL, bad)) {
+      const uint64_t je = min(w0 + 32, j1);
+      for (uint64_t q = w0; q < je; q++)
+        warp_decode(data + q * LB, min(__ldg(used + q), LB), [&](uint32_t, uint64_t val) { acc += val; });
+    } else {
+      acc += wacc;
+    }
+  }
 }
 
 }  // namespace cpmadev

@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(kT) k_range(RangeArgs a) {
   ull nbytes = 0;
   uint64_t qend = a.off[qi + 1];
   uint64_t lo = a.lo[qi], hi = a.hi[qi], fl = a.first[qi], qoff = a.off[qi];
-  for (uint64_t g = g0; g < g1; g++) {
+  uint64_t g = g0;
+  while (g < g1) {
     while (g >= qend) {
       s = warp_sum(s);
       c = warp_sum(c);
@@ -111,20 +112,23 @@ __global__ void __launch_bounds__(kT) k_range(RangeArgs a) {
       qend = a.off[qi + 1];
       lo = a.lo[qi]; hi = a.hi[qi]; fl = a.first[qi]; qoff = a.off[qi];
     }
-    const uint64_t li = g - qoff;
+    const uint64_t li = g - qoff, n = qend - qoff;
+    if (li > 0 && li + 1 < n) {
+      // leaves strictly inside the range: no filter, chunked span sum
+      const uint64_t stop = min(g1, qend - 1);  // exclusive, global item index
+      uint64_t cc = 0;
+      warp_span_sum(a.data, a.used, a.cnt, a.LB, fl + li, fl + (stop - qoff), s, cc, nbytes);
+      if (lane == 0) c += warp_sum(cc); else warp_sum(cc);
+      g = stop;
+      continue;
+    }
     const uint64_t j = fl + li;
-    const uint8_t* leaf = a.data + j * a.LB;
-    const bool interior = li > 0 && g + 1 < qend;
     const uint32_t u = min(a.used[j], a.LB);
     nbytes += u;
-    if (interior) {
-      warp_decode(leaf, u, [&](uint32_t, uint64_t v) { s += v; });
-      if (lane == 0) c += a.cnt[j];
-    } else {
-      warp_decode(leaf, u, [&](uint32_t, uint64_t v) {
-        if (v >= lo && v < hi) { s += v; c++; }
-      });
-    }
+    warp_decode(a.data + j * a.LB, u, [&](uint32_t, uint64_t v) {
+      if (v >= lo && v < hi) { s += v; c++; }
+    });
+    g++;
   }
   s = warp_sum(s);
   c = warp_sum(c);
@@ -132,6 +136,7 @@ __global__ void __launch_bounds__(kT) k_range(RangeArgs a) {
     atomicAdd((ull*)&a.sum[qi], (ull)s);
     atomicAdd((ull*)&a.count[qi], (ull)c);
   }
+  nbytes = warp_sum(nbytes);
   if (a.prof && lane == 0 && nbytes) atomicAdd(a.prof, nbytes);
 }
 
@@ -145,19 +150,15 @@ __global__ void __launch_bounds__(kT) k_sum(const uint8_t* __restrict__ data,
   const uint64_t j0 = L * gw / nw, j1 = L * (gw + 1) / nw;
   uint64_t s = 0, c = 0;
   ull nbytes = 0;
-  for (uint64_t j = j0; j < j1; j++) {
-    const uint32_t u = min(used[j], LB);
-    warp_decode(data + j * LB, u, [&](uint32_t, uint64_t v) { s += v; });
-    if (lane == 0) c += cnt[j];
-    nbytes += u + 8;  // leaf bytes + used/count entries
-  }
-  if (prof && lane == 0 && nbytes) atomicAdd(prof, nbytes);
+  warp_span_sum(data, used, cnt, LB, j0, j1, s, c, nbytes);
   s = warp_sum(s);
   c = warp_sum(c);
+  nbytes = warp_sum(nbytes);
   if (lane == 0 && (s | c)) {
     atomicAdd((ull*)sum, (ull)s);
     if (count) atomicAdd((ull*)count, (ull)c);
   }
+  if (prof && lane == 0 && nbytes) atomicAdd(prof, nbytes + 8ull * (j1 - j0));
 }
 
 int persistent_grid(const cpma* h) { return h->num_sms * 8; }

@@ -140,13 +140,225 @@ struct MergeArgs {
   const uint32_t *chunk_begin, *chunk_leaf, *chunk_tid;
   uint32_t* chunk_cnt;
   const uint64_t* chunk_off;
-  const uint32_t *T_begin, *T_oldcnt, *T_oldused;
+  const uint32_t *T_begin, *T_oldcnt, *T_oldused, *T_leaf, *T_first_chunk;
   uint32_t *T_newcnt, *T_state;
   ull* T_newbytes;
   uint64_t* ovf;
   int is_delete;
   Status* st;
 };
+
+// Slices of at most kSmall keys into a non-empty leaf take the splice path.
+constexpr uint32_t kSmall = 32;
+
+__host__ __device__ __forceinline__ size_t small_warp_bytes(uint32_t LB) {
+  // old[LB] u64, pos[LB] u16, out[LB] bytes, keys[kSmall] u64, ranks[kSmall]
+  // u32, edits: old start, old end, new start, cumulative shift (u32 each)
+  return (size_t)8 * LB + 2 * LB + LB + 8 * kSmall + 4 * kSmall + 16 * kSmall;
+}
+
+__device__ __forceinline__ bool small_slice(uint32_t tb, uint32_t te, uint32_t uold) {
+  return te - tb <= kSmall && uold > 0;
+}
+
+// Splice merge of a small slice into one leaf (warp per touched leaf).  The
+// leaf is decoded once into shared memory (values and the byte position where
+// each code ends); every key finds its rank by binary search in its own lane.
+// Keys that land in the same gap (insert) or delete a run of neighbours form
+// one edit: a byte range of the old leaf replaced by new bytes (new head
+// and/or codes).  The new leaf is then the old bytes outside the edits, each
+// shifted by the size change of the edits before it, plus the edits' bytes --
+// the same bytes as encoding the merged sequence from scratch, produced
+// without re-encoding the untouched codes.  A result over LB bytes is left
+// pending for the general merge.
+__global__ void __launch_bounds__(kT, 4) k_merge_small(MergeArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  if (a.st->err) return;
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const unsigned wpb = blockDim.x >> 5;
+  const uint32_t LB = a.LB;
+  uint8_t* wbase = smem + (size_t)warp * small_warp_bytes(LB);
+  uint64_t* old = reinterpret_cast<uint64_t*>(wbase);
+  uint16_t* pos = reinterpret_cast<uint16_t*>(wbase + 8 * (size_t)LB);
+  uint8_t* out = wbase + 10 * (size_t)LB;
+  uint64_t* nk = reinterpret_cast<uint64_t*>(wbase + 11 * (size_t)LB);
+  uint32_t* nr = reinterpret_cast<uint32_t*>(nk + kSmall);
+  uint32_t* es = nr + kSmall;
+  uint32_t* ee = es + kSmall;
+  uint32_t* en = ee + kSmall;
+  int32_t* shc = reinterpret_cast<int32_t*>(en + kSmall);
+  const uint64_t nT = a.st->nT;
+  for (uint64_t t = (uint64_t)blockIdx.x * wpb + warp; t < nT; t += (uint64_t)gridDim.x * wpb) {
+    const uint32_t tb = a.T_begin[t], te = a.T_begin[t + 1];
+    const uint32_t uold = a.T_oldused[t];
+    if (!small_slice(tb, te, uold)) continue;
+    const uint32_t s = te - tb;
+    const uint32_t j = a.T_leaf[t];
+    const uint32_t m = a.T_oldcnt[t];
+    const uint32_t fc0 = a.T_first_chunk[t], fc1 = a.T_first_chunk[t + 1];
+    uint8_t* leafp = a.data + (size_t)j * LB;
+    warp_decode_pos(leafp, min(uold, LB), [&](uint32_t idx, uint64_t v, uint32_t p) {
+      old[idx] = v;
+      pos[idx] = (uint16_t)p;
+    });
+    __syncwarp();
+    // the keys that change the leaf, with their ranks among the old elements
+    uint64_t x = 0;
+    uint32_t r = 0;
+    bool keep = false;
+    if (lane < s) {
+      x = a.u[tb + lane];
+      const bool dup = lane > 0 && a.u[tb + lane - 1] == x;
+      r = (uint32_t)lower_bound(old, m, x);
+      const bool present = r < m && old[r] == x;
+      keep = !dup && (a.is_delete ? present : !present);
+    }
+    const unsigned kb = __ballot_sync(FULL, keep);
+    const uint32_t nn = __popc(kb);
+    if (keep) {
+      const uint32_t k = __popc(kb & lanemask_lt());
+      nk[k] = x;
+      nr[k] = r;
+    }
+    __syncwarp();
+    if (nn == 0) {
+      if (lane == 0) {
+        a.T_state[t] = kUnchanged;
+        a.T_newcnt[t] = m;
+        a.T_newbytes[t] = uold;
+      }
+      for (uint32_t c = fc0 + lane; c < fc1; c += 32) a.chunk_cnt[c] = 0;
+      __syncwarp();
+      continue;
+    }
+    // one edit per group: insert = keys of equal rank, delete = a run of
+    // consecutive ranks
+    bool lead = false;
+    if (lane < nn) {
+      const uint32_t rk = nr[lane];
+      lead = lane == 0 || (a.is_delete ? nr[lane - 1] + 1 != rk : nr[lane - 1] != rk);
+    }
+    const unsigned lb = __ballot_sync(FULL, lead);
+    const uint32_t E = __popc(lb);
+    uint32_t e_os = 0, e_oe = 0, e_nl = 0, gend = 0, r0 = 0;
+    if (lead) {
+      const unsigned after = lb & ~((2u << lane) - 1u);
+      gend = after ? (uint32_t)(__ffs(after) - 1) : nn;
+      r0 = nr[lane];
+      if (!a.is_delete) {
+        if (r0 == 0) { e_os = 0; e_oe = 8; }
+        else if (r0 < m) { e_os = pos[r0 - 1] + 1u; e_oe = pos[r0] + 1u; }
+        else { e_os = uold; e_oe = uold; }
+        uint32_t len;
+        uint64_t prev = nk[lane];
+        len = (r0 == 0) ? 8u : leb_len(nk[lane] - old[r0 - 1]);
+        for (uint32_t q = lane + 1; q < gend; q++) { len += leb_len(nk[q] - prev); prev = nk[q]; }
+        if (r0 < m) len += leb_len(old[r0] - prev);
+        e_nl = len;
+      } else {
+        const uint32_t r1 = r0 + (gend - lane);
+        e_os = (r0 == 0) ? 0u : pos[r0 - 1] + 1u;
+        e_oe = (r1 < m) ? pos[r1] + 1u : uold;
+        e_nl = (r1 >= m) ? 0u : (r0 == 0 ? 8u : leb_len(old[r1] - old[r0 - 1]));
+      }
+    }
+    const uint32_t eidx = __popc(lb & lanemask_lt());
+    const int32_t delta = lead ? (int32_t)e_nl - (int32_t)(e_oe - e_os) : 0;
+    const int32_t dinc = warp_incl_scan(delta);
+    const int32_t total = __shfl_sync(FULL, dinc, 31);
+    if (lead) {
+      es[eidx] = e_os;
+      ee[eidx] = e_oe;
+      en[eidx] = (uint32_t)((int32_t)e_os + dinc - delta);
+      shc[eidx] = dinc;
+    }
+    const uint32_t nb = (uint32_t)((int32_t)uold + total);
+    const uint32_t newc = a.is_delete ? m - nn : m + nn;
+    // new head: the first key when it goes before the old head; the first
+    // survivor when the old head is deleted
+    const uint32_t g0end = __shfl_sync(FULL, gend, 0);
+    uint64_t newhead = old[0];
+    if (nr[0] == 0) newhead = a.is_delete ? (g0end < m ? old[g0end] : KEY_MAX) : nk[0];
+    __syncwarp();
+    if (nb > LB) {
+      if (lane == 0) {
+        a.T_state[t] = kPending;
+        a.T_newcnt[t] = newc;
+        a.T_newbytes[t] = nb;
+      }
+      for (uint32_t c = fc0 + lane; c < fc1; c += 32) a.chunk_cnt[c] = (c == fc0) ? newc : 0u;
+      __syncwarp();
+      continue;
+    }
+    const uint32_t wend = (max(uold, nb) + 15u) & ~15u;
+    for (uint32_t p = lane * 16; p < wend; p += 512)
+      *reinterpret_cast<uint4*>(out + p) = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    // old bytes outside the edits, shifted
+    for (uint32_t p0 = lane * 16; p0 < uold; p0 += 512) {
+      const uint4 v = *reinterpret_cast<const uint4*>(leafp + p0);
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+      uint32_t q = 0;
+      while (q < E && ee[q] <= p0) q++;
+      int32_t shift = q ? shc[q - 1] : 0;
+      const uint32_t lim = min(16u, uold - p0);
+      if (q == E || es[q] >= p0 + 16) {
+#pragma unroll
+        for (int b = 0; b < 16; b++)
+          if ((uint32_t)b < lim) out[(int32_t)(p0 + b) + shift] = (uint8_t)(w[b >> 2] >> (8 * (b & 3)));
+      } else {
+#pragma unroll
+        for (int b = 0; b < 16; b++) {
+          const uint32_t tt = p0 + b;
+          if ((uint32_t)b >= lim) continue;
+          while (q < E && ee[q] <= tt) { shift = shc[q]; q++; }
+          if (q < E && es[q] <= tt) continue;
+          out[(int32_t)tt + shift] = (uint8_t)(w[b >> 2] >> (8 * (b & 3)));
+        }
+      }
+    }
+    // the edits' new bytes
+    if (lead) {
+      uint8_t* o = out + en[eidx];
+      if (!a.is_delete) {
+        uint64_t prev = nk[lane];
+        if (r0 == 0) {
+#pragma unroll
+          for (int b = 0; b < 8; b++) o[b] = (uint8_t)(prev >> (8 * b));
+          o += 8;
+        } else {
+          o += leb_put(o, prev - old[r0 - 1]);
+        }
+        for (uint32_t q = lane + 1; q < gend; q++) { o += leb_put(o, nk[q] - prev); prev = nk[q]; }
+        if (r0 < m) leb_put(o, old[r0] - prev);
+      } else {
+        const uint32_t r1 = r0 + (gend - lane);
+        if (r1 < m) {
+          if (r0 == 0) {
+#pragma unroll
+            for (int b = 0; b < 8; b++) o[b] = (uint8_t)(old[r1] >> (8 * b));
+          } else {
+            leb_put(o, old[r1] - old[r0 - 1]);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    for (uint32_t p = lane * 16; p < wend; p += 512)
+      *reinterpret_cast<uint4*>(leafp + p) = *reinterpret_cast<const uint4*>(out + p);
+    if (lane == 0) {
+      a.used[j] = nb;
+      a.cnt[j] = newc;
+      a.heads[j] = newc ? newhead : KEY_MAX;
+      a.T_state[t] = kInPlace;
+      a.T_newcnt[t] = newc;
+      a.T_newbytes[t] = nb;
+      if (newc == 0) atomicAdd(&a.st->nempty, 1ull);
+    }
+    for (uint32_t c = fc0 + lane; c < fc1; c += 32) a.chunk_cnt[c] = 0;
+    __syncwarp();
+  }
+}
 
 // WRITE == false: count every work item, rewrite single-item leaves in place
 // when they fit.  WRITE == true: recompute the items of pending leaves and
@@ -164,12 +376,36 @@ __global__ void __launch_bounds__(kT) k_merge(MergeArgs a) {
   uint64_t* nk = sl + kChunk;
   uint8_t* buf = reinterpret_cast<uint8_t*>(nk + kChunk);
   const uint64_t nch = a.st->nchunks;
-  for (uint64_t c = (uint64_t)blockIdx.x * wpb + warp; c < nch; c += (uint64_t)gridDim.x * wpb) {
+  // 32 work items are screened per step (one per lane), then the warp takes
+  // the ones that need this kernel in turn
+  for (uint64_t base = ((uint64_t)blockIdx.x * wpb + warp) * 32; base < nch;
+       base += (uint64_t)gridDim.x * wpb * 32) {
+   bool need = false;
+   {
+    const uint64_t cc = base + lane;
+    if (cc < nch) {
+      const uint32_t tt = a.chunk_tid[cc];
+      need = WRITE ? a.T_state[tt] == kPending
+                   : !small_slice(a.T_begin[tt], a.T_begin[tt + 1], a.T_oldused[tt]);
+    }
+   }
+   unsigned todo = __ballot_sync(FULL, need);
+   while (todo) {
+    const uint64_t c = base + (__ffs(todo) - 1);
+    todo &= todo - 1;
     const uint32_t t = a.chunk_tid[c];
-    if (WRITE && a.T_state[t] != kPending) continue;
     const uint32_t j = a.chunk_leaf[c];
-    const uint32_t b = a.chunk_begin[c], e = a.chunk_begin[c + 1];
+    uint32_t b = a.chunk_begin[c], e = a.chunk_begin[c + 1];
     const uint32_t tb = a.T_begin[t], te = a.T_begin[t + 1];
+    // a slice of at most kChunk keys that the chunk grid happens to split is
+    // merged whole by its first item (the others have nothing to do)
+    if (te - tb <= kChunk) {
+      if (b != tb) {
+        if (!WRITE && lane == 0) a.chunk_cnt[c] = 0;
+        continue;
+      }
+      e = te;
+    }
     const bool first = (b == tb), last = (e == te);
     const uint32_t s = e - b;
     const uint32_t uold = a.T_oldused[t], m = a.T_oldcnt[t];
@@ -303,6 +539,7 @@ __global__ void __launch_bounds__(kT) k_merge(MergeArgs a) {
       a.chunk_cnt[c] = r;
     }
     __syncwarp();
+   }
   }
 }
 
@@ -342,7 +579,7 @@ struct FinArgs {
 __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
   if (a.st->err) return;
   const uint64_t nT = a.st->nT;
-  ull mb = 0;
+  ull mb = 0, dl = 0, np = 0;
   for (uint64_t t = gtid(); t < nT; t += gstride()) {
     const uint32_t state = a.T_state[t];
     const uint32_t oldc = a.T_oldcnt[t], newc = a.T_newcnt[t];
@@ -360,12 +597,12 @@ __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
       }
       continue;
     }
-    atomicAdd(&a.st->delta, (ull)(a.is_delete ? oldc - newc : newc - oldc));
+    dl += (ull)(a.is_delete ? oldc - newc : newc - oldc);
     const uint64_t nb = a.T_newbytes[t];
     if (state == kPending) {
       a.used[j] = (uint32_t)nb;
       a.cnt[j] = newc;
-      atomicAdd(&a.st->npend, 1ull);
+      np++;
     }
     if (node_violates(a.B, a.H, 0, 1, nb)) {
       const ull v = atomicAdd(&a.st->nviol, 1ull);
@@ -373,6 +610,13 @@ __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
     } else if (state == kPending) {
       mark_node(a.bits, a.lv, 0, j, a.cand, a.st);
     }
+  }
+  // one atomic per warp for the batch totals
+  dl = warp_sum(dl);
+  np = warp_sum(np);
+  if (lane_id() == 0) {
+    if (dl) atomicAdd(&a.st->delta, dl);
+    if (np) atomicAdd(&a.st->npend, np);
   }
   if (a.merge_bytes) {
     mb = warp_sum(mb);
@@ -935,6 +1179,8 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   ma.T_begin = ro.T_begin;
   ma.T_oldcnt = ro.T_oldcnt;
   ma.T_oldused = ro.T_oldused;
+  ma.T_leaf = ro.T_leaf;
+  ma.T_first_chunk = ro.T_first_chunk;
   ma.T_newcnt = ro.T_newcnt;
   ma.T_state = ro.T_state;
   ma.T_newbytes = ro.T_newbytes;
@@ -956,6 +1202,20 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
       1, std::min<uint64_t>((k + kChunk + mwarps - 1) / mwarps, (uint64_t)h->num_sms * 4));
   prof_end(h, st);
   prof_begin(h, PH_MERGE, st);
+  {
+    const size_t sper = small_warp_bytes(LB);
+    const int swarps = (int)std::max<size_t>(1, std::min<size_t>(8, (216 * 1024) / (4 * sper)));
+    static bool sattr = false;
+    if (!sattr) {
+      CPMA_CUDA(cudaFuncSetAttribute(k_merge_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     200 * 1024));
+      sattr = true;
+    }
+    const int sgrid = (int)std::max<uint64_t>(
+        1, std::min<uint64_t>((k + swarps - 1) / swarps, (uint64_t)h->num_sms * 8));
+    k_merge_small<<<sgrid, swarps * 32, sper * swarps, st>>>(ma);
+    h->launches++;
+  }
   k_merge<false><<<mgrid, mwarps * 32, msmem, st>>>(ma);
   h->launches++;
   CPMA_CUDA(cudaGetLastError());
