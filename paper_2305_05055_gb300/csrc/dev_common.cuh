@@ -227,6 +227,120 @@ __device__ __forceinline__ uint32_t elem_cost(const uint64_t* z, uint32_t i) {
 }
 
 // ---------------------------------------------------------------------------
+// Bit-parallel summary of the codes in one lane's 16 bytes of a leaf, for
+// leaves whose codes are at most 4 bytes long (deltas < 2^28).
+//
+// Bytes outside [b_lo, b_hi) are zeroed; they then read as one-byte codes of
+// value 0 and are dropped from the terminator mask.  For every byte the group
+// index g (its position inside its code, counted within this lane) follows
+// from the continuation flags of the 1, 2 and 3 bytes before it (funnel
+// shifts across words); the sum of the codes' own bits is then
+// sum_g 2^(7g) * (sum of the 7-bit values of the bytes with that g), four
+// byte-class dot products per word (__vcmpeq4, __dp4a).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t bytemask4(uint32_t b4) {  // 4 bits -> 0x00/0xFF bytes
+  return ((b4 * 0x00204081u) & 0x01010101u) * 0xFFu;
+}
+__device__ __forceinline__ uint32_t gather4(uint32_t x01) {  // bit 0 of each byte -> 4 bits
+  return ((x01 * 0x01020408u) >> 24) & 0xFu;
+}
+__device__ __forceinline__ uint32_t compact7(uint32_t y) {  // 4 bytes' 7-bit groups, LSB first
+  y &= 0x7F7F7F7Fu;
+  return (y & 0x7Fu) | ((y >> 1) & 0x3F80u) | ((y >> 2) & 0x1FC000u) | ((y >> 3) & 0xFE00000u);
+}
+__device__ __forceinline__ uint32_t mask7(uint32_t groups) {  // low 7*groups bits, groups <= 4
+  return groups >= 4 ? 0x0FFFFFFFu : ((1u << (7u * groups)) - 1u);
+}
+// 32-bit window of the 16 bytes x[] starting at byte s (zeros past the end)
+__device__ __forceinline__ uint32_t window32(const uint32_t x[4], uint32_t s) {
+  const uint64_t lo = (uint64_t)x[0] | ((uint64_t)x[1] << 32);
+  const uint64_t hi = (uint64_t)x[2] | ((uint64_t)x[3] << 32);
+  uint64_t win;
+  if (s == 0) win = lo;
+  else if (s < 8) win = (lo >> (8u * s)) | (hi << (64u - 8u * s));
+  else if (s < 16) win = hi >> (8u * (s - 8u));
+  else win = 0;
+  return (uint32_t)win;
+}
+
+struct LaneCodes {
+  uint32_t x[4];      // the lane's bytes, zero outside [b_lo, b_hi)
+  uint32_t term;      // bit b: byte b ends a code
+  uint32_t D;         // own bits of the codes ending here (first one without carry)
+  uint32_t W;         // sum over those codes of (index among them) * own bits
+  uint32_t first_own; // own bits of the first code ending here
+  uint32_t first_len; // its own byte count
+  uint32_t tail;      // bits of the partial code after the last terminator
+  uint32_t tail_sh;   // 7 * its byte count
+  bool bad;           // a code longer than 4 bytes, or no terminator
+};
+
+template <bool WANT_W>
+__device__ __forceinline__ void lane_codes(const uint32_t w[4], int b_lo, int b_hi, LaneCodes& L) {
+  uint32_t range = 0;
+  if (b_hi > b_lo) range = ((b_hi == 16) ? 0xFFFFu : ((1u << b_hi) - 1u)) & ~((1u << b_lo) - 1u);
+  uint32_t cb[4], tb[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const uint32_t rm = bytemask4((range >> (4 * q)) & 0xFu);
+    L.x[q] = w[q] & rm;
+    cb[q] = (L.x[q] >> 7) & 0x01010101u;
+    tb[q] = (rm & 0x01010101u) & ~cb[q];
+  }
+  L.term = gather4(tb[0]) | (gather4(tb[1]) << 4) | (gather4(tb[2]) << 8) | (gather4(tb[3]) << 12);
+  uint32_t S0 = 0, S1 = 0, S2 = 0, S3 = 0, W0 = 0, W1 = 0, W2 = 0, W3 = 0;
+  uint32_t badm = 0, base = 0;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const uint32_t prev = q ? cb[q - 1] : 0u;
+    const uint32_t p1 = __funnelshift_l(prev, cb[q], 8);
+    const uint32_t p2 = __funnelshift_l(prev, cb[q], 16);
+    const uint32_t p3 = __funnelshift_l(prev, cb[q], 24);
+    const uint32_t a12 = p1 & p2, a123 = a12 & p3;
+    const uint32_t g = p1 + a12 + a123;
+    badm |= a123 & cb[q];
+    const uint32_t v = L.x[q] & 0x7F7F7F7Fu;
+    const uint32_t v0 = v & __vcmpeq4(g, 0u), v1 = v & __vcmpeq4(g, 0x01010101u);
+    const uint32_t v2 = v & __vcmpeq4(g, 0x02020202u), v3 = v & __vcmpeq4(g, 0x03030303u);
+    S0 = __dp4a(v0, 0x01010101u, S0);
+    S1 = __dp4a(v1, 0x01010101u, S1);
+    S2 = __dp4a(v2, 0x01010101u, S2);
+    S3 = __dp4a(v3, 0x01010101u, S3);
+    if constexpr (WANT_W) {
+      // terminators before each byte of the word (bytes), plus the earlier words'
+      const uint32_t lidx = tb[q] * 0x01010100u + base * 0x01010101u;
+      W0 = __dp4a(v0, lidx, W0);
+      W1 = __dp4a(v1, lidx, W1);
+      W2 = __dp4a(v2, lidx, W2);
+      W3 = __dp4a(v3, lidx, W3);
+      base += __popc(tb[q]);
+    }
+  }
+  const uint32_t Dall = S0 + (S1 << 7) + (S2 << 14) + (S3 << 21);
+  L.bad = badm != 0 || (range != 0 && L.term == 0);
+  L.tail = 0;
+  L.tail_sh = 0;
+  L.first_own = 0;
+  L.first_len = 0;
+  L.D = 0;
+  L.W = 0;
+  if (L.term) {
+    const uint32_t lt = 31u - (uint32_t)__clz(L.term);
+    const uint32_t tl = (uint32_t)b_hi - 1u - lt;
+    L.tail = compact7(window32(L.x, lt + 1u));
+    L.tail_sh = 7u * tl;
+    const uint32_t ft = (uint32_t)__ffs(L.term) - 1u;
+    L.first_len = ft + 1u - (uint32_t)b_lo;
+    L.first_own = compact7(b_lo == 0 ? L.x[0] : L.x[2]) & mask7(L.first_len);
+    L.D = Dall - L.tail;
+    if constexpr (WANT_W) {
+      const uint32_t c = __popc(L.term);
+      L.W = (W0 + (W1 << 7) + (W2 << 14) + (W3 << 21)) - c * L.tail;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Sum (mod 2^64) and count of every element of the leaves [j0, j1), added to
 // the calling lane's partials (the caller reduces them over the warp).
 //
@@ -238,9 +352,9 @@ __device__ __forceinline__ uint32_t elem_cost(const uint64_t* z, uint32_t i) {
 // (m - 1 - B) * D - W with D = sum of its deltas and W = sum of lidx * delta
 // (lidx = position among the chunk's codes).  The code a chunk starts in the
 // middle of is completed with the previous chunk's partial bits (one
-// shuffle).  Chunks decode with 32-bit arithmetic, valid while every code is
-// at most 4 bytes (deltas < 2^28); a window of leaves with a longer code is
-// summed again by the general decoder instead.
+// shuffle).  Chunks are summarised bit-parallel (lane_codes), valid while
+// every code is at most 4 bytes (deltas < 2^28); a window of leaves with a
+// longer code is summed again by the general decoder instead.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void warp_span_sum(const uint8_t* __restrict__ data,
                                               const uint32_t* __restrict__ used,
@@ -283,40 +397,23 @@ __device__ __forceinline__ void warp_span_sum(const uint8_t* __restrict__ data,
       const uint32_t w[4] = {v.x, v.y, v.z, v.w};
       const int b_lo = (cw == 0) ? 8 : 0;
       const int b_hi = act ? (int)min(16u, u - p0) : 0;
-      uint32_t range = 0;
-      if (b_hi > b_lo)
-        range = ((b_hi == 16) ? 0xFFFFu : ((1u << b_hi) - 1u)) & ~((1u << b_lo) - 1u);
-      uint32_t cur = 0, sh = 0, D = 0, W = 0, lidx = 0, first_own = 0, term = 0;
-#pragma unroll
-      for (int b = 0; b < 16; b++) {
-        const uint32_t byte = (w[b >> 2] >> (8 * (b & 3))) & 0xFFu;
-        const bool inr = (range >> b) & 1u;
-        const bool t = inr && !(byte & 0x80u);
-        bad |= inr && (byte & 0x80u) && sh >= 21u;
-        if (inr) { cur |= (byte & 0x7Fu) << sh; sh += 7u; }
-        if (t) {
-          if (term == 0) first_own = cur;
-          D += cur;
-          W += lidx * cur;
-          lidx++;
-          term |= 1u << b;
-          cur = 0;
-          sh = 0;
-        }
-      }
-      if (range && !term) bad = true;
+      LaneCodes lc;
+      lane_codes<true>(w, b_lo, b_hi, lc);
+      bad |= lc.bad;
       // the partial code left by the previous chunk of the same leaf
       const uint32_t prev_li = __shfl_up_sync(FULL, li, 1);
-      uint32_t pv = __shfl_up_sync(FULL, cur, 1);
-      uint32_t ps = __shfl_up_sync(FULL, sh, 1);
+      uint32_t pv = __shfl_up_sync(FULL, lc.tail, 1);
+      uint32_t ps = __shfl_up_sync(FULL, lc.tail_sh, 1);
       if (lane == 0 || prev_li != li) {
         if (lane == 0 && cont_li == li && cw > 0) { pv = cont_val; ps = cont_sh; }
         else { pv = 0; ps = 0; }
       }
+      const uint32_t term = lc.term;
+      uint32_t D = 0;
+      const uint32_t W = lc.W;
       if (term) {
-        const uint32_t own = (uint32_t)__ffs(term) - (uint32_t)b_lo;
-        if (ps / 7u + own > 4u) bad = true;
-        D = D - first_own + pv + (first_own << ps);
+        if (ps / 7u + lc.first_len > 4u) bad = true;
+        D = lc.D - lc.first_own + pv + (lc.first_own << ps);
       }
       // codes of this leaf in earlier chunks (segmented scan)
       const uint32_t c = __popc(term);
@@ -333,8 +430,8 @@ __device__ __forceinline__ void warp_span_sum(const uint8_t* __restrict__ data,
       }
       cont_li = __shfl_sync(FULL, li, 31);
       cont_cnt = __shfl_sync(FULL, B + c, 31);
-      cont_val = __shfl_sync(FULL, cur, 31);
-      cont_sh = __shfl_sync(FULL, sh, 31);
+      cont_val = __shfl_sync(FULL, lc.tail, 31);
+      cont_sh = __shfl_sync(FULL, lc.tail_sh, 31);
     }
     if (__any_sync(FULL, bad)) {
       const uint64_t je = min(w0 + 32, j1);

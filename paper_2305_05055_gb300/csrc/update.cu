@@ -150,15 +150,379 @@ struct MergeArgs {
 
 // Slices of at most kSmall keys into a non-empty leaf take the splice path.
 constexpr uint32_t kSmall = 32;
+// T-entry state set by the lane-granular insert when a leaf holds a code of
+// more than 4 bytes: the element-array splice takes it instead.
+constexpr uint32_t kFallback = 3;
+
+// Copy the bytes of the old leaf (global, uold bytes) that lie outside the E
+// edits into out[] (shared, zeroed), each shifted by the size change of the
+// edits before it.  Edit e replaces old bytes [es[e], ee[e]); shc[e] is the
+// total size change of edits 0..e.  A lane whose 16 bytes hold no edit
+// boundary copies them as words (funnel shifts; the two partial words are
+// OR-ed in, the buffer being zeroed and every byte having one writer).  The
+// word copy writes up to 20 bytes from a lane's start, past the used bytes
+// (zeros there, packed left): out[] needs 32 bytes of slack after LB.
+__device__ __forceinline__ void splice_copy(const uint8_t* __restrict__ leafp, uint32_t uold,
+                                            uint8_t* out, uint32_t E, const uint32_t* es,
+                                            const uint32_t* ee, const int32_t* shc) {
+  const unsigned lane = lane_id();
+  for (uint32_t p0 = lane * 16; p0 < uold; p0 += 512) {
+    const uint4 v = *reinterpret_cast<const uint4*>(leafp + p0);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t q = 0;
+    while (q < E && ee[q] <= p0) q++;
+    int32_t shift = q ? shc[q - 1] : 0;
+    const uint32_t lim = min(16u, uold - p0);
+    if (q == E || es[q] >= p0 + 16) {
+      // bytes past uold are zero (packed left), so the whole 16 can go
+      const uint32_t d0 = (uint32_t)((int32_t)p0 + shift);
+      uint32_t* ow = reinterpret_cast<uint32_t*>(out);
+      const uint32_t k0 = d0 >> 2, sb = d0 & 3u;
+      if (sb == 0) {
+        ow[k0] = w[0]; ow[k0 + 1] = w[1]; ow[k0 + 2] = w[2]; ow[k0 + 3] = w[3];
+      } else {
+        const uint32_t sh8 = 8u * sb;
+        atomicOr(ow + k0, w[0] << sh8);
+        ow[k0 + 1] = __funnelshift_l(w[0], w[1], sh8);
+        ow[k0 + 2] = __funnelshift_l(w[1], w[2], sh8);
+        ow[k0 + 3] = __funnelshift_l(w[2], w[3], sh8);
+        atomicOr(ow + k0 + 4, w[3] >> (32u - sh8));
+      }
+    } else {
+#pragma unroll
+      for (int b = 0; b < 16; b++) {
+        const uint32_t tt = p0 + b;
+        if ((uint32_t)b >= lim) continue;
+        while (q < E && ee[q] <= tt) { shift = shc[q]; q++; }
+        if (q < E && es[q] <= tt) continue;
+        out[(int32_t)tt + shift] = (uint8_t)(w[b >> 2] >> (8 * (b & 3)));
+      }
+    }
+  }
+}
 
 __host__ __device__ __forceinline__ size_t small_warp_bytes(uint32_t LB) {
-  // old[LB] u64, pos[LB] u16, out[LB] bytes, keys[kSmall] u64, ranks[kSmall]
-  // u32, edits: old start, old end, new start, cumulative shift (u32 each)
-  return (size_t)8 * LB + 2 * LB + LB + 8 * kSmall + 4 * kSmall + 16 * kSmall;
+  // old[LB] u64, pos[LB] u16, out[LB + 32] bytes (the word copy may spill
+  // up to 20 zero bytes past LB), keys[kSmall] u64, ranks[kSmall] u32, edits:
+  // old start, old end, new start, cumulative shift (u32 each)
+  return (size_t)8 * LB + 2 * LB + LB + 32 + 8 * kSmall + 4 * kSmall + 16 * kSmall;
 }
 
 __device__ __forceinline__ bool small_slice(uint32_t tb, uint32_t te, uint32_t uold) {
   return te - tb <= kSmall && uold > 0;
+}
+
+// out[512 + 32] (slack for the word copy), 4 u64 and 8 u32 arrays of kSmall
+constexpr size_t kLaneOut = 512 + 32;
+constexpr size_t kLaneWarpBytes = kLaneOut + 8 * kSmall * 4 + 4 * kSmall * 8 + 16;
+
+// Copy of the kept old bytes for the lane-granular insert: the lane's 16
+// bytes are cut into the segments that no edit removes, and each segment is
+// OR-ed into out[] as five shifted words (out[] zeroed, one writer per byte,
+// 32 bytes of slack after the leaf).
+__device__ __forceinline__ void splice_copy_words(const uint32_t w[4], uint32_t p0, uint32_t uold,
+                                                  uint8_t* out, uint32_t E, const uint32_t* es,
+                                                  const uint32_t* ee, const int32_t* shc) {
+  if (p0 >= uold) return;
+  uint32_t q = 0;
+  while (q < E && ee[q] <= p0) q++;
+  int32_t shift = q ? shc[q - 1] : 0;
+  uint32_t cur = p0;
+  const uint32_t lim = min(p0 + 16u, uold);
+  uint32_t* ow = reinterpret_cast<uint32_t*>(out);
+  while (cur < lim) {
+    const uint32_t send = (q < E) ? min(es[q], lim) : lim;
+    if (send > cur) {
+      // bytes [cur, send) of the lane, shifted by `shift`
+      const uint32_t a = cur - p0, b = send - p0;
+      const uint32_t segm = ((b >= 16) ? 0xFFFFu : ((1u << b) - 1u)) & ~((1u << a) - 1u);
+      uint32_t m[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) m[k] = w[k] & bytemask4((segm >> (4 * k)) & 0xFu);
+      const uint32_t d0 = (uint32_t)((int32_t)p0 + shift);
+      const uint32_t k0 = d0 >> 2, sh8 = 8u * (d0 & 3u);
+      if (sh8 == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+          if (m[k]) atomicOr(ow + k0 + k, m[k]);
+      } else {
+        atomicOr(ow + k0, m[0] << sh8);
+#pragma unroll
+        for (int k = 1; k < 4; k++) {
+          const uint32_t y = __funnelshift_l(m[k - 1], m[k], sh8);
+          if (y) atomicOr(ow + k0 + k, y);
+        }
+        const uint32_t yl = m[3] >> (32u - sh8);
+        if (yl) atomicOr(ow + k0 + 4, yl);
+      }
+    }
+    if (q < E && es[q] < lim) {
+      cur = max(cur, ee[q]);
+      shift = shc[q];
+      q++;
+    } else {
+      break;
+    }
+  }
+}
+
+// Insert of a slice of at most kSmall keys into a leaf of at most 512 used
+// bytes, without decoding the whole leaf into an element array.  Each lane
+// summarises its 16 bytes bit-parallel (lane_codes: how many codes end there
+// and the sum of their deltas); warp scans then give every lane the value of
+// the element before its first code.  A key x belongs to the lane whose value
+// interval holds it; for each such lane the whole warp decodes that lane's
+// codes one byte position per lane, a scan gives their values and a ballot the
+// first code >= x: x's rank, its neighbours and the byte span of the code x
+// splits.  Edits are as in the element-array splice below, which also takes
+// any leaf this kernel cannot (a code longer than 4 bytes, or a result over
+// 512 bytes that still fits a larger leaf: state kFallback).  Per-leaf
+// metadata is loaded for 32 leaves at once.
+__global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  if (a.st->err) return;
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const unsigned wpb = blockDim.x >> 5;
+  uint8_t* wbase = smem + (size_t)warp * kLaneWarpBytes;
+  uint8_t* out = wbase;
+  uint64_t* kx = reinterpret_cast<uint64_t*>(wbase + kLaneOut);  // key
+  uint64_t* kp = kx + kSmall;                                     // predecessor value
+  uint64_t* ks = kp + kSmall;                                     // successor value
+  uint64_t* kpad = ks + kSmall;
+  uint32_t* kr = reinterpret_cast<uint32_t*>(kpad + kSmall);  // rank; bit 31 = present
+  uint32_t* kcs = kr + kSmall;                                 // successor code start
+  uint32_t* kce = kcs + kSmall;                                // successor code end (excl.)
+  uint32_t* ktl = kce + kSmall;                                // owning lane
+  uint32_t* es = ktl + kSmall;
+  uint32_t* ee = es + kSmall;
+  uint32_t* en = ee + kSmall;
+  int32_t* shc = reinterpret_cast<int32_t*>(en + kSmall);
+  const uint64_t nT = a.st->nT;
+  for (uint64_t tbase = ((uint64_t)blockIdx.x * wpb + warp) * 32; tbase < nT;
+       tbase += (uint64_t)gridDim.x * wpb * 32) {
+    // metadata of 32 touched leaves, one per lane
+    const uint64_t ti = tbase + lane;
+    uint32_t i_tb = 0, i_te = 0, i_uold = 0, i_j = 0, i_m = 0, i_fc0 = 0, i_fc1 = 0;
+    if (ti < nT) {
+      i_tb = a.T_begin[ti]; i_te = a.T_begin[ti + 1]; i_uold = a.T_oldused[ti];
+      i_j = a.T_leaf[ti]; i_m = a.T_oldcnt[ti];
+      i_fc0 = a.T_first_chunk[ti]; i_fc1 = a.T_first_chunk[ti + 1];
+    }
+    unsigned todo = __ballot_sync(FULL, ti < nT && small_slice(i_tb, i_te, i_uold) && i_uold <= 512);
+    while (todo) {
+    const unsigned src = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const uint64_t t = tbase + src;
+    const uint32_t tb = __shfl_sync(FULL, i_tb, src), te = __shfl_sync(FULL, i_te, src);
+    const uint32_t uold = __shfl_sync(FULL, i_uold, src), j = __shfl_sync(FULL, i_j, src);
+    const uint32_t m = __shfl_sync(FULL, i_m, src);
+    const uint32_t fc0 = __shfl_sync(FULL, i_fc0, src), fc1 = __shfl_sync(FULL, i_fc1, src);
+    const uint32_t s = te - tb;
+    uint8_t* leafp = a.data + (size_t)j * a.LB;
+    // ---- bit-parallel summary of each lane's 16 bytes ----
+    const uint32_t p0 = lane * 16u;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (p0 < uold) v = *reinterpret_cast<const uint4*>(leafp + p0);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    const int b_lo = lane == 0 ? 8 : 0;
+    const int b_hi = (uold > p0) ? (int)min(16u, uold - p0) : 0;
+    LaneCodes lc;
+    lane_codes<false>(w, b_lo, b_hi, lc);
+    bool bad = lc.bad;
+    uint32_t pv = __shfl_up_sync(FULL, lc.tail, 1);
+    uint32_t ps = __shfl_up_sync(FULL, lc.tail_sh, 1);
+    if (lane == 0) { pv = 0; ps = 0; }
+    uint32_t D = 0;
+    if (lc.term) {
+      if (ps / 7u + lc.first_len > 4u) bad = true;
+      D = lc.D - lc.first_own + pv + (lc.first_own << ps);
+    }
+    if (__any_sync(FULL, bad)) {
+      if (lane == 0) a.T_state[t] = kFallback;
+      continue;
+    }
+    const uint32_t c = __popc(lc.term);
+    const uint32_t B = warp_incl_scan(c) - c;                 // codes in earlier lanes
+    if (__shfl_sync(FULL, B + c, 31) + 1u != m) {           // must match the stored count
+      if (lane == 0) atomicOr(&a.st->err, kErrState);
+      continue;
+    }
+    const uint64_t Dinc = warp_incl_scan((uint64_t)D);
+    const uint64_t head = __shfl_sync(FULL, (uint64_t)w[0] | ((uint64_t)w[1] << 32), 0);
+    const uint64_t V = head + (Dinc - D);                       // element before my codes
+    const uint64_t lastv = head + __shfl_sync(FULL, Dinc, 31);  // the last element
+    // ---- keys: owning lane, or before the head / after the last element ----
+    uint64_t x = 0;
+    bool valid = false;
+    if (lane < s) {
+      x = a.u[tb + lane];
+      valid = !(lane > 0 && a.u[tb + lane - 1] == x);
+    }
+    unsigned owners = 0;
+    for (uint32_t k = 0; k < s; k++) {
+      const uint64_t xk = __shfl_sync(FULL, x, k);
+      const unsigned own = __ballot_sync(FULL, c > 0 && V < xk && xk <= V + D);
+      if (lane == k) ktl[k] = own ? (uint32_t)(__ffs(own) - 1) : 0xFFFFFFFFu;
+      owners |= own;
+    }
+    if (lane < s) {
+      kx[lane] = x;
+      if (x <= head) {            // before the head, or the head itself
+        kr[lane] = (x == head) ? 0x80000000u : 0u;
+        kp[lane] = 0; ks[lane] = head; kcs[lane] = 0; kce[lane] = 8;
+      } else if (x > lastv) {     // after the last element
+        kr[lane] = m;
+        kp[lane] = lastv; ks[lane] = 0; kcs[lane] = uold; kce[lane] = uold;
+      }
+    }
+    __syncwarp();
+    // ---- each owning lane's codes, decoded by the whole warp ----
+    while (owners) {
+      const unsigned o = __ffs(owners) - 1;
+      owners &= owners - 1;
+      uint32_t xo[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) xo[k] = __shfl_sync(FULL, lc.x[k], o);
+      const uint32_t term_o = __shfl_sync(FULL, lc.term, o);
+      const uint32_t pv_o = __shfl_sync(FULL, pv, o), ps_o = __shfl_sync(FULL, ps, o);
+      const uint32_t B_o = __shfl_sync(FULL, B, o);
+      const uint64_t V_o = __shfl_sync(FULL, V, o);
+      const uint32_t blo_o = o == 0 ? 8u : 0u;
+      // lane t < 16 takes the code ending at byte t of lane o
+      const bool is_t = lane < 16 && ((term_o >> lane) & 1u);
+      const uint32_t before = lane < 16 ? (term_o & ((1u << lane) - 1u)) : 0u;
+      const bool firstc = before == 0;
+      const uint32_t st0 = firstc ? blo_o : (32u - (uint32_t)__clz(before));
+      uint32_t code = 0;
+      if (is_t) {
+        const uint32_t own = compact7(window32(xo, st0)) & mask7(lane + 1u - st0);
+        code = firstc ? pv_o + (own << ps_o) : own;
+      }
+      const uint32_t cinc = warp_incl_scan(code);
+      const uint64_t val = V_o + cinc;
+      uint32_t kk = 0, kend = 0;
+      for (uint32_t k = 0; k < s; k++)
+        if (ktl[k] == o) { if (kend == 0) kk = k; kend = k + 1; }
+      for (uint32_t k = kk; k < kend; k++) {
+        const uint64_t xk = kx[k];
+        const unsigned hit = __ballot_sync(FULL, is_t && val >= xk);
+        if (lane == (unsigned)(__ffs(hit) - 1)) {
+          kr[k] = (1u + B_o + (uint32_t)__popc(before)) | (xk == val ? 0x80000000u : 0u);
+          kp[k] = val - code;
+          ks[k] = val;
+          kcs[k] = 16u * o + st0 - (firstc ? ps_o / 7u : 0u);
+          kce[k] = 16u * o + lane + 1u;
+        }
+      }
+      __syncwarp();
+    }
+    // ---- kept keys and their gaps ----
+    uint32_t r = 0;
+    bool keep = false;
+    if (lane < s) {
+      r = kr[lane];
+      keep = valid && !(r & 0x80000000u);
+    }
+    const unsigned kb = __ballot_sync(FULL, keep);
+    const uint32_t nn = __popc(kb);
+    uint64_t mx = 0, mp = 0, ms = 0;
+    uint32_t mcs = 0, mce = 0;
+    if (keep) { mx = kx[lane]; mp = kp[lane]; ms = ks[lane]; mcs = kcs[lane]; mce = kce[lane]; }
+    __syncwarp();
+    if (keep) {
+      const uint32_t q = __popc(kb & lanemask_lt());
+      kx[q] = mx; kp[q] = mp; ks[q] = ms; kcs[q] = mcs; kce[q] = mce; kr[q] = r;
+    }
+    __syncwarp();
+    if (nn == 0) {
+      if (lane == 0) {
+        a.T_state[t] = kUnchanged;
+        a.T_newcnt[t] = m;
+        a.T_newbytes[t] = uold;
+      }
+      for (uint32_t cq = fc0 + lane; cq < fc1; cq += 32) a.chunk_cnt[cq] = 0;
+      __syncwarp();
+      continue;
+    }
+    bool lead = false;
+    if (lane < nn) lead = lane == 0 || kr[lane - 1] != kr[lane];
+    const unsigned lb = __ballot_sync(FULL, lead);
+    const uint32_t E = __popc(lb);
+    uint32_t e_os = 0, e_oe = 0, e_nl = 0, gend = 0, r0 = 0;
+    if (lead) {
+      const unsigned after = lb & ~((2u << lane) - 1u);
+      gend = after ? (uint32_t)(__ffs(after) - 1) : nn;
+      r0 = kr[lane];
+      e_os = kcs[lane];
+      e_oe = kce[lane];
+      uint64_t prev = kx[lane];
+      uint32_t len = (r0 == 0) ? 8u : leb_len(kx[lane] - kp[lane]);
+      for (uint32_t q = lane + 1; q < gend; q++) { len += leb_len(kx[q] - prev); prev = kx[q]; }
+      if (r0 < m) len += leb_len(ks[lane] - prev);
+      e_nl = len;
+    }
+    const uint32_t eidx = __popc(lb & lanemask_lt());
+    const int32_t delta = lead ? (int32_t)e_nl - (int32_t)(e_oe - e_os) : 0;
+    const int32_t dinc = warp_incl_scan(delta);
+    const int32_t total = __shfl_sync(FULL, dinc, 31);
+    if (lead) {
+      es[eidx] = e_os;
+      ee[eidx] = e_oe;
+      en[eidx] = (uint32_t)((int32_t)e_os + dinc - delta);
+      shc[eidx] = dinc;
+    }
+    const uint32_t nb = (uint32_t)((int32_t)uold + total);
+    const uint32_t newc = m + nn;
+    const uint64_t newhead = (kr[0] == 0) ? kx[0] : head;
+    __syncwarp();
+    if (nb > a.LB) {
+      if (lane == 0) {
+        a.T_state[t] = kPending;
+        a.T_newcnt[t] = newc;
+        a.T_newbytes[t] = nb;
+      }
+      for (uint32_t cq = fc0 + lane; cq < fc1; cq += 32) a.chunk_cnt[cq] = (cq == fc0) ? newc : 0u;
+      __syncwarp();
+      continue;
+    }
+    if (nb > 512) {  // fits the leaf but not this kernel's 512-byte buffer
+      if (lane == 0) a.T_state[t] = kFallback;
+      __syncwarp();
+      continue;
+    }
+    const uint32_t wend = (max(uold, nb) + 15u) & ~15u;
+    if (lane * 16 < wend) *reinterpret_cast<uint4*>(out + lane * 16) = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    splice_copy_words(w, p0, uold, out, E, es, ee, shc);
+    __syncwarp();
+    if (lead) {
+      uint8_t* o = out + en[eidx];
+      uint64_t prev = kx[lane];
+      if (r0 == 0) {
+#pragma unroll
+        for (int b = 0; b < 8; b++) o[b] = (uint8_t)(prev >> (8 * b));
+        o += 8;
+      } else {
+        o += leb_put(o, prev - kp[lane]);
+      }
+      for (uint32_t q = lane + 1; q < gend; q++) { o += leb_put(o, kx[q] - prev); prev = kx[q]; }
+      if (r0 < m) leb_put(o, ks[lane] - prev);
+    }
+    __syncwarp();
+    if (lane * 16 < wend)
+      *reinterpret_cast<uint4*>(leafp + lane * 16) = *reinterpret_cast<const uint4*>(out + lane * 16);
+    if (lane == 0) {
+      a.used[j] = nb;
+      a.cnt[j] = newc;
+      a.heads[j] = newhead;
+      a.T_state[t] = kInPlace;
+      a.T_newcnt[t] = newc;
+      a.T_newbytes[t] = nb;
+    }
+    for (uint32_t cq = fc0 + lane; cq < fc1; cq += 32) a.chunk_cnt[cq] = 0;
+    __syncwarp();
+    }
+  }
 }
 
 // Splice merge of a small slice into one leaf (warp per touched leaf).  The
@@ -181,7 +545,7 @@ __global__ void __launch_bounds__(kT, 4) k_merge_small(MergeArgs a) {
   uint64_t* old = reinterpret_cast<uint64_t*>(wbase);
   uint16_t* pos = reinterpret_cast<uint16_t*>(wbase + 8 * (size_t)LB);
   uint8_t* out = wbase + 10 * (size_t)LB;
-  uint64_t* nk = reinterpret_cast<uint64_t*>(wbase + 11 * (size_t)LB);
+  uint64_t* nk = reinterpret_cast<uint64_t*>(wbase + 11 * (size_t)LB + 32);
   uint32_t* nr = reinterpret_cast<uint32_t*>(nk + kSmall);
   uint32_t* es = nr + kSmall;
   uint32_t* ee = es + kSmall;
@@ -192,6 +556,7 @@ __global__ void __launch_bounds__(kT, 4) k_merge_small(MergeArgs a) {
     const uint32_t tb = a.T_begin[t], te = a.T_begin[t + 1];
     const uint32_t uold = a.T_oldused[t];
     if (!small_slice(tb, te, uold)) continue;
+    if (!a.is_delete && uold <= 512 && a.T_state[t] != kFallback) continue;  // lane kernel
     const uint32_t s = te - tb;
     const uint32_t j = a.T_leaf[t];
     const uint32_t m = a.T_oldcnt[t];
@@ -295,28 +660,8 @@ __global__ void __launch_bounds__(kT, 4) k_merge_small(MergeArgs a) {
       *reinterpret_cast<uint4*>(out + p) = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
     // old bytes outside the edits, shifted
-    for (uint32_t p0 = lane * 16; p0 < uold; p0 += 512) {
-      const uint4 v = *reinterpret_cast<const uint4*>(leafp + p0);
-      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-      uint32_t q = 0;
-      while (q < E && ee[q] <= p0) q++;
-      int32_t shift = q ? shc[q - 1] : 0;
-      const uint32_t lim = min(16u, uold - p0);
-      if (q == E || es[q] >= p0 + 16) {
-#pragma unroll
-        for (int b = 0; b < 16; b++)
-          if ((uint32_t)b < lim) out[(int32_t)(p0 + b) + shift] = (uint8_t)(w[b >> 2] >> (8 * (b & 3)));
-      } else {
-#pragma unroll
-        for (int b = 0; b < 16; b++) {
-          const uint32_t tt = p0 + b;
-          if ((uint32_t)b >= lim) continue;
-          while (q < E && ee[q] <= tt) { shift = shc[q]; q++; }
-          if (q < E && es[q] <= tt) continue;
-          out[(int32_t)tt + shift] = (uint8_t)(w[b >> 2] >> (8 * (b & 3)));
-        }
-      }
-    }
+    splice_copy(leafp, uold, out, E, es, ee, shc);
+    __syncwarp();
     // the edits' new bytes
     if (lead) {
       uint8_t* o = out + en[eidx];
@@ -1213,6 +1558,10 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
     }
     const int sgrid = (int)std::max<uint64_t>(
         1, std::min<uint64_t>((k + swarps - 1) / swarps, (uint64_t)h->num_sms * 8));
+    if (!is_delete) {
+      k_insert_lane<<<sgrid, 256, kLaneWarpBytes * 8, st>>>(ma);
+      h->launches++;
+    }
     k_merge_small<<<sgrid, swarps * 32, sper * swarps, st>>>(ma);
     h->launches++;
   }

@@ -216,3 +216,41 @@ def test_many_uneven_ranges_one_launch():
     ws, wc = p.range_map(lo, hi)
     assert np.array_equal(cp.to_u64(c), wc)
     assert np.array_equal(cp.to_u64(s), ws)
+
+
+@pytest.mark.parametrize("LB", [256, 512, 1024])
+def test_small_batches_hit_every_splice_case(LB):
+    """Many batches of 1..40 keys: keys just below / equal to / just above
+    existing keys and heads, runs in one gap, keys past the last element,
+    repeats and deletes of neighbours -- the splice paths' edge cases."""
+    rng = np.random.default_rng(LB + 7)
+    base = np.unique(W.uniform_keys(81, 6000, bits=30))
+    g = cp.CPMA(T(base), leaf_bytes=LB)
+    o = oracle.SeqCPMA(base, leaf_bytes=LB)
+    p = oracle.PlainSet(base)
+    for r in range(60):
+        S = p.S
+        k = int(rng.integers(1, 41))
+        pick = S[rng.integers(0, S.size, size=k)].astype(np.int64)
+        kind = r % 5
+        if kind == 0:
+            keys = pick + rng.integers(-2, 3, size=k)           # neighbours and equals
+        elif kind == 1:
+            _, _, heads = g.layout()
+            hd = cp.to_u64(heads).astype(np.int64)
+            keys = hd[rng.integers(0, hd.size, size=k)] + rng.integers(-3, 2, size=k)
+        elif kind == 2:
+            keys = np.concatenate([pick[:1] + np.arange(1, k + 1), pick[:1] + 1])  # one gap
+        elif kind == 3:
+            keys = np.int64(S[-1]) + rng.integers(1, 1 << 20, size=k)  # past the end
+        else:
+            keys = np.concatenate([pick, pick[:3]])
+        keys = np.clip(keys, 0, None).astype(np.uint64)
+        if r % 3 == 2:
+            got = int(g.delete_batch(T(keys)).item())
+            assert got == o.delete_batch(keys) == p.delete_batch(keys)
+        else:
+            got = int(g.insert_batch(T(keys)).item())
+            assert got == o.insert_batch(keys) == p.insert_batch(keys)
+        same_layout(g, o)
+    same_queries(g, p, 85)
