@@ -38,6 +38,45 @@ METRIC = "batch-insert keys/s, range-sum elems/s at n=1e8 (% HBM peak); serve p9
 PAPER_INSERT_1E6 = 1.1e8  # Table batch-ins-del, uniform, batch 1e6, 64-core Xeon (context)
 
 
+def aggregate(local_ms: float, units_per_rank: float, dist=None):
+    """Max of the ranks' times and the whole-job rate: every rank processed
+    units_per_rank units, the job took the slowest rank's time."""
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        import torch
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        local_ms = float(t.item())
+        world = dist.get_world_size()
+    else:
+        world = 1
+    return local_ms, world * units_per_rank / (local_ms / 1e3)
+
+
+def kernel_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("update.cu", "dev_common.cuh", "query.cu"):
+        with open(os.path.join(ROOT, "paper_2305_05055_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str, alg_bytes_per_launch: float):
+    """DRAM bytes per launch from the committed ncu summary, scaled from the
+    captured launch to this one by algorithmic bytes; None when the kernel's
+    sources changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        e = t[kernel]
+        if e["sources_sha256"] != kernel_sources_sha():
+            return None
+        return e["dram_bytes"] * alg_bytes_per_launch / e["alg_bytes"]
+    except Exception:
+        return None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -51,6 +90,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="headline only")
     ap.add_argument("--sweep", action="store_true", help="insert/delete sweep 1e3..1e7")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-skew", action="store_true", help="skip the skewed-update rounds")
+    ap.add_argument("--skew-rounds", type=int, default=100)
     return ap.parse_args()
 
 
@@ -253,22 +294,21 @@ def main():
     launches = g.launches() - l0
     prof = g.profile_read()
     g.profile(False)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * nsteps * k / (ms / 1e3)
+    ms, value = aggregate(ms, nsteps * k, dist)
 
     # roofline of the dominant kernel of the step
-    upd = ["sort", "route", "merge", "count", "redistribute", "finish"]
+    upd = ["sort", "route", "merge", "merge_other", "count", "redistribute", "finish"]
     dom = max(upd, key=lambda p: prof[p]["ms"])
+    kernel_of = {"merge": "k_insert_lane", "merge_other": "k_merge_small+k_merge",
+                 "sort": "radix sort", "route": "route", "count": "counting",
+                 "redistribute": "redistribute", "finish": "k_fix_heads"}
     def roof(p, pk=hbm_peak):
         msp, by, calls = prof[p]["ms"], prof[p]["bytes"], max(1, prof[p]["calls"])
         ach = by / (msp / 1e3) / 1e9 if msp > 0 else 0.0
         return {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
-                "frac": ach / pk, "traffic": None, "kernel": p,
-                "ms_per_launch": msp / calls, "bytes_per_launch": by / calls,
-                "peak_kind": peak_kind}
+                "frac": ach / pk, "traffic": measured_traffic(kernel_of.get(p, p), by / calls),
+                "kernel": kernel_of.get(p, p), "ms_per_launch": msp / calls,
+                "bytes_per_launch": by / calls, "peak_kind": peak_kind}
     roofline = roof(dom)
     phases = {p: {"ms_per_step": prof[p]["ms"] / nsteps,
                   "gbs": (prof[p]["bytes"] / (prof[p]["ms"] / 1e3) / 1e9) if prof[p]["ms"] else None}
@@ -286,12 +326,8 @@ def main():
         cp.cpma_insert_batch(ref.handle, dbuf, False, added_d)
         added_h.copy_(added_d, non_blocking=True)
         torch.cuda.current_stream().synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * nsteps * k / e2e_s, "unit": "keys/s",
+    e2e_ms, e2e_v = aggregate(1e3 * (time.perf_counter() - t0), nsteps * k, dist)
+    e2e = {"value": e2e_v, "unit": "keys/s", "ms_per_step": e2e_ms / nsteps,
            "h2d_bytes_per_step": 8 * k, "d2h_bytes_per_step": 8}
     del ref
 
@@ -300,7 +336,7 @@ def main():
         extra = measure_extra(a, g, batches[nwarm:], dev, st, hbm_peak, peak_kind, T)
 
     cpu_base = None
-    if not a.no_cpu_baseline and rank == 0:
+    if not a.no_cpu_baseline and rank == 0 and world == 1:
         try:
             cpu_base = oracle_insert_sample()
         except Exception as ex:  # the oracle is optional for the GPU number
@@ -344,12 +380,16 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps, r
 
+    kname = {"range": "k_range", "sum": "k_sum", "has": "k_has", "merge": "k_insert_lane",
+             "merge_other": "k_merge_small+k_merge"}
     def roof(prof, p):
         msp, by, calls = prof[p]["ms"], prof[p]["bytes"], max(1, prof[p]["calls"])
         ach = by / (msp / 1e3) / 1e9 if msp > 0 else 0.0
+        kn = kname.get(p, p)
         return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "kernel": p, "ms_per_launch": msp / calls,
-                "bytes_per_launch": by / calls, "peak_kind": peak_kind}
+                "frac": ach / hbm_peak, "kernel": kn, "ms_per_launch": msp / calls,
+                "bytes_per_launch": by / calls, "peak_kind": peak_kind,
+                "traffic": measured_traffic(kn, by / calls)}
 
     # range_map: 1e5 queries by rank, widths log-uniform 10..1e6 elements
     q = int(a.queries)
@@ -405,7 +445,7 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
         removed += int(rm.item())
     prof = g.profile_read()
     g.profile(False)
-    upd = ["sort", "route", "merge", "count", "redistribute", "finish"]
+    upd = ["sort", "route", "merge", "merge_other", "count", "redistribute", "finish"]
     dom = max(upd, key=lambda p: prof[p]["ms"])
     out["delete"] = {"value": removed / (tot / 1e3), "unit": "keys/s",
                      "batches": min(5, len(ins_batches)), "batch": int(a.batch),
@@ -413,7 +453,43 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
                      "phases_ms": {p: prof[p]["ms"] for p in upd}}
     if a.sweep:
         out["sweep"] = sweep(a, g, dev, T, timed)
+    if not a.no_skew:
+        out["skew"] = skew(a, dev, T, timed)
     return out
+
+
+def skew(a, dev, T, timed):
+    """Skewed updates: 5e7 keys uniform in [0, 2^34), then 100 rounds of 1e5
+    zipfian (0.99, 2^34 universe, scattered ranks) inserts + 5e4 deletes of
+    present keys; device time per round and final bytes/key."""
+    import torch
+    from paper_2305_05055_gb300 import cpma as cp
+    from paper_2305_05055_gb300 import workloads as W
+    n0, rounds, ki, kd = int(5e7), int(a.skew_rounds), 10 ** 5, 5 * 10 ** 4
+    base = W.uniform_keys(4, n0, bits=34)
+    S = np.unique(base)
+    g = cp.CPMA(T(base), leaf_bytes=a.leaf_bytes)
+    del base
+    L0, b0 = g.leaves(), g.bytes()
+    ins = T(W.zipf_keys(44, rounds * ki, bits=34))
+    dels = T(S[W.permuted_indices(S.size, rounds * kd, 45)])
+    del S
+    per = []
+    g.profile(True)
+    for r in range(rounds):
+        ms, _ = timed(lambda: (g.insert_batch(ins[r * ki:(r + 1) * ki]),
+                               g.delete_batch(dels[r * kd:(r + 1) * kd])))
+        per.append(ms)
+    prof = g.profile_read()
+    g.profile(False)
+    per_s = sorted(per)
+    return {"rounds": rounds, "insert_per_round": ki, "delete_per_round": kd,
+            "round_ms_median": statistics.median(per), "round_ms_p99": per_s[int(0.99 * (len(per) - 1))],
+            "round_ms_max": per_s[-1], "total_ms": sum(per),
+            "keys_per_s": rounds * (ki + kd) / (sum(per) / 1e3),
+            "leaves_start": L0, "leaves_end": g.leaves(), "size_end": g.size(),
+            "bytes_per_key_start": b0 / n0, "bytes_per_key_end": g.bytes() / max(1, g.size()),
+            "phases_ms": {p: prof[p]["ms"] for p in prof if prof[p]["ms"] > 0}}
 
 
 def sweep(a, g, dev, T, timed):

@@ -225,7 +225,7 @@ def cpma_reset_stats(h):
 
 
 PHASES = ("sort", "route", "merge", "count", "redistribute", "finish", "has",
-          "range_prep", "range", "sum")
+          "range_prep", "range", "sum", "merge_other")
 
 
 def cpma_profile(h, enable: bool = True):

@@ -75,7 +75,7 @@ struct Scratch {
 // Profiling phases (cpma_profile_read order).
 enum Phase {
   PH_SORT = 0, PH_ROUTE, PH_MERGE, PH_COUNT, PH_REDIST, PH_FINISH,
-  PH_HAS, PH_RANGE_PREP, PH_RANGE, PH_SUM, PH_N
+  PH_HAS, PH_RANGE_PREP, PH_RANGE, PH_SUM, PH_MERGE2, PH_N
 };
 
 // Optional per-phase device timing: event pairs recorded around each phase

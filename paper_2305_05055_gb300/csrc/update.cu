@@ -146,6 +146,7 @@ struct MergeArgs {
   uint64_t* ovf;
   int is_delete;
   Status* st;
+  ull* prof;  // profiling: algorithmic bytes of this kernel (nullable)
 };
 
 // Slices of at most kSmall keys into a non-empty leaf take the splice path.
@@ -298,6 +299,7 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
   uint32_t* en = ee + kSmall;
   int32_t* shc = reinterpret_cast<int32_t*>(en + kSmall);
   const uint64_t nT = a.st->nT;
+  ull nbytes = 0;  // algorithmic bytes (lane 0's count)
   for (uint64_t tbase = ((uint64_t)blockIdx.x * wpb + warp) * 32; tbase < nT;
        tbase += (uint64_t)gridDim.x * wpb * 32) {
     // metadata of 32 touched leaves, one per lane
@@ -319,6 +321,8 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
     const uint32_t fc0 = __shfl_sync(FULL, i_fc0, src), fc1 = __shfl_sync(FULL, i_fc1, src);
     const uint32_t s = te - tb;
     uint8_t* leafp = a.data + (size_t)j * a.LB;
+    // the old leaf, the slice and ~28 bytes of per-leaf metadata
+    nbytes += uold + 8u * s + 28u;
     // ---- bit-parallel summary of each lane's 16 bytes ----
     const uint32_t p0 = lane * 16u;
     uint4 v = make_uint4(0u, 0u, 0u, 0u);
@@ -511,6 +515,7 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
     __syncwarp();
     if (lane * 16 < wend)
       *reinterpret_cast<uint4*>(leafp + lane * 16) = *reinterpret_cast<const uint4*>(out + lane * 16);
+    nbytes += wend;
     if (lane == 0) {
       a.used[j] = nb;
       a.cnt[j] = newc;
@@ -523,6 +528,7 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
     __syncwarp();
     }
   }
+  if (a.prof && lane == 0 && nbytes) atomicAdd(a.prof, nbytes);
 }
 
 // Splice merge of a small slice into one leaf (warp per touched leaf).  The
@@ -552,6 +558,7 @@ __global__ void __launch_bounds__(kT, 4) k_merge_small(MergeArgs a) {
   uint32_t* en = ee + kSmall;
   int32_t* shc = reinterpret_cast<int32_t*>(en + kSmall);
   const uint64_t nT = a.st->nT;
+  ull nbytes = 0;
   for (uint64_t t = (uint64_t)blockIdx.x * wpb + warp; t < nT; t += (uint64_t)gridDim.x * wpb) {
     const uint32_t tb = a.T_begin[t], te = a.T_begin[t + 1];
     const uint32_t uold = a.T_oldused[t];
@@ -562,6 +569,7 @@ __global__ void __launch_bounds__(kT, 4) k_merge_small(MergeArgs a) {
     const uint32_t m = a.T_oldcnt[t];
     const uint32_t fc0 = a.T_first_chunk[t], fc1 = a.T_first_chunk[t + 1];
     uint8_t* leafp = a.data + (size_t)j * LB;
+    nbytes += uold + 8u * s + 24u;
     warp_decode_pos(leafp, min(uold, LB), [&](uint32_t idx, uint64_t v, uint32_t p) {
       old[idx] = v;
       pos[idx] = (uint16_t)p;
@@ -691,6 +699,7 @@ __global__ void __launch_bounds__(kT, 4) k_merge_small(MergeArgs a) {
     __syncwarp();
     for (uint32_t p = lane * 16; p < wend; p += 512)
       *reinterpret_cast<uint4*>(leafp + p) = *reinterpret_cast<const uint4*>(out + p);
+    nbytes += wend;
     if (lane == 0) {
       a.used[j] = nb;
       a.cnt[j] = newc;
@@ -703,6 +712,7 @@ __global__ void __launch_bounds__(kT, 4) k_merge_small(MergeArgs a) {
     for (uint32_t c = fc0 + lane; c < fc1; c += 32) a.chunk_cnt[c] = 0;
     __syncwarp();
   }
+  if (a.prof && lane == 0 && nbytes) atomicAdd(a.prof, nbytes);
 }
 
 // WRITE == false: count every work item, rewrite single-item leaves in place
@@ -929,9 +939,9 @@ __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
     const uint32_t state = a.T_state[t];
     const uint32_t oldc = a.T_oldcnt[t], newc = a.T_newcnt[t];
     const uint32_t j = a.T_leaf[t];
-    if (a.merge_bytes) {
-      // the merge reads the old leaf, the batch slice and ~24 bytes of
-      // per-leaf metadata, and writes the leaf when it rewrites it in place
+    if (a.merge_bytes && state != kUnchanged && a.T_begin[t + 1] - a.T_begin[t] > kSmall) {
+      // leaves of the element-array / general merge: old leaf, slice,
+      // metadata, and the rewrite when in place
       mb += a.T_oldused[t] + 8ull * (a.T_begin[t + 1] - a.T_begin[t]) + 24;
       if (state == kInPlace) mb += (max(a.T_oldused[t], (uint32_t)a.T_newbytes[t]) + 15u) & ~15u;
     }
@@ -1532,6 +1542,7 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   ma.ovf = nullptr;
   ma.is_delete = is_delete;
   ma.st = ds;
+  ma.prof = nullptr;
   const size_t per = merge_warp_bytes(LB);
   const int mwarps = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));
   const size_t msmem = per * mwarps;
@@ -1559,11 +1570,17 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
     const int sgrid = (int)std::max<uint64_t>(
         1, std::min<uint64_t>((k + swarps - 1) / swarps, (uint64_t)h->num_sms * 8));
     if (!is_delete) {
+      ma.prof = prof_bytes(h, PH_MERGE);
       k_insert_lane<<<sgrid, 256, kLaneWarpBytes * 8, st>>>(ma);
       h->launches++;
+      ma.prof = nullptr;
     }
+    prof_end(h, st);
+    prof_begin(h, PH_MERGE2, st);
+    ma.prof = prof_bytes(h, PH_MERGE2);
     k_merge_small<<<sgrid, swarps * 32, sper * swarps, st>>>(ma);
     h->launches++;
+    ma.prof = nullptr;
   }
   k_merge<false><<<mgrid, mwarps * 32, msmem, st>>>(ma);
   h->launches++;
@@ -1580,7 +1597,7 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   fa.T_newcnt = ro.T_newcnt;
   fa.T_begin = ro.T_begin;
   fa.T_oldused = ro.T_oldused;
-  fa.merge_bytes = prof_bytes(h, PH_MERGE);
+  fa.merge_bytes = prof_bytes(h, PH_MERGE2);
   fa.T_state = ro.T_state;
   fa.T_newbytes = ro.T_newbytes;
   fa.chunk_cnt = ma.chunk_cnt;

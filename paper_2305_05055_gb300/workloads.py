@@ -132,6 +132,19 @@ def sample_present(sorted_keys: np.ndarray, seed: int, count: int) -> np.ndarray
     return sorted_keys[out].copy()
 
 
+def permuted_indices(n: int, count: int, seed: int, offset: int = 0) -> np.ndarray:
+    """Indices offset..offset+count-1 of a seeded permutation of [0, n):
+    i -> (a*i + b) mod n with a odd-ish and coprime to n (distinct indices)."""
+    a = int(splitmix64(seed, 1)[0] % np.uint64(max(n, 1))) | 1
+    while math.gcd(a, n) != 1:
+        a += 2
+    b = int(splitmix64(seed, 1, 1)[0] % np.uint64(max(n, 1)))
+    i = np.arange(offset, offset + count, dtype=object)
+    return np.array([(a * int(v) + b) % n for v in i], dtype=np.int64) if count < 4096 else \
+        ((np.arange(offset, offset + count, dtype=np.uint64) * np.uint64(a) % np.uint64(n)
+          + np.uint64(b)) % np.uint64(n)).astype(np.int64)
+
+
 def range_queries_fixed_width(seed: int, count: int, width: int, bits: int = 40):
     """[lo, lo + width) with lo uniform in [0, 2^bits)."""
     lo = uniform_keys(seed, count, bits)
