@@ -92,6 +92,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-skew", action="store_true", help="skip the skewed-update rounds")
     ap.add_argument("--skew-rounds", type=int, default=100)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop comparison")
+    ap.add_argument("--serve-requests", type=int, default=3000)
+    ap.add_argument("--serve-rate", type=float, default=5000.0, help="offered requests/s")
     return ap.parse_args()
 
 
@@ -434,6 +437,7 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
     g.profile(False)
     out["has"] = {"value": hq.numel() / (ms / 1e3), "unit": "keys/s", "ms_per_call": ms,
                   "found": int(found.sum().item()), "roofline": roof(prof, "has")}
+    S_host = None if a.no_serve else cp.to_u64(S)
     del S
     # delete of present keys (the batches inserted by the timed steps)
     g.profile(True)
@@ -455,7 +459,30 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
         out["sweep"] = sweep(a, g, dev, T, timed)
     if not a.no_skew:
         out["skew"] = skew(a, dev, T, timed)
+    if not a.no_serve:
+        out["serve"] = serving(a, g, S_host)
     return out
+
+
+def serving(a, g, S):
+    """Continuous batching vs one library call per request on the same seeded
+    trace: 64 clients with Poisson arrivals, 45% inserts of log-uniform
+    1..1e5 fresh keys, 10% deletes of log-uniform 1..1e4 present keys, 45%
+    range sums of log-uniform 10..1e6 elements, 16 GB device budget."""
+    import torch
+    from paper_2305_05055_gb300 import serve
+    mk = lambda: serve.make_trace(a.serve_requests, a.serve_rate, 95, S, S)
+    plain_g = g.clone()
+    torch.cuda.synchronize()
+    srv = serve.Server(g, mem_budget_bytes=16 << 30)
+    served = srv.run(mk())
+    plain = serve.run_one_at_a_time(plain_g, mk())
+    del plain_g
+    return {"offered_requests_per_s": a.serve_rate, "requests": a.serve_requests,
+            "served": served, "one_at_a_time": plain,
+            "p99_ms": served["p99_ms"], "p50_ms": served["p50_ms"],
+            "p99_speedup": plain["p99_ms"] / served["p99_ms"],
+            "throughput_ratio": served["requests_per_s"] / plain["requests_per_s"]}
 
 
 def skew(a, dev, T, timed):

@@ -107,6 +107,35 @@ int cpma_insert_batch(cpma_t* h, const uint64_t* d_keys, uint64_t k,
 int cpma_delete_batch(cpma_t* h, const uint64_t* d_keys, uint64_t k,
                       int sorted, uint64_t* d_removed, cpma_stream_t stream);
 
+/* Tagged forms of the two updates, for callers that coalesce the batches of
+ * several requests into one (Sec. 4 batch updates): d_tags[i] < ntags names
+ * the request of d_keys[i].  The result is the set the untagged call gives;
+ * in addition d_counts[t] (ntags device uint64, zeroed by the call) receives
+ * how many keys request t added (insert) or removed (delete), every changed
+ * key being credited to the request of its first occurrence in the batch
+ * (the sort is stable, so with the keys laid out in request order the result
+ * equals applying the requests one after another in that order).  With
+ * sorted != 0 the keys must be non-decreasing and d_tags ordered with them.
+ * A tag >= ntags is rejected with CPMA_EINVAL and the set is unchanged. */
+int cpma_insert_batch_tagged(cpma_t* h, const uint64_t* d_keys,
+                             const uint32_t* d_tags, uint64_t k, int sorted,
+                             uint64_t ntags, uint64_t* d_counts,
+                             cpma_stream_t stream);
+int cpma_delete_batch_tagged(cpma_t* h, const uint64_t* d_keys,
+                             const uint32_t* d_tags, uint64_t k, int sorted,
+                             uint64_t ntags, uint64_t* d_counts,
+                             cpma_stream_t stream);
+
+/* The batch sort of the update path (Sec. 4: an unsorted batch is sorted
+ * first) on its own: d_keys[0..k) ascending into d_keys_out, stable, moving
+ * d_tags (nullable) along into d_tags_out.  Lets a caller sort the next batch
+ * while queries still run on another stream; pass the result to an update
+ * with sorted = 1.  Uses the handle's sort scratch: do not overlap it with an
+ * update on the same handle. */
+int cpma_sort_batch(cpma_t* h, const uint64_t* d_keys, const uint32_t* d_tags,
+                    uint64_t k, uint64_t* d_keys_out, uint32_t* d_tags_out,
+                    cpma_stream_t stream);
+
 /* App. A has, batched: d_out[i] = 1 if d_keys[i] is in the set, else 0
  * (Sec. 5 "Point queries": binary search on the heads, then one pass over
  * the leaf).  d_keys: q device uint64 in any order; d_out: q device bytes. */

@@ -70,6 +70,9 @@ def lib():
                 "cpma_reset_stats": (I, [V]),
                 "cpma_strerror": (C.c_char_p, [I]),
                 "cpma_range_map_noalloc": (I, [V, V, V, U64, V, V, V]),
+                "cpma_insert_batch_tagged": (I, [V, V, V, U64, I, U64, V, V]),
+                "cpma_delete_batch_tagged": (I, [V, V, V, U64, I, U64, V, V]),
+                "cpma_sort_batch": (I, [V, V, V, U64, V, V, V]),
                 "cpma_profile": (I, [V, I]),
                 "cpma_profile_read": (I, [V, C.POINTER(C.c_double), P64, P64, I]),
             }
@@ -151,6 +154,47 @@ def cpma_delete_batch(h, keys, sorted=False, out=None, stream=None):
     _check(lib().cpma_delete_batch(h, _ptr(k), k.numel(), int(bool(sorted)), _ptr(out),
                                    C.c_void_p(_stream(stream))), "cpma_delete_batch")
     return out
+
+
+def _tags(t):
+    if not (t.is_cuda and t.element_size() == 4):
+        raise TypeError("tags: expected a CUDA tensor of 32-bit integers")
+    return t.contiguous()
+
+
+def cpma_insert_batch_tagged(h, keys, tags, ntags, counts=None, sorted=False, stream=None):
+    """Insert with per-request attribution: counts[t] = keys request t added."""
+    k, tg = _keys(keys), _tags(tags)
+    if counts is None:
+        counts = torch.empty(ntags, dtype=torch.int64, device=k.device)
+    _check(lib().cpma_insert_batch_tagged(h, _ptr(k), _ptr(tg), k.numel(), int(bool(sorted)),
+                                          ntags, _ptr(counts), C.c_void_p(_stream(stream))),
+           "cpma_insert_batch_tagged")
+    return counts
+
+
+def cpma_delete_batch_tagged(h, keys, tags, ntags, counts=None, sorted=False, stream=None):
+    """Delete with per-request attribution: counts[t] = keys request t removed."""
+    k, tg = _keys(keys), _tags(tags)
+    if counts is None:
+        counts = torch.empty(ntags, dtype=torch.int64, device=k.device)
+    _check(lib().cpma_delete_batch_tagged(h, _ptr(k), _ptr(tg), k.numel(), int(bool(sorted)),
+                                          ntags, _ptr(counts), C.c_void_p(_stream(stream))),
+           "cpma_delete_batch_tagged")
+    return counts
+
+
+def cpma_sort_batch(h, keys, tags=None, keys_out=None, tags_out=None, stream=None):
+    k = _keys(keys)
+    if keys_out is None:
+        keys_out = torch.empty_like(k)
+    tg = _tags(tags) if tags is not None else None
+    if tg is not None and tags_out is None:
+        tags_out = torch.empty_like(tg)
+    _check(lib().cpma_sort_batch(h, _ptr(k), _ptr(tg), k.numel(), _ptr(keys_out),
+                                 _ptr(tags_out) if tg is not None else None,
+                                 C.c_void_p(_stream(stream))), "cpma_sort_batch")
+    return keys_out, tags_out
 
 
 def cpma_has_batch(h, keys, out=None, stream=None):

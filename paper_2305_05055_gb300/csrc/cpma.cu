@@ -135,12 +135,12 @@ int validate(const cpma_config& c) {
 
 void release_all(cpma* h) {
   Scratch& s = h->s;
-  for (Buf* b : {&s.keysA, &s.keysB, &s.hist, &s.hoff, &s.flags, &s.flags_scan, &s.leaf_of,
+  for (Buf* b : {&s.keysA, &s.keysB, &s.valsA, &s.valsB, &s.hist, &s.hoff, &s.flags, &s.flags_scan, &s.leaf_of,
                  &s.chunk_begin, &s.chunk_leaf, &s.chunk_tid, &s.chunk_cnt, &s.chunk_off,
                  &s.T_leaf, &s.T_begin, &s.T_first_chunk, &s.T_oldcnt, &s.T_oldused, &s.T_newcnt,
                  &s.T_newbytes, &s.T_state, &s.viol, &s.cand, &s.wins, &s.bits, &s.prefix, &s.ovf,
                  &s.E, &s.cost, &s.C, &s.srccnt, &s.srcoff, &s.dstart, &s.win_src, &s.win_dst,
-                 &s.win_leaf_off, &s.win_elem_off, &s.win_dst_off, &s.partials, &s.q_first,
+                 &s.win_leaf_off, &s.win_elem_off, &s.win_dst_off, &s.partials, &s.partials_q, &s.q_first,
                  &s.q_items, &s.q_off})
     release(*b);
   cudaFree(h->data);
@@ -298,6 +298,36 @@ int cpma_delete_batch(cpma_t* h, const uint64_t* d_keys, uint64_t k, int sorted,
                       uint64_t* d_removed, cpma_stream_t stream) {
   if (!h || (k && !d_keys)) return CPMA_EINVAL;
   return run_update(h, d_keys, k, sorted, 1, d_removed, (cudaStream_t)stream);
+}
+
+int cpma_insert_batch_tagged(cpma_t* h, const uint64_t* d_keys, const uint32_t* d_tags,
+                             uint64_t k, int sorted, uint64_t ntags, uint64_t* d_counts,
+                             cpma_stream_t stream) {
+  if (!h || (k && (!d_keys || !d_tags)) || !d_counts || ntags == 0) return CPMA_EINVAL;
+  return run_update(h, d_keys, k, sorted, 0, nullptr, (cudaStream_t)stream, d_tags, d_counts,
+                    ntags);
+}
+
+int cpma_delete_batch_tagged(cpma_t* h, const uint64_t* d_keys, const uint32_t* d_tags,
+                             uint64_t k, int sorted, uint64_t ntags, uint64_t* d_counts,
+                             cpma_stream_t stream) {
+  if (!h || (k && (!d_keys || !d_tags)) || !d_counts || ntags == 0) return CPMA_EINVAL;
+  return run_update(h, d_keys, k, sorted, 1, nullptr, (cudaStream_t)stream, d_tags, d_counts,
+                    ntags);
+}
+
+int cpma_sort_batch(cpma_t* h, const uint64_t* d_keys, const uint32_t* d_tags, uint64_t k,
+                    uint64_t* d_keys_out, uint32_t* d_tags_out, cpma_stream_t stream) {
+  if (!h || (k && (!d_keys || !d_keys_out)) || (d_tags && !d_tags_out)) return CPMA_EINVAL;
+  if (k == 0) return CPMA_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint64_t* u = nullptr;
+  const uint32_t* ut = nullptr;
+  if (d_tags) CPMA_TRY(sort_pairs(h, d_keys, d_tags, k, &u, &ut, st));
+  else CPMA_TRY(sort_keys(h, d_keys, k, &u, st));
+  CPMA_CUDA(cudaMemcpyAsync(d_keys_out, u, k * 8, cudaMemcpyDeviceToDevice, st));
+  if (d_tags) CPMA_CUDA(cudaMemcpyAsync(d_tags_out, ut, k * 4, cudaMemcpyDeviceToDevice, st));
+  return CPMA_OK;
 }
 
 int cpma_has_batch(const cpma_t* h, const uint64_t* d_keys, uint64_t q, uint8_t* d_out,

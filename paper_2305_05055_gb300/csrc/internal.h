@@ -54,6 +54,7 @@ struct Buf {
 
 struct Scratch {
   Buf keysA, keysB;       // sort ping-pong (u64)
+  Buf valsA, valsB;       // sort ping-pong of 32-bit tags
   Buf hist;               // radix histograms (u32)
   Buf hoff;               // scanned histograms (u64)
   Buf flags;              // route / unique flags (u64)
@@ -68,7 +69,9 @@ struct Scratch {
   Buf E, cost, C;         // redistribution: elements, costs, cost prefix
   Buf srccnt, srcoff, dstart;
   Buf win_src, win_dst, win_leaf_off, win_elem_off, win_dst_off;
-  Buf partials;           // scan partials
+  Buf partials;           // scan partials (update path)
+  Buf partials_q;         // scan partials of the query path, which may run
+                          // on another stream while an update sorts
   Buf q_first, q_items, q_off; // range queries
 };
 
@@ -130,6 +133,8 @@ int scan_u8_to_u64(cpma* h, const uint8_t* in, uint64_t* out, uint64_t n_host,
                    const ull* n_dev, cudaStream_t st);
 int scan_u64(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host, const ull* n_dev,
              cudaStream_t st);
+// scan_u64 with the query path's own partials buffer
+int scan_u64_query(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
 // Same as scan_u64 for a host-known count, with caller-provided partials
 // (partials_cap entries); it never allocates.
 int scan_u64_given_partials(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host,
@@ -138,12 +143,19 @@ int scan_u64_given_partials(cpma* h, const uint64_t* in, uint64_t* out, uint64_t
 // sort.cu: sort k keys ascending into *out (one of the scratch buffers).
 int sort_keys(cpma* h, const uint64_t* d_in, uint64_t k, const uint64_t** out,
               cudaStream_t st);
+// the same, moving a 32-bit payload with every key (stable)
+int sort_pairs(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k,
+               const uint64_t** out, const uint32_t** vout, cudaStream_t st);
 // sort.cu: drop adjacent repeats of sorted keys; result count into status->nunique.
 int unique_keys(cpma* h, const uint64_t* in, uint64_t k, uint64_t* out, cudaStream_t st);
 
 // update.cu
+// tags / tag_counts (nullable): per key a request tag; every key that the
+// batch adds (insert) or removes (delete) adds 1 to tag_counts[tag of its
+// first occurrence in the sorted batch]; tag_counts has ntags entries.
 int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_delete,
-               uint64_t* d_delta, cudaStream_t st);
+               uint64_t* d_delta, cudaStream_t st, const uint32_t* tags = nullptr,
+               uint64_t* tag_counts = nullptr, uint64_t ntags = 0);
 int build_from_sorted_unique(cpma* h, const uint64_t* E, uint64_t n, cudaStream_t st);
 
 // query.cu

@@ -227,7 +227,7 @@ int run_range(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q,
   prof_add_bytes(h, PH_RANGE_PREP, 72ull * q);  // lo, hi in; first, items, sums out; scan
   k_range_prep<<<g1, kT, 0, st>>>(lo, hi, q, h->heads, h->L, first, items, sum, count);
   CPMA_LAUNCHED(h);
-  CPMA_TRY(scan_u64(hm, items, off, q, nullptr, st));
+  CPMA_TRY(scan_u64_query(hm, items, off, q, st));
   prof_end(h, st);
   RangeArgs a;
   a.lo = lo;

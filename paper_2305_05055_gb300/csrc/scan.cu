@@ -117,11 +117,12 @@ __global__ void __launch_bounds__(kT) k_down(const Tin* __restrict__ in, uint64_
 
 template <typename Tin>
 int scan_impl(cpma* h, const Tin* in, uint64_t* out, uint64_t n_host, const ull* n_dev,
-              cudaStream_t st) {
+              cudaStream_t st, Buf* partials = nullptr) {
   uint64_t tiles = (n_host + kTile - 1) / kTile;
   int G = (int)std::min<uint64_t>((uint64_t)2 * h->num_sms, std::max<uint64_t>(tiles, 1));
-  CPMA_TRY(ensure(h->s.partials, (size_t)(G + 1) * 8));
-  uint64_t* part = (uint64_t*)h->s.partials.p;
+  Buf& pb = partials ? *partials : h->s.partials;
+  CPMA_TRY(ensure(pb, (size_t)(G + 1) * 8));
+  uint64_t* part = (uint64_t*)pb.p;
   k_reduce<Tin><<<G, kT, 0, st>>>(in, n_host, n_dev, part);
   k_partials<<<1, 1024, 0, st>>>(part, G);
   k_down<Tin><<<G, kT, 0, st>>>(in, out, n_host, n_dev, part);
@@ -142,6 +143,10 @@ int scan_u8_to_u64(cpma* h, const uint8_t* in, uint64_t* out, uint64_t n_host,
 int scan_u64(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host, const ull* n_dev,
              cudaStream_t st) {
   return scan_impl<uint64_t>(h, in, out, n_host, n_dev, st);
+}
+
+int scan_u64_query(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t st) {
+  return scan_impl<uint64_t>(h, in, out, n, nullptr, st, &h->s.partials_q);
 }
 
 int scan_u64_given_partials(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host,

@@ -25,8 +25,10 @@ constexpr int kWarps = kT / 32;
 constexpr int kItems = 16;
 constexpr int kTile = kT * kItems;  // 4096 keys
 
-struct TileSmem {
+template <bool VALS>
+struct TileSmemT {
   uint64_t keys[kTile];
+  uint32_t vals[VALS ? kTile : 1];  // optional 32-bit payload moved with the keys
   uint32_t wcnt[kWarps][256];
   uint32_t dstart[256];
   uint64_t goff[256];
@@ -37,8 +39,9 @@ struct TileSmem {
 // l in warp w is tile element w*32*kItems + j*32 + l; the first `nvalid`
 // elements are real.  On return sm.keys[0..nvalid) holds the tile sorted by
 // digit (stable) and sm.dstart[d] is where digit d starts.
-__device__ __forceinline__ void tile_rank(const uint64_t (&key)[kItems], uint32_t nvalid,
-                                          int shift, TileSmem& sm) {
+template <bool VALS>
+__device__ __forceinline__ void tile_rank(const uint64_t (&key)[kItems], const uint32_t (&val)[kItems],
+                                          uint32_t nvalid, int shift, TileSmemT<VALS>& sm) {
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kWarps * 256; i += kT) (&sm.wcnt[0][0])[i] = 0;
   __syncthreads();
@@ -87,7 +90,9 @@ __device__ __forceinline__ void tile_rank(const uint64_t (&key)[kItems], uint32_
     const uint32_t li = warp * 32 * kItems + j * 32 + lane;
     if (li < nvalid) {
       const uint32_t d = (uint32_t)(key[j] >> shift) & 255u;
-      sm.keys[sm.dstart[d] + sm.wcnt[warp][d] + rank[j]] = key[j];
+      const uint32_t pos = sm.dstart[d] + sm.wcnt[warp][d] + rank[j];
+      sm.keys[pos] = key[j];
+      if constexpr (VALS) sm.vals[pos] = val[j];
     }
   }
   __syncthreads();
@@ -132,45 +137,59 @@ __global__ void __launch_bounds__(kT) k_hist(const uint64_t* __restrict__ in, ui
   hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = hs[threadIdx.x];
 }
 
+template <bool VALS>
 __global__ void __launch_bounds__(kT) k_scatter(const uint64_t* __restrict__ in,
-                                                uint64_t* __restrict__ out, uint64_t k, int shift,
+                                                uint64_t* __restrict__ out,
+                                                const uint32_t* __restrict__ vin,
+                                                uint32_t* __restrict__ vout, uint64_t k, int shift,
                                                 const uint64_t* __restrict__ hoff,
                                                 uint32_t ntiles) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  TileSmem& sm = *reinterpret_cast<TileSmem*>(smem_raw);
+  TileSmemT<VALS>& sm = *reinterpret_cast<TileSmemT<VALS>*>(smem_raw);
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const uint64_t base = (uint64_t)blockIdx.x * kTile;
   const uint32_t nvalid = (uint32_t)min((uint64_t)kTile, k - base);
   sm.goff[threadIdx.x] = hoff[(uint64_t)threadIdx.x * ntiles + blockIdx.x];
   uint64_t key[kItems];
+  uint32_t val[kItems];
 #pragma unroll
   for (int j = 0; j < kItems; j++) {
     const uint32_t li = warp * 32 * kItems + j * 32 + lane;
     key[j] = li < nvalid ? in[base + li] : 0ull;
+    if constexpr (VALS) val[j] = li < nvalid ? vin[base + li] : 0u;
+    else val[j] = 0u;
   }
-  tile_rank(key, nvalid, shift, sm);
+  tile_rank<VALS>(key, val, nvalid, shift, sm);
   for (uint32_t i = threadIdx.x; i < nvalid; i += kT) {
     const uint64_t x = sm.keys[i];
     const uint32_t d = (uint32_t)(x >> shift) & 255u;
-    out[sm.goff[d] + i - sm.dstart[d]] = x;
+    const uint64_t o = sm.goff[d] + i - sm.dstart[d];
+    out[o] = x;
+    if constexpr (VALS) vout[o] = sm.vals[i];
   }
 }
 
 // Whole batch in one tile: all varying digits in one block.
+template <bool VALS>
 __global__ void __launch_bounds__(kT) k_sort_small(const uint64_t* __restrict__ in,
-                                                   uint64_t* __restrict__ out, uint32_t k) {
+                                                   uint64_t* __restrict__ out,
+                                                   const uint32_t* __restrict__ vin,
+                                                   uint32_t* __restrict__ vout, uint32_t k) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  TileSmem& sm = *reinterpret_cast<TileSmem*>(smem_raw);
+  TileSmemT<VALS>& sm = *reinterpret_cast<TileSmemT<VALS>*>(smem_raw);
   __shared__ ull s_or, s_and;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) { s_or = 0; s_and = ~0ull; }
   __syncthreads();
   uint64_t key[kItems];
+  uint32_t val[kItems];
   ull o = 0, a = ~0ull;
 #pragma unroll
   for (int j = 0; j < kItems; j++) {
     const uint32_t li = warp * 32 * kItems + j * 32 + lane;
     key[j] = li < k ? in[li] : 0ull;
+    if constexpr (VALS) val[j] = li < k ? vin[li] : 0u;
+    else val[j] = 0u;
     if (li < k) { o |= key[j]; a &= key[j]; }
   }
   atomicOr(&s_or, o);
@@ -179,18 +198,24 @@ __global__ void __launch_bounds__(kT) k_sort_small(const uint64_t* __restrict__ 
   const ull vary = s_or ^ s_and;
   for (int p = 0; p < 8; p++) {
     if (((vary >> (8 * p)) & 255u) == 0) continue;
-    tile_rank(key, k, 8 * p, sm);
+    tile_rank<VALS>(key, val, k, 8 * p, sm);
 #pragma unroll
     for (int j = 0; j < kItems; j++) {
       const uint32_t li = warp * 32 * kItems + j * 32 + lane;
-      if (li < k) key[j] = sm.keys[li];
+      if (li < k) {
+        key[j] = sm.keys[li];
+        if constexpr (VALS) val[j] = sm.vals[li];
+      }
     }
     __syncthreads();
   }
 #pragma unroll
   for (int j = 0; j < kItems; j++) {
     const uint32_t li = warp * 32 * kItems + j * 32 + lane;
-    if (li < k) out[li] = key[j];
+    if (li < k) {
+      out[li] = key[j];
+      if constexpr (VALS) vout[li] = val[j];
+    }
   }
 }
 
@@ -214,28 +239,41 @@ __global__ void k_unique_scatter(const uint64_t* __restrict__ in, uint64_t k,
 
 }  // namespace
 
-int sort_keys(cpma* h, const uint64_t* d_in, uint64_t k, const uint64_t** out,
-              cudaStream_t st) {
+template <bool VALS>
+int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, const uint64_t** out,
+              const uint32_t** vout, cudaStream_t st) {
   *out = d_in;
+  if (vout) *vout = v_in;
   if (k <= 1) return CPMA_OK;
   CPMA_TRY(ensure(h->s.keysA, k * 8));
   uint64_t* A = (uint64_t*)h->s.keysA.p;
-  const size_t smem = sizeof(TileSmem);
-  static bool attr_done = false;
+  uint32_t* VA = nullptr;
+  if (VALS) {
+    CPMA_TRY(ensure(h->s.valsA, k * 4));
+    VA = (uint32_t*)h->s.valsA.p;
+  }
+  const size_t smem = sizeof(TileSmemT<VALS>);
+  static bool attr_done = false;  // one per instantiation
   if (!attr_done) {
-    CPMA_CUDA(cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    CPMA_CUDA(cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CPMA_CUDA(cudaFuncSetAttribute(k_scatter<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CPMA_CUDA(cudaFuncSetAttribute(k_sort_small<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr_done = true;
   }
   if (k <= (uint64_t)kTile) {
-    prof_add_bytes(h, PH_SORT, 16ull * k);
-    k_sort_small<<<1, kT, smem, st>>>(d_in, A, (uint32_t)k);
+    prof_add_bytes(h, PH_SORT, (VALS ? 24ull : 16ull) * k);
+    k_sort_small<VALS><<<1, kT, smem, st>>>(d_in, A, v_in, VA, (uint32_t)k);
     h->launches++;
     *out = A;
+    if (vout) *vout = VA;
     return check_cuda(cudaGetLastError());
   }
   CPMA_TRY(ensure(h->s.keysB, k * 8));
   uint64_t* B = (uint64_t*)h->s.keysB.p;
+  uint32_t* VB = nullptr;
+  if (VALS) {
+    CPMA_TRY(ensure(h->s.valsB, k * 4));
+    VB = (uint32_t*)h->s.valsB.p;
+  }
   k_mask_init<<<1, 1, 0, st>>>(h->d_status);
   const int grid = (int)std::min<uint64_t>((uint64_t)h->num_sms * 4, (k + kT - 1) / kT);
   k_mask<<<grid, kT, 0, st>>>(d_in, k, h->d_status);
@@ -249,27 +287,44 @@ int sort_keys(cpma* h, const uint64_t* d_in, uint64_t k, const uint64_t** out,
   uint32_t* hist = (uint32_t*)h->s.hist.p;
   uint64_t* hoff = (uint64_t*)h->s.hoff.p;
   const uint64_t* src = d_in;
+  const uint32_t* vsrc = v_in;
   uint64_t* dst = A;
+  uint32_t* vdst = VA;
   prof_add_bytes(h, PH_SORT, 8ull * k);  // the OR/AND pass
   for (int p = 0; p < 8; p++) {
     if (((vary >> (8 * p)) & 255u) == 0) continue;
-    // histogram reads the keys; the scatter reads and writes them
-    prof_add_bytes(h, PH_SORT, 24ull * k);
+    // histogram reads the keys; the scatter reads and writes keys (and tags)
+    prof_add_bytes(h, PH_SORT, (VALS ? 32ull : 24ull) * k);
     k_hist<<<ntiles, kT, 0, st>>>(src, k, 8 * p, hist, ntiles);
     h->launches++;
     CPMA_TRY(scan_u32_to_u64(h, hist, hoff, (uint64_t)256 * ntiles, nullptr, st));
-    k_scatter<<<ntiles, kT, smem, st>>>(src, dst, k, 8 * p, hoff, ntiles);
+    k_scatter<VALS><<<ntiles, kT, smem, st>>>(src, dst, vsrc, vdst, k, 8 * p, hoff, ntiles);
     h->launches++;
     CPMA_CUDA(cudaGetLastError());
     src = dst;
+    vsrc = vdst;
     dst = (dst == A) ? B : A;
+    vdst = (vdst == VA) ? VB : VA;
   }
   if (src == d_in) {  // every key equal
     CPMA_CUDA(cudaMemcpyAsync(A, d_in, k * 8, cudaMemcpyDeviceToDevice, st));
+    if (VALS) CPMA_CUDA(cudaMemcpyAsync(VA, v_in, k * 4, cudaMemcpyDeviceToDevice, st));
     src = A;
+    vsrc = VA;
   }
   *out = src;
+  if (vout) *vout = vsrc;
   return CPMA_OK;
+}
+
+int sort_keys(cpma* h, const uint64_t* d_in, uint64_t k, const uint64_t** out,
+              cudaStream_t st) {
+  return sort_impl<false>(h, d_in, nullptr, k, out, nullptr, st);
+}
+
+int sort_pairs(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k,
+               const uint64_t** out, const uint32_t** vout, cudaStream_t st) {
+  return sort_impl<true>(h, d_in, v_in, k, out, vout, st);
 }
 
 int unique_keys(cpma* h, const uint64_t* in, uint64_t k, uint64_t* out, cudaStream_t st) {

@@ -147,7 +147,15 @@ struct MergeArgs {
   int is_delete;
   Status* st;
   ull* prof;  // profiling: algorithmic bytes of this kernel (nullable)
+  const uint32_t* tags;  // per sorted key: request tag (nullable)
+  ull* tag_counts;       // per tag: keys added / removed (nullable)
 };
+
+// Credit one added / removed key to the request that owns its first
+// occurrence in the sorted batch.
+__device__ __forceinline__ void credit(const MergeArgs& a, uint64_t key_index) {
+  if (a.tag_counts) atomicAdd(a.tag_counts + a.tags[key_index], 1ull);
+}
 
 // Slices of at most kSmall keys into a non-empty leaf take the splice path.
 constexpr uint32_t kSmall = 32;
@@ -486,6 +494,7 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
         a.T_newbytes[t] = nb;
       }
       for (uint32_t cq = fc0 + lane; cq < fc1; cq += 32) a.chunk_cnt[cq] = (cq == fc0) ? newc : 0u;
+      if (keep) credit(a, tb + lane);
       __syncwarp();
       continue;
     }
@@ -516,6 +525,7 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
     if (lane * 16 < wend)
       *reinterpret_cast<uint4*>(leafp + lane * 16) = *reinterpret_cast<const uint4*>(out + lane * 16);
     nbytes += wend;
+    if (keep) credit(a, tb + lane);
     if (lane == 0) {
       a.used[j] = nb;
       a.cnt[j] = newc;
@@ -660,6 +670,7 @@ __global__ void __launch_bounds__(kT, 4) k_merge_small(MergeArgs a) {
         a.T_newbytes[t] = nb;
       }
       for (uint32_t c = fc0 + lane; c < fc1; c += 32) a.chunk_cnt[c] = (c == fc0) ? newc : 0u;
+      if (keep) credit(a, tb + lane);
       __syncwarp();
       continue;
     }
@@ -700,6 +711,7 @@ __global__ void __launch_bounds__(kT, 4) k_merge_small(MergeArgs a) {
     for (uint32_t p = lane * 16; p < wend; p += 512)
       *reinterpret_cast<uint4*>(leafp + p) = *reinterpret_cast<const uint4*>(out + p);
     nbytes += wend;
+    if (keep) credit(a, tb + lane);
     if (lane == 0) {
       a.used[j] = nb;
       a.cnt[j] = newc;
@@ -786,6 +798,7 @@ __global__ void __launch_bounds__(kT) k_merge(MergeArgs a) {
         }
         const unsigned bal = __ballot_sync(FULL, keep);
         if (keep) nk[nn + __popc(bal & lanemask_lt())] = x;
+        if (!WRITE && keep) credit(a, b + i);
         nn += __popc(bal);
       }
       __syncwarp();
@@ -805,7 +818,9 @@ __global__ void __launch_bounds__(kT) k_merge(MergeArgs a) {
         uint64_t x = 0;
         if (q < ob) {
           x = old[q];
-          keep = !bsearch_sm(sl, s, x);
+          const uint32_t p = (uint32_t)lower_bound(sl, s, x);
+          keep = !(p < s && sl[p] == x);
+          if (!WRITE && !keep) credit(a, b + p);
         }
         const unsigned bal = __ballot_sync(FULL, keep);
         if (keep) z[r + __popc(bal & lanemask_lt())] = x;
@@ -980,6 +995,13 @@ __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
 }
 
 __global__ void k_copy_total(const uint64_t* arr, const ull* n, ull* dst) { *dst = arr[*n]; }
+
+__global__ void __launch_bounds__(kT) k_check_tags(const uint32_t* __restrict__ tags, uint64_t k,
+                                                   uint64_t ntags, Status* st) {
+  bool bad = false;
+  for (uint64_t i = gtid(); i < k; i += gstride()) bad |= tags[i] >= ntags;
+  if (__any_sync(FULL, bad) && lane_id() == 0) atomicOr(&st->err, kErrUnsorted);
+}
 
 struct WalkArgs {
   const uint32_t* viol;
@@ -1459,8 +1481,10 @@ int do_resize(cpma* h, cudaStream_t st, uint64_t T, uint64_t n_after, uint64_t n
 }  // namespace
 
 int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_delete,
-               uint64_t* d_delta, cudaStream_t st) {
+               uint64_t* d_delta, cudaStream_t st, const uint32_t* tags, uint64_t* tag_counts,
+               uint64_t ntags) {
   Status* ds = h->d_status;
+  if (tag_counts && ntags) CPMA_CUDA(cudaMemsetAsync(tag_counts, 0, ntags * 8, st));
   if (k == 0) {
     if (d_delta) CPMA_CUDA(cudaMemsetAsync(d_delta, 0, 8, st));
     return CPMA_OK;
@@ -1468,9 +1492,15 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   if (k >= (1ull << 31)) return CPMA_EINVAL;
   CPMA_CUDA(cudaMemsetAsync(ds, 0, offsetof(Status, empties), st));
   const uint64_t* u = d_keys;
+  const uint32_t* ut = tags;
+  if (tags) {
+    k_check_tags<<<grid_for(h, k), kT, 0, st>>>(tags, k, ntags, ds);
+    h->launches++;
+  }
   if (!sorted) {
     prof_begin(h, PH_SORT, st);
-    CPMA_TRY(sort_keys(h, d_keys, k, &u, st));
+    if (tags) CPMA_TRY(sort_pairs(h, d_keys, tags, k, &u, &ut, st));
+    else CPMA_TRY(sort_keys(h, d_keys, k, &u, st));
     prof_end(h, st);
   }
   // ---- scratch (all before any change to the structure) ----
@@ -1543,6 +1573,8 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   ma.is_delete = is_delete;
   ma.st = ds;
   ma.prof = nullptr;
+  ma.tags = ut;
+  ma.tag_counts = tags ? reinterpret_cast<ull*>(tag_counts) : nullptr;
   const size_t per = merge_warp_bytes(LB);
   const int mwarps = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));
   const size_t msmem = per * mwarps;
@@ -1629,6 +1661,7 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   if (hs.npend) {
     CPMA_TRY(ensure(s.ovf, (hs.novf + 1) * 8));
     ma.ovf = P<uint64_t>(s.ovf);
+    ma.tag_counts = nullptr;
     k_merge<true><<<mgrid, mwarps * 32, msmem, st>>>(ma);
     h->launches++;
     CPMA_CUDA(cudaGetLastError());

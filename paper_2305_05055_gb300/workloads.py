@@ -139,10 +139,10 @@ def permuted_indices(n: int, count: int, seed: int, offset: int = 0) -> np.ndarr
     while math.gcd(a, n) != 1:
         a += 2
     b = int(splitmix64(seed, 1, 1)[0] % np.uint64(max(n, 1)))
-    i = np.arange(offset, offset + count, dtype=object)
-    return np.array([(a * int(v) + b) % n for v in i], dtype=np.int64) if count < 4096 else \
-        ((np.arange(offset, offset + count, dtype=np.uint64) * np.uint64(a) % np.uint64(n)
-          + np.uint64(b)) % np.uint64(n)).astype(np.int64)
+    if n >= (1 << 32) or offset + count >= (1 << 32):
+        return np.array([(a * v + b) % n for v in range(offset, offset + count)], dtype=np.int64)
+    i = np.arange(offset, offset + count, dtype=np.uint64)
+    return ((i * np.uint64(a) % np.uint64(n) + np.uint64(b)) % np.uint64(n)).astype(np.int64)
 
 
 def range_queries_fixed_width(seed: int, count: int, width: int, bits: int = 40):
