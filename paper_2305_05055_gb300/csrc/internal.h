@@ -31,7 +31,10 @@ struct Status {
   ull nelem;       // elements moved by the current redistribution
   ull nunique;     // distinct keys after sort+dedup (create)
   ull stream_bytes;// bytes of the build stream (create)
-  ull pad[13];
+  ull n_lane;      // touched leaves for the lane-granular insert
+  ull n_v1;        // touched leaves for the element-array splice
+  ull n_gen;       // work items for the general merge
+  ull pad[10];
   ull empties;     // empty leaves in the structure (written by the head
                    // fix-up; not cleared at the start of a batch)
 };
@@ -63,6 +66,7 @@ struct Scratch {
   Buf chunk_begin, chunk_leaf, chunk_tid, chunk_cnt, chunk_off;
   Buf T_leaf, T_begin, T_first_chunk, T_oldcnt, T_oldused, T_newcnt, T_newbytes, T_state;
   Buf viol, cand, wins;   // violating leaves, window candidates, windows
+  Buf list_lane, list_v1, list_gen;  // merge work lists
   Buf bits;               // per-level window bitsets (u32 words)
   Buf prefix;             // prefix sums of used bytes (u64, L+1)
   Buf ovf;                // overflow elements (u64)

@@ -149,7 +149,21 @@ struct MergeArgs {
   ull* prof;  // profiling: algorithmic bytes of this kernel (nullable)
   const uint32_t* tags;  // per sorted key: request tag (nullable)
   ull* tag_counts;       // per tag: keys added / removed (nullable)
+  uint32_t* list_lane;   // touched leaves for k_insert_lane (count st->n_lane)
+  uint32_t* list_v1;     // touched leaves for k_merge_small (count st->n_v1)
+  uint32_t* list_gen;    // work items for k_merge in count mode (st->n_gen)
 };
+
+// Append to a work list, one atomic per warp (all lanes must call).
+__device__ __forceinline__ void warp_append(bool pred, uint32_t value, uint32_t* list, ull* ctr) {
+  const unsigned m = __ballot_sync(FULL, pred);
+  if (!m) return;
+  const unsigned leader = __ffs(m) - 1;
+  ull base = 0;
+  if (lane_id() == leader) base = atomicAdd(ctr, (ull)__popc(m));
+  base = __shfl_sync(FULL, base, leader);
+  if (pred) list[base + __popc(m & lanemask_lt())] = value;
+}
 
 // Credit one added / removed key to the request that owns its first
 // occurrence in the sorted batch.
@@ -306,23 +320,24 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
   uint32_t* ee = es + kSmall;
   uint32_t* en = ee + kSmall;
   int32_t* shc = reinterpret_cast<int32_t*>(en + kSmall);
-  const uint64_t nT = a.st->nT;
+  const uint64_t nL = a.st->n_lane;
   ull nbytes = 0;  // algorithmic bytes (lane 0's count)
-  for (uint64_t tbase = ((uint64_t)blockIdx.x * wpb + warp) * 32; tbase < nT;
+  for (uint64_t tbase = ((uint64_t)blockIdx.x * wpb + warp) * 32; tbase < nL;
        tbase += (uint64_t)gridDim.x * wpb * 32) {
-    // metadata of 32 touched leaves, one per lane
-    const uint64_t ti = tbase + lane;
+    // metadata of 32 touched leaves of the work list, one per lane
+    const bool have = tbase + lane < nL;
+    const uint32_t ti = have ? a.list_lane[tbase + lane] : 0u;
     uint32_t i_tb = 0, i_te = 0, i_uold = 0, i_j = 0, i_m = 0, i_fc0 = 0, i_fc1 = 0;
-    if (ti < nT) {
+    if (have) {
       i_tb = a.T_begin[ti]; i_te = a.T_begin[ti + 1]; i_uold = a.T_oldused[ti];
       i_j = a.T_leaf[ti]; i_m = a.T_oldcnt[ti];
       i_fc0 = a.T_first_chunk[ti]; i_fc1 = a.T_first_chunk[ti + 1];
     }
-    unsigned todo = __ballot_sync(FULL, ti < nT && small_slice(i_tb, i_te, i_uold) && i_uold <= 512);
+    unsigned todo = __ballot_sync(FULL, have);
     while (todo) {
     const unsigned src = __ffs(todo) - 1;
     todo &= todo - 1;
-    const uint64_t t = tbase + src;
+    const uint32_t t = __shfl_sync(FULL, ti, src);
     const uint32_t tb = __shfl_sync(FULL, i_tb, src), te = __shfl_sync(FULL, i_te, src);
     const uint32_t uold = __shfl_sync(FULL, i_uold, src), j = __shfl_sync(FULL, i_j, src);
     const uint32_t m = __shfl_sync(FULL, i_m, src);
@@ -350,7 +365,10 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
       D = lc.D - lc.first_own + pv + (lc.first_own << ps);
     }
     if (__any_sync(FULL, bad)) {
-      if (lane == 0) a.T_state[t] = kFallback;
+      if (lane == 0) {
+        a.T_state[t] = kFallback;
+        a.list_v1[atomicAdd(&a.st->n_v1, 1ull)] = t;
+      }
       continue;
     }
     const uint32_t c = __popc(lc.term);
@@ -499,7 +517,10 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
       continue;
     }
     if (nb > 512) {  // fits the leaf but not this kernel's 512-byte buffer
-      if (lane == 0) a.T_state[t] = kFallback;
+      if (lane == 0) {
+        a.T_state[t] = kFallback;
+        a.list_v1[atomicAdd(&a.st->n_v1, 1ull)] = t;
+      }
       __syncwarp();
       continue;
     }
@@ -541,6 +562,45 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
   if (a.prof && lane == 0 && nbytes) atomicAdd(a.prof, nbytes);
 }
 
+// Sort the touched leaves into the merge kernels' work lists: small inserts
+// into leaves of at most 512 used bytes -> k_insert_lane; other small slices
+// into non-empty leaves -> k_merge_small; the rest -> k_merge, one entry per
+// work item (a slice of at most kChunk keys is merged whole by its first item,
+// the others get a zero overflow count here).
+__global__ void __launch_bounds__(kT) k_classify(MergeArgs a) {
+  if (a.st->err) return;
+  const unsigned lane = lane_id();
+  const uint64_t nT = a.st->nT;
+  for (uint64_t base = gtid() - lane; base < nT; base += gstride()) {
+    const uint64_t t = base + lane;
+    uint32_t cls = 3;
+    uint32_t tb = 0, te = 0, fc0 = 0, fc1 = 0;
+    if (t < nT) {
+      tb = a.T_begin[t];
+      te = a.T_begin[t + 1];
+      const uint32_t uold = a.T_oldused[t];
+      if (small_slice(tb, te, uold)) cls = (!a.is_delete && uold <= 512) ? 0u : 1u;
+      else {
+        cls = 2;
+        fc0 = a.T_first_chunk[t];
+        fc1 = a.T_first_chunk[t + 1];
+      }
+    }
+    warp_append(cls == 0, (uint32_t)t, a.list_lane, &a.st->n_lane);
+    warp_append(cls == 1, (uint32_t)t, a.list_v1, &a.st->n_v1);
+    if (cls == 2) {
+      if (te - tb <= kChunk) {
+        const ull i = atomicAdd(&a.st->n_gen, 1ull);
+        a.list_gen[i] = fc0;
+        for (uint32_t c = fc0 + 1; c < fc1; c++) a.chunk_cnt[c] = 0;
+      } else {
+        const ull i = atomicAdd(&a.st->n_gen, (ull)(fc1 - fc0));
+        for (uint32_t c = fc0; c < fc1; c++) a.list_gen[i + (c - fc0)] = c;
+      }
+    }
+  }
+}
+
 // Splice merge of a small slice into one leaf (warp per touched leaf).  The
 // leaf is decoded once into shared memory (values and the byte position where
 // each code ends); every key finds its rank by binary search in its own lane.
@@ -567,13 +627,12 @@ __global__ void __launch_bounds__(kT, 4) k_merge_small(MergeArgs a) {
   uint32_t* ee = es + kSmall;
   uint32_t* en = ee + kSmall;
   int32_t* shc = reinterpret_cast<int32_t*>(en + kSmall);
-  const uint64_t nT = a.st->nT;
+  const uint64_t nV = a.st->n_v1;
   ull nbytes = 0;
-  for (uint64_t t = (uint64_t)blockIdx.x * wpb + warp; t < nT; t += (uint64_t)gridDim.x * wpb) {
+  for (uint64_t li = (uint64_t)blockIdx.x * wpb + warp; li < nV; li += (uint64_t)gridDim.x * wpb) {
+    const uint32_t t = a.list_v1[li];
     const uint32_t tb = a.T_begin[t], te = a.T_begin[t + 1];
     const uint32_t uold = a.T_oldused[t];
-    if (!small_slice(tb, te, uold)) continue;
-    if (!a.is_delete && uold <= 512 && a.T_state[t] != kFallback) continue;  // lane kernel
     const uint32_t s = te - tb;
     const uint32_t j = a.T_leaf[t];
     const uint32_t m = a.T_oldcnt[t];
@@ -742,23 +801,28 @@ __global__ void __launch_bounds__(kT) k_merge(MergeArgs a) {
   uint64_t* sl = z + LB + kChunk;
   uint64_t* nk = sl + kChunk;
   uint8_t* buf = reinterpret_cast<uint8_t*>(nk + kChunk);
-  const uint64_t nch = a.st->nchunks;
-  // 32 work items are screened per step (one per lane), then the warp takes
-  // the ones that need this kernel in turn
-  for (uint64_t base = ((uint64_t)blockIdx.x * wpb + warp) * 32; base < nch;
+  // count mode: the work items of the list; write mode: the items of pending
+  // leaves, 32 screened per step (one per lane)
+  const uint64_t nitems = WRITE ? a.st->nchunks : a.st->n_gen;
+  for (uint64_t base = ((uint64_t)blockIdx.x * wpb + warp) * 32; base < nitems;
        base += (uint64_t)gridDim.x * wpb * 32) {
    bool need = false;
+   uint64_t myc = 0;
    {
     const uint64_t cc = base + lane;
-    if (cc < nch) {
-      const uint32_t tt = a.chunk_tid[cc];
-      need = WRITE ? a.T_state[tt] == kPending
-                   : !small_slice(a.T_begin[tt], a.T_begin[tt + 1], a.T_oldused[tt]);
+    if (cc < nitems) {
+      if (WRITE) {
+        myc = cc;
+        need = a.T_state[a.chunk_tid[cc]] == kPending;
+      } else {
+        myc = a.list_gen[cc];
+        need = true;
+      }
     }
    }
    unsigned todo = __ballot_sync(FULL, need);
    while (todo) {
-    const uint64_t c = base + (__ffs(todo) - 1);
+    const uint64_t c = __shfl_sync(FULL, myc, __ffs(todo) - 1);
     todo &= todo - 1;
     const uint32_t t = a.chunk_tid[c];
     const uint32_t j = a.chunk_leaf[c];
@@ -1513,6 +1577,9 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
     CPMA_TRY(ensure(*b, (k + 2) * 4));
   CPMA_TRY(ensure(s.chunk_off, (k + 2) * 8));
   CPMA_TRY(ensure(s.T_newbytes, (k + 2) * 8));
+  CPMA_TRY(ensure(s.list_lane, (k + 2) * 4));
+  CPMA_TRY(ensure(s.list_v1, (k + 2) * 4));
+  CPMA_TRY(ensure(s.list_gen, (k + 2) * 4));
   CPMA_TRY(ensure(s.cand, (2 * k + 2) * 8));
   CPMA_TRY(ensure(s.wins, (2 * k + 2) * 16));
   CPMA_TRY(ensure(s.prefix, (h->L + 2) * 8));
@@ -1575,6 +1642,9 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   ma.prof = nullptr;
   ma.tags = ut;
   ma.tag_counts = tags ? reinterpret_cast<ull*>(tag_counts) : nullptr;
+  ma.list_lane = P<uint32_t>(s.list_lane);
+  ma.list_v1 = P<uint32_t>(s.list_v1);
+  ma.list_gen = P<uint32_t>(s.list_gen);
   const size_t per = merge_warp_bytes(LB);
   const int mwarps = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));
   const size_t msmem = per * mwarps;
@@ -1588,6 +1658,8 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   }
   const int mgrid = (int)std::max<uint64_t>(
       1, std::min<uint64_t>((k + kChunk + mwarps - 1) / mwarps, (uint64_t)h->num_sms * 4));
+  k_classify<<<grid_for(h, k), kT, 0, st>>>(ma);
+  h->launches++;
   prof_end(h, st);
   prof_begin(h, PH_MERGE, st);
   {
