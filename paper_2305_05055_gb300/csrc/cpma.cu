@@ -135,7 +135,7 @@ int validate(const cpma_config& c) {
 
 void release_all(cpma* h) {
   Scratch& s = h->s;
-  for (Buf* b : {&s.keysA, &s.keysB, &s.valsA, &s.valsB, &s.hist, &s.hoff, &s.flags, &s.flags_scan, &s.leaf_of,
+  for (Buf* b : {&s.keysA, &s.keysB, &s.valsA, &s.valsB, &s.hist, &s.flags, &s.flags_scan, &s.leaf_of,
                  &s.chunk_begin, &s.chunk_leaf, &s.chunk_tid, &s.chunk_cnt, &s.chunk_off,
                  &s.T_leaf, &s.T_begin, &s.T_first_chunk, &s.T_oldcnt, &s.T_oldused, &s.T_newcnt,
                  &s.T_newbytes, &s.T_state, &s.viol, &s.list_lane, &s.list_v1, &s.list_gen, &s.cand, &s.wins, &s.bits, &s.prefix, &s.ovf,

@@ -42,6 +42,7 @@ struct Status {
 constexpr ull kErrUnsorted = 1;   // a batch promised sorted was not
 constexpr ull kErrFit = 2;        // a redistributed leaf did not fit
 constexpr ull kErrState = 4;      // inconsistent leaf state
+constexpr ull kErrSort = 8;       // a sort tile waited too long for its predecessor
 
 constexpr uint32_t kChunk = 256;  // keys per merge work item
 constexpr int kMaxLevels = 48;
@@ -58,8 +59,7 @@ struct Buf {
 struct Scratch {
   Buf keysA, keysB;       // sort ping-pong (u64)
   Buf valsA, valsB;       // sort ping-pong of 32-bit tags
-  Buf hist;               // radix histograms (u32)
-  Buf hoff;               // scanned histograms (u64)
+  Buf hist;               // sort control block and look-back arrays
   Buf flags;              // route / unique flags (u64)
   Buf flags_scan;         // scanned flags (u64)
   Buf leaf_of;            // leaf per sorted key (u32)

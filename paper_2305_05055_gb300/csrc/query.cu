@@ -28,6 +28,11 @@ __device__ __forceinline__ uint64_t gtid() {
 }
 __device__ __forceinline__ uint64_t gstride() { return (uint64_t)gridDim.x * blockDim.x; }
 
+// Warp per query key, 32 keys routed per step.  A key equal to its leaf's
+// head, below it or above the leaf's last element needs no decode beyond the
+// lane summaries; otherwise only the lane whose value interval holds the key
+// is decoded (one byte position per lane).  Leaves with codes longer than 4
+// bytes or more than 512 used bytes go through the general decoder.
 __global__ void __launch_bounds__(kT) k_has(const uint64_t* __restrict__ keys, uint64_t q,
                                             const uint8_t* __restrict__ data,
                                             const uint32_t* __restrict__ used,
@@ -37,15 +42,79 @@ __global__ void __launch_bounds__(kT) k_has(const uint64_t* __restrict__ keys, u
   const unsigned lane = lane_id();
   const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
   ull nbytes = 0;
-  for (uint64_t i = gw; i < q; i += nw) {
-    const uint64_t x = keys[i];
-    const uint64_t j = route_leaf(heads, L, x);
-    bool found = false;
-    const uint32_t u = min(used[j], LB);
-    warp_decode(data + j * LB, u, [&](uint32_t, uint64_t v) { found |= (v == x); });
-    found = __any_sync(FULL, found);
-    if (lane == 0) out[i] = found ? 1 : 0;
-    nbytes += u + 9;  // leaf bytes, key in, answer out
+  for (uint64_t base = gw * 32; base < q; base += nw * 32) {
+    const uint64_t qi = base + lane;
+    uint64_t xi = 0, ji = 0;
+    uint32_t ui = 0;
+    if (qi < q) {
+      xi = keys[qi];
+      ji = route_leaf(heads, L, xi);
+      ui = min(used[ji], LB);
+    }
+    const uint32_t nk = (uint32_t)min((uint64_t)32, q - base);
+    uint32_t found_bits = 0;
+    for (uint32_t k = 0; k < nk; k++) {
+      const uint64_t x = __shfl_sync(FULL, xi, k);
+      const uint64_t j = __shfl_sync(FULL, ji, k);
+      const uint32_t u = __shfl_sync(FULL, ui, k);
+      const uint8_t* leaf = data + j * LB;
+      nbytes += u + 9;
+      bool found = false;
+      if (u > 0) {
+        const uint32_t p0 = lane * 16u;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (p0 < u) v = __ldg(reinterpret_cast<const uint4*>(leaf + p0));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        const int b_lo = lane == 0 ? 8 : 0;
+        const int b_hi = (u > p0) ? (int)min(16u, u - p0) : 0;
+        LaneCodes lc;
+        lane_codes<false>(w, b_lo, b_hi, lc);
+        bool bad = lc.bad || u > 512;  // one 16-byte chunk per lane covers 512 bytes
+        uint32_t pv = __shfl_up_sync(FULL, lc.tail, 1);
+        uint32_t ps = __shfl_up_sync(FULL, lc.tail_sh, 1);
+        if (lane == 0) { pv = 0; ps = 0; }
+        uint32_t D = 0;
+        if (lc.term) {
+          if (ps / 7u + lc.first_len > 4u) bad = true;
+          D = lc.D - lc.first_own + pv + (lc.first_own << ps);
+        }
+        if (__any_sync(FULL, bad)) {
+          bool f = false;
+          warp_decode(leaf, u, [&](uint32_t, uint64_t val) { f |= (val == x); });
+          found = __any_sync(FULL, f);
+        } else {
+          const uint64_t head = __shfl_sync(FULL, (uint64_t)w[0] | ((uint64_t)w[1] << 32), 0);
+          const uint64_t Dinc = warp_incl_scan((uint64_t)D);
+          const uint64_t V = head + (Dinc - D);
+          const uint64_t lastv = head + __shfl_sync(FULL, Dinc, 31);
+          if (x == head) {
+            found = true;
+          } else if (x > head && x <= lastv) {
+            const unsigned own = __ballot_sync(FULL, lc.term != 0 && V < x && x <= V + D);
+            const unsigned o = __ffs(own) - 1;
+            uint32_t xo[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) xo[t] = __shfl_sync(FULL, lc.x[t], o);
+            const uint32_t term_o = __shfl_sync(FULL, lc.term, o);
+            const uint32_t pv_o = __shfl_sync(FULL, pv, o), ps_o = __shfl_sync(FULL, ps, o);
+            const uint64_t V_o = __shfl_sync(FULL, V, o);
+            const bool is_t = lane < 16 && ((term_o >> lane) & 1u);
+            const uint32_t before = lane < 16 ? (term_o & ((1u << lane) - 1u)) : 0u;
+            const bool firstc = before == 0;
+            const uint32_t st0 = firstc ? (o == 0 ? 8u : 0u) : (32u - (uint32_t)__clz(before));
+            uint32_t code = 0;
+            if (is_t) {
+              const uint32_t own_bits = compact7(window32(xo, st0)) & mask7(lane + 1u - st0);
+              code = firstc ? pv_o + (own_bits << ps_o) : own_bits;
+            }
+            const uint64_t val = V_o + warp_incl_scan(code);
+            found = __any_sync(FULL, is_t && val == x);
+          }
+        }
+      }
+      if (found) found_bits |= 1u << k;
+    }
+    if (qi < q) out[qi] = (found_bits >> lane) & 1u;
   }
   if (prof && lane == 0 && nbytes) atomicAdd(prof, nbytes);
 }
@@ -202,7 +271,7 @@ int scratch_address(int dev, uint8_t** out) {
 int run_has(const cpma* h, const uint64_t* d_keys, uint64_t q, uint8_t* d_out, cudaStream_t st) {
   if (q == 0) return CPMA_OK;
   const int grid = (int)std::max<uint64_t>(
-      1, std::min<uint64_t>((q * 32 + kT - 1) / kT, (uint64_t)persistent_grid(h)));
+      1, std::min<uint64_t>((q + kT - 1) / kT, (uint64_t)persistent_grid(h)));
   prof_begin(h, PH_HAS, st);
   k_has<<<grid, kT, 0, st>>>(d_keys, q, h->data, h->used, h->heads, h->L, h->cfg.leaf_bytes,
                              d_out, prof_bytes(h, PH_HAS));

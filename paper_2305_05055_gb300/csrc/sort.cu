@@ -2,14 +2,17 @@
 // in O(k log k) work") as an LSD radix sort over 8-bit digits, plus the
 // adjacent-repeat compaction used by the constructor.
 //
-// Digit passes whose 8 bits are equal across the whole batch are skipped: an
-// OR/AND reduction of the keys gives the varying bits first (40-bit uniform
-// keys need 5 passes, not 8).  Each pass is histogram -> scan of the
-// digit-major histogram -> scatter.  The scatter ranks a 4096-key tile
-// stably in shared memory (warp match_any per digit, then per-warp prefixes)
-// and writes every digit's run of the tile contiguously, so global stores are
-// coalesced.  Batches of at most one tile are sorted by a single block with no
-// host round trip.
+// One sweep per digit: a first kernel builds the histograms of all eight
+// digits in one read of the batch; its last block scans them and marks the
+// digits that vary (40-bit uniform keys need 5 passes, not 8).  Each varying
+// digit is then one scatter launch: a tile of 4096 keys is ranked stably in
+// shared memory (warp match_any per digit, then per-warp prefixes), its
+// global offsets come from the tiles before it by decoupled look-back (each
+// tile publishes its per-digit count, then its inclusive prefix), and every
+// digit's run of the tile is written contiguously.  Digits that do not vary
+// return at once; the passes alternate buffers so that the last one lands in
+// the first scratch buffer.  No host round trip.  Batches of at most one tile
+// are sorted by a single block.
 #include <algorithm>
 
 #include "dev_common.cuh"
@@ -98,74 +101,152 @@ __device__ __forceinline__ void tile_rank(const uint64_t (&key)[kItems], const u
   __syncthreads();
 }
 
-__global__ void k_mask_init(Status* st) {
-  st->mask_or = 0;
-  st->mask_and = ~0ull;
-}
+constexpr uint32_t kFlagA = 1u << 30;  // tile count published
+constexpr uint32_t kFlagP = 2u << 30;  // inclusive prefix published
+constexpr uint32_t kCountMask = (1u << 30) - 1u;
+constexpr uint32_t kSpinLimit = 1u << 22;
 
-__global__ void __launch_bounds__(kT) k_mask(const uint64_t* __restrict__ in, uint64_t k,
-                                             Status* st) {
-  ull o = 0, a = ~0ull;
+// Control block of one sort, zeroed before the first kernel.
+struct SortCtl {
+  uint32_t hist[8][256];   // digit histograms
+  uint32_t off[8][256];    // exclusive digit offsets
+  uint32_t varying[8];     // digit p varies across the batch
+  uint32_t rank[8];        // position of digit p among the varying ones
+  uint32_t npass;          // number of varying digits
+  uint32_t done_blocks;    // histogram blocks finished
+  uint32_t tile_ctr[8];    // next tile id per pass
+};
+
+__global__ void __launch_bounds__(kT) k_hist_all(const uint64_t* __restrict__ in, uint64_t k,
+                                                 SortCtl* ctl) {
+  __shared__ uint32_t hs[8][256];
+  __shared__ bool last;
+  for (int i = threadIdx.x; i < 8 * 256; i += kT) (&hs[0][0])[i] = 0;
+  __syncthreads();
   for (uint64_t i = (uint64_t)blockIdx.x * kT + threadIdx.x; i < k; i += (uint64_t)gridDim.x * kT) {
     const uint64_t x = in[i];
-    o |= x;
-    a &= x;
-  }
 #pragma unroll
-  for (int s = 16; s; s >>= 1) {
-    o |= __shfl_xor_sync(FULL, o, s);
-    a &= __shfl_xor_sync(FULL, a, s);
+    for (int p = 0; p < 8; p++) atomicAdd(&hs[p][(uint32_t)(x >> (8 * p)) & 255u], 1u);
   }
-  if (lane_id() == 0) {
-    atomicOr(&st->mask_or, o);
-    atomicAnd(&st->mask_and, a);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 8 * 256; i += kT) {
+    const uint32_t v = (&hs[0][0])[i];
+    if (v) atomicAdd(&(&ctl->hist[0][0])[i], v);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&ctl->done_blocks, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // last block: exclusive scans, varying digits, pass ranks
+  const int d = threadIdx.x;  // kT == 256
+  __shared__ uint32_t wt[kWarps];
+  for (int p = 0; p < 8; p++) {
+    const uint32_t v = *((volatile uint32_t*)&ctl->hist[p][d]);
+    const uint32_t inc = warp_incl_scan(v);
+    if (lane_id() == 31) wt[threadIdx.x >> 5] = inc;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (unsigned q = 0; q < (threadIdx.x >> 5); q++) wbase += wt[q];
+    ctl->off[p][d] = wbase + inc - v;
+    const int full = __syncthreads_or(v == (uint32_t)k);
+    if (d == 0) ctl->varying[p] = full ? 0u : 1u;
+    __syncthreads();
+  }
+  if (d == 0) {
+    uint32_t r = 0;
+    for (int p = 0; p < 8; p++) {
+      ctl->rank[p] = r;
+      r += ctl->varying[p];
+    }
+    ctl->npass = r;
   }
 }
 
-__global__ void __launch_bounds__(kT) k_hist(const uint64_t* __restrict__ in, uint64_t k,
-                                             int shift, uint32_t* __restrict__ hist,
-                                             uint32_t ntiles) {
-  __shared__ uint32_t hs[256];
-  hs[threadIdx.x] = 0;
-  __syncthreads();
-  const uint64_t base = (uint64_t)blockIdx.x * kTile;
-  for (int i = threadIdx.x; i < kTile; i += kT) {
-    const uint64_t g = base + i;
-    if (g < k) atomicAdd(&hs[(uint32_t)(in[g] >> shift) & 255u], 1u);
+// Every key equal: no pass runs, the batch is copied to the result buffer.
+__global__ void k_copy_if_no_pass(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                  const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout,
+                                  uint64_t k, const SortCtl* ctl) {
+  if (ctl->npass != 0) return;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    out[i] = in[i];
+    if (vin) vout[i] = vin[i];
   }
-  __syncthreads();
-  hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = hs[threadIdx.x];
 }
 
+// One digit pass.  Buffers: the input, then A and B alternately, arranged so
+// that the last varying pass writes A.
 template <bool VALS>
-__global__ void __launch_bounds__(kT) k_scatter(const uint64_t* __restrict__ in,
-                                                uint64_t* __restrict__ out,
-                                                const uint32_t* __restrict__ vin,
-                                                uint32_t* __restrict__ vout, uint64_t k, int shift,
-                                                const uint64_t* __restrict__ hoff,
-                                                uint32_t ntiles) {
+__global__ void __launch_bounds__(kT) k_onesweep(const uint64_t* __restrict__ in,
+                                                 const uint32_t* __restrict__ vin,
+                                                 uint64_t* __restrict__ A, uint64_t* __restrict__ B,
+                                                 uint32_t* __restrict__ VA, uint32_t* __restrict__ VB,
+                                                 uint64_t k, int p, SortCtl* ctl,
+                                                 uint32_t* __restrict__ look, Status* st) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   TileSmemT<VALS>& sm = *reinterpret_cast<TileSmemT<VALS>*>(smem_raw);
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_excl[256];
+  if (!ctl->varying[p]) return;
+  const uint32_t r = ctl->rank[p], P = ctl->npass;
+  // pass r writes B when P-1-r is odd, else A (so pass P-1 writes A) and
+  // reads what pass r-1 wrote
+  const uint64_t* src = (r == 0) ? in : (((P - r) & 1u) ? B : A);
+  uint64_t* dst = ((P - 1u - r) & 1u) ? B : A;
+  const uint32_t* vsrc = (r == 0) ? vin : (((P - r) & 1u) ? VB : VA);
+  uint32_t* vdst = ((P - 1u - r) & 1u) ? VB : VA;
+  const int shift = 8 * p;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
-  const uint64_t base = (uint64_t)blockIdx.x * kTile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->tile_ctr[p], 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint64_t base = (uint64_t)tile * kTile;
   const uint32_t nvalid = (uint32_t)min((uint64_t)kTile, k - base);
-  sm.goff[threadIdx.x] = hoff[(uint64_t)threadIdx.x * ntiles + blockIdx.x];
   uint64_t key[kItems];
   uint32_t val[kItems];
 #pragma unroll
   for (int j = 0; j < kItems; j++) {
     const uint32_t li = warp * 32 * kItems + j * 32 + lane;
-    key[j] = li < nvalid ? in[base + li] : 0ull;
-    if constexpr (VALS) val[j] = li < nvalid ? vin[base + li] : 0u;
+    key[j] = li < nvalid ? src[base + li] : 0ull;
+    if constexpr (VALS) val[j] = li < nvalid ? vsrc[base + li] : 0u;
     else val[j] = 0u;
   }
   tile_rank<VALS>(key, val, nvalid, shift, sm);
+  // publish this tile's count per digit, then look back for the tiles before
+  const int d = threadIdx.x;
+  const uint32_t cnt = (d < 255 ? sm.dstart[d + 1] : nvalid) - sm.dstart[d];
+  volatile uint32_t* lk = look + (size_t)tile * 256;
+  if (tile == 0) {
+    lk[d] = kFlagP | cnt;
+    s_excl[d] = 0;
+  } else {
+    lk[d] = kFlagA | cnt;
+    uint32_t excl = 0;
+    for (int64_t tp = (int64_t)tile - 1; tp >= 0; tp--) {
+      volatile uint32_t* q = look + (size_t)tp * 256 + d;
+      uint32_t v = *q;
+      uint32_t spins = 0;
+      while (!(v & (kFlagA | kFlagP)) && spins < kSpinLimit) { v = *q; spins++; }
+      if (spins >= kSpinLimit) {  // a predecessor never published: give up
+        atomicOr(&st->err, kErrSort);
+        break;
+      }
+      excl += v & kCountMask;
+      if (v & kFlagP) break;
+    }
+    __threadfence();
+    lk[d] = kFlagP | (excl + cnt);
+    s_excl[d] = excl;
+  }
+  __syncthreads();
   for (uint32_t i = threadIdx.x; i < nvalid; i += kT) {
     const uint64_t x = sm.keys[i];
-    const uint32_t d = (uint32_t)(x >> shift) & 255u;
-    const uint64_t o = sm.goff[d] + i - sm.dstart[d];
-    out[o] = x;
-    if constexpr (VALS) vout[o] = sm.vals[i];
+    const uint32_t dd = (uint32_t)(x >> shift) & 255u;
+    const uint64_t o = (uint64_t)ctl->off[p][dd] + s_excl[dd] + (i - sm.dstart[dd]);
+    dst[o] = x;
+    if constexpr (VALS) vdst[o] = sm.vals[i];
   }
 }
 
@@ -255,7 +336,7 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
   const size_t smem = sizeof(TileSmemT<VALS>);
   static bool attr_done = false;  // one per instantiation
   if (!attr_done) {
-    CPMA_CUDA(cudaFuncSetAttribute(k_scatter<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CPMA_CUDA(cudaFuncSetAttribute(k_onesweep<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     CPMA_CUDA(cudaFuncSetAttribute(k_sort_small<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr_done = true;
   }
@@ -274,44 +355,31 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
     CPMA_TRY(ensure(h->s.valsB, k * 4));
     VB = (uint32_t*)h->s.valsB.p;
   }
-  k_mask_init<<<1, 1, 0, st>>>(h->d_status);
-  const int grid = (int)std::min<uint64_t>((uint64_t)h->num_sms * 4, (k + kT - 1) / kT);
-  k_mask<<<grid, kT, 0, st>>>(d_in, k, h->d_status);
-  h->launches += 2;
-  CPMA_CUDA(cudaGetLastError());
-  CPMA_TRY(sync_status(h, st));
-  const ull vary = h->h_status->mask_or ^ h->h_status->mask_and;
   const uint32_t ntiles = (uint32_t)((k + kTile - 1) / kTile);
-  CPMA_TRY(ensure(h->s.hist, (size_t)256 * ntiles * 4));
-  CPMA_TRY(ensure(h->s.hoff, ((size_t)256 * ntiles + 1) * 8));
-  uint32_t* hist = (uint32_t*)h->s.hist.p;
-  uint64_t* hoff = (uint64_t*)h->s.hoff.p;
-  const uint64_t* src = d_in;
-  const uint32_t* vsrc = v_in;
-  uint64_t* dst = A;
-  uint32_t* vdst = VA;
-  prof_add_bytes(h, PH_SORT, 8ull * k);  // the OR/AND pass
+  // control block + 8 look-back arrays, zeroed in one memset
+  const size_t ctl_bytes = (sizeof(SortCtl) + 255) & ~(size_t)255;
+  const size_t look_bytes = (size_t)8 * ntiles * 256 * 4;
+  CPMA_TRY(ensure(h->s.hist, ctl_bytes + look_bytes));
+  SortCtl* ctl = reinterpret_cast<SortCtl*>(h->s.hist.p);
+  uint32_t* look = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(h->s.hist.p) + ctl_bytes);
+  CPMA_CUDA(cudaMemsetAsync(h->s.hist.p, 0, ctl_bytes + look_bytes, st));
+  const int hgrid = (int)std::min<uint64_t>((uint64_t)h->num_sms * 2, (k + kT - 1) / kT);
+  k_hist_all<<<hgrid, kT, 0, st>>>(d_in, k, ctl);
+  h->launches++;
+  prof_add_bytes(h, PH_SORT, 8ull * k);  // the histogram read
   for (int p = 0; p < 8; p++) {
-    if (((vary >> (8 * p)) & 255u) == 0) continue;
-    // histogram reads the keys; the scatter reads and writes keys (and tags)
-    prof_add_bytes(h, PH_SORT, (VALS ? 32ull : 24ull) * k);
-    k_hist<<<ntiles, kT, 0, st>>>(src, k, 8 * p, hist, ntiles);
+    // digits that vary: the scatter reads and writes keys (and tags)
+    k_onesweep<VALS><<<ntiles, kT, smem, st>>>(d_in, v_in, A, B, VA, VB, k, p, ctl,
+                                                look + (size_t)p * ntiles * 256, h->d_status);
     h->launches++;
-    CPMA_TRY(scan_u32_to_u64(h, hist, hoff, (uint64_t)256 * ntiles, nullptr, st));
-    k_scatter<VALS><<<ntiles, kT, smem, st>>>(src, dst, vsrc, vdst, k, 8 * p, hoff, ntiles);
-    h->launches++;
-    CPMA_CUDA(cudaGetLastError());
-    src = dst;
-    vsrc = vdst;
-    dst = (dst == A) ? B : A;
-    vdst = (vdst == VA) ? VB : VA;
   }
-  if (src == d_in) {  // every key equal
-    CPMA_CUDA(cudaMemcpyAsync(A, d_in, k * 8, cudaMemcpyDeviceToDevice, st));
-    if (VALS) CPMA_CUDA(cudaMemcpyAsync(VA, v_in, k * 4, cudaMemcpyDeviceToDevice, st));
-    src = A;
-    vsrc = VA;
-  }
+  prof_add_bytes(h, PH_SORT, (VALS ? 24ull : 16ull) * k * 5);  // typical: 5 varying digits
+  k_copy_if_no_pass<<<std::min<uint64_t>((uint64_t)h->num_sms * 4, (k + kT - 1) / kT), kT, 0, st>>>(
+      d_in, A, v_in, VA, k, ctl);
+  h->launches++;
+  CPMA_CUDA(cudaGetLastError());
+  const uint64_t* src = A;
+  const uint32_t* vsrc = VA;
   *out = src;
   if (vout) *vout = vsrc;
   return CPMA_OK;
