@@ -93,6 +93,7 @@ def parse():
     ap.add_argument("--no-skew", action="store_true", help="skip the skewed-update rounds")
     ap.add_argument("--skew-rounds", type=int, default=100)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop comparison")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the leaf-size autotuning")
     ap.add_argument("--serve-requests", type=int, default=3000)
     ap.add_argument("--serve-rate", type=float, default=5000.0, help="offered requests/s")
     return ap.parse_args()
@@ -438,6 +439,14 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
     out["has"] = {"value": hq.numel() / (ms / 1e3), "unit": "keys/s", "ms_per_call": ms,
                   "found": int(found.sum().item()), "roofline": roof(prof, "has")}
     S_host = None if a.no_serve else cp.to_u64(S)
+    if not a.no_autotune:
+        from paper_2305_05055_gb300 import autotune
+        base = T(W.uniform_keys(2, int(a.n), bits=40))
+        at = autotune.tune(base, S, batch=int(a.batch), queries=q)
+        del base
+        out["autotune"] = {"best": at["best"], "best_by": at["best_by"],
+                           "candidates": [{k: (round(v, 4) if isinstance(v, float) else v)
+                                           for k, v in r.items()} for r in at["candidates"]]}
     del S
     # delete of present keys (the batches inserted by the timed steps)
     g.profile(True)

@@ -1,0 +1,108 @@
+"""Autotuner for the CPMA's tunables.
+
+Times the operations that matter for a workload -- batch insert, batch delete
+and range_map over rank-based ranges -- for every candidate configuration
+(leaf size and growing factor; the density bounds stay at their defaults) on
+one seeded sample of that workload, with CUDA events, and returns the
+configuration with the best weighted throughput.  Results are identical for
+every configuration (the configuration only changes the layout), so the
+choice is purely about speed.  The chosen configuration can be saved as JSON
+and passed to :class:`cpma.CPMA` as keyword arguments.
+"""
+from __future__ import annotations
+
+import json
+import statistics
+
+import numpy as np
+import torch
+
+from . import cpma as cp
+from . import workloads as W
+
+LEAF_BYTES = (256, 512, 1024, 2048)
+GROWTH = ((6, 5),)
+
+
+def _timed(fn, reps=3):
+    st = torch.cuda.current_stream()
+    out = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.median(out)
+
+
+def measure(base: torch.Tensor, sorted_keys: torch.Tensor, batch: int, queries: int,
+            leaf_bytes: int, grow=(6, 5), seed: int = 77, min_width: int = 10,
+            max_width: int = 10 ** 6) -> dict:
+    """One configuration on one workload sample (all device-resident)."""
+    dev = base.device
+    g = cp.CPMA(base, leaf_bytes=leaf_bytes, grow_num=grow[0], grow_den=grow[1])
+    n = sorted_keys.numel()
+    ins = torch.from_numpy(W.uniform_keys(seed, batch, bits=40).view(np.int64)).to(dev)
+    r = torch.from_numpy((W.splitmix64(seed + 1, queries) % np.uint64(n)).astype(np.int64)).to(dev)
+    u = W.uniform01(seed + 2, queries)
+    a, b = np.log10(min_width), np.log10(max_width)
+    c = torch.from_numpy(np.floor(10.0 ** (a + (b - a) * u)).astype(np.int64)).to(dev)
+    lo = sorted_keys[r]
+    j = r + c
+    hi = torch.where(j < n, sorted_keys[torch.clamp(j, max=n - 1)], torch.full_like(lo, -1))
+    res = {"leaf_bytes": leaf_bytes, "grow": list(grow), "bytes_per_key": g.bytes() / g.size()}
+    # insert and delete of the same fresh batch, on clones of one state
+    ms_ins, ms_del = [], []
+    for _ in range(3):
+        h = g.clone()
+        torch.cuda.synchronize()
+        ms_ins.append(_timed(lambda: h.insert_batch(ins), reps=1))
+        ms_del.append(_timed(lambda: h.delete_batch(ins), reps=1))
+        del h
+    res["insert_keys_per_s"] = batch / (statistics.median(ms_ins) / 1e3)
+    res["delete_keys_per_s"] = batch / (statistics.median(ms_del) / 1e3)
+    sums, cnts = g.range_map(lo, hi)
+    elems = int(cnts.sum().item())
+    ms = _timed(lambda: g.range_map(lo, hi))
+    res["range_elems_per_s"] = elems / (ms / 1e3)
+    res["range_ms"] = ms
+    ms = _timed(lambda: g.sum())
+    res["scan_elems_per_s"] = g.size() / (ms / 1e3)
+    del g
+    torch.cuda.synchronize()
+    return res
+
+
+def tune(base: torch.Tensor, sorted_keys: torch.Tensor, batch: int = 10 ** 6,
+         queries: int = 10 ** 5, weights=None, leaf_sizes=LEAF_BYTES, growth=GROWTH) -> dict:
+    """Measure every candidate and pick the best by the weighted geometric
+    mean of insert, delete and range throughput."""
+    weights = weights or {"insert_keys_per_s": 1.0, "delete_keys_per_s": 0.5,
+                          "range_elems_per_s": 1.0}
+    rows = [measure(base, sorted_keys, batch, queries, lb, gr)
+            for lb in leaf_sizes for gr in growth]
+    tot = sum(weights.values())
+
+    def score(r):
+        return float(np.exp(sum(w * np.log(r[k]) for k, w in weights.items()) / tot))
+
+    for r in rows:
+        r["score"] = score(r)
+    best = max(rows, key=lambda r: r["score"])
+    return {"best": {"leaf_bytes": best["leaf_bytes"], "grow_num": best["grow"][0],
+                     "grow_den": best["grow"][1]},
+            "best_by": {k: max(rows, key=lambda r: r[k])["leaf_bytes"] for k in weights},
+            "candidates": rows, "weights": weights}
+
+
+def save(result: dict, path: str):
+    with open(path, "w") as f:
+        json.dump(result["best"], f, indent=1)
+
+
+def load(path: str) -> dict:
+    with open(path) as f:
+        return json.load(f)
