@@ -88,7 +88,8 @@ def parse():
     ap.add_argument("--leaf-bytes", type=int, default=512)
     ap.add_argument("--queries", type=float, default=1e5)
     ap.add_argument("--no-extra", action="store_true", help="headline only")
-    ap.add_argument("--sweep", action="store_true", help="insert/delete sweep 1e3..1e7")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the insert/delete sweep 1e3..1e7")
+    ap.add_argument("--sweep-trials", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-skew", action="store_true", help="skip the skewed-update rounds")
     ap.add_argument("--skew-rounds", type=int, default=100)
@@ -464,7 +465,7 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
                      "batches": min(5, len(ins_batches)), "batch": int(a.batch),
                      "roofline": roof(prof, dom),
                      "phases_ms": {p: prof[p]["ms"] for p in upd}}
-    if a.sweep:
+    if not a.no_sweep:
         out["sweep"] = sweep(a, g, dev, T, timed)
     if not a.no_skew:
         out["skew"] = skew(a, dev, T, timed)
@@ -528,26 +529,60 @@ def skew(a, dev, T, timed):
             "phases_ms": {p: prof[p]["ms"] for p in prof if prof[p]["ms"] > 0}}
 
 
+def flush_l2(dev):
+    import torch
+    buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    buf.fill_(1)  # larger than the 129 MB L2
+    return buf
+
+
 def sweep(a, g, dev, T, timed):
+    """Batch-insert sweep at n = 1e8: for k = 1e3 .. 1e7 fresh uniform keys,
+    one untimed warm-up trial and `--sweep-trials` timed ones, each on a
+    device-to-device clone of the 1e8 state (clone not timed) whose scratch
+    is reserved for k and whose update graphs (graph mode) are warm: a warm-up
+    insert + delete of another batch of the same size first, which leaves the
+    same set.  Then the insert of the trial's batch and the delete of the
+    same keys, each timed alone after an L2 flush.  Reported: medians, launch
+    by launch and with the front segment as a CUDA graph."""
     import torch
     from paper_2305_05055_gb300 import workloads as W
     rows = []
     for kk in (10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7):
-        ins_ms, del_ms = [], []
-        for trial in range(3):
-            c = g.clone()
-            b = T(W.uniform_keys(3 * 10 ** 7 + 100 * trial + kk % 97, kk, bits=40))
-            c.insert_batch(b)  # warm
-            c2 = g.clone()
-            torch.cuda.synchronize()
-            ms, added = timed(lambda: c2.insert_batch(b))
-            ins_ms.append(ms)
-            ms, rm = timed(lambda: c2.delete_batch(b))
-            del_ms.append(ms)
-            del c, c2
-        rows.append({"batch": kk, "insert_keys_per_s": kk / (statistics.median(ins_ms) / 1e3),
-                     "delete_keys_per_s": kk / (statistics.median(del_ms) / 1e3),
-                     "insert_ms": statistics.median(ins_ms), "delete_ms": statistics.median(del_ms)})
+        res = {"batch": kk}
+        batches = [T(W.uniform_keys(3 * 10 ** 7 + 100 * t + kk % 97, kk, bits=40))
+                   for t in range(a.sweep_trials + 2)]
+        for mode in ("eager", "graph"):
+            ins_ms, del_ms, added = [], [], []
+            for t in range(a.sweep_trials + 1):
+                c = g.clone()
+                c.reserve(kk)
+                c.use_graphs((1 << 31) - 1 if mode == "graph" else 0)
+                w = batches[-1]
+                c.insert_batch(w)
+                c.delete_batch(w)
+                b = batches[t]
+                flush = flush_l2(dev)
+                ms_i, ad = timed(lambda: c.insert_batch(b))
+                flush = flush_l2(dev)
+                ms_d, rm = timed(lambda: c.delete_batch(b))
+                del flush
+                if t:
+                    ins_ms.append(ms_i)
+                    del_ms.append(ms_d)
+                    added.append(int(ad.item()))
+                del c
+            mi, md = statistics.median(ins_ms), statistics.median(del_ms)
+            res[mode] = {"insert_ms": mi, "delete_ms": md,
+                         "insert_keys_per_s": kk / (mi / 1e3),
+                         "delete_keys_per_s": kk / (md / 1e3),
+                         "insert_ms_min": min(ins_ms), "delete_ms_min": min(del_ms)}
+        res["insert_keys_per_s"] = max(res["eager"]["insert_keys_per_s"],
+                                       res["graph"]["insert_keys_per_s"])
+        res["delete_keys_per_s"] = max(res["eager"]["delete_keys_per_s"],
+                                       res["graph"]["delete_keys_per_s"])
+        rows.append(res)
+        del batches
     return rows
 
 

@@ -197,6 +197,38 @@ int cpma_leaves(const cpma_t* h, uint64_t* out);
 int cpma_export_layout(const cpma_t* h, uint8_t* d_data, uint32_t* d_used,
                        uint64_t* d_heads, cpma_stream_t stream);
 
+/* Pre-size the scratch that an update of up to max_batch keys (tagged != 0:
+ * with request tags) and a range_map of up to max_queries queries use, so
+ * that those calls do not allocate.  Buffers whose size depends on the data
+ * -- the overflow elements of leaves that outgrow leaf_bytes, the elements of
+ * redistributed windows, a resized array -- still grow on first use.  With
+ * graphs on (cpma_use_graphs) it also sizes the staging buffer of the padded
+ * batch.  Errors: CPMA_EINVAL (null handle, max_batch >= 2^31), CPMA_ENOMEM.
+ * Synchronises the device when an existing buffer has to grow. */
+int cpma_reserve(cpma_t* h, uint64_t max_batch, uint64_t max_queries, int tagged,
+                 cpma_stream_t stream);
+
+/* Run the front segment of untagged updates of at most max_batch keys --
+ * sort, route, the in-place merges and the finalize pass, everything before
+ * the update's first host read -- as a CUDA graph (max_batch = 0: never; the
+ * default).  A batch of k keys is staged into a library buffer of K keys, K =
+ * k rounded up to four significant bits (at least 16, at most k * 9/8 for k
+ * >= 16), entry j being key floor(j k / K): each key appears once or twice,
+ * in the batch's order.  Repeats of a key change nothing (Sec. 4 batches are
+ * sets; App. A counts only keys actually added or removed), so one graph
+ * serves every k of a bucket.  Graphs are captured on first use per (K,
+ * sorted, insert or delete) and replayed afterwards; a graph is captured
+ * again after the leaf arrays are replaced (resize) or a scratch buffer it
+ * uses moved; the 8 most recently used are kept.  Sets, counts and layouts
+ * are the same with and without graphs.  While per-phase profiling is on,
+ * updates take the launch-by-launch path.  Graphs pay off for small batches,
+ * whose time is launch latency; larger batches do up to 1/8 more sort and
+ * route work.  Errors: CPMA_EINVAL (null handle). */
+int cpma_use_graphs(cpma_t* h, uint64_t max_batch);
+
+/* Graph captures and graph launches of updates on this handle so far. */
+int cpma_graph_stats(const cpma_t* h, uint64_t* captures, uint64_t* launches);
+
 /* Device time and kernel-launch counters of the calls on this handle since the
  * last reset, for profiling: *launches = kernels launched by the library. */
 int cpma_stats(const cpma_t* h, uint64_t* launches);

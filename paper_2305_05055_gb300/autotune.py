@@ -54,10 +54,15 @@ def measure(base: torch.Tensor, sorted_keys: torch.Tensor, batch: int, queries: 
     j = r + c
     hi = torch.where(j < n, sorted_keys[torch.clamp(j, max=n - 1)], torch.full_like(lo, -1))
     res = {"leaf_bytes": leaf_bytes, "grow": list(grow), "bytes_per_key": g.bytes() / g.size()}
-    # insert and delete of the same fresh batch, on clones of one state
+    # insert and delete of the same fresh batch, on clones of one state whose
+    # scratch is reserved and warmed by an insert + delete of another batch
+    warm = torch.from_numpy(W.uniform_keys(seed + 3, batch, bits=40).view(np.int64)).to(dev)
     ms_ins, ms_del = [], []
     for _ in range(3):
         h = g.clone()
+        h.reserve(batch)
+        h.insert_batch(warm)
+        h.delete_batch(warm)
         torch.cuda.synchronize()
         ms_ins.append(_timed(lambda: h.insert_batch(ins), reps=1))
         ms_del.append(_timed(lambda: h.delete_batch(ins), reps=1))

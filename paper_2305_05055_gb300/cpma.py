@@ -75,6 +75,9 @@ def lib():
                 "cpma_sort_batch": (I, [V, V, V, U64, V, V, V]),
                 "cpma_profile": (I, [V, I]),
                 "cpma_profile_read": (I, [V, C.POINTER(C.c_double), P64, P64, I]),
+                "cpma_reserve": (I, [V, U64, U64, I, V]),
+                "cpma_use_graphs": (I, [V, U64]),
+                "cpma_graph_stats": (I, [V, P64, P64]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -268,6 +271,23 @@ def cpma_reset_stats(h):
     _check(lib().cpma_reset_stats(h), "cpma_reset_stats")
 
 
+def cpma_reserve(h, max_batch: int, max_queries: int = 0, tagged: bool = False, stream=None):
+    _check(lib().cpma_reserve(h, int(max_batch), int(max_queries), int(bool(tagged)),
+                              C.c_void_p(_stream(stream))), "cpma_reserve")
+
+
+def cpma_use_graphs(h, max_batch: int = 1 << 16):
+    """Front segment of untagged updates of <= max_batch keys as CUDA graphs
+    (0: off)."""
+    _check(lib().cpma_use_graphs(h, int(max_batch)), "cpma_use_graphs")
+
+
+def cpma_graph_stats(h) -> dict:
+    c, n = C.c_uint64(), C.c_uint64()
+    _check(lib().cpma_graph_stats(h, C.byref(c), C.byref(n)), "cpma_graph_stats")
+    return {"captures": int(c.value), "launches": int(n.value)}
+
+
 PHASES = ("sort", "route", "merge", "count", "redistribute", "finish", "has",
           "range_prep", "range", "sum", "merge_other")
 
@@ -357,6 +377,15 @@ class CPMA:
 
     def launches(self) -> int:
         return cpma_stats(self._h)
+
+    def reserve(self, max_batch: int, max_queries: int = 0, tagged: bool = False, stream=None):
+        cpma_reserve(self._h, max_batch, max_queries, tagged, stream)
+
+    def use_graphs(self, max_batch: int = 1 << 16):
+        cpma_use_graphs(self._h, max_batch)
+
+    def graph_stats(self) -> dict:
+        return cpma_graph_stats(self._h)
 
     def profile(self, enable: bool = True):
         cpma_profile(self._h, enable)

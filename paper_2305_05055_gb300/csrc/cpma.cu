@@ -16,9 +16,16 @@ int check_cuda(cudaError_t e) {
   return CPMA_ECUDA;
 }
 
+namespace {
+thread_local bool g_capturing = false;
+}  // namespace
+
+void set_capturing(bool on) { g_capturing = on; }
+
 int ensure(Buf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.cap >= bytes) return CPMA_OK;
+  if (g_capturing) return CPMA_EINTERNAL;
   size_t want = std::max(bytes, b.cap + b.cap / 2);
   want = (want + 255) & ~(size_t)255;
   if (b.p) {
@@ -141,8 +148,9 @@ void release_all(cpma* h) {
                  &s.T_newbytes, &s.T_state, &s.viol, &s.list_lane, &s.list_v1, &s.list_gen, &s.cand, &s.wins, &s.bits, &s.prefix, &s.ovf,
                  &s.E, &s.cost, &s.C, &s.srccnt, &s.srcoff, &s.dstart, &s.win_src, &s.win_dst,
                  &s.win_leaf_off, &s.win_elem_off, &s.win_dst_off, &s.partials, &s.partials_q, &s.q_first,
-                 &s.q_items, &s.q_off})
+                 &s.q_items, &s.q_off, &s.stage})
     release(*b);
+  graph_cache_free(h);
   cudaFree(h->data);
   cudaFree(h->used);
   cudaFree(h->cnt);
@@ -386,6 +394,33 @@ int cpma_export_layout(const cpma_t* h, uint8_t* d_data, uint32_t* d_used, uint6
 int cpma_stats(const cpma_t* h, uint64_t* launches) {
   if (!h || !launches) return CPMA_EINVAL;
   *launches = h->launches;
+  return CPMA_OK;
+}
+
+int cpma_reserve(cpma_t* h, uint64_t max_batch, uint64_t max_queries, int tagged,
+                 cpma_stream_t stream) {
+  if (!h) return CPMA_EINVAL;
+  CPMA_TRY(reserve(h, max_batch, tagged, (cudaStream_t)stream));
+  if (max_queries) {
+    Scratch& s = h->s;
+    CPMA_TRY(ensure(s.q_first, max_queries * 8));
+    CPMA_TRY(ensure(s.q_items, max_queries * 8));
+    CPMA_TRY(ensure(s.q_off, (max_queries + 1) * 8));
+    CPMA_TRY(ensure(s.partials_q, (size_t)(2 * h->num_sms + 2) * 8));
+  }
+  return CPMA_OK;
+}
+
+int cpma_use_graphs(cpma_t* h, uint64_t max_batch) {
+  if (!h) return CPMA_EINVAL;
+  h->graph_max_batch = max_batch;
+  return CPMA_OK;
+}
+
+int cpma_graph_stats(const cpma_t* h, uint64_t* captures, uint64_t* launches) {
+  if (!h) return CPMA_EINVAL;
+  if (captures) *captures = h->graph_captures;
+  if (launches) *launches = h->graph_launches;
   return CPMA_OK;
 }
 

@@ -13,6 +13,16 @@ constexpr unsigned FULL = 0xffffffffu;
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
 
+// Warp wid of nw takes the contiguous share [r0, r1) of n work items, shares
+// differing by at most one: a short list spreads over all warps instead of
+// filling a few warps 32 items at a time.
+__device__ __forceinline__ void warp_share(uint64_t n, uint64_t wid, uint64_t nw, uint64_t& r0,
+                                           uint64_t& r1) {
+  const uint64_t per = n / nw, extra = n % nw;
+  r0 = wid * per + (wid < extra ? wid : extra);
+  r1 = r0 + per + (wid < extra ? 1 : 0);
+}
+
 // Sec. 5 byte codes read as unsigned LEB128: max(1, ceil(bitlen(d) / 7)).
 __device__ __forceinline__ unsigned leb_len(uint64_t d) {
   unsigned bl = 64u - (unsigned)__clzll((long long)(d | 1ull));

@@ -77,6 +77,7 @@ struct Scratch {
   Buf partials_q;         // scan partials of the query path, which may run
                           // on another stream while an update sorts
   Buf q_first, q_items, q_off; // range queries
+  Buf stage;              // padded batch of a graph-launched update
 };
 
 // Profiling phases (cpma_profile_read order).
@@ -120,13 +121,23 @@ struct cpma {
   cpmaimpl::Scratch s;
   uint64_t launches = 0;
   cpmaimpl::Prof prof;
+  uint64_t graph_max_batch = 0;     // batches up to this size run their front segment as a graph
+  void* graphs = nullptr;           // graph cache (update.cu)
+  cudaStream_t cap_stream = nullptr;  // private stream graphs are captured on
+  uint64_t graph_captures = 0, graph_launches = 0;
 };
 
 namespace cpmaimpl {
 
-// memory
+// memory.  ensure() grows a buffer (never shrinks).  While a graph is being
+// captured on this thread it refuses to allocate (CPMA_EINTERNAL) instead.
 int ensure(Buf& b, size_t bytes);
 void release(Buf& b);
+void set_capturing(bool on);
+
+// update.cu: graph cache and scratch reservation
+void graph_cache_free(cpma* h);
+int reserve(cpma* h, uint64_t max_batch, int tagged, cudaStream_t st);
 
 // scan.cu: exclusive prefix sums.  out has n+1 entries (out[n] = total).
 // The element count is n_host, or *n_dev when n_dev != nullptr (n_host is
@@ -144,6 +155,9 @@ int scan_u64_query(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n, cudaS
 int scan_u64_given_partials(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host,
                             uint64_t* partials, uint64_t partials_cap, cudaStream_t st);
 
+// sort.cu: size the sort scratch for k keys (with 32-bit payloads if vals)
+// and set the kernels' shared-memory attributes.
+int sort_scratch(cpma* h, uint64_t k, bool vals);
 // sort.cu: sort k keys ascending into *out (one of the scratch buffers).
 int sort_keys(cpma* h, const uint64_t* d_in, uint64_t k, const uint64_t** out,
               cudaStream_t st);

@@ -42,16 +42,18 @@ __global__ void __launch_bounds__(kT) k_has(const uint64_t* __restrict__ keys, u
   const unsigned lane = lane_id();
   const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
   ull nbytes = 0;
-  for (uint64_t base = gw * 32; base < q; base += nw * 32) {
+  uint64_t r0, r1;
+  warp_share(q, gw, nw, r0, r1);
+  for (uint64_t base = r0; base < r1; base += 32) {
     const uint64_t qi = base + lane;
     uint64_t xi = 0, ji = 0;
     uint32_t ui = 0;
-    if (qi < q) {
+    if (qi < r1) {
       xi = keys[qi];
       ji = route_leaf(heads, L, xi);
       ui = min(used[ji], LB);
     }
-    const uint32_t nk = (uint32_t)min((uint64_t)32, q - base);
+    const uint32_t nk = (uint32_t)min((uint64_t)32, r1 - base);
     uint32_t found_bits = 0;
     for (uint32_t k = 0; k < nk; k++) {
       const uint64_t x = __shfl_sync(FULL, xi, k);
@@ -114,7 +116,7 @@ __global__ void __launch_bounds__(kT) k_has(const uint64_t* __restrict__ keys, u
       }
       if (found) found_bits |= 1u << k;
     }
-    if (qi < q) out[qi] = (found_bits >> lane) & 1u;
+    if (qi < r1) out[qi] = (found_bits >> lane) & 1u;
   }
   if (prof && lane == 0 && nbytes) atomicAdd(prof, nbytes);
 }

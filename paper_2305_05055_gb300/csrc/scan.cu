@@ -17,6 +17,7 @@ namespace {
 constexpr int kT = 256;
 constexpr int kItems = 8;
 constexpr int kTile = kT * kItems;
+constexpr uint64_t kSingleTiles = 4;  // up to 8192 elements: one block, one launch
 
 __device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* warp_tot,
                                                     uint64_t* total) {
@@ -83,7 +84,8 @@ __global__ void __launch_bounds__(1024) k_partials(uint64_t* partials, int G) {
   if (threadIdx.x == 0) partials[G] = carry;
 }
 
-template <typename Tin>
+// SINGLE: the whole scan in one block (small inputs; no partials pass).
+template <typename Tin, bool SINGLE = false>
 __global__ void __launch_bounds__(kT) k_down(const Tin* __restrict__ in, uint64_t* __restrict__ out,
                                              uint64_t n_host, const ull* n_dev,
                                              const uint64_t* __restrict__ partials) {
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(kT) k_down(const Tin* __restrict__ in, uint64_
   const uint64_t n = n_dev ? *n_dev : n_host;
   const uint64_t G = gridDim.x;
   const uint64_t b0 = n * blockIdx.x / G, b1 = n * (blockIdx.x + 1) / G;
-  uint64_t carry = partials[blockIdx.x];
+  uint64_t carry = SINGLE ? 0 : partials[blockIdx.x];
   for (uint64_t t0 = b0; t0 < b1; t0 += kTile) {
     const uint64_t cnt = min((uint64_t)kTile, b1 - t0);
     for (uint32_t i = threadIdx.x; i < kTile; i += kT)
@@ -112,13 +114,18 @@ __global__ void __launch_bounds__(kT) k_down(const Tin* __restrict__ in, uint64_
     carry += tile_total;
     __syncthreads();
   }
-  if (blockIdx.x == G - 1 && threadIdx.x == 0) out[n] = partials[G];
+  if (blockIdx.x == G - 1 && threadIdx.x == 0) out[n] = SINGLE ? carry : partials[G];
 }
 
 template <typename Tin>
 int scan_impl(cpma* h, const Tin* in, uint64_t* out, uint64_t n_host, const ull* n_dev,
               cudaStream_t st, Buf* partials = nullptr) {
   uint64_t tiles = (n_host + kTile - 1) / kTile;
+  if (tiles <= kSingleTiles) {
+    k_down<Tin, true><<<1, kT, 0, st>>>(in, out, n_host, n_dev, nullptr);
+    h->launches++;
+    return check_cuda(cudaGetLastError());
+  }
   int G = (int)std::min<uint64_t>((uint64_t)2 * h->num_sms, std::max<uint64_t>(tiles, 1));
   Buf& pb = partials ? *partials : h->s.partials;
   CPMA_TRY(ensure(pb, (size_t)(G + 1) * 8));
@@ -152,6 +159,11 @@ int scan_u64_query(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n, cudaS
 int scan_u64_given_partials(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host,
                             uint64_t* partials, uint64_t partials_cap, cudaStream_t st) {
   uint64_t tiles = (n_host + kTile - 1) / kTile;
+  if (tiles <= kSingleTiles) {
+    k_down<uint64_t, true><<<1, kT, 0, st>>>(in, out, n_host, nullptr, nullptr);
+    h->launches++;
+    return check_cuda(cudaGetLastError());
+  }
   int G = (int)std::min<uint64_t>((uint64_t)2 * h->num_sms, std::max<uint64_t>(tiles, 1));
   if ((uint64_t)G + 1 > partials_cap) return CPMA_EINVAL;
   k_reduce<uint64_t><<<G, kT, 0, st>>>(in, n_host, nullptr, partials);

@@ -320,26 +320,46 @@ __global__ void k_unique_scatter(const uint64_t* __restrict__ in, uint64_t k,
 
 }  // namespace
 
+namespace {
+size_t ctl_bytes() { return (sizeof(SortCtl) + 255) & ~(size_t)255; }
+size_t look_bytes(uint64_t k) {
+  const uint64_t ntiles = (k + kTile - 1) / kTile;
+  return (size_t)8 * ntiles * 256 * 4;
+}
+template <bool VALS>
+void sort_attrs() {
+  static bool done = false;  // one per instantiation
+  if (done) return;
+  const int smem = (int)sizeof(TileSmemT<VALS>);
+  cudaFuncSetAttribute(k_onesweep<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_sort_small<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaGetLastError();
+  done = true;
+}
+}  // namespace
+
+int sort_scratch(cpma* h, uint64_t k, bool vals) {
+  sort_attrs<false>();
+  if (vals) sort_attrs<true>();
+  if (k <= 1) return CPMA_OK;
+  CPMA_TRY(ensure(h->s.keysA, k * 8));
+  if (vals) CPMA_TRY(ensure(h->s.valsA, k * 4));
+  if (k <= (uint64_t)kTile) return CPMA_OK;
+  CPMA_TRY(ensure(h->s.keysB, k * 8));
+  if (vals) CPMA_TRY(ensure(h->s.valsB, k * 4));
+  return ensure(h->s.hist, ctl_bytes() + look_bytes(k));
+}
+
 template <bool VALS>
 int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, const uint64_t** out,
               const uint32_t** vout, cudaStream_t st) {
   *out = d_in;
   if (vout) *vout = v_in;
   if (k <= 1) return CPMA_OK;
-  CPMA_TRY(ensure(h->s.keysA, k * 8));
+  CPMA_TRY(sort_scratch(h, k, VALS));
   uint64_t* A = (uint64_t*)h->s.keysA.p;
-  uint32_t* VA = nullptr;
-  if (VALS) {
-    CPMA_TRY(ensure(h->s.valsA, k * 4));
-    VA = (uint32_t*)h->s.valsA.p;
-  }
+  uint32_t* VA = VALS ? (uint32_t*)h->s.valsA.p : nullptr;
   const size_t smem = sizeof(TileSmemT<VALS>);
-  static bool attr_done = false;  // one per instantiation
-  if (!attr_done) {
-    CPMA_CUDA(cudaFuncSetAttribute(k_onesweep<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    CPMA_CUDA(cudaFuncSetAttribute(k_sort_small<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_done = true;
-  }
   if (k <= (uint64_t)kTile) {
     prof_add_bytes(h, PH_SORT, (VALS ? 24ull : 16ull) * k);
     k_sort_small<VALS><<<1, kT, smem, st>>>(d_in, A, v_in, VA, (uint32_t)k);
@@ -348,21 +368,13 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
     if (vout) *vout = VA;
     return check_cuda(cudaGetLastError());
   }
-  CPMA_TRY(ensure(h->s.keysB, k * 8));
   uint64_t* B = (uint64_t*)h->s.keysB.p;
-  uint32_t* VB = nullptr;
-  if (VALS) {
-    CPMA_TRY(ensure(h->s.valsB, k * 4));
-    VB = (uint32_t*)h->s.valsB.p;
-  }
+  uint32_t* VB = VALS ? (uint32_t*)h->s.valsB.p : nullptr;
   const uint32_t ntiles = (uint32_t)((k + kTile - 1) / kTile);
   // control block + 8 look-back arrays, zeroed in one memset
-  const size_t ctl_bytes = (sizeof(SortCtl) + 255) & ~(size_t)255;
-  const size_t look_bytes = (size_t)8 * ntiles * 256 * 4;
-  CPMA_TRY(ensure(h->s.hist, ctl_bytes + look_bytes));
   SortCtl* ctl = reinterpret_cast<SortCtl*>(h->s.hist.p);
-  uint32_t* look = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(h->s.hist.p) + ctl_bytes);
-  CPMA_CUDA(cudaMemsetAsync(h->s.hist.p, 0, ctl_bytes + look_bytes, st));
+  uint32_t* look = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(h->s.hist.p) + ctl_bytes());
+  CPMA_CUDA(cudaMemsetAsync(h->s.hist.p, 0, ctl_bytes() + look_bytes(k), st));
   const int hgrid = (int)std::min<uint64_t>((uint64_t)h->num_sms * 2, (k + kT - 1) / kT);
   k_hist_all<<<hgrid, kT, 0, st>>>(d_in, k, ctl);
   h->launches++;

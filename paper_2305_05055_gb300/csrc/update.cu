@@ -322,10 +322,11 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
   int32_t* shc = reinterpret_cast<int32_t*>(en + kSmall);
   const uint64_t nL = a.st->n_lane;
   ull nbytes = 0;  // algorithmic bytes (lane 0's count)
-  for (uint64_t tbase = ((uint64_t)blockIdx.x * wpb + warp) * 32; tbase < nL;
-       tbase += (uint64_t)gridDim.x * wpb * 32) {
-    // metadata of 32 touched leaves of the work list, one per lane
-    const bool have = tbase + lane < nL;
+  uint64_t r0, r1;
+  warp_share(nL, (uint64_t)blockIdx.x * wpb + warp, (uint64_t)gridDim.x * wpb, r0, r1);
+  for (uint64_t tbase = r0; tbase < r1; tbase += 32) {
+    // metadata of up to 32 touched leaves of the work list, one per lane
+    const bool have = tbase + lane < r1;
     const uint32_t ti = have ? a.list_lane[tbase + lane] : 0u;
     uint32_t i_tb = 0, i_te = 0, i_uold = 0, i_j = 0, i_m = 0, i_fc0 = 0, i_fc1 = 0;
     if (have) {
@@ -804,13 +805,14 @@ __global__ void __launch_bounds__(kT) k_merge(MergeArgs a) {
   // count mode: the work items of the list; write mode: the items of pending
   // leaves, 32 screened per step (one per lane)
   const uint64_t nitems = WRITE ? a.st->nchunks : a.st->n_gen;
-  for (uint64_t base = ((uint64_t)blockIdx.x * wpb + warp) * 32; base < nitems;
-       base += (uint64_t)gridDim.x * wpb * 32) {
+  uint64_t r0, r1;
+  warp_share(nitems, (uint64_t)blockIdx.x * wpb + warp, (uint64_t)gridDim.x * wpb, r0, r1);
+  for (uint64_t base = r0; base < r1; base += 32) {
    bool need = false;
    uint64_t myc = 0;
    {
     const uint64_t cc = base + lane;
-    if (cc < nitems) {
+    if (cc < r1) {
       if (WRITE) {
         myc = cc;
         need = a.T_state[a.chunk_tid[cc]] == kPending;
@@ -1542,33 +1544,34 @@ int do_resize(cpma* h, cudaStream_t st, uint64_t T, uint64_t n_after, uint64_t n
   return CPMA_OK;
 }
 
-}  // namespace
+// Host-side values the front segment of an update leaves for the rest of it.
+struct Front {
+  MergeArgs ma;
+  FinArgs fa;
+  Levels lv;
+  unsigned H = 0;
+  int mgrid = 0, mwarps = 0;
+  size_t msmem = 0;
+};
 
-int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_delete,
-               uint64_t* d_delta, cudaStream_t st, const uint32_t* tags, uint64_t* tag_counts,
-               uint64_t ntags) {
-  Status* ds = h->d_status;
-  if (tag_counts && ntags) CPMA_CUDA(cudaMemsetAsync(tag_counts, 0, ntags * 8, st));
-  if (k == 0) {
-    if (d_delta) CPMA_CUDA(cudaMemsetAsync(d_delta, 0, 8, st));
-    return CPMA_OK;
-  }
-  if (k >= (1ull << 31)) return CPMA_EINVAL;
-  CPMA_CUDA(cudaMemsetAsync(ds, 0, offsetof(Status, empties), st));
-  const uint64_t* u = d_keys;
-  const uint32_t* ut = tags;
-  if (tags) {
-    k_check_tags<<<grid_for(h, k), kT, 0, st>>>(tags, k, ntags, ds);
-    h->launches++;
-  }
-  if (!sorted) {
-    prof_begin(h, PH_SORT, st);
-    if (tags) CPMA_TRY(sort_pairs(h, d_keys, tags, k, &u, &ut, st));
-    else CPMA_TRY(sort_keys(h, d_keys, k, &u, st));
-    prof_end(h, st);
-  }
-  // ---- scratch (all before any change to the structure) ----
+void merge_attrs() {
+  static bool done = false;  // one process, one device
+  if (done) return;
+  cudaFuncSetAttribute(k_merge<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_merge<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_merge_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaGetLastError();
+  done = true;
+}
+
+// Every buffer the front segment of a batch of k keys touches, sized before
+// it runs (a graph capture must not allocate), plus the window bitsets of the
+// current tree.
+int front_scratch(cpma* h, uint64_t k, bool tagged, cudaStream_t st) {
   Scratch& s = h->s;
+  merge_attrs();
+  CPMA_TRY(sort_scratch(h, k, tagged));
+  CPMA_TRY(ensure(s.partials, (size_t)(2 * h->num_sms + 2) * 8));
   CPMA_TRY(ensure(s.leaf_of, k * 4));
   CPMA_TRY(ensure(s.flags, k * 8));
   CPMA_TRY(ensure(s.flags_scan, (k + 1) * 8));
@@ -1584,7 +1587,36 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   CPMA_TRY(ensure(s.wins, (2 * k + 2) * 16));
   CPMA_TRY(ensure(s.prefix, (h->L + 2) * 8));
   Levels lv;
-  CPMA_TRY(ensure_bits(h, st, &lv));
+  return ensure_bits(h, st, &lv);
+}
+
+// The front segment of an update: status reset, tag check, sort, route,
+// work lists, the in-place merges, finalize and the overflow-offset scan --
+// everything before the first host read of the status block.  It reads the
+// host state only through h's fields and its arguments, never allocates
+// (front_scratch sized everything) and never waits, so it can be captured
+// into a CUDA graph.  f receives the host-side values the rest of the update
+// needs.
+int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_delete,
+              cudaStream_t st, const uint32_t* tags, uint64_t* tag_counts, uint64_t ntags,
+              Front* f) {
+  Status* ds = h->d_status;
+  CPMA_CUDA(cudaMemsetAsync(ds, 0, offsetof(Status, empties), st));
+  const uint64_t* u = d_keys;
+  const uint32_t* ut = tags;
+  if (tags) {
+    k_check_tags<<<grid_for(h, k), kT, 0, st>>>(tags, k, ntags, ds);
+    h->launches++;
+  }
+  if (!sorted) {
+    prof_begin(h, PH_SORT, st);
+    if (tags) CPMA_TRY(sort_pairs(h, d_keys, tags, k, &u, &ut, st));
+    else CPMA_TRY(sort_keys(h, d_keys, k, &u, st));
+    prof_end(h, st);
+  }
+  Scratch& s = h->s;
+  Levels lv;
+  CPMA_TRY(ensure_bits(h, st, &lv));  // sized by front_scratch: no memset here
   const unsigned H = ceil_log2(h->L);
   const Bounds B = bounds_of(h);
   const uint32_t LB = h->cfg.leaf_bytes;
@@ -1648,14 +1680,6 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   const size_t per = merge_warp_bytes(LB);
   const int mwarps = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));
   const size_t msmem = per * mwarps;
-  static bool attr_done = false;
-  if (!attr_done) {
-    CPMA_CUDA(cudaFuncSetAttribute(k_merge<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   200 * 1024));
-    CPMA_CUDA(cudaFuncSetAttribute(k_merge<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   200 * 1024));
-    attr_done = true;
-  }
   const int mgrid = (int)std::max<uint64_t>(
       1, std::min<uint64_t>((k + kChunk + mwarps - 1) / mwarps, (uint64_t)h->num_sms * 4));
   k_classify<<<grid_for(h, k), kT, 0, st>>>(ma);
@@ -1665,12 +1689,6 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   {
     const size_t sper = small_warp_bytes(LB);
     const int swarps = (int)std::max<size_t>(1, std::min<size_t>(8, (216 * 1024) / (4 * sper)));
-    static bool sattr = false;
-    if (!sattr) {
-      CPMA_CUDA(cudaFuncSetAttribute(k_merge_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     200 * 1024));
-      sattr = true;
-    }
     const int sgrid = (int)std::max<uint64_t>(
         1, std::min<uint64_t>((k + swarps - 1) / swarps, (uint64_t)h->num_sms * 8));
     if (!is_delete) {
@@ -1720,6 +1738,197 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   h->launches++;
   CPMA_CUDA(cudaGetLastError());
   prof_end(h, st);
+  f->ma = ma;
+  f->fa = fa;
+  f->lv = lv;
+  f->H = H;
+  f->mgrid = mgrid;
+  f->mwarps = mwarps;
+  f->msmem = msmem;
+  return CPMA_OK;
+}
+
+
+// ---- CUDA graphs for the front segment ----
+//
+// A batch of k keys is staged into a library buffer of K = graph_bucket(k)
+// keys, staged[j] = batch[floor(j k / K)]: every key appears once or twice,
+// in the batch's own order (a sorted batch stays sorted), so the repeats are
+// spread evenly over the touched leaves instead of piling into one.  Repeats
+// are dropped by the merge (first occurrence wins), so the padded batch
+// changes the set exactly as the original does, and one graph serves every k
+// of its bucket.  A graph bakes in the addresses of the structure's arrays, of the
+// scratch buffers the segment touches and the leaf count, so it is keyed by
+// (K, sorted, insert/delete, those addresses and L) and captured again when
+// any of them changed (a resize, a scratch buffer that had to grow).
+
+constexpr int kGraphSlots = 8;
+
+constexpr int kSigPtrs = 33;
+
+struct FrontSig {
+  const void* p[kSigPtrs];
+  uint64_t L;
+  bool operator==(const FrontSig& o) const {
+    if (L != o.L) return false;
+    for (int i = 0; i < kSigPtrs; i++)
+      if (p[i] != o.p[i]) return false;
+    return true;
+  }
+};
+
+FrontSig front_sig(const cpma* h) {
+  const Scratch& s = h->s;
+  return FrontSig{{s.stage.p,     s.keysA.p,      s.keysB.p,         s.hist.p,      s.partials.p,
+                   s.leaf_of.p,   s.flags.p,      s.flags_scan.p,    s.chunk_begin.p,
+                   s.chunk_leaf.p, s.chunk_tid.p, s.chunk_cnt.p,     s.chunk_off.p, s.T_leaf.p,
+                   s.T_begin.p,   s.T_first_chunk.p, s.T_oldcnt.p,   s.T_oldused.p, s.T_newcnt.p,
+                   s.T_newbytes.p, s.T_state.p,   s.viol.p,          s.list_lane.p, s.list_v1.p,
+                   s.list_gen.p,  s.cand.p,       s.wins.p,          s.bits.p,      h->data,
+                   h->used,       h->cnt,         h->heads,          h->d_status},
+                  h->L};
+}
+
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t K = 0, last_use = 0, launches = 0;
+  int sorted = 0, is_delete = 0;
+  FrontSig sig{};
+  Front f;
+};
+
+struct GraphCache {
+  GraphSlot slot[kGraphSlots];
+  uint64_t clock = 0;
+};
+
+// k rounded up to 4 significant bits (at most 1/8 extra keys), at least 16
+uint64_t graph_bucket(uint64_t k) {
+  if (k <= 16) return 16;
+  const unsigned e = 63u - (unsigned)__builtin_clzll(k);
+  const uint64_t step = 1ull << (e - 3);
+  return (k + step - 1) / step * step;
+}
+
+__global__ void __launch_bounds__(kT) k_stage(const uint64_t* __restrict__ in, uint64_t k,
+                                              uint64_t* __restrict__ out, uint64_t K) {
+  // j k < 2^31 * 2^31: no overflow
+  for (uint64_t j = gtid(); j < K; j += gstride()) out[j] = in[j * k / K];
+}
+
+int run_front_graph(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_delete,
+                    cudaStream_t st, Front* f) {
+  const uint64_t K = graph_bucket(k);
+  CPMA_TRY(ensure(h->s.stage, K * 8));
+  CPMA_TRY(front_scratch(h, K, false, st));
+  uint64_t* stage = P<uint64_t>(h->s.stage);
+  k_stage<<<grid_for(h, K), kT, 0, st>>>(d_keys, k, stage, K);
+  h->launches++;
+  CPMA_CUDA(cudaGetLastError());
+  if (!h->graphs) h->graphs = new GraphCache();
+  GraphCache& c = *static_cast<GraphCache*>(h->graphs);
+  const FrontSig sig = front_sig(h);
+  GraphSlot* slot = nullptr;
+  for (GraphSlot& g : c.slot)
+    if (g.exec && g.K == K && g.sorted == sorted && g.is_delete == is_delete && g.sig == sig)
+      slot = &g;
+  if (!slot) {
+    slot = &c.slot[0];
+    for (GraphSlot& g : c.slot)
+      if (!g.exec || g.last_use < slot->last_use) slot = &g;
+    if (slot->exec) {
+      // the previous update on this handle has been waited for, so no
+      // launch of this graph is still in flight
+      cudaGraphExecDestroy(slot->exec);
+      slot->exec = nullptr;
+    }
+    if (!h->cap_stream)
+      CPMA_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    const uint64_t l0 = h->launches;
+    CPMA_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    set_capturing(true);
+    int rc = run_front(h, stage, K, sorted, is_delete, h->cap_stream, nullptr, nullptr, 0,
+                       &slot->f);
+    set_capturing(false);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc == CPMA_OK) rc = check_cuda(e);
+    cudaGraphExec_t ex = nullptr;
+    if (rc == CPMA_OK) rc = check_cuda(cudaGraphInstantiate(&ex, g, 0));
+    if (g) cudaGraphDestroy(g);
+    slot->launches = h->launches - l0;
+    h->launches = l0;
+    if (rc != CPMA_OK) {
+      cudaGetLastError();
+      return rc;
+    }
+    slot->exec = ex;
+    slot->K = K;
+    slot->sorted = sorted;
+    slot->is_delete = is_delete;
+    slot->sig = sig;
+    h->graph_captures++;
+  }
+  slot->last_use = ++c.clock;
+  CPMA_CUDA(cudaGraphLaunch(slot->exec, st));
+  h->launches += slot->launches;
+  h->graph_launches++;
+  *f = slot->f;
+  return CPMA_OK;
+}
+
+}  // namespace
+
+void graph_cache_free(cpma* h) {
+  if (!h->graphs) return;
+  GraphCache* c = static_cast<GraphCache*>(h->graphs);
+  for (GraphSlot& g : c->slot)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  delete c;
+  h->graphs = nullptr;
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  h->cap_stream = nullptr;
+}
+
+int reserve(cpma* h, uint64_t max_batch, int tagged, cudaStream_t st) {
+  if (max_batch >= (1ull << 31)) return CPMA_EINVAL;
+  if (max_batch == 0) return CPMA_OK;
+  CPMA_TRY(front_scratch(h, max_batch, tagged != 0, st));
+  if (h->graph_max_batch && !tagged) {
+    const uint64_t K = graph_bucket(std::min(max_batch, h->graph_max_batch));
+    if (K < (1ull << 31)) {
+      CPMA_TRY(ensure(h->s.stage, K * 8));
+      CPMA_TRY(front_scratch(h, K, false, st));
+    }
+  }
+  return CPMA_OK;
+}
+
+int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_delete,
+               uint64_t* d_delta, cudaStream_t st, const uint32_t* tags, uint64_t* tag_counts,
+               uint64_t ntags) {
+  Status* ds = h->d_status;
+  if (tag_counts && ntags) CPMA_CUDA(cudaMemsetAsync(tag_counts, 0, ntags * 8, st));
+  if (k == 0) {
+    if (d_delta) CPMA_CUDA(cudaMemsetAsync(d_delta, 0, 8, st));
+    return CPMA_OK;
+  }
+  if (k >= (1ull << 31)) return CPMA_EINVAL;
+  Scratch& s = h->s;
+  Front f;
+  if (k <= h->graph_max_batch && !tags && !h->prof.on && graph_bucket(k) < (1ull << 31)) {
+    CPMA_TRY(run_front_graph(h, d_keys, k, sorted, is_delete, st, &f));
+  } else {
+    CPMA_TRY(front_scratch(h, k, tags != nullptr, st));
+    CPMA_TRY(run_front(h, d_keys, k, sorted, is_delete, st, tags, tag_counts, ntags, &f));
+  }
+  MergeArgs& ma = f.ma;
+  FinArgs& fa = f.fa;
+  const Levels& lv = f.lv;
+  const unsigned H = f.H;
+  const Bounds B = bounds_of(h);
+  const int mgrid = f.mgrid, mwarps = f.mwarps;
+  const size_t msmem = f.msmem;
   CPMA_TRY(sync_status(h, st));
   prof_begin(h, PH_COUNT, st);
   Status hs = *h->h_status;

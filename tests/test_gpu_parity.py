@@ -254,3 +254,55 @@ def test_small_batches_hit_every_splice_case(LB):
             assert got == o.insert_batch(keys) == p.insert_batch(keys)
         same_layout(g, o)
     same_queries(g, p, 85)
+
+
+@pytest.mark.parametrize("LB", [256, 512, 2048])
+def test_graph_updates_match_oracle(LB):
+    """Updates whose front segment runs as a replayed CUDA graph (batches
+    padded to a size bucket with copies of their last key) give the same
+    counts, sets and byte layout as the oracle, through resizes (which force
+    a new capture) and with several batch sizes sharing one bucket."""
+    base = W.uniform_keys(31, 6000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=LB)
+    g.use_graphs(1 << 20)
+    g.reserve(4500)
+    o = oracle.SeqCPMA(base, leaf_bytes=LB)
+    p = oracle.PlainSet(base)
+    sizes = [1, 7, 16, 17, 4000, 4100, 4095, 300, 300, 300, 4096, 4097]
+    for r, k in enumerate(sizes * 2):
+        if r % 3 == 2 and len(p):
+            keys = W.sample_present(p.S, 800 + r, min(k, len(p)))
+            keys = np.concatenate([keys, W.uniform_keys(850 + r, 5, bits=40)])
+            got = int(g.delete_batch(T(keys)).item())
+            assert got == o.delete_batch(keys) == p.delete_batch(keys)
+        else:
+            keys = W.uniform_keys(700 + r, k, bits=40)
+            if r % 4 == 1:
+                keys = np.sort(keys)
+                got = int(g.insert_batch(T(keys), sorted=True).item())
+            else:
+                got = int(g.insert_batch(T(keys)).item())
+            assert got == o.insert_batch(keys) == p.insert_batch(keys)
+        same_layout(g, o)
+    same_queries(g, p, 77, 200)
+    st = g.graph_stats()
+    assert st["launches"] == 2 * len(sizes)
+    assert 0 < st["captures"] < st["launches"]
+
+
+def test_graphs_replay_within_a_bucket():
+    """After a reserve, batches of different sizes in one bucket reuse one
+    captured graph until the leaf arrays are replaced."""
+    base = W.uniform_keys(41, 200000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=512)
+    g.use_graphs(1 << 20)
+    g.reserve(1100)
+    p = oracle.PlainSet(base)
+    L0 = g.leaves()
+    for r, k in enumerate([1000, 1001, 1024, 1010, 1023, 1017]):  # bucket 1024
+        keys = W.uniform_keys(900 + r, k, bits=40)
+        assert int(g.insert_batch(T(keys)).item()) == p.insert_batch(keys)
+    assert g.leaves() == L0  # no resize at this fill
+    assert g.graph_stats() == {"captures": 1, "launches": 6}
+    s, c = g.sum()
+    assert int(cp.to_u64(s)[0]) == p.sum() and int(c.item()) == len(p)
