@@ -261,16 +261,12 @@ __device__ __forceinline__ uint32_t compact7(uint32_t y) {  // 4 bytes' 7-bit gr
 __device__ __forceinline__ uint32_t mask7(uint32_t groups) {  // low 7*groups bits, groups <= 4
   return groups >= 4 ? 0x0FFFFFFFu : ((1u << (7u * groups)) - 1u);
 }
-// 32-bit window of the 16 bytes x[] starting at byte s (zeros past the end)
+// 32-bit window of the 16 bytes x[] starting at byte s <= 16 (zeros past the end)
 __device__ __forceinline__ uint32_t window32(const uint32_t x[4], uint32_t s) {
-  const uint64_t lo = (uint64_t)x[0] | ((uint64_t)x[1] << 32);
-  const uint64_t hi = (uint64_t)x[2] | ((uint64_t)x[3] << 32);
-  uint64_t win;
-  if (s == 0) win = lo;
-  else if (s < 8) win = (lo >> (8u * s)) | (hi << (64u - 8u * s));
-  else if (s < 16) win = hi >> (8u * (s - 8u));
-  else win = 0;
-  return (uint32_t)win;
+  const uint32_t i = s >> 2, sh = 8u * (s & 3u);
+  const uint32_t lo = i == 0 ? x[0] : i == 1 ? x[1] : i == 2 ? x[2] : i == 3 ? x[3] : 0u;
+  const uint32_t hi = i == 0 ? x[1] : i == 1 ? x[2] : i == 2 ? x[3] : 0u;
+  return __funnelshift_r(lo, hi, sh);
 }
 
 struct LaneCodes {
@@ -298,7 +294,11 @@ __device__ __forceinline__ void lane_codes(const uint32_t w[4], int b_lo, int b_
     tb[q] = (rm & 0x01010101u) & ~cb[q];
   }
   L.term = gather4(tb[0]) | (gather4(tb[1]) << 4) | (gather4(tb[2]) << 8) | (gather4(tb[3]) << 12);
-  uint32_t S0 = 0, S1 = 0, S2 = 0, S3 = 0, W0 = 0, W1 = 0, W2 = 0, W3 = 0;
+  // Byte b's 7 payload bits sit at group g_b = (continuation bytes right
+  // before it, at most 3) of its code.  With 0/1 byte masks m_i of g_b == i,
+  // dp4a with multipliers m0 + 128 m1 and m2 + 128 m3 gives S0 + (S1 << 7)
+  // and S2 + (S3 << 7) directly, S_i the sum of the group-i payloads.
+  uint32_t S01 = 0, S23 = 0, W0 = 0, W1 = 0, W2 = 0, W3 = 0;
   uint32_t badm = 0, base = 0;
 #pragma unroll
   for (int q = 0; q < 4; q++) {
@@ -307,26 +307,22 @@ __device__ __forceinline__ void lane_codes(const uint32_t w[4], int b_lo, int b_
     const uint32_t p2 = __funnelshift_l(prev, cb[q], 16);
     const uint32_t p3 = __funnelshift_l(prev, cb[q], 24);
     const uint32_t a12 = p1 & p2, a123 = a12 & p3;
-    const uint32_t g = p1 + a12 + a123;
     badm |= a123 & cb[q];
     const uint32_t v = L.x[q] & 0x7F7F7F7Fu;
-    const uint32_t v0 = v & __vcmpeq4(g, 0u), v1 = v & __vcmpeq4(g, 0x01010101u);
-    const uint32_t v2 = v & __vcmpeq4(g, 0x02020202u), v3 = v & __vcmpeq4(g, 0x03030303u);
-    S0 = __dp4a(v0, 0x01010101u, S0);
-    S1 = __dp4a(v1, 0x01010101u, S1);
-    S2 = __dp4a(v2, 0x01010101u, S2);
-    S3 = __dp4a(v3, 0x01010101u, S3);
+    const uint32_t m0 = ~p1 & 0x01010101u, m1 = p1 ^ a12, m2 = a12 ^ a123, m3 = a123;
+    S01 = __dp4a(v, m0 | (m1 << 7), S01);
+    S23 = __dp4a(v, m2 | (m3 << 7), S23);
     if constexpr (WANT_W) {
       // terminators before each byte of the word (bytes), plus the earlier words'
       const uint32_t lidx = tb[q] * 0x01010100u + base * 0x01010101u;
-      W0 = __dp4a(v0, lidx, W0);
-      W1 = __dp4a(v1, lidx, W1);
-      W2 = __dp4a(v2, lidx, W2);
-      W3 = __dp4a(v3, lidx, W3);
+      W0 = __dp4a(v & (m0 * 0x7Fu), lidx, W0);
+      W1 = __dp4a(v & (m1 * 0x7Fu), lidx, W1);
+      W2 = __dp4a(v & (m2 * 0x7Fu), lidx, W2);
+      W3 = __dp4a(v & (m3 * 0x7Fu), lidx, W3);
       base += __popc(tb[q]);
     }
   }
-  const uint32_t Dall = S0 + (S1 << 7) + (S2 << 14) + (S3 << 21);
+  const uint32_t Dall = S01 + (S23 << 14);
   L.bad = badm != 0 || (range != 0 && L.term == 0);
   L.tail = 0;
   L.tail_sh = 0;
