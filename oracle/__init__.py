@@ -59,6 +59,9 @@ def lib():
                 "oset_difference": (S, [u64p, S, u64p, S, u64p]),
                 "oset_has": (I, [u64p, S, U64]),
                 "oset_range": (None, [u64p, S, U64, U64, C.POINTER(U64), C.POINTER(U64)]),
+                "oset_range_length": (None, [u64p, S, U64, U64, C.POINTER(U64), C.POINTER(U64)]),
+                "oset_range_reduce": (None, [u64p, S, U64, U64, C.c_int, U64, U64,
+                                             C.POINTER(U64), C.POINTER(U64)]),
                 "o_leb_len": (C.c_uint, [U64]),
                 "o_leb_put": (C.c_uint, [u8p, U64]),
                 "o_leb_get": (C.c_uint, [u8p, C.POINTER(U64)]),
@@ -216,6 +219,37 @@ class PlainSet:
             f(S, self.S.size, int(lo[i]), int(hi[i]), C.byref(s), C.byref(c))
             sums[i], cnts[i] = s.value, c.value
         return sums, cnts
+
+    def range_map_length(self, start, length):
+        """App. A map_range_length with the sum: the first length[i] keys
+        >= start[i]; returns (sums mod 2^64, counts)."""
+        start, length = _u64(start), _u64(length)
+        S = self.S if self.S.size else np.zeros(1, np.uint64)
+        sums = np.zeros(start.size, dtype=np.uint64)
+        cnts = np.zeros(start.size, dtype=np.uint64)
+        s, c = C.c_uint64(), C.c_uint64()
+        f = lib().oset_range_length
+        for i in range(start.size):
+            f(S, self.S.size, int(start[i]), int(length[i]), C.byref(s), C.byref(c))
+            sums[i], cnts[i] = s.value, c.value
+        return sums, cnts
+
+    OPS = {"sum": 0, "min": 1, "max": 2, "xor": 3}
+
+    def range_reduce(self, lo, hi, op="sum", mask=0, value=0):
+        """range_map with another function over the keys in [lo, hi) whose
+        bits under `mask` equal `value`; returns (results, counts)."""
+        lo, hi = _u64(lo), _u64(hi)
+        S = self.S if self.S.size else np.zeros(1, np.uint64)
+        outs = np.zeros(lo.size, dtype=np.uint64)
+        cnts = np.zeros(lo.size, dtype=np.uint64)
+        r, c = C.c_uint64(), C.c_uint64()
+        f = lib().oset_range_reduce
+        for i in range(lo.size):
+            f(S, self.S.size, int(lo[i]), int(hi[i]), self.OPS[op], int(mask), int(value),
+              C.byref(r), C.byref(c))
+            outs[i], cnts[i] = r.value, c.value
+        return outs, cnts
 
     def sum(self) -> int:
         return int(np.sum(self.S, dtype=np.uint64)) if self.S.size else 0

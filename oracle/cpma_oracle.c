@@ -151,6 +151,42 @@ void oset_range(const uint64_t* S, size_t n, uint64_t lo, uint64_t hi,
   *count = c;
 }
 
+/* App. A map_range_length: the function runs on at most `length` elements,
+ * starting from the first key >= start.  Here the function is the sum
+ * (mod 2^64); count = how many elements it ran on. */
+void oset_range_length(const uint64_t* S, size_t n, uint64_t start, uint64_t length,
+                       uint64_t* sum, uint64_t* count) {
+  size_t i = lower_bound_u64(S, n, start);
+  size_t j = (length >= n - i) ? n : i + (size_t)length;
+  uint64_t s = 0;
+  for (size_t t = i; t < j; t++) s += S[t];
+  *sum = s;
+  *count = j - i;
+}
+
+/* Sec. 3 range_map with other functions: over the keys x in [lo, hi) with
+ * (x & mask) == value, op 0 = sum mod 2^64, 1 = minimum (2^64-1 if none),
+ * 2 = maximum (0 if none), 3 = exclusive or (0 if none); count = how many
+ * keys passed the filter. */
+void oset_range_reduce(const uint64_t* S, size_t n, uint64_t lo, uint64_t hi, int op,
+                       uint64_t mask, uint64_t value, uint64_t* out, uint64_t* count) {
+  uint64_t r = (op == 1) ? ~0ull : 0, c = 0;
+  if (lo < hi) {
+    size_t i = lower_bound_u64(S, n, lo), j = lower_bound_u64(S, n, hi);
+    for (size_t t = i; t < j; t++) {
+      const uint64_t x = S[t];
+      if ((x & mask) != value) continue;
+      c++;
+      if (op == 0) r += x;
+      else if (op == 1) r = x < r ? x : r;
+      else if (op == 2) r = x > r ? x : r;
+      else r ^= x;
+    }
+  }
+  *out = r;
+  *count = c;
+}
+
 /* ------------------------------------------------------------------------ */
 /* 2. Codec (R1, R2)                                                        */
 /* ------------------------------------------------------------------------ */

@@ -395,3 +395,59 @@ def test_bytes_per_key_sanity_band():
     o = oracle.SeqCPMA(W.uniform_keys(9, 10 ** 6), leaf_bytes=512, **CFG)
     bpk = o.bytes() / o.size()
     assert 3.0 < bpk < 8.0
+
+
+# --------------------------------------------------------------------------
+# map_range_length and filtered range reductions, by brute force
+# --------------------------------------------------------------------------
+
+def test_range_length_brute_force():
+    """App. A map_range_length(start, length): the function sees at most
+    `length` elements, the first ones with key >= start."""
+    rng = random.Random(7)
+    S = sorted(set(rng.getrandbits(16) for _ in range(2000)) | {0, M64, M64 - 1})
+    plain = oracle.PlainSet(S)
+    starts = [rng.getrandbits(16) for _ in range(200)] + [0, 1, M64, M64 - 1, S[-3], S[5]]
+    lens = [rng.choice([0, 1, 2, 7, 100, 5000, M64]) for _ in range(200)] + [3, M64, 1, 5, 2, 0]
+    want = []
+    for a, ln in zip(starts, lens):
+        sel = [x for x in S if x >= a][: min(ln, len(S))]
+        want.append((sum(sel) & M64, len(sel)))
+    s, c = plain.range_map_length(starts, lens)
+    assert [(int(x), int(y)) for x, y in zip(s, c)] == want
+    # length 1 gives the successor (the PMA search of Sec. 3)
+    s, c = plain.range_map_length([S[10] + 1], [1])
+    assert int(c[0]) == 1 and int(s[0]) == S[11]
+    # everything: the sum of the whole set
+    s, c = plain.range_map_length([0], [M64])
+    assert int(s[0]) == sum(S) & M64 and int(c[0]) == len(S)
+
+
+@pytest.mark.parametrize("op", ["sum", "min", "max", "xor"])
+def test_range_reduce_brute_force(op):
+    rng = random.Random(11)
+    S = sorted(set(rng.getrandbits(18) for _ in range(3000)) | {0, M64 - 1})
+    plain = oracle.PlainSet(S)
+    lo = [rng.getrandbits(18) for _ in range(120)] + [0, 0, 9, M64]
+    hi = [a + rng.getrandbits(rng.choice([3, 10, 17])) for a in lo[:120]] + [M64, 1, 9, M64]
+    for mask, value in [(0, 0), (1, 1), (0xF, 0x5), (1 << 17, 0)]:
+        want = []
+        for a, b in zip(lo, hi):
+            sel = [x for x in S if a <= x < b and (x & mask) == value]
+            if op == "sum":
+                r = sum(sel) & M64
+            elif op == "min":
+                r = min(sel) if sel else M64
+            elif op == "max":
+                r = max(sel) if sel else 0
+            else:
+                r = 0
+                for x in sel:
+                    r ^= x
+            want.append((r, len(sel)))
+        r, c = plain.range_reduce(lo, hi, op, mask, value)
+        assert [(int(x), int(y)) for x, y in zip(r, c)] == want
+    # the unfiltered sum is range_map
+    r, c = plain.range_reduce(lo, hi, "sum")
+    s2, c2 = plain.range_map(lo, hi)
+    assert np.array_equal(r, s2) and np.array_equal(c, c2)
