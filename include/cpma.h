@@ -151,6 +151,36 @@ int cpma_range_map(const cpma_t* h, const uint64_t* d_lo, const uint64_t* d_hi,
                    uint64_t q, uint64_t* d_sum, uint64_t* d_count,
                    cpma_stream_t stream);
 
+/* App. A map_range_length(f, start, length) with f = (sum, count), batched:
+ * for every i < q, the first min(d_length[i], #keys >= d_start[i]) keys that
+ * are >= d_start[i]; d_sum[i] = their sum modulo 2^64, d_count[i] = how many
+ * (all device uint64 arrays of q entries).  Length 1 gives the successor of
+ * start (Sec. 3 search); start 0 and length 1 the minimum.  One prefix sum of
+ * the leaves' element counts per call turns every query into a range of
+ * global ranks; the ranks then run through the same load-balanced leaf walk
+ * as cpma_range_map.  Errors: CPMA_EINVAL (null handle or array with q > 0),
+ * CPMA_ENOMEM (scratch). */
+int cpma_range_map_length(const cpma_t* h, const uint64_t* d_start,
+                          const uint64_t* d_length, uint64_t q, uint64_t* d_sum,
+                          uint64_t* d_count, cpma_stream_t stream);
+
+/* Functions for cpma_range_reduce. */
+#define CPMA_OP_SUM 0 /* sum modulo 2^64; 0 when no key passes */
+#define CPMA_OP_MIN 1 /* smallest key; 2^64-1 when no key passes */
+#define CPMA_OP_MAX 2 /* largest key; 0 when no key passes */
+#define CPMA_OP_XOR 3 /* exclusive or; 0 when no key passes */
+
+/* Sec. 3 range_map(start, end, f) with f one of the CPMA_OP_* reductions over
+ * a filter, batched: for every i < q, over the keys x with d_lo[i] <= x <
+ * d_hi[i] and (x & mask) == value, d_out[i] = the reduction and d_count[i] =
+ * how many keys passed (so mask/value filters give filter-counts).  Every
+ * covered leaf is decoded; with CPMA_OP_SUM and mask = value = 0 this is
+ * cpma_range_map.  Errors: CPMA_EINVAL (null handle or array with q > 0, op
+ * not a CPMA_OP_*), CPMA_ENOMEM. */
+int cpma_range_reduce(const cpma_t* h, const uint64_t* d_lo, const uint64_t* d_hi,
+                      uint64_t q, int op, uint64_t mask, uint64_t value,
+                      uint64_t* d_out, uint64_t* d_count, cpma_stream_t stream);
+
 /* cpma_range_map without any device allocation (the paper has no counterpart:
  * this is a deployment variant).  cpma_range_map grows private scratch with
  * cudaMalloc/cudaFree when a larger batch of queries arrives; some callers

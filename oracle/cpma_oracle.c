@@ -44,7 +44,9 @@
  *   R5 routing (Sec. 4 batch merge search, Sec. 5 point queries): a key goes
  *      to the last leaf whose head-index entry is <= key, else leaf 0; an
  *      empty leaf's head-index entry is the head of the next non-empty leaf,
- *      or 2^64-1 if there is none.
+ *      or 2^64-1 if there is none.  The key 2^64-1 goes to the last
+ *      non-empty leaf (else leaf 0): every entry is <= it, and empty leaves
+ *      after the last non-empty one must not take it.
  *   R6 merge (Sec. 4 batch-merge phase): each routed leaf becomes content
  *      union slice (insert) or content minus slice (delete); a leaf is
  *      "touched" when its content changed.
@@ -372,6 +374,11 @@ static void fix_empty_heads(ocpma* o) {
 }
 
 static uint64_t route(const ocpma* o, uint64_t x) {
+  if (x == UINT64_MAX) {
+    for (uint64_t j = o->L; j-- > 0;)
+      if (o->used[j]) return j;
+    return 0;
+  }
   /* number of entries <= x, minus one, floored at 0 */
   uint64_t lo = 0, hi = o->L;
   while (lo < hi) {

@@ -76,6 +76,8 @@ def lib():
                 "cpma_profile": (I, [V, I]),
                 "cpma_profile_read": (I, [V, C.POINTER(C.c_double), P64, P64, I]),
                 "cpma_reserve": (I, [V, U64, U64, I, V]),
+                "cpma_range_map_length": (I, [V, V, V, U64, V, V, V]),
+                "cpma_range_reduce": (I, [V, V, V, U64, I, U64, U64, V, V, V]),
                 "cpma_use_graphs": (I, [V, U64]),
                 "cpma_graph_stats": (I, [V, P64, P64]),
             }
@@ -226,6 +228,45 @@ def cpma_range_map(h, lo, hi, out_sum=None, out_count=None, stream=None):
 RANGE_NOALLOC_MAX_QUERIES = 65536
 
 
+def cpma_range_map_length(h, start, length, out_sum=None, out_count=None, stream=None):
+    """App. A map_range_length with (sum, count): the first length[i] keys >=
+    start[i] (length may be a scalar)."""
+    start = _keys(start, "start")
+    if not torch.is_tensor(length):
+        length = torch.full_like(start, int(np.uint64(length).view(np.int64)))
+    length = _keys(length, "length")
+    if length.numel() != start.numel():
+        raise ValueError("start and length differ in size")
+    q = start.numel()
+    s = out_sum if out_sum is not None else torch.empty(q, dtype=torch.int64, device=start.device)
+    c = out_count if out_count is not None else torch.empty(q, dtype=torch.int64,
+                                                            device=start.device)
+    _check(lib().cpma_range_map_length(h, _ptr(start), _ptr(length), q, _ptr(s), _ptr(c),
+                                       C.c_void_p(_stream(stream))), "cpma_range_map_length")
+    return s, c
+
+
+OPS = {"sum": 0, "min": 1, "max": 2, "xor": 3}
+
+
+def cpma_range_reduce(h, lo, hi, op="sum", mask=0, value=0, out=None, out_count=None,
+                      stream=None):
+    """range_map with min / max / xor / sum over the keys of [lo, hi) whose
+    bits under mask equal value; returns (results, counts)."""
+    lo, hi = _keys(lo, "lo"), _keys(hi, "hi")
+    if lo.numel() != hi.numel():
+        raise ValueError("lo and hi differ in size")
+    q = lo.numel()
+    r = out if out is not None else torch.empty(q, dtype=torch.int64, device=lo.device)
+    c = out_count if out_count is not None else torch.empty(q, dtype=torch.int64,
+                                                            device=lo.device)
+    _check(lib().cpma_range_reduce(h, _ptr(lo), _ptr(hi), q, OPS[op] if isinstance(op, str)
+                                   else int(op), C.c_uint64(int(mask)), C.c_uint64(int(value)),
+                                   _ptr(r), _ptr(c), C.c_void_p(_stream(stream))),
+           "cpma_range_reduce")
+    return r, c
+
+
 def cpma_range_map_noalloc(h, lo, hi, out_sum, out_count, stream=None):
     """cpma_range_map with no device allocation inside the call: the caller
     passes the output buffers, the library uses its fixed scratch array."""
@@ -359,6 +400,12 @@ class CPMA:
 
     def range_map(self, lo, hi, stream=None):
         return cpma_range_map(self._h, lo, hi, None, None, stream)
+
+    def range_map_length(self, start, length, stream=None):
+        return cpma_range_map_length(self._h, start, length, stream=stream)
+
+    def range_reduce(self, lo, hi, op="sum", mask=0, value=0, stream=None):
+        return cpma_range_reduce(self._h, lo, hi, op, mask, value, stream=stream)
 
     def sum(self, stream=None):
         return cpma_sum(self._h, stream)

@@ -148,7 +148,7 @@ void release_all(cpma* h) {
                  &s.T_newbytes, &s.T_state, &s.viol, &s.list_lane, &s.list_v1, &s.list_gen, &s.cand, &s.wins, &s.bits, &s.prefix, &s.ovf,
                  &s.E, &s.cost, &s.C, &s.srccnt, &s.srcoff, &s.dstart, &s.win_src, &s.win_dst,
                  &s.win_leaf_off, &s.win_elem_off, &s.win_dst_off, &s.partials, &s.partials_q, &s.q_first,
-                 &s.q_items, &s.q_off, &s.stage})
+                 &s.q_items, &s.q_off, &s.stage, &s.q_lo, &s.q_hi, &s.q_rank})
     release(*b);
   graph_cache_free(h);
   cudaFree(h->data);
@@ -270,7 +270,8 @@ int cpma_clone(const cpma_t* src, cpma_t** out, cpma_stream_t stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const uint64_t L = src->L, LB = src->cfg.leaf_bytes;
   if (cudaMalloc(&h->data, L * LB) != cudaSuccess || cudaMalloc(&h->used, L * 4) != cudaSuccess ||
-      cudaMalloc(&h->cnt, L * 4) != cudaSuccess || cudaMalloc(&h->heads, L * 8) != cudaSuccess) {
+      cudaMalloc(&h->cnt, L * 4) != cudaSuccess ||
+      cudaMalloc(&h->heads, (L + 1) * 8) != cudaSuccess) {
     cudaGetLastError();
     release_all(h);
     delete h;
@@ -280,7 +281,8 @@ int cpma_clone(const cpma_t* src, cpma_t** out, cpma_stream_t stream) {
   rc |= check_cuda(cudaMemcpyAsync(h->data, src->data, L * LB, cudaMemcpyDeviceToDevice, st));
   rc |= check_cuda(cudaMemcpyAsync(h->used, src->used, L * 4, cudaMemcpyDeviceToDevice, st));
   rc |= check_cuda(cudaMemcpyAsync(h->cnt, src->cnt, L * 4, cudaMemcpyDeviceToDevice, st));
-  rc |= check_cuda(cudaMemcpyAsync(h->heads, src->heads, L * 8, cudaMemcpyDeviceToDevice, st));
+  rc |= check_cuda(cudaMemcpyAsync(h->heads, src->heads, (L + 1) * 8, cudaMemcpyDeviceToDevice,
+                                   st));
   rc |= check_cuda(cudaMemcpyAsync(&h->d_status->empties, &src->d_status->empties, 8,
                                    cudaMemcpyDeviceToDevice, st));
   if (rc != CPMA_OK) {
@@ -348,6 +350,21 @@ int cpma_range_map(const cpma_t* h, const uint64_t* d_lo, const uint64_t* d_hi, 
                    uint64_t* d_sum, uint64_t* d_count, cpma_stream_t stream) {
   if (!h || (q && (!d_lo || !d_hi || !d_sum || !d_count))) return CPMA_EINVAL;
   return run_range(h, d_lo, d_hi, q, d_sum, d_count, (cudaStream_t)stream);
+}
+
+int cpma_range_map_length(const cpma_t* h, const uint64_t* d_start, const uint64_t* d_length,
+                          uint64_t q, uint64_t* d_sum, uint64_t* d_count, cpma_stream_t stream) {
+  if (!h || (q && (!d_start || !d_length || !d_sum || !d_count))) return CPMA_EINVAL;
+  return run_range_length(h, d_start, d_length, q, d_sum, d_count, (cudaStream_t)stream);
+}
+
+int cpma_range_reduce(const cpma_t* h, const uint64_t* d_lo, const uint64_t* d_hi, uint64_t q,
+                      int op, uint64_t mask, uint64_t value, uint64_t* d_out, uint64_t* d_count,
+                      cpma_stream_t stream) {
+  if (!h || (q && (!d_lo || !d_hi || !d_out || !d_count))) return CPMA_EINVAL;
+  if (op < CPMA_OP_SUM || op > CPMA_OP_XOR) return CPMA_EINVAL;
+  return run_range_reduce(h, d_lo, d_hi, q, op, mask, value, d_out, d_count,
+                          (cudaStream_t)stream);
 }
 
 int cpma_range_map_noalloc(const cpma_t* h, const uint64_t* d_lo, const uint64_t* d_hi,

@@ -80,9 +80,13 @@ __device__ __forceinline__ uint64_t upper_count(const uint64_t* __restrict__ a, 
 }
 
 // Routing (Sec. 4 batch merge search, Sec. 5 point queries): the last leaf
-// whose head-index entry is <= x, else leaf 0.
+// whose head-index entry is <= x, else leaf 0.  Every entry is <= 2^64-1, so
+// that key instead goes to the last non-empty leaf, whose index the head
+// array keeps in its extra entry heads[L] (empty leaves after it must not
+// take the key).
 __device__ __forceinline__ uint64_t route_leaf(const uint64_t* __restrict__ heads, uint64_t L,
                                                uint64_t x) {
+  if (x == KEY_MAX) return heads[L];
   uint64_t c = upper_count(heads, L, x);
   return c ? c - 1 : 0;
 }

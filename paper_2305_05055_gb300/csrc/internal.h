@@ -77,6 +77,7 @@ struct Scratch {
   Buf partials_q;         // scan partials of the query path, which may run
                           // on another stream while an update sorts
   Buf q_first, q_items, q_off; // range queries
+  Buf q_lo, q_hi, q_rank;       // map_range_length: rank bounds, leaf-count prefix
   Buf stage;              // padded batch of a graph-launched update
 };
 
@@ -113,7 +114,7 @@ struct cpma {
   uint8_t* data = nullptr;
   uint32_t* used = nullptr;
   uint32_t* cnt = nullptr;
-  uint64_t* heads = nullptr;
+  uint64_t* heads = nullptr;       // L + 1 entries; heads[L] = last non-empty leaf
   uint64_t bits_words = 0;          // words of the window bitsets now zeroed
   bool may_have_empty = false;      // some leaf may be empty (head fix-up)
   cpmaimpl::Status* d_status = nullptr;
@@ -150,6 +151,7 @@ int scan_u64(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host, const 
              cudaStream_t st);
 // scan_u64 with the query path's own partials buffer
 int scan_u64_query(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
+int scan_u32_query(cpma* h, const uint32_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
 // Same as scan_u64 for a host-known count, with caller-provided partials
 // (partials_cap entries); it never allocates.
 int scan_u64_given_partials(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host,
@@ -181,6 +183,11 @@ int run_has(const cpma* h, const uint64_t* d_keys, uint64_t q, uint8_t* d_out, c
 int run_range(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q, uint64_t* sum,
               uint64_t* count, cudaStream_t st);
 int run_sum(const cpma* h, uint64_t* sum, uint64_t* count, cudaStream_t st);
+int run_range_length(const cpma* h, const uint64_t* start, const uint64_t* length, uint64_t q,
+                     uint64_t* sum, uint64_t* count, cudaStream_t st);
+int run_range_reduce(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q, int op,
+                     uint64_t mask, uint64_t value, uint64_t* out, uint64_t* count,
+                     cudaStream_t st);
 int run_range_noalloc(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q,
                       uint64_t* sum, uint64_t* count, cudaStream_t st);
 

@@ -10,6 +10,14 @@
 //    sums while it stays on one query and adds them atomically when it
 //    leaves it (addition mod 2^64 is associative, so the order is free).
 //  sum (App. A sum()): every leaf once.
+//  map_range_length (App. A: f on at most `length` elements from the first
+//    key >= start): a prefix sum of the leaves' element counts turns each
+//    query into a range of global ranks [r0, r1); the same load-balanced
+//    walk then sums whole leaves inside it and filters the two end leaves by
+//    rank instead of by key.
+//  range_reduce (Sec. 3 range_map with other functions): min, max, xor or
+//    sum of the keys of [lo, hi) whose masked bits match a value, with the
+//    count of those keys; every covered leaf is decoded.
 #include <algorithm>
 #include <mutex>
 
@@ -121,27 +129,6 @@ __global__ void __launch_bounds__(kT) k_has(const uint64_t* __restrict__ keys, u
   if (prof && lane == 0 && nbytes) atomicAdd(prof, nbytes);
 }
 
-__global__ void __launch_bounds__(kT) k_range_prep(const uint64_t* __restrict__ lo,
-                                                   const uint64_t* __restrict__ hi, uint64_t q,
-                                                   const uint64_t* __restrict__ heads, uint64_t L,
-                                                   uint64_t* __restrict__ first,
-                                                   uint64_t* __restrict__ items,
-                                                   uint64_t* __restrict__ sum,
-                                                   uint64_t* __restrict__ count) {
-  for (uint64_t i = gtid(); i < q; i += gstride()) {
-    const uint64_t a = lo[i], b = hi[i];
-    uint64_t fl = 0, n = 0;
-    if (a < b) {
-      fl = route_leaf(heads, L, a);
-      n = route_leaf(heads, L, b - 1) - fl + 1;
-    }
-    first[i] = fl;
-    items[i] = n;
-    sum[i] = 0;
-    count[i] = 0;
-  }
-}
-
 struct RangeArgs {
   const uint64_t* lo;
   const uint64_t* hi;
@@ -155,8 +142,141 @@ struct RangeArgs {
   uint64_t* sum;
   uint64_t* count;
   ull* prof;  // profiling: leaf bytes scanned (nullable)
+  const uint64_t* P = nullptr;  // rank mode: elements before each leaf (L + 1)
 };
 
+__global__ void __launch_bounds__(kT) k_range_prep(const uint64_t* __restrict__ lo,
+                                                   const uint64_t* __restrict__ hi, uint64_t q,
+                                                   const uint64_t* __restrict__ heads, uint64_t L,
+                                                   uint64_t* __restrict__ first,
+                                                   uint64_t* __restrict__ items,
+                                                   uint64_t* __restrict__ sum,
+                                                   uint64_t* __restrict__ count,
+                                                   uint64_t init = 0) {
+  for (uint64_t i = gtid(); i < q; i += gstride()) {
+    const uint64_t a = lo[i], b = hi[i];
+    uint64_t fl = 0, n = 0;
+    if (a < b) {
+      fl = route_leaf(heads, L, a);
+      n = route_leaf(heads, L, b - 1) - fl + 1;
+    }
+    first[i] = fl;
+    items[i] = n;
+    sum[i] = init;
+    count[i] = 0;
+  }
+}
+
+// map_range_length, step 1 (warp per query): rank r0 of the first key >=
+// start (elements before its leaf + elements of the leaf below start),
+// r1 = min(r0 + length, n), and the leaves holding ranks r0 .. r1-1.
+__global__ void __launch_bounds__(kT) k_len_prep(const uint64_t* __restrict__ start,
+                                                 const uint64_t* __restrict__ length, uint64_t q,
+                                                 const uint64_t* __restrict__ heads,
+                                                 const uint8_t* __restrict__ data,
+                                                 const uint32_t* __restrict__ used, uint64_t L,
+                                                 uint32_t LB, const uint64_t* __restrict__ P,
+                                                 uint64_t* __restrict__ r0o,
+                                                 uint64_t* __restrict__ r1o,
+                                                 uint64_t* __restrict__ first,
+                                                 uint64_t* __restrict__ items,
+                                                 uint64_t* __restrict__ sum,
+                                                 uint64_t* __restrict__ count) {
+  const unsigned lane = lane_id();
+  const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
+  const uint64_t n = P[L];
+  for (uint64_t i = gw; i < q; i += nw) {
+    const uint64_t x = start[i];
+    const uint64_t j0 = route_leaf(heads, L, x);
+    uint32_t below = 0;
+    warp_decode(data + j0 * LB, min(used[j0], LB), [&](uint32_t, uint64_t v) { below += v < x; });
+    below = warp_sum(below);
+    const uint64_t r0 = P[j0] + below;
+    const uint64_t len = length[i];
+    const uint64_t r1 = (len >= n - r0) ? n : r0 + len;
+    uint64_t f = 0, it = 0;
+    if (r1 > r0) {
+      f = upper_count(P, L + 1, r0) - 1;
+      it = upper_count(P, L + 1, r1 - 1) - f;
+    }
+    if (lane == 0) {
+      r0o[i] = r0;
+      r1o[i] = r1;
+      first[i] = f;
+      items[i] = it;
+      sum[i] = 0;
+      count[i] = 0;
+    }
+  }
+}
+
+// range_reduce: the functions, their identities and their atomics
+template <int OP>
+__device__ __forceinline__ uint64_t op_apply(uint64_t a, uint64_t b) {
+  if constexpr (OP == CPMA_OP_SUM) return a + b;
+  else if constexpr (OP == CPMA_OP_MIN) return a < b ? a : b;
+  else if constexpr (OP == CPMA_OP_MAX) return a > b ? a : b;
+  else return a ^ b;
+}
+template <int OP>
+__host__ __device__ __forceinline__ uint64_t op_identity() {
+  return OP == CPMA_OP_MIN ? ~0ull : 0ull;
+}
+template <int OP>
+__device__ __forceinline__ void op_atomic(uint64_t* p, uint64_t v) {
+  if constexpr (OP == CPMA_OP_SUM) atomicAdd((ull*)p, (ull)v);
+  else if constexpr (OP == CPMA_OP_MIN) atomicMin((ull*)p, (ull)v);
+  else if constexpr (OP == CPMA_OP_MAX) atomicMax((ull*)p, (ull)v);
+  else atomicXor((ull*)p, (ull)v);
+}
+
+// Same load-balanced (query, leaf) walk as k_range; every covered leaf is
+// decoded and its keys filtered by range and mask.
+template <int OP>
+__global__ void __launch_bounds__(kT) k_range_reduce(RangeArgs a, uint64_t mask,
+                                                     uint64_t value) {
+  const unsigned lane = lane_id();
+  const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
+  const uint64_t N = a.off[a.q];
+  const uint64_t g0 = N * gw / nw, g1 = N * (gw + 1) / nw;
+  if (g0 >= g1) return;
+  uint64_t qi = upper_count(a.off, a.q + 1, g0) - 1;
+  uint64_t r = op_identity<OP>(), c = 0;
+  uint64_t qend = a.off[qi + 1];
+  uint64_t lo = a.lo[qi], hi = a.hi[qi], fl = a.first[qi], qoff = a.off[qi];
+  for (uint64_t g = g0; g < g1; g++) {
+    while (g >= qend) {
+#pragma unroll
+      for (int o = 16; o; o >>= 1) r = op_apply<OP>(r, __shfl_xor_sync(FULL, r, o));
+      c = warp_sum(c);
+      if (lane == 0 && c) {
+        op_atomic<OP>(&a.sum[qi], r);
+        atomicAdd((ull*)&a.count[qi], (ull)c);
+      }
+      r = op_identity<OP>();
+      c = 0;
+      qi++;
+      qend = a.off[qi + 1];
+      lo = a.lo[qi]; hi = a.hi[qi]; fl = a.first[qi]; qoff = a.off[qi];
+    }
+    const uint64_t j = fl + (g - qoff);
+    warp_decode(a.data + j * a.LB, min(a.used[j], a.LB), [&](uint32_t, uint64_t v) {
+      if (v >= lo && v < hi && (v & mask) == value) { r = op_apply<OP>(r, v); c++; }
+    });
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) r = op_apply<OP>(r, __shfl_xor_sync(FULL, r, o));
+  c = warp_sum(c);
+  if (lane == 0 && c) {
+    op_atomic<OP>(&a.sum[qi], r);
+    atomicAdd((ull*)&a.count[qi], (ull)c);
+  }
+}
+
+
+// RANK: lo/hi of a query are global element ranks [r0, r1) and the end
+// leaves filter by rank P[j] + index; otherwise they are keys.
+template <bool RANK>
 __global__ void __launch_bounds__(kT) k_range(RangeArgs a) {
   const unsigned lane = lane_id();
   const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
@@ -196,9 +316,16 @@ __global__ void __launch_bounds__(kT) k_range(RangeArgs a) {
     const uint64_t j = fl + li;
     const uint32_t u = min(a.used[j], a.LB);
     nbytes += u;
-    warp_decode(a.data + j * a.LB, u, [&](uint32_t, uint64_t v) {
-      if (v >= lo && v < hi) { s += v; c++; }
-    });
+    if constexpr (RANK) {
+      const uint64_t r = a.P[j];
+      warp_decode(a.data + j * a.LB, u, [&](uint32_t idx, uint64_t v) {
+        if (r + idx >= lo && r + idx < hi) { s += v; c++; }
+      });
+    } else {
+      warp_decode(a.data + j * a.LB, u, [&](uint32_t, uint64_t v) {
+        if (v >= lo && v < hi) { s += v; c++; }
+      });
+    }
     g++;
   }
   s = warp_sum(s);
@@ -314,7 +441,109 @@ int run_range(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q,
   a.count = count;
   a.prof = prof_bytes(h, PH_RANGE);
   prof_begin(h, PH_RANGE, st);
-  k_range<<<persistent_grid(h), kT, 0, st>>>(a);
+  k_range<false><<<persistent_grid(h), kT, 0, st>>>(a);
+  CPMA_LAUNCHED(h);
+  prof_end(h, st);
+  return check_cuda(cudaGetLastError());
+}
+
+int run_range_length(const cpma* h, const uint64_t* start, const uint64_t* length, uint64_t q,
+                     uint64_t* sum, uint64_t* count, cudaStream_t st) {
+  if (q == 0) return CPMA_OK;
+  cpma* hm = const_cast<cpma*>(h);
+  Scratch& s = hm->s;
+  CPMA_TRY(ensure(s.q_first, q * 8));
+  CPMA_TRY(ensure(s.q_items, q * 8));
+  CPMA_TRY(ensure(s.q_off, (q + 1) * 8));
+  CPMA_TRY(ensure(s.q_lo, q * 8));
+  CPMA_TRY(ensure(s.q_hi, q * 8));
+  CPMA_TRY(ensure(s.q_rank, (h->L + 1) * 8));
+  uint64_t* P = (uint64_t*)s.q_rank.p;
+  uint64_t* r0 = (uint64_t*)s.q_lo.p;
+  uint64_t* r1 = (uint64_t*)s.q_hi.p;
+  uint64_t* first = (uint64_t*)s.q_first.p;
+  uint64_t* items = (uint64_t*)s.q_items.p;
+  uint64_t* off = (uint64_t*)s.q_off.p;
+  prof_begin(h, PH_RANGE_PREP, st);
+  prof_add_bytes(h, PH_RANGE_PREP, 12ull * h->L + 88ull * q);
+  CPMA_TRY(scan_u32_query(hm, h->cnt, P, h->L, st));
+  const int g1 = (int)std::max<uint64_t>(
+      1, std::min<uint64_t>((q * 32 + kT - 1) / kT, (uint64_t)h->num_sms * 16));
+  k_len_prep<<<g1, kT, 0, st>>>(start, length, q, h->heads, h->data, h->used, h->L,
+                                h->cfg.leaf_bytes, P, r0, r1, first, items, sum, count);
+  CPMA_LAUNCHED(h);
+  CPMA_TRY(scan_u64_query(hm, items, off, q, st));
+  prof_end(h, st);
+  RangeArgs a;
+  a.lo = r0;
+  a.hi = r1;
+  a.q = q;
+  a.first = first;
+  a.off = off;
+  a.data = h->data;
+  a.used = h->used;
+  a.cnt = h->cnt;
+  a.LB = h->cfg.leaf_bytes;
+  a.sum = sum;
+  a.count = count;
+  a.prof = prof_bytes(h, PH_RANGE);
+  a.P = P;
+  prof_begin(h, PH_RANGE, st);
+  k_range<true><<<persistent_grid(h), kT, 0, st>>>(a);
+  CPMA_LAUNCHED(h);
+  prof_end(h, st);
+  return check_cuda(cudaGetLastError());
+}
+
+int run_range_reduce(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q, int op,
+                     uint64_t mask, uint64_t value, uint64_t* out, uint64_t* count,
+                     cudaStream_t st) {
+  if (op == CPMA_OP_SUM && mask == 0 && value == 0)
+    return run_range(h, lo, hi, q, out, count, st);
+  if (q == 0) return CPMA_OK;
+  cpma* hm = const_cast<cpma*>(h);
+  CPMA_TRY(ensure(hm->s.q_first, q * 8));
+  CPMA_TRY(ensure(hm->s.q_items, q * 8));
+  CPMA_TRY(ensure(hm->s.q_off, (q + 1) * 8));
+  uint64_t* first = (uint64_t*)hm->s.q_first.p;
+  uint64_t* items = (uint64_t*)hm->s.q_items.p;
+  uint64_t* off = (uint64_t*)hm->s.q_off.p;
+  const int g1 = (int)std::max<uint64_t>(
+      1, std::min<uint64_t>((q + kT - 1) / kT, (uint64_t)h->num_sms * 8));
+  uint64_t init = 0;
+  switch (op) {
+    case CPMA_OP_SUM: init = op_identity<CPMA_OP_SUM>(); break;
+    case CPMA_OP_MIN: init = op_identity<CPMA_OP_MIN>(); break;
+    case CPMA_OP_MAX: init = op_identity<CPMA_OP_MAX>(); break;
+    case CPMA_OP_XOR: init = op_identity<CPMA_OP_XOR>(); break;
+    default: return CPMA_EINVAL;
+  }
+  prof_begin(h, PH_RANGE_PREP, st);
+  k_range_prep<<<g1, kT, 0, st>>>(lo, hi, q, h->heads, h->L, first, items, out, count, init);
+  CPMA_LAUNCHED(h);
+  CPMA_TRY(scan_u64_query(hm, items, off, q, st));
+  prof_end(h, st);
+  RangeArgs a;
+  a.lo = lo;
+  a.hi = hi;
+  a.q = q;
+  a.first = first;
+  a.off = off;
+  a.data = h->data;
+  a.used = h->used;
+  a.cnt = h->cnt;
+  a.LB = h->cfg.leaf_bytes;
+  a.sum = out;
+  a.count = count;
+  a.prof = nullptr;
+  prof_begin(h, PH_RANGE, st);
+  const int G = persistent_grid(h);
+  switch (op) {
+    case CPMA_OP_SUM: k_range_reduce<CPMA_OP_SUM><<<G, kT, 0, st>>>(a, mask, value); break;
+    case CPMA_OP_MIN: k_range_reduce<CPMA_OP_MIN><<<G, kT, 0, st>>>(a, mask, value); break;
+    case CPMA_OP_MAX: k_range_reduce<CPMA_OP_MAX><<<G, kT, 0, st>>>(a, mask, value); break;
+    default: k_range_reduce<CPMA_OP_XOR><<<G, kT, 0, st>>>(a, mask, value); break;
+  }
   CPMA_LAUNCHED(h);
   prof_end(h, st);
   return check_cuda(cudaGetLastError());
@@ -355,7 +584,7 @@ int run_range_noalloc(const cpma* h, const uint64_t* lo, const uint64_t* hi, uin
   a.sum = sum;
   a.count = count;
   a.prof = nullptr;
-  k_range<<<persistent_grid(h), kT, 0, st>>>(a);
+  k_range<false><<<persistent_grid(h), kT, 0, st>>>(a);
   CPMA_LAUNCHED(h);
   return check_cuda(cudaGetLastError());
 }

@@ -155,6 +155,9 @@ int scan_u64(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host, const 
 int scan_u64_query(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t st) {
   return scan_impl<uint64_t>(h, in, out, n, nullptr, st, &h->s.partials_q);
 }
+int scan_u32_query(cpma* h, const uint32_t* in, uint64_t* out, uint64_t n, cudaStream_t st) {
+  return scan_impl<uint32_t>(h, in, out, n, nullptr, st, &h->s.partials_q);
+}
 
 int scan_u64_given_partials(cpma* h, const uint64_t* in, uint64_t* out, uint64_t n_host,
                             uint64_t* partials, uint64_t partials_cap, cudaStream_t st) {

@@ -1300,16 +1300,17 @@ __global__ void __launch_bounds__(1024) k_fix_heads(const uint32_t* __restrict__
                                                     uint64_t* __restrict__ heads, uint64_t L,
                                                     Status* st) {
   __shared__ uint64_t segmin[1024];
-  __shared__ ull empties;
-  if (threadIdx.x == 0) empties = 0;
+  __shared__ ull empties, last1;  // last1: 1 + index of the last non-empty leaf
+  if (threadIdx.x == 0) { empties = 0; last1 = 0; }
   const uint64_t seg = (L + 1023) / 1024;
   const uint64_t s0 = min(L, threadIdx.x * seg), s1 = min(L, s0 + seg);
   uint64_t first = KEY_MAX;
-  ull ne = 0;
+  ull ne = 0, l1 = 0;
   for (uint64_t j = s0; j < s1; j++) {
-    if (used[j]) { if (first == KEY_MAX) first = heads[j]; }
+    if (used[j]) { if (first == KEY_MAX) first = heads[j]; l1 = j + 1; }
     else ne++;
   }
+  if (l1) atomicMax(&last1, l1);
   segmin[threadIdx.x] = first;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1330,7 +1331,10 @@ __global__ void __launch_bounds__(1024) k_fix_heads(const uint32_t* __restrict__
   }
   atomicAdd(&empties, ne);
   __syncthreads();
-  if (threadIdx.x == 0) st->empties = empties;
+  if (threadIdx.x == 0) {
+    st->empties = empties;
+    heads[L] = last1 ? last1 - 1 : 0;  // routing of the key 2^64-1
+  }
 }
 
 __global__ void k_set_window(uint64_t* win_src, uint64_t* win_dst, uint64_t* leaf_off,
@@ -1397,7 +1401,8 @@ struct Arrays {
 int alloc_arrays(uint64_t L, uint32_t LB, Arrays* a) {
   *a = Arrays{nullptr, nullptr, nullptr, nullptr};
   if (cudaMalloc(&a->data, L * LB) != cudaSuccess || cudaMalloc(&a->used, L * 4) != cudaSuccess ||
-      cudaMalloc(&a->cnt, L * 4) != cudaSuccess || cudaMalloc(&a->heads, L * 8) != cudaSuccess) {
+      cudaMalloc(&a->cnt, L * 4) != cudaSuccess ||
+      cudaMalloc(&a->heads, (L + 1) * 8) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(a->data); cudaFree(a->used); cudaFree(a->cnt); cudaFree(a->heads);
     *a = Arrays{nullptr, nullptr, nullptr, nullptr};

@@ -306,3 +306,75 @@ def test_graphs_replay_within_a_bucket():
     assert g.graph_stats() == {"captures": 1, "launches": 6}
     s, c = g.sum()
     assert int(cp.to_u64(s)[0]) == p.sum() and int(c.item()) == len(p)
+
+
+def test_max_key_with_trailing_empty_leaf():
+    """Low lower bounds leave an empty leaf after the one holding 2^64-1; the
+    key must still route to the last non-empty leaf (has, insert, ranges)."""
+    keys = np.array([4 * i for i in range(3000)] + [M64], dtype=np.uint64)
+    cfg = dict(leaf_bytes=256, tau_leaf=900, tau_root=700, rho_leaf=5, rho_root=20)
+    g = cp.CPMA(T(keys), **cfg)
+    o = oracle.SeqCPMA(keys, **cfg)
+    p = oracle.PlainSet(keys)
+    dele = keys[2400:-1]
+    assert int(g.delete_batch(T(dele)).item()) == o.delete_batch(dele) == p.delete_batch(dele)
+    same_layout(g, o)
+    _, used, _ = o.layout()
+    assert used[-1] == 0 and used[-2] > 0
+    q = np.array([M64, M64 - 1, 0, 4 * 2399], dtype=np.uint64)
+    assert g.has_batch(T(q)).cpu().numpy().tolist() == p.has_batch(q).tolist() == [1, 0, 1, 1]
+    for k in ([M64], [M64 - 1, M64]):
+        k = np.array(k, dtype=np.uint64)
+        assert int(g.insert_batch(T(k)).item()) == o.insert_batch(k) == p.insert_batch(k)
+        same_layout(g, o)
+    same_queries(g, p, 31, 100)
+
+
+@pytest.mark.parametrize("LB", [256, 512, 2048])
+def test_range_map_length_matches_oracle(LB):
+    """App. A map_range_length: first `length` keys >= start, sum and count,
+    against the plain set; lengths from 0 to 2^64-1, starts below, inside,
+    between and above the keys, and after updates that empty leaves."""
+    base = W.uniform_keys(51, 60000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=LB)
+    p = oracle.PlainSet(base)
+    rng = np.random.default_rng(LB)
+    for step in range(3):
+        S = p.S
+        starts = np.concatenate([W.uniform_keys(60 + step, 2000, bits=40),
+                                 S[rng.integers(0, S.size, 500)],
+                                 S[rng.integers(0, S.size, 200)] + np.uint64(1),
+                                 np.array([0, 1, M64, M64 - 1, S[-1], S[0]], np.uint64)])
+        lens = np.concatenate([W.log_uniform_int(70 + step, starts.size - 6, 1, 10 ** 5)
+                               .astype(np.uint64),
+                               np.array([0, M64, 1, 5, 1, S.size + 3], np.uint64)])
+        lens[::97] = 0
+        lens[1::89] = M64
+        s, c = g.range_map_length(T(starts), T(lens))
+        ws, wc = p.range_map_length(starts, lens)
+        assert np.array_equal(cp.to_u64(c), wc)
+        assert np.array_equal(cp.to_u64(s), ws)
+        # then change the set: a big delete (leaves empty and get refilled)
+        dele = W.sample_present(S, 80 + step, S.size // 3)
+        assert int(g.delete_batch(T(dele)).item()) == p.delete_batch(dele)
+    # whole set, successor, empty set
+    s, c = g.range_map_length(T(np.array([0], np.uint64)), M64)
+    assert int(cp.to_u64(s)[0]) == p.sum() and int(c.item()) == len(p)
+    e = cp.CPMA(None, leaf_bytes=LB)
+    s, c = e.range_map_length(T(np.array([0, 5, M64], np.uint64)), 10)
+    assert cp.to_u64(s).tolist() == [0, 0, 0] and cp.to_u64(c).tolist() == [0, 0, 0]
+
+
+@pytest.mark.parametrize("op", ["sum", "min", "max", "xor"])
+def test_range_reduce_matches_oracle(op):
+    base = np.concatenate([W.uniform_keys(52, 80000, bits=40), np.array([0, M64 - 1], np.uint64)])
+    g = cp.CPMA(T(base), leaf_bytes=512)
+    p = oracle.PlainSet(base)
+    lo, hi, _ = W.range_queries_by_rank(p.S, 53, 1500, 1, 20000)
+    lo = np.concatenate([lo, np.array([0, 0, 5, M64, M64 - 1], np.uint64)])
+    hi = np.concatenate([hi, np.array([M64, 1, 5, M64, M64], np.uint64)])
+    for mask, value in [(0, 0), (1, 0), (0xFF, 0x3C), (1 << 39, 1 << 39)]:
+        r, c = g.range_reduce(T(lo), T(hi), op, mask, value)
+        wr, wc = p.range_reduce(lo, hi, op, mask, value)
+        assert np.array_equal(cp.to_u64(c), wc)
+        assert np.array_equal(cp.to_u64(r), wr)

@@ -451,3 +451,26 @@ def test_range_reduce_brute_force(op):
     r, c = plain.range_reduce(lo, hi, "sum")
     s2, c2 = plain.range_map(lo, hi)
     assert np.array_equal(r, s2) and np.array_equal(c, c2)
+
+
+def test_max_key_routes_to_last_nonempty_leaf():
+    """With low lower bounds a sparse window at the end of the array can be
+    redistributed so that its last leaf stays empty; every head-index entry is
+    <= 2^64-1, so that key must route to the last non-empty leaf, not to the
+    empty leaf after it (reading R5).  Found by comparing with the plain set."""
+    keys = np.array([4 * i for i in range(3000)] + [M64], dtype=np.uint64)
+    o = oracle.SeqCPMA(keys, leaf_bytes=256, tau_leaf=900, tau_root=700, rho_leaf=5,
+                       rho_root=20)
+    p = oracle.PlainSet(keys)
+    dele = keys[2400:-1]
+    assert o.delete_batch(dele) == p.delete_batch(dele)
+    _, used, _ = o.layout()
+    assert used[-1] == 0 and used[-2] > 0  # an empty leaf after the one holding 2^64-1
+    q = np.array([M64, M64 - 1, 0, 4 * 2399], dtype=np.uint64)
+    assert o.has_batch(q).tolist() == p.has_batch(q).tolist() == [1, 0, 1, 1]
+    assert o.insert_batch([M64]) == p.insert_batch([M64]) == 0
+    assert o.insert_batch([M64 - 1]) == p.insert_batch([M64 - 1]) == 1
+    assert o.elements().tolist() == p.S.tolist()
+    s, c = o.range_map([M64 - 1], [M64])
+    assert int(s[0]) == M64 - 1 and int(c[0]) == 1
+    assert o.check() == 0
