@@ -74,6 +74,7 @@ def lib():
                 "o_cut_points": (None, [u64p, S, U64, u64p]),
                 "ocpma_create": (I, [C.POINTER(V), U32, U32, U32, U32, U32, U32, U32, U32, u64p, U64]),
                 "ocpma_destroy": (None, [V]),
+                "ocpma_set_rebuild": (None, [V, U32]),
                 "ocpma_insert": (I, [V, u64p, U64, C.POINTER(U64)]),
                 "ocpma_delete": (I, [V, u64p, U64, C.POINTER(U64)]),
                 "ocpma_has": (I, [V, U64]),
@@ -260,7 +261,7 @@ class PlainSet:
 # --------------------------------------------------------------------------
 
 DEFAULTS = dict(leaf_bytes=512, tau_leaf=900, tau_root=700, rho_leaf=100,
-                rho_root=300, grow_num=6, grow_den=5, build_pm=500)
+                rho_root=300, grow_num=6, grow_den=5, build_pm=500, rebuild_pm=0)
 
 
 class OracleError(RuntimeError):
@@ -283,6 +284,8 @@ class SeqCPMA:
         if rc != 0:
             raise OracleError("ocpma_create failed: %d" % rc)
         self._h = h
+        if c.get("rebuild_pm"):
+            lib().ocpma_set_rebuild(h, int(c["rebuild_pm"]))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -275,6 +275,7 @@ typedef struct {
   uint32_t* used;  /* L */
   uint64_t* head;  /* L: head-index entry (R5) */
   uint64_t n;
+  uint32_t rebuild_pm; /* R14: 0 = never */
   /* diagnostics of the last batch, for invariant tests */
   uint64_t last_resized, last_nwindows, last_touched;
   uint64_t* last_win;   /* pairs (first leaf, leaf count) */
@@ -456,10 +457,48 @@ static size_t leaf_content(const ocpma* o, const touched_t* T, size_t nT,
   return o_leaf_decode(o->data + j * o->LB, o->used[j], out);
 }
 
+/* R14 (Sec. 4: for a batch of k >= n/10 keys the best strategy is to rebuild
+ * the whole structure by one merge): when rebuild_pm > 0 and
+ * 1000 k >= rebuild_pm n (k = the batch's length as given, n = keys before
+ * it), the new set S' = S union U (or S minus U) is built like the App. A
+ * constructor (R10, then R8 over all leaves). */
+void ocpma_set_rebuild(ocpma* o, uint32_t rebuild_pm) { o->rebuild_pm = rebuild_pm; }
+
+static int rebuild(ocpma* o, const uint64_t* keys, uint64_t k, int is_delete, uint64_t* delta) {
+  const uint32_t LB = o->LB;
+  uint64_t* S = (uint64_t*)malloc((o->n + 1) * sizeof(uint64_t));
+  size_t m = 0;
+  for (uint64_t j = 0; j < o->L; j++)
+    m += o_leaf_decode(o->data + j * LB, o->used[j], S + m);
+  uint64_t* U = (uint64_t*)malloc((k ? k : 1) * sizeof(uint64_t));
+  memcpy(U, keys, k * sizeof(uint64_t));
+  size_t ku = oset_sort_unique(U, k);
+  uint64_t* e = (uint64_t*)malloc((m + ku + 1) * sizeof(uint64_t));
+  size_t mn = is_delete ? oset_difference(S, m, U, ku, e) : oset_union(S, m, U, ku, e);
+  *delta = is_delete ? (uint64_t)(m - mn) : (uint64_t)(mn - m);
+  free(S);
+  free(U);
+  uint64_t L = o_build_leaves(o_leaf_bytes(e, mn), LB, o->build_pm);
+  uint8_t* d;
+  uint32_t* u;
+  uint64_t* h;
+  int rc = alloc_arrays(L, LB, &d, &u, &h);
+  if (rc == OK) rc = spread(d, u, h, LB, 0, L, e, mn);
+  free(e);
+  if (rc != OK) return rc;
+  free(o->data); free(o->used); free(o->head);
+  o->data = d; o->used = u; o->head = h; o->L = L; o->n = mn;
+  fix_empty_heads(o);
+  o->last_resized = 1; o->last_nwindows = 0; o->last_touched = 0;
+  return OK;
+}
+
 /* Sec. 4: one batch (insert when is_delete == 0).  Returns the number of keys
  * added or removed through *delta; the return value is OK or an error. */
 static int update(ocpma* o, const uint64_t* keys, uint64_t k, int is_delete,
                   uint64_t* delta) {
+  if (o->rebuild_pm && k && (u128)1000 * k >= (u128)o->rebuild_pm * o->n)
+    return rebuild(o, keys, k, is_delete, delta);
   const uint32_t LB = o->LB;
   const uint64_t L = o->L;
   const unsigned H = ceil_log2(L);

@@ -474,3 +474,39 @@ def test_max_key_routes_to_last_nonempty_leaf():
     s, c = o.range_map([M64 - 1], [M64])
     assert int(s[0]) == M64 - 1 and int(c[0]) == 1
     assert o.check() == 0
+
+
+def test_rebuild_rule():
+    """R14: a batch with 1000 k >= rebuild_pm n is applied by rebuilding: the
+    set is the plain union / difference and the layout is exactly the
+    constructor's over the new set; a batch just below the threshold takes
+    the merge path (same layout as rebuild_pm = 0)."""
+    rng = random.Random(3)
+    base = [rng.getrandbits(30) for _ in range(20000)]
+    n = len(set(base))
+    for is_del in (False, True):
+        o = oracle.SeqCPMA(base, leaf_bytes=256, rebuild_pm=100)
+        m = oracle.SeqCPMA(base, leaf_bytes=256)
+        p = oracle.PlainSet(base)
+        k_lo = (100 * n - 1) // 1000  # 1000 k < 100 n: merge
+        keys = sorted(p.S.tolist())[:k_lo] if is_del else [rng.getrandbits(30) for _ in range(k_lo)]
+        f = "delete_batch" if is_del else "insert_batch"
+        assert getattr(o, f)(keys) == getattr(m, f)(keys) == getattr(p, f)(keys)
+        assert o.last_batch()["resized"] == m.last_batch()["resized"]
+        for a, b in zip(o.layout(), m.layout()):
+            assert np.array_equal(a, b)
+        n2 = len(p)
+        k_hi = -(-100 * n2 // 1000)  # ceil: 1000 k >= 100 n: rebuild
+        keys = p.S.tolist()[::2][:k_hi] if is_del else [rng.getrandbits(30) for _ in range(k_hi)]
+        assert getattr(o, f)(keys) == getattr(p, f)(keys)
+        assert o.elements().tolist() == p.S.tolist()
+        fresh = oracle.SeqCPMA(p.S, leaf_bytes=256)
+        for a, b in zip(o.layout(), fresh.layout()):
+            assert np.array_equal(a, b)
+        assert o.leaves() == fresh.leaves() and o.bytes() == fresh.bytes()
+        assert o.check() == 0
+    # an empty set always rebuilds (n = 0), into the constructor's layout
+    e = oracle.SeqCPMA([], leaf_bytes=512, rebuild_pm=100)
+    assert e.insert_batch(base) == n
+    for a, b in zip(e.layout(), oracle.SeqCPMA(base, leaf_bytes=512).layout()):
+        assert np.array_equal(a, b)
