@@ -444,10 +444,18 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
         from paper_2305_05055_gb300 import autotune
         base = T(W.uniform_keys(2, int(a.n), bits=40))
         at = autotune.tune(base, S, batch=int(a.batch), queries=q)
+        rb = autotune.tune_rebuild(base)
         del base
-        out["autotune"] = {"best": at["best"], "best_by": at["best_by"],
-                           "candidates": [{k: (round(v, 4) if isinstance(v, float) else v)
-                                           for k, v in r.items()} for r in at["candidates"]]}
+        gr = autotune.tune_growth(dev=dev)
+        rnd = lambda rows: [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
+                            for r in rows]
+        out["autotune"] = {"best": dict(at["best"], rebuild_pm=rb["rebuild_pm"],
+                                        grow_num=gr["best"]["grow_num"],
+                                        grow_den=gr["best"]["grow_den"]),
+                           "best_by": at["best_by"], "candidates": rnd(at["candidates"]),
+                           "rebuild": rnd(rb["rows"]),
+                           "growth": dict(rows=rnd(gr["rows"]), n0=gr["n0"], batch=gr["batch"],
+                                          steps=gr["steps"])}
     del S
     # delete of present keys (the batches inserted by the timed steps)
     g.profile(True)

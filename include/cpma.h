@@ -63,7 +63,13 @@ enum {
  * rho_leaf <= rho_root < tau_root <= tau_leaf < 1000,
  * (1000 - tau_leaf) * leaf_bytes >= 20000 (a redistributed leaf then always
  * fits), grow_num > grow_den > 0, 8000 < build_pm * leaf_bytes,
- * build_pm <= tau_root. */
+ * build_pm <= tau_root.
+ * rebuild_pm (Sec. 4: a batch of k >= n/10 keys is best applied by one merge
+ * of everything): when it is > 0, an untagged batch of k keys (its length as
+ * given) into a set of n keys with 1000 k >= rebuild_pm * n is applied by
+ * merging it with all the keys and building the result like cpma_create
+ * (layout included); other batches take the batch-merge path.  0 = never
+ * (default). */
 typedef struct {
   uint32_t leaf_bytes; /* LB; default 512 */
   uint32_t tau_leaf;   /* default 900 */
@@ -73,6 +79,7 @@ typedef struct {
   uint32_t grow_num;   /* growing factor grow_num / grow_den; default 6/5 */
   uint32_t grow_den;
   uint32_t build_pm;   /* fill density of cpma_create; default 500 */
+  uint32_t rebuild_pm; /* batch-to-set ratio that rebuilds; default 0 = never */
 } cpma_config;
 
 /* Fill *cfg with the defaults above. */

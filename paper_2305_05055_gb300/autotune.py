@@ -1,17 +1,26 @@
 """Autotuner for the CPMA's tunables.
 
-Times the operations that matter for a workload -- batch insert, batch delete
-and range_map over rank-based ranges -- for every candidate configuration
-(leaf size and growing factor; the density bounds stay at their defaults) on
-one seeded sample of that workload, with CUDA events, and returns the
-configuration with the best weighted throughput.  Results are identical for
-every configuration (the configuration only changes the layout), so the
-choice is purely about speed.  The chosen configuration can be saved as JSON
-and passed to :class:`cpma.CPMA` as keyword arguments.
+* Leaf size: times the operations that matter for a workload -- batch
+  insert, batch delete and range_map over rank-based ranges -- for every
+  candidate leaf size on one seeded sample of that workload, with CUDA
+  events, and picks the best weighted throughput.
+* Merge-versus-rebuild threshold (Sec. 4: small batches merge leaf by leaf,
+  batches of k >= n/10 are best applied by rebuilding everything): times
+  both strategies on clones of the same state for growing batch sizes and
+  sets ``rebuild_pm`` at the smallest batch-to-set ratio from which the
+  rebuild stays faster (0 when it never is).
+* Growing factor (App. C): grows a set by a run of inserts under each
+  candidate factor and weighs time against the final bytes per key.
+
+Set-level results are identical for every configuration (it only changes
+the layout), so the choice is purely about speed and space.  The chosen
+configuration can be saved as JSON and passed to :class:`cpma.CPMA` as
+keyword arguments.
 """
 from __future__ import annotations
 
 import json
+import math
 import statistics
 
 import numpy as np
@@ -22,6 +31,8 @@ from . import workloads as W
 
 LEAF_BYTES = (256, 512, 1024, 2048)
 GROWTH = ((6, 5),)
+GROWTH_SWEEP = ((11, 10), (6, 5), (3, 2), (2, 1))
+REBUILD_RATIOS = (0.01, 0.03, 0.1, 0.3)
 
 
 def _timed(fn, reps=3):
@@ -101,6 +112,80 @@ def tune(base: torch.Tensor, sorted_keys: torch.Tensor, batch: int = 10 ** 6,
                      "grow_den": best["grow"][1]},
             "best_by": {k: max(rows, key=lambda r: r[k])["leaf_bytes"] for k in weights},
             "candidates": rows, "weights": weights}
+
+
+def _keys(seed, count, dev):
+    return torch.from_numpy(W.uniform_keys(seed, count, bits=40).view(np.int64)).to(dev)
+
+
+def tune_rebuild(base: torch.Tensor, ratios=REBUILD_RATIOS, leaf_bytes: int = 512,
+                 trials: int = 2, seed: int = 91) -> dict:
+    """Median insert and delete time of a batch of ratio * n fresh keys by
+    the batch merge (rebuild_pm = 0) and by the rebuild (rebuild_pm = 1),
+    on clones of one state with reserved, warm scratch.  rebuild_pm becomes
+    the smallest ratio (in permille) from which the rebuild is faster for
+    every larger ratio measured, else 0."""
+    dev = base.device
+    rows = []
+    for pm in (0, 1):
+        g = cp.CPMA(base, leaf_bytes=leaf_bytes, rebuild_pm=pm)
+        n = g.size()
+        for ratio in ratios:
+            k = max(1, int(ratio * n))
+            b, w = _keys(seed, k, dev), _keys(seed + 1, k, dev)
+            ti, td = [], []
+            for _ in range(trials):
+                h = g.clone()
+                h.reserve(k)
+                h.insert_batch(w)
+                h.delete_batch(w)
+                torch.cuda.synchronize()
+                ti.append(_timed(lambda: h.insert_batch(b), reps=1))
+                td.append(_timed(lambda: h.delete_batch(b), reps=1))
+                del h
+            rows.append({"rebuild": bool(pm), "ratio": ratio, "batch": k,
+                         "insert_ms": statistics.median(ti), "delete_ms": statistics.median(td)})
+            del b, w
+        del g
+        torch.cuda.synchronize()
+    merge = {r["ratio"]: r for r in rows if not r["rebuild"]}
+    reb = {r["ratio"]: r for r in rows if r["rebuild"]}
+    wins = [reb[x]["insert_ms"] + reb[x]["delete_ms"] < merge[x]["insert_ms"] + merge[x]["delete_ms"]
+            for x in ratios]
+    pm = 0
+    for i, x in enumerate(ratios):
+        if all(wins[i:]):
+            pm = int(math.ceil(1000 * x))
+            break
+    return {"rebuild_pm": pm, "rows": rows}
+
+
+def tune_growth(n0: int = 10 ** 7, batch: int = 10 ** 6, steps: int = 40,
+                factors=GROWTH_SWEEP, leaf_bytes: int = 512, dev="cuda", seed: int = 61) -> dict:
+    """Grow a set of n0 uniform keys by `steps` inserts of `batch` fresh keys
+    under each growing factor: total device time, resizes (leaf-count
+    changes) and final bytes per key.  The pick minimises time x bytes/key
+    (both cost the same fraction when doubled)."""
+    base = _keys(seed, n0, dev)
+    batches = [_keys(seed + 1 + i, batch, dev) for i in range(steps)]
+    rows = []
+    for num, den in factors:
+        g = cp.CPMA(base, leaf_bytes=leaf_bytes, grow_num=num, grow_den=den)
+        g.reserve(batch)
+        torch.cuda.synchronize()
+        total, resizes, L = 0.0, 0, g.leaves()
+        for b in batches:
+            total += _timed(lambda: g.insert_batch(b), reps=1)
+            if g.leaves() != L:
+                resizes += 1
+                L = g.leaves()
+        rows.append({"grow": [num, den], "total_ms": total, "resizes": resizes,
+                     "bytes_per_key": g.bytes() / g.size(), "size": g.size()})
+        del g
+        torch.cuda.synchronize()
+    best = min(rows, key=lambda r: r["total_ms"] * r["bytes_per_key"])
+    return {"best": {"grow_num": best["grow"][0], "grow_den": best["grow"][1]}, "rows": rows,
+            "n0": n0, "batch": batch, "steps": steps}
 
 
 def save(result: dict, path: str):

@@ -148,7 +148,7 @@ void release_all(cpma* h) {
                  &s.T_newbytes, &s.T_state, &s.viol, &s.list_lane, &s.list_v1, &s.list_gen, &s.cand, &s.wins, &s.bits, &s.prefix, &s.ovf,
                  &s.E, &s.cost, &s.C, &s.srccnt, &s.srcoff, &s.dstart, &s.win_src, &s.win_dst,
                  &s.win_leaf_off, &s.win_elem_off, &s.win_dst_off, &s.partials, &s.partials_q, &s.q_first,
-                 &s.q_items, &s.q_off, &s.stage, &s.q_lo, &s.q_hi, &s.q_rank})
+                 &s.q_items, &s.q_off, &s.stage, &s.q_lo, &s.q_hi, &s.q_rank, &s.fh})
     release(*b);
   graph_cache_free(h);
   cudaFree(h->data);
@@ -218,6 +218,7 @@ void cpma_default_config(cpma_config* c) {
   c->grow_num = 6;
   c->grow_den = 5;
   c->build_pm = 500;
+  c->rebuild_pm = 0;
 }
 
 int cpma_create(cpma_t** out, const cpma_config* cfg, const uint64_t* d_keys, uint64_t n,

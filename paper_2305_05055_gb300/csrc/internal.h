@@ -79,6 +79,7 @@ struct Scratch {
   Buf q_first, q_items, q_off; // range queries
   Buf q_lo, q_hi, q_rank;       // map_range_length: rank bounds, leaf-count prefix
   Buf stage;              // padded batch of a graph-launched update
+  Buf fh;                 // head fix-up: per-tile summaries
 };
 
 // Profiling phases (cpma_profile_read order).

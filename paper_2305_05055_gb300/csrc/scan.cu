@@ -37,14 +37,56 @@ __device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* warp_t
   return r;
 }
 
+// The kItems consecutive elements of one thread in a full tile, by vector
+// loads (p is 16-byte aligned for 32- and 64-bit input, 8-byte for bytes).
+__device__ __forceinline__ void load_items(const uint8_t* p, uint64_t v[kItems]) {
+  const uint2 x = *reinterpret_cast<const uint2*>(p);
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    v[q] = (x.x >> (8 * q)) & 0xFFu;
+    v[q + 4] = (x.y >> (8 * q)) & 0xFFu;
+  }
+}
+__device__ __forceinline__ void load_items(const uint32_t* p, uint64_t v[kItems]) {
+  const uint4 a = reinterpret_cast<const uint4*>(p)[0], b = reinterpret_cast<const uint4*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void load_items(const uint64_t* p, uint64_t v[kItems]) {
+#pragma unroll
+  for (int q = 0; q < kItems; q += 2) {
+    const ulonglong2 x = reinterpret_cast<const ulonglong2*>(p)[q / 2];
+    v[q] = x.x;
+    v[q + 1] = x.y;
+  }
+}
+
+// Blocks own whole tiles: block b scans tiles [T b / G, T (b+1) / G).
+__device__ __forceinline__ void block_tiles(uint64_t n, uint64_t& t0, uint64_t& t1) {
+  const uint64_t T = (n + kTile - 1) / kTile, G = gridDim.x;
+  t0 = T * blockIdx.x / G;
+  t1 = T * (blockIdx.x + 1) / G;
+}
+
 template <typename Tin>
 __global__ void __launch_bounds__(kT) k_reduce(const Tin* __restrict__ in, uint64_t n_host,
                                                const ull* n_dev, uint64_t* partials) {
   const uint64_t n = n_dev ? *n_dev : n_host;
-  const uint64_t G = gridDim.x;
-  const uint64_t b0 = n * blockIdx.x / G, b1 = n * (blockIdx.x + 1) / G;
+  uint64_t tb0, tb1;
+  block_tiles(n, tb0, tb1);
+  const bool vec = (reinterpret_cast<uintptr_t>(in) & 15) == 0;
   uint64_t s = 0;
-  for (uint64_t i = b0 + threadIdx.x; i < b1; i += kT) s += (uint64_t)in[i];
+  for (uint64_t t = tb0; t < tb1; t++) {
+    const uint64_t base = t * kTile, cnt = min((uint64_t)kTile, n - base);
+    if (vec && cnt == kTile) {
+      uint64_t v[kItems];
+      load_items(in + base + threadIdx.x * kItems, v);
+#pragma unroll
+      for (int q = 0; q < kItems; q++) s += v[q];
+    } else {
+      for (uint64_t i = threadIdx.x; i < cnt; i += kT) s += (uint64_t)in[base + i];
+    }
+  }
   s = warp_sum(s);
   __shared__ uint64_t ws[kT / 32];
   if (lane_id() == 0) ws[threadIdx.x >> 5] = s;
@@ -94,17 +136,25 @@ __global__ void __launch_bounds__(kT) k_down(const Tin* __restrict__ in, uint64_
   __shared__ uint64_t tile_total;
   const uint64_t n = n_dev ? *n_dev : n_host;
   const uint64_t G = gridDim.x;
-  const uint64_t b0 = n * blockIdx.x / G, b1 = n * (blockIdx.x + 1) / G;
+  uint64_t tb0, tb1;
+  block_tiles(n, tb0, tb1);
+  const bool vec = (reinterpret_cast<uintptr_t>(in) & 15) == 0;
   uint64_t carry = SINGLE ? 0 : partials[blockIdx.x];
-  for (uint64_t t0 = b0; t0 < b1; t0 += kTile) {
-    const uint64_t cnt = min((uint64_t)kTile, b1 - t0);
-    for (uint32_t i = threadIdx.x; i < kTile; i += kT)
-      tile[i] = i < cnt ? (uint64_t)in[t0 + i] : 0;
-    __syncthreads();
+  for (uint64_t t = tb0; t < tb1; t++) {
+    const uint64_t t0 = t * kTile, cnt = min((uint64_t)kTile, n - t0);
     uint64_t v[kItems];
+    if (vec && cnt == kTile) {
+      load_items(in + t0 + threadIdx.x * kItems, v);
+    } else {
+      for (uint32_t i = threadIdx.x; i < kTile; i += kT)
+        tile[i] = i < cnt ? (uint64_t)in[t0 + i] : 0;
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < kItems; q++) v[q] = tile[threadIdx.x * kItems + q];
+    }
     uint64_t s = 0;
 #pragma unroll
-    for (int q = 0; q < kItems; q++) { v[q] = tile[threadIdx.x * kItems + q]; s += v[q]; }
+    for (int q = 0; q < kItems; q++) s += v[q];
     uint64_t ex = block_excl_scan(s, warp_tot, &tile_total);
     uint64_t run = carry + ex;
 #pragma unroll

@@ -1061,6 +1061,7 @@ __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
 }
 
 __global__ void k_copy_total(const uint64_t* arr, const ull* n, ull* dst) { *dst = arr[*n]; }
+__global__ void k_put_u64(uint64_t* dst, uint64_t v) { *dst = v; }
 
 __global__ void __launch_bounds__(kT) k_check_tags(const uint32_t* __restrict__ tags, uint64_t k,
                                                    uint64_t ntags, Status* st) {
@@ -1296,44 +1297,151 @@ __global__ void __launch_bounds__(kT) k_encode(EncodeArgs a) {
 
 // Head index of empty leaves: the head of the next non-empty leaf, or
 // 2^64-1.  One block; each thread owns a contiguous segment.
-__global__ void __launch_bounds__(1024) k_fix_heads(const uint32_t* __restrict__ used,
-                                                    uint64_t* __restrict__ heads, uint64_t L,
-                                                    Status* st) {
-  __shared__ uint64_t segmin[1024];
-  __shared__ ull empties, last1;  // last1: 1 + index of the last non-empty leaf
-  if (threadIdx.x == 0) { empties = 0; last1 = 0; }
-  const uint64_t seg = (L + 1023) / 1024;
-  const uint64_t s0 = min(L, threadIdx.x * seg), s1 = min(L, s0 + seg);
-  uint64_t first = KEY_MAX;
-  ull ne = 0, l1 = 0;
-  for (uint64_t j = s0; j < s1; j++) {
-    if (used[j]) { if (first == KEY_MAX) first = heads[j]; l1 = j + 1; }
-    else ne++;
+// Head fix-up (R5): every empty leaf's head-index entry becomes the head of
+// the next non-empty leaf (2^64-1 if none), heads[L] the index of the last
+// non-empty leaf, status->empties the number of empty leaves.  Three passes
+// over tiles of kFHTile leaves: per-tile first non-empty head and counts;
+// one block turns those into each tile's carry (the first non-empty head
+// after it); per-tile fill with a block-wide suffix scan.
+constexpr int kFH = 1024, kFHItems = 4;
+constexpr uint64_t kFHTile = (uint64_t)kFH * kFHItems;
+
+struct FHTile {
+  uint64_t first;     // head of the tile's first non-empty leaf
+  uint64_t carry;     // first non-empty head after the tile (valid if carry_ok)
+  uint64_t last1;     // 1 + index of the tile's last non-empty leaf (0: none)
+  uint32_t has_first, carry_ok, empties, pad;
+};
+
+__global__ void __launch_bounds__(kFH) k_fh_tiles(const uint32_t* __restrict__ used,
+                                                  const uint64_t* __restrict__ heads, uint64_t L,
+                                                  FHTile* __restrict__ tiles) {
+  __shared__ int first_t;
+  __shared__ unsigned int ne_s;
+  __shared__ ull last_s;
+  if (threadIdx.x == 0) { first_t = kFH; ne_s = 0; last_s = 0; }
+  __syncthreads();
+  const uint64_t j0 = blockIdx.x * kFHTile + (uint64_t)threadIdx.x * kFHItems;
+  unsigned int ne = 0;
+  ull l1 = 0;
+  uint64_t fj = KEY_MAX;
+#pragma unroll
+  for (int q = 0; q < kFHItems; q++) {
+    const uint64_t j = j0 + q;
+    if (j < L) {
+      if (used[j]) { if (fj == KEY_MAX) fj = j; l1 = j + 1; }
+      else ne++;
+    }
   }
-  if (l1) atomicMax(&last1, l1);
-  segmin[threadIdx.x] = first;
+  if (fj != KEY_MAX) atomicMin(&first_t, (int)threadIdx.x);
+  if (ne) atomicAdd(&ne_s, ne);
+  if (l1) atomicMax(&last_s, l1);
+  __syncthreads();
+  FHTile& t = tiles[blockIdx.x];
+  if ((int)threadIdx.x == first_t) t.first = heads[fj];
+  if (threadIdx.x == 0) {
+    t.has_first = first_t < kFH;
+    t.empties = ne_s;
+    t.last1 = last_s;
+  }
+}
+
+// One block: carry of every tile (first non-empty head in later tiles), the
+// empty-leaf count and heads[L].
+__global__ void __launch_bounds__(kFH) k_fh_carry(FHTile* __restrict__ tiles, uint64_t nt,
+                                                  uint64_t* __restrict__ heads, uint64_t L,
+                                                  Status* st) {
+  __shared__ uint64_t cv[kFH];
+  __shared__ uint32_t cok[kFH];
+  __shared__ ull ne_s, last_s;
+  if (threadIdx.x == 0) { ne_s = 0; last_s = 0; }
+  __syncthreads();
+  const uint64_t per = (nt + kFH - 1) / kFH;
+  const uint64_t c0 = min(nt, threadIdx.x * per), c1 = min(nt, c0 + per);
+  // this thread's chunk of tiles: its first non-empty head, counts
+  uint64_t fv = 0;
+  bool fok = false;
+  ull ne = 0, l1 = 0;
+  for (uint64_t b = c0; b < c1; b++) {
+    if (!fok && tiles[b].has_first) { fok = true; fv = tiles[b].first; }
+    ne += tiles[b].empties;
+    l1 = max(l1, (ull)tiles[b].last1);
+  }
+  cv[threadIdx.x] = fv;
+  cok[threadIdx.x] = fok;
+  atomicAdd(&ne_s, ne);
+  if (l1) atomicMax(&last_s, l1);
   __syncthreads();
   if (threadIdx.x == 0) {
-    uint64_t nxt = KEY_MAX;
-    for (int t = 1023; t >= 0; t--) {
-      const uint64_t v = segmin[t];
-      segmin[t] = nxt;  // first non-empty head after segment t
-      if (v != KEY_MAX) nxt = v;
+    // exclusive suffix over the chunks, in place
+    uint64_t nv = 0;
+    uint32_t nok = 0;
+    for (int t = kFH - 1; t >= 0; t--) {
+      const uint64_t v = cv[t];
+      const uint32_t ok = cok[t];
+      cv[t] = nv;
+      cok[t] = nok;
+      if (ok) { nv = v; nok = 1; }
+    }
+    st->empties = ne_s;
+    heads[L] = last_s ? last_s - 1 : 0;  // routing of the key 2^64-1
+  }
+  __syncthreads();
+  uint64_t nv = cv[threadIdx.x];
+  uint32_t nok = cok[threadIdx.x];
+  for (uint64_t b = c1; b-- > c0;) {
+    tiles[b].carry = nv;
+    tiles[b].carry_ok = nok;
+    if (tiles[b].has_first) { nv = tiles[b].first; nok = 1; }
+  }
+}
+
+__global__ void __launch_bounds__(kFH) k_fh_fill(const uint32_t* __restrict__ used,
+                                                 uint64_t* __restrict__ heads, uint64_t L,
+                                                 const FHTile* __restrict__ tiles) {
+  __shared__ uint64_t wv[kFH / 32], wc[kFH / 32];
+  __shared__ uint32_t wok[kFH / 32], wcok[kFH / 32];
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint64_t j0 = blockIdx.x * kFHTile + (uint64_t)threadIdx.x * kFHItems;
+  // first non-empty head of this thread's leaves
+  bool ok = false;
+  uint64_t v = 0;
+#pragma unroll
+  for (int q = 0; q < kFHItems; q++) {
+    const uint64_t j = j0 + q;
+    if (!ok && j < L && used[j]) { ok = true; v = heads[j]; }
+  }
+  // inclusive suffix "first valid at or after me" within the warp
+  bool sok = ok;
+  uint64_t sv = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const bool ok2 = __shfl_down_sync(FULL, sok, o);
+    const uint64_t v2 = __shfl_down_sync(FULL, sv, o);
+    if (!sok && lane + o < 32) { sok = ok2; sv = v2; }
+  }
+  if (lane == 0) { wv[warp] = sv; wok[warp] = sok; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t nv = tiles[blockIdx.x].carry;
+    uint32_t nok = tiles[blockIdx.x].carry_ok;
+    for (int w = kFH / 32 - 1; w >= 0; w--) {
+      wc[w] = nv;
+      wcok[w] = nok;
+      if (wok[w]) { nv = wv[w]; nok = 1; }
     }
   }
   __syncthreads();
-  // a segment whose only non-empty heads equal KEY_MAX is handled by the
-  // backward walk below, which reads real heads
-  uint64_t nxt = segmin[threadIdx.x];
-  for (uint64_t j = s1; j-- > s0;) {
-    if (used[j]) nxt = heads[j];
-    else heads[j] = nxt;
-  }
-  atomicAdd(&empties, ne);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    st->empties = empties;
-    heads[L] = last1 ? last1 - 1 : 0;  // routing of the key 2^64-1
+  // exclusive: the next lane's inclusive value, else the warp's carry
+  bool nok = __shfl_down_sync(FULL, sok, 1);
+  uint64_t nv = __shfl_down_sync(FULL, sv, 1);
+  if (lane == 31 || !nok) { nok = wcok[warp]; nv = wc[warp]; }
+  if (!nok) nv = KEY_MAX;
+  for (int q = kFHItems - 1; q >= 0; q--) {
+    const uint64_t j = j0 + q;
+    if (j >= L) continue;
+    if (used[j]) nv = heads[j];
+    else heads[j] = nv;
   }
 }
 
@@ -1471,8 +1579,8 @@ int ensure_win(cpma* h, uint64_t nwin) {
 
 // Pack the source windows into E (sources are the live arrays plus the
 // pending leaves of the current batch), then spread into dst.
-int redistribute(cpma* h, cudaStream_t st, uint64_t nwin, uint64_t nsrc, uint64_t ndst,
-                 uint64_t nelem_bound, uint64_t nT, Arrays dst) {
+int pack(cpma* h, cudaStream_t st, uint64_t nwin, uint64_t nsrc, uint64_t nelem_bound,
+         uint64_t nT) {
   WinArgs w = win_args(h, nwin);
   CPMA_TRY(ensure(h->s.srccnt, (nsrc + 1) * 4));
   CPMA_TRY(ensure(h->s.srcoff, (nsrc + 2) * 8));
@@ -1501,13 +1609,23 @@ int redistribute(cpma* h, cudaStream_t st, uint64_t nwin, uint64_t nsrc, uint64_
   ua.st = h->d_status;
   k_unpack<<<grid_for(h, nsrc * 32), kT, 0, st>>>(ua);
   h->launches++;
-  CPMA_CUDA(cudaGetLastError());
-  return spread(h, st, w, nelem_bound, &h->d_status->nelem, ndst, dst);
+  return check_cuda(cudaGetLastError());
+}
+
+int redistribute(cpma* h, cudaStream_t st, uint64_t nwin, uint64_t nsrc, uint64_t ndst,
+                 uint64_t nelem_bound, uint64_t nT, Arrays dst) {
+  CPMA_TRY(pack(h, st, nwin, nsrc, nelem_bound, nT));
+  return spread(h, st, win_args(h, nwin), nelem_bound, &h->d_status->nelem, ndst, dst);
 }
 
 int fix_heads(cpma* h, cudaStream_t st) {
-  k_fix_heads<<<1, 1024, 0, st>>>(h->used, h->heads, h->L, h->d_status);
-  h->launches++;
+  const uint64_t nt = (h->L + kFHTile - 1) / kFHTile;
+  CPMA_TRY(ensure(h->s.fh, nt * sizeof(FHTile)));
+  FHTile* tiles = P<FHTile>(h->s.fh);
+  k_fh_tiles<<<(unsigned)nt, kFH, 0, st>>>(h->used, h->heads, h->L, tiles);
+  k_fh_carry<<<1, kFH, 0, st>>>(tiles, nt, h->heads, h->L, h->d_status);
+  k_fh_fill<<<(unsigned)nt, kFH, 0, st>>>(h->used, h->heads, h->L, tiles);
+  h->launches += 3;
   return check_cuda(cudaGetLastError());
 }
 
@@ -1547,6 +1665,121 @@ int do_resize(cpma* h, cudaStream_t st, uint64_t T, uint64_t n_after, uint64_t n
   h->data = na.data; h->used = na.used; h->cnt = na.cnt; h->heads = na.heads;
   h->L = Lp;
   return CPMA_OK;
+}
+
+// ---- rebuild of the whole set for a large batch (reading R14) ----
+//
+// All n elements are packed into E, merged with the sorted batch u into M
+// (stable: an element of E precedes equal batch keys), compacted to the
+// union or the difference, and built like the constructor.
+
+__global__ void __launch_bounds__(kT) k_check_sorted(const uint64_t* __restrict__ u, uint64_t k,
+                                                     Status* st) {
+  bool bad = false;
+  for (uint64_t i = gtid() + 1; i < k; i += gstride()) bad |= u[i - 1] > u[i];
+  if (__any_sync(FULL, bad) && lane_id() == 0) atomicOr(&st->err, kErrUnsorted);
+}
+
+// Number of E elements among the first d outputs of the stable merge of
+// A[0..na) and B[0..nb) (merge path: ties take A first).
+template <typename PA, typename PB>
+__device__ __forceinline__ uint64_t merge_split(PA A, uint64_t na, PB B, uint64_t nb, uint64_t d) {
+  uint64_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (A[mid] <= B[d - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kMergeItems = 8;
+constexpr int kMergeTile = kT * kMergeItems;  // outputs per block step
+
+// Stable merge of A (n) and B (k) into M with fromB[i] = 1 for batch keys.
+// Each tile of kMergeTile outputs stages its A and B ranges in shared memory
+// (found by two merge-path searches), every thread merges kMergeItems
+// outputs from its own split, and the tile is written back coalesced.
+__global__ void __launch_bounds__(kT) k_merge_path(const uint64_t* __restrict__ A, uint64_t n,
+                                                   const uint64_t* __restrict__ B, uint64_t k,
+                                                   uint64_t* __restrict__ M,
+                                                   uint8_t* __restrict__ fromB) {
+  __shared__ uint64_t sA[kMergeTile + 1], sB[kMergeTile + 1];
+  __shared__ uint64_t split[2];
+  const uint64_t N = n + k;
+  for (uint64_t d0 = (uint64_t)blockIdx.x * kMergeTile; d0 < N;
+       d0 += (uint64_t)gridDim.x * kMergeTile) {
+    const uint64_t d1 = min(N, d0 + kMergeTile);
+    if (threadIdx.x < 2) split[threadIdx.x] = merge_split(A, n, B, k, threadIdx.x ? d1 : d0);
+    __syncthreads();
+    const uint64_t a0 = split[0], a1 = split[1];
+    const uint64_t b0 = d0 - a0, b1 = d1 - a1;
+    const uint32_t na = (uint32_t)(a1 - a0), nb = (uint32_t)(b1 - b0);
+    for (uint32_t i = threadIdx.x; i < na; i += kT) sA[i] = A[a0 + i];
+    for (uint32_t i = threadIdx.x; i < nb; i += kT) sB[i] = B[b0 + i];
+    __syncthreads();
+    const uint32_t dd = threadIdx.x * kMergeItems, tot = na + nb;
+    // outputs dd .. dd+cnt-1 of the tile (ia + ib = dd + q < tot keeps every
+    // read below na or nb)
+    const uint32_t cnt = dd < tot ? min((uint32_t)kMergeItems, tot - dd) : 0u;
+    uint64_t v[kMergeItems];
+    uint32_t fb = 0;
+    if (cnt) {
+      uint32_t ia = (uint32_t)merge_split(sA, na, sB, nb, dd), ib = dd - ia;
+#pragma unroll
+      for (int q = 0; q < kMergeItems; q++) {
+        if ((uint32_t)q < cnt) {
+          const bool takeA = ib >= nb || (ia < na && sA[ia] <= sB[ib]);
+          v[q] = takeA ? sA[ia] : sB[ib];
+          if (takeA) ia++; else { ib++; fb |= 1u << q; }
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kMergeItems; q++) {
+      if ((uint32_t)q < cnt) {
+        sA[dd + q] = v[q];
+        reinterpret_cast<uint8_t*>(sB)[dd + q] = (uint8_t)((fb >> q) & 1u);
+      }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < tot; i += kT) {
+      M[d0 + i] = sA[i];
+      fromB[d0 + i] = reinterpret_cast<const uint8_t*>(sB)[i];
+    }
+    __syncthreads();
+  }
+}
+
+// keep[i]: union keeps the first of every run of equal keys; difference keeps
+// an element of E that no batch key equals (equal batch keys follow it).
+__global__ void __launch_bounds__(kT) k_rebuild_flags(const uint64_t* __restrict__ M,
+                                                      const uint8_t* __restrict__ fromB,
+                                                      uint64_t N, int is_delete,
+                                                      uint8_t* __restrict__ keep) {
+  for (uint64_t i = gtid(); i < N; i += gstride()) {
+    const uint64_t x = M[i];
+    bool kp;
+    if (is_delete) kp = !fromB[i] && (i + 1 == N || M[i + 1] != x);
+    else kp = i == 0 || M[i - 1] != x;
+    keep[i] = kp ? 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(kT) k_rebuild_scatter(const uint64_t* __restrict__ M,
+                                                        const uint8_t* __restrict__ keep,
+                                                        const uint64_t* __restrict__ pos,
+                                                        uint64_t N, uint64_t n_old,
+                                                        int is_delete,
+                                                        uint64_t* __restrict__ E, Status* st) {
+  for (uint64_t i = gtid(); i < N; i += gstride())
+    if (keep[i]) E[pos[i]] = M[i];
+  if (gtid() == 0) {
+    const uint64_t m = pos[N];
+    st->nelem = m;
+    st->delta = is_delete ? n_old - m : m - n_old;
+  }
 }
 
 // Host-side values the front segment of an update leaves for the rest of it.
@@ -1895,6 +2128,69 @@ void graph_cache_free(cpma* h) {
   h->cap_stream = nullptr;
 }
 
+// R14: apply the batch by merging it with every element and building the
+// result like the constructor.  Nothing is replaced before the new arrays
+// are complete, so a rejected batch leaves the set unchanged.
+int run_rebuild(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_delete,
+                uint64_t* d_delta, cudaStream_t st) {
+  Status* ds = h->d_status;
+  Scratch& s = h->s;
+  const uint64_t n = h->n, N = n + k;
+  CPMA_CUDA(cudaMemsetAsync(ds, 0, offsetof(Status, empties), st));
+  const uint64_t* u = d_keys;
+  prof_begin(h, PH_SORT, st);
+  if (!sorted) {
+    CPMA_TRY(sort_keys(h, d_keys, k, &u, st));
+  } else {
+    k_check_sorted<<<grid_for(h, k), kT, 0, st>>>(u, k, ds);
+    h->launches++;
+  }
+  prof_end(h, st);
+  prof_begin(h, PH_REDIST, st);
+  // every element, in order, into E (one window over all leaves); E later
+  // takes the merged set, up to n + k keys
+  CPMA_TRY(ensure(s.E, (N + 1) * 8));
+  CPMA_TRY(ensure_win(h, 1));
+  k_set_window<<<1, 1, 0, st>>>(P<uint64_t>(s.win_src), P<uint64_t>(s.win_dst),
+                                P<uint64_t>(s.win_leaf_off), P<uint64_t>(s.win_dst_off), 0, h->L,
+                                0, h->L);
+  h->launches++;
+  CPMA_TRY(pack(h, st, 1, h->L, n, 0));
+  CPMA_TRY(ensure(s.ovf, (N + 1) * 8));
+  CPMA_TRY(ensure(s.cost, N + 1));
+  CPMA_TRY(ensure(s.flags_scan, (N + 2) * 8));
+  CPMA_TRY(ensure(s.srccnt, N + 1));
+  uint64_t* M = P<uint64_t>(s.ovf);
+  uint8_t* fromB = P<uint8_t>(s.srccnt);
+  uint8_t* keep = P<uint8_t>(s.cost);
+  uint64_t* pos = P<uint64_t>(s.flags_scan);
+  // one block per tile of outputs: the scheduler overlaps the tiles' load,
+  // merge and store phases across blocks
+  const uint64_t mg = std::max<uint64_t>(1, (N + kMergeTile - 1) / kMergeTile);
+  if (mg >= (1ull << 31)) return CPMA_EINVAL;
+  k_merge_path<<<(unsigned)mg, kT, 0, st>>>(P<uint64_t>(s.E), n, u, k, M, fromB);
+  k_rebuild_flags<<<grid_for(h, N), kT, 0, st>>>(M, fromB, N, is_delete, keep);
+  h->launches += 2;
+  CPMA_TRY(scan_u8_to_u64(h, keep, pos, N, nullptr, st));
+  k_rebuild_scatter<<<grid_for(h, N), kT, 0, st>>>(M, keep, pos, N, n, is_delete,
+                                                   P<uint64_t>(s.E), ds);
+  h->launches++;
+  CPMA_CUDA(cudaGetLastError());
+  CPMA_TRY(sync_status(h, st));
+  Status hs = *h->h_status;
+  if (hs.err & kErrUnsorted) return CPMA_EINVAL;
+  if (hs.err) return CPMA_EINTERNAL;
+  CPMA_TRY(build_from_sorted_unique(h, P<uint64_t>(s.E), hs.nelem, st));
+  prof_end(h, st);
+  if (d_delta) {
+    // build_from_sorted_unique reset the status block; the count is on the host
+    const uint64_t delta = is_delete ? n - hs.nelem : hs.nelem - n;
+    k_put_u64<<<1, 1, 0, st>>>(d_delta, delta);
+    h->launches++;
+  }
+  return check_cuda(cudaGetLastError());
+}
+
 int reserve(cpma* h, uint64_t max_batch, int tagged, cudaStream_t st) {
   if (max_batch >= (1ull << 31)) return CPMA_EINVAL;
   if (max_batch == 0) return CPMA_OK;
@@ -1919,6 +2215,9 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
     return CPMA_OK;
   }
   if (k >= (1ull << 31)) return CPMA_EINVAL;
+  if (h->cfg.rebuild_pm && !tags &&
+      (unsigned __int128)1000 * k >= (unsigned __int128)h->cfg.rebuild_pm * h->n)
+    return run_rebuild(h, d_keys, k, sorted, is_delete, d_delta, st);
   Scratch& s = h->s;
   Front f;
   if (k <= h->graph_max_batch && !tags && !h->prof.on && graph_bucket(k) < (1ull << 31)) {

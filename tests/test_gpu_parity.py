@@ -378,3 +378,45 @@ def test_range_reduce_matches_oracle(op):
         wr, wc = p.range_reduce(lo, hi, op, mask, value)
         assert np.array_equal(cp.to_u64(c), wc)
         assert np.array_equal(cp.to_u64(r), wr)
+
+
+@pytest.mark.parametrize("LB", [256, 512, 2048])
+def test_rebuild_threshold_matches_oracle(LB):
+    """rebuild_pm > 0: batches with 1000 k >= rebuild_pm n are applied by a
+    merge of everything and a fresh build (reading R14); the others by the
+    batch merge.  Counts, sets and layouts against the oracle, across the
+    threshold, for inserts, deletes, sorted batches and an empty start."""
+    cfg = dict(leaf_bytes=LB, rebuild_pm=100)
+    g = cp.CPMA(None, **cfg)
+    o = oracle.SeqCPMA([], **cfg)
+    p = oracle.PlainSet([])
+    rng = np.random.default_rng(LB + 1)
+    for r in range(14):
+        n = len(p)
+        kind = r % 4
+        if kind == 0 or n == 0:   # large insert: rebuild (or first fill)
+            keys = W.uniform_keys(400 + r, max(n // 5, 5000), bits=40)
+            keys = np.concatenate([keys, keys[:100]])
+        elif kind == 1:           # small insert, below the threshold: merge
+            keys = W.uniform_keys(400 + r, max(1, n // 50), bits=40)
+        elif kind == 2:           # large delete of present and absent keys
+            keys = np.concatenate([W.sample_present(p.S, 500 + r, n // 4),
+                                   W.uniform_keys(600 + r, 50, bits=40)])
+        else:                     # sorted batch exactly at the threshold
+            k = -(-100 * n // 1000)
+            keys = np.sort(W.uniform_keys(700 + r, k, bits=40))
+        srt = kind == 3
+        if kind == 2:
+            got = int(g.delete_batch(T(keys)).item())
+            assert got == o.delete_batch(keys) == p.delete_batch(keys)
+        else:
+            got = int(g.insert_batch(T(keys), sorted=srt).item())
+            assert got == o.insert_batch(keys) == p.insert_batch(keys)
+        same_layout(g, o)
+    same_queries(g, p, 88, 200)
+    # an unsorted batch flagged sorted is rejected on the rebuild path too
+    bad = np.array([9, 3, 5], np.uint64)
+    small = cp.CPMA(T(np.array([1, 2], np.uint64)), **cfg)
+    with pytest.raises(cp.CPMAError):
+        small.insert_batch(T(bad), sorted=True)
+    assert small.size() == 2
