@@ -10,8 +10,14 @@ time of the K steps (CUDA events on the stream, max over ranks).
 After the timed region the same run measures, with CUDA events, the other rows
 of the hot path on the same structure: batch delete of 1e6 present keys,
 has_batch of 1e6 keys, range_map of 1e5 queries whose widths are log-uniform
-between 10 and 1e6 elements (one launch), and a full-set scan sum; each with
-its algorithmic bytes and achieved fraction of the measured HBM bandwidth.
+between 10 and 1e6 elements (one launch), map_range_length and filtered
+reductions over the same queries, and a full-set scan sum; each with its
+algorithmic bytes and achieved fraction of the measured HBM bandwidth.  Then
+the batch-size sweep (1e3..1e7 inserts and deletes at 1e8, launch by launch
+and with CUDA graphs), the autotuner (leaf size, merge-versus-rebuild
+threshold, growing factor), the skewed-update rounds, the continuous-batching
+server against one call per request (offered-rate sweep, p50/p99 at 70% of
+saturation) and the R-MAT edge set.  Each has a --no-* switch.
 
 --impl reference times the CPU oracle (oracle/, single thread) on a bounded
 sample of the same workload.  Several GPUs: independent replicas, one per
@@ -89,6 +95,8 @@ def parse():
     ap.add_argument("--queries", type=float, default=1e5)
     ap.add_argument("--no-extra", action="store_true", help="headline only")
     ap.add_argument("--no-sweep", action="store_true", help="skip the insert/delete sweep 1e3..1e7")
+    ap.add_argument("--no-graph", action="store_true", help="skip the R-MAT edge-set workload")
+    ap.add_argument("--graph-scale", type=int, default=20)
     ap.add_argument("--sweep-trials", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-skew", action="store_true", help="skip the skewed-update rounds")
@@ -96,7 +104,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop comparison")
     ap.add_argument("--no-autotune", action="store_true", help="skip the leaf-size autotuning")
     ap.add_argument("--serve-requests", type=int, default=3000)
-    ap.add_argument("--serve-rate", type=float, default=5000.0, help="offered requests/s")
+    ap.add_argument("--serve-rates", type=lambda x: [float(v) for v in x.split(",")],
+                    default=[2500, 5000, 10000, 20000, 40000, 80000],
+                    help="offered request rates of the serving sweep (comma separated)")
     return ap.parse_args()
 
 
@@ -338,7 +348,7 @@ def main():
 
     extra = {}
     if not a.no_extra and rank == 0:
-        extra = measure_extra(a, g, batches[nwarm:], dev, st, hbm_peak, peak_kind, T)
+        extra = measure_extra(a, g, batches, dev, st, hbm_peak, peak_kind, T)
 
     cpu_base = None
     if not a.no_cpu_baseline and rank == 0 and world == 1:
@@ -370,6 +380,8 @@ def main():
 
 
 def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
+    """Secondary workloads on the CPMA of the headline run; ins_batches are
+    every batch inserted into it (warm-up and timed), so the set is known."""
     import torch
     from paper_2305_05055_gb300 import cpma as cp
     from paper_2305_05055_gb300 import workloads as W
@@ -422,6 +434,23 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
                         "ms_per_call": ms, "roofline": roof(prof, "range"),
                         "note": "widths log-uniform 10..1e6 elements; overlapping queries may "
                                 "hit in L2, so algorithmic GB/s can exceed HBM"}
+    # map_range_length over the same queries: the first c keys >= lo are
+    # exactly [lo, hi) of the rank-based query, so the sums must agree
+    g.profile(True)
+    ms_l, (s_l, c_l) = timed(lambda: g.range_map_length(lo, c), reps=3)
+    prof = g.profile_read()
+    g.profile(False)
+    same = bool(torch.equal(s_l, s) and torch.equal(c_l, cnt))
+    out["range_map_length"] = {"value": int(c_l.sum().item()) / (ms_l / 1e3), "unit": "elems/s",
+                               "queries": q, "ms_per_call": ms_l, "equals_range_map": same,
+                               "prep_ms_per_call": prof["range_prep"]["ms"] / 3,
+                               "roofline": roof(prof, "range")}
+    # filtered reductions (decode every covered leaf): odd keys, minimum
+    for op, mask, value in (("sum", 1, 1), ("min", 0, 0)):
+        ms_r, (r_r, c_r) = timed(lambda: g.range_reduce(lo, hi, op, mask, value), reps=3)
+        out["range_reduce_%s%s" % (op, "_odd" if mask else "")] = {
+            "value": elems / (ms_r / 1e3), "unit": "elems/s (covered)", "ms_per_call": ms_r,
+            "passed": int(c_r.sum().item())}
     # full-set scan
     g.profile(True)
     ms, (s, cnt) = timed(lambda: g.sum(), reps=5)
@@ -477,6 +506,8 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
         out["sweep"] = sweep(a, g, dev, T, timed)
     if not a.no_skew:
         out["skew"] = skew(a, dev, T, timed)
+    if not a.no_graph:
+        out["graph"] = graph_workload(a, dev, timed)
     if not a.no_serve:
         out["serve"] = serving(a, g, S_host)
     return out
@@ -484,23 +515,87 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
 
 def serving(a, g, S):
     """Continuous batching vs one library call per request on the same seeded
-    trace: 64 clients with Poisson arrivals, 45% inserts of log-uniform
+    traces: 64 clients with Poisson arrivals, 45% inserts of log-uniform
     1..1e5 fresh keys, 10% deletes of log-uniform 1..1e4 present keys, 45%
-    range sums of log-uniform 10..1e6 elements, 16 GB device budget."""
+    range sums of log-uniform 10..1e6 elements, 16 GB device budget.  A sweep
+    of offered rates finds each form's saturation (the throughput it reaches
+    when offered far more than it can serve); the headline p50/p99 are
+    measured at 70% of the continuous-batching loop's saturation."""
     import torch
     from paper_2305_05055_gb300 import serve
-    mk = lambda: serve.make_trace(a.serve_requests, a.serve_rate, 95, S, S)
-    plain_g = g.clone()
+
+    def point(rate, seed):
+        mk = lambda: serve.make_trace(a.serve_requests, rate, seed, S, S)
+        plain_g = g.clone()
+        torch.cuda.synchronize()
+        served = serve.Server(g, mem_budget_bytes=16 << 30).run(mk())
+        plain = serve.run_one_at_a_time(plain_g, mk())
+        del plain_g
+        keep = ("requests_per_s", "p50_ms", "p99_ms", "mean_ms", "max_ms")
+        s_ = {k: served[k] for k in keep}
+        s_.update(epochs=served["epochs"], max_epoch_requests=served["max_epoch_requests"])
+        return {"offered_requests_per_s": rate, "served": s_,
+                "one_at_a_time": {k: plain[k] for k in keep}}
+
+    sweep = [point(r, 95 + i) for i, r in enumerate(a.serve_rates)]
+    sat_served = max(p["served"]["requests_per_s"] for p in sweep)
+    sat_plain = max(p["one_at_a_time"]["requests_per_s"] for p in sweep)
+    rate = 0.7 * sat_served
+    head = point(rate, 90)
+    return {"requests_per_point": a.serve_requests, "sweep": sweep,
+            "saturation_requests_per_s": {"served": sat_served, "one_at_a_time": sat_plain},
+            "offered_requests_per_s": rate, "at_offered": head,
+            "p50_ms": head["served"]["p50_ms"], "p99_ms": head["served"]["p99_ms"],
+            "one_at_a_time_p50_ms": head["one_at_a_time"]["p50_ms"],
+            "one_at_a_time_p99_ms": head["one_at_a_time"]["p99_ms"],
+            "p99_speedup": head["one_at_a_time"]["p99_ms"] / head["served"]["p99_ms"],
+            "throughput_ratio": head["served"]["requests_per_s"] /
+                                head["one_at_a_time"]["requests_per_s"],
+            "saturation_ratio": sat_served / sat_plain}
+
+
+def graph_workload(a, dev, timed):
+    """F-Graph-style edge set (keys u << 32 | v) on an R-MAT graph with
+    2^scale vertices and 16 edges per vertex: build, batch edge inserts,
+    a neighbour scan of every vertex (degrees by one range_map, neighbour
+    lists by one range_extract) and a BFS (edges scanned per second)."""
+    import torch
+    from paper_2305_05055_gb300 import graph
+    from paper_2305_05055_gb300 import workloads as W
+    scale = int(a.graph_scale)
+    nv, ne = 1 << scale, 16 << scale
+    src, dst = W.rmat_edges(7, scale, ne)
+    t0 = time.perf_counter()
+    es = graph.EdgeSet(src, dst, device=dev)
     torch.cuda.synchronize()
-    srv = serve.Server(g, mem_budget_bytes=16 << 30)
-    served = srv.run(mk())
-    plain = serve.run_one_at_a_time(plain_g, mk())
-    del plain_g
-    return {"offered_requests_per_s": a.serve_rate, "requests": a.serve_requests,
-            "served": served, "one_at_a_time": plain,
-            "p99_ms": served["p99_ms"], "p50_ms": served["p50_ms"],
-            "p99_speedup": plain["p99_ms"] / served["p99_ms"],
-            "throughput_ratio": served["requests_per_s"] / plain["requests_per_s"]}
+    build_s = time.perf_counter() - t0
+    del src, dst
+    m0 = es.num_edges()
+    batches = [W.rmat_edges(100 + i, scale, 10 ** 6) for i in range(5)]
+    bk = [es._vkeys(s_, d_) for s_, d_ in batches]
+    es.g.reserve(10 ** 6)
+    ins = []
+    for k_ in bk:
+        ms, _ = timed(lambda: es.g.insert_batch(k_))
+        ins.append(ms)
+    verts = torch.arange(nv, dtype=torch.int64, device=dev)
+    ms_deg, deg = timed(lambda: es.degrees(verts), reps=3)
+    ms_nb, (off, nb) = timed(lambda: es.neighbors(verts), reps=3)
+    m = es.num_edges()
+    assert int(off[-1].item()) == m == int(deg.sum().item())
+    root = int(torch.argmax(deg).item())
+    ms_bfs, lvl = timed(lambda: es.bfs(root, nv))
+    reached = lvl >= 0
+    scanned = int(deg[reached].sum().item())
+    return {"scale": scale, "vertices": nv, "edges_generated": ne, "edges_after_build": m0,
+            "build_s": build_s, "edges": m, "bytes_per_edge": es.g.bytes() / m,
+            "insert_edges_per_s": 10 ** 6 * len(ins) / (sum(ins) / 1e3),
+            "degrees_all_vertices_ms": ms_deg,
+            "neighbors_all_vertices_ms": ms_nb,
+            "neighbor_scan_edges_per_s": m / (ms_nb / 1e3),
+            "bfs_ms": ms_bfs, "bfs_levels": int(lvl.max().item()),
+            "bfs_reached": int(reached.sum().item()),
+            "bfs_edges_scanned_per_s": scanned / (ms_bfs / 1e3)}
 
 
 def skew(a, dev, T, timed):

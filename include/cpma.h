@@ -171,6 +171,22 @@ int cpma_range_map_length(const cpma_t* h, const uint64_t* d_start,
                           const uint64_t* d_length, uint64_t q, uint64_t* d_sum,
                           uint64_t* d_count, cpma_stream_t stream);
 
+/* Sec. 3 range_map with f = "emit the key", batched: the keys of [d_lo[i],
+ * d_hi[i]) in order, all queries' keys packed into one device array.
+ * d_offsets (q + 1 device uint64) receives the exclusive prefix sum of the
+ * per-query counts: query i's keys go to d_out[d_offsets[i] ..
+ * d_offsets[i+1]) and d_offsets[q] is the total.  Keys at positions >=
+ * out_cap are not written; with d_out NULL or out_cap 0 only d_offsets is
+ * computed, so a caller sizes d_out from d_offsets[q] and calls again.  Both
+ * range ends are turned into global ranks (a prefix sum of the leaves'
+ * element counts, then one leaf decode per end), and the leaves between them
+ * are decoded by the load-balanced walk of cpma_range_map.  Errors:
+ * CPMA_EINVAL (null handle, d_offsets NULL, or d_lo / d_hi NULL with q > 0),
+ * CPMA_ENOMEM. */
+int cpma_range_extract(const cpma_t* h, const uint64_t* d_lo, const uint64_t* d_hi,
+                       uint64_t q, uint64_t* d_offsets, uint64_t* d_out, uint64_t out_cap,
+                       cpma_stream_t stream);
+
 /* Functions for cpma_range_reduce. */
 #define CPMA_OP_SUM 0 /* sum modulo 2^64; 0 when no key passes */
 #define CPMA_OP_MIN 1 /* smallest key; 2^64-1 when no key passes */

@@ -235,6 +235,19 @@ class PlainSet:
             sums[i], cnts[i] = s.value, c.value
         return sums, cnts
 
+    def range_extract(self, lo, hi):
+        """Sec. 3 range_map emitting the keys: (offsets, keys) with the keys
+        of [lo[i], hi[i]) at keys[offsets[i]:offsets[i+1]]."""
+        lo, hi = _u64(lo), _u64(hi)
+        parts, off = [], [0]
+        for a, b in zip(lo.tolist(), hi.tolist()):
+            i = int(np.searchsorted(self.S, np.uint64(a), side="left"))
+            j = int(np.searchsorted(self.S, np.uint64(b), side="left")) if a < b else i
+            parts.append(self.S[i:j])
+            off.append(off[-1] + (j - i))
+        keys = np.concatenate(parts) if parts else np.zeros(0, np.uint64)
+        return np.array(off, dtype=np.uint64), keys.astype(np.uint64)
+
     OPS = {"sum": 0, "min": 1, "max": 2, "xor": 3}
 
     def range_reduce(self, lo, hi, op="sum", mask=0, value=0):

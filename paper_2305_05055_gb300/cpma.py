@@ -78,6 +78,7 @@ def lib():
                 "cpma_reserve": (I, [V, U64, U64, I, V]),
                 "cpma_range_map_length": (I, [V, V, V, U64, V, V, V]),
                 "cpma_range_reduce": (I, [V, V, V, U64, I, U64, U64, V, V, V]),
+                "cpma_range_extract": (I, [V, V, V, U64, V, V, U64, V]),
                 "cpma_use_graphs": (I, [V, U64]),
                 "cpma_graph_stats": (I, [V, P64, P64]),
             }
@@ -246,6 +247,25 @@ def cpma_range_map_length(h, start, length, out_sum=None, out_count=None, stream
     return s, c
 
 
+def cpma_range_extract(h, lo, hi, stream=None):
+    """The keys of every [lo[i], hi[i]), packed: returns (offsets, keys) with
+    query i's keys at keys[offsets[i]:offsets[i+1]] (two library calls: the
+    first sizes the output)."""
+    lo, hi = _keys(lo, "lo"), _keys(hi, "hi")
+    if lo.numel() != hi.numel():
+        raise ValueError("lo and hi differ in size")
+    q = lo.numel()
+    off = torch.empty(q + 1, dtype=torch.int64, device=lo.device)
+    st = C.c_void_p(_stream(stream))
+    _check(lib().cpma_range_extract(h, _ptr(lo), _ptr(hi), q, _ptr(off), None, 0, st),
+           "cpma_range_extract")
+    total = int(off[q].item())
+    out = torch.empty(max(total, 1), dtype=torch.int64, device=lo.device)
+    _check(lib().cpma_range_extract(h, _ptr(lo), _ptr(hi), q, _ptr(off), _ptr(out), total, st),
+           "cpma_range_extract")
+    return off, out[:total]
+
+
 OPS = {"sum": 0, "min": 1, "max": 2, "xor": 3}
 
 
@@ -403,6 +423,9 @@ class CPMA:
 
     def range_map_length(self, start, length, stream=None):
         return cpma_range_map_length(self._h, start, length, stream=stream)
+
+    def range_extract(self, lo, hi, stream=None):
+        return cpma_range_extract(self._h, lo, hi, stream=stream)
 
     def range_reduce(self, lo, hi, op="sum", mask=0, value=0, stream=None):
         return cpma_range_reduce(self._h, lo, hi, op, mask, value, stream=stream)

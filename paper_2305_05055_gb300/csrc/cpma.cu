@@ -359,6 +359,13 @@ int cpma_range_map_length(const cpma_t* h, const uint64_t* d_start, const uint64
   return run_range_length(h, d_start, d_length, q, d_sum, d_count, (cudaStream_t)stream);
 }
 
+int cpma_range_extract(const cpma_t* h, const uint64_t* d_lo, const uint64_t* d_hi, uint64_t q,
+                       uint64_t* d_offsets, uint64_t* d_out, uint64_t out_cap,
+                       cpma_stream_t stream) {
+  if (!h || !d_offsets || (q && (!d_lo || !d_hi))) return CPMA_EINVAL;
+  return run_range_extract(h, d_lo, d_hi, q, d_offsets, d_out, out_cap, (cudaStream_t)stream);
+}
+
 int cpma_range_reduce(const cpma_t* h, const uint64_t* d_lo, const uint64_t* d_hi, uint64_t q,
                       int op, uint64_t mask, uint64_t value, uint64_t* d_out, uint64_t* d_count,
                       cpma_stream_t stream) {

@@ -186,6 +186,8 @@ int run_range(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q,
 int run_sum(const cpma* h, uint64_t* sum, uint64_t* count, cudaStream_t st);
 int run_range_length(const cpma* h, const uint64_t* start, const uint64_t* length, uint64_t q,
                      uint64_t* sum, uint64_t* count, cudaStream_t st);
+int run_range_extract(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q,
+                      uint64_t* offsets, uint64_t* out, uint64_t cap, cudaStream_t st);
 int run_range_reduce(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q, int op,
                      uint64_t mask, uint64_t value, uint64_t* out, uint64_t* count,
                      cudaStream_t st);

@@ -167,33 +167,44 @@ __global__ void __launch_bounds__(kT) k_range_prep(const uint64_t* __restrict__ 
   }
 }
 
-// map_range_length, step 1 (warp per query): rank r0 of the first key >=
-// start (elements before its leaf + elements of the leaf below start),
-// r1 = min(r0 + length, n), and the leaves holding ranks r0 .. r1-1.
-__global__ void __launch_bounds__(kT) k_len_prep(const uint64_t* __restrict__ start,
-                                                 const uint64_t* __restrict__ length, uint64_t q,
-                                                 const uint64_t* __restrict__ heads,
-                                                 const uint8_t* __restrict__ data,
-                                                 const uint32_t* __restrict__ used, uint64_t L,
-                                                 uint32_t LB, const uint64_t* __restrict__ P,
-                                                 uint64_t* __restrict__ r0o,
-                                                 uint64_t* __restrict__ r1o,
-                                                 uint64_t* __restrict__ first,
-                                                 uint64_t* __restrict__ items,
-                                                 uint64_t* __restrict__ sum,
-                                                 uint64_t* __restrict__ count) {
+// Rank of the first key >= x: elements before its leaf plus the leaf's
+// elements below x (the whole warp decodes the leaf).
+__device__ __forceinline__ uint64_t rank_of(uint64_t x, const uint64_t* __restrict__ heads,
+                                            const uint8_t* __restrict__ data,
+                                            const uint32_t* __restrict__ used, uint64_t L,
+                                            uint32_t LB, const uint64_t* __restrict__ P) {
+  const uint64_t j = route_leaf(heads, L, x);
+  uint32_t below = 0;
+  warp_decode(data + j * LB, min(used[j], LB), [&](uint32_t, uint64_t v) { below += v < x; });
+  return P[j] + warp_sum(below);
+}
+
+// Step 1 of the rank-space queries (warp per query): the rank range
+// [r0, r1) and the leaves holding it.  KEYS: [a, b) is a key range, r0 =
+// rank(a), r1 = rank(b) (r1 = r0 when a >= b).  Otherwise (map_range_length)
+// a is the start key and b the length: r1 = min(r0 + b, n).
+template <bool KEYS>
+__global__ void __launch_bounds__(kT) k_rank_prep(const uint64_t* __restrict__ A,
+                                                  const uint64_t* __restrict__ B, uint64_t q,
+                                                  const uint64_t* __restrict__ heads,
+                                                  const uint8_t* __restrict__ data,
+                                                  const uint32_t* __restrict__ used, uint64_t L,
+                                                  uint32_t LB, const uint64_t* __restrict__ P,
+                                                  uint64_t* __restrict__ r0o,
+                                                  uint64_t* __restrict__ r1o,
+                                                  uint64_t* __restrict__ first,
+                                                  uint64_t* __restrict__ items,
+                                                  uint64_t* __restrict__ sum,
+                                                  uint64_t* __restrict__ count) {
   const unsigned lane = lane_id();
   const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
   const uint64_t n = P[L];
   for (uint64_t i = gw; i < q; i += nw) {
-    const uint64_t x = start[i];
-    const uint64_t j0 = route_leaf(heads, L, x);
-    uint32_t below = 0;
-    warp_decode(data + j0 * LB, min(used[j0], LB), [&](uint32_t, uint64_t v) { below += v < x; });
-    below = warp_sum(below);
-    const uint64_t r0 = P[j0] + below;
-    const uint64_t len = length[i];
-    const uint64_t r1 = (len >= n - r0) ? n : r0 + len;
+    const uint64_t a = A[i], b = B[i];
+    const uint64_t r0 = rank_of(a, heads, data, used, L, LB, P);
+    uint64_t r1;
+    if constexpr (KEYS) r1 = a < b ? rank_of(b, heads, data, used, L, LB, P) : r0;
+    else r1 = (b >= n - r0) ? n : r0 + b;
     uint64_t f = 0, it = 0;
     if (r1 > r0) {
       f = upper_count(P, L + 1, r0) - 1;
@@ -204,9 +215,44 @@ __global__ void __launch_bounds__(kT) k_len_prep(const uint64_t* __restrict__ st
       r1o[i] = r1;
       first[i] = f;
       items[i] = it;
-      sum[i] = 0;
-      count[i] = 0;
+      if (sum) sum[i] = 0;
+      if (count) count[i] = KEYS ? r1 - r0 : 0;
     }
+  }
+}
+
+// range_extract: the keys of ranks [r0, r1) of every query, written from
+// out[off[i]] on (entries at or past cap are dropped).  Same load-balanced
+// (query, leaf) walk as k_range.
+struct ExtractArgs {
+  const uint64_t* r0;
+  const uint64_t* r1;
+  uint64_t q;
+  const uint64_t* first;
+  const uint64_t* item_off;  // q + 1
+  const uint64_t* out_off;   // q + 1
+  const uint64_t* P;
+  const uint8_t* data;
+  const uint32_t* used;
+  uint32_t LB;
+  uint64_t* out;
+  uint64_t cap;
+};
+
+__global__ void __launch_bounds__(kT) k_extract(ExtractArgs a) {
+  const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
+  const uint64_t N = a.item_off[a.q];
+  const uint64_t g0 = N * gw / nw, g1 = N * (gw + 1) / nw;
+  if (g0 >= g1) return;
+  uint64_t qi = upper_count(a.item_off, a.q + 1, g0) - 1;
+  for (uint64_t g = g0; g < g1; g++) {
+    while (g >= a.item_off[qi + 1]) qi++;
+    const uint64_t j = a.first[qi] + (g - a.item_off[qi]);
+    const uint64_t r0 = a.r0[qi], r1 = a.r1[qi], base = a.P[j], o = a.out_off[qi];
+    warp_decode(a.data + j * a.LB, min(a.used[j], a.LB), [&](uint32_t idx, uint64_t v) {
+      const uint64_t r = base + idx;
+      if (r >= r0 && r < r1 && o + (r - r0) < a.cap) a.out[o + (r - r0)] = v;
+    });
   }
 }
 
@@ -469,8 +515,8 @@ int run_range_length(const cpma* h, const uint64_t* start, const uint64_t* lengt
   CPMA_TRY(scan_u32_query(hm, h->cnt, P, h->L, st));
   const int g1 = (int)std::max<uint64_t>(
       1, std::min<uint64_t>((q * 32 + kT - 1) / kT, (uint64_t)h->num_sms * 16));
-  k_len_prep<<<g1, kT, 0, st>>>(start, length, q, h->heads, h->data, h->used, h->L,
-                                h->cfg.leaf_bytes, P, r0, r1, first, items, sum, count);
+  k_rank_prep<false><<<g1, kT, 0, st>>>(start, length, q, h->heads, h->data, h->used, h->L,
+                                        h->cfg.leaf_bytes, P, r0, r1, first, items, sum, count);
   CPMA_LAUNCHED(h);
   CPMA_TRY(scan_u64_query(hm, items, off, q, st));
   prof_end(h, st);
@@ -490,6 +536,56 @@ int run_range_length(const cpma* h, const uint64_t* start, const uint64_t* lengt
   a.P = P;
   prof_begin(h, PH_RANGE, st);
   k_range<true><<<persistent_grid(h), kT, 0, st>>>(a);
+  CPMA_LAUNCHED(h);
+  prof_end(h, st);
+  return check_cuda(cudaGetLastError());
+}
+
+int run_range_extract(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q,
+                      uint64_t* offsets, uint64_t* out, uint64_t cap, cudaStream_t st) {
+  if (q == 0) return check_cuda(cudaMemsetAsync(offsets, 0, 8, st));
+  cpma* hm = const_cast<cpma*>(h);
+  Scratch& s = hm->s;
+  CPMA_TRY(ensure(s.q_first, q * 8));
+  CPMA_TRY(ensure(s.q_items, (q + 1) * 8));
+  CPMA_TRY(ensure(s.q_off, (q + 1) * 8));
+  CPMA_TRY(ensure(s.q_lo, q * 8));
+  CPMA_TRY(ensure(s.q_hi, q * 8));
+  CPMA_TRY(ensure(s.q_rank, (h->L + 1) * 8));
+  uint64_t* P = (uint64_t*)s.q_rank.p;
+  uint64_t* r0 = (uint64_t*)s.q_lo.p;
+  uint64_t* r1 = (uint64_t*)s.q_hi.p;
+  uint64_t* first = (uint64_t*)s.q_first.p;
+  uint64_t* items = (uint64_t*)s.q_items.p;
+  uint64_t* off = (uint64_t*)s.q_off.p;
+  prof_begin(h, PH_RANGE_PREP, st);
+  CPMA_TRY(scan_u32_query(hm, h->cnt, P, h->L, st));
+  const int g1 = (int)std::max<uint64_t>(
+      1, std::min<uint64_t>((q * 32 + kT - 1) / kT, (uint64_t)h->num_sms * 16));
+  // counts (r1 - r0) go into `items` of a second pass: first the ranks
+  k_rank_prep<true><<<g1, kT, 0, st>>>(lo, hi, q, h->heads, h->data, h->used, h->L,
+                                       h->cfg.leaf_bytes, P, r0, r1, first, items, nullptr,
+                                       offsets);
+  CPMA_LAUNCHED(h);
+  CPMA_TRY(scan_u64_query(hm, offsets, offsets, q, st));
+  CPMA_TRY(scan_u64_query(hm, items, off, q, st));
+  prof_end(h, st);
+  if (!out || cap == 0) return check_cuda(cudaGetLastError());
+  ExtractArgs a;
+  a.r0 = r0;
+  a.r1 = r1;
+  a.q = q;
+  a.first = first;
+  a.item_off = off;
+  a.out_off = offsets;
+  a.P = P;
+  a.data = h->data;
+  a.used = h->used;
+  a.LB = h->cfg.leaf_bytes;
+  a.out = out;
+  a.cap = cap;
+  prof_begin(h, PH_RANGE, st);
+  k_extract<<<persistent_grid(h), kT, 0, st>>>(a);
   CPMA_LAUNCHED(h);
   prof_end(h, st);
   return check_cuda(cudaGetLastError());

@@ -172,3 +172,26 @@ def log_uniform_int(seed: int, count: int, lo: int, hi: int) -> np.ndarray:
     u = uniform01(seed, count)
     a, b = math.log10(lo), math.log10(hi + 1)
     return np.clip(np.floor(10.0 ** (a + (b - a) * u)), lo, hi).astype(np.int64)
+
+
+def rmat_edges(seed: int, scale: int, count: int, a: float = 0.57, b: float = 0.19,
+               c: float = 0.19, offset: int = 0):
+    """`count` directed edges of an R-MAT graph on 2^scale vertices
+    (Chakrabarti, Zhan, Faloutsos, "R-MAT: A recursive model for graph
+    mining", SDM 2004; Graph500 probabilities a = 0.57, b = c = 0.19): each
+    of the `scale` bit levels picks a quadrant with probabilities a, b, c,
+    1 - a - b - c.  Vertex ids are then scattered by a seeded bijection so
+    that high-degree vertices are not the small ids.  Returns (src, dst)
+    uint64 arrays; repeats and self loops are kept (an edge set drops
+    repeats)."""
+    if not 1 <= scale <= 31:
+        raise ValueError("scale must be in [1, 31]")
+    src = np.zeros(count, dtype=np.uint64)
+    dst = np.zeros(count, dtype=np.uint64)
+    for level in range(scale):
+        u = uniform01(seed * 64 + level, count, offset)
+        right = (u >= a) & (u < a + b) | (u >= a + b + c)   # dst bit
+        down = u >= a + b                                     # src bit
+        src = (src << np.uint64(1)) | down.astype(np.uint64)
+        dst = (dst << np.uint64(1)) | right.astype(np.uint64)
+    return mix_bits(src, scale, seed ^ 0x1234), mix_bits(dst, scale, seed ^ 0x1234)

@@ -420,3 +420,23 @@ def test_rebuild_threshold_matches_oracle(LB):
     with pytest.raises(cp.CPMAError):
         small.insert_batch(T(bad), sorted=True)
     assert small.size() == 2
+
+
+@pytest.mark.parametrize("LB", [256, 512, 2048])
+def test_range_extract_matches_oracle(LB):
+    base = np.concatenate([W.uniform_keys(54, 70000, bits=40), np.array([0, M64], np.uint64)])
+    g = cp.CPMA(T(base), leaf_bytes=LB)
+    p = oracle.PlainSet(base)
+    lo, hi, _ = W.range_queries_by_rank(p.S, 55, 700, 1, 30000)
+    lo = np.concatenate([lo, np.array([0, 0, 5, M64, M64 - 1, 9], np.uint64)])
+    hi = np.concatenate([hi, np.array([M64, 1, 5, M64, M64, 3], np.uint64)])
+    off, keys = g.range_extract(T(lo), T(hi))
+    woff, wkeys = p.range_extract(lo, hi)
+    assert np.array_equal(cp.to_u64(off), woff)
+    assert np.array_equal(cp.to_u64(keys), wkeys)
+    # counts agree with range_map
+    s, c = g.range_map(T(lo), T(hi))
+    assert np.array_equal(np.diff(cp.to_u64(off)), cp.to_u64(c))
+    # no queries
+    off, keys = g.range_extract(T(np.zeros(0, np.uint64)), T(np.zeros(0, np.uint64)))
+    assert cp.to_u64(off).tolist() == [0] and keys.numel() == 0

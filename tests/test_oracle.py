@@ -510,3 +510,28 @@ def test_rebuild_rule():
     assert e.insert_batch(base) == n
     for a, b in zip(e.layout(), oracle.SeqCPMA(base, leaf_bytes=512).layout()):
         assert np.array_equal(a, b)
+
+
+def test_range_extract_brute_force():
+    """range_map emitting the keys (offsets + packed keys) against a Python
+    filter; empty and inverted ranges, ranges past the ends."""
+    rng = random.Random(21)
+    S = sorted(set(rng.getrandbits(14) for _ in range(3000)) | {0, M64})
+    plain = oracle.PlainSet(S)
+    lo = [rng.getrandbits(14) for _ in range(100)] + [0, 5, M64, 9, M64 - 1]
+    hi = [a + rng.getrandbits(rng.choice([2, 8, 13])) for a in lo[:100]] + [M64, 5, M64, 3, M64]
+    off, keys = plain.range_extract(lo, hi)
+    want = [[x for x in S if a <= x < b] for a, b in zip(lo, hi)]
+    assert off.tolist() == [0] + list(np.cumsum([len(w) for w in want]))
+    assert keys.tolist() == [x for w in want for x in w]
+
+
+def test_rmat_generator_shape():
+    """R-MAT edges stay inside 2^scale vertices and are skewed: the busiest
+    source has far more edges than the average."""
+    from paper_2305_05055_gb300 import workloads as W
+    src, dst = W.rmat_edges(3, 12, 50000)
+    assert src.max() < 4096 and dst.max() < 4096
+    assert np.array_equal(W.rmat_edges(3, 12, 50000)[0], src)  # seeded
+    deg = np.bincount(src.astype(np.int64), minlength=4096)
+    assert deg.max() > 20 * deg.mean()
