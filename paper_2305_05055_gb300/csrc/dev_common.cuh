@@ -385,26 +385,39 @@ __device__ __forceinline__ void warp_span_sum(const uint8_t* __restrict__ data,
     uint64_t wacc = 0;
     bool bad = false;
     uint32_t cont_li = 0xFFFFFFFFu, cont_cnt = 0, cont_val = 0, cont_sh = 0;
-    for (uint32_t g0 = 0; g0 < NC; g0 += 32) {
+    // Chunk ci of the 32 leaves: its leaf slot (the number of leaves whose
+    // chunks end at or before ci), that leaf's first chunk, used bytes and
+    // count; the 16 bytes are loaded one step ahead of their use so the load
+    // of the next step overlaps the decode of this one.
+    struct Chunk { uint32_t li, lis, cstart, u, m; uint4 v; };
+    auto locate = [&](uint32_t g0, Chunk& k) {
       const uint32_t ci = g0 + lane;
-      const bool act = ci < NC;
-      // leaf slot of chunk ci: the number of leaves whose chunks end at or
-      // before ci
       uint32_t li = 0;
 #pragma unroll
       for (int stp = 16; stp >= 1; stp >>= 1) {
         const uint32_t v = __shfl_sync(FULL, cinc, li + stp - 1);
         if (v <= ci) li += stp;
       }
-      const uint32_t lis = min(li, 31u);
-      const uint32_t cstart = __shfl_sync(FULL, cinc, lis) - __shfl_sync(FULL, nc_i, lis);
-      const uint32_t u = __shfl_sync(FULL, u_i, lis);
-      const uint32_t m = __shfl_sync(FULL, m_i, lis);
+      k.li = li;
+      k.lis = min(li, 31u);
+      k.cstart = __shfl_sync(FULL, cinc, k.lis) - __shfl_sync(FULL, nc_i, k.lis);
+      k.u = __shfl_sync(FULL, u_i, k.lis);
+      k.m = __shfl_sync(FULL, m_i, k.lis);
+      k.v = make_uint4(0u, 0u, 0u, 0u);
+      if (ci < NC)
+        k.v = __ldg(reinterpret_cast<const uint4*>(data + (w0 + k.lis) * LB +
+                                                    (ci - k.cstart) * 16u));
+    };
+    Chunk cur, nxt;
+    if (NC) locate(0, cur);
+    for (uint32_t g0 = 0; g0 < NC; g0 += 32) {
+      if (g0 + 32 < NC) locate(g0 + 32, nxt);
+      const uint32_t ci = g0 + lane;
+      const bool act = ci < NC;
+      const uint32_t li = cur.li, cstart = cur.cstart, u = cur.u, m = cur.m;
       const uint32_t cw = ci - cstart;
       const uint32_t p0 = cw * 16u;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (act) v = __ldg(reinterpret_cast<const uint4*>(data + (w0 + lis) * LB + p0));
-      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+      const uint32_t w[4] = {cur.v.x, cur.v.y, cur.v.z, cur.v.w};
       const int b_lo = (cw == 0) ? 8 : 0;
       const int b_hi = act ? (int)min(16u, u - p0) : 0;
       LaneCodes lc;
@@ -442,6 +455,7 @@ __device__ __forceinline__ void warp_span_sum(const uint8_t* __restrict__ data,
       cont_cnt = __shfl_sync(FULL, B + c, 31);
       cont_val = __shfl_sync(FULL, lc.tail, 31);
       cont_sh = __shfl_sync(FULL, lc.tail_sh, 31);
+      cur = nxt;
     }
     if (__any_sync(FULL, bad)) {
       const uint64_t je = min(w0 + 32, j1);

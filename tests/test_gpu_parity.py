@@ -440,3 +440,20 @@ def test_range_extract_matches_oracle(LB):
     # no queries
     off, keys = g.range_extract(T(np.zeros(0, np.uint64)), T(np.zeros(0, np.uint64)))
     assert cp.to_u64(off).tolist() == [0] and keys.numel() == 0
+
+
+@pytest.mark.parametrize("LB", [512, 2048])
+def test_full_scan_large(LB):
+    """Full scan at 1e7 keys (every warp walks many 32-leaf groups with the
+    next group's chunks loaded ahead): sum and count against the plain set,
+    also after a skewed insert that leaves leaves of very different fill."""
+    keys = W.uniform_keys(71, 10 ** 7, bits=40)
+    g = cp.CPMA(T(keys), leaf_bytes=LB)
+    S = np.unique(keys)
+    s, c = g.sum()
+    assert int(cp.to_u64(s)[0]) == int(np.sum(S, dtype=np.uint64)) and int(c.item()) == S.size
+    ins = W.zipf_keys(72, 10 ** 6, bits=40)
+    g.insert_batch(T(ins))
+    S = np.union1d(S, ins)
+    s, c = g.sum()
+    assert int(cp.to_u64(s)[0]) == int(np.sum(S, dtype=np.uint64)) and int(c.item()) == S.size
