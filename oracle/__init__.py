@@ -72,7 +72,10 @@ def lib():
                 "o_build_leaves": (U64, [U64, U32, U32]),
                 "o_resize_leaves": (U64, [U64, U64, U32, U32, U32, U32, U32]),
                 "o_cut_points": (None, [u64p, S, U64, u64p]),
-                "ocpma_create": (I, [C.POINTER(V), U32, U32, U32, U32, U32, U32, U32, U32, u64p, U64]),
+                "ocpma_create": (I, [C.POINTER(V), U32, U32, U32, U32, U32, U32, U32, U32, U32,
+                                     u64p, U64]),
+                "o_raw_leaf_encode": (U64, [u8p, U32, u64p, S]),
+                "o_raw_leaf_decode": (S, [u8p, U64, u64p]),
                 "ocpma_destroy": (None, [V]),
                 "ocpma_set_rebuild": (None, [V, U32]),
                 "ocpma_insert": (I, [V, u64p, U64, C.POINTER(U64)]),
@@ -274,7 +277,7 @@ class PlainSet:
 # --------------------------------------------------------------------------
 
 DEFAULTS = dict(leaf_bytes=512, tau_leaf=900, tau_root=700, rho_leaf=100,
-                rho_root=300, grow_num=6, grow_den=5, build_pm=500, rebuild_pm=0)
+                rho_root=300, grow_num=6, grow_den=5, build_pm=500, rebuild_pm=0, codec=0)
 
 
 class OracleError(RuntimeError):
@@ -292,7 +295,7 @@ class SeqCPMA:
         h = C.c_void_p()
         rc = lib().ocpma_create(C.byref(h), c["leaf_bytes"], c["tau_leaf"],
                                 c["tau_root"], c["rho_leaf"], c["rho_root"],
-                                c["grow_num"], c["grow_den"], c["build_pm"],
+                                c["grow_num"], c["grow_den"], c["build_pm"], c["codec"],
                                 k if k.size else np.zeros(1, np.uint64), k.size)
         if rc != 0:
             raise OracleError("ocpma_create failed: %d" % rc)

@@ -41,6 +41,11 @@
  *      (tau_leaf - tau_root) h/H, lower rho_h = rho_leaf + (rho_root -
  *      rho_leaf) h/H, in permille, tested in exact 128-bit integers; with
  *      L == 1 only the upper root bound applies.
+ *   R16 uncompressed PMA (Sec. 3 PMA; the compression ablation of Sec. 6):
+ *      codec 1 stores every element in an 8-byte little-endian cell, packed
+ *      left; costs are 8 per element, so byte-balanced cut points are
+ *      element-balanced; everything else (bounds, routing, counting,
+ *      resizing) is the same batch algorithm.
  *   R5 routing (Sec. 4 batch merge search, Sec. 5 point queries): a key goes
  *      to the last leaf whose head-index entry is <= key, else leaf 0; an
  *      empty leaf's head-index entry is the head of the next non-empty leaf,
@@ -261,6 +266,27 @@ size_t o_leaf_decode(const uint8_t* leaf, uint64_t used, uint64_t* out) {
   return m;
 }
 
+/* R16, the uncompressed PMA of Sec. 3 as a leaf format: every element in an
+ * 8-byte little-endian cell, packed left (the head is cell 0). */
+uint64_t o_raw_leaf_bytes(size_t m) { return 8 * (uint64_t)m; }
+
+uint64_t o_raw_leaf_encode(uint8_t* leaf, uint32_t LB, const uint64_t* e, size_t m) {
+  memset(leaf, 0, LB);
+  for (size_t i = 0; i < m; i++)
+    for (int t = 0; t < 8; t++) leaf[8 * i + t] = (uint8_t)(e[i] >> (8 * t));
+  return 8 * (uint64_t)m;
+}
+
+size_t o_raw_leaf_decode(const uint8_t* leaf, uint64_t used, uint64_t* out) {
+  size_t m = (size_t)(used / 8);
+  for (size_t i = 0; i < m; i++) {
+    uint64_t v = 0;
+    for (int t = 0; t < 8; t++) v |= (uint64_t)leaf[8 * i + t] << (8 * t);
+    out[i] = v;
+  }
+  return m;
+}
+
 /* ------------------------------------------------------------------------ */
 /* 3. Sequential CPMA                                                       */
 /* ------------------------------------------------------------------------ */
@@ -276,6 +302,7 @@ typedef struct {
   uint64_t* head;  /* L: head-index entry (R5) */
   uint64_t n;
   uint32_t rebuild_pm; /* R14: 0 = never */
+  uint32_t codec;      /* R16: 0 = byte codes (CPMA), 1 = 8-byte cells (PMA) */
   /* diagnostics of the last batch, for invariant tests */
   uint64_t last_resized, last_nwindows, last_touched;
   uint64_t* last_win;   /* pairs (first leaf, leaf count) */
@@ -332,12 +359,24 @@ uint64_t o_resize_leaves(uint64_t T, uint64_t L, uint32_t LB,
   return Lp;
 }
 
+/* Leaf format of this instance (R1/R2 byte codes, or R16 cells). */
+static uint64_t leaf_bytes(const ocpma* o, const uint64_t* e, size_t m) {
+  return o->codec ? o_raw_leaf_bytes(m) : o_leaf_bytes(e, m);
+}
+static uint64_t leaf_encode(const ocpma* o, uint8_t* leaf, const uint64_t* e, size_t m) {
+  return o->codec ? o_raw_leaf_encode(leaf, o->LB, e, m) : o_leaf_encode(leaf, o->LB, e, m);
+}
+static size_t leaf_decode(const ocpma* o, const uint8_t* leaf, uint64_t used, uint64_t* out) {
+  return o->codec ? o_raw_leaf_decode(leaf, used, out) : o_leaf_decode(leaf, used, out);
+}
+
 /* R8: cut points.  starts[w] for w in [0, W], starts[W] = m. */
-void o_cut_points(const uint64_t* e, size_t m, uint64_t W, uint64_t* starts) {
+static void cut_points(uint32_t codec, const uint64_t* e, size_t m, uint64_t W,
+                       uint64_t* starts) {
   uint64_t* C = (uint64_t*)malloc((m + 1) * sizeof(uint64_t));
   C[0] = 0;
-  for (size_t i = 0; i < m; i++)
-    C[i + 1] = C[i] + (i == 0 ? 8 : o_leb_len(e[i] - e[i - 1]));
+  for (size_t i = 0; i < m; i++)  /* cost of e[i] in a leaf: head or code (R8), cell (R16) */
+    C[i + 1] = C[i] + ((i == 0 || codec) ? 8 : o_leb_len(e[i] - e[i - 1]));
   uint64_t S = C[m];
   for (uint64_t w = 0; w < W; w++) {
     uint64_t theta = (uint64_t)((u128)w * S / W);
@@ -347,18 +386,24 @@ void o_cut_points(const uint64_t* e, size_t m, uint64_t W, uint64_t* starts) {
   free(C);
 }
 
+void o_cut_points(const uint64_t* e, size_t m, uint64_t W, uint64_t* starts) {
+  cut_points(0, e, m, W, starts);
+}
+
 /* Redistribute e[0..m) over leaves [first, first+W) of the arrays given.
  * Returns OK or E_FIT. */
-static int spread(uint8_t* data, uint32_t* used, uint64_t* head, uint32_t LB,
+static int spread(uint32_t codec, uint8_t* data, uint32_t* used, uint64_t* head, uint32_t LB,
                   uint64_t first, uint64_t W, const uint64_t* e, size_t m) {
   uint64_t* s = (uint64_t*)malloc((W + 1) * sizeof(uint64_t));
-  o_cut_points(e, m, W, s);
+  cut_points(codec, e, m, W, s);
   int rc = OK;
   for (uint64_t w = 0; w < W; w++) {
     uint64_t j = first + w;
     size_t a = s[w], b = s[w + 1];
-    if (o_leaf_bytes(e + a, b - a) > LB) { rc = E_FIT; break; }
-    used[j] = (uint32_t)o_leaf_encode(data + j * LB, LB, e + a, b - a);
+    const uint64_t nb = codec ? o_raw_leaf_bytes(b - a) : o_leaf_bytes(e + a, b - a);
+    if (nb > LB) { rc = E_FIT; break; }
+    used[j] = (uint32_t)(codec ? o_raw_leaf_encode(data + j * LB, LB, e + a, b - a)
+                               : o_leaf_encode(data + j * LB, LB, e + a, b - a));
     head[j] = (b > a) ? e[a] : UINT64_MAX;
   }
   free(s);
@@ -409,8 +454,9 @@ void ocpma_destroy(ocpma* o) {
 int ocpma_create(ocpma** out, uint32_t LB, uint32_t tau_leaf,
                  uint32_t tau_root, uint32_t rho_leaf, uint32_t rho_root,
                  uint32_t grow_num, uint32_t grow_den, uint32_t build_pm,
-                 const uint64_t* keys, uint64_t k) {
+                 uint32_t codec, const uint64_t* keys, uint64_t k) {
   *out = NULL;
+  if (codec > 1) return E_INVAL;
   if (LB < 64 || LB % 16 || !(rho_leaf <= rho_root && rho_root < tau_root &&
                                tau_root <= tau_leaf && tau_leaf < 1000) ||
       grow_num <= grow_den || grow_den == 0 ||
@@ -421,14 +467,15 @@ int ocpma_create(ocpma** out, uint32_t LB, uint32_t tau_leaf,
   o->LB = LB; o->tau_leaf = tau_leaf; o->tau_root = tau_root;
   o->rho_leaf = rho_leaf; o->rho_root = rho_root;
   o->grow_num = grow_num; o->grow_den = grow_den; o->build_pm = build_pm;
+  o->codec = codec;
   uint64_t* e = (uint64_t*)malloc((k ? k : 1) * sizeof(uint64_t));
   memcpy(e, keys, k * sizeof(uint64_t));
   size_t m = oset_sort_unique(e, k);
-  uint64_t L = o_build_leaves(o_leaf_bytes(e, m), LB, build_pm);
+  uint64_t L = o_build_leaves(leaf_bytes(o, e, m), LB, build_pm);
   int rc = alloc_arrays(L, LB, &o->data, &o->used, &o->head);
   if (rc == OK) {
     o->L = L;
-    rc = spread(o->data, o->used, o->head, LB, 0, L, e, m);
+    rc = spread(o->codec, o->data, o->used, o->head, LB, 0, L, e, m);
     fix_empty_heads(o);
     o->n = m;
   }
@@ -454,7 +501,7 @@ static size_t leaf_content(const ocpma* o, const touched_t* T, size_t nT,
     return t->m;
   }
   (void)nT;
-  return o_leaf_decode(o->data + j * o->LB, o->used[j], out);
+  return leaf_decode(o, o->data + j * o->LB, o->used[j], out);
 }
 
 /* R14 (Sec. 4: for a batch of k >= n/10 keys the best strategy is to rebuild
@@ -469,7 +516,7 @@ static int rebuild(ocpma* o, const uint64_t* keys, uint64_t k, int is_delete, ui
   uint64_t* S = (uint64_t*)malloc((o->n + 1) * sizeof(uint64_t));
   size_t m = 0;
   for (uint64_t j = 0; j < o->L; j++)
-    m += o_leaf_decode(o->data + j * LB, o->used[j], S + m);
+    m += leaf_decode(o, o->data + j * LB, o->used[j], S + m);
   uint64_t* U = (uint64_t*)malloc((k ? k : 1) * sizeof(uint64_t));
   memcpy(U, keys, k * sizeof(uint64_t));
   size_t ku = oset_sort_unique(U, k);
@@ -478,12 +525,12 @@ static int rebuild(ocpma* o, const uint64_t* keys, uint64_t k, int is_delete, ui
   *delta = is_delete ? (uint64_t)(m - mn) : (uint64_t)(mn - m);
   free(S);
   free(U);
-  uint64_t L = o_build_leaves(o_leaf_bytes(e, mn), LB, o->build_pm);
+  uint64_t L = o_build_leaves(leaf_bytes(o, e, mn), LB, o->build_pm);
   uint8_t* d;
   uint32_t* u;
   uint64_t* h;
   int rc = alloc_arrays(L, LB, &d, &u, &h);
-  if (rc == OK) rc = spread(d, u, h, LB, 0, L, e, mn);
+  if (rc == OK) rc = spread(o->codec, d, u, h, LB, 0, L, e, mn);
   free(e);
   if (rc != OK) return rc;
   free(o->data); free(o->used); free(o->head);
@@ -523,13 +570,13 @@ static int update(ocpma* o, const uint64_t* keys, uint64_t k, int is_delete,
     size_t b = i;
     while (i < ku && route(o, U[i]) == j) i++;
     size_t s = i - b;
-    size_t m = o_leaf_decode(o->data + j * LB, o->used[j], old);
+    size_t m = leaf_decode(o, o->data + j * LB, o->used[j], old);
     uint64_t* e = (uint64_t*)malloc((m + s + 1) * sizeof(uint64_t));
     size_t mn = is_delete ? oset_difference(old, m, U + b, s, e)
                           : oset_union(old, m, U + b, s, e);
     if (mn == m) { free(e); continue; }   /* content unchanged: untouched */
     T[nT].leaf = j; T[nT].e = e; T[nT].m = mn;
-    T[nT].bytes = o_leaf_bytes(e, mn);
+    T[nT].bytes = leaf_bytes(o, e, mn);
     tidx[j] = (int64_t)nT;
     *delta += is_delete ? (uint64_t)(m - mn) : (uint64_t)(mn - m);
     nT++;
@@ -550,7 +597,7 @@ static int update(ocpma* o, const uint64_t* keys, uint64_t k, int is_delete,
     uint64_t j = T[t].leaf;
     if (!violates(o, H, 0, 1, bytes[j])) {
       /* within its own bounds: rewrite the leaf in place */
-      o->used[j] = (uint32_t)o_leaf_encode(o->data + j * LB, LB, T[t].e,
+      o->used[j] = (uint32_t)leaf_encode(o, o->data + j * LB, T[t].e,
                                            T[t].m);
       o->head[j] = T[t].m ? T[t].e[0] : UINT64_MAX;
       continue;
@@ -585,7 +632,7 @@ static int update(ocpma* o, const uint64_t* keys, uint64_t k, int is_delete,
     uint8_t* nd; uint32_t* nu; uint64_t* nh;
     rc = alloc_arrays(Lp, LB, &nd, &nu, &nh);
     if (rc == OK) {
-      rc = spread(nd, nu, nh, LB, 0, Lp, buf, m);
+      rc = spread(o->codec, nd, nu, nh, LB, 0, Lp, buf, m);
       free(o->data); free(o->used); free(o->head);
       o->data = nd; o->used = nu; o->head = nh; o->L = Lp;
     }
@@ -619,7 +666,7 @@ static int update(ocpma* o, const uint64_t* keys, uint64_t k, int is_delete,
       uint64_t* e = (uint64_t*)malloc((cap + 1) * sizeof(uint64_t));
       size_t m = 0;
       for (uint64_t j = a; j < a + W; j++) m += leaf_content(o, T, nT, tidx, j, e + m);
-      rc = spread(o->data, o->used, o->head, LB, a, W, e, m);
+      rc = spread(o->codec, o->data, o->used, o->head, LB, a, W, e, m);
       free(e);
     }
   }
@@ -649,7 +696,7 @@ int ocpma_delete(ocpma* o, const uint64_t* keys, uint64_t k,
 int ocpma_has(const ocpma* o, uint64_t x) {
   uint64_t j = route(o, x);
   uint64_t* e = (uint64_t*)malloc((o->LB + 1) * sizeof(uint64_t));
-  size_t m = o_leaf_decode(o->data + j * o->LB, o->used[j], e);
+  size_t m = leaf_decode(o, o->data + j * o->LB, o->used[j], e);
   int r = oset_has(e, m, x);
   free(e);
   return r;
@@ -663,7 +710,7 @@ void ocpma_range(const ocpma* o, uint64_t lo, uint64_t hi, uint64_t* sum,
     uint64_t* e = (uint64_t*)malloc((o->LB + 1) * sizeof(uint64_t));
     for (uint64_t j = route(o, lo); j < o->L; j++) {
       if (o->used[j] && o->head[j] >= hi) break;
-      size_t m = o_leaf_decode(o->data + j * o->LB, o->used[j], e);
+      size_t m = leaf_decode(o, o->data + j * o->LB, o->used[j], e);
       for (size_t t = 0; t < m; t++)
         if (e[t] >= lo && e[t] < hi) { s += e[t]; c++; }
     }
@@ -678,7 +725,7 @@ uint64_t ocpma_sum(const ocpma* o) {
   uint64_t s = 0;
   uint64_t* e = (uint64_t*)malloc((o->LB + 1) * sizeof(uint64_t));
   for (uint64_t j = 0; j < o->L; j++) {
-    size_t m = o_leaf_decode(o->data + j * o->LB, o->used[j], e);
+    size_t m = leaf_decode(o, o->data + j * o->LB, o->used[j], e);
     for (size_t t = 0; t < m; t++) s += e[t];
   }
   free(e);
@@ -693,7 +740,7 @@ uint64_t ocpma_bytes(const ocpma* o) { return o->L * ((uint64_t)o->LB + 16); }
 uint64_t ocpma_elements(const ocpma* o, uint64_t* out) {
   uint64_t m = 0;
   for (uint64_t j = 0; j < o->L; j++)
-    m += o_leaf_decode(o->data + j * o->LB, o->used[j], out + m);
+    m += leaf_decode(o, o->data + j * o->LB, o->used[j], out + m);
   return m;
 }
 
@@ -730,9 +777,9 @@ int ocpma_check(const ocpma* o) {
     for (uint64_t t = u; t < o->LB; t++)
       if (leaf[t]) { rc = 3; break; }                 /* packed left */
     if (rc) break;
-    size_t m = o_leaf_decode(leaf, u, e);
+    size_t m = leaf_decode(o, leaf, u, e);
     /* the decode consumed exactly `used` bytes: re-encoding gives u back */
-    if (o_leaf_bytes(e, m) != u) { rc = 4; break; }
+    if (leaf_bytes(o, e, m) != u) { rc = 4; break; }
     for (size_t t = 0; t < m; t++) {
       if (have_prev && e[t] <= prev) { rc = 5; break; } /* strictly sorted */
       prev = e[t]; have_prev = 1;

@@ -535,3 +535,69 @@ def test_rmat_generator_shape():
     assert np.array_equal(W.rmat_edges(3, 12, 50000)[0], src)  # seeded
     deg = np.bincount(src.astype(np.int64), minlength=4096)
     assert deg.max() > 20 * deg.mean()
+
+
+# --------------------------------------------------------------------------
+# uncompressed PMA (reading R16): 8-byte cells, same batch algorithm
+# --------------------------------------------------------------------------
+
+def test_raw_cells_are_little_endian_values():
+    e = np.array([5, 300, 1 << 40, M64 - 1], dtype=np.uint64)
+    buf = np.zeros(64, dtype=np.uint8)
+    used = oracle.lib().o_raw_leaf_encode(buf, 64, e, e.size)
+    assert used == 32
+    want = b"".join(int(x).to_bytes(8, "little") for x in e.tolist())
+    assert bytes(buf[:32]) == want and not buf[32:].any()
+    out = np.zeros(8, dtype=np.uint64)
+    assert oracle.lib().o_raw_leaf_decode(buf, used, out) == 4
+    assert out[:4].tolist() == e.tolist()
+
+
+def test_pma_build_by_hand():
+    """40 keys, LB 256, build density 500: S = 40 * 8 = 320 bytes, L =
+    ceil(1000 * 320 / (500 * 256 - 8000)) = ceil(2.67) = 3.  Element costs
+    are all 8, so leaf w starts at the first i with 8 i >= floor(w * 320 / 3):
+    i = 14 (>= 106) and i = 27 (>= 213); leaves hold 14, 13, 13 elements.
+    An insert into leaf 1 (well within 0.9 * 256 bytes) rewrites it in
+    place with 14 cells."""
+    keys = [10 * i + 3 for i in range(40)]
+    o = oracle.SeqCPMA(keys, leaf_bytes=256, codec=1)
+    data, used, head = o.layout()
+    assert list(used) == [112, 104, 104]
+    assert list(head) == [keys[0], keys[14], keys[27]]
+    raw = b"".join(int(x).to_bytes(8, "little") for x in keys[14:27])
+    assert bytes(data[256:256 + 104]) == raw
+    assert o.insert_batch([145]) == 1  # between 143 (keys[14]) and 153
+    data, used, head = o.layout()
+    assert list(used) == [112, 112, 104]
+    cells = sorted(keys[14:27] + [145])
+    assert bytes(data[256:256 + 112]) == b"".join(int(x).to_bytes(8, "little") for x in cells)
+    assert o.check() == 0
+
+
+@pytest.mark.parametrize("LB", [256, 1024])
+def test_pma_vs_plain_set(LB):
+    rng = random.Random(LB + 7)
+    base = [rng.getrandbits(24) for _ in range(4000)] + [0, M64]
+    o = oracle.SeqCPMA(base, leaf_bytes=LB, codec=1)
+    p = oracle.PlainSet(base)
+    for step in range(30):
+        if rng.random() < 0.6:
+            keys = [rng.getrandbits(rng.choice([24, 64])) for _ in range(rng.choice([1, 30, 2000]))]
+            assert o.insert_batch(keys) == p.insert_batch(keys)
+        else:
+            S = p.S.tolist()
+            keys = [S[rng.randrange(len(S))] for _ in range(rng.choice([1, 50, len(S) // 2]))]
+            assert o.delete_batch(keys) == p.delete_batch(keys)
+        assert o.elements().tolist() == p.S.tolist()
+        assert o.check() == 0
+    q = [rng.getrandbits(24) for _ in range(100)] + [0, M64]
+    assert o.has_batch(q).tolist() == p.has_batch(q).tolist()
+    lo = [rng.getrandbits(24) for _ in range(50)]
+    hi = [a + rng.getrandbits(18) for a in lo]
+    s1, c1 = o.range_map(lo, hi)
+    s2, c2 = p.range_map(lo, hi)
+    assert np.array_equal(s1, s2) and np.array_equal(c1, c2)
+    # 8 bytes per key over the leaves, so more leaves than the CPMA of the same set
+    cp_ = oracle.SeqCPMA(p.S, leaf_bytes=LB)
+    assert o.leaves() > cp_.leaves()
