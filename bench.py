@@ -96,6 +96,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="headline only")
     ap.add_argument("--no-sweep", action="store_true", help="skip the insert/delete sweep 1e3..1e7")
     ap.add_argument("--no-graph", action="store_true", help="skip the R-MAT edge-set workload")
+    ap.add_argument("--no-pma", action="store_true", help="skip the uncompressed-PMA ablation")
     ap.add_argument("--graph-scale", type=int, default=20)
     ap.add_argument("--sweep-trials", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -508,6 +509,8 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
         out["skew"] = skew(a, dev, T, timed)
     if not a.no_graph:
         out["graph"] = graph_workload(a, dev, timed)
+    if not a.no_pma:
+        out["pma_ablation"] = pma_ablation(a, dev, lo, hi, timed)
     if not a.no_serve:
         out["serve"] = serving(a, g, S_host)
     return out
@@ -552,6 +555,50 @@ def serving(a, g, S):
             "throughput_ratio": head["served"]["requests_per_s"] /
                                 head["one_at_a_time"]["requests_per_s"],
             "saturation_ratio": sat_served / sat_plain}
+
+
+def pma_ablation(a, dev, lo, hi, timed):
+    """The compression ablation (Sec. 6: the CPMA against the uncompressed
+    PMA under the same batch algorithm): the same 1e8 uniform keys as an
+    uncompressed PMA (codec 1, 8-byte cells) and as the CPMA; bytes per key,
+    a 1e6-key insert and delete on warmed clones, range_map over the headline
+    queries and a full scan."""
+    import torch
+    from paper_2305_05055_gb300 import cpma as cp
+    from paper_2305_05055_gb300 import workloads as W
+    T = lambda x: torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).to(dev)
+    base = T(W.uniform_keys(2, int(a.n), bits=40))
+    b = T(W.uniform_keys(808, 10 ** 6, bits=40))
+    w = T(W.uniform_keys(809, 10 ** 6, bits=40))
+    out = {}
+    for name, codec in (("cpma", 0), ("pma", 1)):
+        g = cp.CPMA(base, leaf_bytes=a.leaf_bytes, codec=codec)
+        ins, dele = [], []
+        for _ in range(3):
+            c = g.clone()
+            c.reserve(10 ** 6)
+            c.insert_batch(w)
+            c.delete_batch(w)
+            flush = flush_l2(dev)
+            ms_i, _ = timed(lambda: c.insert_batch(b))
+            flush = flush_l2(dev)
+            ms_d, _ = timed(lambda: c.delete_batch(b))
+            del flush, c
+            ins.append(ms_i)
+            dele.append(ms_d)
+        ms_r, (s_, cnt) = timed(lambda: g.range_map(lo, hi), reps=3)
+        ms_s, (s2, c2) = timed(lambda: g.sum(), reps=5)
+        out[name] = {"bytes_per_key": g.bytes() / g.size(), "leaves": g.leaves(),
+                     "insert_keys_per_s": 10 ** 6 / (statistics.median(ins) / 1e3),
+                     "delete_keys_per_s": 10 ** 6 / (statistics.median(dele) / 1e3),
+                     "range_elems_per_s": int(cnt.sum().item()) / (ms_r / 1e3),
+                     "range_ms": ms_r,
+                     "scan_elems_per_s": int(c2.item()) / (ms_s / 1e3),
+                     "scan_ms": ms_s, "range_sum_check": int(s_.sum().item())}
+        del g
+        torch.cuda.synchronize()
+    out["same_range_sums"] = out["cpma"].pop("range_sum_check") == out["pma"].pop("range_sum_check")
+    return out
 
 
 def graph_workload(a, dev, timed):

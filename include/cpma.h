@@ -69,7 +69,10 @@ enum {
  * given) into a set of n keys with 1000 k >= rebuild_pm * n is applied by
  * merging it with all the keys and building the result like cpma_create
  * (layout included); other batches take the batch-merge path.  0 = never
- * (default). */
+ * (default).
+ * codec 1 keeps every key in an 8-byte little-endian cell, packed left,
+ * under the same batch algorithm (bounds, routing, counting, resizing): the
+ * uncompressed PMA, for measuring what the compression buys. */
 typedef struct {
   uint32_t leaf_bytes; /* LB; default 512 */
   uint32_t tau_leaf;   /* default 900 */
@@ -80,6 +83,8 @@ typedef struct {
   uint32_t grow_den;
   uint32_t build_pm;   /* fill density of cpma_create; default 500 */
   uint32_t rebuild_pm; /* batch-to-set ratio that rebuilds; default 0 = never */
+  uint32_t codec;      /* leaf format: 0 = byte codes (the CPMA, default),
+                          1 = 8-byte cells (the uncompressed PMA of Sec. 3) */
 } cpma_config;
 
 /* Fill *cfg with the defaults above. */

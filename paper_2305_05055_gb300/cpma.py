@@ -35,7 +35,7 @@ class CPMAError(RuntimeError):
 class cpma_config(C.Structure):
     _fields_ = [(n, C.c_uint32) for n in (
         "leaf_bytes", "tau_leaf", "tau_root", "rho_leaf", "rho_root", "grow_num",
-        "grow_den", "build_pm", "rebuild_pm")]
+        "grow_den", "build_pm", "rebuild_pm", "codec")]
 
 
 def lib():

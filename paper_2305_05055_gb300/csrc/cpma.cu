@@ -136,6 +136,7 @@ int validate(const cpma_config& c) {
     return CPMA_EINVAL;
   if ((uint64_t)(1000 - c.tau_leaf) * c.leaf_bytes < 20000) return CPMA_EINVAL;
   if (c.grow_den == 0 || c.grow_num <= c.grow_den) return CPMA_EINVAL;
+  if (c.codec > 1) return CPMA_EINVAL;
   if ((uint64_t)c.build_pm * c.leaf_bytes <= 8000 || c.build_pm > c.tau_root) return CPMA_EINVAL;
   return CPMA_OK;
 }
@@ -219,6 +220,7 @@ void cpma_default_config(cpma_config* c) {
   c->grow_den = 5;
   c->build_pm = 500;
   c->rebuild_pm = 0;
+  c->codec = 0;
 }
 
 int cpma_create(cpma_t** out, const cpma_config* cfg, const uint64_t* d_keys, uint64_t n,

@@ -202,24 +202,50 @@ __device__ __forceinline__ uint32_t warp_decode_impl(const uint8_t* __restrict__
   return base_idx;
 }
 
+// The uncompressed format (8-byte cells, codec 1): lane l reads two cells of
+// every 512-byte step; f sees the same (index, value[, last byte]) calls.
+template <bool WITH_POS, class F>
+__device__ __forceinline__ uint32_t warp_decode_cells(const uint8_t* __restrict__ leaf,
+                                                      uint32_t used, F&& f) {
+  const unsigned lane = lane_id();
+  for (uint32_t p0 = lane * 16u; p0 < used; p0 += 512) {
+    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(leaf + p0));
+    const uint32_t i = p0 >> 3;
+    if constexpr (WITH_POS) f(i, (uint64_t)v.x, p0 + 7u);
+    else f(i, (uint64_t)v.x);
+    if (p0 + 8 < used) {
+      if constexpr (WITH_POS) f(i + 1, (uint64_t)v.y, p0 + 15u);
+      else f(i + 1, (uint64_t)v.y);
+    }
+  }
+  return used >> 3;
+}
+
+// raw: the leaf holds 8-byte cells (codec 1) instead of byte codes.
 template <class F>
 __device__ __forceinline__ uint32_t warp_decode(const uint8_t* __restrict__ leaf, uint32_t used,
-                                                F&& f) {
-  return warp_decode_impl<false>(leaf, used, f);
+                                                F&& f, bool raw = false) {
+  return raw ? warp_decode_cells<false>(leaf, used, f) : warp_decode_impl<false>(leaf, used, f);
 }
 
 template <class F>
 __device__ __forceinline__ uint32_t warp_decode_pos(const uint8_t* __restrict__ leaf,
-                                                    uint32_t used, F&& f) {
-  return warp_decode_impl<true>(leaf, used, f);
+                                                    uint32_t used, F&& f, bool raw = false) {
+  return raw ? warp_decode_cells<true>(leaf, used, f) : warp_decode_impl<true>(leaf, used, f);
 }
 
 // Encodes z[0..r) (shared memory) into buf (shared, zeroed, 8-byte aligned):
 // head as 8 little-endian bytes, then one code per following delta.  Returns
 // the used byte count (0 when r == 0).  The caller guarantees it fits.
-__device__ __forceinline__ uint32_t warp_encode(const uint64_t* z, uint32_t r, uint8_t* buf) {
+__device__ __forceinline__ uint32_t warp_encode(const uint64_t* z, uint32_t r, uint8_t* buf,
+                                               bool raw = false) {
   if (r == 0) return 0;
   const unsigned lane = lane_id();
+  if (raw) {  // codec 1: one 8-byte cell per element
+    for (uint32_t i = lane; i < r; i += 32) reinterpret_cast<uint64_t*>(buf)[i] = z[i];
+    __syncwarp();
+    return 8 * r;
+  }
   if (lane == 0) *reinterpret_cast<uint64_t*>(buf) = z[0];
   uint32_t pos = 8;
   for (uint32_t c0 = 1; c0 < r; c0 += 32) {
@@ -235,9 +261,10 @@ __device__ __forceinline__ uint32_t warp_encode(const uint64_t* z, uint32_t r, u
   return pos;
 }
 
-// Byte cost of z[i] in a stream: 8 for the first element, else its code.
-__device__ __forceinline__ uint32_t elem_cost(const uint64_t* z, uint32_t i) {
-  return i == 0 ? 8u : leb_len(z[i] - z[i - 1]);
+// Byte cost of z[i] in a stream: 8 for the first element, else its code
+// (8 for every element of the uncompressed format).
+__device__ __forceinline__ uint32_t elem_cost(const uint64_t* z, uint32_t i, bool raw = false) {
+  return (i == 0 || raw) ? 8u : leb_len(z[i] - z[i - 1]);
 }
 
 // ---------------------------------------------------------------------------
@@ -370,8 +397,19 @@ __device__ __forceinline__ void warp_span_sum(const uint8_t* __restrict__ data,
                                               const uint32_t* __restrict__ used,
                                               const uint32_t* __restrict__ cnt, uint32_t LB,
                                               uint64_t j0, uint64_t j1, uint64_t& acc,
-                                              uint64_t& cacc, ull& nbytes) {
+                                              uint64_t& cacc, ull& nbytes, bool raw = false) {
   const unsigned lane = lane_id();
+  if (raw) {  // codec 1: add the cells, 16 bytes per lane
+    for (uint64_t j = j0; j < j1; j++) {
+      const uint32_t u = min(__ldg(used + j), LB);
+      if (lane == 0) { cacc += __ldg(cnt + j); nbytes += u; }
+      for (uint32_t p0 = lane * 16u; p0 < u; p0 += 512) {
+        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(data + j * LB + p0));
+        acc += v.x + (p0 + 8 < u ? v.y : 0ull);
+      }
+    }
+    return;
+  }
   for (uint64_t w0 = j0; w0 < j1; w0 += 32) {
     const uint64_t jj = w0 + lane;
     const bool lv = jj < j1;

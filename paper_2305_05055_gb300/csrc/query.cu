@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kT) k_has(const uint64_t* __restrict__ keys, u
                                             const uint32_t* __restrict__ used,
                                             const uint64_t* __restrict__ heads, uint64_t L,
                                             uint32_t LB, uint8_t* __restrict__ out,
-                                            ull* prof) {
+                                            ull* prof, int raw) {
   const unsigned lane = lane_id();
   const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
   ull nbytes = 0;
@@ -70,7 +70,11 @@ __global__ void __launch_bounds__(kT) k_has(const uint64_t* __restrict__ keys, u
       const uint8_t* leaf = data + j * LB;
       nbytes += u + 9;
       bool found = false;
-      if (u > 0) {
+      if (raw) {  // codec 1: compare the cells
+        bool f = false;
+        warp_decode(leaf, u, [&](uint32_t, uint64_t val) { f |= (val == x); }, true);
+        found = __any_sync(FULL, f);
+      } else if (u > 0) {
         const uint32_t p0 = lane * 16u;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (p0 < u) v = __ldg(reinterpret_cast<const uint4*>(leaf + p0));
@@ -143,6 +147,7 @@ struct RangeArgs {
   uint64_t* count;
   ull* prof;  // profiling: leaf bytes scanned (nullable)
   const uint64_t* P = nullptr;  // rank mode: elements before each leaf (L + 1)
+  int raw = 0;                  // leaves hold 8-byte cells (codec 1)
 };
 
 __global__ void __launch_bounds__(kT) k_range_prep(const uint64_t* __restrict__ lo,
@@ -172,10 +177,11 @@ __global__ void __launch_bounds__(kT) k_range_prep(const uint64_t* __restrict__ 
 __device__ __forceinline__ uint64_t rank_of(uint64_t x, const uint64_t* __restrict__ heads,
                                             const uint8_t* __restrict__ data,
                                             const uint32_t* __restrict__ used, uint64_t L,
-                                            uint32_t LB, const uint64_t* __restrict__ P) {
+                                            uint32_t LB, const uint64_t* __restrict__ P, int raw) {
   const uint64_t j = route_leaf(heads, L, x);
   uint32_t below = 0;
-  warp_decode(data + j * LB, min(used[j], LB), [&](uint32_t, uint64_t v) { below += v < x; });
+  warp_decode(data + j * LB, min(used[j], LB), [&](uint32_t, uint64_t v) { below += v < x; },
+              raw);
   return P[j] + warp_sum(below);
 }
 
@@ -195,15 +201,15 @@ __global__ void __launch_bounds__(kT) k_rank_prep(const uint64_t* __restrict__ A
                                                   uint64_t* __restrict__ first,
                                                   uint64_t* __restrict__ items,
                                                   uint64_t* __restrict__ sum,
-                                                  uint64_t* __restrict__ count) {
+                                                  uint64_t* __restrict__ count, int raw) {
   const unsigned lane = lane_id();
   const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
   const uint64_t n = P[L];
   for (uint64_t i = gw; i < q; i += nw) {
     const uint64_t a = A[i], b = B[i];
-    const uint64_t r0 = rank_of(a, heads, data, used, L, LB, P);
+    const uint64_t r0 = rank_of(a, heads, data, used, L, LB, P, raw);
     uint64_t r1;
-    if constexpr (KEYS) r1 = a < b ? rank_of(b, heads, data, used, L, LB, P) : r0;
+    if constexpr (KEYS) r1 = a < b ? rank_of(b, heads, data, used, L, LB, P, raw) : r0;
     else r1 = (b >= n - r0) ? n : r0 + b;
     uint64_t f = 0, it = 0;
     if (r1 > r0) {
@@ -237,6 +243,7 @@ struct ExtractArgs {
   uint32_t LB;
   uint64_t* out;
   uint64_t cap;
+  int raw;
 };
 
 __global__ void __launch_bounds__(kT) k_extract(ExtractArgs a) {
@@ -252,7 +259,7 @@ __global__ void __launch_bounds__(kT) k_extract(ExtractArgs a) {
     warp_decode(a.data + j * a.LB, min(a.used[j], a.LB), [&](uint32_t idx, uint64_t v) {
       const uint64_t r = base + idx;
       if (r >= r0 && r < r1 && o + (r - r0) < a.cap) a.out[o + (r - r0)] = v;
-    });
+    }, a.raw);
   }
 }
 
@@ -308,7 +315,7 @@ __global__ void __launch_bounds__(kT) k_range_reduce(RangeArgs a, uint64_t mask,
     const uint64_t j = fl + (g - qoff);
     warp_decode(a.data + j * a.LB, min(a.used[j], a.LB), [&](uint32_t, uint64_t v) {
       if (v >= lo && v < hi && (v & mask) == value) { r = op_apply<OP>(r, v); c++; }
-    });
+    }, a.raw);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) r = op_apply<OP>(r, __shfl_xor_sync(FULL, r, o));
@@ -354,7 +361,8 @@ __global__ void __launch_bounds__(kT) k_range(RangeArgs a) {
       // leaves strictly inside the range: no filter, chunked span sum
       const uint64_t stop = min(g1, qend - 1);  // exclusive, global item index
       uint64_t cc = 0;
-      warp_span_sum(a.data, a.used, a.cnt, a.LB, fl + li, fl + (stop - qoff), s, cc, nbytes);
+      warp_span_sum(a.data, a.used, a.cnt, a.LB, fl + li, fl + (stop - qoff), s, cc, nbytes,
+                    a.raw);
       if (lane == 0) c += warp_sum(cc); else warp_sum(cc);
       g = stop;
       continue;
@@ -366,11 +374,11 @@ __global__ void __launch_bounds__(kT) k_range(RangeArgs a) {
       const uint64_t r = a.P[j];
       warp_decode(a.data + j * a.LB, u, [&](uint32_t idx, uint64_t v) {
         if (r + idx >= lo && r + idx < hi) { s += v; c++; }
-      });
+      }, a.raw);
     } else {
       warp_decode(a.data + j * a.LB, u, [&](uint32_t, uint64_t v) {
         if (v >= lo && v < hi) { s += v; c++; }
-      });
+      }, a.raw);
     }
     g++;
   }
@@ -388,13 +396,13 @@ __global__ void __launch_bounds__(kT) k_sum(const uint8_t* __restrict__ data,
                                             const uint32_t* __restrict__ used,
                                             const uint32_t* __restrict__ cnt, uint64_t L,
                                             uint32_t LB, uint64_t* sum, uint64_t* count,
-                                            ull* prof) {
+                                            ull* prof, int raw) {
   const unsigned lane = lane_id();
   const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
   const uint64_t j0 = L * gw / nw, j1 = L * (gw + 1) / nw;
   uint64_t s = 0, c = 0;
   ull nbytes = 0;
-  warp_span_sum(data, used, cnt, LB, j0, j1, s, c, nbytes);
+  warp_span_sum(data, used, cnt, LB, j0, j1, s, c, nbytes, raw);
   s = warp_sum(s);
   c = warp_sum(c);
   nbytes = warp_sum(nbytes);
@@ -449,7 +457,7 @@ int run_has(const cpma* h, const uint64_t* d_keys, uint64_t q, uint8_t* d_out, c
       1, std::min<uint64_t>((q + kT - 1) / kT, (uint64_t)persistent_grid(h)));
   prof_begin(h, PH_HAS, st);
   k_has<<<grid, kT, 0, st>>>(d_keys, q, h->data, h->used, h->heads, h->L, h->cfg.leaf_bytes,
-                             d_out, prof_bytes(h, PH_HAS));
+                             d_out, prof_bytes(h, PH_HAS), (int)h->cfg.codec);
   CPMA_LAUNCHED(h);
   prof_end(h, st);
   return check_cuda(cudaGetLastError());
@@ -486,6 +494,7 @@ int run_range(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q,
   a.sum = sum;
   a.count = count;
   a.prof = prof_bytes(h, PH_RANGE);
+  a.raw = (int)h->cfg.codec;
   prof_begin(h, PH_RANGE, st);
   k_range<false><<<persistent_grid(h), kT, 0, st>>>(a);
   CPMA_LAUNCHED(h);
@@ -516,7 +525,8 @@ int run_range_length(const cpma* h, const uint64_t* start, const uint64_t* lengt
   const int g1 = (int)std::max<uint64_t>(
       1, std::min<uint64_t>((q * 32 + kT - 1) / kT, (uint64_t)h->num_sms * 16));
   k_rank_prep<false><<<g1, kT, 0, st>>>(start, length, q, h->heads, h->data, h->used, h->L,
-                                        h->cfg.leaf_bytes, P, r0, r1, first, items, sum, count);
+                                        h->cfg.leaf_bytes, P, r0, r1, first, items, sum, count,
+                                        (int)h->cfg.codec);
   CPMA_LAUNCHED(h);
   CPMA_TRY(scan_u64_query(hm, items, off, q, st));
   prof_end(h, st);
@@ -534,6 +544,7 @@ int run_range_length(const cpma* h, const uint64_t* start, const uint64_t* lengt
   a.count = count;
   a.prof = prof_bytes(h, PH_RANGE);
   a.P = P;
+  a.raw = (int)h->cfg.codec;
   prof_begin(h, PH_RANGE, st);
   k_range<true><<<persistent_grid(h), kT, 0, st>>>(a);
   CPMA_LAUNCHED(h);
@@ -565,7 +576,7 @@ int run_range_extract(const cpma* h, const uint64_t* lo, const uint64_t* hi, uin
   // counts (r1 - r0) go into `items` of a second pass: first the ranks
   k_rank_prep<true><<<g1, kT, 0, st>>>(lo, hi, q, h->heads, h->data, h->used, h->L,
                                        h->cfg.leaf_bytes, P, r0, r1, first, items, nullptr,
-                                       offsets);
+                                       offsets, (int)h->cfg.codec);
   CPMA_LAUNCHED(h);
   CPMA_TRY(scan_u64_query(hm, offsets, offsets, q, st));
   CPMA_TRY(scan_u64_query(hm, items, off, q, st));
@@ -584,6 +595,7 @@ int run_range_extract(const cpma* h, const uint64_t* lo, const uint64_t* hi, uin
   a.LB = h->cfg.leaf_bytes;
   a.out = out;
   a.cap = cap;
+  a.raw = (int)h->cfg.codec;
   prof_begin(h, PH_RANGE, st);
   k_extract<<<persistent_grid(h), kT, 0, st>>>(a);
   CPMA_LAUNCHED(h);
@@ -632,6 +644,7 @@ int run_range_reduce(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint
   a.sum = out;
   a.count = count;
   a.prof = nullptr;
+  a.raw = (int)h->cfg.codec;
   prof_begin(h, PH_RANGE, st);
   const int G = persistent_grid(h);
   switch (op) {
@@ -680,6 +693,7 @@ int run_range_noalloc(const cpma* h, const uint64_t* lo, const uint64_t* hi, uin
   a.sum = sum;
   a.count = count;
   a.prof = nullptr;
+  a.raw = (int)h->cfg.codec;
   k_range<false><<<persistent_grid(h), kT, 0, st>>>(a);
   CPMA_LAUNCHED(h);
   return check_cuda(cudaGetLastError());
@@ -690,7 +704,7 @@ int run_sum(const cpma* h, uint64_t* sum, uint64_t* count, cudaStream_t st) {
   if (count) CPMA_CUDA(cudaMemsetAsync(count, 0, 8, st));
   prof_begin(h, PH_SUM, st);
   k_sum<<<persistent_grid(h), kT, 0, st>>>(h->data, h->used, h->cnt, h->L, h->cfg.leaf_bytes, sum,
-                                           count, prof_bytes(h, PH_SUM));
+                                           count, prof_bytes(h, PH_SUM), (int)h->cfg.codec);
   CPMA_LAUNCHED(h);
   prof_end(h, st);
   return check_cuda(cudaGetLastError());

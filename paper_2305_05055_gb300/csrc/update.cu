@@ -152,6 +152,7 @@ struct MergeArgs {
   uint32_t* list_lane;   // touched leaves for k_insert_lane (count st->n_lane)
   uint32_t* list_v1;     // touched leaves for k_merge_small (count st->n_v1)
   uint32_t* list_gen;    // work items for k_merge in count mode (st->n_gen)
+  int raw;               // leaves hold 8-byte cells (codec 1), not byte codes
 };
 
 // Append to a work list, one atomic per warp (all lanes must call).
@@ -580,7 +581,7 @@ __global__ void __launch_bounds__(kT) k_classify(MergeArgs a) {
       tb = a.T_begin[t];
       te = a.T_begin[t + 1];
       const uint32_t uold = a.T_oldused[t];
-      if (small_slice(tb, te, uold)) cls = (!a.is_delete && uold <= 512) ? 0u : 1u;
+      if (small_slice(tb, te, uold)) cls = (!a.is_delete && uold <= 512 && !a.raw) ? 0u : 1u;
       else {
         cls = 2;
         fc0 = a.T_first_chunk[t];
@@ -643,7 +644,7 @@ __global__ void __launch_bounds__(kT, 4) k_merge_small(MergeArgs a) {
     warp_decode_pos(leafp, min(uold, LB), [&](uint32_t idx, uint64_t v, uint32_t p) {
       old[idx] = v;
       pos[idx] = (uint16_t)p;
-    });
+    }, a.raw);
     __syncwarp();
     // the keys that change the leaf, with their ranks among the old elements
     uint64_t x = 0;
@@ -688,7 +689,12 @@ __global__ void __launch_bounds__(kT, 4) k_merge_small(MergeArgs a) {
       const unsigned after = lb & ~((2u << lane) - 1u);
       gend = after ? (uint32_t)(__ffs(after) - 1) : nn;
       r0 = nr[lane];
-      if (!a.is_delete) {
+      if (a.raw) {
+        // cells: an insert adds one cell per key before old cell r0, a delete
+        // removes cells r0 .. r1-1; no neighbouring cell changes
+        if (!a.is_delete) { e_os = e_oe = 8u * r0; e_nl = 8u * (gend - lane); }
+        else { e_os = 8u * r0; e_oe = 8u * (r0 + (gend - lane)); e_nl = 0; }
+      } else if (!a.is_delete) {
         if (r0 == 0) { e_os = 0; e_oe = 8; }
         else if (r0 < m) { e_os = pos[r0 - 1] + 1u; e_oe = pos[r0] + 1u; }
         else { e_os = uold; e_oe = uold; }
@@ -742,7 +748,11 @@ __global__ void __launch_bounds__(kT, 4) k_merge_small(MergeArgs a) {
     splice_copy(leafp, uold, out, E, es, ee, shc);
     __syncwarp();
     // the edits' new bytes
-    if (lead) {
+    if (lead && a.raw) {
+      if (!a.is_delete)
+        for (uint32_t q = lane; q < gend; q++)
+          reinterpret_cast<uint64_t*>(out + en[eidx])[q - lane] = nk[q];
+    } else if (lead) {
       uint8_t* o = out + en[eidx];
       if (!a.is_delete) {
         uint64_t prev = nk[lane];
@@ -843,7 +853,7 @@ __global__ void __launch_bounds__(kT) k_merge(MergeArgs a) {
     const uint32_t s = e - b;
     const uint32_t uold = a.T_oldused[t], m = a.T_oldcnt[t];
     uint8_t* leafp = a.data + (size_t)j * LB;
-    warp_decode(leafp, min(uold, LB), [&](uint32_t idx, uint64_t v) { old[idx] = v; });
+    warp_decode(leafp, min(uold, LB), [&](uint32_t idx, uint64_t v) { old[idx] = v; }, a.raw);
     for (uint32_t i = lane; i < s; i += 32) sl[i] = a.u[b + i];
     __syncwarp();
     const bool has_hi = !last;
@@ -926,7 +936,8 @@ __global__ void __launch_bounds__(kT) k_merge(MergeArgs a) {
     }
     uint32_t bsum = 0;
     for (uint32_t i = lane; i < r; i += 32)
-      bsum += (i == 0) ? (has_pred ? leb_len(z[0] - pred) : 8u) : leb_len(z[i] - z[i - 1]);
+      bsum += a.raw ? 8u
+                    : (i == 0) ? (has_pred ? leb_len(z[0] - pred) : 8u) : leb_len(z[i] - z[i - 1]);
     bsum = warp_sum(bsum);
     if (WRITE) {
       const uint64_t off = a.chunk_off[c];
@@ -947,7 +958,7 @@ __global__ void __launch_bounds__(kT) k_merge(MergeArgs a) {
         for (uint32_t p = lane * 16; p < LB; p += 512)
           *reinterpret_cast<uint4*>(buf + p) = make_uint4(0u, 0u, 0u, 0u);
         __syncwarp();
-        const uint32_t nb = warp_encode(z, r, buf);
+        const uint32_t nb = warp_encode(z, r, buf, a.raw);
         const uint32_t wend = (max(uold, nb) + 15u) & ~15u;
         for (uint32_t p = lane * 16; p < wend; p += 512)
           *reinterpret_cast<uint4*>(leafp + p) = *reinterpret_cast<const uint4*>(buf + p);
@@ -1192,6 +1203,7 @@ struct UnpackArgs {
   const uint64_t* ovf;
   uint64_t* E;
   Status* st;
+  int raw;
 };
 
 __global__ void __launch_bounds__(kT) k_unpack(UnpackArgs a) {
@@ -1214,18 +1226,20 @@ __global__ void __launch_bounds__(kT) k_unpack(UnpackArgs a) {
     } else {
       const uint32_t m = a.cnt[j];
       const uint32_t got = warp_decode(a.data + j * a.LB, min(a.used[j], a.LB),
-                                       [&](uint32_t idx, uint64_t v) { if (idx < m) dst[idx] = v; });
+                                       [&](uint32_t idx, uint64_t v) { if (idx < m) dst[idx] = v; },
+                                       a.raw);
       if (lane == 0 && got != m) atomicOr(&a.st->err, kErrState);
     }
   }
 }
 
 __global__ void __launch_bounds__(kT) k_costs(WinArgs w, const uint64_t* __restrict__ E,
-                                              const ull* nelem, uint8_t* __restrict__ cost) {
+                                              const ull* nelem, uint8_t* __restrict__ cost,
+                                              int raw) {
   const uint64_t n = *nelem;
   for (uint64_t i = gtid(); i < n; i += gstride()) {
     const uint64_t s = find_seg(w.elem_off, w.nwin, i);
-    cost[i] = (i == w.elem_off[s]) ? (uint8_t)8 : (uint8_t)leb_len(E[i] - E[i - 1]);
+    cost[i] = (raw || i == w.elem_off[s]) ? (uint8_t)8 : (uint8_t)leb_len(E[i] - E[i - 1]);
   }
 }
 
@@ -1255,6 +1269,7 @@ struct EncodeArgs {
   uint64_t* heads;
   uint32_t LB;
   Status* st;
+  int raw;
 };
 
 __global__ void __launch_bounds__(kT) k_encode(EncodeArgs a) {
@@ -1281,7 +1296,7 @@ __global__ void __launch_bounds__(kT) k_encode(EncodeArgs a) {
     for (uint32_t p = lane * 16; p < a.LB; p += 512)
       *reinterpret_cast<uint4*>(buf + p) = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
-    const uint32_t got = warp_encode(a.E + b, r, buf);
+    const uint32_t got = warp_encode(a.E + b, r, buf, a.raw);
     for (uint32_t p = lane * 16; p < a.LB; p += 512)
       *reinterpret_cast<uint4*>(leafp + p) = *reinterpret_cast<const uint4*>(buf + p);
     if (lane == 0) {
@@ -1532,7 +1547,7 @@ int spread(cpma* h, cudaStream_t st, WinArgs w, uint64_t nelem_bound, const ull*
   CPMA_TRY(ensure(h->s.C, (nelem_bound + 2) * 8));
   CPMA_TRY(ensure(h->s.dstart, (ndst + 1) * 8));
   k_costs<<<grid_for(h, nelem_bound), kT, 0, st>>>(w, P<uint64_t>(h->s.E), nelem_dev,
-                                                   P<uint8_t>(h->s.cost));
+                                                   P<uint8_t>(h->s.cost), (int)h->cfg.codec);
   h->launches++;
   CPMA_TRY(scan_u8_to_u64(h, P<uint8_t>(h->s.cost), P<uint64_t>(h->s.C), nelem_bound, nelem_dev,
                           st));
@@ -1551,6 +1566,7 @@ int spread(cpma* h, cudaStream_t st, WinArgs w, uint64_t nelem_bound, const ull*
   ea.heads = dst.heads;
   ea.LB = h->cfg.leaf_bytes;
   ea.st = h->d_status;
+  ea.raw = (int)h->cfg.codec;
   const size_t smem = (size_t)(kT / 32) * h->cfg.leaf_bytes;
   k_encode<<<grid_for(h, ndst * 32), kT, smem, st>>>(ea);
   h->launches++;
@@ -1607,6 +1623,7 @@ int pack(cpma* h, cudaStream_t st, uint64_t nwin, uint64_t nsrc, uint64_t nelem_
   ua.ovf = P<uint64_t>(h->s.ovf);
   ua.E = P<uint64_t>(h->s.E);
   ua.st = h->d_status;
+  ua.raw = (int)h->cfg.codec;
   k_unpack<<<grid_for(h, nsrc * 32), kT, 0, st>>>(ua);
   h->launches++;
   return check_cuda(cudaGetLastError());
@@ -1915,6 +1932,7 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   ma.list_lane = P<uint32_t>(s.list_lane);
   ma.list_v1 = P<uint32_t>(s.list_v1);
   ma.list_gen = P<uint32_t>(s.list_gen);
+  ma.raw = (int)h->cfg.codec;
   const size_t per = merge_warp_bytes(LB);
   const int mwarps = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));
   const size_t msmem = per * mwarps;
@@ -2336,7 +2354,8 @@ int build_from_sorted_unique(cpma* h, const uint64_t* E, uint64_t n, cudaStream_
   CPMA_CUDA(cudaMemcpyAsync(s.win_elem_off.p, eo, 16, cudaMemcpyHostToDevice, st));
   CPMA_CUDA(cudaMemcpyAsync(&h->d_status->nelem, &n, 8, cudaMemcpyHostToDevice, st));
   WinArgs w = win_args(h, 1);
-  k_costs<<<grid_for(h, n), kT, 0, st>>>(w, E, &h->d_status->nelem, P<uint8_t>(s.cost));
+  k_costs<<<grid_for(h, n), kT, 0, st>>>(w, E, &h->d_status->nelem, P<uint8_t>(s.cost),
+                                         (int)h->cfg.codec);
   h->launches++;
   CPMA_TRY(scan_u8_to_u64(h, P<uint8_t>(s.cost), P<uint64_t>(s.C), n, nullptr, st));
   CPMA_CUDA(cudaMemcpyAsync(&h->d_status->stream_bytes, P<uint64_t>(s.C) + n, 8,
@@ -2367,6 +2386,7 @@ int build_from_sorted_unique(cpma* h, const uint64_t* E, uint64_t n, cudaStream_
   ea.heads = na.heads;
   ea.LB = LB;
   ea.st = h->d_status;
+  ea.raw = (int)h->cfg.codec;
   k_encode<<<grid_for(h, L * 32), kT, (size_t)(kT / 32) * LB, st>>>(ea);
   h->launches++;
   CPMA_CUDA(cudaGetLastError());

@@ -39,8 +39,8 @@ def test_default_config_and_strerror(lib):
     from paper_2305_05055_gb300 import cpma
     c = cpma.default_config()
     assert (c.leaf_bytes, c.tau_leaf, c.tau_root, c.rho_leaf, c.rho_root,
-            c.grow_num, c.grow_den, c.build_pm, c.rebuild_pm) == (512, 900, 700, 100, 300, 6, 5,
-                                                                  500, 0)
+            c.grow_num, c.grow_den, c.build_pm, c.rebuild_pm, c.codec) == (
+        512, 900, 700, 100, 300, 6, 5, 500, 0, 0)
     assert lib.cpma_strerror(0) == b"ok"
     assert b"invalid" in lib.cpma_strerror(-1)
 

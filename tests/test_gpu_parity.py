@@ -457,3 +457,59 @@ def test_full_scan_large(LB):
     S = np.union1d(S, ins)
     s, c = g.sum()
     assert int(cp.to_u64(s)[0]) == int(np.sum(S, dtype=np.uint64)) and int(c.item()) == S.size
+
+
+@pytest.mark.parametrize("LB", [256, 512, 2048])
+@pytest.mark.parametrize("n", [0, 1, 5000, 70000])
+def test_pma_build_layout(LB, n):
+    """Uncompressed PMA (codec 1): build layout and queries against the
+    oracle's cells."""
+    keys = W.uniform_keys(13 + n, n, bits=40)
+    keys = np.concatenate([keys, keys[: n // 4], np.array([M64], np.uint64)]) if n else keys
+    g = cp.CPMA(T(keys) if keys.size else None, leaf_bytes=LB, codec=1)
+    o = oracle.SeqCPMA(keys, leaf_bytes=LB, codec=1)
+    same_layout(g, o)
+    same_queries(g, oracle.PlainSet(keys), 17 + n)
+
+
+@pytest.mark.parametrize("LB", [256, 1024])
+def test_pma_update_sequence(LB):
+    """Uncompressed PMA through inserts, zipfian hot leaves, sorted batches,
+    deletes (shrink) and full-range keys: counts, layout and every query
+    kind against the oracle."""
+    base = W.uniform_keys(23, 30000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=LB, codec=1)
+    o = oracle.SeqCPMA(base, leaf_bytes=LB, codec=1)
+    p = oracle.PlainSet(base)
+    for r in range(18):
+        kind = r % 6
+        if kind == 0:
+            keys = W.uniform_keys(110 + r, 20000, bits=40)
+        elif kind == 1:
+            keys = W.zipf_keys(210 + r, 20000, bits=34)
+        elif kind == 2:
+            keys = np.sort(W.uniform_keys(310 + r, 5000, bits=40))
+        elif kind == 3:
+            keys = np.concatenate([W.sample_present(p.S, 410 + r, 4000),
+                                   W.uniform_keys(510 + r, 1000, bits=40)])
+        elif kind == 4:
+            keys = W.sample_present(p.S, 610 + r, len(p) // 2)
+        else:
+            keys = W.full_range_keys(710 + r, 3000)
+        if kind in (3, 4):
+            assert int(g.delete_batch(T(keys)).item()) == o.delete_batch(keys) == p.delete_batch(keys)
+        else:
+            got = int(g.insert_batch(T(keys), sorted=kind == 2).item())
+            assert got == o.insert_batch(keys) == p.insert_batch(keys)
+        same_layout(g, o)
+    same_queries(g, p, 919, 200)
+    lo, hi, c = W.range_queries_by_rank(p.S, 920, 300, 1, 5000)
+    s1, c1 = g.range_map_length(T(lo), T(c.astype(np.uint64)))
+    ws, wc = p.range_map_length(lo, c.astype(np.uint64))
+    assert np.array_equal(cp.to_u64(s1), ws) and np.array_equal(cp.to_u64(c1), wc)
+    off, keys = g.range_extract(T(lo), T(hi))
+    woff, wkeys = p.range_extract(lo, hi)
+    assert np.array_equal(cp.to_u64(off), woff) and np.array_equal(cp.to_u64(keys), wkeys)
+    r_, c_ = g.range_reduce(T(lo), T(hi), "max", 3, 1)
+    wr, wc = p.range_reduce(lo, hi, "max", 3, 1)
+    assert np.array_equal(cp.to_u64(r_), wr) and np.array_equal(cp.to_u64(c_), wc)
