@@ -352,6 +352,12 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
     const uint32_t p0 = lane * 16u;
     uint4 v = make_uint4(0u, 0u, 0u, 0u);
     if (p0 < uold) v = *reinterpret_cast<const uint4*>(leafp + p0);
+    // the slice's keys, loaded now so their latency overlaps the summary
+    uint64_t x = 0, xprev = 0;
+    if (lane < s) {
+      x = a.u[tb + lane];
+      if (lane > 0) xprev = a.u[tb + lane - 1];
+    }
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
     const int b_lo = lane == 0 ? 8 : 0;
     const int b_hi = (uold > p0) ? (int)min(16u, uold - p0) : 0;
@@ -384,12 +390,7 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
     const uint64_t V = head + (Dinc - D);                       // element before my codes
     const uint64_t lastv = head + __shfl_sync(FULL, Dinc, 31);  // the last element
     // ---- keys: owning lane, or before the head / after the last element ----
-    uint64_t x = 0;
-    bool valid = false;
-    if (lane < s) {
-      x = a.u[tb + lane];
-      valid = !(lane > 0 && a.u[tb + lane - 1] == x);
-    }
+    const bool valid = lane < s && !(lane > 0 && xprev == x);
     unsigned owners = 0;
     for (uint32_t k = 0; k < s; k++) {
       const uint64_t xk = __shfl_sync(FULL, x, k);
@@ -408,46 +409,39 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
       }
     }
     __syncwarp();
-    // ---- each owning lane's codes, decoded by the whole warp ----
-    while (owners) {
-      const unsigned o = __ffs(owners) - 1;
-      owners &= owners - 1;
-      uint32_t xo[4];
-#pragma unroll
-      for (int k = 0; k < 4; k++) xo[k] = __shfl_sync(FULL, lc.x[k], o);
-      const uint32_t term_o = __shfl_sync(FULL, lc.term, o);
-      const uint32_t pv_o = __shfl_sync(FULL, pv, o), ps_o = __shfl_sync(FULL, ps, o);
-      const uint32_t B_o = __shfl_sync(FULL, B, o);
-      const uint64_t V_o = __shfl_sync(FULL, V, o);
-      const uint32_t blo_o = o == 0 ? 8u : 0u;
-      // lane t < 16 takes the code ending at byte t of lane o
-      const bool is_t = lane < 16 && ((term_o >> lane) & 1u);
-      const uint32_t before = lane < 16 ? (term_o & ((1u << lane) - 1u)) : 0u;
-      const bool firstc = before == 0;
-      const uint32_t st0 = firstc ? blo_o : (32u - (uint32_t)__clz(before));
-      uint32_t code = 0;
-      if (is_t) {
-        const uint32_t own = compact7(window32(xo, st0)) & mask7(lane + 1u - st0);
-        code = firstc ? pv_o + (own << ps_o) : own;
-      }
-      const uint32_t cinc = warp_incl_scan(code);
-      const uint64_t val = V_o + cinc;
-      uint32_t kk = 0, kend = 0;
-      for (uint32_t k = 0; k < s; k++)
-        if (ktl[k] == o) { if (kend == 0) kk = k; kend = k + 1; }
-      for (uint32_t k = kk; k < kend; k++) {
-        const uint64_t xk = kx[k];
-        const unsigned hit = __ballot_sync(FULL, is_t && val >= xk);
-        if (lane == (unsigned)(__ffs(hit) - 1)) {
-          kr[k] = (1u + B_o + (uint32_t)__popc(before)) | (xk == val ? 0x80000000u : 0u);
-          kp[k] = val - code;
-          ks[k] = val;
-          kcs[k] = 16u * o + st0 - (firstc ? ps_o / 7u : 0u);
-          kce[k] = 16u * o + lane + 1u;
+    // ---- each owning lane decodes its own codes (all owners at once) ----
+    // Walking its codes in order, the lane keeps the running value; a key
+    // takes the first code whose value reaches it: that code's element is
+    // its successor (rank 1 + codes before it), the value before is its
+    // predecessor, and the code's bytes are the ones an insert replaces.
+    if ((owners >> lane) & 1u) {
+      uint32_t kq = 0;
+      while (ktl[kq] != lane) kq++;  // this lane's keys are consecutive
+      uint32_t tm = lc.term, st = (lane == 0) ? 8u : 0u, rank = 1u + B;
+      uint64_t val = V;
+      bool firstc = true;
+      while (tm && kq < s && ktl[kq] == lane) {
+        const uint32_t tb8 = (uint32_t)__ffs(tm) - 1u;
+        tm &= tm - 1u;
+        const uint32_t own = compact7(window32(lc.x, st)) & mask7(tb8 + 1u - st);
+        const uint32_t code = firstc ? pv + (own << ps) : own;
+        const uint32_t cs = 16u * lane + st - (firstc ? ps / 7u : 0u);
+        const uint64_t prev = val;
+        val += code;
+        while (kq < s && ktl[kq] == lane && kx[kq] <= val) {
+          kr[kq] = rank | (kx[kq] == val ? 0x80000000u : 0u);
+          kp[kq] = prev;
+          ks[kq] = val;
+          kcs[kq] = cs;
+          kce[kq] = 16u * lane + tb8 + 1u;
+          kq++;
         }
+        rank++;
+        st = tb8 + 1u;
+        firstc = false;
       }
-      __syncwarp();
     }
+    __syncwarp();
     // ---- kept keys and their gaps ----
     uint32_t r = 0;
     bool keep = false;
@@ -527,9 +521,12 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
       continue;
     }
     const uint32_t wend = (max(uold, nb) + 15u) & ~15u;
-    if (lane * 16 < wend) *reinterpret_cast<uint4*>(out + lane * 16) = make_uint4(0u, 0u, 0u, 0u);
+    // 16-byte chunks wholly before the first edit keep their bytes: those
+    // lanes neither rebuild nor rewrite them
+    const bool touched = p0 + 16u > es[0];
+    if (touched && p0 < wend) *reinterpret_cast<uint4*>(out + p0) = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
-    splice_copy_words(w, p0, uold, out, E, es, ee, shc);
+    if (touched) splice_copy_words(w, p0, uold, out, E, es, ee, shc);
     __syncwarp();
     if (lead) {
       uint8_t* o = out + en[eidx];
@@ -545,9 +542,9 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
       if (r0 < m) leb_put(o, ks[lane] - prev);
     }
     __syncwarp();
-    if (lane * 16 < wend)
-      *reinterpret_cast<uint4*>(leafp + lane * 16) = *reinterpret_cast<const uint4*>(out + lane * 16);
-    nbytes += wend;
+    if (touched && p0 < wend)
+      *reinterpret_cast<uint4*>(leafp + p0) = *reinterpret_cast<const uint4*>(out + p0);
+    nbytes += wend - min(wend, es[0] & ~15u);
     if (keep) credit(a, tb + lane);
     if (lane == 0) {
       a.used[j] = nb;
@@ -613,7 +610,7 @@ __global__ void __launch_bounds__(kT) k_classify(MergeArgs a) {
 // the same bytes as encoding the merged sequence from scratch, produced
 // without re-encoding the untouched codes.  A result over LB bytes is left
 // pending for the general merge.
-__global__ void __launch_bounds__(kT, 4) k_merge_small(MergeArgs a) {
+__global__ void __launch_bounds__(kT, 3) k_merge_small(MergeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   if (a.st->err) return;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
