@@ -399,13 +399,43 @@ __device__ __forceinline__ void warp_span_sum(const uint8_t* __restrict__ data,
                                               uint64_t j0, uint64_t j1, uint64_t& acc,
                                               uint64_t& cacc, ull& nbytes, bool raw = false) {
   const unsigned lane = lane_id();
-  if (raw) {  // codec 1: add the cells, 16 bytes per lane
-    for (uint64_t j = j0; j < j1; j++) {
-      const uint32_t u = min(__ldg(used + j), LB);
-      if (lane == 0) { cacc += __ldg(cnt + j); nbytes += u; }
-      for (uint32_t p0 = lane * 16u; p0 < u; p0 += 512) {
-        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(data + j * LB + p0));
-        acc += v.x + (p0 + 8 < u ? v.y : 0ull);
+  if (raw) {
+    // codec 1: add the cells.  The used 16-byte chunks of 32 leaves are
+    // numbered by a prefix sum and spread over the lanes, four loads in
+    // flight per lane.
+    for (uint64_t w0 = j0; w0 < j1; w0 += 32) {
+      const uint64_t jj = w0 + lane;
+      const uint32_t u_i = jj < j1 ? min(__ldg(used + jj), LB) : 0u;
+      cacc += jj < j1 ? __ldg(cnt + jj) : 0u;
+      nbytes += u_i;
+      const uint32_t nc_i = (u_i + 15u) >> 4;
+      const uint32_t cinc = warp_incl_scan(nc_i);
+      const uint32_t NC = __shfl_sync(FULL, cinc, 31);
+      for (uint32_t g0 = 0; g0 < NC; g0 += 128) {
+        ulonglong2 v[4];
+        uint32_t lim[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const uint32_t ci = g0 + 32u * q + lane;
+          uint32_t li = 0;
+#pragma unroll
+          for (int stp = 16; stp >= 1; stp >>= 1) {
+            const uint32_t cv = __shfl_sync(FULL, cinc, li + stp - 1);
+            if (cv <= ci) li += stp;
+          }
+          const uint32_t lis = min(li, 31u);
+          const uint32_t cstart = __shfl_sync(FULL, cinc, lis) - __shfl_sync(FULL, nc_i, lis);
+          const uint32_t u = __shfl_sync(FULL, u_i, lis);
+          const uint32_t p0 = (ci - cstart) * 16u;
+          v[q] = make_ulonglong2(0ull, 0ull);
+          lim[q] = 0;
+          if (ci < NC) {
+            v[q] = __ldg(reinterpret_cast<const ulonglong2*>(data + (w0 + lis) * LB + p0));
+            lim[q] = u - p0;  // used bytes from this chunk on: 8 or at least 16
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc += v[q].x * (lim[q] >= 8) + v[q].y * (lim[q] >= 16);
       }
     }
     return;
