@@ -292,16 +292,29 @@ __device__ __forceinline__ uint32_t compact7(uint32_t y) {  // 4 bytes' 7-bit gr
 __device__ __forceinline__ uint32_t mask7(uint32_t groups) {  // low 7*groups bits, groups <= 4
   return groups >= 4 ? 0x0FFFFFFFu : ((1u << (7u * groups)) - 1u);
 }
-// 32-bit window of the 16 bytes x[] starting at byte s <= 16 (zeros past the end)
-__device__ __forceinline__ uint32_t window32(const uint32_t x[4], uint32_t s) {
+// 32-bit window of the 4*NW bytes x[] starting at byte s <= 4*NW (zeros past
+// the end)
+template <int NW = 4>
+__device__ __forceinline__ uint32_t window32(const uint32_t (&x)[NW], uint32_t s) {
+  static_assert(NW == 4 || NW == 8, "4 or 8 words per lane");
   const uint32_t i = s >> 2, sh = 8u * (s & 3u);
-  const uint32_t lo = i == 0 ? x[0] : i == 1 ? x[1] : i == 2 ? x[2] : i == 3 ? x[3] : 0u;
-  const uint32_t hi = i == 0 ? x[1] : i == 1 ? x[2] : i == 2 ? x[3] : 0u;
+  uint32_t lo, hi;
+  // explicit selects: an indexed form would put x[] in local memory
+  if constexpr (NW == 4) {
+    lo = i == 0 ? x[0] : i == 1 ? x[1] : i == 2 ? x[2] : i == 3 ? x[3] : 0u;
+    hi = i == 0 ? x[1] : i == 1 ? x[2] : i == 2 ? x[3] : 0u;
+  } else {
+    lo = i == 0 ? x[0] : i == 1 ? x[1] : i == 2 ? x[2] : i == 3 ? x[3] : i == 4 ? x[4]
+       : i == 5 ? x[5] : i == 6 ? x[6] : i == 7 ? x[7] : 0u;
+    hi = i == 0 ? x[1] : i == 1 ? x[2] : i == 2 ? x[3] : i == 3 ? x[4] : i == 4 ? x[5]
+       : i == 5 ? x[6] : i == 6 ? x[7] : 0u;
+  }
   return __funnelshift_r(lo, hi, sh);
 }
 
-struct LaneCodes {
-  uint32_t x[4];      // the lane's bytes, zero outside [b_lo, b_hi)
+template <int NW>
+struct LaneCodesN {
+  uint32_t x[NW];     // the lane's bytes, zero outside [b_lo, b_hi)
   uint32_t term;      // bit b: byte b ends a code
   uint32_t D;         // own bits of the codes ending here (first one without carry)
   uint32_t W;         // sum over those codes of (index among them) * own bits
@@ -312,19 +325,26 @@ struct LaneCodes {
   bool bad;           // a code longer than 4 bytes, or no terminator
 };
 
-template <bool WANT_W>
-__device__ __forceinline__ void lane_codes(const uint32_t w[4], int b_lo, int b_hi, LaneCodes& L) {
+using LaneCodes = LaneCodesN<4>;
+
+// NW words (4*NW <= 32 bytes) per lane; b_lo, b_hi in bytes of the lane.
+template <bool WANT_W, int NW = 4>
+__device__ __forceinline__ void lane_codes(const uint32_t (&w)[NW], int b_lo, int b_hi,
+                                           LaneCodesN<NW>& L) {
   uint32_t range = 0;
-  if (b_hi > b_lo) range = ((b_hi == 16) ? 0xFFFFu : ((1u << b_hi) - 1u)) & ~((1u << b_lo) - 1u);
-  uint32_t cb[4], tb[4];
+  if (b_hi > b_lo)
+    range = ((b_hi >= 32) ? 0xFFFFFFFFu : ((1u << b_hi) - 1u)) & ~((1u << b_lo) - 1u);
+  uint32_t cb[NW], tb[NW];
 #pragma unroll
-  for (int q = 0; q < 4; q++) {
+  for (int q = 0; q < NW; q++) {
     const uint32_t rm = bytemask4((range >> (4 * q)) & 0xFu);
     L.x[q] = w[q] & rm;
     cb[q] = (L.x[q] >> 7) & 0x01010101u;
     tb[q] = (rm & 0x01010101u) & ~cb[q];
   }
-  L.term = gather4(tb[0]) | (gather4(tb[1]) << 4) | (gather4(tb[2]) << 8) | (gather4(tb[3]) << 12);
+  L.term = 0;
+#pragma unroll
+  for (int q = 0; q < NW; q++) L.term |= gather4(tb[q]) << (4 * q);
   // Byte b's 7 payload bits sit at group g_b = (continuation bytes right
   // before it, at most 3) of its code.  With 0/1 byte masks m_i of g_b == i,
   // dp4a with multipliers m0 + 128 m1 and m2 + 128 m3 gives S0 + (S1 << 7)
@@ -332,7 +352,7 @@ __device__ __forceinline__ void lane_codes(const uint32_t w[4], int b_lo, int b_
   uint32_t S01 = 0, S23 = 0, W0 = 0, W1 = 0, W2 = 0, W3 = 0;
   uint32_t badm = 0, base = 0;
 #pragma unroll
-  for (int q = 0; q < 4; q++) {
+  for (int q = 0; q < NW; q++) {
     const uint32_t prev = q ? cb[q - 1] : 0u;
     const uint32_t p1 = __funnelshift_l(prev, cb[q], 8);
     const uint32_t p2 = __funnelshift_l(prev, cb[q], 16);
@@ -364,7 +384,7 @@ __device__ __forceinline__ void lane_codes(const uint32_t w[4], int b_lo, int b_
   if (L.term) {
     const uint32_t lt = 31u - (uint32_t)__clz(L.term);
     const uint32_t tl = (uint32_t)b_hi - 1u - lt;
-    L.tail = compact7(window32(L.x, lt + 1u));
+    L.tail = compact7(window32<NW>(L.x, lt + 1u));
     L.tail_sh = 7u * tl;
     const uint32_t ft = (uint32_t)__ffs(L.term) - 1u;
     L.first_len = ft + 1u - (uint32_t)b_lo;

@@ -236,48 +236,61 @@ __device__ __forceinline__ bool small_slice(uint32_t tb, uint32_t te, uint32_t u
   return te - tb <= kSmall && uold > 0;
 }
 
-// out[512 + 32] (slack for the word copy), 4 u64 and 8 u32 arrays of kSmall
+// Lane-granular insert: lanes per leaf (a segment), and per segment
+// out[512 + 32] (slack for the word copy), 3 u64 and 8 u32 arrays of SEG keys.
+// A whole warp per leaf (16 bytes per lane) measured slightly faster than a
+// half warp per leaf (32 bytes per lane, two leaves per warp step): the
+// per-lane summary and splice work dominates, not the per-leaf bookkeeping.
+constexpr int kLaneSeg = 32;
 constexpr size_t kLaneOut = 512 + 32;
-constexpr size_t kLaneWarpBytes = kLaneOut + 8 * kSmall * 4 + 4 * kSmall * 8 + 16;
+__host__ __device__ constexpr size_t lane_seg_bytes(int seg) {
+  return kLaneOut + (size_t)seg * (3 * 8 + 8 * 4);
+}
+__host__ __device__ constexpr size_t lane_warp_bytes(int seg) {
+  return (size_t)(32 / seg) * lane_seg_bytes(seg);
+}
 
-// Copy of the kept old bytes for the lane-granular insert: the lane's 16
+// Copy of the kept old bytes for the lane-granular insert: the lane's 4*NW
 // bytes are cut into the segments that no edit removes, and each segment is
-// OR-ed into out[] as five shifted words (out[] zeroed, one writer per byte,
+// OR-ed into out[] as NW + 1 shifted words (out[] zeroed, one writer per byte,
 // 32 bytes of slack after the leaf).
-__device__ __forceinline__ void splice_copy_words(const uint32_t w[4], uint32_t p0, uint32_t uold,
-                                                  uint8_t* out, uint32_t E, const uint32_t* es,
-                                                  const uint32_t* ee, const int32_t* shc) {
+template <int NW = 4>
+__device__ __forceinline__ void splice_copy_words(const uint32_t (&w)[NW], uint32_t p0,
+                                                  uint32_t uold, uint8_t* out, uint32_t E,
+                                                  const uint32_t* es, const uint32_t* ee,
+                                                  const int32_t* shc) {
+  constexpr uint32_t kB = 4 * NW;  // bytes per lane
   if (p0 >= uold) return;
   uint32_t q = 0;
   while (q < E && ee[q] <= p0) q++;
   int32_t shift = q ? shc[q - 1] : 0;
   uint32_t cur = p0;
-  const uint32_t lim = min(p0 + 16u, uold);
+  const uint32_t lim = min(p0 + kB, uold);
   uint32_t* ow = reinterpret_cast<uint32_t*>(out);
   while (cur < lim) {
     const uint32_t send = (q < E) ? min(es[q], lim) : lim;
     if (send > cur) {
       // bytes [cur, send) of the lane, shifted by `shift`
       const uint32_t a = cur - p0, b = send - p0;
-      const uint32_t segm = ((b >= 16) ? 0xFFFFu : ((1u << b) - 1u)) & ~((1u << a) - 1u);
-      uint32_t m[4];
+      const uint32_t segm = ((b >= 32) ? 0xFFFFFFFFu : ((1u << b) - 1u)) & ~((1u << a) - 1u);
+      uint32_t m[NW];
 #pragma unroll
-      for (int k = 0; k < 4; k++) m[k] = w[k] & bytemask4((segm >> (4 * k)) & 0xFu);
+      for (int k = 0; k < NW; k++) m[k] = w[k] & bytemask4((segm >> (4 * k)) & 0xFu);
       const uint32_t d0 = (uint32_t)((int32_t)p0 + shift);
       const uint32_t k0 = d0 >> 2, sh8 = 8u * (d0 & 3u);
       if (sh8 == 0) {
 #pragma unroll
-        for (int k = 0; k < 4; k++)
+        for (int k = 0; k < NW; k++)
           if (m[k]) atomicOr(ow + k0 + k, m[k]);
       } else {
-        atomicOr(ow + k0, m[0] << sh8);
+        if (m[0] << sh8) atomicOr(ow + k0, m[0] << sh8);
 #pragma unroll
-        for (int k = 1; k < 4; k++) {
+        for (int k = 1; k < NW; k++) {
           const uint32_t y = __funnelshift_l(m[k - 1], m[k], sh8);
           if (y) atomicOr(ow + k0 + k, y);
         }
-        const uint32_t yl = m[3] >> (32u - sh8);
-        if (yl) atomicOr(ow + k0 + 4, yl);
+        const uint32_t yl = m[NW - 1] >> (32u - sh8);
+        if (yl) atomicOr(ow + k0 + NW, yl);
       }
     }
     if (q < E && es[q] < lim) {
@@ -290,39 +303,66 @@ __device__ __forceinline__ void splice_copy_words(const uint32_t w[4], uint32_t 
   }
 }
 
-// Insert of a slice of at most kSmall keys into a leaf of at most 512 used
-// bytes, without decoding the whole leaf into an element array.  Each lane
-// summarises its 16 bytes bit-parallel (lane_codes: how many codes end there
-// and the sum of their deltas); warp scans then give every lane the value of
-// the element before its first code.  A key x belongs to the lane whose value
-// interval holds it; for each such lane the whole warp decodes that lane's
-// codes one byte position per lane, a scan gives their values and a ballot the
-// first code >= x: x's rank, its neighbours and the byte span of the code x
-// splits.  Edits are as in the element-array splice below, which also takes
-// any leaf this kernel cannot (a code longer than 4 bytes, or a result over
-// 512 bytes that still fits a larger leaf: state kFallback).  Per-leaf
-// metadata is loaded for 32 leaves at once.
-__global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
+// Segment (SEG consecutive lanes, mask `seg`, segment index sg, lane sl in
+// it) ballot as SEG bits, and inclusive scan.
+template <int SEG>
+__device__ __forceinline__ unsigned seg_ballot(unsigned seg, unsigned sg, bool p) {
+  const unsigned b = __ballot_sync(seg, p);
+  return SEG == 32 ? b : (b >> (sg * SEG)) & ((1u << SEG) - 1u);
+}
+template <int SEG, typename T>
+__device__ __forceinline__ T seg_scan(unsigned seg, unsigned sl, T v) {
+#pragma unroll
+  for (int o = 1; o < SEG; o <<= 1) {
+    const T n = __shfl_up_sync(seg, v, o, SEG);
+    if ((int)sl >= o) v += n;
+  }
+  return v;
+}
+
+// Insert of a small slice (at most SEG keys) into a leaf of at most 512 used
+// bytes, without decoding the whole leaf into an element array.  A segment
+// of SEG lanes takes one leaf (32 / SEG leaves per warp step), each lane
+// 512 / SEG bytes of it.  Each lane summarises its bytes bit-parallel
+// (lane_codes: how many codes end there and the sum of their deltas);
+// segment scans then give every lane the value of the element before its
+// first code.  A key x belongs to the lane whose value interval holds it;
+// every owning lane walks its own codes to the first value >= x: x's rank,
+// its neighbours and the byte span of the code x splits.  Edits are as in
+// the element-array splice below, which also takes any leaf this kernel
+// cannot (a code longer than 4 bytes, or a result over 512 bytes that still
+// fits a larger leaf: state kFallback).  Per-leaf metadata is loaded for 32
+// leaves at once; segments of a warp run independently (segment-masked
+// shuffles and ballots) between those loads.
+template <int SEG>
+__global__ void __launch_bounds__(kT, SEG == 32 ? 4 : 3) k_insert_lane(MergeArgs a) {
+  constexpr int NW = 512 / (4 * SEG);        // words per lane
+  constexpr uint32_t kLB = 4u * NW;          // bytes per lane
+  constexpr int SPW = 32 / SEG;              // segments (leaves) per warp step
+  constexpr uint32_t KS = SEG;               // keys per slice
+  constexpr unsigned SEGBITS = SEG == 32 ? 0xFFFFFFFFu : ((1u << SEG) - 1u);
   extern __shared__ __align__(16) uint8_t smem[];
   if (a.st->err) return;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const unsigned sg = lane / SEG, sl = lane % SEG;
+  const unsigned seg = SEGBITS << (sg * SEG);
+  const unsigned lt_mask = (1u << sl) - 1u;
   const unsigned wpb = blockDim.x >> 5;
-  uint8_t* wbase = smem + (size_t)warp * kLaneWarpBytes;
+  uint8_t* wbase = smem + (size_t)warp * lane_warp_bytes(SEG) + (size_t)sg * lane_seg_bytes(SEG);
   uint8_t* out = wbase;
   uint64_t* kx = reinterpret_cast<uint64_t*>(wbase + kLaneOut);  // key
-  uint64_t* kp = kx + kSmall;                                     // predecessor value
-  uint64_t* ks = kp + kSmall;                                     // successor value
-  uint64_t* kpad = ks + kSmall;
-  uint32_t* kr = reinterpret_cast<uint32_t*>(kpad + kSmall);  // rank; bit 31 = present
-  uint32_t* kcs = kr + kSmall;                                 // successor code start
-  uint32_t* kce = kcs + kSmall;                                // successor code end (excl.)
-  uint32_t* ktl = kce + kSmall;                                // owning lane
-  uint32_t* es = ktl + kSmall;
-  uint32_t* ee = es + kSmall;
-  uint32_t* en = ee + kSmall;
-  int32_t* shc = reinterpret_cast<int32_t*>(en + kSmall);
+  uint64_t* kp = kx + KS;                                         // predecessor value
+  uint64_t* ks = kp + KS;                                         // successor value
+  uint32_t* kr = reinterpret_cast<uint32_t*>(ks + KS);  // rank; bit 31 = present
+  uint32_t* kcs = kr + KS;                              // successor code start
+  uint32_t* kce = kcs + KS;                             // successor code end (excl.)
+  uint32_t* ktl = kce + KS;                             // owning lane
+  uint32_t* es = ktl + KS;
+  uint32_t* ee = es + KS;
+  uint32_t* en = ee + KS;
+  int32_t* shc = reinterpret_cast<int32_t*>(en + KS);
   const uint64_t nL = a.st->n_lane;
-  ull nbytes = 0;  // algorithmic bytes (lane 0's count)
+  ull nbytes = 0;  // algorithmic bytes (lane 0 of each segment)
   uint64_t r0, r1;
   warp_share(nL, (uint64_t)blockIdx.x * wpb + warp, (uint64_t)gridDim.x * wpb, r0, r1);
   for (uint64_t tbase = r0; tbase < r1; tbase += 32) {
@@ -337,103 +377,113 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
     }
     unsigned todo = __ballot_sync(FULL, have);
     while (todo) {
-    const unsigned src = __ffs(todo) - 1;
-    todo &= todo - 1;
+    // segment sg takes the sg-th remaining leaf of this step
+    unsigned tm = todo;
+    for (unsigned q = 0; q < sg; q++) tm &= tm - 1u;
+    const bool mine = tm != 0;
+    const unsigned src = mine ? (unsigned)(__ffs(tm) - 1) : 0u;
     const uint32_t t = __shfl_sync(FULL, ti, src);
     const uint32_t tb = __shfl_sync(FULL, i_tb, src), te = __shfl_sync(FULL, i_te, src);
     const uint32_t uold = __shfl_sync(FULL, i_uold, src), j = __shfl_sync(FULL, i_j, src);
     const uint32_t m = __shfl_sync(FULL, i_m, src);
     const uint32_t fc0 = __shfl_sync(FULL, i_fc0, src), fc1 = __shfl_sync(FULL, i_fc1, src);
+#pragma unroll
+    for (int q = 0; q < SPW; q++) todo &= todo - 1u;
+    if (!mine) continue;
     const uint32_t s = te - tb;
     uint8_t* leafp = a.data + (size_t)j * a.LB;
     // the old leaf, the slice and ~28 bytes of per-leaf metadata
     nbytes += uold + 8u * s + 28u;
-    // ---- bit-parallel summary of each lane's 16 bytes ----
-    const uint32_t p0 = lane * 16u;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (p0 < uold) v = *reinterpret_cast<const uint4*>(leafp + p0);
+    // ---- bit-parallel summary of each lane's bytes ----
+    const uint32_t p0 = sl * kLB;
+    uint32_t w[NW];
+#pragma unroll
+    for (int q = 0; q < NW; q += 4) {
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (p0 + 4u * q < uold) v = *reinterpret_cast<const uint4*>(leafp + p0 + 4u * q);
+      w[q] = v.x; w[q + 1] = v.y; w[q + 2] = v.z; w[q + 3] = v.w;
+    }
     // the slice's keys, loaded now so their latency overlaps the summary
     uint64_t x = 0, xprev = 0;
-    if (lane < s) {
-      x = a.u[tb + lane];
-      if (lane > 0) xprev = a.u[tb + lane - 1];
+    if (sl < s) {
+      x = a.u[tb + sl];
+      if (sl > 0) xprev = a.u[tb + sl - 1];
     }
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-    const int b_lo = lane == 0 ? 8 : 0;
-    const int b_hi = (uold > p0) ? (int)min(16u, uold - p0) : 0;
-    LaneCodes lc;
-    lane_codes<false>(w, b_lo, b_hi, lc);
+    const int b_lo = sl == 0 ? 8 : 0;
+    const int b_hi = (uold > p0) ? (int)min(kLB, uold - p0) : 0;
+    LaneCodesN<NW> lc;
+    lane_codes<false, NW>(w, b_lo, b_hi, lc);
     bool bad = lc.bad;
-    uint32_t pv = __shfl_up_sync(FULL, lc.tail, 1);
-    uint32_t ps = __shfl_up_sync(FULL, lc.tail_sh, 1);
-    if (lane == 0) { pv = 0; ps = 0; }
+    uint32_t pv = __shfl_up_sync(seg, lc.tail, 1, SEG);
+    uint32_t ps = __shfl_up_sync(seg, lc.tail_sh, 1, SEG);
+    if (sl == 0) { pv = 0; ps = 0; }
     uint32_t D = 0;
     if (lc.term) {
       if (ps / 7u + lc.first_len > 4u) bad = true;
       D = lc.D - lc.first_own + pv + (lc.first_own << ps);
     }
-    if (__any_sync(FULL, bad)) {
-      if (lane == 0) {
+    if (__any_sync(seg, bad)) {
+      if (sl == 0) {
         a.T_state[t] = kFallback;
         a.list_v1[atomicAdd(&a.st->n_v1, 1ull)] = t;
       }
       continue;
     }
     const uint32_t c = __popc(lc.term);
-    const uint32_t B = warp_incl_scan(c) - c;                 // codes in earlier lanes
-    if (__shfl_sync(FULL, B + c, 31) + 1u != m) {           // must match the stored count
-      if (lane == 0) atomicOr(&a.st->err, kErrState);
+    const uint32_t B = seg_scan<SEG, uint32_t>(seg, sl, c) - c;                       // codes in earlier lanes
+    if (__shfl_sync(seg, B + c, SEG - 1, SEG) + 1u != m) {   // must match the stored count
+      if (sl == 0) atomicOr(&a.st->err, kErrState);
       continue;
     }
-    const uint64_t Dinc = warp_incl_scan((uint64_t)D);
-    const uint64_t head = __shfl_sync(FULL, (uint64_t)w[0] | ((uint64_t)w[1] << 32), 0);
-    const uint64_t V = head + (Dinc - D);                       // element before my codes
-    const uint64_t lastv = head + __shfl_sync(FULL, Dinc, 31);  // the last element
+    const uint64_t Dinc = seg_scan<SEG, uint64_t>(seg, sl, (uint64_t)D);
+    const uint64_t head = __shfl_sync(seg, (uint64_t)w[0] | ((uint64_t)w[1] << 32), 0, SEG);
+    const uint64_t V = head + (Dinc - D);                             // element before my codes
+    const uint64_t lastv = head + __shfl_sync(seg, Dinc, SEG - 1, SEG);  // the last element
     // ---- keys: owning lane, or before the head / after the last element ----
-    const bool valid = lane < s && !(lane > 0 && xprev == x);
+    const bool valid = sl < s && !(sl > 0 && xprev == x);
     unsigned owners = 0;
     for (uint32_t k = 0; k < s; k++) {
-      const uint64_t xk = __shfl_sync(FULL, x, k);
-      const unsigned own = __ballot_sync(FULL, c > 0 && V < xk && xk <= V + D);
-      if (lane == k) ktl[k] = own ? (uint32_t)(__ffs(own) - 1) : 0xFFFFFFFFu;
+      const uint64_t xk = __shfl_sync(seg, x, k, SEG);
+      const unsigned own = seg_ballot<SEG>(seg, sg, c > 0 && V < xk && xk <= V + D);
+      if (sl == k) ktl[k] = own ? (uint32_t)(__ffs(own) - 1) : 0xFFFFFFFFu;
       owners |= own;
     }
-    if (lane < s) {
-      kx[lane] = x;
+    if (sl < s) {
+      kx[sl] = x;
       if (x <= head) {            // before the head, or the head itself
-        kr[lane] = (x == head) ? 0x80000000u : 0u;
-        kp[lane] = 0; ks[lane] = head; kcs[lane] = 0; kce[lane] = 8;
+        kr[sl] = (x == head) ? 0x80000000u : 0u;
+        kp[sl] = 0; ks[sl] = head; kcs[sl] = 0; kce[sl] = 8;
       } else if (x > lastv) {     // after the last element
-        kr[lane] = m;
-        kp[lane] = lastv; ks[lane] = 0; kcs[lane] = uold; kce[lane] = uold;
+        kr[sl] = m;
+        kp[sl] = lastv; ks[sl] = 0; kcs[sl] = uold; kce[sl] = uold;
       }
     }
-    __syncwarp();
+    __syncwarp(seg);
     // ---- each owning lane decodes its own codes (all owners at once) ----
     // Walking its codes in order, the lane keeps the running value; a key
     // takes the first code whose value reaches it: that code's element is
     // its successor (rank 1 + codes before it), the value before is its
     // predecessor, and the code's bytes are the ones an insert replaces.
-    if ((owners >> lane) & 1u) {
+    if ((owners >> sl) & 1u) {
       uint32_t kq = 0;
-      while (ktl[kq] != lane) kq++;  // this lane's keys are consecutive
-      uint32_t tm = lc.term, st = (lane == 0) ? 8u : 0u, rank = 1u + B;
+      while (ktl[kq] != sl) kq++;  // this lane's keys are consecutive
+      uint32_t tm2 = lc.term, st = (sl == 0) ? 8u : 0u, rank = 1u + B;
       uint64_t val = V;
       bool firstc = true;
-      while (tm && kq < s && ktl[kq] == lane) {
-        const uint32_t tb8 = (uint32_t)__ffs(tm) - 1u;
-        tm &= tm - 1u;
-        const uint32_t own = compact7(window32(lc.x, st)) & mask7(tb8 + 1u - st);
+      while (tm2 && kq < s && ktl[kq] == sl) {
+        const uint32_t tb8 = (uint32_t)__ffs(tm2) - 1u;
+        tm2 &= tm2 - 1u;
+        const uint32_t own = compact7(window32<NW>(lc.x, st)) & mask7(tb8 + 1u - st);
         const uint32_t code = firstc ? pv + (own << ps) : own;
-        const uint32_t cs = 16u * lane + st - (firstc ? ps / 7u : 0u);
+        const uint32_t cs = kLB * sl + st - (firstc ? ps / 7u : 0u);
         const uint64_t prev = val;
         val += code;
-        while (kq < s && ktl[kq] == lane && kx[kq] <= val) {
+        while (kq < s && ktl[kq] == sl && kx[kq] <= val) {
           kr[kq] = rank | (kx[kq] == val ? 0x80000000u : 0u);
           kp[kq] = prev;
           ks[kq] = val;
           kcs[kq] = cs;
-          kce[kq] = 16u * lane + tb8 + 1u;
+          kce[kq] = kLB * sl + tb8 + 1u;
           kq++;
         }
         rank++;
@@ -441,56 +491,56 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
         firstc = false;
       }
     }
-    __syncwarp();
+    __syncwarp(seg);
     // ---- kept keys and their gaps ----
     uint32_t r = 0;
     bool keep = false;
-    if (lane < s) {
-      r = kr[lane];
+    if (sl < s) {
+      r = kr[sl];
       keep = valid && !(r & 0x80000000u);
     }
-    const unsigned kb = __ballot_sync(FULL, keep);
+    const unsigned kb = seg_ballot<SEG>(seg, sg, keep);
     const uint32_t nn = __popc(kb);
     uint64_t mx = 0, mp = 0, ms = 0;
     uint32_t mcs = 0, mce = 0;
-    if (keep) { mx = kx[lane]; mp = kp[lane]; ms = ks[lane]; mcs = kcs[lane]; mce = kce[lane]; }
-    __syncwarp();
+    if (keep) { mx = kx[sl]; mp = kp[sl]; ms = ks[sl]; mcs = kcs[sl]; mce = kce[sl]; }
+    __syncwarp(seg);
     if (keep) {
-      const uint32_t q = __popc(kb & lanemask_lt());
+      const uint32_t q = __popc(kb & lt_mask);
       kx[q] = mx; kp[q] = mp; ks[q] = ms; kcs[q] = mcs; kce[q] = mce; kr[q] = r;
     }
-    __syncwarp();
+    __syncwarp(seg);
     if (nn == 0) {
-      if (lane == 0) {
+      if (sl == 0) {
         a.T_state[t] = kUnchanged;
         a.T_newcnt[t] = m;
         a.T_newbytes[t] = uold;
       }
-      for (uint32_t cq = fc0 + lane; cq < fc1; cq += 32) a.chunk_cnt[cq] = 0;
-      __syncwarp();
+      for (uint32_t cq = fc0 + sl; cq < fc1; cq += SEG) a.chunk_cnt[cq] = 0;
+      __syncwarp(seg);
       continue;
     }
     bool lead = false;
-    if (lane < nn) lead = lane == 0 || kr[lane - 1] != kr[lane];
-    const unsigned lb = __ballot_sync(FULL, lead);
+    if (sl < nn) lead = sl == 0 || kr[sl - 1] != kr[sl];
+    const unsigned lb = seg_ballot<SEG>(seg, sg, lead);
     const uint32_t E = __popc(lb);
-    uint32_t e_os = 0, e_oe = 0, e_nl = 0, gend = 0, r0 = 0;
+    uint32_t e_os = 0, e_oe = 0, e_nl = 0, gend = 0, g0 = 0;
     if (lead) {
-      const unsigned after = lb & ~((2u << lane) - 1u);
+      const unsigned after = lb & ~((2u << sl) - 1u);
       gend = after ? (uint32_t)(__ffs(after) - 1) : nn;
-      r0 = kr[lane];
-      e_os = kcs[lane];
-      e_oe = kce[lane];
-      uint64_t prev = kx[lane];
-      uint32_t len = (r0 == 0) ? 8u : leb_len(kx[lane] - kp[lane]);
-      for (uint32_t q = lane + 1; q < gend; q++) { len += leb_len(kx[q] - prev); prev = kx[q]; }
-      if (r0 < m) len += leb_len(ks[lane] - prev);
+      g0 = kr[sl];
+      e_os = kcs[sl];
+      e_oe = kce[sl];
+      uint64_t prev = kx[sl];
+      uint32_t len = (g0 == 0) ? 8u : leb_len(kx[sl] - kp[sl]);
+      for (uint32_t q = sl + 1; q < gend; q++) { len += leb_len(kx[q] - prev); prev = kx[q]; }
+      if (g0 < m) len += leb_len(ks[sl] - prev);
       e_nl = len;
     }
-    const uint32_t eidx = __popc(lb & lanemask_lt());
+    const uint32_t eidx = __popc(lb & lt_mask);
     const int32_t delta = lead ? (int32_t)e_nl - (int32_t)(e_oe - e_os) : 0;
-    const int32_t dinc = warp_incl_scan(delta);
-    const int32_t total = __shfl_sync(FULL, dinc, 31);
+    const int32_t dinc = (int32_t)seg_scan<SEG, uint32_t>(seg, sl, (uint32_t)delta);
+    const int32_t total = (int32_t)__shfl_sync(seg, (uint32_t)dinc, SEG - 1, SEG);
     if (lead) {
       es[eidx] = e_os;
       ee[eidx] = e_oe;
@@ -500,53 +550,59 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
     const uint32_t nb = (uint32_t)((int32_t)uold + total);
     const uint32_t newc = m + nn;
     const uint64_t newhead = (kr[0] == 0) ? kx[0] : head;
-    __syncwarp();
+    __syncwarp(seg);
     if (nb > a.LB) {
-      if (lane == 0) {
+      if (sl == 0) {
         a.T_state[t] = kPending;
         a.T_newcnt[t] = newc;
         a.T_newbytes[t] = nb;
       }
-      for (uint32_t cq = fc0 + lane; cq < fc1; cq += 32) a.chunk_cnt[cq] = (cq == fc0) ? newc : 0u;
-      if (keep) credit(a, tb + lane);
-      __syncwarp();
+      for (uint32_t cq = fc0 + sl; cq < fc1; cq += SEG) a.chunk_cnt[cq] = (cq == fc0) ? newc : 0u;
+      if (keep) credit(a, tb + sl);
+      __syncwarp(seg);
       continue;
     }
     if (nb > 512) {  // fits the leaf but not this kernel's 512-byte buffer
-      if (lane == 0) {
+      if (sl == 0) {
         a.T_state[t] = kFallback;
         a.list_v1[atomicAdd(&a.st->n_v1, 1ull)] = t;
       }
-      __syncwarp();
+      __syncwarp(seg);
       continue;
     }
     const uint32_t wend = (max(uold, nb) + 15u) & ~15u;
-    // 16-byte chunks wholly before the first edit keep their bytes: those
-    // lanes neither rebuild nor rewrite them
-    const bool touched = p0 + 16u > es[0];
-    if (touched && p0 < wend) *reinterpret_cast<uint4*>(out + p0) = make_uint4(0u, 0u, 0u, 0u);
-    __syncwarp();
-    if (touched) splice_copy_words(w, p0, uold, out, E, es, ee, shc);
-    __syncwarp();
+    // lanes whose bytes lie wholly before the first edit keep them: they
+    // neither rebuild nor rewrite them
+    const bool touched = p0 + kLB > es[0];
+    if (touched)
+#pragma unroll
+      for (uint32_t q = 0; q < kLB; q += 16)
+        if (p0 + q < wend) *reinterpret_cast<uint4*>(out + p0 + q) = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp(seg);
+    if (touched) splice_copy_words<NW>(w, p0, uold, out, E, es, ee, shc);
+    __syncwarp(seg);
     if (lead) {
       uint8_t* o = out + en[eidx];
-      uint64_t prev = kx[lane];
-      if (r0 == 0) {
+      uint64_t prev = kx[sl];
+      if (g0 == 0) {
 #pragma unroll
         for (int b = 0; b < 8; b++) o[b] = (uint8_t)(prev >> (8 * b));
         o += 8;
       } else {
-        o += leb_put(o, prev - kp[lane]);
+        o += leb_put(o, prev - kp[sl]);
       }
-      for (uint32_t q = lane + 1; q < gend; q++) { o += leb_put(o, kx[q] - prev); prev = kx[q]; }
-      if (r0 < m) leb_put(o, ks[lane] - prev);
+      for (uint32_t q = sl + 1; q < gend; q++) { o += leb_put(o, kx[q] - prev); prev = kx[q]; }
+      if (g0 < m) leb_put(o, ks[sl] - prev);
     }
-    __syncwarp();
-    if (touched && p0 < wend)
-      *reinterpret_cast<uint4*>(leafp + p0) = *reinterpret_cast<const uint4*>(out + p0);
-    nbytes += wend - min(wend, es[0] & ~15u);
-    if (keep) credit(a, tb + lane);
-    if (lane == 0) {
+    __syncwarp(seg);
+    if (touched)
+#pragma unroll
+      for (uint32_t q = 0; q < kLB; q += 16)
+        if (p0 + q < wend)
+          *reinterpret_cast<uint4*>(leafp + p0 + q) = *reinterpret_cast<const uint4*>(out + p0 + q);
+    if (sl == 0) nbytes += wend - min(wend, es[0] & ~15u);
+    if (keep) credit(a, tb + sl);
+    if (sl == 0) {
       a.used[j] = nb;
       a.cnt[j] = newc;
       a.heads[j] = newhead;
@@ -554,10 +610,11 @@ __global__ void __launch_bounds__(kT, 4) k_insert_lane(MergeArgs a) {
       a.T_newcnt[t] = newc;
       a.T_newbytes[t] = nb;
     }
-    for (uint32_t cq = fc0 + lane; cq < fc1; cq += 32) a.chunk_cnt[cq] = 0;
-    __syncwarp();
+    for (uint32_t cq = fc0 + sl; cq < fc1; cq += SEG) a.chunk_cnt[cq] = 0;
+    __syncwarp(seg);
     }
   }
+  nbytes = warp_sum(sl == 0 ? nbytes : 0ull);
   if (a.prof && lane == 0 && nbytes) atomicAdd(a.prof, nbytes);
 }
 
@@ -578,7 +635,8 @@ __global__ void __launch_bounds__(kT) k_classify(MergeArgs a) {
       tb = a.T_begin[t];
       te = a.T_begin[t + 1];
       const uint32_t uold = a.T_oldused[t];
-      if (small_slice(tb, te, uold)) cls = (!a.is_delete && uold <= 512 && !a.raw) ? 0u : 1u;
+      if (small_slice(tb, te, uold))
+        cls = (!a.is_delete && uold <= 512 && !a.raw && te - tb <= (uint32_t)kLaneSeg) ? 0u : 1u;
       else {
         cls = 2;
         fc0 = a.T_first_chunk[t];
@@ -1946,7 +2004,7 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
         1, std::min<uint64_t>((k + swarps - 1) / swarps, (uint64_t)h->num_sms * 8));
     if (!is_delete) {
       ma.prof = prof_bytes(h, PH_MERGE);
-      k_insert_lane<<<sgrid, 256, kLaneWarpBytes * 8, st>>>(ma);
+      k_insert_lane<kLaneSeg><<<sgrid, 256, lane_warp_bytes(kLaneSeg) * 8, st>>>(ma);
       h->launches++;
       ma.prof = nullptr;
     }
