@@ -663,7 +663,8 @@ def skew(a, dev, T, timed):
     from paper_2305_05055_gb300 import workloads as W
     n0, rounds, ki, kd = int(5e7), int(a.skew_rounds), 10 ** 5, 5 * 10 ** 4
     base = W.uniform_keys(4, n0, bits=34)
-    S = np.unique(base)
+    S = np.sort(base)
+    S = S[np.concatenate([[True], S[1:] != S[:-1]])]  # distinct keys (np.unique is slow here)
     g = cp.CPMA(T(base), leaf_bytes=a.leaf_bytes)
     del base
     L0, b0 = g.leaves(), g.bytes()

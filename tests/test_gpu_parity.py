@@ -9,6 +9,7 @@ import torch
 import oracle
 from paper_2305_05055_gb300 import cpma as cp
 from paper_2305_05055_gb300 import workloads as W
+from setops import sorted_unique, union
 
 pytestmark = pytest.mark.gpu
 M64 = (1 << 64) - 1
@@ -449,12 +450,12 @@ def test_full_scan_large(LB):
     also after a skewed insert that leaves leaves of very different fill."""
     keys = W.uniform_keys(71, 10 ** 7, bits=40)
     g = cp.CPMA(T(keys), leaf_bytes=LB)
-    S = np.unique(keys)
+    S = sorted_unique(keys)
     s, c = g.sum()
     assert int(cp.to_u64(s)[0]) == int(np.sum(S, dtype=np.uint64)) and int(c.item()) == S.size
     ins = W.zipf_keys(72, 10 ** 6, bits=40)
     g.insert_batch(T(ins))
-    S = np.union1d(S, ins)
+    S = union(S, ins)
     s, c = g.sum()
     assert int(cp.to_u64(s)[0]) == int(np.sum(S, dtype=np.uint64)) and int(c.item()) == S.size
 
@@ -513,3 +514,30 @@ def test_pma_update_sequence(LB):
     r_, c_ = g.range_reduce(T(lo), T(hi), "max", 3, 1)
     wr, wc = p.range_reduce(lo, hi, "max", 3, 1)
     assert np.array_equal(cp.to_u64(r_), wr) and np.array_equal(cp.to_u64(c_), wc)
+
+
+def test_degenerate_batches_and_queries():
+    """Batches of one repeated key, of keys all present, deletes from an
+    empty set, empty query batches, and a batch length at the 2^31 limit
+    (rejected before anything is read)."""
+    base = W.uniform_keys(81, 50000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=512)
+    o = oracle.SeqCPMA(base, leaf_bytes=512)
+    p = oracle.PlainSet(base)
+    same = np.full(5000, 123456789, dtype=np.uint64)
+    assert int(g.insert_batch(T(same)).item()) == o.insert_batch(same) == p.insert_batch(same) == 1
+    present = p.S[::3].copy()
+    assert int(g.insert_batch(T(present)).item()) == o.insert_batch(present) == 0
+    same_layout(g, o)
+    e = cp.CPMA(None, leaf_bytes=256)
+    assert int(e.delete_batch(T(base[:100])).item()) == 0 and e.size() == 0
+    z = T(np.zeros(0, np.uint64))
+    assert int(g.insert_batch(z).item()) == 0 and int(g.delete_batch(z).item()) == 0
+    assert g.has_batch(z).numel() == 0
+    s, c = g.range_map(z, z)
+    assert s.numel() == 0 and c.numel() == 0
+    one = T(np.array([5], np.uint64))
+    added = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rc = cp.lib().cpma_insert_batch(g.handle, cp._ptr(one), 1 << 31, 0, cp._ptr(added), None)
+    assert rc == cp.CPMA_EINVAL
+    same_layout(g, o)
