@@ -289,6 +289,12 @@ def main():
     build_s = time.perf_counter() - t0
     batches = [T(W.uniform_keys(10 ** 6 + 1000 * rank + i, k, bits=40))
                for i in range(nwarm + nsteps)]
+    # the library's fastest form for this batch size: scratch reserved and
+    # the batch front segment replayed as a CUDA graph (captured, with its
+    # profiling event nodes, during the warm-up steps)
+    g.reserve(k)
+    g.use_graphs(1 << 21)
+    g.profile(True)
     for i in range(nwarm):
         g.insert_batch(batches[i])
     torch.cuda.synchronize()
@@ -296,7 +302,7 @@ def main():
     torch.cuda.synchronize()
 
     # ---- timed region: K insert steps ----
-    g.profile(True)
+    g.profile(True)          # reset the per-phase counters
     l0 = g.launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
@@ -375,6 +381,7 @@ def main():
         "config": {"workload": "batch insert of 1e6 uniform 40-bit keys into a CPMA holding "
                                "1e8 keys (grows by 1e6 per step)",
                    "n": n, "batch": k, "leaf_bytes": a.leaf_bytes,
+                   "graphs": True, "graph_stats": g.graph_stats(),
                    "l2": "inputs larger than L2 (CPMA %.2f GB, fresh 8 MB batch per step)"
                          % (g.bytes() / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},

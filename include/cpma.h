@@ -278,8 +278,10 @@ int cpma_reserve(cpma_t* h, uint64_t max_batch, uint64_t max_queries, int tagged
  * sorted, insert or delete) and replayed afterwards; a graph is captured
  * again after the leaf arrays are replaced (resize) or a scratch buffer it
  * uses moved; the 8 most recently used are kept.  Sets, counts and layouts
- * are the same with and without graphs.  While per-phase profiling is on,
- * updates take the launch-by-launch path.  Graphs pay off for small batches,
+ * are the same with and without graphs.  Per-phase profiling works with
+ * graphs: a graph captured while profiling is on carries its phase
+ * boundaries as event-record nodes, resolved after every replay.  Graphs pay
+ * off for small batches,
  * whose time is launch latency; larger batches do up to 1/8 more sort and
  * route work.  Errors: CPMA_EINVAL (null handle). */
 int cpma_use_graphs(cpma_t* h, uint64_t max_batch);

@@ -85,6 +85,19 @@ void prof_begin(const cpma* hc, int phase, cudaStream_t st) {
   if (!p.on) return;
   if (p.open_rec.phase >= 0) prof_end(h, st);
   p.open_rec.phase = phase;
+  if (p.capturing) {
+    // events of the graph being captured: recorded by every replay
+    p.open_rec.a = p.open_rec.b = nullptr;
+    p.open_rec.pooled = false;
+    if (cudaEventCreate(&p.open_rec.a) != cudaSuccess ||
+        cudaEventCreate(&p.open_rec.b) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cudaEventRecordWithFlags(p.open_rec.a, st, cudaEventRecordExternal);
+    return;
+  }
+  p.open_rec.pooled = true;
   p.open_rec.a = take_event(p);
   p.open_rec.b = take_event(p);
   if (p.open_rec.a) cudaEventRecord(p.open_rec.a, st);
@@ -94,6 +107,20 @@ void prof_end(const cpma* hc, cudaStream_t st) {
   cpma* h = const_cast<cpma*>(hc);
   Prof& p = h->prof;
   if (!p.on || p.open_rec.phase < 0) return;
+  if (p.capturing) {
+    if (p.open_rec.b) cudaEventRecordWithFlags(p.open_rec.b, st, cudaEventRecordExternal);
+    if (p.ncap == p.cap_max) {
+      int nc = p.cap_max ? 2 * p.cap_max : 16;
+      Prof::Rec* np = new Prof::Rec[nc];
+      for (int i = 0; i < p.ncap; i++) np[i] = p.cap_recs[i];
+      delete[] p.cap_recs;
+      p.cap_recs = np;
+      p.cap_max = nc;
+    }
+    p.cap_recs[p.ncap++] = p.open_rec;
+    p.open_rec.phase = -1;
+    return;
+  }
   if (p.open_rec.b) cudaEventRecord(p.open_rec.b, st);
   if (p.npending == p.cap) {
     int nc = p.cap ? 2 * p.cap : 64;
@@ -119,10 +146,29 @@ void prof_resolve(const cpma* hc) {
     } else {
       cudaGetLastError();
     }
-    give_event(p, r.a);
-    give_event(p, r.b);
+    if (r.pooled) {
+      give_event(p, r.a);
+      give_event(p, r.b);
+    }
   }
   p.npending = 0;
+}
+
+void prof_push(const cpma* hc, const Prof::Rec* recs, int n, const unsigned long long* host_bytes) {
+  cpma* h = const_cast<cpma*>(hc);
+  Prof& p = h->prof;
+  for (int i = 0; i < n; i++) {
+    if (p.npending == p.cap) {
+      int nc = p.cap ? 2 * p.cap : 64;
+      Prof::Rec* np = new Prof::Rec[nc];
+      for (int q = 0; q < p.npending; q++) np[q] = p.pending[q];
+      delete[] p.pending;
+      p.pending = np;
+      p.cap = nc;
+    }
+    p.pending[p.npending++] = recs[i];
+  }
+  for (int i = 0; i < PH_N; i++) p.host_bytes[i] += host_bytes[i];
 }
 
 }  // namespace cpmaimpl
@@ -151,6 +197,7 @@ void release_all(cpma* h) {
                  &s.win_leaf_off, &s.win_elem_off, &s.win_dst_off, &s.partials, &s.partials_q, &s.q_first,
                  &s.q_items, &s.q_off, &s.stage, &s.q_lo, &s.q_hi, &s.q_rank, &s.fh})
     release(*b);
+  prof_resolve(h);  // before the graphs (and their events) go
   graph_cache_free(h);
   cudaFree(h->data);
   cudaFree(h->used);
@@ -162,6 +209,9 @@ void release_all(cpma* h) {
   for (int i = 0; i < h->prof.npool; i++) cudaEventDestroy(h->prof.pool[i]);
   delete[] h->prof.pool;
   delete[] h->prof.pending;
+  delete[] h->prof.cap_recs;
+  h->prof.cap_recs = nullptr;
+  h->prof.ncap = h->prof.cap_max = 0;
   h->prof.pool = nullptr;
   h->prof.pending = nullptr;
   h->prof.npool = h->prof.pool_cap = h->prof.npending = h->prof.cap = 0;

@@ -92,8 +92,16 @@ enum Phase {
 // and resolved at the next host synchronisation, so profiling adds no waits.
 struct Prof {
   bool on = false;
-  struct Rec { int phase; cudaEvent_t a, b; };
-  Rec open_rec{-1, nullptr, nullptr};
+  // pooled: the events go back to the pool once resolved; a captured graph's
+  // events belong to the graph and are recorded again by every replay
+  struct Rec { int phase; cudaEvent_t a, b; bool pooled; };
+  Rec open_rec{-1, nullptr, nullptr, true};
+  // while a graph is being captured: its event pairs and its host-side byte
+  // counts, which each replay adds
+  bool capturing = false;
+  Rec* cap_recs = nullptr;
+  int ncap = 0, cap_max = 0;
+  unsigned long long cap_host_bytes[PH_N] = {0};
   Rec* pending = nullptr;
   int npending = 0, cap = 0;
   cudaEvent_t* pool = nullptr;
@@ -201,8 +209,13 @@ int sync_status(cpma* h, cudaStream_t st);
 void prof_begin(const cpma* h, int phase, cudaStream_t st);
 void prof_end(const cpma* h, cudaStream_t st);
 void prof_resolve(const cpma* h);  // call only after the stream is idle
+// queue a replayed graph's event pairs for resolution and add its host bytes
+void prof_push(const cpma* h, const Prof::Rec* recs, int n, const unsigned long long* host_bytes);
 inline void prof_add_bytes(const cpma* h, int phase, unsigned long long b) {
-  if (h->prof.on) const_cast<cpma*>(h)->prof.host_bytes[phase] += b;
+  Prof& p = const_cast<cpma*>(h)->prof;
+  if (!p.on) return;
+  if (p.capturing) p.cap_host_bytes[phase] += b;
+  else p.host_bytes[phase] += b;
 }
 inline unsigned long long* prof_bytes(const cpma* h, int phase) {
   return h->prof.on ? h->prof.d_bytes + phase : nullptr;

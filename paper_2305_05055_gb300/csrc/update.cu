@@ -22,6 +22,7 @@
 //     byte-balanced cut points and re-encode every destination leaf.
 //     A resize is the same with the whole array as one window and L' leaves.
 #include <algorithm>
+#include <vector>
 
 #include "dev_common.cuh"
 #include "internal.h"
@@ -2104,8 +2105,20 @@ struct GraphSlot {
   cudaGraphExec_t exec = nullptr;
   uint64_t K = 0, last_use = 0, launches = 0;
   int sorted = 0, is_delete = 0;
+  bool prof = false;  // captured with per-phase profiling (event record nodes)
   FrontSig sig{};
   Front f;
+  std::vector<Prof::Rec> recs;        // the graph's event pairs
+  unsigned long long host_bytes[PH_N] = {0};
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    for (Prof::Rec& r : recs) {
+      if (r.a) cudaEventDestroy(r.a);
+      if (r.b) cudaEventDestroy(r.b);
+    }
+    recs.clear();
+  }
 };
 
 struct GraphCache {
@@ -2140,8 +2153,10 @@ int run_front_graph(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int
   GraphCache& c = *static_cast<GraphCache*>(h->graphs);
   const FrontSig sig = front_sig(h);
   GraphSlot* slot = nullptr;
+  const bool prof = h->prof.on;
   for (GraphSlot& g : c.slot)
-    if (g.exec && g.K == K && g.sorted == sorted && g.is_delete == is_delete && g.sig == sig)
+    if (g.exec && g.K == K && g.sorted == sorted && g.is_delete == is_delete && g.sig == sig &&
+        g.prof == prof)
       slot = &g;
   if (!slot) {
     slot = &c.slot[0];
@@ -2149,18 +2164,30 @@ int run_front_graph(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int
       if (!g.exec || g.last_use < slot->last_use) slot = &g;
     if (slot->exec) {
       // the previous update on this handle has been waited for, so no
-      // launch of this graph is still in flight
-      cudaGraphExecDestroy(slot->exec);
-      slot->exec = nullptr;
+      // launch of this graph is still in flight; its event pairs were
+      // resolved at that wait
+      slot->release();
     }
     if (!h->cap_stream)
       CPMA_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     const uint64_t l0 = h->launches;
+    Prof& pr = h->prof;
+    if (prof) {
+      pr.capturing = true;
+      pr.ncap = 0;
+      for (int i = 0; i < PH_N; i++) pr.cap_host_bytes[i] = 0;
+    }
     CPMA_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     set_capturing(true);
     int rc = run_front(h, stage, K, sorted, is_delete, h->cap_stream, nullptr, nullptr, 0,
                        &slot->f);
     set_capturing(false);
+    if (prof) {
+      pr.capturing = false;
+      slot->recs.assign(pr.cap_recs, pr.cap_recs + pr.ncap);
+      for (int i = 0; i < PH_N; i++) slot->host_bytes[i] = pr.cap_host_bytes[i];
+      pr.ncap = 0;
+    }
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
     if (rc == CPMA_OK) rc = check_cuda(e);
@@ -2171,9 +2198,11 @@ int run_front_graph(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int
     h->launches = l0;
     if (rc != CPMA_OK) {
       cudaGetLastError();
+      slot->release();  // events created during the failed capture
       return rc;
     }
     slot->exec = ex;
+    slot->prof = prof;
     slot->K = K;
     slot->sorted = sorted;
     slot->is_delete = is_delete;
@@ -2182,6 +2211,7 @@ int run_front_graph(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int
   }
   slot->last_use = ++c.clock;
   CPMA_CUDA(cudaGraphLaunch(slot->exec, st));
+  if (slot->prof) prof_push(h, slot->recs.data(), (int)slot->recs.size(), slot->host_bytes);
   h->launches += slot->launches;
   h->graph_launches++;
   *f = slot->f;
@@ -2193,8 +2223,7 @@ int run_front_graph(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int
 void graph_cache_free(cpma* h) {
   if (!h->graphs) return;
   GraphCache* c = static_cast<GraphCache*>(h->graphs);
-  for (GraphSlot& g : c->slot)
-    if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (GraphSlot& g : c->slot) g.release();
   delete c;
   h->graphs = nullptr;
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -2293,7 +2322,7 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
     return run_rebuild(h, d_keys, k, sorted, is_delete, d_delta, st);
   Scratch& s = h->s;
   Front f;
-  if (k <= h->graph_max_batch && !tags && !h->prof.on && graph_bucket(k) < (1ull << 31)) {
+  if (k <= h->graph_max_batch && !tags && graph_bucket(k) < (1ull << 31)) {
     CPMA_TRY(run_front_graph(h, d_keys, k, sorted, is_delete, st, &f));
   } else {
     CPMA_TRY(front_scratch(h, k, tags != nullptr, st));

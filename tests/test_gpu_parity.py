@@ -541,3 +541,26 @@ def test_degenerate_batches_and_queries():
     rc = cp.lib().cpma_insert_batch(g.handle, cp._ptr(one), 1 << 31, 0, cp._ptr(added), None)
     assert rc == cp.CPMA_EINVAL
     same_layout(g, o)
+
+
+def test_profiling_with_graph_replays():
+    """Per-phase profiling stays live when the front segment is a replayed
+    graph (its phase boundaries are event nodes): phase times and calls
+    accumulate per replay, and results still match the oracle."""
+    base = W.uniform_keys(91, 100000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=512)
+    o = oracle.SeqCPMA(base, leaf_bytes=512)
+    g.use_graphs(1 << 20)
+    g.reserve(3000)
+    g.profile(True)
+    for r in range(5):
+        keys = W.uniform_keys(920 + r, 3000, bits=40)
+        assert int(g.insert_batch(T(keys)).item()) == o.insert_batch(keys)
+    prof = g.profile_read()
+    same_layout(g, o)
+    st = g.graph_stats()
+    assert st["launches"] == 5 and st["captures"] >= 1
+    for ph in ("sort", "route", "merge"):
+        assert prof[ph]["calls"] == 5 and prof[ph]["ms"] > 0, (ph, prof[ph])
+    assert prof["merge"]["bytes"] > 0
+    g.profile(False)
