@@ -857,7 +857,7 @@ __global__ void __launch_bounds__(kT, 3) k_merge_small(MergeArgs a) {
 // when they fit.  WRITE == true: recompute the items of pending leaves and
 // store their merged elements in the overflow buffer.
 template <bool WRITE>
-__global__ void __launch_bounds__(kT) k_merge(MergeArgs a) {
+__global__ void __launch_bounds__(kT, 2) k_merge(MergeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   if (a.st->err) return;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
