@@ -114,6 +114,18 @@ class Server:
         self.s_read = torch.cuda.Stream()
         self.epochs: list[EpochLog] = []
         self.stats = dict(epochs=0, admitted=0, deferred=0, max_epoch_requests=0)
+        # pinned staging for a run's keys and tags, reused: every run's copy
+        # has completed before the next run is staged (each run ends with a
+        # wait on the update stream)
+        self._pin_keys = torch.empty(0, dtype=torch.int64).pin_memory()
+        self._pin_tags = torch.empty(0, dtype=torch.int32).pin_memory()
+
+    def _staging(self, n: int):
+        if self._pin_keys.numel() < n:
+            cap = max(n, 2 * self._pin_keys.numel(), 1 << 16)
+            self._pin_keys = torch.empty(cap, dtype=torch.int64).pin_memory()
+            self._pin_tags = torch.empty(cap, dtype=torch.int32).pin_memory()
+        return self._pin_keys[:n], self._pin_tags[:n]
 
     def _admit(self, waiting: deque, now: float) -> list:
         used = self.g.bytes() * 3  # structure plus the library's scratch and a resize
@@ -142,12 +154,14 @@ class Server:
         return runs
 
     def _prepare_run(self, reqs: list):
-        keys = np.concatenate([r.keys for r in reqs])
-        tags = np.concatenate([np.full(r.keys.size, i, dtype=np.int32)
-                               for i, r in enumerate(reqs)])
+        sizes = [r.keys.size for r in reqs]
+        n = sum(sizes)
+        pk, pt = self._staging(n)
+        np.concatenate([r.keys.view(np.int64) for r in reqs], out=pk.numpy())
+        pt.numpy()[:] = np.repeat(np.arange(len(reqs), dtype=np.int32), sizes)
         with torch.cuda.stream(self.s_upd):
-            dk = torch.from_numpy(keys.view(np.int64)).pin_memory().to(self.dev, non_blocking=True)
-            dt = torch.from_numpy(tags).pin_memory().to(self.dev, non_blocking=True)
+            dk = pk.to(self.dev, non_blocking=True)
+            dt = pt.to(self.dev, non_blocking=True)
             sk, st = cp.cpma_sort_batch(self.g.handle, dk, dt, stream=self.s_upd)
         return sk, st
 
