@@ -319,9 +319,11 @@ def main():
     ms, value = aggregate(ms, nsteps * k, dist)
 
     # roofline of the dominant kernel of the step
-    upd = ["sort", "route", "merge", "merge_other", "count", "redistribute", "finish"]
+    upd = ["sort", "route", "merge", "merge_lane", "merge_other", "count", "redistribute",
+           "finish"]
     dom = max(upd, key=lambda p: prof[p]["ms"])
-    kernel_of = {"merge": "k_insert_lane", "merge_other": "k_merge_small+k_merge",
+    kernel_of = {"merge": "k_insert_thread", "merge_lane": "k_insert_lane",
+                 "merge_other": "k_merge_small+k_merge",
                  "sort": "radix sort", "route": "route", "count": "counting",
                  "redistribute": "redistribute", "finish": "k_fix_heads"}
     def roof(p, pk=hbm_peak):
@@ -415,7 +417,8 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps, r
 
-    kname = {"range": "k_range", "sum": "k_sum", "has": "k_has", "merge": "k_insert_lane",
+    kname = {"range": "k_range", "sum": "k_sum", "has": "k_has", "merge": "k_insert_thread",
+             "merge_lane": "k_insert_lane",
              "merge_other": "k_merge_small+k_merge"}
     def roof(prof, p):
         msp, by, calls = prof[p]["ms"], prof[p]["bytes"], max(1, prof[p]["calls"])
@@ -514,7 +517,8 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
         removed += int(rm.item())
     prof = g.profile_read()
     g.profile(False)
-    upd = ["sort", "route", "merge", "merge_other", "count", "redistribute", "finish"]
+    upd = ["sort", "route", "merge", "merge_lane", "merge_other", "count", "redistribute",
+           "finish"]
     dom = max(upd, key=lambda p: prof[p]["ms"])
     out["delete"] = {"value": removed / (tot / 1e3), "unit": "keys/s",
                      "batches": min(5, len(ins_batches)), "batch": int(a.batch),

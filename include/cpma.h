@@ -299,13 +299,15 @@ int cpma_reset_stats(cpma_t* h);
  * events around each phase on the caller's stream, resolved at the host
  * synchronisations the update calls already make, and counts each phase's
  * algorithmic bytes (what the method must read and write).  Phases, in
- * order: 0 sort, 1 route, 2 merge of small inserts (the lane-granular
- * kernel), 3 counting (incl. overflow write), 4 redistribute/resize,
- * 5 finish (head fix-up), 6 has, 7 range routing + scan, 8 range scan of the
- * leaves, 9 sum, 10 the other merges (deletes, large slices, fallbacks).
+ * order: 0 sort, 1 route, 2 merge of inserts of a few keys per leaf (the
+ * thread-granular kernel), 3 counting (incl. overflow write),
+ * 4 redistribute/resize, 5 finish (head fix-up), 6 has, 7 range routing +
+ * scan, 8 range scan of the leaves, 9 sum, 10 the other merges (deletes,
+ * large slices, fallbacks), 11 merge of other small inserts (the
+ * lane-granular kernel).
  * cpma_profile_read synchronises the device and copies up to nphases entries
  * (any pointer may be NULL). */
-#define CPMA_NPHASES 11
+#define CPMA_NPHASES 12
 int cpma_profile(cpma_t* h, int enable);
 int cpma_profile_read(cpma_t* h, double* ms, uint64_t* bytes, uint64_t* calls, int nphases);
 

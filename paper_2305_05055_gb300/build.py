@@ -13,7 +13,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcpma.so")
 UNITS = ["cpma.cu", "scan.cu", "sort.cu", "update.cu", "query.cu"]
-HEADERS = ["dev_common.cuh", "internal.h"]
+HEADERS = ["dev_common.cuh", "internal.h", "leaf_thread.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -350,7 +350,7 @@ def cpma_graph_stats(h) -> dict:
 
 
 PHASES = ("sort", "route", "merge", "count", "redistribute", "finish", "has",
-          "range_prep", "range", "sum", "merge_other")
+          "range_prep", "range", "sum", "merge_other", "merge_lane")
 
 
 def cpma_profile(h, enable: bool = True):

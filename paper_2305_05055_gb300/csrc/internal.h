@@ -34,7 +34,8 @@ struct Status {
   ull n_lane;      // touched leaves for the lane-granular insert
   ull n_v1;        // touched leaves for the element-array splice
   ull n_gen;       // work items for the general merge
-  ull pad[10];
+  ull n_thr;       // touched leaves for the thread-granular insert
+  ull pad[9];
   ull empties;     // empty leaves in the structure (written by the head
                    // fix-up; not cleared at the start of a batch)
 };
@@ -85,7 +86,7 @@ struct Scratch {
 // Profiling phases (cpma_profile_read order).
 enum Phase {
   PH_SORT = 0, PH_ROUTE, PH_MERGE, PH_COUNT, PH_REDIST, PH_FINISH,
-  PH_HAS, PH_RANGE_PREP, PH_RANGE, PH_SUM, PH_MERGE2, PH_N
+  PH_HAS, PH_RANGE_PREP, PH_RANGE, PH_SUM, PH_MERGE2, PH_MERGE_LANE, PH_N
 };
 
 // Optional per-phase device timing: event pairs recorded around each phase

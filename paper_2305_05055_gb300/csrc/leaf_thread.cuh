@@ -1,0 +1,413 @@
+// Thread-granular insert of a few keys into one leaf of byte codes (Sec. 4
+// batch merge, Sec. 5 leaf format: an 8-byte little-endian head, then the
+// deltas to the following keys as unsigned LEB128 codes, packed left, zero
+// bytes after the used ones).
+//
+// One thread owns one leaf.  Pass A decodes the leaf byte by byte and places
+// every key of the slice: before the head (a new head), inside the gap that
+// one code spans (the code is split), or after the last element (appended);
+// a key equal to an element or to the slice key before it is skipped.  Keys
+// sharing a gap form one edit: old bytes [os, oe) replaced by nl new bytes.
+// Every edit of an insert grows or keeps the size (a split code never needs
+// more bytes than its two parts), so pass B rewrites the leaf in place from
+// the end backwards, 16 bytes at a time: each destination chunk gathers the
+// old bytes that land in it (one shift per segment between edits) and is
+// stored whole, before the edits' own bytes are written.  Every read of pass
+// B is of a chunk at or below the one being written, so it sees old bytes.
+//
+// The functions are __host__ __device__ so that the same code can be run on
+// the host.
+#pragma once
+#include <stdint.h>
+#include <string.h>
+
+#if defined(__CUDACC__)
+#define LT_HD __host__ __device__ __forceinline__
+#else
+#define LT_HD inline
+#endif
+
+namespace leafthr {
+
+constexpr uint32_t kKeys = 4;  // slice keys per leaf on this path
+
+// key record kinds
+constexpr uint32_t kGap = 0;    // inside the gap of the code [cs, ce)
+constexpr uint32_t kHead = 1;   // before the head
+constexpr uint32_t kAfter = 2;  // after the last element
+constexpr uint32_t kSkip = 3;   // present already, or a repeat of the slice key before it
+constexpr uint32_t kChunk = 4;  // (pass A, step 1) in a code ending in the chunk at cs
+
+// results
+constexpr uint32_t kUnchanged = 0;  // every key present: nothing written
+constexpr uint32_t kWritten = 1;    // leaf rewritten in place
+constexpr uint32_t kTooBig = 2;     // result exceeds the leaf: nothing written
+constexpr uint32_t kLongCode = 3;   // a code of more than 4 bytes: nothing written
+constexpr uint32_t kBadCount = 4;   // decoded count differs from the stored one
+
+struct Result {
+  uint32_t nb;       // new used bytes
+  uint32_t newc;     // new element count
+  uint32_t added;    // bit q: slice key q was added
+  uint32_t wlo, whi; // byte range rewritten (kWritten)
+  uint64_t newhead;
+};
+
+LT_HD uint32_t fshr(uint32_t lo, uint32_t hi, uint32_t sh) {  // low word of (hi:lo) >> sh, sh < 32
+#if defined(__CUDA_ARCH__)
+  return __funnelshift_r(lo, hi, sh);
+#else
+  return sh ? (lo >> sh) | (hi << (32u - sh)) : lo;
+#endif
+}
+
+LT_HD void ld16(const uint8_t* p, uint32_t (&w)[4]) {
+#if defined(__CUDA_ARCH__)
+  const uint4 v = *reinterpret_cast<const uint4*>(p);
+  w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+#else
+  memcpy(w, p, 16);
+#endif
+}
+
+LT_HD void st16(uint8_t* p, const uint32_t (&w)[4]) {
+#if defined(__CUDA_ARCH__)
+  *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+#else
+  memcpy(p, w, 16);
+#endif
+}
+
+LT_HD uint32_t popc(uint32_t x) {
+#if defined(__CUDA_ARCH__)
+  return (uint32_t)__popc(x);
+#else
+  return (uint32_t)__builtin_popcount(x);
+#endif
+}
+
+LT_HD uint32_t bmask4(uint32_t b4) {  // 4 bits -> 0x00 / 0xFF bytes
+  return ((b4 * 0x00204081u) & 0x01010101u) * 0xFFu;
+}
+
+LT_HD uint32_t leb_bytes(uint64_t d) {  // unsigned LEB128 length of d
+#if defined(__CUDA_ARCH__)
+  const uint32_t bl = 64u - (uint32_t)__clzll((long long)(d | 1ull));
+#else
+  const uint32_t bl = 64u - (uint32_t)__builtin_clzll(d | 1ull);
+#endif
+  return (bl + 6u) / 7u;
+}
+
+LT_HD uint32_t leb_write(uint8_t* p, uint64_t d) {
+  uint32_t n = 0;
+  while (d >= 128u) { p[n++] = (uint8_t)(d | 0x80u); d >>= 7; }
+  p[n++] = (uint8_t)d;
+  return n;
+}
+
+LT_HD uint64_t pick(const uint64_t (&y)[kKeys], uint32_t q) {
+  static_assert(kKeys == 4, "four slice keys");
+  return q == 0 ? y[0] : q == 1 ? y[1] : q == 2 ? y[2] : y[3];
+}
+
+// Per-thread scratch: arrays of kKeys entries at stride `rs` (key records and
+// edits), so that a block's threads index shared memory without conflicts.
+struct Scratch {
+  uint32_t* rpos;   // key q: cs | ce << 12 | kind << 24
+  uint64_t* rval;   // key q: successor value (kGap), the head (kHead), the last value (kAfter)
+  uint32_t* rcode;  // key q: value of the code [cs, ce) (kGap)
+  uint32_t* epos;   // edit e: os | oe << 12 | kind << 24
+  int32_t* esa;     // edit e: total size change of edits 0..e
+  uint32_t* ekey;   // edit e: first key | end key << 8 | nl << 16
+  uint32_t rs;
+};
+
+LT_HD uint32_t byte_of(uint32_t v, int i) {  // byte i of v, zero-extended
+#if defined(__CUDA_ARCH__)
+  return __byte_perm(v, 0u, 0x4440u + (uint32_t)i);
+#else
+  return (v >> (8 * i)) & 0xFFu;
+#endif
+}
+
+// Pass A, step 1, over one 16-byte chunk (FIRST: the chunk holding the
+// head; its first 8 bytes are skipped).  Every byte adds its 7 payload bits
+// times pw = 128^(bytes of its code before it) to tot, so tot is the sum of
+// the codes completed so far in the chunk plus the open code's bits (tot
+// enters with the bits the open code got in earlier chunks); tt keeps tot as
+// of the last terminator.  pwmax >= 2^28 marks a code of more than 4 bytes
+// (pw wraps to 0 after that, harmlessly).
+template <bool FIRST>
+LT_HD void sum_chunk(const uint32_t (&w)[4], uint32_t& tot, uint32_t& tt, uint32_t& pw,
+                     uint32_t& pwmax) {
+#pragma unroll
+  for (int b = FIRST ? 8 : 0; b < 16; b++) {
+    const uint32_t wb = w[b >> 2];
+    tot += (byte_of(wb, b & 3) & 0x7Fu) * pw;
+    const bool term = (wb & (0x80u << (8 * (b & 3)))) == 0u;
+    pwmax = pwmax > pw ? pwmax : pw;
+    tt = term ? tot : tt;
+    pw = term ? 1u : pw << 7;
+  }
+}
+
+// Pass A, step 2: the codes of the chunk at p0 take keys q..q1-1 (all of
+// them: their values lie between the element before the chunk and the last
+// element completed in it).  Decode the chunk byte by byte from the state it
+// was entered with (val0: the element before it; carry0, g0: the bits and
+// byte count of the code open at p0) and give each key its gap.
+LT_HD void place_in_chunk(const uint8_t* leafp, uint32_t uold, uint32_t p0, uint64_t val0,
+                          uint32_t carry0, uint32_t g0, const uint64_t (&y)[kKeys], uint32_t q,
+                          uint32_t q1, const Scratch& S) {
+  uint32_t w[4];
+  ld16(leafp + p0, w);
+  if (p0 + 16u > uold) {
+    const uint32_t keep = (1u << (uold - p0)) - 1u;
+#pragma unroll
+    for (int i = 0; i < 4; i++) w[i] &= bmask4((keep >> (4 * i)) & 0xFu);
+  }
+  uint64_t val = val0;
+  uint32_t acc = carry0, sh = 7u * g0, cs = p0 == 0 ? 8u : p0 - g0;
+  uint64_t ycur = pick(y, q);
+  const int b0 = p0 == 0 ? 8 : 0;
+#pragma unroll
+  for (int b = 0; b < 16; b++) {  // unrolled: w[] stays in registers
+    if (b < b0) continue;
+    const uint32_t c = byte_of(w[b >> 2], b & 3);
+    acc |= (c & 0x7Fu) << sh;
+    if (c & 0x80u) {
+      sh += 7u;
+      continue;
+    }
+    val += acc;
+    const uint32_t ce = p0 + (uint32_t)b + 1u;
+    while (ycur <= val) {  // this code's gap (val - acc, val] takes the keys up to val
+      const bool rep = q > 0 && pick(y, q - 1) == ycur;
+      const uint32_t kind = (rep || ycur == val) ? kSkip : kGap;
+      S.rpos[q * S.rs] = cs | (ce << 12) | (kind << 24);
+      S.rval[q * S.rs] = val;
+      S.rcode[q * S.rs] = acc;
+      if (++q >= q1) return;
+      ycur = pick(y, q);
+    }
+    acc = 0u;
+    sh = 0u;
+    cs = ce;
+  }
+}
+
+// The 16 bytes at byte offset `src` (which may be negative: missing bytes
+// read as zero) of the old leaf, masked to chunk bytes [a, b), OR-ed into r.
+LT_HD void gather(const uint8_t* leafp, uint32_t LB, int32_t src, uint32_t a, uint32_t b,
+                  uint32_t (&r)[4]) {
+  const int32_t A = (src >> 4) * 16;  // floor to 16
+  const uint32_t d = (uint32_t)(src - A);
+  uint32_t W[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  if (A >= 0) {
+    uint32_t t[4];
+    ld16(leafp + A, t);
+    W[0] = t[0]; W[1] = t[1]; W[2] = t[2]; W[3] = t[3];
+  }
+  if (d != 0u && A + 16 >= 0 && (uint32_t)(A + 16) < LB) {
+    uint32_t t[4];
+    ld16(leafp + A + 16, t);
+    W[4] = t[0]; W[5] = t[1]; W[6] = t[2]; W[7] = t[3];
+  }
+  const uint32_t q = d >> 2, s8 = 8u * (d & 3u);
+  uint32_t V[5];
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+    V[i] = q == 0 ? W[i] : q == 1 ? W[i + 1] : q == 2 ? W[i + 2] : W[i + 3];
+  const uint32_t m16 = ((b >= 16u ? 0xFFFFu : ((1u << b) - 1u)) & ~((1u << a) - 1u));
+#pragma unroll
+  for (int i = 0; i < 4; i++) r[i] |= fshr(V[i], V[i + 1], s8) & bmask4((m16 >> (4 * i)) & 0xFu);
+}
+
+// Insert the sorted slice y[0..s) (1 <= s <= kKeys, repeats allowed) into the
+// leaf at leafp (uold >= 8 used bytes, m elements, LB bytes, 16-byte
+// aligned).  Returns one of the results above; the leaf is written only for
+// kWritten.
+LT_HD uint32_t insert_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
+                           const uint64_t (&y)[kKeys], uint32_t s, const Scratch& S,
+                           Result& R) {
+  uint32_t w[4];
+  ld16(leafp, w);
+  const uint64_t head = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+  // ---- pass A: place every key ----
+  uint32_t k = 0;
+  while (k < s && pick(y, k) <= head) {
+    const uint64_t x = pick(y, k);
+    const bool rep = k > 0 && pick(y, k - 1) == x;
+    const uint32_t kind = (rep || x == head) ? kSkip : kHead;
+    S.rpos[k * S.rs] = 0u | (8u << 12) | (kind << 24);
+    S.rval[k * S.rs] = head;
+    S.rcode[k * S.rs] = 0u;
+    k++;
+  }
+  // step 1: chunk sums; every key gets the chunk (p0, entry state) of the
+  // code it falls in, or stays for the end
+  uint64_t ycur = k < s ? pick(y, k) : ~0ull;
+  uint64_t val = head;
+  uint32_t carry = 0, pw = 1, pwmax = 0, nterm = 0;
+  for (uint32_t p0 = 0; p0 < uold; p0 += 16) {
+    if (p0) ld16(leafp + p0, w);
+    if (p0 + 16u > uold) {  // bytes past the used ones read as zero
+      const uint32_t keep = (1u << (uold - p0)) - 1u;
+#pragma unroll
+      for (int i = 0; i < 4; i++) w[i] &= bmask4((keep >> (4 * i)) & 0xFu);
+    }
+    // terminator bytes (zero bytes past uold included; subtracted below)
+    nterm += popc(~w[2] & 0x80808080u) + popc(~w[3] & 0x80808080u);
+    uint32_t tot = carry, tt = 0;
+    const uint32_t pw0 = pw;
+    if (p0) {
+      nterm += popc(~w[0] & 0x80808080u) + popc(~w[1] & 0x80808080u);
+      sum_chunk<false>(w, tot, tt, pw, pwmax);
+    } else {
+      sum_chunk<true>(w, tot, tt, pw, pwmax);
+    }
+    const uint64_t vend = val + tt;
+    if (vend >= ycur) {
+      // open code bytes at p0: pw0 = 128^g0
+      const uint32_t g0 = pw0 >= (1u << 21) ? 3u : pw0 >= (1u << 14) ? 2u : pw0 >= 128u ? 1u : 0u;
+      while (k < s && ycur <= vend) {
+        S.rpos[k * S.rs] = p0 | (g0 << 12) | (kChunk << 24);
+        S.rval[k * S.rs] = val;
+        S.rcode[k * S.rs] = carry;
+        k++;
+        ycur = k < s ? pick(y, k) : ~0ull;
+      }
+    }
+    val = vend;
+    carry = tot - tt;
+  }
+  if (pwmax >= (1u << 28)) return kLongCode;
+  nterm -= ((uold + 15u) & ~15u) - uold;
+  if (nterm + 1u != m) return kBadCount;
+  // step 2: exact gaps inside the recorded chunks
+  for (uint32_t q = 0; q < k; q++) {
+    const uint32_t rp = S.rpos[q * S.rs];
+    if ((rp >> 24) != kChunk) continue;  // placed (head keys, or by an earlier chunk)
+    const uint32_t p0 = rp & 0xFFFu;
+    uint32_t q1 = q + 1;
+    while (q1 < k && S.rpos[q1 * S.rs] == rp) q1++;
+    place_in_chunk(leafp, uold, p0, S.rval[q * S.rs], S.rcode[q * S.rs], (rp >> 12) & 0xFFFu, y,
+                   q, q1, S);
+    q = q1 - 1;
+  }
+  const uint64_t lastv = val;
+  for (; k < s; k++) {
+    const uint64_t x = pick(y, k);
+    const bool rep = k > 0 && pick(y, k - 1) == x;
+    S.rpos[k * S.rs] = uold | (uold << 12) | ((rep ? kSkip : kAfter) << 24);
+    S.rval[k * S.rs] = lastv;
+    S.rcode[k * S.rs] = 0u;
+  }
+  // ---- edits: new keys grouped by the gap they fall in ----
+  uint32_t E = 0, nn = 0, added = 0;
+  int32_t tot = 0;
+  uint64_t newhead = head;
+  for (uint32_t q = 0; q < s;) {
+    const uint32_t rp = S.rpos[q * S.rs];
+    const uint32_t kind = rp >> 24;
+    if (kind == kSkip) { q++; continue; }
+    // keys q..q1 (kSkip ones among them are repeats) share this gap
+    const uint32_t os = rp & 0xFFFu, oe = (rp >> 12) & 0xFFFu;
+    const uint64_t rv = S.rval[q * S.rs];
+    uint64_t prev = pick(y, q);
+    uint32_t nl;
+    if (kind == kHead) { nl = 8u; newhead = prev; }
+    else if (kind == kGap) nl = leb_bytes(prev - (rv - S.rcode[q * S.rs]));
+    else nl = leb_bytes(prev - rv);
+    added |= 1u << q;
+    nn++;
+    uint32_t q1 = q + 1;
+    for (; q1 < s; q1++) {
+      const uint32_t rp1 = S.rpos[q1 * S.rs];
+      if ((rp1 & 0xFFFu) != os) break;
+      if ((rp1 >> 24) == kSkip) continue;
+      const uint64_t x = pick(y, q1);
+      nl += leb_bytes(x - prev);
+      prev = x;
+      added |= 1u << q1;
+      nn++;
+    }
+    if (kind != kAfter) nl += leb_bytes(rv - prev);  // the old successor (head or code end)
+    tot += (int32_t)nl - (int32_t)(oe - os);
+    S.epos[E * S.rs] = os | (oe << 12) | (kind << 24);
+    S.esa[E * S.rs] = tot;
+    S.ekey[E * S.rs] = q | (q1 << 8) | (nl << 16);
+    E++;
+    q = q1;
+  }
+  R.added = added;
+  R.newc = m + nn;
+  R.nb = (uint32_t)((int32_t)uold + tot);
+  R.newhead = newhead;
+  if (nn == 0) return kUnchanged;
+  if (R.nb > LB) return kTooBig;
+  // ---- pass B: rewrite from the end ----
+  // segment e (-1 .. E-1): old bytes [oe_e, os_{e+1}) moved by sa_e
+  // (oe_{-1} = 0, os_E = uold, sa_{-1} = 0)
+  const uint32_t os0 = S.epos[0] & 0xFFFu;
+  const uint32_t olo = os0 & ~15u;
+  const uint32_t ohi = (R.nb + 15u) & ~15u;
+  R.wlo = olo;
+  R.whi = ohi;
+  int cur = (int)E - 1;
+  for (int32_t o = (int32_t)ohi - 16; o >= (int32_t)olo; o -= 16) {
+    uint32_t r[4] = {0u, 0u, 0u, 0u};
+    for (int e = cur; e >= -1; e--) {
+      uint32_t lo, hi;
+      int32_t sa;
+      if (e >= 0) {
+        lo = (S.epos[e * S.rs] >> 12) & 0xFFFu;
+        hi = (e + 1 < (int)E) ? (S.epos[(e + 1) * S.rs] & 0xFFFu) : uold;
+        sa = S.esa[e * S.rs];
+      } else {
+        lo = 0u;
+        hi = os0;
+        sa = 0;
+      }
+      const int32_t dlo = (int32_t)lo + sa, dhi = (int32_t)hi + sa;
+      if (dlo >= o + 16) { cur = e - 1; continue; }  // wholly above this chunk (and the rest)
+      if (dhi <= o) break;                           // wholly below: so are the earlier ones
+      if (dhi > dlo) {
+        const uint32_t a = (uint32_t)((dlo > o ? dlo : o) - o);
+        const uint32_t b = (uint32_t)((dhi < o + 16 ? dhi : o + 16) - o);
+        gather(leafp, LB, o - sa, a, b, r);
+      }
+    }
+    st16(leafp + o, r);
+  }
+  // the edits' own bytes
+  for (uint32_t e = 0; e < E; e++) {
+    const uint32_t ep = S.epos[e * S.rs], ek = S.ekey[e * S.rs];
+    const uint32_t kind = ep >> 24, os = ep & 0xFFFu;
+    const uint32_t q0 = ek & 0xFFu, q1 = (ek >> 8) & 0xFFu;
+    const int32_t sb = e ? S.esa[(e - 1) * S.rs] : 0;
+    uint8_t* p = leafp + (int32_t)os + sb;
+    const uint64_t rv = S.rval[q0 * S.rs];
+    uint64_t prev = pick(y, q0);
+    if (kind == kHead) {
+#pragma unroll
+      for (int i = 0; i < 8; i++) p[i] = (uint8_t)(prev >> (8 * i));
+      p += 8;
+    } else if (kind == kGap) {
+      p += leb_write(p, prev - (rv - S.rcode[q0 * S.rs]));
+    } else {
+      p += leb_write(p, prev - rv);
+    }
+    for (uint32_t q = q0 + 1; q < q1; q++) {
+      if ((S.rpos[q * S.rs] >> 24) == kSkip) continue;
+      const uint64_t x = pick(y, q);
+      p += leb_write(p, x - prev);
+      prev = x;
+    }
+    if (kind != kAfter) leb_write(p, rv - prev);
+  }
+  return kWritten;
+}
+
+}  // namespace leafthr
