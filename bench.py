@@ -59,10 +59,13 @@ def aggregate(local_ms: float, units_per_rank: float, dist=None):
     return local_ms, world * units_per_rank / (local_ms / 1e3)
 
 
-def kernel_sources_sha():
+KERNEL_SOURCES = ("update.cu", "dev_common.cuh", "query.cu")
+
+
+def kernel_sources_sha(files=KERNEL_SOURCES):
     import hashlib
     h = hashlib.sha256()
-    for f in ("update.cu", "dev_common.cuh", "query.cu"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2305_05055_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -71,12 +74,12 @@ def kernel_sources_sha():
 def measured_traffic(kernel: str, alg_bytes_per_launch: float):
     """DRAM bytes per launch from the committed ncu summary, scaled from the
     captured launch to this one by algorithmic bytes; None when the kernel's
-    sources changed since the capture."""
+    sources (the entry's list) changed since the capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
         e = t[kernel]
-        if e["sources_sha256"] != kernel_sources_sha():
+        if e["sources_sha256"] != kernel_sources_sha(tuple(e.get("sources", KERNEL_SOURCES))):
             return None
         return e["dram_bytes"] * alg_bytes_per_launch / e["alg_bytes"]
     except Exception:

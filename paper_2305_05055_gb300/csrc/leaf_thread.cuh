@@ -50,6 +50,7 @@ struct Result {
   uint32_t newc;     // new element count
   uint32_t added;    // bit q: slice key q was added
   uint32_t wlo, whi; // byte range rewritten (kWritten)
+  uint32_t E;        // edits
   uint64_t newhead;
 };
 
@@ -224,11 +225,28 @@ LT_HD void gather(const uint8_t* leafp, uint32_t LB, int32_t src, uint32_t a, ui
   for (int i = 0; i < 4; i++) r[i] |= fshr(V[i], V[i + 1], s8) & bmask4((m16 >> (4 * i)) & 0xFu);
 }
 
-// Insert the sorted slice y[0..s) (1 <= s <= kKeys, repeats allowed) into the
-// leaf at leafp (uold >= 8 used bytes, m elements, LB bytes, 16-byte
-// aligned).  Returns one of the results above; the leaf is written only for
-// kWritten.
-LT_HD uint32_t insert_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
+// Pass B: destination bounds [dlo, dhi) and shift sa of segment e (-1 .. E-1):
+// the old bytes [oe_e, os_{e+1}) moved by sa_e (oe_{-1} = 0, os_E = uold,
+// sa_{-1} = 0).
+LT_HD void seg_bounds(const Scratch& S, uint32_t E, uint32_t uold, uint32_t os0, int e,
+                      int32_t& dlo, int32_t& dhi, int32_t& sa) {
+  uint32_t lo = 0u, hi = os0;
+  sa = 0;
+  if (e >= 0) {
+    lo = (S.epos[e * S.rs] >> 12) & 0xFFFu;
+    hi = (e + 1 < (int)E) ? (S.epos[(e + 1) * S.rs] & 0xFFFu) : uold;
+    sa = S.esa[e * S.rs];
+  }
+  dlo = (int32_t)lo + sa;
+  dhi = (int32_t)hi + sa;
+}
+
+// Pass A and the edits of inserting the sorted slice y[0..s) (1 <= s <=
+// kKeys, repeats allowed) into the leaf at leafp (uold >= 8 used bytes, m
+// elements, LB bytes, 16-byte aligned).  Returns one of the results above
+// and writes nothing; kWritten means the leaf is to be rewritten (R.wlo ..
+// R.whi, the R.E edits in S).
+LT_HD uint32_t plan_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
                            const uint64_t (&y)[kKeys], uint32_t s, const Scratch& S,
                            Result& R) {
   uint32_t w[4];
@@ -345,34 +363,35 @@ LT_HD uint32_t insert_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t 
   R.newc = m + nn;
   R.nb = (uint32_t)((int32_t)uold + tot);
   R.newhead = newhead;
+  R.E = E;
   if (nn == 0) return kUnchanged;
   if (R.nb > LB) return kTooBig;
-  // ---- pass B: rewrite from the end ----
-  // segment e (-1 .. E-1): old bytes [oe_e, os_{e+1}) moved by sa_e
-  // (oe_{-1} = 0, os_E = uold, sa_{-1} = 0)
+  R.wlo = (S.epos[0] & 0xFFFu) & ~15u;
+  R.whi = (R.nb + 15u) & ~15u;
+  return kWritten;
+}
+
+// Pass B by one thread: the chunks R.wlo .. R.whi of the leaf from the end
+// backwards, each gathered from the segments that land in it and stored
+// whole (the edits' own bytes are left zero: write_edits fills them).
+LT_HD void rewrite_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, const Scratch& S,
+                        const Result& R) {
+  const uint32_t E = R.E;
   const uint32_t os0 = S.epos[0] & 0xFFFu;
-  const uint32_t olo = os0 & ~15u;
-  const uint32_t ohi = (R.nb + 15u) & ~15u;
-  R.wlo = olo;
-  R.whi = ohi;
+  const uint32_t olo = R.wlo, ohi = R.whi;
   int cur = (int)E - 1;
   for (int32_t o = (int32_t)ohi - 16; o >= (int32_t)olo; o -= 16) {
+    for (;;) {  // the highest segment not wholly above chunk o
+      int32_t dlo, dhi, sa;
+      seg_bounds(S, E, uold, os0, cur, dlo, dhi, sa);
+      if (cur < 0 || dlo < o + 16) break;
+      cur--;
+    }
     uint32_t r[4] = {0u, 0u, 0u, 0u};
     for (int e = cur; e >= -1; e--) {
-      uint32_t lo, hi;
-      int32_t sa;
-      if (e >= 0) {
-        lo = (S.epos[e * S.rs] >> 12) & 0xFFFu;
-        hi = (e + 1 < (int)E) ? (S.epos[(e + 1) * S.rs] & 0xFFFu) : uold;
-        sa = S.esa[e * S.rs];
-      } else {
-        lo = 0u;
-        hi = os0;
-        sa = 0;
-      }
-      const int32_t dlo = (int32_t)lo + sa, dhi = (int32_t)hi + sa;
-      if (dlo >= o + 16) { cur = e - 1; continue; }  // wholly above this chunk (and the rest)
-      if (dhi <= o) break;                           // wholly below: so are the earlier ones
+      int32_t dlo, dhi, sa;
+      seg_bounds(S, E, uold, os0, e, dlo, dhi, sa);
+      if (dhi <= o) break;  // wholly below this chunk: so are the earlier ones
       if (dhi > dlo) {
         const uint32_t a = (uint32_t)((dlo > o ? dlo : o) - o);
         const uint32_t b = (uint32_t)((dhi < o + 16 ? dhi : o + 16) - o);
@@ -381,8 +400,12 @@ LT_HD uint32_t insert_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t 
     }
     st16(leafp + o, r);
   }
-  // the edits' own bytes
-  for (uint32_t e = 0; e < E; e++) {
+}
+
+// The edits' own bytes (new head, split codes), after the chunks are stored.
+LT_HD void write_edits(uint8_t* leafp, const uint64_t (&y)[kKeys], const Scratch& S,
+                       const Result& R) {
+  for (uint32_t e = 0; e < R.E; e++) {
     const uint32_t ep = S.epos[e * S.rs], ek = S.ekey[e * S.rs];
     const uint32_t kind = ep >> 24, os = ep & 0xFFFu;
     const uint32_t q0 = ek & 0xFFu, q1 = (ek >> 8) & 0xFFu;
@@ -407,7 +430,19 @@ LT_HD uint32_t insert_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t 
     }
     if (kind != kAfter) leb_write(p, rv - prev);
   }
-  return kWritten;
+}
+
+// All of it by one thread: returns one of the results above; the leaf is
+// written only for kWritten.
+LT_HD uint32_t insert_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
+                           const uint64_t (&y)[kKeys], uint32_t s, const Scratch& S,
+                           Result& R) {
+  const uint32_t res = plan_leaf(leafp, LB, uold, m, y, s, S, R);
+  if (res == kWritten) {
+    rewrite_leaf(leafp, LB, uold, S, R);
+    write_edits(leafp, y, S, R);
+  }
+  return res;
 }
 
 }  // namespace leafthr

@@ -642,8 +642,8 @@ __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
   __shared__ uint32_t s_hist[kThrBuckets];
   if (a.st->err) return;
   const unsigned tid = threadIdx.x;
-  const leafthr::Scratch S{s_rpos + tid, s_rval + tid, s_rcode + tid,
-                           s_epos + tid, s_esa + tid,  s_ekey + tid, (uint32_t)kThrT};
+  const leafthr::Scratch S{s_rpos + tid, s_rval + tid, s_rcode + tid, s_epos + tid,
+                           s_esa + tid,  s_ekey + tid, (uint32_t)kThrT};
   const uint64_t n = a.st->n_thr;
   // Tiles of R * kThrT list entries, R <= kThrR chosen so that the grid's
   // tiles cover the list at most once where it can.  Each tile is sorted by
@@ -689,20 +689,29 @@ __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
     const uint64_t cnt = std::min<uint64_t>(tile, n - base);
     for (uint32_t r = 0; r < R; r++) {
       const uint32_t pos = r * kThrT + tid;
-      if (pos >= cnt) continue;
-      const uint32_t t = s_tile[pos];
-      const uint32_t tb = a.T_begin[t], te = a.T_begin[t + 1];
-      const uint32_t uold = a.T_oldused[t], j = a.T_leaf[t], m = a.T_oldcnt[t];
-      const uint32_t fc0 = a.T_first_chunk[t], fc1 = a.T_first_chunk[t + 1];
-      const uint32_t s = te - tb;
-      uint64_t y[K];
-#pragma unroll
-      for (uint32_t q = 0; q < K; q++) y[q] = q < s ? a.u[tb + q] : 0ull;
-      // the old leaf, the slice and ~28 bytes of per-leaf metadata
-      nbytes += uold + 8u * s + 28u;
+      const bool have = pos < cnt;
+      uint32_t t = 0, tb = 0, s = 0, uold = 0, j = 0, m = 0, fc0 = 0, fc1 = 0;
+      uint32_t res = leafthr::kUnchanged;
+      uint64_t y[K] = {0ull, 0ull, 0ull, 0ull};
       leafthr::Result R2;
-      const uint32_t res =
-          leafthr::insert_leaf(a.data + (size_t)j * a.LB, a.LB, uold, m, y, s, S, R2);
+      R2.E = 0;
+      if (have) {
+        t = s_tile[pos];
+        tb = a.T_begin[t];
+        s = a.T_begin[t + 1] - tb;
+        uold = a.T_oldused[t];
+        j = a.T_leaf[t];
+        m = a.T_oldcnt[t];
+        fc0 = a.T_first_chunk[t];
+        fc1 = a.T_first_chunk[t + 1];
+#pragma unroll
+        for (uint32_t q = 0; q < K; q++) y[q] = q < s ? a.u[tb + q] : 0ull;
+        // the old leaf, the slice and ~28 bytes of per-leaf metadata
+        nbytes += uold + 8u * s + 28u;
+        res = leafthr::plan_leaf(a.data + (size_t)j * a.LB, a.LB, uold, m, y, s, S, R2);
+      }
+      if (!have) continue;
+      if (res == leafthr::kWritten) leafthr::rewrite_leaf(a.data + (size_t)j * a.LB, a.LB, uold, S, R2);
       if (res == leafthr::kLongCode) {
         a.T_state[t] = kFallback;
         a.list_v1[atomicAdd(&a.st->n_v1, 1ull)] = t;
@@ -723,6 +732,7 @@ __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
         a.T_newbytes[t] = R2.nb;
         c0 = R2.newc;
       } else {
+        leafthr::write_edits(a.data + (size_t)j * a.LB, y, S, R2);
         a.used[j] = R2.nb;
         a.cnt[j] = R2.newc;
         a.heads[j] = R2.newhead;
