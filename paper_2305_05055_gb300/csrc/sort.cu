@@ -13,6 +13,14 @@
 // return at once; the passes alternate buffers so that the last one lands in
 // the first scratch buffer.  No host round trip.  Batches of at most one tile
 // are sorted by a single block.
+//
+// Batches of up to 1.5M keys go most significant digit first instead: one
+// scatter pass by the highest varying digit (same tile ranking and
+// look-back), then each of its 256 buckets (k / 256 keys on average) is sorted
+// by the lower digits in the shared memory of one block.  Three reads and two
+// writes of the batch instead of six and five.  A bucket of more than 8192
+// keys (heavy repeats) sets a flag, and the digit passes, launched gated on
+// that flag, sort the input again from scratch.
 #include <algorithm>
 
 #include "dev_common.cuh"
@@ -27,31 +35,41 @@ constexpr int kT = 256;
 constexpr int kWarps = kT / 32;
 constexpr int kItems = 16;
 constexpr int kTile = kT * kItems;  // 4096 keys
+// Bucket sort: one block of kBT threads, kBItems keys each, sorts a bucket of
+// up to kBTile keys (spread evenly over its warps).
+constexpr int kBT = 1024;
+constexpr int kBItems = 8;
+constexpr int kBTile = kBT * kBItems;  // 8192 keys
+// Batches of more than one tile and at most this many keys take the
+// top-digit buckets (k / 256 keys per bucket on average, far below kBTile).
+constexpr uint64_t kBucketMax = 1536ull * 1024;
 
-template <bool VALS>
+template <bool VALS, int KT = kT, int ITEMS = kItems>
 struct TileSmemT {
-  uint64_t keys[kTile];
-  uint32_t vals[VALS ? kTile : 1];  // optional 32-bit payload moved with the keys
-  uint32_t wcnt[kWarps][256];
+  uint64_t keys[KT * ITEMS];
+  uint32_t vals[VALS ? KT * ITEMS : 1];  // optional 32-bit payload moved with the keys
+  uint32_t wcnt[KT / 32][256];
   uint32_t dstart[256];
-  uint64_t goff[256];
-  uint32_t scan_tmp[kWarps];
+  uint32_t scan_tmp[8];
 };
 
 // Stable partition of the tile by digit (key >> shift) & 255.  Item j of lane
-// l in warp w is tile element w*32*kItems + j*32 + l; the first `nvalid`
+// l in warp w (j < ipw <= ITEMS) is tile element w*32*ipw + j*32 + l; the first `nvalid`
 // elements are real.  On return sm.keys[0..nvalid) holds the tile sorted by
 // digit (stable) and sm.dstart[d] is where digit d starts.
-template <bool VALS>
-__device__ __forceinline__ void tile_rank(const uint64_t (&key)[kItems], const uint32_t (&val)[kItems],
-                                          uint32_t nvalid, int shift, TileSmemT<VALS>& sm) {
+template <bool VALS, int KT = kT, int ITEMS = kItems>
+__device__ __forceinline__ void tile_rank(const uint64_t (&key)[ITEMS], const uint32_t (&val)[ITEMS],
+                                          uint32_t nvalid, int shift, TileSmemT<VALS, KT, ITEMS>& sm,
+                                          uint32_t ipw = ITEMS) {
+  constexpr int W = KT / 32;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < kWarps * 256; i += kT) (&sm.wcnt[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < W * 256; i += KT) (&sm.wcnt[0][0])[i] = 0;
   __syncthreads();
-  uint32_t rank[kItems];
+  uint32_t rank[ITEMS];
 #pragma unroll
-  for (int j = 0; j < kItems; j++) {
-    const uint32_t li = warp * 32 * kItems + j * 32 + lane;
+  for (int j = 0; j < ITEMS; j++) {
+    if ((uint32_t)j >= ipw) break;
+    const uint32_t li = warp * 32 * ipw + j * 32 + lane;
     const bool valid = li < nvalid;
     const uint32_t d = (uint32_t)(key[j] >> shift) & 255u;
     const unsigned vm = __ballot_sync(FULL, valid);
@@ -66,31 +84,34 @@ __device__ __forceinline__ void tile_rank(const uint64_t (&key)[kItems], const u
     __syncwarp();
   }
   __syncthreads();
-  // per digit: exclusive prefix over warps, then over digits
+  // per digit (threads 0..255): exclusive prefix over warps, then over digits
   {
-    const int d = threadIdx.x;  // kT == 256 digits
-    uint32_t run = 0;
+    const int d = threadIdx.x;
+    uint32_t run = 0, inc = 0;
+    if (d < 256) {
 #pragma unroll
-    for (int w = 0; w < kWarps; w++) {
-      uint32_t c = sm.wcnt[w][d];
-      sm.wcnt[w][d] = run;
-      run += c;
+      for (int w = 0; w < W; w++) {
+        uint32_t c = sm.wcnt[w][d];
+        sm.wcnt[w][d] = run;
+        run += c;
+      }
+      inc = warp_incl_scan(run);
+      if (lane == 31) sm.scan_tmp[warp] = inc;
     }
-    uint32_t inc = warp_incl_scan(run);
-    if (lane == 31) sm.scan_tmp[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-      uint32_t v = lane < kWarps ? sm.scan_tmp[lane] : 0;
+      uint32_t v = lane < 8 ? sm.scan_tmp[lane] : 0;
       uint32_t vi = warp_incl_scan(v);
-      if (lane < kWarps) sm.scan_tmp[lane] = vi - v;
+      if (lane < 8) sm.scan_tmp[lane] = vi - v;
     }
     __syncthreads();
-    sm.dstart[d] = sm.scan_tmp[warp] + inc - run;
+    if (d < 256) sm.dstart[d] = sm.scan_tmp[warp] + inc - run;
   }
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < kItems; j++) {
-    const uint32_t li = warp * 32 * kItems + j * 32 + lane;
+  for (int j = 0; j < ITEMS; j++) {
+    if ((uint32_t)j >= ipw) break;
+    const uint32_t li = warp * 32 * ipw + j * 32 + lane;
     if (li < nvalid) {
       const uint32_t d = (uint32_t)(key[j] >> shift) & 255u;
       const uint32_t pos = sm.dstart[d] + sm.wcnt[warp][d] + rank[j];
@@ -114,7 +135,9 @@ struct SortCtl {
   uint32_t rank[8];        // position of digit p among the varying ones
   uint32_t npass;          // number of varying digits
   uint32_t done_blocks;    // histogram blocks finished
-  uint32_t tile_ctr[8];    // next tile id per pass
+  uint32_t tile_ctr[9];    // next tile id per pass (8: the top-digit scatter)
+  uint32_t top;            // highest varying digit
+  uint32_t fallback;       // a top-digit bucket exceeded kBTile: the digit passes run
 };
 
 __global__ void __launch_bounds__(kT) k_hist_all(const uint64_t* __restrict__ in, uint64_t k,
@@ -155,12 +178,14 @@ __global__ void __launch_bounds__(kT) k_hist_all(const uint64_t* __restrict__ in
     __syncthreads();
   }
   if (d == 0) {
-    uint32_t r = 0;
+    uint32_t r = 0, top = 0;
     for (int p = 0; p < 8; p++) {
       ctl->rank[p] = r;
       r += ctl->varying[p];
+      if (ctl->varying[p]) top = (uint32_t)p;
     }
     ctl->npass = r;
+    ctl->top = top;
   }
 }
 
@@ -177,76 +202,167 @@ __global__ void k_copy_if_no_pass(const uint64_t* __restrict__ in, uint64_t* __r
 }
 
 // One digit pass.  Buffers: the input, then A and B alternately, arranged so
-// that the last varying pass writes A.
+// that the last varying pass writes A.  With top != 0 it is instead the
+// stable scatter of the input by its highest varying digit into B (the
+// buckets k_bucket_sort finishes); with gate != 0 it runs only if a bucket
+// overflowed.  Blocks take tiles in order from a counter until none is left,
+// so the grid can be smaller than the tile count (a pass that does not run
+// costs one short launch).
 template <bool VALS>
-__global__ void __launch_bounds__(kT) k_onesweep(const uint64_t* __restrict__ in,
+__global__ void __launch_bounds__(kT, 3) k_onesweep(const uint64_t* __restrict__ in,
                                                  const uint32_t* __restrict__ vin,
                                                  uint64_t* __restrict__ A, uint64_t* __restrict__ B,
                                                  uint32_t* __restrict__ VA, uint32_t* __restrict__ VB,
-                                                 uint64_t k, int p, SortCtl* ctl,
+                                                 uint64_t k, int p, int top, int gate, SortCtl* ctl,
                                                  uint32_t* __restrict__ look, Status* st) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   TileSmemT<VALS>& sm = *reinterpret_cast<TileSmemT<VALS>*>(smem_raw);
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_excl[256];
-  if (!ctl->varying[p]) return;
-  const uint32_t r = ctl->rank[p], P = ctl->npass;
-  // pass r writes B when P-1-r is odd, else A (so pass P-1 writes A) and
-  // reads what pass r-1 wrote
-  const uint64_t* src = (r == 0) ? in : (((P - r) & 1u) ? B : A);
-  uint64_t* dst = ((P - 1u - r) & 1u) ? B : A;
-  const uint32_t* vsrc = (r == 0) ? vin : (((P - r) & 1u) ? VB : VA);
-  uint32_t* vdst = ((P - 1u - r) & 1u) ? VB : VA;
+  const uint64_t* src;
+  uint64_t* dst;
+  const uint32_t* vsrc;
+  uint32_t* vdst;
+  uint32_t* ctr;
+  if (top) {
+    if (ctl->npass == 0) return;
+    p = (int)ctl->top;
+    src = in;
+    dst = B;
+    vsrc = vin;
+    vdst = VB;
+    ctr = &ctl->tile_ctr[8];
+  } else {
+    if (!ctl->varying[p] || (gate && !ctl->fallback)) return;
+    const uint32_t r = ctl->rank[p], P = ctl->npass;
+    // pass r writes B when P-1-r is odd, else A (so pass P-1 writes A) and
+    // reads what pass r-1 wrote
+    src = (r == 0) ? in : (((P - r) & 1u) ? B : A);
+    dst = ((P - 1u - r) & 1u) ? B : A;
+    vsrc = (r == 0) ? vin : (((P - r) & 1u) ? VB : VA);
+    vdst = ((P - 1u - r) & 1u) ? VB : VA;
+    ctr = &ctl->tile_ctr[p];
+  }
   const int shift = 8 * p;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->tile_ctr[p], 1u);
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const uint64_t base = (uint64_t)tile * kTile;
-  const uint32_t nvalid = (uint32_t)min((uint64_t)kTile, k - base);
-  uint64_t key[kItems];
-  uint32_t val[kItems];
+  const uint32_t ntiles = (uint32_t)((k + kTile - 1) / kTile);
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(ctr, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= ntiles) return;
+    const uint64_t base = (uint64_t)tile * kTile;
+    const uint32_t nvalid = (uint32_t)min((uint64_t)kTile, k - base);
+    uint64_t key[kItems];
+    uint32_t val[kItems];
 #pragma unroll
-  for (int j = 0; j < kItems; j++) {
-    const uint32_t li = warp * 32 * kItems + j * 32 + lane;
-    key[j] = li < nvalid ? src[base + li] : 0ull;
-    if constexpr (VALS) val[j] = li < nvalid ? vsrc[base + li] : 0u;
-    else val[j] = 0u;
-  }
-  tile_rank<VALS>(key, val, nvalid, shift, sm);
-  // publish this tile's count per digit, then look back for the tiles before
-  const int d = threadIdx.x;
-  const uint32_t cnt = (d < 255 ? sm.dstart[d + 1] : nvalid) - sm.dstart[d];
-  volatile uint32_t* lk = look + (size_t)tile * 256;
-  if (tile == 0) {
-    lk[d] = kFlagP | cnt;
-    s_excl[d] = 0;
-  } else {
-    lk[d] = kFlagA | cnt;
-    uint32_t excl = 0;
-    for (int64_t tp = (int64_t)tile - 1; tp >= 0; tp--) {
-      volatile uint32_t* q = look + (size_t)tp * 256 + d;
-      uint32_t v = *q;
-      uint32_t spins = 0;
-      while (!(v & (kFlagA | kFlagP)) && spins < kSpinLimit) { v = *q; spins++; }
-      if (spins >= kSpinLimit) {  // a predecessor never published: give up
-        atomicOr(&st->err, kErrSort);
-        break;
-      }
-      excl += v & kCountMask;
-      if (v & kFlagP) break;
+    for (int j = 0; j < kItems; j++) {
+      const uint32_t li = warp * 32 * kItems + j * 32 + lane;
+      key[j] = li < nvalid ? src[base + li] : 0ull;
+      if constexpr (VALS) val[j] = li < nvalid ? vsrc[base + li] : 0u;
+      else val[j] = 0u;
     }
-    __threadfence();
-    lk[d] = kFlagP | (excl + cnt);
-    s_excl[d] = excl;
+    tile_rank<VALS>(key, val, nvalid, shift, sm);
+    // publish this tile's count per digit, then look back for the tiles before
+    const int d = threadIdx.x;
+    const uint32_t cnt = (d < 255 ? sm.dstart[d + 1] : nvalid) - sm.dstart[d];
+    volatile uint32_t* lk = look + (size_t)tile * 256;
+    if (tile == 0) {
+      lk[d] = kFlagP | cnt;
+      s_excl[d] = 0;
+    } else {
+      lk[d] = kFlagA | cnt;
+      uint32_t excl = 0;
+      for (int64_t tp = (int64_t)tile - 1; tp >= 0; tp--) {
+        volatile uint32_t* q = look + (size_t)tp * 256 + d;
+        uint32_t v = *q;
+        uint32_t spins = 0;
+        while (!(v & (kFlagA | kFlagP)) && spins < kSpinLimit) { v = *q; spins++; }
+        if (spins >= kSpinLimit) {  // a predecessor never published: give up
+          atomicOr(&st->err, kErrSort);
+          break;
+        }
+        excl += v & kCountMask;
+        if (v & kFlagP) break;
+      }
+      __threadfence();
+      lk[d] = kFlagP | (excl + cnt);
+      s_excl[d] = excl;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nvalid; i += kT) {
+      const uint64_t x = sm.keys[i];
+      const uint32_t dd = (uint32_t)(x >> shift) & 255u;
+      const uint64_t o = (uint64_t)ctl->off[p][dd] + s_excl[dd] + (i - sm.dstart[dd]);
+      dst[o] = x;
+      if constexpr (VALS) vdst[o] = sm.vals[i];
+    }
+    __syncthreads();  // the next tile reuses the shared arrays
   }
+}
+
+// Bucket b of the top-digit scatter (B[off .. off + count)), sorted stably by
+// every lower digit that varies inside it, in shared memory, into the same
+// positions of A.  A bucket of more than kBTile keys sets the fallback flag
+// instead (the digit passes then sort the whole batch again).
+template <bool VALS>
+__global__ void __launch_bounds__(kBT) k_bucket_sort(const uint64_t* __restrict__ B,
+                                                     const uint32_t* __restrict__ VB,
+                                                     uint64_t* __restrict__ A,
+                                                     uint32_t* __restrict__ VA, SortCtl* ctl) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  TileSmemT<VALS, kBT, kBItems>& sm = *reinterpret_cast<TileSmemT<VALS, kBT, kBItems>*>(smem_raw);
+  __shared__ ull s_or, s_and;
+  if (ctl->npass == 0) return;
+  const uint32_t top = ctl->top, b = blockIdx.x;
+  const uint32_t n = ctl->hist[top][b];
+  if (n == 0) return;
+  if (n > (uint32_t)kBTile) {
+    if (threadIdx.x == 0) atomicExch(&ctl->fallback, 1u);
+    return;
+  }
+  const uint64_t base = ctl->off[top][b];
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  // items per warp: the bucket spread over every warp, in element order
+  const uint32_t ipw = (n + 32u * (kBT / 32) - 1u) / (32u * (kBT / 32));
+  if (threadIdx.x == 0) { s_or = 0; s_and = ~0ull; }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < nvalid; i += kT) {
-    const uint64_t x = sm.keys[i];
-    const uint32_t dd = (uint32_t)(x >> shift) & 255u;
-    const uint64_t o = (uint64_t)ctl->off[p][dd] + s_excl[dd] + (i - sm.dstart[dd]);
-    dst[o] = x;
-    if constexpr (VALS) vdst[o] = sm.vals[i];
+  uint64_t key[kBItems];
+  uint32_t val[kBItems];
+  ull o = 0, a = ~0ull;
+#pragma unroll
+  for (int j = 0; j < kBItems; j++) {
+    const uint32_t li = warp * 32 * ipw + j * 32 + lane;
+    const bool ok = (uint32_t)j < ipw && li < n;
+    key[j] = ok ? B[base + li] : 0ull;
+    if constexpr (VALS) val[j] = ok ? VB[base + li] : 0u;
+    else val[j] = 0u;
+    if (ok) { o |= key[j]; a &= key[j]; }
+  }
+  atomicOr(&s_or, o);
+  atomicAnd(&s_and, a);
+  __syncthreads();
+  const ull vary = s_or ^ s_and;
+  for (uint32_t p = 0; p < top; p++) {
+    if (((vary >> (8 * p)) & 255u) == 0) continue;
+    tile_rank<VALS, kBT, kBItems>(key, val, n, 8 * (int)p, sm, ipw);
+#pragma unroll
+    for (int j = 0; j < kBItems; j++) {
+      const uint32_t li = warp * 32 * ipw + j * 32 + lane;
+      if ((uint32_t)j < ipw && li < n) {
+        key[j] = sm.keys[li];
+        if constexpr (VALS) val[j] = sm.vals[li];
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < kBItems; j++) {
+    const uint32_t li = warp * 32 * ipw + j * 32 + lane;
+    if ((uint32_t)j < ipw && li < n) {
+      A[base + li] = key[j];
+      if constexpr (VALS) VA[base + li] = val[j];
+    }
   }
 }
 
@@ -322,9 +438,14 @@ __global__ void k_unique_scatter(const uint64_t* __restrict__ in, uint64_t k,
 
 namespace {
 size_t ctl_bytes() { return (sizeof(SortCtl) + 255) & ~(size_t)255; }
-size_t look_bytes(uint64_t k) {
+size_t look_bytes(uint64_t k) {  // eight digit passes and the top-digit scatter
   const uint64_t ntiles = (k + kTile - 1) / kTile;
-  return (size_t)8 * ntiles * 256 * 4;
+  return (size_t)9 * ntiles * 256 * 4;
+}
+template <bool VALS>
+int& sweep_blocks_per_sm() {
+  static int n = 1;
+  return n;
 }
 template <bool VALS>
 void sort_attrs() {
@@ -333,6 +454,13 @@ void sort_attrs() {
   const int smem = (int)sizeof(TileSmemT<VALS>);
   cudaFuncSetAttribute(k_onesweep<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_sort_small<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_bucket_sort<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(TileSmemT<VALS, kBT, kBItems>));
+  int bps = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_onesweep<VALS>, kT, smem) ==
+          cudaSuccess &&
+      bps > 0)
+    sweep_blocks_per_sm<VALS>() = bps;
   cudaGetLastError();
   done = true;
 }
@@ -371,7 +499,7 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
   uint64_t* B = (uint64_t*)h->s.keysB.p;
   uint32_t* VB = VALS ? (uint32_t*)h->s.valsB.p : nullptr;
   const uint32_t ntiles = (uint32_t)((k + kTile - 1) / kTile);
-  // control block + 8 look-back arrays, zeroed in one memset
+  // control block + 9 look-back arrays, zeroed in one memset
   SortCtl* ctl = reinterpret_cast<SortCtl*>(h->s.hist.p);
   uint32_t* look = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(h->s.hist.p) + ctl_bytes());
   CPMA_CUDA(cudaMemsetAsync(h->s.hist.p, 0, ctl_bytes() + look_bytes(k), st));
@@ -379,13 +507,27 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
   k_hist_all<<<hgrid, kT, 0, st>>>(d_in, k, ctl);
   h->launches++;
   prof_add_bytes(h, PH_SORT, 8ull * k);  // the histogram read
+  const unsigned sgrid = (unsigned)std::min<uint64_t>(
+      ntiles, (uint64_t)h->num_sms * (uint64_t)sweep_blocks_per_sm<VALS>());
+  const bool buckets = k <= kBucketMax;
+  if (buckets) {
+    // scatter by the highest varying digit, then each of its 256 buckets
+    // sorted in shared memory; the digit passes below run only if a bucket
+    // overflowed
+    k_onesweep<VALS><<<sgrid, kT, smem, st>>>(d_in, v_in, A, B, VA, VB, k, 0, 1, 0, ctl,
+                                               look + (size_t)8 * ntiles * 256, h->d_status);
+    k_bucket_sort<VALS><<<256, kBT, sizeof(TileSmemT<VALS, kBT, kBItems>), st>>>(B, VB, A, VA,
+                                                                                 ctl);
+    h->launches += 2;
+    prof_add_bytes(h, PH_SORT, (VALS ? 24ull : 16ull) * k * 2);
+  }
   for (int p = 0; p < 8; p++) {
     // digits that vary: the scatter reads and writes keys (and tags)
-    k_onesweep<VALS><<<ntiles, kT, smem, st>>>(d_in, v_in, A, B, VA, VB, k, p, ctl,
-                                                look + (size_t)p * ntiles * 256, h->d_status);
+    k_onesweep<VALS><<<sgrid, kT, smem, st>>>(d_in, v_in, A, B, VA, VB, k, p, 0, buckets ? 1 : 0,
+                                               ctl, look + (size_t)p * ntiles * 256, h->d_status);
     h->launches++;
   }
-  prof_add_bytes(h, PH_SORT, (VALS ? 24ull : 16ull) * k * 5);  // typical: 5 varying digits
+  if (!buckets) prof_add_bytes(h, PH_SORT, (VALS ? 24ull : 16ull) * k * 5);  // typical: 5 varying digits
   k_copy_if_no_pass<<<std::min<uint64_t>((uint64_t)h->num_sms * 4, (k + kT - 1) / kT), kT, 0, st>>>(
       d_in, A, v_in, VA, k, ctl);
   h->launches++;
