@@ -79,36 +79,29 @@ void give_event(Prof& p, cudaEvent_t e) {
 }
 }  // namespace
 
-void prof_begin(const cpma* hc, int phase, cudaStream_t st) {
-  cpma* h = const_cast<cpma*>(hc);
-  Prof& p = h->prof;
-  if (!p.on) return;
-  if (p.open_rec.phase >= 0) prof_end(h, st);
-  p.open_rec.phase = phase;
+namespace {
+void rec_begin(Prof& p, Prof::Rec& r, int phase, cudaStream_t st) {
+  r.phase = phase;
   if (p.capturing) {
     // events of the graph being captured: recorded by every replay
-    p.open_rec.a = p.open_rec.b = nullptr;
-    p.open_rec.pooled = false;
-    if (cudaEventCreate(&p.open_rec.a) != cudaSuccess ||
-        cudaEventCreate(&p.open_rec.b) != cudaSuccess) {
+    r.a = r.b = nullptr;
+    r.pooled = false;
+    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
       cudaGetLastError();
       return;
     }
-    cudaEventRecordWithFlags(p.open_rec.a, st, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(r.a, st, cudaEventRecordExternal);
     return;
   }
-  p.open_rec.pooled = true;
-  p.open_rec.a = take_event(p);
-  p.open_rec.b = take_event(p);
-  if (p.open_rec.a) cudaEventRecord(p.open_rec.a, st);
+  r.pooled = true;
+  r.a = take_event(p);
+  r.b = take_event(p);
+  if (r.a) cudaEventRecord(r.a, st);
 }
 
-void prof_end(const cpma* hc, cudaStream_t st) {
-  cpma* h = const_cast<cpma*>(hc);
-  Prof& p = h->prof;
-  if (!p.on || p.open_rec.phase < 0) return;
+void rec_end(Prof& p, Prof::Rec& r, cudaStream_t st) {
   if (p.capturing) {
-    if (p.open_rec.b) cudaEventRecordWithFlags(p.open_rec.b, st, cudaEventRecordExternal);
+    if (r.b) cudaEventRecordWithFlags(r.b, st, cudaEventRecordExternal);
     if (p.ncap == p.cap_max) {
       int nc = p.cap_max ? 2 * p.cap_max : 16;
       Prof::Rec* np = new Prof::Rec[nc];
@@ -117,11 +110,11 @@ void prof_end(const cpma* hc, cudaStream_t st) {
       p.cap_recs = np;
       p.cap_max = nc;
     }
-    p.cap_recs[p.ncap++] = p.open_rec;
-    p.open_rec.phase = -1;
+    p.cap_recs[p.ncap++] = r;
+    r.phase = -1;
     return;
   }
-  if (p.open_rec.b) cudaEventRecord(p.open_rec.b, st);
+  if (r.b) cudaEventRecord(r.b, st);
   if (p.npending == p.cap) {
     int nc = p.cap ? 2 * p.cap : 64;
     Prof::Rec* np = new Prof::Rec[nc];
@@ -130,8 +123,39 @@ void prof_end(const cpma* hc, cudaStream_t st) {
     p.pending = np;
     p.cap = nc;
   }
-  p.pending[p.npending++] = p.open_rec;
-  p.open_rec.phase = -1;
+  p.pending[p.npending++] = r;
+  r.phase = -1;
+}
+}  // namespace
+
+void prof_begin(const cpma* hc, int phase, cudaStream_t st) {
+  cpma* h = const_cast<cpma*>(hc);
+  Prof& p = h->prof;
+  if (!p.on) return;
+  if (p.open_rec.phase >= 0) prof_end(h, st);
+  rec_begin(p, p.open_rec, phase, st);
+}
+
+void prof_end(const cpma* hc, cudaStream_t st) {
+  cpma* h = const_cast<cpma*>(hc);
+  Prof& p = h->prof;
+  if (!p.on || p.open_rec.phase < 0) return;
+  rec_end(p, p.open_rec, st);
+}
+
+void prof_begin_side(const cpma* hc, int phase, cudaStream_t st) {
+  cpma* h = const_cast<cpma*>(hc);
+  Prof& p = h->prof;
+  if (!p.on) return;
+  if (p.side_rec.phase >= 0) rec_end(p, p.side_rec, st);
+  rec_begin(p, p.side_rec, phase, st);
+}
+
+void prof_end_side(const cpma* hc, cudaStream_t st) {
+  cpma* h = const_cast<cpma*>(hc);
+  Prof& p = h->prof;
+  if (!p.on || p.side_rec.phase < 0) return;
+  rec_end(p, p.side_rec, st);
 }
 
 void prof_resolve(const cpma* hc) {

@@ -34,8 +34,7 @@ struct Status {
   ull n_lane;      // touched leaves for the lane-granular insert
   ull n_v1;        // touched leaves for the element-array splice
   ull n_gen;       // work items for the general merge
-  ull n_thr;       // touched leaves for the thread-granular insert
-  ull pad[9];
+  ull pad[10];
   ull empties;     // empty leaves in the structure (written by the head
                    // fix-up; not cleared at the start of a batch)
 };
@@ -97,6 +96,7 @@ struct Prof {
   // events belong to the graph and are recorded again by every replay
   struct Rec { int phase; cudaEvent_t a, b; bool pooled; };
   Rec open_rec{-1, nullptr, nullptr, true};
+  Rec side_rec{-1, nullptr, nullptr, true};  // a phase running on the side stream meanwhile
   // while a graph is being captured: its event pairs and its host-side byte
   // counts, which each replay adds
   bool capturing = false;
@@ -135,6 +135,10 @@ struct cpma {
   uint64_t graph_max_batch = 0;     // batches up to this size run their front segment as a graph
   void* graphs = nullptr;           // graph cache (update.cu)
   cudaStream_t cap_stream = nullptr;  // private stream graphs are captured on
+  // side stream of the merge fork (k_insert_lane next to k_insert_thread) and
+  // its fork / join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   uint64_t graph_captures = 0, graph_launches = 0;
 };
 
@@ -209,6 +213,10 @@ int sync_status(cpma* h, cudaStream_t st);
 // profiling (no-ops unless enabled)
 void prof_begin(const cpma* h, int phase, cudaStream_t st);
 void prof_end(const cpma* h, cudaStream_t st);
+// A second phase open at the same time, on another stream (the side stream
+// of a fork).
+void prof_begin_side(const cpma* h, int phase, cudaStream_t st);
+void prof_end_side(const cpma* h, cudaStream_t st);
 void prof_resolve(const cpma* h);  // call only after the stream is idle
 // queue a replayed graph's event pairs for resolution and add its host bytes
 void prof_push(const cpma* h, const Prof::Rec* recs, int n, const unsigned long long* host_bytes);

@@ -51,6 +51,7 @@ struct Result {
   uint32_t added;    // bit q: slice key q was added
   uint32_t wlo, whi; // byte range rewritten (kWritten)
   uint32_t E;        // edits
+  uint32_t maxcode;  // longest code the edits write (bytes)
   uint64_t newhead;
 };
 
@@ -323,7 +324,7 @@ LT_HD uint32_t plan_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
     S.rcode[k * S.rs] = 0u;
   }
   // ---- edits: new keys grouped by the gap they fall in ----
-  uint32_t E = 0, nn = 0, added = 0;
+  uint32_t E = 0, nn = 0, added = 0, mc = 0;
   int32_t tot = 0;
   uint64_t newhead = head;
   for (uint32_t q = 0; q < s;) {
@@ -334,10 +335,11 @@ LT_HD uint32_t plan_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
     const uint32_t os = rp & 0xFFFu, oe = (rp >> 12) & 0xFFFu;
     const uint64_t rv = S.rval[q * S.rs];
     uint64_t prev = pick(y, q);
-    uint32_t nl;
+    uint32_t nl, cl = 0;
     if (kind == kHead) { nl = 8u; newhead = prev; }
-    else if (kind == kGap) nl = leb_bytes(prev - (rv - S.rcode[q * S.rs]));
-    else nl = leb_bytes(prev - rv);
+    else if (kind == kGap) nl = cl = leb_bytes(prev - (rv - S.rcode[q * S.rs]));
+    else nl = cl = leb_bytes(prev - rv);
+    mc = mc > cl ? mc : cl;
     added |= 1u << q;
     nn++;
     uint32_t q1 = q + 1;
@@ -346,12 +348,18 @@ LT_HD uint32_t plan_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
       if ((rp1 & 0xFFFu) != os) break;
       if ((rp1 >> 24) == kSkip) continue;
       const uint64_t x = pick(y, q1);
-      nl += leb_bytes(x - prev);
+      cl = leb_bytes(x - prev);
+      mc = mc > cl ? mc : cl;
+      nl += cl;
       prev = x;
       added |= 1u << q1;
       nn++;
     }
-    if (kind != kAfter) nl += leb_bytes(rv - prev);  // the old successor (head or code end)
+    if (kind != kAfter) {  // the old successor (head or code end)
+      cl = leb_bytes(rv - prev);
+      mc = mc > cl ? mc : cl;
+      nl += cl;
+    }
     tot += (int32_t)nl - (int32_t)(oe - os);
     S.epos[E * S.rs] = os | (oe << 12) | (kind << 24);
     S.esa[E * S.rs] = tot;
@@ -360,6 +368,7 @@ LT_HD uint32_t plan_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
     q = q1;
   }
   R.added = added;
+  R.maxcode = mc;
   R.newc = m + nn;
   R.nb = (uint32_t)((int32_t)uold + tot);
   R.newhead = newhead;

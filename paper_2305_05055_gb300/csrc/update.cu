@@ -151,7 +151,6 @@ struct MergeArgs {
   ull* prof;  // profiling: algorithmic bytes of this kernel (nullable)
   const uint32_t* tags;  // per sorted key: request tag (nullable)
   ull* tag_counts;       // per tag: keys added / removed (nullable)
-  uint32_t* list_thr;    // touched leaves for k_insert_thread (count st->n_thr)
   uint32_t* list_lane;   // touched leaves for k_insert_lane (count st->n_lane)
   uint32_t* list_v1;     // touched leaves for k_merge_small (count st->n_v1)
   uint32_t* list_gen;    // work items for k_merge in count mode (st->n_gen)
@@ -630,121 +629,108 @@ __global__ void __launch_bounds__(kT, SEG == 32 ? 4 : 3) k_insert_lane(MergeArgs
 // bytes goes to the element-array splice (state kFallback); a result over LB
 // bytes is left pending for the general merge.
 constexpr int kThrT = 256;
-constexpr int kThrR = 1;         // leaves per thread and tile, at most
 constexpr int kThrBuckets = 128;  // tile sort buckets: 16-byte chunks of the old leaf
+constexpr uint32_t kThrKeys = leafthr::kKeys;
+
+// The touched leaves k_insert_thread takes (the kernel runs for inserts into
+// byte-code leaves only).
+__device__ __forceinline__ bool thread_class(uint32_t s, uint32_t uold) {
+  return s >= 1 && s <= kThrKeys && uold > 0;
+}
+
 __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
   constexpr uint32_t K = leafthr::kKeys;
   __shared__ uint32_t s_rpos[K * kThrT], s_rcode[K * kThrT];
   __shared__ uint64_t s_rval[K * kThrT];
   __shared__ uint32_t s_epos[K * kThrT], s_ekey[K * kThrT];
   __shared__ int32_t s_esa[K * kThrT];
-  __shared__ uint32_t s_tile[kThrR * kThrT];
-  __shared__ uint32_t s_hist[kThrBuckets];
+  __shared__ uint32_t s_tile[kThrT];
+  __shared__ uint32_t s_hist[kThrBuckets + 1];
   if (a.st->err) return;
   const unsigned tid = threadIdx.x;
   const leafthr::Scratch S{s_rpos + tid, s_rval + tid, s_rcode + tid, s_epos + tid,
                            s_esa + tid,  s_ekey + tid, (uint32_t)kThrT};
-  const uint64_t n = a.st->n_thr;
-  // Tiles of R * kThrT list entries, R <= kThrR chosen so that the grid's
-  // tiles cover the list at most once where it can.  Each tile is sorted by
-  // the size of the old leaf (counting sort in shared memory), so that the
-  // 32 leaves of a warp take about the same number of decode steps.
-  const uint64_t per = (uint64_t)gridDim.x * kThrT;
-  const uint32_t R = (uint32_t)std::min<uint64_t>(kThrR, std::max<uint64_t>(1, (n + per - 1) / per));
-  const uint64_t tile = (uint64_t)R * kThrT;
+  const uint64_t n = a.st->nT;
   ull nbytes = 0;
-  for (uint64_t base = (uint64_t)blockIdx.x * tile; base < n; base += (uint64_t)gridDim.x * tile) {
-    for (uint32_t i = tid; i < kThrBuckets; i += kThrT) s_hist[i] = 0u;
+  // Tiles of kThrT touched leaves; those of this kernel's class are sorted by
+  // the size of the old leaf (counting sort in shared memory), so that the 32
+  // leaves of a warp take about the same number of decode steps.
+  for (uint64_t base = (uint64_t)blockIdx.x * kThrT; base < n; base += (uint64_t)gridDim.x * kThrT) {
+    for (uint32_t i = tid; i <= kThrBuckets; i += kThrT) s_hist[i] = 0u;
     __syncthreads();
-    uint32_t ent[kThrR], bkt[kThrR], slot[kThrR];
-#pragma unroll
-    for (uint32_t r = 0; r < kThrR; r++) {
-      const uint64_t idx = base + tid + (uint64_t)r * kThrT;
-      ent[r] = 0xFFFFFFFFu;
-      bkt[r] = 0u;
-      slot[r] = 0u;
-      if (r < R && idx < n) {
-        ent[r] = a.list_thr[idx];
-        bkt[r] = min((uint32_t)kThrBuckets - 1u, (a.T_oldused[ent[r]] + 15u) >> 4);
-        slot[r] = atomicAdd(&s_hist[bkt[r]], 1u);
+    const uint64_t idx = base + tid;
+    uint32_t bkt = 0, slot = 0;
+    bool mine = false;
+    if (idx < n) {
+      const uint32_t uo = a.T_oldused[idx];
+      mine = thread_class(a.T_begin[idx + 1] - a.T_begin[idx], uo);
+      if (mine) {
+        bkt = min((uint32_t)kThrBuckets - 1u, (uo + 15u) >> 4);
+        slot = atomicAdd(&s_hist[bkt], 1u);
       }
     }
     __syncthreads();
-    if (tid < 32) {  // exclusive scan of the bucket counts
+    if (tid < 32) {  // exclusive scan of the bucket counts, total in s_hist[128]
       static_assert(kThrBuckets == 128, "4 buckets per lane");
       const uint32_t c0 = s_hist[4 * tid], c1 = s_hist[4 * tid + 1], c2 = s_hist[4 * tid + 2],
                      c3 = s_hist[4 * tid + 3];
       const uint32_t sum = c0 + c1 + c2 + c3;
-      const uint32_t ex = warp_incl_scan(sum) - sum;
+      const uint32_t inc = warp_incl_scan(sum), ex = inc - sum;
       s_hist[4 * tid] = ex;
       s_hist[4 * tid + 1] = ex + c0;
       s_hist[4 * tid + 2] = ex + c0 + c1;
       s_hist[4 * tid + 3] = ex + c0 + c1 + c2;
+      if (tid == 31) s_hist[kThrBuckets] = inc;
     }
     __syncthreads();
-#pragma unroll
-    for (uint32_t r = 0; r < kThrR; r++)
-      if (ent[r] != 0xFFFFFFFFu) s_tile[s_hist[bkt[r]] + slot[r]] = ent[r];
+    if (mine) s_tile[s_hist[bkt] + slot] = (uint32_t)idx;
     __syncthreads();
-    const uint64_t cnt = std::min<uint64_t>(tile, n - base);
-    for (uint32_t r = 0; r < R; r++) {
-      const uint32_t pos = r * kThrT + tid;
-      const bool have = pos < cnt;
-      uint32_t t = 0, tb = 0, s = 0, uold = 0, j = 0, m = 0, fc0 = 0, fc1 = 0;
-      uint32_t res = leafthr::kUnchanged;
-      uint64_t y[K] = {0ull, 0ull, 0ull, 0ull};
-      leafthr::Result R2;
-      R2.E = 0;
-      if (have) {
-        t = s_tile[pos];
-        tb = a.T_begin[t];
-        s = a.T_begin[t + 1] - tb;
-        uold = a.T_oldused[t];
-        j = a.T_leaf[t];
-        m = a.T_oldcnt[t];
-        fc0 = a.T_first_chunk[t];
-        fc1 = a.T_first_chunk[t + 1];
+    if (tid < s_hist[kThrBuckets]) {
+      const uint32_t t = s_tile[tid];
+      const uint32_t tb = a.T_begin[t], s = a.T_begin[t + 1] - tb;
+      const uint32_t uold = a.T_oldused[t], j = a.T_leaf[t], m = a.T_oldcnt[t];
+      const uint32_t fc0 = a.T_first_chunk[t], fc1 = a.T_first_chunk[t + 1];
+      uint8_t* leafp = a.data + (size_t)j * a.LB;
+      // the old leaf, the slice and ~28 bytes of per-leaf metadata
+      nbytes += uold + 8u * s + 28u;
+      uint64_t y[K];
 #pragma unroll
-        for (uint32_t q = 0; q < K; q++) y[q] = q < s ? a.u[tb + q] : 0ull;
-        // the old leaf, the slice and ~28 bytes of per-leaf metadata
-        nbytes += uold + 8u * s + 28u;
-        res = leafthr::plan_leaf(a.data + (size_t)j * a.LB, a.LB, uold, m, y, s, S, R2);
-      }
-      if (!have) continue;
-      if (res == leafthr::kWritten) leafthr::rewrite_leaf(a.data + (size_t)j * a.LB, a.LB, uold, S, R2);
+      for (uint32_t q = 0; q < K; q++) y[q] = q < s ? a.u[tb + q] : 0ull;
+      leafthr::Result R;
+      R.E = 0;
+      const uint32_t res = leafthr::plan_leaf(leafp, a.LB, uold, m, y, s, S, R);
       if (res == leafthr::kLongCode) {
         a.T_state[t] = kFallback;
         a.list_v1[atomicAdd(&a.st->n_v1, 1ull)] = t;
-        continue;
-      }
-      if (res == leafthr::kBadCount) {
+      } else if (res == leafthr::kBadCount) {
         atomicOr(&a.st->err, kErrState);
-        continue;
-      }
-      uint32_t c0 = 0;
-      if (res == leafthr::kUnchanged) {
-        a.T_state[t] = kUnchanged;
-        a.T_newcnt[t] = m;
-        a.T_newbytes[t] = uold;
-      } else if (res == leafthr::kTooBig) {
-        a.T_state[t] = kPending;
-        a.T_newcnt[t] = R2.newc;
-        a.T_newbytes[t] = R2.nb;
-        c0 = R2.newc;
       } else {
-        leafthr::write_edits(a.data + (size_t)j * a.LB, y, S, R2);
-        a.used[j] = R2.nb;
-        a.cnt[j] = R2.newc;
-        a.heads[j] = R2.newhead;
-        a.T_state[t] = kInPlace;
-        a.T_newcnt[t] = R2.newc;
-        a.T_newbytes[t] = R2.nb;
-        nbytes += R2.whi - R2.wlo;
+        uint32_t c0 = 0;
+        if (res == leafthr::kUnchanged) {
+          a.T_state[t] = kUnchanged;
+          a.T_newcnt[t] = m;
+          a.T_newbytes[t] = uold;
+        } else if (res == leafthr::kTooBig) {
+          a.T_state[t] = kPending;
+          a.T_newcnt[t] = R.newc;
+          a.T_newbytes[t] = R.nb;
+          c0 = R.newc;
+        } else {
+          leafthr::rewrite_leaf(leafp, a.LB, uold, S, R);
+          leafthr::write_edits(leafp, y, S, R);
+          nbytes += R.whi - R.wlo;
+          a.used[j] = R.nb;
+          a.cnt[j] = R.newc;
+          a.heads[j] = R.newhead;
+          a.T_state[t] = kInPlace;
+          a.T_newcnt[t] = R.newc;
+          a.T_newbytes[t] = R.nb;
+        }
+        for (uint32_t cq = fc0; cq < fc1; cq++) a.chunk_cnt[cq] = cq == fc0 ? c0 : 0u;
+        if (a.tag_counts)
+          for (uint32_t q = 0; q < s; q++)
+            if ((R.added >> q) & 1u) credit(a, tb + q);
       }
-      for (uint32_t cq = fc0; cq < fc1; cq++) a.chunk_cnt[cq] = cq == fc0 ? c0 : 0u;
-      if (a.tag_counts)
-        for (uint32_t q = 0; q < s; q++)
-          if ((R2.added >> q) & 1u) credit(a, tb + q);
     }
     __syncthreads();
   }
@@ -753,8 +739,9 @@ __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
 }
 
 // Sort the touched leaves into the merge kernels' work lists: inserts of at
-// most leafthr::kKeys keys -> k_insert_thread; other small inserts into leaves
-// of at most 512 used bytes -> k_insert_lane; other small slices
+// most kThrKeys keys go to k_insert_thread, which walks the touched leaves
+// itself (no list); other small inserts into leaves of at most 512 used
+// bytes -> k_insert_lane; other small slices
 // into non-empty leaves -> k_merge_small; the rest -> k_merge, one entry per
 // work item (a slice of at most kChunk keys is merged whole by its first item,
 // the others get a zero overflow count here).
@@ -772,7 +759,7 @@ __global__ void __launch_bounds__(kT) k_classify(MergeArgs a) {
       const uint32_t uold = a.T_oldused[t];
       if (small_slice(tb, te, uold)) {
         const bool ins = !a.is_delete && !a.raw;
-        cls = (ins && te - tb <= leafthr::kKeys) ? 4u
+        cls = (ins && thread_class(te - tb, uold)) ? 4u
             : (ins && uold <= 512 && te - tb <= (uint32_t)kLaneSeg) ? 0u : 1u;
       } else {
         cls = 2;
@@ -780,7 +767,6 @@ __global__ void __launch_bounds__(kT) k_classify(MergeArgs a) {
         fc1 = a.T_first_chunk[t + 1];
       }
     }
-    warp_append(cls == 4, (uint32_t)t, a.list_thr, &a.st->n_thr);
     warp_append(cls == 0, (uint32_t)t, a.list_lane, &a.st->n_lane);
     warp_append(cls == 1, (uint32_t)t, a.list_v1, &a.st->n_v1);
     if (cls == 2) {
@@ -2018,6 +2004,9 @@ void merge_attrs() {
 int front_scratch(cpma* h, uint64_t k, bool tagged, cudaStream_t st) {
   Scratch& s = h->s;
   merge_attrs();
+  if (!h->side) CPMA_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  if (!h->ev_fork) CPMA_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  if (!h->ev_join) CPMA_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   CPMA_TRY(sort_scratch(h, k, tagged));
   CPMA_TRY(ensure(s.partials, (size_t)(2 * h->num_sms + 2) * 8));
   CPMA_TRY(ensure(s.leaf_of, k * 4));
@@ -2028,7 +2017,7 @@ int front_scratch(cpma* h, uint64_t k, bool tagged, cudaStream_t st) {
     CPMA_TRY(ensure(*b, (k + 2) * 4));
   CPMA_TRY(ensure(s.chunk_off, (k + 2) * 8));
   CPMA_TRY(ensure(s.T_newbytes, (k + 2) * 8));
-  CPMA_TRY(ensure(s.list_lane, 2 * (k + 2) * 4));  // lane list, then the thread list
+  CPMA_TRY(ensure(s.list_lane, (k + 2) * 4));
   CPMA_TRY(ensure(s.list_v1, (k + 2) * 4));
   CPMA_TRY(ensure(s.list_gen, (k + 2) * 4));
   CPMA_TRY(ensure(s.cand, (2 * k + 2) * 8));
@@ -2123,7 +2112,6 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   ma.tags = ut;
   ma.tag_counts = tags ? reinterpret_cast<ull*>(tag_counts) : nullptr;
   ma.list_lane = P<uint32_t>(s.list_lane);
-  ma.list_thr = P<uint32_t>(s.list_lane) + (k + 2);
   ma.list_v1 = P<uint32_t>(s.list_v1);
   ma.list_gen = P<uint32_t>(s.list_gen);
   ma.raw = (int)h->cfg.codec;
@@ -2142,6 +2130,18 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
     const int sgrid = (int)std::max<uint64_t>(
         1, std::min<uint64_t>((k + swarps - 1) / swarps, (uint64_t)h->num_sms * 8));
     if (!is_delete) {
+      // the thread-granular insert on st and the lane-granular one on the
+      // side stream at the same time: disjoint leaves and outputs (shared
+      // counters by atomics); the lane kernel's few leaves are latency-bound
+      CPMA_CUDA(cudaEventRecord(h->ev_fork, st));
+      CPMA_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+      prof_begin_side(h, PH_MERGE_LANE, h->side);
+      MergeArgs ml = ma;
+      ml.prof = prof_bytes(h, PH_MERGE_LANE);
+      k_insert_lane<kLaneSeg><<<sgrid, 256, lane_warp_bytes(kLaneSeg) * 8, h->side>>>(ml);
+      h->launches++;
+      prof_end_side(h, h->side);
+      CPMA_CUDA(cudaEventRecord(h->ev_join, h->side));
       ma.prof = prof_bytes(h, PH_MERGE);
       if (!ma.raw) {
         const int tgrid = (int)std::max<uint64_t>(
@@ -2149,12 +2149,8 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
         k_insert_thread<<<tgrid, kThrT, 0, st>>>(ma);
         h->launches++;
       }
-      prof_end(h, st);
-      prof_begin(h, PH_MERGE_LANE, st);
-      ma.prof = prof_bytes(h, PH_MERGE_LANE);
-      k_insert_lane<kLaneSeg><<<sgrid, 256, lane_warp_bytes(kLaneSeg) * 8, st>>>(ma);
-      h->launches++;
       ma.prof = nullptr;
+      CPMA_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
     }
     prof_end(h, st);
     prof_begin(h, PH_MERGE2, st);
@@ -2375,6 +2371,11 @@ void graph_cache_free(cpma* h) {
   h->graphs = nullptr;
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   h->cap_stream = nullptr;
+  if (h->side) cudaStreamDestroy(h->side);
+  h->side = nullptr;
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  h->ev_fork = h->ev_join = nullptr;
 }
 
 // R14: apply the batch by merging it with every element and building the

@@ -564,3 +564,34 @@ def test_profiling_with_graph_replays():
         assert prof[ph]["calls"] == 5 and prof[ph]["ms"] > 0, (ph, prof[ph])
     assert prof["merge"]["bytes"] > 0
     g.profile(False)
+
+
+@pytest.mark.parametrize("bits", [40, 26])
+def test_insert_five_to_eight_keys_per_leaf(bits):
+    """Batches of about six keys per touched leaf: slices of up to 4 keys take
+    the thread-granular insert, larger ones the lane-granular insert running
+    on the side stream at the same time (or the element-array splice).
+    26-bit keys make one-byte codes and full leaves.  Layout against the
+    sequential oracle; per-request counts of a tagged insert against applying
+    the requests in order."""
+    base = W.uniform_keys(71 + bits, 1 << 18, bits=bits)
+    g = cp.CPMA(T(base), leaf_bytes=512)
+    o = oracle.SeqCPMA(base, leaf_bytes=512)
+    p = oracle.PlainSet(base)
+    ins = W.uniform_keys(72 + bits, 6 * g.leaves(), bits=bits)
+    assert int(g.insert_batch(T(ins)).item()) == o.insert_batch(ins) == p.insert_batch(ins)
+    same_layout(g, o)
+    # tagged: 7 requests of consecutive keys
+    more = W.uniform_keys(73 + bits, 6 * g.leaves(), bits=bits)
+    tags = (np.arange(more.size) * 7 // more.size).astype(np.int32)
+    counts = torch.zeros(7, dtype=torch.int64, device="cuda")
+    cp.cpma_insert_batch_tagged(g.handle, T(more), torch.from_numpy(tags).cuda(), 7, counts)
+    seen = set(p.S.tolist())
+    want = [0] * 7
+    for x, t in zip(more.tolist(), tags.tolist()):
+        if x not in seen:
+            seen.add(x)
+            want[t] += 1
+    assert counts.cpu().tolist() == want
+    o.insert_batch(more)
+    same_layout(g, o)
