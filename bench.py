@@ -290,14 +290,19 @@ def main():
     g = cp.CPMA(base, leaf_bytes=a.leaf_bytes)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
+    nphase = 3  # profiled steps after the timed region, for the per-phase split
     batches = [T(W.uniform_keys(10 ** 6 + 1000 * rank + i, k, bits=40))
-               for i in range(nwarm + nsteps)]
+               for i in range(nwarm + nsteps + 1 + nphase)]
     # the library's fastest form for this batch size: scratch reserved and
     # the batch front segment replayed as a CUDA graph (captured, with its
-    # profiling event nodes, during the warm-up steps)
+    # profiling event nodes, during the warm-up steps).  The timed steps time
+    # only the merge phase (the dominant kernel) on the device, so that the
+    # profiler adds as little as possible to them; the per-phase split comes
+    # from a few fully profiled steps afterwards.
+    TIMED_PHASES = ["merge"]
     g.reserve(k)
     g.use_graphs(1 << 21)
-    g.profile(True)
+    g.profile(True, phases=TIMED_PHASES)
     for i in range(nwarm):
         g.insert_batch(batches[i])
     torch.cuda.synchronize()
@@ -305,7 +310,7 @@ def main():
     torch.cuda.synchronize()
 
     # ---- timed region: K insert steps ----
-    g.profile(True)          # reset the per-phase counters
+    g.profile(True, phases=TIMED_PHASES)  # reset the per-phase counters
     l0 = g.launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
@@ -318,13 +323,26 @@ def main():
     ms = e0.elapsed_time(e1)
     launches = g.launches() - l0
     prof = g.profile_read()
-    g.profile(False)
     ms, value = aggregate(ms, nsteps * k, dist)
 
-    # roofline of the dominant kernel of the step
+    # per-phase split: every phase timed, a few more steps (the first one
+    # captures the graph with all its event nodes)
+    g.profile(True)
+    g.insert_batch(batches[nwarm + nsteps])
+    torch.cuda.synchronize()
+    g.profile(True)
+    for i in range(nphase):
+        g.insert_batch(batches[nwarm + nsteps + 1 + i])
+    torch.cuda.synchronize()
+    prof_all = g.profile_read()
+    g.profile(False)
+
+    # roofline of the dominant kernel of the step (timed in the timed region)
     upd = ["sort", "route", "merge", "merge_lane", "merge_other", "count", "redistribute",
            "finish"]
-    dom = max(upd, key=lambda p: prof[p]["ms"])
+    dom = max(upd, key=lambda p: prof_all[p]["ms"])
+    if dom not in TIMED_PHASES:
+        prof = prof_all
     kernel_of = {"merge": "k_insert_thread", "merge_lane": "k_insert_lane",
                  "merge_other": "k_merge_small+k_merge",
                  "sort": "radix sort", "route": "route", "count": "counting",
@@ -337,9 +355,12 @@ def main():
                 "kernel": kernel_of.get(p, p), "ms_per_launch": msp / calls,
                 "bytes_per_launch": by / calls, "peak_kind": peak_kind}
     roofline = roof(dom)
-    phases = {p: {"ms_per_step": prof[p]["ms"] / nsteps,
-                  "gbs": (prof[p]["bytes"] / (prof[p]["ms"] / 1e3) / 1e9) if prof[p]["ms"] else None}
+    phases = {p: {"ms_per_step": prof_all[p]["ms"] / nphase,
+                  "gbs": (prof_all[p]["bytes"] / (prof_all[p]["ms"] / 1e3) / 1e9)
+                  if prof_all[p]["ms"] else None}
               for p in upd}
+    phases["note"] = ("device time per step of each phase over %d fully profiled steps after "
+                      "the timed ones; the timed steps time only %s" % (nphase, TIMED_PHASES))
 
     # ---- end to end through the public API with host buffers ----
     host_batches = [batches[nwarm + i].cpu().pin_memory() for i in range(nsteps)]

@@ -309,6 +309,11 @@ int cpma_reset_stats(cpma_t* h);
  * (any pointer may be NULL). */
 #define CPMA_NPHASES 12
 int cpma_profile(cpma_t* h, int enable);
+/* Time only the phases whose bit is set in mask (bit i = phase i; default
+ * all): fewer event pairs on the stream and in captured graphs, so the timed
+ * work is disturbed less.  Byte counts still cover every phase.  Synchronises
+ * the device; graphs captured under another mask are captured again. */
+int cpma_profile_mask(cpma_t* h, uint32_t mask);
 int cpma_profile_read(cpma_t* h, double* ms, uint64_t* bytes, uint64_t* calls, int nphases);
 
 /* Text for an error code. */

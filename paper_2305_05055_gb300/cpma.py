@@ -74,6 +74,7 @@ def lib():
                 "cpma_delete_batch_tagged": (I, [V, V, V, U64, I, U64, V, V]),
                 "cpma_sort_batch": (I, [V, V, V, U64, V, V, V]),
                 "cpma_profile": (I, [V, I]),
+                "cpma_profile_mask": (I, [V, C.c_uint32]),
                 "cpma_profile_read": (I, [V, C.POINTER(C.c_double), P64, P64, I]),
                 "cpma_reserve": (I, [V, U64, U64, I, V]),
                 "cpma_range_map_length": (I, [V, V, V, U64, V, V, V]),
@@ -357,6 +358,12 @@ def cpma_profile(h, enable: bool = True):
     _check(lib().cpma_profile(h, int(bool(enable))), "cpma_profile")
 
 
+def cpma_profile_mask(h, phases=None):
+    """Time only the named phases (None: all of them)."""
+    mask = 0xFFFFFFFF if phases is None else sum(1 << PHASES.index(p) for p in phases)
+    _check(lib().cpma_profile_mask(h, mask), "cpma_profile_mask")
+
+
 def cpma_profile_read(h) -> dict:
     n = len(PHASES)
     ms = (C.c_double * n)()
@@ -457,7 +464,10 @@ class CPMA:
     def graph_stats(self) -> dict:
         return cpma_graph_stats(self._h)
 
-    def profile(self, enable: bool = True):
+    def profile(self, enable: bool = True, phases=None):
+        """Reset and enable (or disable) per-phase profiling; `phases` limits
+        the timed phases (names of PHASES), the byte counts cover all."""
+        cpma_profile_mask(self._h, phases)
         cpma_profile(self._h, enable)
 
     def profile_read(self) -> dict:

@@ -133,6 +133,7 @@ void prof_begin(const cpma* hc, int phase, cudaStream_t st) {
   Prof& p = h->prof;
   if (!p.on) return;
   if (p.open_rec.phase >= 0) prof_end(h, st);
+  if (!((p.mask >> phase) & 1u)) return;
   rec_begin(p, p.open_rec, phase, st);
 }
 
@@ -148,6 +149,7 @@ void prof_begin_side(const cpma* hc, int phase, cudaStream_t st) {
   Prof& p = h->prof;
   if (!p.on) return;
   if (p.side_rec.phase >= 0) rec_end(p, p.side_rec, st);
+  if (!((p.mask >> phase) & 1u)) return;
   rec_begin(p, p.side_rec, phase, st);
 }
 
@@ -546,6 +548,14 @@ int cpma_profile(cpma_t* h, int enable) {
   CPMA_CUDA(cudaMemset(p.d_bytes, 0, sizeof(unsigned long long) * PH_N));
   for (int i = 0; i < PH_N; i++) { p.ms[i] = 0; p.calls[i] = 0; p.host_bytes[i] = 0; }
   p.on = enable != 0;
+  return CPMA_OK;
+}
+
+int cpma_profile_mask(cpma_t* h, uint32_t mask) {
+  if (!h) return CPMA_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return CPMA_ECUDA;
+  prof_resolve(h);
+  h->prof.mask = mask;
   return CPMA_OK;
 }
 

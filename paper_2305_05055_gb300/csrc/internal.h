@@ -92,6 +92,7 @@ enum Phase {
 // and resolved at the next host synchronisation, so profiling adds no waits.
 struct Prof {
   bool on = false;
+  uint32_t mask = ~0u;  // phases timed (bit per phase); the byte counts cover all
   // pooled: the events go back to the pool once resolved; a captured graph's
   // events belong to the graph and are recorded again by every replay
   struct Rec { int phase; cudaEvent_t a, b; bool pooled; };

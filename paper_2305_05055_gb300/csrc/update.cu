@@ -2249,6 +2249,7 @@ struct GraphSlot {
   uint64_t K = 0, last_use = 0, launches = 0;
   int sorted = 0, is_delete = 0;
   bool prof = false;  // captured with per-phase profiling (event record nodes)
+  uint32_t prof_mask = 0;  // the phases that got event nodes
   FrontSig sig{};
   Front f;
   std::vector<Prof::Rec> recs;        // the graph's event pairs
@@ -2299,7 +2300,7 @@ int run_front_graph(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int
   const bool prof = h->prof.on;
   for (GraphSlot& g : c.slot)
     if (g.exec && g.K == K && g.sorted == sorted && g.is_delete == is_delete && g.sig == sig &&
-        g.prof == prof)
+        g.prof == prof && (!prof || g.prof_mask == h->prof.mask))
       slot = &g;
   if (!slot) {
     slot = &c.slot[0];
@@ -2346,6 +2347,7 @@ int run_front_graph(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int
     }
     slot->exec = ex;
     slot->prof = prof;
+    slot->prof_mask = h->prof.mask;
     slot->K = K;
     slot->sorted = sorted;
     slot->is_delete = is_delete;
