@@ -57,6 +57,24 @@ __device__ __forceinline__ bool bsearch_sm(const uint64_t* a, uint32_t n, uint64
 // ---------------------------------------------------------------------------
 // 2. routing
 // ---------------------------------------------------------------------------
+// Leaf of x given that the count of heads <= x lies in [lo, lo + n]
+// (route_leaf restricted to that range).
+__device__ __forceinline__ uint32_t route_in(const uint64_t* __restrict__ heads, uint64_t L,
+                                             uint64_t lo, uint64_t n, uint64_t x) {
+  if (x == KEY_MAX) return (uint32_t)heads[L];
+  const uint64_t c = lo + (n ? upper_count(heads + lo, n, x) : 0);
+  return (uint32_t)(c ? c - 1 : 0);
+}
+
+// Route every key of the sorted batch; flag run starts (a new leaf) and
+// chunk starts.  A warp's keys are consecutive in sorted order, so they fall
+// in a short stretch of leaves: the warp first narrows the head range that
+// holds the counts of its smallest and largest key (including the key
+// before the warp, for the run flag of lane 0) with up to four rounds of 32
+// evenly spaced samples and two ballots, then each lane searches the
+// narrowed range.  The dependent-load chain drops from log2 L loads to about
+// four plus log2 of the stretch.  (An unsorted batch, which is flagged, can
+// only make the range empty: every index stays in [0, L).)
 __global__ void __launch_bounds__(kT) k_route_flags(const uint64_t* __restrict__ u, uint64_t k,
                                                     const uint64_t* __restrict__ heads, uint64_t L,
                                                     uint32_t* __restrict__ leaf_of,
@@ -67,13 +85,30 @@ __global__ void __launch_bounds__(kT) k_route_flags(const uint64_t* __restrict__
     const uint64_t i = base + lane;
     const bool valid = i < k;
     const uint64_t x = valid ? u[i] : 0;
-    const uint32_t leaf = valid ? (uint32_t)route_leaf(heads, L, x) : 0u;
-    uint32_t prev = __shfl_up_sync(FULL, leaf, 1);
+    const unsigned vm = __ballot_sync(FULL, valid);
+    const int last = 31 - __clz(vm);
     uint64_t px = __shfl_up_sync(FULL, x, 1);
-    if (lane == 0 && i > 0 && valid) {
-      px = u[i - 1];
-      prev = (uint32_t)route_leaf(heads, L, px);
+    if (lane == 0 && i > 0) px = u[i - 1];
+    const uint64_t xlo = __shfl_sync(FULL, (lane == 0 && i > 0) ? min(px, x) : x, 0);
+    const uint64_t xhi = __shfl_sync(FULL, x, last);
+    uint64_t lo = 0, n = L;
+    for (int it = 0; it < 4 && n > 64; it++) {
+      const uint64_t step = (n + 31) / 32;
+      const uint64_t ns = (n + step - 1) / step;  // samples inside the range
+      const uint64_t p = lo + lane * step;
+      const bool in = lane < ns;
+      const uint64_t hv = in ? __ldg(heads + p) : 0;
+      const unsigned mlo = __popc(__ballot_sync(FULL, in && hv <= xlo));
+      const unsigned mhi = __popc(__ballot_sync(FULL, in && hv <= xhi));
+      const uint64_t nlo = mlo ? lo + (uint64_t)(mlo - 1) * step + 1 : lo;
+      uint64_t nhi = mhi < ns ? lo + (uint64_t)mhi * step : lo + n;
+      if (nhi < nlo) nhi = nlo;  // unsorted batch
+      lo = nlo;
+      n = nhi - nlo;
     }
+    const uint32_t leaf = valid ? route_in(heads, L, lo, n, x) : 0u;
+    uint32_t prev = __shfl_up_sync(FULL, leaf, 1);
+    if (lane == 0 && i > 0 && valid) prev = route_in(heads, L, lo, n, px);
     if (valid) {
       if (i > 0 && px > x) atomicOr(&st->err, kErrUnsorted);
       const uint64_t run = (i == 0 || leaf != prev) ? 1u : 0u;
