@@ -287,6 +287,18 @@ __host__ __device__ constexpr size_t lane_warp_bytes(int seg) {
   return (size_t)(32 / seg) * lane_seg_bytes(seg);
 }
 
+// Inserts into byte-code leaves are split by slice size: up to kThrKeys keys
+// -> k_insert_thread (which walks the touched leaves itself), then up to
+// kLaneSeg keys into leaves of at most 512 used bytes -> k_insert_lane (from
+// the list k_classify builds).
+constexpr uint32_t kThrKeys = leafthr::kKeys;
+__device__ __forceinline__ bool thread_class(uint32_t s, uint32_t uold) {
+  return s >= 1 && s <= kThrKeys && uold > 0;
+}
+__device__ __forceinline__ bool lane_class(uint32_t s, uint32_t uold) {
+  return s > kThrKeys && s <= (uint32_t)kLaneSeg && uold > 0 && uold <= 512;
+}
+
 // Copy of the kept old bytes for the lane-granular insert: the lane's 4*NW
 // bytes are cut into the segments that no edit removes, and each segment is
 // OR-ed into out[] as NW + 1 shifted words (out[] zeroed, one writer per byte,
@@ -665,13 +677,6 @@ __global__ void __launch_bounds__(kT, SEG == 32 ? 4 : 3) k_insert_lane(MergeArgs
 // bytes is left pending for the general merge.
 constexpr int kThrT = 256;
 constexpr int kThrBuckets = 128;  // tile sort buckets: 16-byte chunks of the old leaf
-constexpr uint32_t kThrKeys = leafthr::kKeys;
-
-// The touched leaves k_insert_thread takes (the kernel runs for inserts into
-// byte-code leaves only).
-__device__ __forceinline__ bool thread_class(uint32_t s, uint32_t uold) {
-  return s >= 1 && s <= kThrKeys && uold > 0;
-}
 
 __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
   constexpr uint32_t K = leafthr::kKeys;
@@ -776,8 +781,8 @@ __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
 // Sort the touched leaves into the merge kernels' work lists: inserts of at
 // most kThrKeys keys go to k_insert_thread, which walks the touched leaves
 // itself (no list); other small inserts into leaves of at most 512 used
-// bytes -> k_insert_lane; other small slices
-// into non-empty leaves -> k_merge_small; the rest -> k_merge, one entry per
+// bytes -> k_insert_lane; other small slices into non-empty leaves ->
+// k_merge_small; the rest -> k_merge, one entry per
 // work item (a slice of at most kChunk keys is merged whole by its first item,
 // the others get a zero overflow count here).
 __global__ void __launch_bounds__(kT) k_classify(MergeArgs a) {
@@ -794,8 +799,7 @@ __global__ void __launch_bounds__(kT) k_classify(MergeArgs a) {
       const uint32_t uold = a.T_oldused[t];
       if (small_slice(tb, te, uold)) {
         const bool ins = !a.is_delete && !a.raw;
-        cls = (ins && thread_class(te - tb, uold)) ? 4u
-            : (ins && uold <= 512 && te - tb <= (uint32_t)kLaneSeg) ? 0u : 1u;
+        cls = (ins && thread_class(te - tb, uold)) ? 4u : (ins && lane_class(te - tb, uold)) ? 0u : 1u;
       } else {
         cls = 2;
         fc0 = a.T_first_chunk[t];
@@ -2039,7 +2043,13 @@ void merge_attrs() {
 int front_scratch(cpma* h, uint64_t k, bool tagged, cudaStream_t st) {
   Scratch& s = h->s;
   merge_attrs();
-  if (!h->side) CPMA_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  if (!h->side) {
+    // highest priority: the side kernels' few blocks go ahead of the thread
+    // kernel's many
+    int least = 0, greatest = 0;
+    CPMA_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CPMA_CUDA(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest));
+  }
   if (!h->ev_fork) CPMA_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   if (!h->ev_join) CPMA_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   CPMA_TRY(sort_scratch(h, k, tagged));
@@ -2155,8 +2165,12 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   const size_t msmem = per * mwarps;
   const int mgrid = (int)std::max<uint64_t>(
       1, std::min<uint64_t>((k + kChunk + mwarps - 1) / mwarps, (uint64_t)h->num_sms * 4));
-  k_classify<<<grid_for(h, k), kT, 0, st>>>(ma);
-  h->launches++;
+  // inserts: k_classify runs on the side stream, ahead of the lane kernel
+  // and beside the thread kernel (which walks the touched leaves itself)
+  if (is_delete) {
+    k_classify<<<grid_for(h, k), kT, 0, st>>>(ma);
+    h->launches++;
+  }
   prof_end(h, st);
   prof_begin(h, PH_MERGE, st);
   {
@@ -2165,16 +2179,18 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
     const int sgrid = (int)std::max<uint64_t>(
         1, std::min<uint64_t>((k + swarps - 1) / swarps, (uint64_t)h->num_sms * 8));
     if (!is_delete) {
-      // the thread-granular insert on st and the lane-granular one on the
-      // side stream at the same time: disjoint leaves and outputs (shared
-      // counters by atomics); the lane kernel's few leaves are latency-bound
+      // the thread-granular insert on st and the work lists plus the
+      // lane-granular insert on the side stream at the same time: disjoint
+      // leaves and outputs (shared counters by atomics); the lane kernel's
+      // few leaves are latency-bound
       CPMA_CUDA(cudaEventRecord(h->ev_fork, st));
       CPMA_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
       prof_begin_side(h, PH_MERGE_LANE, h->side);
       MergeArgs ml = ma;
       ml.prof = prof_bytes(h, PH_MERGE_LANE);
+      k_classify<<<grid_for(h, k), kT, 0, h->side>>>(ma);
       k_insert_lane<kLaneSeg><<<sgrid, 256, lane_warp_bytes(kLaneSeg) * 8, h->side>>>(ml);
-      h->launches++;
+      h->launches += 2;
       prof_end_side(h, h->side);
       CPMA_CUDA(cudaEventRecord(h->ev_join, h->side));
       ma.prof = prof_bytes(h, PH_MERGE);
