@@ -35,8 +35,12 @@ constexpr uint32_t kKeys = 4;  // slice keys per leaf on this path
 constexpr uint32_t kGap = 0;    // inside the gap of the code [cs, ce)
 constexpr uint32_t kHead = 1;   // before the head
 constexpr uint32_t kAfter = 2;  // after the last element
-constexpr uint32_t kSkip = 3;   // present already, or a repeat of the slice key before it
+constexpr uint32_t kSkip = 3;   // a repeat of the slice key before it
 constexpr uint32_t kChunk = 4;  // (pass A, step 1) in a code ending in the chunk at cs
+constexpr uint32_t kHit = 5;    // equal to an element: the code [cs, ce) is its own
+
+// kinds an insert leaves alone
+LT_HD bool no_insert(uint32_t kind) { return kind == kSkip || kind == kHit; }
 
 // results
 constexpr uint32_t kUnchanged = 0;  // every key present: nothing written
@@ -186,7 +190,7 @@ LT_HD void place_in_chunk(const uint8_t* leafp, uint32_t uold, uint32_t p0, uint
     const uint32_t ce = p0 + (uint32_t)b + 1u;
     while (ycur <= val) {  // this code's gap (val - acc, val] takes the keys up to val
       const bool rep = q > 0 && pick(y, q - 1) == ycur;
-      const uint32_t kind = (rep || ycur == val) ? kSkip : kGap;
+      const uint32_t kind = rep ? kSkip : ycur == val ? kHit : kGap;
       S.rpos[q * S.rs] = cs | (ce << 12) | (kind << 24);
       S.rval[q * S.rs] = val;
       S.rcode[q * S.rs] = acc;
@@ -242,23 +246,20 @@ LT_HD void seg_bounds(const Scratch& S, uint32_t E, uint32_t uold, uint32_t os0,
   dhi = (int32_t)hi + sa;
 }
 
-// Pass A and the edits of inserting the sorted slice y[0..s) (1 <= s <=
-// kKeys, repeats allowed) into the leaf at leafp (uold >= 8 used bytes, m
-// elements, LB bytes, 16-byte aligned).  Returns one of the results above
-// and writes nothing; kWritten means the leaf is to be rewritten (R.wlo ..
-// R.whi, the R.E edits in S).
-LT_HD uint32_t plan_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
-                           const uint64_t (&y)[kKeys], uint32_t s, const Scratch& S,
-                           Result& R) {
+// Pass A: a record for every slice key (kind, code bytes, values; see
+// Scratch).  Returns kWritten when every key is placed (nothing is written),
+// else kLongCode or kBadCount.  head receives the leaf's first element.
+constexpr uint32_t kPlaced = kWritten;
+LT_HD uint32_t pass_a(const uint8_t* leafp, uint32_t uold, uint32_t m, const uint64_t (&y)[kKeys],
+                      uint32_t s, const Scratch& S, uint64_t& head) {
   uint32_t w[4];
   ld16(leafp, w);
-  const uint64_t head = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
-  // ---- pass A: place every key ----
+  head = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
   uint32_t k = 0;
   while (k < s && pick(y, k) <= head) {
     const uint64_t x = pick(y, k);
     const bool rep = k > 0 && pick(y, k - 1) == x;
-    const uint32_t kind = (rep || x == head) ? kSkip : kHead;
+    const uint32_t kind = rep ? kSkip : x == head ? kHit : kHead;
     S.rpos[k * S.rs] = 0u | (8u << 12) | (kind << 24);
     S.rval[k * S.rs] = head;
     S.rcode[k * S.rs] = 0u;
@@ -323,6 +324,20 @@ LT_HD uint32_t plan_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
     S.rval[k * S.rs] = lastv;
     S.rcode[k * S.rs] = 0u;
   }
+  return kPlaced;
+}
+
+// Pass A and the edits of inserting the sorted slice y[0..s) (1 <= s <=
+// kKeys, repeats allowed) into the leaf at leafp (uold >= 8 used bytes, m
+// elements, LB bytes, 16-byte aligned).  Returns one of the results above
+// and writes nothing; kWritten means the leaf is to be rewritten (R.wlo ..
+// R.whi, the R.E edits in S).
+LT_HD uint32_t plan_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
+                           const uint64_t (&y)[kKeys], uint32_t s, const Scratch& S,
+                           Result& R) {
+  uint64_t head;
+  const uint32_t pa = pass_a(leafp, uold, m, y, s, S, head);
+  if (pa != kPlaced) return pa;
   // ---- edits: new keys grouped by the gap they fall in ----
   uint32_t E = 0, nn = 0, added = 0, mc = 0;
   int32_t tot = 0;
@@ -330,7 +345,7 @@ LT_HD uint32_t plan_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
   for (uint32_t q = 0; q < s;) {
     const uint32_t rp = S.rpos[q * S.rs];
     const uint32_t kind = rp >> 24;
-    if (kind == kSkip) { q++; continue; }
+    if (no_insert(kind)) { q++; continue; }
     // keys q..q1 (kSkip ones among them are repeats) share this gap
     const uint32_t os = rp & 0xFFFu, oe = (rp >> 12) & 0xFFFu;
     const uint64_t rv = S.rval[q * S.rs];
@@ -346,7 +361,7 @@ LT_HD uint32_t plan_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
     for (; q1 < s; q1++) {
       const uint32_t rp1 = S.rpos[q1 * S.rs];
       if ((rp1 & 0xFFFu) != os) break;
-      if ((rp1 >> 24) == kSkip) continue;
+      if (no_insert(rp1 >> 24)) continue;
       const uint64_t x = pick(y, q1);
       cl = leb_bytes(x - prev);
       mc = mc > cl ? mc : cl;
@@ -432,13 +447,166 @@ LT_HD void write_edits(uint8_t* leafp, const uint64_t (&y)[kKeys], const Scratch
       p += leb_write(p, prev - rv);
     }
     for (uint32_t q = q0 + 1; q < q1; q++) {
-      if ((S.rpos[q * S.rs] >> 24) == kSkip) continue;
+      if (no_insert(S.rpos[q * S.rs] >> 24)) continue;
       const uint64_t x = pick(y, q);
       p += leb_write(p, x - prev);
       prev = x;
     }
     if (kind != kAfter) leb_write(p, rv - prev);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Delete.  Keys equal to elements (kHit) whose codes are adjacent form a run;
+// a run's edit replaces the codes of its elements and of the element after
+// it (the successor) by one code: successor minus the element before the run
+// (Sec. 3: the neighbours of a removed key become neighbours), or, for a run
+// that starts at the head, the successor as the new 8-byte head; a run that
+// reaches the last element just goes.  Such an edit never grows the leaf
+// (the merged delta needs no more bytes than the two it replaces), so the
+// rewrite runs forward.
+// ---------------------------------------------------------------------------
+
+// Unsigned LEB128 code at p (at most 10 bytes): value, and its length in len.
+LT_HD uint64_t leb_read(const uint8_t* p, uint32_t& len) {
+  uint64_t v = 0;
+  uint32_t n = 0;
+  for (;;) {
+    const uint32_t c = p[n];
+    v |= (uint64_t)(c & 0x7Fu) << (7u * n);
+    n++;
+    if (!(c & 0x80u) || n == 10u) break;
+  }
+  len = n;
+  return v;
+}
+
+// Pass A and the edits of deleting the sorted slice y[0..s) (1 <= s <=
+// kKeys, repeats allowed) from the leaf (as plan_leaf).  R.added: bit q =
+// slice key q was removed; R.wlo .. R.whi covers the old used bytes from the
+// first edit on, so the bytes freed at the end are cleared.
+LT_HD uint32_t plan_delete(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
+                           const uint64_t (&y)[kKeys], uint32_t s, const Scratch& S,
+                           Result& R) {
+  uint64_t head;
+  const uint32_t pa = pass_a(leafp, uold, m, y, s, S, head);
+  if (pa != kPlaced) return pa;
+  uint32_t E = 0, nn = 0, removed = 0;
+  int32_t tot = 0;
+  uint64_t newhead = head;
+  for (uint32_t q = 0; q < s;) {
+    const uint32_t rp = S.rpos[q * S.rs];
+    if ((rp >> 24) != kHit) { q++; continue; }
+    const uint32_t os = rp & 0xFFFu;
+    uint32_t ce = (rp >> 12) & 0xFFFu;
+    const uint64_t pred = S.rval[q * S.rs] - S.rcode[q * S.rs];  // unused when os == 0
+    uint64_t lastv = S.rval[q * S.rs];
+    removed |= 1u << q;
+    nn++;
+    uint32_t q1 = q + 1;
+    for (; q1 < s; q1++) {
+      const uint32_t r1 = S.rpos[q1 * S.rs], k1 = r1 >> 24;
+      if (k1 == kSkip) continue;          // a repeat
+      if ((r1 & 0xFFFu) != ce) break;     // beyond the successor's code
+      if (k1 != kHit) continue;           // absent, in the gap before the successor
+      ce = (r1 >> 12) & 0xFFFu;           // the successor itself goes: the run grows
+      lastv = S.rval[q1 * S.rs];
+      removed |= 1u << q1;
+      nn++;
+    }
+    uint32_t oe = uold, nl = 0;
+    uint64_t nv = 0;
+    if (ce < uold) {  // the successor's code: right after the run
+      uint32_t dl;
+      const uint64_t succ = lastv + leb_read(leafp + ce, dl);
+      oe = ce + dl;
+      if (os == 0) {
+        nl = 8u;
+        nv = succ;
+        newhead = succ;
+      } else {
+        nv = succ - pred;
+        nl = leb_bytes(nv);
+      }
+    }
+    tot += (int32_t)nl - (int32_t)(oe - os);
+    S.epos[E * S.rs] = os | (oe << 12) | ((os == 0 ? kHead : kGap) << 24);
+    S.esa[E * S.rs] = tot;
+    S.ekey[E * S.rs] = q | (q1 << 8) | (nl << 16);
+    S.rval[q * S.rs] = nv;  // what the edit writes (the record is used up)
+    E++;
+    q = q1;
+  }
+  R.added = removed;
+  R.maxcode = 0;
+  R.newc = m - nn;
+  R.nb = (uint32_t)((int32_t)uold + tot);
+  R.newhead = R.newc ? newhead : ~0ull;
+  R.E = E;
+  if (nn == 0) return kUnchanged;
+  R.wlo = (S.epos[0] & 0xFFFu) & ~15u;
+  R.whi = (uold + 15u) & ~15u;
+  return kWritten;
+}
+
+// Pass B of a delete by one thread: the chunks R.wlo .. R.whi from the front,
+// each gathered from the segments that land in it (every shift is <= 0, so a
+// chunk's sources lie at or above it: not yet written).
+LT_HD void rewrite_forward(uint8_t* leafp, uint32_t LB, uint32_t uold, const Scratch& S,
+                           const Result& R) {
+  const uint32_t E = R.E;
+  const uint32_t os0 = S.epos[0] & 0xFFFu;
+  int cur = -1;
+  for (int32_t o = (int32_t)R.wlo; o < (int32_t)R.whi; o += 16) {
+    for (;;) {  // the lowest segment not wholly below chunk o
+      int32_t dlo, dhi, sa;
+      seg_bounds(S, E, uold, os0, cur, dlo, dhi, sa);
+      if (cur + 1 >= (int)E || dhi > o) break;
+      cur++;
+    }
+    uint32_t r[4] = {0u, 0u, 0u, 0u};
+    for (int e = cur; e < (int)E; e++) {
+      int32_t dlo, dhi, sa;
+      seg_bounds(S, E, uold, os0, e, dlo, dhi, sa);
+      if (dlo >= o + 16) break;  // wholly above this chunk: so are the later ones
+      if (dhi > dlo && dhi > o) {
+        const uint32_t a = (uint32_t)((dlo > o ? dlo : o) - o);
+        const uint32_t b = (uint32_t)((dhi < o + 16 ? dhi : o + 16) - o);
+        gather(leafp, LB, o - sa, a, b, r);
+      }
+    }
+    st16(leafp + o, r);
+  }
+}
+
+// The delete edits' own bytes: a new head, or the merged code.
+LT_HD void write_delete_edits(uint8_t* leafp, const Scratch& S, const Result& R) {
+  for (uint32_t e = 0; e < R.E; e++) {
+    const uint32_t ep = S.epos[e * S.rs], ek = S.ekey[e * S.rs];
+    const uint32_t nl = ek >> 16;
+    if (!nl) continue;
+    const uint32_t q0 = ek & 0xFFu, os = ep & 0xFFFu;
+    const int32_t sb = e ? S.esa[(e - 1) * S.rs] : 0;
+    uint8_t* p = leafp + (int32_t)os + sb;
+    const uint64_t nv = S.rval[q0 * S.rs];
+    if ((ep >> 24) == kHead) {
+#pragma unroll
+      for (int i = 0; i < 8; i++) p[i] = (uint8_t)(nv >> (8 * i));
+    } else {
+      leb_write(p, nv);
+    }
+  }
+}
+
+LT_HD uint32_t delete_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
+                           const uint64_t (&y)[kKeys], uint32_t s, const Scratch& S,
+                           Result& R) {
+  const uint32_t res = plan_delete(leafp, LB, uold, m, y, s, S, R);
+  if (res == kWritten) {
+    rewrite_forward(leafp, LB, uold, S, R);
+    write_delete_edits(leafp, S, R);
+  }
+  return res;
 }
 
 // All of it by one thread: returns one of the results above; the leaf is

@@ -678,6 +678,9 @@ __global__ void __launch_bounds__(kT, SEG == 32 ? 4 : 3) k_insert_lane(MergeArgs
 constexpr int kThrT = 256;
 constexpr int kThrBuckets = 128;  // tile sort buckets: 16-byte chunks of the old leaf
 
+// DEL: the same for deletes of at most kThrKeys keys from a byte-code leaf
+// (plan_delete, forward rewrite; never over LB bytes).
+template <bool DEL>
 __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
   constexpr uint32_t K = leafthr::kKeys;
   __shared__ uint32_t s_rpos[K * kThrT], s_rcode[K * kThrT];
@@ -738,7 +741,8 @@ __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
       for (uint32_t q = 0; q < K; q++) y[q] = q < s ? a.u[tb + q] : 0ull;
       leafthr::Result R;
       R.E = 0;
-      const uint32_t res = leafthr::plan_leaf(leafp, a.LB, uold, m, y, s, S, R);
+      const uint32_t res = DEL ? leafthr::plan_delete(leafp, a.LB, uold, m, y, s, S, R)
+                               : leafthr::plan_leaf(leafp, a.LB, uold, m, y, s, S, R);
       if (res == leafthr::kLongCode) {
         a.T_state[t] = kFallback;
         a.list_v1[atomicAdd(&a.st->n_v1, 1ull)] = t;
@@ -756,8 +760,14 @@ __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
           a.T_newbytes[t] = R.nb;
           c0 = R.newc;
         } else {
-          leafthr::rewrite_leaf(leafp, a.LB, uold, S, R);
-          leafthr::write_edits(leafp, y, S, R);
+          if (DEL) {
+            leafthr::rewrite_forward(leafp, a.LB, uold, S, R);
+            leafthr::write_delete_edits(leafp, S, R);
+            if (R.newc == 0) atomicAdd(&a.st->nempty, 1ull);
+          } else {
+            leafthr::rewrite_leaf(leafp, a.LB, uold, S, R);
+            leafthr::write_edits(leafp, y, S, R);
+          }
           nbytes += R.whi - R.wlo;
           a.used[j] = R.nb;
           a.cnt[j] = R.newc;
@@ -799,7 +809,8 @@ __global__ void __launch_bounds__(kT) k_classify(MergeArgs a) {
       const uint32_t uold = a.T_oldused[t];
       if (small_slice(tb, te, uold)) {
         const bool ins = !a.is_delete && !a.raw;
-        cls = (ins && thread_class(te - tb, uold)) ? 4u : (ins && lane_class(te - tb, uold)) ? 0u : 1u;
+        cls = (!a.raw && thread_class(te - tb, uold)) ? 4u
+            : (ins && lane_class(te - tb, uold)) ? 0u : 1u;
       } else {
         cls = 2;
         fc0 = a.T_first_chunk[t];
@@ -2197,11 +2208,19 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
       if (!ma.raw) {
         const int tgrid = (int)std::max<uint64_t>(
             1, std::min<uint64_t>((k + kThrT - 1) / kThrT, (uint64_t)h->num_sms * 16));
-        k_insert_thread<<<tgrid, kThrT, 0, st>>>(ma);
+        k_insert_thread<false><<<tgrid, kThrT, 0, st>>>(ma);
         h->launches++;
       }
       ma.prof = nullptr;
       CPMA_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
+    }
+    if (is_delete && !ma.raw) {
+      ma.prof = prof_bytes(h, PH_MERGE);
+      const int tgrid = (int)std::max<uint64_t>(
+          1, std::min<uint64_t>((k + kThrT - 1) / kThrT, (uint64_t)h->num_sms * 16));
+      k_insert_thread<true><<<tgrid, kThrT, 0, st>>>(ma);
+      h->launches++;
+      ma.prof = nullptr;
     }
     prof_end(h, st);
     prof_begin(h, PH_MERGE2, st);

@@ -1,5 +1,5 @@
-// Host build of the thread-granular leaf insert (leaf_thread.cuh) for the
-// CPU tests.  The leaf is copied next to an inaccessible page (before it or
+// Host build of the thread-granular leaf insert and delete (leaf_thread.cuh)
+// for the CPU tests.  The leaf is copied next to an inaccessible page (before it or
 // after it), so any access outside the leaf's LB bytes faults the test.
 #include <sys/mman.h>
 #include <unistd.h>
@@ -7,7 +7,8 @@
 #include "../paper_2305_05055_gb300/csrc/leaf_thread.cuh"
 
 extern "C" int lt_insert(uint8_t* leaf, uint32_t LB, uint32_t uold, uint32_t m,
-                         const uint64_t* keys, uint32_t s, uint32_t* out, int guard_after) {
+                         const uint64_t* keys, uint32_t s, uint32_t* out, int guard_after,
+                         int del) {
   const size_t pg = (size_t)sysconf(_SC_PAGESIZE);
   const size_t span = ((LB + pg - 1) / pg + 2) * pg;
   uint8_t* base = (uint8_t*)mmap(nullptr, span, PROT_READ | PROT_WRITE,
@@ -30,7 +31,8 @@ extern "C" int lt_insert(uint8_t* leaf, uint32_t LB, uint32_t uold, uint32_t m,
   int32_t esa[leafthr::kKeys];
   const leafthr::Scratch S{rpos, rval, rcode, epos, esa, ekey, 1};
   leafthr::Result R{};
-  const uint32_t st = leafthr::insert_leaf(lp, LB, uold, m, y, s, S, R);
+  const uint32_t st = del ? leafthr::delete_leaf(lp, LB, uold, m, y, s, S, R)
+                          : leafthr::insert_leaf(lp, LB, uold, m, y, s, S, R);
   memcpy(leaf, lp, LB);
   munmap(base, span);
   out[0] = R.nb;

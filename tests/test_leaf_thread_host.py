@@ -1,10 +1,11 @@
-"""Host build of the thread-granular leaf insert (the code the GPU kernel
-k_insert_thread runs per leaf) against the oracle's leaf encoder: inserting a
-slice of at most four keys into an encoded leaf must give exactly the bytes
-of encoding the union from scratch (Sec. 5 leaf format), the right count,
-head and added-key mask, and must leave the leaf untouched when the result
-does not fit or a code is longer than 4 bytes.  Every access outside the
-leaf's LB bytes faults (guard pages)."""
+"""Host build of the thread-granular leaf insert and delete (the code the
+GPU kernels k_insert_thread and k_delete_thread run per leaf) against the
+oracle's leaf encoder: inserting (deleting) a slice of at most four keys
+must give exactly the bytes of encoding the union (difference) from scratch
+(Sec. 5 leaf format, zero bytes after the used ones), the right count, head
+and changed-key mask, and must leave the leaf untouched when the result does
+not fit or a code is longer than 4 bytes.  Every access outside the leaf's
+LB bytes faults (guard pages)."""
 import ctypes as C
 import os
 import random
@@ -39,14 +40,14 @@ def encode(keys, LB):
     return bytes(buf[:used])
 
 
-def run(lib, keys, sl, LB, guard_after):
+def run(lib, keys, sl, LB, guard_after, delete=False):
     enc = encode(keys, LB)
     leaf = bytearray(LB)
     leaf[:len(enc)] = enc
     buf = (C.c_uint8 * LB).from_buffer(leaf)
     ks = (C.c_uint64 * 4)(*sl)
     out = (C.c_uint32 * 8)()
-    st = lib.lt_insert(buf, LB, len(enc), len(keys), ks, len(sl), out, guard_after)
+    st = lib.lt_insert(buf, LB, len(enc), len(keys), ks, len(sl), out, guard_after, int(delete))
     return st, bytes(leaf), list(out), enc
 
 
@@ -152,5 +153,66 @@ def test_leaf_thread_cases(lt):
     leaf[:len(enc)] = enc
     out = (C.c_uint32 * 8)()
     st = lt.lt_insert((C.c_uint8 * 256).from_buffer(leaf), 256, len(enc), 4,
-                      (C.c_uint64 * 4)(8, 0, 0, 0), 1, out, 0)
+                      (C.c_uint64 * 4)(8, 0, 0, 0), 1, out, 0, 0)
     assert st == BAD_COUNT
+
+
+def check_delete(lib, keys, sl, LB, guard_after):
+    st, leaf, out, enc = run(lib, keys, sl, LB, guard_after, delete=True)
+    old = set(keys)
+    if any(oracle.leb_len(b - a) > 4 for a, b in zip(keys, keys[1:])):
+        assert st == LONG_CODE and leaf[:len(enc)] == enc
+        return st
+    new = sorted(old - set(sl))
+    removed = 0
+    for q, x in enumerate(sl):
+        if x in old and (q == 0 or sl[q - 1] != x):
+            removed |= 1 << q
+    if removed == 0:
+        assert st == UNCHANGED and leaf[:len(enc)] == enc
+        return st
+    assert st == WRITTEN
+    nb = oracle.leaf_bytes(np.array(new, dtype=np.uint64)) if new else 0
+    assert out[0] == nb and out[1] == len(new) and out[2] == removed
+    assert out[5] | (out[6] << 32) == (new[0] if new else M64)
+    assert leaf[:nb] == (encode(new, LB) if new else b"") and not any(leaf[nb:])
+    return st
+
+
+def test_leaf_thread_delete_random(lt):
+    rng = random.Random(20240601)
+    seen = set()
+    for it in range(4000):
+        LB = rng.choice([256, 512, 1024, 2048])
+        keys = leaf_keys(rng, LB)
+        if not keys:
+            continue
+        r = rng.random()
+        if r < 0.5:     # present keys, often neighbours, with absent ones between
+            i = rng.randrange(len(keys))
+            sl = [keys[min(len(keys) - 1, i + d)] for d in range(rng.randint(1, 4))]
+            for q in range(len(sl) - 1):
+                if rng.random() < 0.3 and sl[q + 1] - sl[q] > 1:
+                    sl.append(rng.randrange(sl[q] + 1, sl[q + 1]))
+        elif r < 0.6:   # the head and the last elements
+            sl = keys[:rng.randint(1, 4)] if rng.random() < 0.5 else keys[-rng.randint(1, 4):]
+        else:
+            sl = slice_keys(rng, keys)
+        if rng.random() < 0.2:
+            sl = sl + [sl[-1]]
+        seen.add(check_delete(lt, keys, sorted(sl)[:4], LB, it & 1))
+    assert seen == {UNCHANGED, WRITTEN, LONG_CODE}
+
+
+def test_leaf_thread_delete_cases(lt):
+    assert check_delete(lt, [1000], [1000], 256, 0) == WRITTEN               # the only element
+    assert check_delete(lt, [5, 6, 7], [5, 6, 7], 256, 1) == WRITTEN         # all of them
+    assert check_delete(lt, [5, 6, 7], [5, 5], 256, 0) == WRITTEN            # the head, repeated
+    assert check_delete(lt, [5, 6, 7], [7], 256, 1) == WRITTEN               # the last one
+    assert check_delete(lt, [0, 127, 128, 300], [127], 256, 0) == WRITTEN    # merged code keeps size
+    assert check_delete(lt, [0, 127, 128, 300], [1, 129], 256, 1) == UNCHANGED
+    assert check_delete(lt, list(range(0, 2 * 247, 2)), [2, 4, 6, 8], 256, 0) == WRITTEN
+    # absent keys between deleted neighbours: still one run
+    assert check_delete(lt, [10, 20, 30, 40], [20, 25, 30], 256, 1) == WRITTEN
+    assert check_delete(lt, [10, 20, 30, 40], [10, 15, 20, 25], 256, 0) == WRITTEN
+    assert check_delete(lt, [10, 20, 30, 40], [30, 35, 40, 45], 256, 1) == WRITTEN
