@@ -14,11 +14,11 @@
 // the first scratch buffer.  No host round trip.  Batches of at most one tile
 // are sorted by a single block.
 //
-// Batches of up to 1.5M keys go most significant digit first instead: one
+// Batches of up to 1.25M keys go most significant digit first instead: one
 // scatter pass by the highest varying digit (same tile ranking and
 // look-back), then each of its 256 buckets (k / 256 keys on average) is sorted
 // by the lower digits in the shared memory of one block.  Three reads and two
-// writes of the batch instead of six and five.  A bucket of more than 8192
+// writes of the batch instead of six and five.  A bucket of more than 6144
 // keys (heavy repeats) sets a flag, and the digit passes, launched gated on
 // that flag, sort the input again from scratch.
 #include <algorithm>
@@ -37,12 +37,12 @@ constexpr int kItems = 16;
 constexpr int kTile = kT * kItems;  // 4096 keys
 // Bucket sort: one block of kBT threads, kBItems keys each, sorts a bucket of
 // up to kBTile keys (spread evenly over its warps).
-constexpr int kBT = 1024;
-constexpr int kBItems = 8;
-constexpr int kBTile = kBT * kBItems;  // 8192 keys
+constexpr int kBT = 512;
+constexpr int kBItems = 12;
+constexpr int kBTile = kBT * kBItems;  // 6144 keys
 // Batches of more than one tile and at most this many keys take the
 // top-digit buckets (k / 256 keys per bucket on average, far below kBTile).
-constexpr uint64_t kBucketMax = 1536ull * 1024;
+constexpr uint64_t kBucketMax = 1280ull * 1024;
 
 template <bool VALS, int KT = kT, int ITEMS = kItems>
 struct TileSmemT {
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kT, 3) k_onesweep(const uint64_t* __restrict__
 // positions of A.  A bucket of more than kBTile keys sets the fallback flag
 // instead (the digit passes then sort the whole batch again).
 template <bool VALS>
-__global__ void __launch_bounds__(kBT) k_bucket_sort(const uint64_t* __restrict__ B,
+__global__ void __launch_bounds__(kBT, 2) k_bucket_sort(const uint64_t* __restrict__ B,
                                                      const uint32_t* __restrict__ VB,
                                                      uint64_t* __restrict__ A,
                                                      uint32_t* __restrict__ VA, SortCtl* ctl) {
