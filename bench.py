@@ -544,9 +544,12 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
     upd = ["sort", "route", "merge", "merge_lane", "merge_other", "count", "redistribute",
            "finish"]
     dom = max(upd, key=lambda p: prof[p]["ms"])
+    droof = roof(prof, dom)
+    if dom == "merge":  # the delete form of the thread-granular kernel: no capture of its own
+        droof.update(kernel="k_insert_thread<true> (delete)", traffic=None)
     out["delete"] = {"value": removed / (tot / 1e3), "unit": "keys/s",
                      "batches": min(5, len(ins_batches)), "batch": int(a.batch),
-                     "roofline": roof(prof, dom),
+                     "roofline": droof,
                      "phases_ms": {p: prof[p]["ms"] for p in upd}}
     if not a.no_sweep:
         out["sweep"] = sweep(a, g, dev, T, timed)
