@@ -398,6 +398,88 @@ __device__ __forceinline__ void lane_codes(const uint32_t (&w)[NW], int b_lo, in
 }
 
 // ---------------------------------------------------------------------------
+// Thread-per-leaf sum of byte-code leaves (codec 0): the sum (mod 2^64) of
+// the elements of the leaf at leafp with u >= 8 used bytes.  One thread walks
+// the leaf 16 bytes at a time keeping the running element value and the
+// running sum: each byte adds its payload times 128^(bytes before it in its
+// code) to the open code, a terminator adds the code to the value and the
+// value to the sum.  Bytes after u are read as zero: each of them acts as a
+// terminator adding the last value again, which is taken off at the end.  A
+// code of more than 4 bytes overflows the 32-bit code accumulator; such a
+// leaf is summed again exactly, byte by byte.
+template <bool FIRST>
+__device__ __forceinline__ void leaf_sum_chunk(const uint32_t (&w)[4], uint64_t& val, uint64_t& s,
+                                               uint32_t& acc, uint32_t& pw, uint32_t& pwmax) {
+#pragma unroll
+  for (int b = FIRST ? 8 : 0; b < 16; b++) {
+    const uint32_t wb = w[b >> 2];
+    acc += (__byte_perm(wb, 0u, 0x4440u + (uint32_t)(b & 3)) & 0x7Fu) * pw;
+    const bool term = (wb & (0x80u << (8 * (b & 3)))) == 0u;
+    pwmax = pwmax > pw ? pwmax : pw;
+    val += term ? (uint64_t)acc : 0ull;
+    s += term ? val : 0ull;
+    acc = term ? 0u : acc;
+    pw = term ? 1u : pw << 7;
+  }
+}
+
+__device__ __forceinline__ uint64_t thread_leaf_sum(const uint8_t* __restrict__ leafp, uint32_t u) {
+  uint4 v = *reinterpret_cast<const uint4*>(leafp);
+  uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  uint64_t val = (uint64_t)w[0] | ((uint64_t)w[1] << 32), s = val;
+  uint32_t acc = 0, pw = 1, pwmax = 0;
+  for (uint32_t p0 = 0; p0 < u; p0 += 16) {
+    if (p0) {
+      v = *reinterpret_cast<const uint4*>(leafp + p0);
+      w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    }
+    if (p0 + 16u > u) {  // bytes past the used ones read as zero
+      const uint32_t keep = (1u << (u - p0)) - 1u;
+#pragma unroll
+      for (int i = 0; i < 4; i++) w[i] &= bytemask4((keep >> (4 * i)) & 0xFu);
+    }
+    if (p0) leaf_sum_chunk<false>(w, val, s, acc, pw, pwmax);
+    else leaf_sum_chunk<true>(w, val, s, acc, pw, pwmax);
+  }
+  s -= (uint64_t)(((u + 15u) & ~15u) - u) * val;
+  if (pwmax >= (1u << 28)) {  // a long code: exact 64-bit decode
+    val = *reinterpret_cast<const uint64_t*>(leafp);
+    s = val;
+    uint64_t a64 = 0;
+    uint32_t sh = 0;
+    for (uint32_t p = 8; p < u; p++) {
+      const uint32_t c = leafp[p];
+      if (sh < 64) a64 |= (uint64_t)(c & 0x7Fu) << sh;
+      if (c & 0x80u) {
+        sh += 7;
+      } else {
+        val += a64;
+        s += val;
+        a64 = 0;
+        sh = 0;
+      }
+    }
+  }
+  return s;
+}
+
+// Sum (mod 2^64), count and used bytes of the byte-code leaves [j0, j1), one
+// leaf per lane at a time, added to the calling lane's partials.
+__device__ __forceinline__ void thread_span_sum(const uint8_t* __restrict__ data,
+                                                const uint32_t* __restrict__ used,
+                                                const uint32_t* __restrict__ cnt, uint32_t LB,
+                                                uint64_t j0, uint64_t j1, uint64_t& s,
+                                                uint64_t& c, unsigned long long& nbytes) {
+  for (uint64_t j = j0 + lane_id(); j < j1; j += 32) {
+    const uint32_t u = min(used[j], LB);
+    if (u == 0) continue;
+    s += thread_leaf_sum(data + j * LB, u);
+    c += cnt[j];
+    nbytes += u;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Sum (mod 2^64) and count of every element of the leaves [j0, j1), added to
 // the calling lane's partials (the caller reduces them over the warp).
 //

@@ -361,8 +361,11 @@ __global__ void __launch_bounds__(kT) k_range(RangeArgs a) {
       // leaves strictly inside the range: no filter, chunked span sum
       const uint64_t stop = min(g1, qend - 1);  // exclusive, global item index
       uint64_t cc = 0;
-      warp_span_sum(a.data, a.used, a.cnt, a.LB, fl + li, fl + (stop - qoff), s, cc, nbytes,
-                    a.raw);
+      if (a.raw)
+        warp_span_sum(a.data, a.used, a.cnt, a.LB, fl + li, fl + (stop - qoff), s, cc, nbytes,
+                      a.raw);
+      else  // byte codes: one leaf per lane
+        thread_span_sum(a.data, a.used, a.cnt, a.LB, fl + li, fl + (stop - qoff), s, cc, nbytes);
       if (lane == 0) c += warp_sum(cc); else warp_sum(cc);
       g = stop;
       continue;
@@ -402,7 +405,8 @@ __global__ void __launch_bounds__(kT) k_sum(const uint8_t* __restrict__ data,
   const uint64_t j0 = L * gw / nw, j1 = L * (gw + 1) / nw;
   uint64_t s = 0, c = 0;
   ull nbytes = 0;
-  warp_span_sum(data, used, cnt, LB, j0, j1, s, c, nbytes, raw);
+  if (raw) warp_span_sum(data, used, cnt, LB, j0, j1, s, c, nbytes, raw);
+  else thread_span_sum(data, used, cnt, LB, j0, j1, s, c, nbytes);
   s = warp_sum(s);
   c = warp_sum(c);
   nbytes = warp_sum(nbytes);
