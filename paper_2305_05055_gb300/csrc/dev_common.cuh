@@ -463,6 +463,71 @@ __device__ __forceinline__ uint64_t thread_leaf_sum(const uint8_t* __restrict__ 
   return s;
 }
 
+// Is x an element of the byte-code leaf at leafp (u used bytes)?  One
+// thread decodes the leaf from its head, 16 bytes at a time, until the
+// running value passes x (same per-byte arithmetic as thread_leaf_sum; zero
+// bytes after u repeat the last value, which is an element).  A leaf with a
+// code over 4 bytes is decoded again exactly, byte by byte.
+template <bool FIRST>
+__device__ __forceinline__ void leaf_has_chunk(const uint32_t (&w)[4], uint64_t x, uint64_t& val,
+                                               bool& found, uint32_t& acc, uint32_t& pw,
+                                               uint32_t& pwmax) {
+#pragma unroll
+  for (int b = FIRST ? 8 : 0; b < 16; b++) {
+    const uint32_t wb = w[b >> 2];
+    acc += (__byte_perm(wb, 0u, 0x4440u + (uint32_t)(b & 3)) & 0x7Fu) * pw;
+    const bool term = (wb & (0x80u << (8 * (b & 3)))) == 0u;
+    pwmax = pwmax > pw ? pwmax : pw;
+    val += term ? (uint64_t)acc : 0ull;
+    found |= term && val == x;
+    acc = term ? 0u : acc;
+    pw = term ? 1u : pw << 7;
+  }
+}
+
+__device__ __forceinline__ bool thread_leaf_has(const uint8_t* __restrict__ leafp, uint32_t u,
+                                                uint64_t x) {
+  if (u == 0) return false;
+  uint4 v = *reinterpret_cast<const uint4*>(leafp);
+  uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  uint64_t val = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+  if (x <= val) return x == val;
+  bool found = false;
+  uint32_t acc = 0, pw = 1, pwmax = 0;
+  for (uint32_t p0 = 0; p0 < u && val < x; p0 += 16) {
+    if (p0) {
+      v = *reinterpret_cast<const uint4*>(leafp + p0);
+      w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    }
+    if (p0 + 16u > u) {
+      const uint32_t keep = (1u << (u - p0)) - 1u;
+#pragma unroll
+      for (int i = 0; i < 4; i++) w[i] &= bytemask4((keep >> (4 * i)) & 0xFu);
+    }
+    if (p0) leaf_has_chunk<false>(w, x, val, found, acc, pw, pwmax);
+    else leaf_has_chunk<true>(w, x, val, found, acc, pw, pwmax);
+  }
+  if (pwmax >= (1u << 28)) {  // a long code: exact 64-bit decode
+    val = *reinterpret_cast<const uint64_t*>(leafp);
+    found = false;
+    uint64_t a64 = 0;
+    uint32_t sh = 0;
+    for (uint32_t p = 8; p < u && val < x; p++) {
+      const uint32_t c = leafp[p];
+      if (sh < 64) a64 |= (uint64_t)(c & 0x7Fu) << sh;
+      if (c & 0x80u) {
+        sh += 7;
+      } else {
+        val += a64;
+        found |= val == x;
+        a64 = 0;
+        sh = 0;
+      }
+    }
+  }
+  return found;
+}
+
 // Sum (mod 2^64), count and used bytes of the byte-code leaves [j0, j1), one
 // leaf per lane at a time, added to the calling lane's partials.
 __device__ __forceinline__ void thread_span_sum(const uint8_t* __restrict__ data,

@@ -52,6 +52,19 @@ __global__ void __launch_bounds__(kT) k_has(const uint64_t* __restrict__ keys, u
   ull nbytes = 0;
   uint64_t r0, r1;
   warp_share(q, gw, nw, r0, r1);
+  if (!raw) {
+    // byte codes: one key per thread, its leaf decoded up to the key
+    for (uint64_t qi = r0 + lane; qi < r1; qi += 32) {
+      const uint64_t x = keys[qi];
+      const uint64_t j = route_leaf(heads, L, x);
+      const uint32_t u = min(used[j], LB);
+      nbytes += u + 9;
+      out[qi] = thread_leaf_has(data + j * LB, u, x) ? 1u : 0u;
+    }
+    nbytes = warp_sum(nbytes);
+    if (prof && lane == 0 && nbytes) atomicAdd(prof, nbytes);
+    return;
+  }
   for (uint64_t base = r0; base < r1; base += 32) {
     const uint64_t qi = base + lane;
     uint64_t xi = 0, ji = 0;
