@@ -423,23 +423,37 @@ __device__ __forceinline__ void leaf_sum_chunk(const uint32_t (&w)[4], uint64_t&
   }
 }
 
+// Bytes of w past u - p0 cleared (the leaf's zero padding, read as such).
+__device__ __forceinline__ void mask_past(uint32_t (&w)[4], uint32_t p0, uint32_t u) {
+  if (p0 + 16u > u) {
+    const uint32_t keep = u > p0 ? (1u << (u - p0)) - 1u : 0u;
+#pragma unroll
+    for (int i = 0; i < 4; i++) w[i] &= bytemask4((keep >> (4 * i)) & 0xFu);
+  }
+}
+
 __device__ __forceinline__ uint64_t thread_leaf_sum(const uint8_t* __restrict__ leafp, uint32_t u) {
+  // 32 bytes (one sector) per step: both halves are loaded before either is
+  // decoded, so each sector is requested once
   uint4 v = *reinterpret_cast<const uint4*>(leafp);
+  uint4 v2 = u > 16u ? *reinterpret_cast<const uint4*>(leafp + 16) : make_uint4(0u, 0u, 0u, 0u);
   uint32_t w[4] = {v.x, v.y, v.z, v.w};
   uint64_t val = (uint64_t)w[0] | ((uint64_t)w[1] << 32), s = val;
   uint32_t acc = 0, pw = 1, pwmax = 0;
-  for (uint32_t p0 = 0; p0 < u; p0 += 16) {
+  for (uint32_t p0 = 0; p0 < u; p0 += 32) {
     if (p0) {
       v = *reinterpret_cast<const uint4*>(leafp + p0);
+      v2 = p0 + 16u < u ? *reinterpret_cast<const uint4*>(leafp + p0 + 16) : make_uint4(0u, 0u, 0u, 0u);
       w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
     }
-    if (p0 + 16u > u) {  // bytes past the used ones read as zero
-      const uint32_t keep = (1u << (u - p0)) - 1u;
-#pragma unroll
-      for (int i = 0; i < 4; i++) w[i] &= bytemask4((keep >> (4 * i)) & 0xFu);
-    }
+    mask_past(w, p0, u);
     if (p0) leaf_sum_chunk<false>(w, val, s, acc, pw, pwmax);
     else leaf_sum_chunk<true>(w, val, s, acc, pw, pwmax);
+    if (p0 + 16u < u) {
+      uint32_t w2[4] = {v2.x, v2.y, v2.z, v2.w};
+      mask_past(w2, p0 + 16u, u);
+      leaf_sum_chunk<false>(w2, val, s, acc, pw, pwmax);
+    }
   }
   s -= (uint64_t)(((u + 15u) & ~15u) - u) * val;
   if (pwmax >= (1u << 28)) {  // a long code: exact 64-bit decode
