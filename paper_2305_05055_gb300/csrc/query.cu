@@ -298,6 +298,81 @@ __device__ __forceinline__ void op_atomic(uint64_t* p, uint64_t v) {
 
 // Same load-balanced (query, leaf) walk as k_range; every covered leaf is
 // decoded and its keys filtered by range and mask.
+// Thread-per-leaf reduction of a byte-code leaf: every element v with
+// (v & mask) == value is reduced into (r, c), the running value kept as in
+// thread_leaf_sum; bytes past u are no terminators here (a repeated value
+// would count twice), and a leaf with a code over 4 bytes is reduced again
+// exactly.
+template <int OP, bool FIRST>
+__device__ __forceinline__ void leaf_reduce_chunk(const uint32_t (&w)[4], uint32_t valid,
+                                                  uint64_t mask, uint64_t value, uint64_t& val,
+                                                  uint64_t& r, uint64_t& c, uint32_t& acc,
+                                                  uint32_t& pw, uint32_t& pwmax) {
+#pragma unroll
+  for (int b = FIRST ? 8 : 0; b < 16; b++) {
+    const uint32_t wb = w[b >> 2];
+    const bool in = (valid >> b) & 1u;  // bytes past u: neither codes nor terminators
+    acc += (__byte_perm(wb, 0u, 0x4440u + (uint32_t)(b & 3)) & 0x7Fu) * pw;
+    const bool term = in && (wb & (0x80u << (8 * (b & 3)))) == 0u;
+    pwmax = (in && pw > pwmax) ? pw : pwmax;
+    val += term ? (uint64_t)acc : 0ull;
+    const bool hit = term && (val & mask) == value;
+    r = hit ? op_apply<OP>(r, val) : r;
+    c += hit ? 1u : 0u;
+    acc = (term || !in) ? 0u : acc;
+    pw = (term || !in) ? 1u : pw << 7;
+  }
+}
+
+template <int OP>
+__device__ __forceinline__ void thread_leaf_reduce(const uint8_t* __restrict__ leafp, uint32_t u,
+                                                   uint64_t mask, uint64_t value, uint64_t& r,
+                                                   uint64_t& c) {
+  uint4 v = *reinterpret_cast<const uint4*>(leafp);
+  uint4 v2 = u > 16u ? *reinterpret_cast<const uint4*>(leafp + 16) : make_uint4(0u, 0u, 0u, 0u);
+  uint64_t val = (uint64_t)v.x | ((uint64_t)v.y << 32);
+  uint64_t lr = op_identity<OP>(), lc = 0;
+  if ((val & mask) == value) { lr = op_apply<OP>(lr, val); lc++; }
+  uint32_t acc = 0, pw = 1, pwmax = 0;
+  for (uint32_t p0 = 0; p0 < u; p0 += 32) {
+    if (p0) {
+      v = *reinterpret_cast<const uint4*>(leafp + p0);
+      v2 = p0 + 16u < u ? *reinterpret_cast<const uint4*>(leafp + p0 + 16) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    const uint32_t va = p0 + 16u <= u ? 0xFFFFu : (1u << (u - p0)) - 1u;
+    if (p0) leaf_reduce_chunk<OP, false>(w, va, mask, value, val, lr, lc, acc, pw, pwmax);
+    else leaf_reduce_chunk<OP, true>(w, va, mask, value, val, lr, lc, acc, pw, pwmax);
+    if (p0 + 16u < u) {
+      const uint32_t w2[4] = {v2.x, v2.y, v2.z, v2.w};
+      const uint32_t vb = p0 + 32u <= u ? 0xFFFFu : (1u << (u - p0 - 16u)) - 1u;
+      leaf_reduce_chunk<OP, false>(w2, vb, mask, value, val, lr, lc, acc, pw, pwmax);
+    }
+  }
+  if (pwmax >= (1u << 28)) {  // a long code: exact 64-bit decode
+    val = *reinterpret_cast<const uint64_t*>(leafp);
+    lr = op_identity<OP>();
+    lc = 0;
+    if ((val & mask) == value) { lr = op_apply<OP>(lr, val); lc++; }
+    uint64_t a64 = 0;
+    uint32_t sh = 0;
+    for (uint32_t p = 8; p < u; p++) {
+      const uint32_t b = leafp[p];
+      if (sh < 64) a64 |= (uint64_t)(b & 0x7Fu) << sh;
+      if (b & 0x80u) {
+        sh += 7;
+      } else {
+        val += a64;
+        if ((val & mask) == value) { lr = op_apply<OP>(lr, val); lc++; }
+        a64 = 0;
+        sh = 0;
+      }
+    }
+  }
+  r = op_apply<OP>(r, lr);
+  c += lc;
+}
+
 template <int OP>
 __global__ void __launch_bounds__(kT) k_range_reduce(RangeArgs a, uint64_t mask,
                                                      uint64_t value) {
@@ -310,7 +385,7 @@ __global__ void __launch_bounds__(kT) k_range_reduce(RangeArgs a, uint64_t mask,
   uint64_t r = op_identity<OP>(), c = 0;
   uint64_t qend = a.off[qi + 1];
   uint64_t lo = a.lo[qi], hi = a.hi[qi], fl = a.first[qi], qoff = a.off[qi];
-  for (uint64_t g = g0; g < g1; g++) {
+  for (uint64_t g = g0; g < g1;) {
     while (g >= qend) {
 #pragma unroll
       for (int o = 16; o; o >>= 1) r = op_apply<OP>(r, __shfl_xor_sync(FULL, r, o));
@@ -325,10 +400,22 @@ __global__ void __launch_bounds__(kT) k_range_reduce(RangeArgs a, uint64_t mask,
       qend = a.off[qi + 1];
       lo = a.lo[qi]; hi = a.hi[qi]; fl = a.first[qi]; qoff = a.off[qi];
     }
-    const uint64_t j = fl + (g - qoff);
+    const uint64_t li = g - qoff, n = qend - qoff;
+    if (!a.raw && li > 0 && li + 1 < n) {
+      // leaves strictly inside the range (byte codes): one leaf per lane
+      const uint64_t stop = min(g1, qend - 1);
+      for (uint64_t j = fl + li + lane; j < fl + (stop - qoff); j += 32) {
+        const uint32_t u = min(a.used[j], a.LB);
+        if (u) thread_leaf_reduce<OP>(a.data + j * a.LB, u, mask, value, r, c);
+      }
+      g = stop;
+      continue;
+    }
+    const uint64_t j = fl + li;
     warp_decode(a.data + j * a.LB, min(a.used[j], a.LB), [&](uint32_t, uint64_t v) {
       if (v >= lo && v < hi && (v & mask) == value) { r = op_apply<OP>(r, v); c++; }
     }, a.raw);
+    g++;
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) r = op_apply<OP>(r, __shfl_xor_sync(FULL, r, o));
