@@ -296,8 +296,6 @@ __device__ __forceinline__ void op_atomic(uint64_t* p, uint64_t v) {
   else atomicXor((ull*)p, (ull)v);
 }
 
-// Same load-balanced (query, leaf) walk as k_range; every covered leaf is
-// decoded and its keys filtered by range and mask.
 // Thread-per-leaf reduction of a byte-code leaf: every element v with
 // (v & mask) == value is reduced into (r, c), the running value kept as in
 // thread_leaf_sum; bytes past u are no terminators here (a repeated value
@@ -373,6 +371,9 @@ __device__ __forceinline__ void thread_leaf_reduce(const uint8_t* __restrict__ l
   c += lc;
 }
 
+// Same load-balanced (query, leaf) walk as k_range: the end leaves of a
+// query are decoded by the warp and filtered by range and mask, the leaves
+// strictly inside are reduced one per thread (byte codes).
 template <int OP>
 __global__ void __launch_bounds__(kT) k_range_reduce(RangeArgs a, uint64_t mask,
                                                      uint64_t value) {
