@@ -400,27 +400,38 @@ __device__ __forceinline__ void lane_codes(const uint32_t (&w)[NW], int b_lo, in
 // ---------------------------------------------------------------------------
 // Thread-per-leaf sum of byte-code leaves (codec 0): the sum (mod 2^64) of
 // the elements of the leaf at leafp with u >= 8 used bytes.  One thread walks
-// the leaf 16 bytes at a time keeping the running element value and the
-// running sum: each byte adds its payload times 128^(bytes before it in its
-// code) to the open code, a terminator adds the code to the value and the
-// value to the sum.  Bytes after u are read as zero: each of them acts as a
+// the leaf eight bytes at a time keeping the running element value val and
+// the running sum s.  Inside the eight bytes everything is 32-bit: each byte
+// adds its payload times 128^(bytes before it in its code) to acc, and acc is
+// not cleared at a terminator, so at the k-th terminator of the group acc_k
+// holds the bits of every code closed so far in the group (plus the open code
+// carried in): the element closed there is val + acc_k.  The group adds T *
+// val + sum_k acc_k to s (T terminators), val moves on by the acc of its last
+// terminator and acc keeps only the open code's bits.  With codes of at most 4
+// bytes at most 11 bytes of payload feed one group and sum_k acc_k < 9 * 2^28
+// fits in 32 bits.  Bytes after u are read as zero: each of them acts as a
 // terminator adding the last value again, which is taken off at the end.  A
 // code of more than 4 bytes overflows the 32-bit code accumulator; such a
 // leaf is summed again exactly, byte by byte.
-template <bool FIRST>
-__device__ __forceinline__ void leaf_sum_chunk(const uint32_t (&w)[4], uint64_t& val, uint64_t& s,
-                                               uint32_t& acc, uint32_t& pw, uint32_t& pwmax) {
+__device__ __forceinline__ void leaf_sum_group(uint32_t wa, uint32_t wb, uint64_t& val,
+                                               uint64_t& s, uint32_t& acc, uint32_t& pw,
+                                               uint32_t& pwor) {
+  const uint32_t pa = wa & 0x7F7F7F7Fu, pb = wb & 0x7F7F7F7Fu;
+  uint32_t ss = 0, r = 0;
 #pragma unroll
-  for (int b = FIRST ? 8 : 0; b < 16; b++) {
-    const uint32_t wb = w[b >> 2];
-    acc += (__byte_perm(wb, 0u, 0x4440u + (uint32_t)(b & 3)) & 0x7Fu) * pw;
-    const bool term = (wb & (0x80u << (8 * (b & 3)))) == 0u;
-    pwmax = pwmax > pw ? pwmax : pw;
-    val += term ? (uint64_t)acc : 0ull;
-    s += term ? val : 0ull;
-    acc = term ? 0u : acc;
+  for (int b = 0; b < 8; b++) {
+    const uint32_t wv = b < 4 ? wa : wb, pv = b < 4 ? pa : pb;
+    acc += __byte_perm(pv, 0u, 0x4440u + (uint32_t)(b & 3)) * pw;
+    const bool term = (wv & (0x80u << (8 * (b & 3)))) == 0u;
+    pwor |= pw;
+    ss += term ? acc : 0u;
+    r = term ? acc : r;
     pw = term ? 1u : pw << 7;
   }
+  const uint32_t T = __popc(~wa & 0x80808080u) + __popc(~wb & 0x80808080u);
+  s += (uint64_t)T * val + ss;
+  val += r;
+  acc -= r;
 }
 
 // Bytes of w past u - p0 cleared (the leaf's zero padding, read as such).
@@ -439,7 +450,7 @@ __device__ __forceinline__ uint64_t thread_leaf_sum(const uint8_t* __restrict__ 
   uint4 v2 = u > 16u ? *reinterpret_cast<const uint4*>(leafp + 16) : make_uint4(0u, 0u, 0u, 0u);
   uint32_t w[4] = {v.x, v.y, v.z, v.w};
   uint64_t val = (uint64_t)w[0] | ((uint64_t)w[1] << 32), s = val;
-  uint32_t acc = 0, pw = 1, pwmax = 0;
+  uint32_t acc = 0, pw = 1, pwor = 0;
   for (uint32_t p0 = 0; p0 < u; p0 += 32) {
     if (p0) {
       v = *reinterpret_cast<const uint4*>(leafp + p0);
@@ -447,16 +458,17 @@ __device__ __forceinline__ uint64_t thread_leaf_sum(const uint8_t* __restrict__ 
       w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
     }
     mask_past(w, p0, u);
-    if (p0) leaf_sum_chunk<false>(w, val, s, acc, pw, pwmax);
-    else leaf_sum_chunk<true>(w, val, s, acc, pw, pwmax);
+    if (p0) leaf_sum_group(w[0], w[1], val, s, acc, pw, pwor);  // bytes 0-7 are the head
+    leaf_sum_group(w[2], w[3], val, s, acc, pw, pwor);
     if (p0 + 16u < u) {
       uint32_t w2[4] = {v2.x, v2.y, v2.z, v2.w};
       mask_past(w2, p0 + 16u, u);
-      leaf_sum_chunk<false>(w2, val, s, acc, pw, pwmax);
+      leaf_sum_group(w2[0], w2[1], val, s, acc, pw, pwor);
+      leaf_sum_group(w2[2], w2[3], val, s, acc, pw, pwor);
     }
   }
   s -= (uint64_t)(((u + 15u) & ~15u) - u) * val;
-  if (pwmax >= (1u << 28)) {  // a long code: exact 64-bit decode
+  if (pwor >= (1u << 28)) {  // a long code: exact 64-bit decode
     val = *reinterpret_cast<const uint64_t*>(leafp);
     s = val;
     uint64_t a64 = 0;
@@ -479,24 +491,31 @@ __device__ __forceinline__ uint64_t thread_leaf_sum(const uint8_t* __restrict__ 
 
 // Is x an element of the byte-code leaf at leafp (u used bytes)?  One
 // thread decodes the leaf from its head, 16 bytes at a time, until the
-// running value passes x (same per-byte arithmetic as thread_leaf_sum; zero
-// bytes after u repeat the last value, which is an element).  A leaf with a
-// code over 4 bytes is decoded again exactly, byte by byte.
-template <bool FIRST>
-__device__ __forceinline__ void leaf_has_chunk(const uint32_t (&w)[4], uint64_t x, uint64_t& val,
-                                               bool& found, uint32_t& acc, uint32_t& pw,
-                                               uint32_t& pwmax) {
+// running value passes x.  The bytes are taken eight at a time as in
+// thread_leaf_sum: the element closed at a terminator is val + acc with a
+// 32-bit acc, so it equals x exactly when acc equals x - val (no element of
+// the group can when x - val >= 2^32, since acc stays below 9 * 2^28).
+// Zero bytes after u repeat the last value, which is an element.  A leaf
+// with a code over 4 bytes is decoded again exactly, byte by byte.
+__device__ __forceinline__ void leaf_has_group(uint32_t wa, uint32_t wb, uint64_t x,
+                                               uint64_t& val, bool& found, uint32_t& acc,
+                                               uint32_t& pw, uint32_t& pwor) {
+  const uint64_t dx = x - val;  // wraps past 2^32 once val > x: no match then
+  const uint32_t d32 = dx > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)dx;
+  const uint32_t pa = wa & 0x7F7F7F7Fu, pb = wb & 0x7F7F7F7Fu;
+  uint32_t r = 0;
 #pragma unroll
-  for (int b = FIRST ? 8 : 0; b < 16; b++) {
-    const uint32_t wb = w[b >> 2];
-    acc += (__byte_perm(wb, 0u, 0x4440u + (uint32_t)(b & 3)) & 0x7Fu) * pw;
-    const bool term = (wb & (0x80u << (8 * (b & 3)))) == 0u;
-    pwmax = pwmax > pw ? pwmax : pw;
-    val += term ? (uint64_t)acc : 0ull;
-    found |= term && val == x;
-    acc = term ? 0u : acc;
+  for (int b = 0; b < 8; b++) {
+    const uint32_t wv = b < 4 ? wa : wb, pv = b < 4 ? pa : pb;
+    acc += __byte_perm(pv, 0u, 0x4440u + (uint32_t)(b & 3)) * pw;
+    const bool term = (wv & (0x80u << (8 * (b & 3)))) == 0u;
+    pwor |= pw;
+    found |= term && acc == d32;
+    r = term ? acc : r;
     pw = term ? 1u : pw << 7;
   }
+  val += r;
+  acc -= r;
 }
 
 __device__ __forceinline__ bool thread_leaf_has(const uint8_t* __restrict__ leafp, uint32_t u,
@@ -507,21 +526,17 @@ __device__ __forceinline__ bool thread_leaf_has(const uint8_t* __restrict__ leaf
   uint64_t val = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
   if (x <= val) return x == val;
   bool found = false;
-  uint32_t acc = 0, pw = 1, pwmax = 0;
+  uint32_t acc = 0, pw = 1, pwor = 0;
   for (uint32_t p0 = 0; p0 < u && val < x; p0 += 16) {
     if (p0) {
       v = *reinterpret_cast<const uint4*>(leafp + p0);
       w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
     }
-    if (p0 + 16u > u) {
-      const uint32_t keep = (1u << (u - p0)) - 1u;
-#pragma unroll
-      for (int i = 0; i < 4; i++) w[i] &= bytemask4((keep >> (4 * i)) & 0xFu);
-    }
-    if (p0) leaf_has_chunk<false>(w, x, val, found, acc, pw, pwmax);
-    else leaf_has_chunk<true>(w, x, val, found, acc, pw, pwmax);
+    mask_past(w, p0, u);
+    if (p0) leaf_has_group(w[0], w[1], x, val, found, acc, pw, pwor);  // bytes 0-7: the head
+    leaf_has_group(w[2], w[3], x, val, found, acc, pw, pwor);
   }
-  if (pwmax >= (1u << 28)) {  // a long code: exact 64-bit decode
+  if (pwor >= (1u << 28)) {  // a long code: exact 64-bit decode
     val = *reinterpret_cast<const uint64_t*>(leafp);
     found = false;
     uint64_t a64 = 0;
