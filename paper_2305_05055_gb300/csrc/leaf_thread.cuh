@@ -142,17 +142,21 @@ LT_HD uint32_t byte_of(uint32_t v, int i) {  // byte i of v, zero-extended
 // times pw = 128^(bytes of its code before it) to tot, so tot is the sum of
 // the codes completed so far in the chunk plus the open code's bits (tot
 // enters with the bits the open code got in earlier chunks); tt keeps tot as
-// of the last terminator.  pwmax >= 2^28 marks a code of more than 4 bytes
-// (pw wraps to 0 after that, harmlessly).
+// of the last terminator.  pw is a power of two (or 0 once it wraps past a
+// fifth byte, harmlessly), so pwor, the OR of every pw, is >= 2^28 exactly
+// when some code has more than 4 bytes.
 template <bool FIRST>
 LT_HD void sum_chunk(const uint32_t (&w)[4], uint32_t& tot, uint32_t& tt, uint32_t& pw,
-                     uint32_t& pwmax) {
+                     uint32_t& pwor) {
+  uint32_t pm[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) pm[i] = w[i] & 0x7F7F7F7Fu;  // payload bits only
 #pragma unroll
   for (int b = FIRST ? 8 : 0; b < 16; b++) {
     const uint32_t wb = w[b >> 2];
-    tot += (byte_of(wb, b & 3) & 0x7Fu) * pw;
+    tot += byte_of(pm[b >> 2], b & 3) * pw;
     const bool term = (wb & (0x80u << (8 * (b & 3)))) == 0u;
-    pwmax = pwmax > pw ? pwmax : pw;
+    pwor |= pw;
     tt = term ? tot : tt;
     pw = term ? 1u : pw << 7;
   }
@@ -269,7 +273,7 @@ LT_HD uint32_t pass_a(const uint8_t* leafp, uint32_t uold, uint32_t m, const uin
   // code it falls in, or stays for the end
   uint64_t ycur = k < s ? pick(y, k) : ~0ull;
   uint64_t val = head;
-  uint32_t carry = 0, pw = 1, pwmax = 0, nterm = 0;
+  uint32_t carry = 0, pw = 1, pwor = 0, nterm = 0;
   for (uint32_t p0 = 0; p0 < uold; p0 += 16) {
     if (p0) ld16(leafp + p0, w);
     if (p0 + 16u > uold) {  // bytes past the used ones read as zero
@@ -283,9 +287,9 @@ LT_HD uint32_t pass_a(const uint8_t* leafp, uint32_t uold, uint32_t m, const uin
     const uint32_t pw0 = pw;
     if (p0) {
       nterm += popc(~w[0] & 0x80808080u) + popc(~w[1] & 0x80808080u);
-      sum_chunk<false>(w, tot, tt, pw, pwmax);
+      sum_chunk<false>(w, tot, tt, pw, pwor);
     } else {
-      sum_chunk<true>(w, tot, tt, pw, pwmax);
+      sum_chunk<true>(w, tot, tt, pw, pwor);
     }
     const uint64_t vend = val + tt;
     if (vend >= ycur) {
@@ -302,7 +306,7 @@ LT_HD uint32_t pass_a(const uint8_t* leafp, uint32_t uold, uint32_t m, const uin
     val = vend;
     carry = tot - tt;
   }
-  if (pwmax >= (1u << 28)) return kLongCode;
+  if (pwor >= (1u << 28)) return kLongCode;
   nterm -= ((uold + 15u) & ~15u) - uold;
   if (nterm + 1u != m) return kBadCount;
   // step 2: exact gaps inside the recorded chunks
