@@ -6,7 +6,8 @@
 // digits in one read of the batch; its last block scans them and marks the
 // digits that vary (40-bit uniform keys need 5 passes, not 8).  Each varying
 // digit is then one scatter launch: a tile of 4096 keys is ranked stably in
-// shared memory (warp match_any per digit, then per-warp prefixes), its
+// shared memory (the lanes of a warp sharing a digit found by eight ballots,
+// then per-warp prefixes), its
 // global offsets come from the tiles before it by decoupled look-back (each
 // tile publishes its per-digit count, then its inclusive prefix), and every
 // digit's run of the tile is written contiguously.  Digits that do not vary
@@ -73,9 +74,15 @@ __device__ __forceinline__ void tile_rank(const uint64_t (&key)[ITEMS], const ui
     const bool valid = li < nvalid;
     const uint32_t d = (uint32_t)(key[j] >> shift) & 255u;
     const unsigned vm = __ballot_sync(FULL, valid);
-    unsigned peers = 0, before = 0;
+    // lanes holding the same digit: one ballot per digit bit
+    unsigned peers = vm, before = 0;
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+      const bool bit = (d >> b) & 1u;
+      const unsigned bb = __ballot_sync(FULL, bit);
+      peers &= bit ? bb : ~bb;
+    }
     if (valid) {
-      peers = __match_any_sync(vm, d);
       before = __popc(peers & lanemask_lt());
       rank[j] = sm.wcnt[warp][d] + before;
     }
