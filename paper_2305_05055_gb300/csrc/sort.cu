@@ -133,6 +133,7 @@ constexpr uint32_t kFlagA = 1u << 30;  // tile count published
 constexpr uint32_t kFlagP = 2u << 30;  // inclusive prefix published
 constexpr uint32_t kCountMask = (1u << 30) - 1u;
 constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kLook = 8;  // predecessors read per look-back step
 
 // Control block of one sort, zeroed before the first kernel.
 struct SortCtl {
@@ -280,17 +281,30 @@ __global__ void __launch_bounds__(kT, 3) k_onesweep(const uint64_t* __restrict__
     } else {
       lk[d] = kFlagA | cnt;
       uint32_t excl = 0;
-      for (int64_t tp = (int64_t)tile - 1; tp >= 0; tp--) {
-        volatile uint32_t* q = look + (size_t)tp * 256 + d;
-        uint32_t v = *q;
-        uint32_t spins = 0;
-        while (!(v & (kFlagA | kFlagP)) && spins < kSpinLimit) { v = *q; spins++; }
-        if (spins >= kSpinLimit) {  // a predecessor never published: give up
-          atomicOr(&st->err, kErrSort);
-          break;
+      bool done = false;
+      const volatile uint32_t* lv = look;
+      // kLook predecessors are read at once (their loads in flight together),
+      // then taken in order until one with an inclusive prefix
+      for (int64_t tp = (int64_t)tile - 1; tp >= 0 && !done; tp -= kLook) {
+        uint32_t v[kLook];
+#pragma unroll
+        for (int i = 0; i < kLook; i++) v[i] = tp >= i ? lv[(size_t)(tp - i) * 256 + d] : 0u;
+#pragma unroll
+        for (int i = 0; i < kLook; i++) {
+          if (done || tp < i) break;
+          uint32_t spins = 0;
+          while (!(v[i] & (kFlagA | kFlagP)) && spins < kSpinLimit) {
+            v[i] = lv[(size_t)(tp - i) * 256 + d];
+            spins++;
+          }
+          if (spins >= kSpinLimit) {  // a predecessor never published: give up
+            atomicOr(&st->err, kErrSort);
+            done = true;
+            break;
+          }
+          excl += v[i] & kCountMask;
+          if (v[i] & kFlagP) done = true;
         }
-        excl += v & kCountMask;
-        if (v & kFlagP) break;
       }
       __threadfence();
       lk[d] = kFlagP | (excl + cnt);
