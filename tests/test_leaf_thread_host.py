@@ -1,5 +1,5 @@
 """Host build of the thread-granular leaf insert and delete (the code the
-GPU kernels k_insert_thread and k_delete_thread run per leaf) against the
+GPU kernel k_insert_thread runs per leaf, for deletes as k_insert_thread<true>) against the
 oracle's leaf encoder: inserting (deleting) a slice of at most four keys
 must give exactly the bytes of encoding the union (difference) from scratch
 (Sec. 5 leaf format, zero bytes after the used ones), the right count, head
