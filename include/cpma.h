@@ -21,8 +21,14 @@
  *  - Every uint64 value 0 .. 2^64-1 is a valid key.  Batches may be unsorted
  *    and may repeat keys; repeats are counted once.
  *  - Updates on one handle are single-writer: issue them on one stream (or
- *    order the streams).  Queries may run concurrently with other queries,
- *    never with an update unless the caller orders them.
+ *    order the streams).  cpma_has_batch and cpma_sum use no scratch and may
+ *    run concurrently with each other and with the range calls; the range
+ *    calls (cpma_range_map, _length, _extract, _reduce) share the handle's
+ *    query scratch, so two of them on one handle must be ordered (one
+ *    stream, or events).  No query may overlap an update unless the caller
+ *    orders them.  A handle's host-side state is not locked: calls on one
+ *    handle from several host threads must be serialised by the caller,
+ *    except the const queries above, which only read it.
  *  - Every call returns CPMA_OK (0) or a negative error code (below).  An
  *    update that fails before it starts changing the structure leaves the set
  *    unchanged; CPMA_ECUDA and CPMA_EINTERNAL after that point leave the
@@ -222,8 +228,11 @@ int cpma_range_reduce(const cpma_t* h, const uint64_t* d_lo, const uint64_t* d_h
  *    CPMA_EINVAL without doing anything.
  *  - The handle's device must be the current device (else CPMA_EINVAL).
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) and caches it; make that first call before any
- *    stream capture.
+ *    (cudaGetSymbolAddress) and caches it for the life of the process; make
+ *    that first call before any stream capture.  cudaDeviceReset destroys
+ *    the array together with every handle on that device, and the cached
+ *    address then points nowhere: do not use this entry point on a device
+ *    after resetting it (reload the library in a new process).
  *  - Every call on a device shares the one array: calls whose work overlaps
  *    on the GPU (different streams, not ordered) race and give wrong results.
  *    Order them on one stream. */

@@ -1,6 +1,7 @@
 // Host-side internals of the CPMA library: the handle, its scratch buffers and
 // the kernel launchers of each translation unit.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -131,7 +132,9 @@ struct cpma {
   cpmaimpl::Status* d_status = nullptr;
   cpmaimpl::Status* h_status = nullptr;  // pinned
   cpmaimpl::Scratch s;
-  uint64_t launches = 0;
+  // kernels launched; atomic because const queries on one handle may be
+  // issued from several host threads
+  std::atomic<uint64_t> launches{0};
   cpmaimpl::Prof prof;
   uint64_t graph_max_batch = 0;     // batches up to this size run their front segment as a graph
   void* graphs = nullptr;           // graph cache (update.cu)
@@ -245,4 +248,4 @@ inline unsigned ceil_log2(uint64_t L) {
     if (_rc != CPMA_OK) return _rc; \
   } while (0)
 #define CPMA_CUDA(x) CPMA_TRY(::cpmaimpl::check_cuda(x))
-#define CPMA_LAUNCHED(h) (const_cast<cpma*>(h)->launches++)
+#define CPMA_LAUNCHED(h) (const_cast<cpma*>(h)->launches.fetch_add(1, std::memory_order_relaxed))

@@ -776,6 +776,9 @@ int run_range_noalloc(const cpma* h, const uint64_t* lo, const uint64_t* hi, uin
   uint64_t* items = first + kNoAllocMaxQueries;
   uint64_t* off = items + kNoAllocMaxQueries;            // q + 1 entries
   uint64_t* partials = off + kNoAllocMaxQueries + 1;     // kNoAllocPartials entries
+  // the offset scan needs at most 2 * SMs + 1 partials: checked before any
+  // launch, so a rejected call leaves the outputs untouched
+  if ((uint64_t)2 * h->num_sms + 1 > kNoAllocPartials) return CPMA_EINVAL;
   const int g1 = (int)std::max<uint64_t>(
       1, std::min<uint64_t>((q + kT - 1) / kT, (uint64_t)h->num_sms * 8));
   // every scratch entry read below is written first on this stream: nothing

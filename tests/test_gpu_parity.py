@@ -115,6 +115,36 @@ def test_update_sequence(LB):
             same_queries(g, p, 900 + r, 200)
 
 
+@pytest.mark.parametrize("num,den", [(11, 10), (3, 2), (2, 1)])
+def test_growing_factors_grow_and_shrink(num, den):
+    # App. C: growing factors 1.1 ... 2 (R9 with g = num/den).  The set grows
+    # from 2000 keys by batches that force several resizes, then big deletes
+    # shrink it; layout parity after every batch, and both directions seen.
+    cfg = dict(leaf_bytes=256, grow_num=num, grow_den=den)
+    base = W.uniform_keys(31, 2000, bits=40)
+    g = cp.CPMA(T(base), **cfg)
+    o = oracle.SeqCPMA(base, **cfg)
+    p = oracle.PlainSet(base)
+    same_layout(g, o)
+    Ls = [g.leaves()]
+    for r in range(8):
+        keys = W.uniform_keys(800 + r, 1500 * (r + 1), bits=40)
+        if r % 3 == 2:
+            keys = np.concatenate([keys, W.zipf_keys(850 + r, 3000, bits=34)])
+        assert int(g.insert_batch(T(keys)).item()) == o.insert_batch(keys) == p.insert_batch(keys)
+        same_layout(g, o)
+        Ls.append(g.leaves())
+    same_queries(g, p, 860)
+    for r in range(6):
+        keys = W.sample_present(p.S, 870 + r, (len(p) * 3) // 5)
+        assert int(g.delete_batch(T(keys)).item()) == o.delete_batch(keys) == p.delete_batch(keys)
+        assert o.check() == 0
+        same_layout(g, o)
+        Ls.append(g.leaves())
+    same_queries(g, p, 880)
+    assert max(Ls) > Ls[0] and Ls[-1] < max(Ls), Ls
+
+
 def test_grow_from_empty_and_delete_everything():
     g = cp.CPMA(None, leaf_bytes=256)
     o = oracle.SeqCPMA([], leaf_bytes=256)

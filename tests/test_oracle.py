@@ -217,37 +217,80 @@ def test_scenario_in_place():
     assert list(head) == [0, 376, 780, 1184, 1588, 1992]
 
 
-def test_scenario_grow():
+def test_resize_leaf_counts_other_growing_factors():
+    # App. C sweeps the growing factor over 1.1 ... 2; R9 with g = num/den:
+    # grow L' = ceil(L' num / den) while 1000 T > 700 L' 512 = 358400 L',
+    # shrink L' = floor(L' den / num) while L' > 1 and 1000 T < 153600 L'.
+    R = oracle.resize_leaves
+    # g = 11/10, T = 5000 (5,000,000): 10 -> 11 (3,942,400) -> ceil(12.1) = 13
+    # (4,659,200) -> ceil(14.3) = 15 (5,376,000 >= 5,000,000)
+    assert R(5000, 10, 512, 700, 300, 11, 10) == 15
+    # one leaf: ceil(1.1) = 2 (716,800 >= 400,000)
+    assert R(400, 1, 512, 700, 300, 11, 10) == 2
+    # shrink, T = 1000 (1,000,000): 10 -> floor(100/11) = 9 (1,382,400) -> 8
+    # (1,228,800) -> 7 (1,075,200) -> floor(70/11) = 6 (921,600: stop)
+    assert R(1000, 10, 512, 700, 300, 11, 10) == 6
+    assert R(1000, 11, 512, 700, 300, 11, 10) == 6   # 11 -> 10 -> 9 -> 8 -> 7 -> 6
+    # g = 3/2: T = 9000 (9,000,000): 10 -> 15 (5,376,000) -> ceil(22.5) = 23
+    # (8,243,200) -> ceil(34.5) = 35 (12,544,000)
+    assert R(9000, 10, 512, 700, 300, 3, 2) == 35
+    assert R(5000, 10, 512, 700, 300, 3, 2) == 15
+    # shrink T = 1000: 10 -> floor(20/3) = 6 (921,600: stop); T = 300
+    # (300,000): 10 -> 6 (921,600) -> 4 (614,400) -> 2 (307,200) -> 1
+    assert R(1000, 10, 512, 700, 300, 3, 2) == 6
+    assert R(300, 10, 512, 700, 300, 3, 2) == 1
+    # g = 2: T = 9000: 10 -> 20 (7,168,000) -> 40 (14,336,000)
+    assert R(9000, 10, 512, 700, 300, 2, 1) == 40
+    assert R(400, 1, 512, 700, 300, 2, 1) == 2
+    # shrink T = 1000: 10 -> 5 (768,000: stop); T = 300: 10 -> 5 -> 2
+    # (307,200) -> 1
+    assert R(1000, 10, 512, 700, 300, 2, 1) == 5
+    assert R(300, 10, 512, 700, 300, 2, 1) == 1
+    # at the exact bound nothing moves: 1000 T = 358400 L and 153600 L
+    for num, den in ((6, 5), (11, 10), (3, 2), (2, 1)):
+        assert R(3584, 10, 512, 700, 300, num, den) == 10
+        assert R(1536, 10, 512, 700, 300, num, den) == 10
+
+
+@pytest.mark.parametrize("num,den,Lp", [(6, 5, 15), (11, 10, 15), (3, 2, 14), (2, 1, 24)])
+def test_scenario_grow(num, den, Lp):
     # Insert 4i+1, 4i+2, 4i+3 for every i < 599: 1797 keys, every delta
     # becomes 1.  Per leaf after the merge: leaf 0 has 94*4 = 376 elements
     # (383 bytes), leaves 1-4 have 404 (411 bytes), leaf 5 has 102 + 101*3 =
     # 405 (412 bytes): T = 383 + 4*411 + 412 = 2439.  Every walk passes the
-    # root, so resize: 1000 T = 2,439,000 > 700 * L' * 256 for L' = 6, 8, 10,
-    # 12 and <= for L' = 15 (6 -> 8 -> 10 -> 12 -> 15).  2397 elements,
-    # S = 8 + 2396 = 2404, all costs after the first are 1, so
-    # s_w = floor(2404 w / 15) - 7 and leaf w uses s_{w+1} - s_w + 7 bytes.
-    o = _base()
+    # root, so resize while 1000 T = 2,439,000 > 700 * L' * 256, i.e. until
+    # L' >= 13.62: g = 6/5: 6 -> 8 -> 10 -> 12 -> 15; g = 11/10: 6 -> 7 -> 8
+    # -> 9 -> 10 -> 11 -> 13 -> 15; g = 3/2: 6 -> 9 -> 14; g = 2: 6 -> 12 ->
+    # 24.  2397 elements, S = 8 + 2396 = 2404, all costs after the first are
+    # 1, so s_w = floor(2404 w / L') - 7 (every cut is past the head's 8
+    # bytes) and leaf w uses s_{w+1} - s_w + 7 bytes.
+    o = oracle.SeqCPMA([4 * i for i in range(600)][::-1] + [8, 8, 12], leaf_bytes=256,
+                       grow_num=num, grow_den=den, **CFG)
     ins = [4 * i + r for i in range(599) for r in (1, 2, 3)]
     assert o.insert_batch(ins) == 1797
     assert o.last_batch()["resized"] == 1
-    assert o.leaves() == 15
-    s = [0] + [2404 * w // 15 - 7 for w in range(1, 15)] + [2397]
+    assert o.leaves() == Lp
+    s = [0] + [2404 * w // Lp - 7 for w in range(1, Lp)] + [2397]
     _, used, head = o.layout()
-    assert list(used) == [s[w + 1] - s[w] + 7 for w in range(15)]
+    assert list(used) == [s[w + 1] - s[w] + 7 for w in range(Lp)]
     elems = sorted([4 * i for i in range(600)] + ins)
-    assert list(head) == [elems[s[w]] for w in range(15)]
+    assert list(head) == [elems[s[w]] for w in range(Lp)]
     assert o.check() == 0
 
 
-def test_scenario_shrink():
+@pytest.mark.parametrize("num,den", [(6, 5), (11, 10), (3, 2), (2, 1)])
+def test_scenario_shrink(num, den):
     # Delete 4i for i in [50, 550): leaves 1-4 become empty (0 bytes), leaves
     # 0 and 5 keep 50 elements (57 bytes).  Leaf 0 is within [25.6, 230.4]:
     # rewritten in place.  Leaf 1: 0 < 25.6 -> walk: [0,2) 57 < 85.3,
     # [0,4) 57 < 1024 * (0.1 + 0.4/3) = 238.9, root [0,6) 114 < 0.3*1536 =
     # 460.8 -> resize.  T = 114: shrink 6 -> 5 -> 4 -> 3 -> 2 -> 1 (at every
-    # step 114000 < 300 * L' * 256).  One leaf: 100 elements, deltas 4 (1 byte)
-    # except 4*550 - 4*49 = 2004 (2 bytes): 8 + 98 + 2 = 108 bytes.
-    o = _base()
+    # step 114000 < 300 * L' * 256; with g = 11/10: 6 -> 5 -> 4 -> 3 -> 2 ->
+    # 1, g = 3/2: 6 -> 4 -> 2 -> 1, g = 2: 6 -> 3 -> 1).  One leaf: 100
+    # elements, deltas 4 (1 byte) except 4*550 - 4*49 = 2004 (2 bytes): 8 +
+    # 98 + 2 = 108 bytes.
+    o = oracle.SeqCPMA([4 * i for i in range(600)][::-1] + [8, 8, 12], leaf_bytes=256,
+                       grow_num=num, grow_den=den, **CFG)
     assert o.delete_batch([4 * i for i in range(50, 550)] + [3, 5, 7]) == 500
     assert o.last_batch()["resized"] == 1
     assert o.leaves() == 1

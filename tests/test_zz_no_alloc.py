@@ -4,8 +4,10 @@ Callers that cannot allocate device memory inside a call (their memory is all
 handed to another allocator up front, or they must not hit the device-wide
 synchronisation that cudaFree implies) use cpma_range_map_noalloc, whose
 scratch is a fixed array inside the library.  Through the C ABI, two calls in a
-row must give exactly what cpma_range_map gives on the same queries (integer
-sums and counts: bit for bit), and oversized batches must be rejected.
+row must give exactly what cpma_range_map gives on the same queries and what
+the CPU oracle's plain sorted set gives (integer sums and counts: bit for
+bit), on batches that take the offset scan's one-block path (q <= 8192) and
+its multi-block path, and oversized batches must be rejected.
 
 This file is named to be collected last, so a run that stops at the first
 failure has already run every other test.
@@ -16,6 +18,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2305_05055_gb300 import cpma as cp
 from paper_2305_05055_gb300 import workloads as W
 
@@ -36,11 +39,18 @@ def test_noalloc_range_map_matches_range_map_twice():
     assert torch.cuda.is_available()
     lib = cp.lib()
     base = W.uniform_keys(71, 400000, bits=40)
+    extra = W.zipf_keys(72, 50000, bits=34)
     g = cp.CPMA(T(base), leaf_bytes=512)
-    g.insert_batch(T(W.zipf_keys(72, 50000, bits=34)))
-    S = np.unique(np.concatenate([base]))
-    for rnd, (nq, seed) in enumerate([(20000, 73), (cp.RANGE_NOALLOC_MAX_QUERIES, 74)]):
+    g.insert_batch(T(extra))
+    p = oracle.PlainSet(base)
+    p.insert_batch(extra)
+    S = p.S
+    # 1 and 5000 queries: the one-block offset scan; 20000 and the maximum:
+    # the multi-block scan
+    cases = [(1, 76), (5000, 77), (20000, 73), (cp.RANGE_NOALLOC_MAX_QUERIES, 74)]
+    for rnd, (nq, seed) in enumerate(cases):
         lo, hi, _ = W.range_queries_by_rank(S, seed, nq, 1, 100000)
+        ws, wc = p.range_map(lo, hi)
         lo, hi = T(lo), T(hi)
         s0 = torch.empty(nq, dtype=torch.int64, device="cuda")
         c0 = torch.empty_like(s0)
@@ -51,6 +61,8 @@ def test_noalloc_range_map_matches_range_map_twice():
         torch.cuda.synchronize()
         assert torch.equal(c0, c1), "counts differ in call %d" % rnd
         assert torch.equal(s0, s1), "sums differ in call %d" % rnd
+        assert np.array_equal(cp.to_u64(c1), wc), "counts differ from the oracle in call %d" % rnd
+        assert np.array_equal(cp.to_u64(s1), ws), "sums differ from the oracle in call %d" % rnd
         assert int(c1.sum().item()) > 0
 
 
