@@ -30,9 +30,16 @@
  *    handle from several host threads must be serialised by the caller,
  *    except the const queries above, which only read it.
  *  - Every call returns CPMA_OK (0) or a negative error code (below).  An
- *    update that fails before it starts changing the structure leaves the set
- *    unchanged; CPMA_ECUDA and CPMA_EINTERNAL after that point leave the
- *    handle unusable (destroy it).
+ *    update is all or nothing with respect to memory: before it changes
+ *    anything it reserves every byte of device memory it can need (scratch
+ *    for the batch, overflow and redistribution buffers for the whole set,
+ *    and new leaf arrays when the batch can make the array grow), so
+ *    CPMA_ENOMEM -- from the allocator or the memory budget -- and
+ *    CPMA_EINVAL, CPMA_ETIMEOUT and the rejection of an unsorted "sorted"
+ *    batch all leave the set and the handle exactly as they were.  Only
+ *    CPMA_ECUDA (a failed CUDA call) and CPMA_EINTERNAL (a device-side
+ *    consistency check) can come after the structure has started to change;
+ *    the handle is then unusable (destroy it).
  *  - Calls that take a stream enqueue device work on it; the update calls and
  *    cpma_create also wait on it once or twice for small control values
  *    (batch sizes, whether to resize), so they return with the update
@@ -57,7 +64,21 @@ enum {
   CPMA_ENOMEM = -2,    /* device or host allocation failed */
   CPMA_ECUDA = -3,     /* a CUDA call failed */
   CPMA_EINTERNAL = -4, /* a device-side consistency check failed */
+  CPMA_ETIMEOUT = -5,  /* a bounded device-side wait gave up (the batch sort's
+                          look-back: a tile whose predecessor never published
+                          its counts); the set is unchanged */
 };
+
+/* Device memory callbacks (cpma_config.alloc / .free).  alloc returns
+ * `bytes` of device memory on the handle's device, aligned to at least 256
+ * bytes, or NULL when it cannot (the call then fails with CPMA_ENOMEM and
+ * leaves the set unchanged).  `stream` is the stream of the library call that
+ * needs the memory (NULL when the call has none).  free(p, stream, ctx)
+ * returns a block; the library frees a block only after the device has
+ * finished all work that uses it (it synchronises first), so any allocator
+ * -- stream-ordered or not -- may hand the block out again at once. */
+typedef void* (*cpma_alloc_fn)(size_t bytes, cpma_stream_t stream, void* ctx);
+typedef void (*cpma_free_fn)(void* p, cpma_stream_t stream, void* ctx);
 
 /* Tunables.  The density bounds follow Sec. 3 ("the density bound of a node
  * depends on its height"; leaf bound 0.9 in the figure captions) read as a
@@ -78,7 +99,17 @@ enum {
  * (default).
  * codec 1 keeps every key in an 8-byte little-endian cell, packed left,
  * under the same batch algorithm (bounds, routing, counting, resizing): the
- * uncompressed PMA, for measuring what the compression buys. */
+ * uncompressed PMA, for measuring what the compression buys.
+ * leaf_growth > 0 makes the leaf size grow with the number of keys, as the
+ * CPMA's Theta(log n) leaves do (Sec. 5 "CPMA structure"; Sec. 6 space
+ * usage): whenever the leaf array is built (cpma_create, a rebuild) or
+ * resized, the leaf size becomes
+ *   LB(n) = min(2048, max(leaf_bytes, 16 * ceil(leaf_growth * bitlen(n) / 16)))
+ * for the n keys it will hold (bitlen(n) = floor(log2 n) + 1, 0 for n = 0),
+ * leaf_bytes being the smallest size.  A resize to size LB' starts from the
+ * leaf count of equal capacity, ceil(L * LB / LB'), and then grows or
+ * shrinks by the growing factor as with a fixed size.  cpma_leaf_bytes
+ * returns the size in use. */
 typedef struct {
   uint32_t leaf_bytes; /* LB; default 512 */
   uint32_t tau_leaf;   /* default 900 */
@@ -91,6 +122,16 @@ typedef struct {
   uint32_t rebuild_pm; /* batch-to-set ratio that rebuilds; default 0 = never */
   uint32_t codec;      /* leaf format: 0 = byte codes (the CPMA, default),
                           1 = 8-byte cells (the uncompressed PMA of Sec. 3) */
+  uint32_t leaf_growth; /* leaf size that grows with n: 0 = fixed leaf_bytes
+                           (default); else bytes per bit of n (see below) */
+  uint32_t reserved;    /* must be 0 */
+  cpma_alloc_fn alloc;  /* device memory; NULL (default) = cudaMalloc */
+  cpma_free_fn free;    /* NULL (default) = cudaFree; set both or neither */
+  void* alloc_ctx;      /* passed to alloc and free */
+  uint64_t mem_budget_bytes; /* cap on the device memory the handle holds
+                                (structure and every scratch buffer); a call
+                                that would exceed it fails with CPMA_ENOMEM
+                                before it changes anything; 0 = no cap */
 } cpma_config;
 
 /* Fill *cfg with the defaults above. */
@@ -257,6 +298,31 @@ int cpma_bytes(const cpma_t* h, uint64_t* out);
 
 /* Number of leaves L (host value). */
 int cpma_leaves(const cpma_t* h, uint64_t* out);
+
+/* Leaf size in bytes now in use (cfg.leaf_bytes unless leaf_growth > 0). */
+int cpma_leaf_bytes(const cpma_t* h, uint64_t* out);
+
+/* Device memory the handle holds now: structure, spare leaf arrays kept for
+ * a possible resize, and every scratch buffer (what mem_budget_bytes caps). */
+int cpma_mem_held(const cpma_t* h, uint64_t* out);
+
+/* The most device memory the handle has held at any moment (within calls
+ * too: an update holds its reservation and, during a resize, both leaf
+ * arrays). */
+int cpma_mem_peak(const cpma_t* h, uint64_t* out);
+
+/* Change the memory budget of a live handle (0 = no cap).  Memory already
+ * held is kept; the cap applies to the next allocations. */
+int cpma_set_mem_budget(cpma_t* h, uint64_t bytes);
+
+/* For tests of the bounded wait (no counterpart in the paper): poll_limit
+ * replaces the number of polls after which a tile of the batch sort stops
+ * waiting for its predecessor (0 restores the default, 2^22), and
+ * silent_tile >= 0 makes that tile of every sort pass skip publishing its
+ * counts, so the tiles after it wait until the limit; the update then
+ * returns CPMA_ETIMEOUT with the set unchanged.  silent_tile < 0 turns it
+ * off. */
+int cpma_test_sort_stall(cpma_t* h, uint32_t poll_limit, int64_t silent_tile);
 
 /* Copy the layout into caller device buffers: d_data (L * leaf_bytes bytes),
  * d_used (L uint32), d_heads (L uint64; for an empty leaf the head of the next

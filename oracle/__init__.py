@@ -73,7 +73,9 @@ def lib():
                 "o_resize_leaves": (U64, [U64, U64, U32, U32, U32, U32, U32]),
                 "o_cut_points": (None, [u64p, S, U64, u64p]),
                 "ocpma_create": (I, [C.POINTER(V), U32, U32, U32, U32, U32, U32, U32, U32, U32,
-                                     u64p, U64]),
+                                     U32, u64p, U64]),
+                "ocpma_leaf_bytes": (U32, [V]),
+                "o_leaf_size": (U32, [U64, U32, U32]),
                 "o_raw_leaf_encode": (U64, [u8p, U32, u64p, S]),
                 "o_raw_leaf_decode": (S, [u8p, U64, u64p]),
                 "ocpma_destroy": (None, [V]),
@@ -152,6 +154,11 @@ def violates(LB, tau_leaf, tau_root, rho_leaf, rho_root, H, h, leaves, nbytes) -
 
 def build_leaves(S: int, LB: int, build_pm: int) -> int:
     return int(lib().o_build_leaves(S, LB, build_pm))
+
+
+def leaf_size(n, lb_min, leaf_growth) -> int:
+    """R13: leaf size for an array that will hold n keys."""
+    return int(lib().o_leaf_size(n, lb_min, leaf_growth))
 
 
 def resize_leaves(T, L, LB, tau_root, rho_root, grow_num=6, grow_den=5) -> int:
@@ -277,7 +284,8 @@ class PlainSet:
 # --------------------------------------------------------------------------
 
 DEFAULTS = dict(leaf_bytes=512, tau_leaf=900, tau_root=700, rho_leaf=100,
-                rho_root=300, grow_num=6, grow_den=5, build_pm=500, rebuild_pm=0, codec=0)
+                rho_root=300, grow_num=6, grow_den=5, build_pm=500, rebuild_pm=0, codec=0,
+                leaf_growth=0)
 
 
 class OracleError(RuntimeError):
@@ -296,7 +304,8 @@ class SeqCPMA:
         rc = lib().ocpma_create(C.byref(h), c["leaf_bytes"], c["tau_leaf"],
                                 c["tau_root"], c["rho_leaf"], c["rho_root"],
                                 c["grow_num"], c["grow_den"], c["build_pm"], c["codec"],
-                                k if k.size else np.zeros(1, np.uint64), k.size)
+                                c["leaf_growth"], k if k.size else np.zeros(1, np.uint64),
+                                k.size)
         if rc != 0:
             raise OracleError("ocpma_create failed: %d" % rc)
         self._h = h
@@ -355,8 +364,11 @@ class SeqCPMA:
         m = lib().ocpma_elements(self._h, out)
         return out[:m].copy()
 
+    def leaf_bytes(self) -> int:
+        return int(lib().ocpma_leaf_bytes(self._h))
+
     def layout(self):
-        L, LB = self.leaves(), self.cfg["leaf_bytes"]
+        L, LB = self.leaves(), self.leaf_bytes()
         data = np.zeros(L * LB, dtype=np.uint8)
         used = np.zeros(L, dtype=np.uint32)
         head = np.zeros(L, dtype=np.uint64)

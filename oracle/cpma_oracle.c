@@ -73,6 +73,14 @@
  *   R11 get_size (App. A): L * (LB + 16): the leaf array plus, per leaf, an
  *      8-byte head-index entry, a 4-byte used count and a 4-byte element
  *      count.
+ *   R13 leaf size (Sec. 5 "CPMA structure": leaves of Theta(log n) so that
+ *      the bounds hold; Sec. 6 space usage: the leaf size grows with the
+ *      number of elements; no formula is given): with leaf_growth = 0 the
+ *      leaf size is fixed; with leaf_growth = g > 0 every build (R10, R14)
+ *      and every resize (R9) first sets LB = min(2048, max(LB_min,
+ *      16 ceil(g bitlen(n) / 16))) for the n keys the array will hold
+ *      (bitlen(0) = 0); a resize then starts from the leaf count of equal
+ *      capacity, ceil(L * LB_old / LB), before growing or shrinking.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -292,7 +300,8 @@ size_t o_raw_leaf_decode(const uint8_t* leaf, uint64_t used, uint64_t* out) {
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-  uint32_t LB;
+  uint32_t LB;     /* leaf size in use */
+  uint32_t lb_min, leaf_growth; /* R13 */
   uint32_t tau_leaf, tau_root, rho_leaf, rho_root; /* permille */
   uint32_t grow_num, grow_den;
   uint32_t build_pm;
@@ -340,6 +349,17 @@ uint64_t o_build_leaves(uint64_t S, uint32_t LB, uint32_t build_pm) {
   u128 num = (u128)S * 1000, den = (u128)build_pm * LB - 8000;
   uint64_t L = (uint64_t)((num + den - 1) / den);
   return L < 1 ? 1 : L;
+}
+
+/* R13: leaf size for an array that will hold n keys. */
+uint32_t o_leaf_size(uint64_t n, uint32_t lb_min, uint32_t leaf_growth) {
+  if (leaf_growth == 0) return lb_min;
+  uint32_t bl = 0;
+  while (bl < 64 && (n >> bl) != 0) bl++;
+  uint64_t want = ((uint64_t)leaf_growth * bl + 15) / 16 * 16;
+  if (want < lb_min) want = lb_min;
+  if (want > 2048) want = 2048;
+  return (uint32_t)want;
 }
 
 /* R9: leaf count after a resize of a CPMA holding T bytes over L leaves. */
@@ -454,9 +474,10 @@ void ocpma_destroy(ocpma* o) {
 int ocpma_create(ocpma** out, uint32_t LB, uint32_t tau_leaf,
                  uint32_t tau_root, uint32_t rho_leaf, uint32_t rho_root,
                  uint32_t grow_num, uint32_t grow_den, uint32_t build_pm,
-                 uint32_t codec, const uint64_t* keys, uint64_t k) {
+                 uint32_t codec, uint32_t leaf_growth, const uint64_t* keys,
+                 uint64_t k) {
   *out = NULL;
-  if (codec > 1) return E_INVAL;
+  if (codec > 1 || leaf_growth > 2048) return E_INVAL;
   if (LB < 64 || LB % 16 || !(rho_leaf <= rho_root && rho_root < tau_root &&
                                tau_root <= tau_leaf && tau_leaf < 1000) ||
       grow_num <= grow_den || grow_den == 0 ||
@@ -464,6 +485,7 @@ int ocpma_create(ocpma** out, uint32_t LB, uint32_t tau_leaf,
       (uint64_t)(1000 - tau_leaf) * LB < 20000)
     return E_INVAL;
   ocpma* o = (ocpma*)calloc(1, sizeof(ocpma));
+  o->lb_min = LB; o->leaf_growth = leaf_growth;
   o->LB = LB; o->tau_leaf = tau_leaf; o->tau_root = tau_root;
   o->rho_leaf = rho_leaf; o->rho_root = rho_root;
   o->grow_num = grow_num; o->grow_den = grow_den; o->build_pm = build_pm;
@@ -471,6 +493,7 @@ int ocpma_create(ocpma** out, uint32_t LB, uint32_t tau_leaf,
   uint64_t* e = (uint64_t*)malloc((k ? k : 1) * sizeof(uint64_t));
   memcpy(e, keys, k * sizeof(uint64_t));
   size_t m = oset_sort_unique(e, k);
+  LB = o->LB = o_leaf_size(m, o->lb_min, o->leaf_growth); /* R13 */
   uint64_t L = o_build_leaves(leaf_bytes(o, e, m), LB, build_pm);
   int rc = alloc_arrays(L, LB, &o->data, &o->used, &o->head);
   if (rc == OK) {
@@ -512,11 +535,11 @@ static size_t leaf_content(const ocpma* o, const touched_t* T, size_t nT,
 void ocpma_set_rebuild(ocpma* o, uint32_t rebuild_pm) { o->rebuild_pm = rebuild_pm; }
 
 static int rebuild(ocpma* o, const uint64_t* keys, uint64_t k, int is_delete, uint64_t* delta) {
-  const uint32_t LB = o->LB;
+  const uint32_t LBold = o->LB;
   uint64_t* S = (uint64_t*)malloc((o->n + 1) * sizeof(uint64_t));
   size_t m = 0;
   for (uint64_t j = 0; j < o->L; j++)
-    m += leaf_decode(o, o->data + j * LB, o->used[j], S + m);
+    m += leaf_decode(o, o->data + j * LBold, o->used[j], S + m);
   uint64_t* U = (uint64_t*)malloc((k ? k : 1) * sizeof(uint64_t));
   memcpy(U, keys, k * sizeof(uint64_t));
   size_t ku = oset_sort_unique(U, k);
@@ -525,6 +548,7 @@ static int rebuild(ocpma* o, const uint64_t* keys, uint64_t k, int is_delete, ui
   *delta = is_delete ? (uint64_t)(m - mn) : (uint64_t)(mn - m);
   free(S);
   free(U);
+  const uint32_t LB = o_leaf_size(mn, o->lb_min, o->leaf_growth); /* R13 */
   uint64_t L = o_build_leaves(leaf_bytes(o, e, mn), LB, o->build_pm);
   uint8_t* d;
   uint32_t* u;
@@ -534,7 +558,7 @@ static int rebuild(ocpma* o, const uint64_t* keys, uint64_t k, int is_delete, ui
   free(e);
   if (rc != OK) return rc;
   free(o->data); free(o->used); free(o->head);
-  o->data = d; o->used = u; o->head = h; o->L = L; o->n = mn;
+  o->data = d; o->used = u; o->head = h; o->L = L; o->n = mn; o->LB = LB;
   fix_empty_heads(o);
   o->last_resized = 1; o->last_nwindows = 0; o->last_touched = 0;
   return OK;
@@ -623,18 +647,21 @@ static int update(ocpma* o, const uint64_t* keys, uint64_t k, int is_delete,
     /* R9: whole-array resize. */
     uint64_t Ttot = 0;
     for (uint64_t j = 0; j < L; j++) Ttot += bytes[j];
-    uint64_t Lp = o_resize_leaves(Ttot, L, LB, o->tau_root, o->rho_root,
-                                  o->grow_num, o->grow_den);
     uint64_t ntot = o->n + (is_delete ? -(int64_t)*delta : (int64_t)*delta);
+    /* R13: the leaf size for the new key count, from equal capacity */
+    const uint32_t LBp = o_leaf_size(ntot, o->lb_min, o->leaf_growth);
+    const uint64_t L0 = LBp == LB ? L : (L * LB + LBp - 1) / LBp;
+    uint64_t Lp = o_resize_leaves(Ttot, L0 ? L0 : 1, LBp, o->tau_root, o->rho_root,
+                                  o->grow_num, o->grow_den);
     buf = (uint64_t*)malloc((ntot + 1) * sizeof(uint64_t));
     size_t m = 0;
     for (uint64_t j = 0; j < L; j++) m += leaf_content(o, T, nT, tidx, j, buf + m);
     uint8_t* nd; uint32_t* nu; uint64_t* nh;
-    rc = alloc_arrays(Lp, LB, &nd, &nu, &nh);
+    rc = alloc_arrays(Lp, LBp, &nd, &nu, &nh);
     if (rc == OK) {
-      rc = spread(o->codec, nd, nu, nh, LB, 0, Lp, buf, m);
+      rc = spread(o->codec, nd, nu, nh, LBp, 0, Lp, buf, m);
       free(o->data); free(o->used); free(o->head);
-      o->data = nd; o->used = nu; o->head = nh; o->L = Lp;
+      o->data = nd; o->used = nu; o->head = nh; o->L = Lp; o->LB = LBp;
     }
     o->last_resized = 1;
     nw = 0;
@@ -734,6 +761,7 @@ uint64_t ocpma_sum(const ocpma* o) {
 
 uint64_t ocpma_size(const ocpma* o) { return o->n; }
 uint64_t ocpma_leaves(const ocpma* o) { return o->L; }
+uint32_t ocpma_leaf_bytes(const ocpma* o) { return o->LB; }
 uint64_t ocpma_bytes(const ocpma* o) { return o->L * ((uint64_t)o->LB + 16); }
 
 /* All elements in order; returns the count. */

@@ -22,7 +22,12 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-CPMA_OK, CPMA_EINVAL, CPMA_ENOMEM, CPMA_ECUDA, CPMA_EINTERNAL = 0, -1, -2, -3, -4
+CPMA_OK, CPMA_EINVAL, CPMA_ENOMEM, CPMA_ECUDA, CPMA_EINTERNAL, CPMA_ETIMEOUT = 0, -1, -2, -3, -4, -5
+
+# device memory callbacks of cpma_config: alloc(bytes, stream, ctx) -> pointer
+# (NULL when it cannot), free(pointer, stream, ctx)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
 
 class CPMAError(RuntimeError):
@@ -35,7 +40,9 @@ class CPMAError(RuntimeError):
 class cpma_config(C.Structure):
     _fields_ = [(n, C.c_uint32) for n in (
         "leaf_bytes", "tau_leaf", "tau_root", "rho_leaf", "rho_root", "grow_num",
-        "grow_den", "build_pm", "rebuild_pm", "codec")]
+        "grow_den", "build_pm", "rebuild_pm", "codec", "leaf_growth", "reserved")] + [
+        ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
+        ("mem_budget_bytes", C.c_uint64)]
 
 
 def lib():
@@ -82,6 +89,11 @@ def lib():
                 "cpma_range_extract": (I, [V, V, V, U64, V, V, U64, V]),
                 "cpma_use_graphs": (I, [V, U64]),
                 "cpma_graph_stats": (I, [V, P64, P64]),
+                "cpma_leaf_bytes": (I, [V, P64]),
+                "cpma_mem_held": (I, [V, P64]),
+                "cpma_mem_peak": (I, [V, P64]),
+                "cpma_set_mem_budget": (I, [V, U64]),
+                "cpma_test_sort_stall": (I, [V, C.c_uint32, C.c_int64]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -119,10 +131,12 @@ def to_u64(t: torch.Tensor) -> np.ndarray:
 
 
 def default_config(**overrides) -> cpma_config:
+    """The library's defaults with some fields replaced; alloc / free take
+    ALLOC_FN / FREE_FN objects (the caller keeps them alive)."""
     c = cpma_config()
     lib().cpma_default_config(C.byref(c))
     for k, v in overrides.items():
-        setattr(c, k, int(v))
+        setattr(c, k, v if k in ("alloc", "free", "alloc_ctx") else int(v))
     return c
 
 
@@ -325,6 +339,27 @@ def cpma_leaves(h) -> int:
     return _u64_out(lib().cpma_leaves, h, "cpma_leaves")
 
 
+def cpma_leaf_bytes(h) -> int:
+    return _u64_out(lib().cpma_leaf_bytes, h, "cpma_leaf_bytes")
+
+
+def cpma_mem_held(h) -> int:
+    return _u64_out(lib().cpma_mem_held, h, "cpma_mem_held")
+
+
+def cpma_mem_peak(h) -> int:
+    return _u64_out(lib().cpma_mem_peak, h, "cpma_mem_peak")
+
+
+def cpma_set_mem_budget(h, nbytes: int):
+    _check(lib().cpma_set_mem_budget(h, int(nbytes)), "cpma_set_mem_budget")
+
+
+def cpma_test_sort_stall(h, poll_limit: int, silent_tile: int):
+    _check(lib().cpma_test_sort_stall(h, int(poll_limit), int(silent_tile)),
+           "cpma_test_sort_stall")
+
+
 def cpma_stats(h) -> int:
     return _u64_out(lib().cpma_stats, h, "cpma_stats")
 
@@ -374,8 +409,10 @@ def cpma_profile_read(h) -> dict:
             for i, p in enumerate(PHASES)}
 
 
-def cpma_export_layout(h, leaf_bytes: int, stream=None, device="cuda"):
+def cpma_export_layout(h, leaf_bytes: int | None = None, stream=None, device="cuda"):
     L = cpma_leaves(h)
+    if leaf_bytes is None:
+        leaf_bytes = cpma_leaf_bytes(h)
     data = torch.empty(L * leaf_bytes, dtype=torch.uint8, device=device)
     used = torch.empty(L, dtype=torch.int32, device=device)
     heads = torch.empty(L, dtype=torch.int64, device=device)
@@ -450,7 +487,19 @@ class CPMA:
         return cpma_leaves(self._h)
 
     def layout(self, stream=None):
-        return cpma_export_layout(self._h, self.config.leaf_bytes, stream)
+        return cpma_export_layout(self._h, None, stream)
+
+    def leaf_bytes(self) -> int:
+        return cpma_leaf_bytes(self._h)
+
+    def mem_held(self) -> int:
+        return cpma_mem_held(self._h)
+
+    def mem_peak(self) -> int:
+        return cpma_mem_peak(self._h)
+
+    def set_mem_budget(self, nbytes: int):
+        cpma_set_mem_budget(self._h, nbytes)
 
     def launches(self) -> int:
         return cpma_stats(self._h)

@@ -1,5 +1,6 @@
 // C ABI of the CPMA library (declared in include/cpma.h): handle lifecycle,
 // argument checks and the dispatch to the update and query launchers.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -22,33 +23,86 @@ thread_local bool g_capturing = false;
 
 void set_capturing(bool on) { g_capturing = on; }
 
-int ensure(Buf& b, size_t bytes) {
+int dev_alloc(cpma* h, void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  if (h->no_alloc || g_capturing) return CPMA_EINTERNAL;
+  if (bytes == 0) bytes = 16;
+  const uint64_t budget = h->cfg.mem_budget_bytes;
+  if (budget && (h->mem_held > budget || bytes > budget - h->mem_held)) return CPMA_ENOMEM;
+  if (h->cfg.alloc) {
+    *p = h->cfg.alloc(bytes, (cpma_stream_t)st, h->cfg.alloc_ctx);
+    if (!*p) return CPMA_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(*p) & 15u) {  // vector loads need 16-byte alignment
+      h->cfg.free(*p, (cpma_stream_t)st, h->cfg.alloc_ctx);
+      *p = nullptr;
+      return CPMA_EINVAL;
+    }
+  } else if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return CPMA_ENOMEM;
+  }
+  h->mem_held += bytes;
+  h->mem_peak = std::max(h->mem_peak, h->mem_held);
+  return CPMA_OK;
+}
+
+void dev_free(cpma* h, void* p, size_t bytes, cudaStream_t st) {
+  if (!p) return;
+  if (bytes == 0) bytes = 16;
+  if (h->cfg.free) h->cfg.free(p, (cpma_stream_t)st, h->cfg.alloc_ctx);
+  else cudaFree(p);
+  h->mem_held -= bytes;
+}
+
+int ensure(cpma* h, Buf& b, size_t bytes, cudaStream_t st) {
   if (bytes == 0) bytes = 16;
   if (b.cap >= bytes) return CPMA_OK;
-  if (g_capturing) return CPMA_EINTERNAL;
+  if (h->no_alloc || g_capturing) return CPMA_EINTERNAL;
   size_t want = std::max(bytes, b.cap + b.cap / 2);
   want = (want + 255) & ~(size_t)255;
   if (b.p) {
     // growth only: the old contents are dead, but queued kernels may still
     // read them
     if (cudaDeviceSynchronize() != cudaSuccess) return CPMA_ECUDA;
-    cudaFree(b.p);
+    dev_free(h, b.p, b.cap, st);
     b.p = nullptr;
     b.cap = 0;
   }
-  if (cudaMalloc(&b.p, want) != cudaSuccess) {
-    cudaGetLastError();
-    b.p = nullptr;
-    return CPMA_ENOMEM;
+  int rc = dev_alloc(h, &b.p, want, st);
+  if (rc == CPMA_ENOMEM && want > bytes) {  // without the growth slack
+    want = (bytes + 255) & ~(size_t)255;
+    rc = dev_alloc(h, &b.p, want, st);
   }
+  if (rc != CPMA_OK) return rc;
   b.cap = want;
   return CPMA_OK;
 }
 
-void release(Buf& b) {
-  if (b.p) cudaFree(b.p);
+void release(cpma* h, Buf& b) {
+  dev_free(h, b.p, b.cap, nullptr);
   b.p = nullptr;
   b.cap = 0;
+}
+
+int alloc_arrays(cpma* h, uint64_t leaves, uint64_t data_bytes, Arrays* a, cudaStream_t st) {
+  *a = Arrays{};
+  int rc = dev_alloc(h, (void**)&a->data, data_bytes, st);
+  if (rc == CPMA_OK) rc = dev_alloc(h, (void**)&a->used, leaves * 4, st);
+  if (rc == CPMA_OK) rc = dev_alloc(h, (void**)&a->cnt, leaves * 4, st);
+  if (rc == CPMA_OK) rc = dev_alloc(h, (void**)&a->heads, (leaves + 1) * 8, st);
+  a->cap_leaves = leaves;
+  a->cap_bytes = data_bytes;
+  if (rc != CPMA_OK) free_arrays(h, a);
+  return rc;
+}
+
+void free_arrays(cpma* h, Arrays* a) {
+  dev_free(h, a->data, a->cap_bytes, nullptr);
+  dev_free(h, a->used, a->cap_leaves * 4, nullptr);
+  dev_free(h, a->cnt, a->cap_leaves * 4, nullptr);
+  dev_free(h, a->heads, (a->cap_leaves + 1) * 8, nullptr);
+  *a = Arrays{};
 }
 
 int sync_status(cpma* h, cudaStream_t st) {
@@ -210,6 +264,8 @@ int validate(const cpma_config& c) {
   if (c.grow_den == 0 || c.grow_num <= c.grow_den) return CPMA_EINVAL;
   if (c.codec > 1) return CPMA_EINVAL;
   if ((uint64_t)c.build_pm * c.leaf_bytes <= 8000 || c.build_pm > c.tau_root) return CPMA_EINVAL;
+  if (c.leaf_growth > 2048 || c.reserved) return CPMA_EINVAL;
+  if ((c.alloc == nullptr) != (c.free == nullptr)) return CPMA_EINVAL;
   return CPMA_OK;
 }
 
@@ -218,18 +274,24 @@ void release_all(cpma* h) {
   for (Buf* b : {&s.keysA, &s.keysB, &s.valsA, &s.valsB, &s.hist, &s.flags, &s.flags_scan, &s.leaf_of,
                  &s.chunk_begin, &s.chunk_leaf, &s.chunk_tid, &s.chunk_cnt, &s.chunk_off,
                  &s.T_leaf, &s.T_begin, &s.T_first_chunk, &s.T_oldcnt, &s.T_oldused, &s.T_newcnt,
-                 &s.T_newbytes, &s.T_state, &s.viol, &s.list_lane, &s.list_v1, &s.list_gen, &s.cand, &s.wins, &s.bits, &s.prefix, &s.ovf,
-                 &s.E, &s.cost, &s.C, &s.srccnt, &s.srcoff, &s.dstart, &s.win_src, &s.win_dst,
-                 &s.win_leaf_off, &s.win_elem_off, &s.win_dst_off, &s.partials, &s.partials_q, &s.q_first,
-                 &s.q_items, &s.q_off, &s.stage, &s.q_lo, &s.q_hi, &s.q_rank, &s.fh})
-    release(*b);
+                 &s.T_newbytes, &s.T_state, &s.viol, &s.list_lane, &s.list_v1, &s.list_gen, &s.cand,
+                 &s.wins, &s.bits, &s.prefix, &s.E, &s.cost, &s.C, &s.srccnt, &s.srcoff, &s.dstart,
+                 &s.win_src, &s.win_dst, &s.win_leaf_off, &s.win_elem_off, &s.win_dst_off,
+                 &s.partials, &s.partials_q, &s.q_first, &s.q_items, &s.q_off, &s.stage, &s.q_lo,
+                 &s.q_hi, &s.q_rank, &s.fh})
+    release(h, *b);
   prof_resolve(h);  // before the graphs (and their events) go
   graph_cache_free(h);
-  cudaFree(h->data);
-  cudaFree(h->used);
-  cudaFree(h->cnt);
-  cudaFree(h->heads);
-  cudaFree(h->d_status);
+  Arrays cur;
+  cur.data = h->data;
+  cur.used = h->used;
+  cur.cnt = h->cnt;
+  cur.heads = h->heads;
+  cur.cap_leaves = h->cap_leaves;
+  cur.cap_bytes = h->cap_bytes;
+  free_arrays(h, &cur);
+  free_arrays(h, &h->spare);
+  dev_free(h, h->d_status, sizeof(Status), nullptr);
   if (h->h_status) cudaFreeHost(h->h_status);
   prof_resolve(h);
   for (int i = 0; i < h->prof.npool; i++) cudaEventDestroy(h->prof.pool[i]);
@@ -241,12 +303,13 @@ void release_all(cpma* h) {
   h->prof.pool = nullptr;
   h->prof.pending = nullptr;
   h->prof.npool = h->prof.pool_cap = h->prof.npending = h->prof.cap = 0;
-  if (h->prof.d_bytes) cudaFree(h->prof.d_bytes);
+  dev_free(h, h->prof.d_bytes, sizeof(unsigned long long) * PH_N, nullptr);
   h->prof.d_bytes = nullptr;
   h->data = nullptr;
   h->used = nullptr;
   h->cnt = nullptr;
   h->heads = nullptr;
+  h->cap_leaves = h->cap_bytes = 0;
   h->d_status = nullptr;
   h->h_status = nullptr;
 }
@@ -266,8 +329,13 @@ int new_handle(const cpma_config* cfg, cpma** out) {
     delete h;
     return CPMA_ECUDA;
   }
-  if (cudaMalloc(&h->d_status, sizeof(Status)) != cudaSuccess ||
-      cudaMallocHost(&h->h_status, sizeof(Status)) != cudaSuccess) {
+  h->lb_min = c.leaf_bytes;
+  int rc = dev_alloc(h, (void**)&h->d_status, sizeof(Status), nullptr);
+  if (rc != CPMA_OK) {
+    delete h;
+    return rc;
+  }
+  if (cudaMallocHost(&h->h_status, sizeof(Status)) != cudaSuccess) {
     cudaGetLastError();
     release_all(h);
     delete h;
@@ -297,6 +365,12 @@ void cpma_default_config(cpma_config* c) {
   c->build_pm = 500;
   c->rebuild_pm = 0;
   c->codec = 0;
+  c->leaf_growth = 0;
+  c->reserved = 0;
+  c->alloc = nullptr;
+  c->free = nullptr;
+  c->alloc_ctx = nullptr;
+  c->mem_budget_bytes = 0;
 }
 
 int cpma_create(cpma_t** out, const cpma_config* cfg, const uint64_t* d_keys, uint64_t n,
@@ -308,7 +382,7 @@ int cpma_create(cpma_t** out, const cpma_config* cfg, const uint64_t* d_keys, ui
   cudaStream_t st = (cudaStream_t)stream;
   int rc = CPMA_OK;
   do {
-    rc = ensure(h->s.E, (n + 1) * 8);
+    rc = ensure(h, h->s.E, (n + 1) * 8);
     if (rc) break;
     uint64_t nu = 0;
     if (n) {
@@ -346,23 +420,29 @@ int cpma_clone(const cpma_t* src, cpma_t** out, cpma_stream_t stream) {
   *out = nullptr;
   cpma* h = nullptr;
   CPMA_TRY(new_handle(&src->cfg, &h));
+  h->lb_min = src->lb_min;
   cudaStream_t st = (cudaStream_t)stream;
   const uint64_t L = src->L, LB = src->cfg.leaf_bytes;
-  if (cudaMalloc(&h->data, L * LB) != cudaSuccess || cudaMalloc(&h->used, L * 4) != cudaSuccess ||
-      cudaMalloc(&h->cnt, L * 4) != cudaSuccess ||
-      cudaMalloc(&h->heads, (L + 1) * 8) != cudaSuccess) {
-    cudaGetLastError();
+  Arrays a;
+  int rc = alloc_arrays(h, L, L * LB, &a, st);
+  if (rc != CPMA_OK) {
     release_all(h);
     delete h;
-    return CPMA_ENOMEM;
+    return rc;
   }
-  int rc = CPMA_OK;
+  h->data = a.data;
+  h->used = a.used;
+  h->cnt = a.cnt;
+  h->heads = a.heads;
+  h->cap_leaves = a.cap_leaves;
+  h->cap_bytes = a.cap_bytes;
   rc |= check_cuda(cudaMemcpyAsync(h->data, src->data, L * LB, cudaMemcpyDeviceToDevice, st));
   rc |= check_cuda(cudaMemcpyAsync(h->used, src->used, L * 4, cudaMemcpyDeviceToDevice, st));
   rc |= check_cuda(cudaMemcpyAsync(h->cnt, src->cnt, L * 4, cudaMemcpyDeviceToDevice, st));
   rc |= check_cuda(cudaMemcpyAsync(h->heads, src->heads, (L + 1) * 8, cudaMemcpyDeviceToDevice,
                                    st));
-  rc |= check_cuda(cudaMemcpyAsync(&h->d_status->empties, &src->d_status->empties, 8,
+  // the empty-leaf count and the byte total (the two fields after it)
+  rc |= check_cuda(cudaMemcpyAsync(&h->d_status->empties, &src->d_status->empties, 16,
                                    cudaMemcpyDeviceToDevice, st));
   if (rc != CPMA_OK) {
     cudaStreamSynchronize(st);
@@ -373,6 +453,8 @@ int cpma_clone(const cpma_t* src, cpma_t** out, cpma_stream_t stream) {
   h->L = L;
   h->n = src->n;
   h->may_have_empty = src->may_have_empty;
+  h->t_known = src->t_known;
+  h->t_slack = src->t_slack;
   *out = h;
   return CPMA_OK;
 }
@@ -482,6 +564,37 @@ int cpma_leaves(const cpma_t* h, uint64_t* out) {
   return CPMA_OK;
 }
 
+int cpma_leaf_bytes(const cpma_t* h, uint64_t* out) {
+  if (!h || !out) return CPMA_EINVAL;
+  *out = h->cfg.leaf_bytes;
+  return CPMA_OK;
+}
+
+int cpma_mem_held(const cpma_t* h, uint64_t* out) {
+  if (!h || !out) return CPMA_EINVAL;
+  *out = h->mem_held;
+  return CPMA_OK;
+}
+
+int cpma_mem_peak(const cpma_t* h, uint64_t* out) {
+  if (!h || !out) return CPMA_EINVAL;
+  *out = h->mem_peak;
+  return CPMA_OK;
+}
+
+int cpma_set_mem_budget(cpma_t* h, uint64_t bytes) {
+  if (!h) return CPMA_EINVAL;
+  h->cfg.mem_budget_bytes = bytes;
+  return CPMA_OK;
+}
+
+int cpma_test_sort_stall(cpma_t* h, uint32_t poll_limit, int64_t silent_tile) {
+  if (!h) return CPMA_EINVAL;
+  h->sort_poll_limit = poll_limit;
+  h->sort_silent_tile = silent_tile < 0 ? -1 : silent_tile;
+  return CPMA_OK;
+}
+
 int cpma_export_layout(const cpma_t* h, uint8_t* d_data, uint32_t* d_used, uint64_t* d_heads,
                        cpma_stream_t stream) {
   if (!h) return CPMA_EINVAL;
@@ -506,10 +619,10 @@ int cpma_reserve(cpma_t* h, uint64_t max_batch, uint64_t max_queries, int tagged
   CPMA_TRY(reserve(h, max_batch, tagged, (cudaStream_t)stream));
   if (max_queries) {
     Scratch& s = h->s;
-    CPMA_TRY(ensure(s.q_first, max_queries * 8));
-    CPMA_TRY(ensure(s.q_items, max_queries * 8));
-    CPMA_TRY(ensure(s.q_off, (max_queries + 1) * 8));
-    CPMA_TRY(ensure(s.partials_q, (size_t)(2 * h->num_sms + 2) * 8));
+    CPMA_TRY(ensure(h, s.q_first, max_queries * 8));
+    CPMA_TRY(ensure(h, s.q_items, max_queries * 8));
+    CPMA_TRY(ensure(h, s.q_off, (max_queries + 1) * 8));
+    CPMA_TRY(ensure(h, s.partials_q, (size_t)(2 * h->num_sms + 2) * 8));
   }
   return CPMA_OK;
 }
@@ -538,13 +651,7 @@ int cpma_profile(cpma_t* h, int enable) {
   if (cudaDeviceSynchronize() != cudaSuccess) return CPMA_ECUDA;
   prof_resolve(h);
   Prof& p = h->prof;
-  if (!p.d_bytes) {
-    if (cudaMalloc(&p.d_bytes, sizeof(unsigned long long) * PH_N) != cudaSuccess) {
-      cudaGetLastError();
-      p.d_bytes = nullptr;
-      return CPMA_ENOMEM;
-    }
-  }
+  if (!p.d_bytes) CPMA_TRY(dev_alloc(h, (void**)&p.d_bytes, sizeof(unsigned long long) * PH_N, nullptr));
   CPMA_CUDA(cudaMemset(p.d_bytes, 0, sizeof(unsigned long long) * PH_N));
   for (int i = 0; i < PH_N; i++) { p.ms[i] = 0; p.calls[i] = 0; p.host_bytes[i] = 0; }
   p.on = enable != 0;
@@ -581,6 +688,7 @@ const char* cpma_strerror(int code) {
     case CPMA_ENOMEM: return "out of device or host memory";
     case CPMA_ECUDA: return "CUDA error";
     case CPMA_EINTERNAL: return "device-side consistency check failed";
+    case CPMA_ETIMEOUT: return "a bounded device-side wait gave up";
     default: return "unknown error";
   }
 }

@@ -38,6 +38,8 @@ struct Status {
   ull pad[10];
   ull empties;     // empty leaves in the structure (written by the head
                    // fix-up; not cleared at the start of a batch)
+  ull bytes_total; // used bytes over all leaves, kept exact by the merge,
+                   // redistribution and build kernels (not cleared either)
 };
 
 constexpr ull kErrUnsorted = 1;   // a batch promised sorted was not
@@ -57,6 +59,17 @@ struct Buf {
   size_t cap = 0;
 };
 
+// Leaf arrays: data (leaves x LB bytes), used, cnt, heads (leaves + 1), with
+// the capacity they were allocated for.
+struct Arrays {
+  uint8_t* data = nullptr;
+  uint32_t* used = nullptr;
+  uint32_t* cnt = nullptr;
+  uint64_t* heads = nullptr;
+  uint64_t cap_leaves = 0;   // entries of used / cnt (heads: one more)
+  uint64_t cap_bytes = 0;    // bytes of data
+};
+
 struct Scratch {
   Buf keysA, keysB;       // sort ping-pong (u64)
   Buf valsA, valsB;       // sort ping-pong of 32-bit tags
@@ -70,8 +83,8 @@ struct Scratch {
   Buf list_lane, list_v1, list_gen;  // merge work lists
   Buf bits;               // per-level window bitsets (u32 words)
   Buf prefix;             // prefix sums of used bytes (u64, L+1)
-  Buf ovf;                // overflow elements (u64)
-  Buf E, cost, C;         // redistribution: elements, costs, cost prefix
+  Buf E, cost, C;         // redistribution: elements, costs, cost prefix; C also holds
+                          // the overflow elements of pending leaves until the pack
   Buf srccnt, srcoff, dstart;
   Buf win_src, win_dst, win_leaf_off, win_elem_off, win_dst_off;
   Buf partials;           // scan partials (update path)
@@ -118,7 +131,8 @@ struct Prof {
 }  // namespace cpmaimpl
 
 struct cpma {
-  cpma_config cfg;
+  cpma_config cfg;       // cfg.leaf_bytes is the leaf size in use
+  uint32_t lb_min = 0;   // the configured leaf size (smallest with leaf_growth)
   int device = 0;
   int num_sms = 0;
   uint64_t L = 0;        // leaves
@@ -127,6 +141,19 @@ struct cpma {
   uint32_t* used = nullptr;
   uint32_t* cnt = nullptr;
   uint64_t* heads = nullptr;       // L + 1 entries; heads[L] = last non-empty leaf
+  uint64_t cap_leaves = 0, cap_bytes = 0;  // capacity of the arrays above
+  cpmaimpl::Arrays spare;          // arrays kept for a resize the next update may need
+  // memory: bytes held (structure, spare arrays, scratch, status), and a
+  // flag that makes every allocation fail (set while an update is changing
+  // the structure: everything it needs was reserved before)
+  uint64_t mem_held = 0, mem_peak = 0;
+  bool no_alloc = false;
+  // used bytes over all leaves: exact after the last merge (t_known) and a
+  // bound on how much the redistribution after it changed them (t_slack)
+  uint64_t t_known = 0, t_slack = 0;
+  // batch sort look-back (tests): poll limit (0 = default), silent tile (-1 = none)
+  uint32_t sort_poll_limit = 0;
+  int64_t sort_silent_tile = -1;
   uint64_t bits_words = 0;          // words of the window bitsets now zeroed
   bool may_have_empty = false;      // some leaf may be empty (head fix-up)
   cpmaimpl::Status* d_status = nullptr;
@@ -148,10 +175,17 @@ struct cpma {
 
 namespace cpmaimpl {
 
-// memory.  ensure() grows a buffer (never shrinks).  While a graph is being
-// captured on this thread it refuses to allocate (CPMA_EINTERNAL) instead.
-int ensure(Buf& b, size_t bytes);
-void release(Buf& b);
+// memory.  Every device allocation goes through dev_alloc / dev_free: the
+// configured allocator (or cudaMalloc / cudaFree), the memory budget, and the
+// handle's count of bytes held.  ensure() grows a buffer (never shrinks).
+// While a graph is being captured on this thread, or while h->no_alloc is
+// set, it refuses to allocate (CPMA_EINTERNAL) instead.
+int dev_alloc(cpma* h, void** p, size_t bytes, cudaStream_t st);
+void dev_free(cpma* h, void* p, size_t bytes, cudaStream_t st);
+int ensure(cpma* h, Buf& b, size_t bytes, cudaStream_t st = nullptr);
+void release(cpma* h, Buf& b);
+int alloc_arrays(cpma* h, uint64_t leaves, uint64_t data_bytes, Arrays* a, cudaStream_t st);
+void free_arrays(cpma* h, Arrays* a);
 void set_capturing(bool on);
 
 // update.cu: graph cache and scratch reservation

@@ -3,17 +3,23 @@
 // deltas to the following keys as unsigned LEB128 codes, packed left, zero
 // bytes after the used ones).
 //
-// One thread owns one leaf.  Pass A decodes the leaf byte by byte and places
-// every key of the slice: before the head (a new head), inside the gap that
-// one code spans (the code is split), or after the last element (appended);
-// a key equal to an element or to the slice key before it is skipped.  Keys
-// sharing a gap form one edit: old bytes [os, oe) replaced by nl new bytes.
-// Every edit of an insert grows or keeps the size (a split code never needs
-// more bytes than its two parts), so pass B rewrites the leaf in place from
-// the end backwards, 16 bytes at a time: each destination chunk gathers the
-// old bytes that land in it (one shift per segment between edits) and is
+// One thread owns one leaf.  Pass A sums the leaf 16 bytes at a time with
+// word-parallel arithmetic (each byte's position inside its code from the
+// continuation flags of the bytes before it, then two dot products per word
+// with byte weights 1 / 128 and 2^14 / 2^21), recording for every key of
+// the slice the chunk it lands in; those chunks are then decoded byte by
+// byte to place each key: before the head (a new head), inside the gap that one code spans
+// (the code is split), or after the last element (appended); a key equal to
+// an element or to the slice key before it is skipped.  Keys sharing a gap
+// form one edit: old bytes [os, oe) replaced by nl new bytes.  Every edit of
+// an insert grows or keeps the size (a split code never needs more bytes
+// than its two parts), so pass B rewrites the leaf in place from the end
+// backwards, 16 bytes at a time: each destination chunk gathers the old
+// bytes that land in it (one shift per segment between edits; a chunk wholly
+// inside the segment after the last edit is one shifted 16-byte read) and is
 // stored whole, before the edits' own bytes are written.  Every read of pass
-// B is of a chunk at or below the one being written, so it sees old bytes.
+// B is of a chunk at or below the one being written, so it sees old bytes
+// (a delete shrinks: forward, reads at or above).
 //
 // The functions are __host__ __device__ so that the same code can be run on
 // the host.
@@ -47,7 +53,6 @@ constexpr uint32_t kUnchanged = 0;  // every key present: nothing written
 constexpr uint32_t kWritten = 1;    // leaf rewritten in place
 constexpr uint32_t kTooBig = 2;     // result exceeds the leaf: nothing written
 constexpr uint32_t kLongCode = 3;   // a code of more than 4 bytes: nothing written
-constexpr uint32_t kBadCount = 4;   // decoded count differs from the stored one
 
 struct Result {
   uint32_t nb;       // new used bytes
@@ -64,6 +69,31 @@ LT_HD uint32_t fshr(uint32_t lo, uint32_t hi, uint32_t sh) {  // low word of (hi
   return __funnelshift_r(lo, hi, sh);
 #else
   return sh ? (lo >> sh) | (hi << (32u - sh)) : lo;
+#endif
+}
+
+LT_HD uint32_t fshl(uint32_t lo, uint32_t hi, uint32_t sh) {  // high word of (hi:lo) << sh, 0 < sh < 32
+#if defined(__CUDA_ARCH__)
+  return __funnelshift_l(lo, hi, sh);
+#else
+  return (hi << sh) | (lo >> (32u - sh));
+#endif
+}
+
+LT_HD uint32_t dp4a(uint32_t a, uint32_t b, uint32_t c) {  // c + sum of the four byte products
+#if defined(__CUDA_ARCH__)
+  return __dp4a(a, b, c);
+#else
+  for (int i = 0; i < 4; i++) c += ((a >> (8 * i)) & 0xFFu) * ((b >> (8 * i)) & 0xFFu);
+  return c;
+#endif
+}
+
+LT_HD uint32_t clz32(uint32_t x) {  // leading zeros, 32 for x == 0
+#if defined(__CUDA_ARCH__)
+  return (uint32_t)__clz((int)x);
+#else
+  return x ? (uint32_t)__builtin_clz(x) : 32u;
 #endif
 }
 
@@ -137,29 +167,29 @@ LT_HD uint32_t byte_of(uint32_t v, int i) {  // byte i of v, zero-extended
 #endif
 }
 
-// Pass A, step 1, over one 16-byte chunk (FIRST: the chunk holding the
-// head; its first 8 bytes are skipped).  Every byte adds its 7 payload bits
-// times pw = 128^(bytes of its code before it) to tot, so tot is the sum of
-// the codes completed so far in the chunk plus the open code's bits (tot
-// enters with the bits the open code got in earlier chunks); tt keeps tot as
-// of the last terminator.  pw is a power of two (or 0 once it wraps past a
-// fifth byte, harmlessly), so pwor, the OR of every pw, is >= 2^28 exactly
-// when some code has more than 4 bytes.
-template <bool FIRST>
-LT_HD void sum_chunk(const uint32_t (&w)[4], uint32_t& tot, uint32_t& tt, uint32_t& pw,
-                     uint32_t& pwor) {
-  uint32_t pm[4];
-#pragma unroll
-  for (int i = 0; i < 4; i++) pm[i] = w[i] & 0x7F7F7F7Fu;  // payload bits only
-#pragma unroll
-  for (int b = FIRST ? 8 : 0; b < 16; b++) {
-    const uint32_t wb = w[b >> 2];
-    tot += byte_of(pm[b >> 2], b & 3) * pw;
-    const bool term = (wb & (0x80u << (8 * (b & 3)))) == 0u;
-    pwor |= pw;
-    tt = term ? tot : tt;
-    pw = term ? 1u : pw << 7;
-  }
+// Pass A, step 1: the byte weights of one 4-byte word of codes.  cb, p1, p2
+// carry the flags of the word before (bit 7 of each byte): cb = the byte is
+// a continuation byte, p1 = the byte before it is one (its position g in its
+// code is >= 1), p2 = g >= 2.  A byte at position g weighs 128^g in the
+// value of its code, so the sum of the (partial) codes in the word is
+// dp4a(pay, w01) + 2^14 dp4a(pay, w23) with w01 = 1 / 128 for g = 0 / 1 and
+// w23 = 1 / 128 for g = 2 / 3 (0 elsewhere).  lc collects continuation
+// bytes at position >= 3: a code of more than 4 bytes, which the 32-bit
+// arithmetic does not cover.
+LT_HD uint32_t word_sum(uint32_t w, uint32_t& cb, uint32_t& p1, uint32_t& p2, uint32_t& lc,
+                        uint32_t& pay, uint32_t& w01, uint32_t& w23) {
+  const uint32_t c = w & 0x80808080u;
+  const uint32_t q1 = fshl(cb, c, 8);
+  const uint32_t q2 = q1 & fshl(p1, q1, 8);
+  const uint32_t q3 = q2 & fshl(p2, q2, 8);
+  lc |= q3 & c;
+  pay = w & 0x7F7F7F7Fu;
+  w01 = ((q1 ^ 0x80808080u) >> 7) | (q1 ^ q2);
+  w23 = ((q2 ^ q3) >> 7) | q3;
+  cb = c;
+  p1 = q1;
+  p2 = q2;
+  return dp4a(pay, w01, 0u) + (dp4a(pay, w23, 0u) << 14);
 }
 
 // Pass A, step 2: the codes of the chunk at p0 take keys q..q1-1 (all of
@@ -252,7 +282,8 @@ LT_HD void seg_bounds(const Scratch& S, uint32_t E, uint32_t uold, uint32_t os0,
 
 // Pass A: a record for every slice key (kind, code bytes, values; see
 // Scratch).  Returns kWritten when every key is placed (nothing is written),
-// else kLongCode or kBadCount.  head receives the leaf's first element.
+// else kLongCode (the leaf holds a code of more than 4 bytes).  head
+// receives the leaf's first element.
 constexpr uint32_t kPlaced = kWritten;
 LT_HD uint32_t pass_a(const uint8_t* leafp, uint32_t uold, uint32_t m, const uint64_t (&y)[kKeys],
                       uint32_t s, const Scratch& S, uint64_t& head) {
@@ -269,32 +300,32 @@ LT_HD uint32_t pass_a(const uint8_t* leafp, uint32_t uold, uint32_t m, const uin
     S.rcode[k * S.rs] = 0u;
     k++;
   }
-  // step 1: chunk sums; every key gets the chunk (p0, entry state) of the
-  // code it falls in, or stays for the end
+  // step 1: chunk sums over the whole leaf (a warp's threads then take the
+  // same number of steps); every key gets the chunk (p0, entry state) of
+  // the code it falls in, or stays for the end
   uint64_t ycur = k < s ? pick(y, k) : ~0ull;
   uint64_t val = head;
-  uint32_t carry = 0, pw = 1, pwor = 0, nterm = 0;
+  uint32_t carry = 0, lc = 0, cb = 0, p1 = 0, p2 = 0;
   for (uint32_t p0 = 0; p0 < uold; p0 += 16) {
-    if (p0) ld16(leafp + p0, w);
-    if (p0 + 16u > uold) {  // bytes past the used ones read as zero
-      const uint32_t keep = (1u << (uold - p0)) - 1u;
-#pragma unroll
-      for (int i = 0; i < 4; i++) w[i] &= bmask4((keep >> (4 * i)) & 0xFu);
-    }
-    // terminator bytes (zero bytes past uold included; subtracted below)
-    nterm += popc(~w[2] & 0x80808080u) + popc(~w[3] & 0x80808080u);
-    uint32_t tot = carry, tt = 0;
-    const uint32_t pw0 = pw;
+    if (p0) ld16(leafp + p0, w);  // bytes past the used ones are zero (packed left)
+    const uint32_t cb_in = cb;    // flags of the last word before p0
+    uint32_t tsum = 0, pay = 0, w01 = 0, w23 = 0;
     if (p0) {
-      nterm += popc(~w[0] & 0x80808080u) + popc(~w[1] & 0x80808080u);
-      sum_chunk<false>(w, tot, tt, pw, pwor);
-    } else {
-      sum_chunk<true>(w, tot, tt, pw, pwor);
+      tsum += word_sum(w[0], cb, p1, p2, lc, pay, w01, w23);
+      tsum += word_sum(w[1], cb, p1, p2, lc, pay, w01, w23);
     }
-    const uint64_t vend = val + tt;
+    tsum += word_sum(w[2], cb, p1, p2, lc, pay, w01, w23);
+    tsum += word_sum(w[3], cb, p1, p2, lc, pay, w01, w23);
+    // the code still open at the chunk end: the bytes of the last word after
+    // its last terminator (a code of at most 4 bytes has one there)
+    const uint32_t tw = ~cb & 0x80808080u;
+    const uint32_t ps = pay & (tw ? ~(0xFFFFFFFFu >> clz32(tw)) : 0xFFFFFFFFu);
+    const uint32_t cnew = dp4a(ps, w01, 0u) + (dp4a(ps, w23, 0u) << 14);
+    lc |= tw ? 0u : 1u;
+    const uint64_t vend = val + (uint32_t)(carry + tsum - cnew);
     if (vend >= ycur) {
-      // open code bytes at p0: pw0 = 128^g0
-      const uint32_t g0 = pw0 >= (1u << 21) ? 3u : pw0 >= (1u << 14) ? 2u : pw0 >= 128u ? 1u : 0u;
+      // bytes of the code open at p0 (trailing continuation bytes before it)
+      const uint32_t g0 = clz32(~cb_in & 0x80808080u) >> 3;
       while (k < s && ycur <= vend) {
         S.rpos[k * S.rs] = p0 | (g0 << 12) | (kChunk << 24);
         S.rval[k * S.rs] = val;
@@ -304,11 +335,9 @@ LT_HD uint32_t pass_a(const uint8_t* leafp, uint32_t uold, uint32_t m, const uin
       }
     }
     val = vend;
-    carry = tot - tt;
+    carry = cnew;
   }
-  if (pwor >= (1u << 28)) return kLongCode;
-  nterm -= ((uold + 15u) & ~15u) - uold;
-  if (nterm + 1u != m) return kBadCount;
+  if (lc) return kLongCode;
   // step 2: exact gaps inside the recorded chunks
   for (uint32_t q = 0; q < k; q++) {
     const uint32_t rp = S.rpos[q * S.rs];
@@ -399,6 +428,42 @@ LT_HD uint32_t plan_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, uint32_t m,
   return kWritten;
 }
 
+// The segment after the last edit: old bytes [oe, uold) land at [dlo, nb)
+// shifted by sa (nb = the new used bytes).
+LT_HD void tail_segment(const Scratch& S, uint32_t E, uint32_t uold, int32_t& dlo, int32_t& nb,
+                        int32_t& sa) {
+  seg_bounds(S, E, uold, S.epos[0] & 0xFFFu, (int)E - 1, dlo, nb, sa);
+}
+
+// The 16 bytes at leaf[src, src + 16) (0 <= src, src + 16 <= the old used
+// bytes): the aligned chunk below src and, unless src is aligned, the one
+// after it, shifted together.  A destination chunk wholly inside the
+// segment after the last edit is exactly this, with src = o - sa.
+LT_HD void chunk_tail(const uint8_t* leafp, int32_t src, uint32_t (&r)[4]) {
+  const int32_t A = src & ~15;
+  const uint32_t d = (uint32_t)(src - A);
+  uint32_t W[8];
+  uint32_t t[4];
+  ld16(leafp + A, t);
+  W[0] = t[0]; W[1] = t[1]; W[2] = t[2]; W[3] = t[3];
+  W[4] = W[5] = W[6] = W[7] = 0u;
+  if (d) {
+    ld16(leafp + A + 16, t);
+    W[4] = t[0]; W[5] = t[1]; W[6] = t[2]; W[7] = t[3];
+  }
+  // words q .. q + 4 of the 32 bytes (two selects per word), then the byte
+  // shift inside a word
+  const uint32_t q = d >> 2, s8 = 8u * (d & 3u);
+  uint32_t X[7];
+#pragma unroll
+  for (int i = 0; i < 7; i++) X[i] = (q & 1u) ? W[i + 1] : W[i];
+  uint32_t V[5];
+#pragma unroll
+  for (int i = 0; i < 5; i++) V[i] = (q & 2u) ? X[i + 2] : X[i];
+#pragma unroll
+  for (int i = 0; i < 4; i++) r[i] = fshr(V[i], V[i + 1], s8);
+}
+
 // Pass B by one thread: the chunks R.wlo .. R.whi of the leaf from the end
 // backwards, each gathered from the segments that land in it and stored
 // whole (the edits' own bytes are left zero: write_edits fills them).
@@ -407,8 +472,16 @@ LT_HD void rewrite_leaf(uint8_t* leafp, uint32_t LB, uint32_t uold, const Scratc
   const uint32_t E = R.E;
   const uint32_t os0 = S.epos[0] & 0xFFFu;
   const uint32_t olo = R.wlo, ohi = R.whi;
+  int32_t tlo, tnb, tsa;
+  tail_segment(S, E, uold, tlo, tnb, tsa);
   int cur = (int)E - 1;
   for (int32_t o = (int32_t)ohi - 16; o >= (int32_t)olo; o -= 16) {
+    if (o >= tlo && o + 16 <= tnb) {  // wholly inside the last segment
+      uint32_t r[4];
+      chunk_tail(leafp, o - tsa, r);
+      st16(leafp + o, r);
+      continue;
+    }
     for (;;) {  // the highest segment not wholly above chunk o
       int32_t dlo, dhi, sa;
       seg_bounds(S, E, uold, os0, cur, dlo, dhi, sa);
@@ -560,8 +633,16 @@ LT_HD void rewrite_forward(uint8_t* leafp, uint32_t LB, uint32_t uold, const Scr
                            const Result& R) {
   const uint32_t E = R.E;
   const uint32_t os0 = S.epos[0] & 0xFFFu;
+  int32_t tlo, tnb, tsa;
+  tail_segment(S, E, uold, tlo, tnb, tsa);
   int cur = -1;
   for (int32_t o = (int32_t)R.wlo; o < (int32_t)R.whi; o += 16) {
+    if (o >= tlo && o + 16 <= tnb) {  // wholly inside the last segment
+      uint32_t r[4];
+      chunk_tail(leafp, o - tsa, r);
+      st16(leafp + o, r);
+      continue;
+    }
     for (;;) {  // the lowest segment not wholly below chunk o
       int32_t dlo, dhi, sa;
       seg_bounds(S, E, uold, os0, cur, dlo, dhi, sa);

@@ -572,9 +572,9 @@ int run_range(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint64_t q,
               uint64_t* count, cudaStream_t st) {
   if (q == 0) return CPMA_OK;
   cpma* hm = const_cast<cpma*>(h);
-  CPMA_TRY(ensure(hm->s.q_first, q * 8));
-  CPMA_TRY(ensure(hm->s.q_items, q * 8));
-  CPMA_TRY(ensure(hm->s.q_off, (q + 1) * 8));
+  CPMA_TRY(ensure(hm, hm->s.q_first, q * 8));
+  CPMA_TRY(ensure(hm, hm->s.q_items, q * 8));
+  CPMA_TRY(ensure(hm, hm->s.q_off, (q + 1) * 8));
   uint64_t* first = (uint64_t*)hm->s.q_first.p;
   uint64_t* items = (uint64_t*)hm->s.q_items.p;
   uint64_t* off = (uint64_t*)hm->s.q_off.p;
@@ -612,12 +612,12 @@ int run_range_length(const cpma* h, const uint64_t* start, const uint64_t* lengt
   if (q == 0) return CPMA_OK;
   cpma* hm = const_cast<cpma*>(h);
   Scratch& s = hm->s;
-  CPMA_TRY(ensure(s.q_first, q * 8));
-  CPMA_TRY(ensure(s.q_items, q * 8));
-  CPMA_TRY(ensure(s.q_off, (q + 1) * 8));
-  CPMA_TRY(ensure(s.q_lo, q * 8));
-  CPMA_TRY(ensure(s.q_hi, q * 8));
-  CPMA_TRY(ensure(s.q_rank, (h->L + 1) * 8));
+  CPMA_TRY(ensure(hm, s.q_first, q * 8));
+  CPMA_TRY(ensure(hm, s.q_items, q * 8));
+  CPMA_TRY(ensure(hm, s.q_off, (q + 1) * 8));
+  CPMA_TRY(ensure(hm, s.q_lo, q * 8));
+  CPMA_TRY(ensure(hm, s.q_hi, q * 8));
+  CPMA_TRY(ensure(hm, s.q_rank, (h->L + 1) * 8));
   uint64_t* P = (uint64_t*)s.q_rank.p;
   uint64_t* r0 = (uint64_t*)s.q_lo.p;
   uint64_t* r1 = (uint64_t*)s.q_hi.p;
@@ -662,12 +662,12 @@ int run_range_extract(const cpma* h, const uint64_t* lo, const uint64_t* hi, uin
   if (q == 0) return check_cuda(cudaMemsetAsync(offsets, 0, 8, st));
   cpma* hm = const_cast<cpma*>(h);
   Scratch& s = hm->s;
-  CPMA_TRY(ensure(s.q_first, q * 8));
-  CPMA_TRY(ensure(s.q_items, (q + 1) * 8));
-  CPMA_TRY(ensure(s.q_off, (q + 1) * 8));
-  CPMA_TRY(ensure(s.q_lo, q * 8));
-  CPMA_TRY(ensure(s.q_hi, q * 8));
-  CPMA_TRY(ensure(s.q_rank, (h->L + 1) * 8));
+  CPMA_TRY(ensure(hm, s.q_first, q * 8));
+  CPMA_TRY(ensure(hm, s.q_items, (q + 1) * 8));
+  CPMA_TRY(ensure(hm, s.q_off, (q + 1) * 8));
+  CPMA_TRY(ensure(hm, s.q_lo, q * 8));
+  CPMA_TRY(ensure(hm, s.q_hi, q * 8));
+  CPMA_TRY(ensure(hm, s.q_rank, (h->L + 1) * 8));
   uint64_t* P = (uint64_t*)s.q_rank.p;
   uint64_t* r0 = (uint64_t*)s.q_lo.p;
   uint64_t* r1 = (uint64_t*)s.q_hi.p;
@@ -715,9 +715,9 @@ int run_range_reduce(const cpma* h, const uint64_t* lo, const uint64_t* hi, uint
     return run_range(h, lo, hi, q, out, count, st);
   if (q == 0) return CPMA_OK;
   cpma* hm = const_cast<cpma*>(h);
-  CPMA_TRY(ensure(hm->s.q_first, q * 8));
-  CPMA_TRY(ensure(hm->s.q_items, q * 8));
-  CPMA_TRY(ensure(hm->s.q_off, (q + 1) * 8));
+  CPMA_TRY(ensure(hm, hm->s.q_first, q * 8));
+  CPMA_TRY(ensure(hm, hm->s.q_items, q * 8));
+  CPMA_TRY(ensure(hm, hm->s.q_off, (q + 1) * 8));
   uint64_t* first = (uint64_t*)hm->s.q_first.p;
   uint64_t* items = (uint64_t*)hm->s.q_items.p;
   uint64_t* off = (uint64_t*)hm->s.q_off.p;

@@ -178,7 +178,7 @@ int scan_impl(cpma* h, const Tin* in, uint64_t* out, uint64_t n_host, const ull*
   }
   int G = (int)std::min<uint64_t>((uint64_t)2 * h->num_sms, std::max<uint64_t>(tiles, 1));
   Buf& pb = partials ? *partials : h->s.partials;
-  CPMA_TRY(ensure(pb, (size_t)(G + 1) * 8));
+  CPMA_TRY(ensure(h, pb, (size_t)(G + 1) * 8));
   uint64_t* part = (uint64_t*)pb.p;
   k_reduce<Tin><<<G, kT, 0, st>>>(in, n_host, n_dev, part);
   k_partials<<<1, 1024, 0, st>>>(part, G);

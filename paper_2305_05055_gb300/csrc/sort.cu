@@ -222,7 +222,8 @@ __global__ void __launch_bounds__(kT, 3) k_onesweep(const uint64_t* __restrict__
                                                  uint64_t* __restrict__ A, uint64_t* __restrict__ B,
                                                  uint32_t* __restrict__ VA, uint32_t* __restrict__ VB,
                                                  uint64_t k, int p, int top, int gate, SortCtl* ctl,
-                                                 uint32_t* __restrict__ look, Status* st) {
+                                                 uint32_t* __restrict__ look, Status* st,
+                                                 uint32_t spin_limit, uint32_t silent) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   TileSmemT<VALS>& sm = *reinterpret_cast<TileSmemT<VALS>*>(smem_raw);
   __shared__ uint32_t s_tile;
@@ -275,11 +276,12 @@ __global__ void __launch_bounds__(kT, 3) k_onesweep(const uint64_t* __restrict__
     const int d = threadIdx.x;
     const uint32_t cnt = (d < 255 ? sm.dstart[d + 1] : nvalid) - sm.dstart[d];
     volatile uint32_t* lk = look + (size_t)tile * 256;
+    const bool publish = tile != silent;  // a silent tile (tests only) never publishes
     if (tile == 0) {
-      lk[d] = kFlagP | cnt;
+      if (publish) lk[d] = kFlagP | cnt;
       s_excl[d] = 0;
     } else {
-      lk[d] = kFlagA | cnt;
+      if (publish) lk[d] = kFlagA | cnt;
       uint32_t excl = 0;
       bool done = false;
       const volatile uint32_t* lv = look;
@@ -293,11 +295,11 @@ __global__ void __launch_bounds__(kT, 3) k_onesweep(const uint64_t* __restrict__
         for (int i = 0; i < kLook; i++) {
           if (done || tp < i) break;
           uint32_t spins = 0;
-          while (!(v[i] & (kFlagA | kFlagP)) && spins < kSpinLimit) {
+          while (!(v[i] & (kFlagA | kFlagP)) && spins < spin_limit) {
             v[i] = lv[(size_t)(tp - i) * 256 + d];
             spins++;
           }
-          if (spins >= kSpinLimit) {  // a predecessor never published: give up
+          if (spins >= spin_limit) {  // a predecessor never published: give up
             atomicOr(&st->err, kErrSort);
             done = true;
             break;
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(kT, 3) k_onesweep(const uint64_t* __restrict__
         }
       }
       __threadfence();
-      lk[d] = kFlagP | (excl + cnt);
+      if (publish) lk[d] = kFlagP | (excl + cnt);
       s_excl[d] = excl;
     }
     __syncthreads();
@@ -491,12 +493,12 @@ int sort_scratch(cpma* h, uint64_t k, bool vals) {
   sort_attrs<false>();
   if (vals) sort_attrs<true>();
   if (k <= 1) return CPMA_OK;
-  CPMA_TRY(ensure(h->s.keysA, k * 8));
-  if (vals) CPMA_TRY(ensure(h->s.valsA, k * 4));
+  CPMA_TRY(ensure(h, h->s.keysA, k * 8));
+  if (vals) CPMA_TRY(ensure(h, h->s.valsA, k * 4));
   if (k <= (uint64_t)kTile) return CPMA_OK;
-  CPMA_TRY(ensure(h->s.keysB, k * 8));
-  if (vals) CPMA_TRY(ensure(h->s.valsB, k * 4));
-  return ensure(h->s.hist, ctl_bytes() + look_bytes(k));
+  CPMA_TRY(ensure(h, h->s.keysB, k * 8));
+  if (vals) CPMA_TRY(ensure(h, h->s.valsB, k * 4));
+  return ensure(h, h->s.hist, ctl_bytes() + look_bytes(k));
 }
 
 template <bool VALS>
@@ -520,6 +522,10 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
   uint64_t* B = (uint64_t*)h->s.keysB.p;
   uint32_t* VB = VALS ? (uint32_t*)h->s.valsB.p : nullptr;
   const uint32_t ntiles = (uint32_t)((k + kTile - 1) / kTile);
+  // the look-back wait's poll limit and a tile that never publishes (tests)
+  const uint32_t spin = h->sort_poll_limit ? h->sort_poll_limit : kSpinLimit;
+  const uint32_t silent = h->sort_silent_tile >= 0 && h->sort_silent_tile < (int64_t)ntiles
+                              ? (uint32_t)h->sort_silent_tile : 0xFFFFFFFFu;
   // control block + 9 look-back arrays, zeroed in one memset
   SortCtl* ctl = reinterpret_cast<SortCtl*>(h->s.hist.p);
   uint32_t* look = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(h->s.hist.p) + ctl_bytes());
@@ -536,7 +542,8 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
     // sorted in shared memory; the digit passes below run only if a bucket
     // overflowed
     k_onesweep<VALS><<<sgrid, kT, smem, st>>>(d_in, v_in, A, B, VA, VB, k, 0, 1, 0, ctl,
-                                               look + (size_t)8 * ntiles * 256, h->d_status);
+                                               look + (size_t)8 * ntiles * 256, h->d_status,
+                                               spin, silent);
     k_bucket_sort<VALS><<<256, kBT, sizeof(TileSmemT<VALS, kBT, kBItems>), st>>>(B, VB, A, VA,
                                                                                  ctl);
     h->launches += 2;
@@ -545,7 +552,8 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
   for (int p = 0; p < 8; p++) {
     // digits that vary: the scatter reads and writes keys (and tags)
     k_onesweep<VALS><<<sgrid, kT, smem, st>>>(d_in, v_in, A, B, VA, VB, k, p, 0, buckets ? 1 : 0,
-                                               ctl, look + (size_t)p * ntiles * 256, h->d_status);
+                                               ctl, look + (size_t)p * ntiles * 256, h->d_status,
+                                               spin, silent);
     h->launches++;
   }
   if (!buckets) prof_add_bytes(h, PH_SORT, (VALS ? 24ull : 16ull) * k * 5);  // typical: 5 varying digits
@@ -575,8 +583,8 @@ int unique_keys(cpma* h, const uint64_t* in, uint64_t k, uint64_t* out, cudaStre
     CPMA_CUDA(cudaMemsetAsync(&h->d_status->nunique, 0, 8, st));
     return CPMA_OK;
   }
-  CPMA_TRY(ensure(h->s.leaf_of, k * 4));
-  CPMA_TRY(ensure(h->s.flags_scan, (k + 1) * 8));
+  CPMA_TRY(ensure(h, h->s.leaf_of, k * 4));
+  CPMA_TRY(ensure(h, h->s.flags_scan, (k + 1) * 8));
   uint32_t* flags = (uint32_t*)h->s.leaf_of.p;
   uint64_t* pos = (uint64_t*)h->s.flags_scan.p;
   const int grid = (int)std::min<uint64_t>((uint64_t)h->num_sms * 8, (k + 255) / 256);

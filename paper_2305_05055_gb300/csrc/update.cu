@@ -668,9 +668,9 @@ __global__ void __launch_bounds__(kT, SEG == 32 ? 4 : 3) k_insert_lane(MergeArgs
 }
 
 // Insert of a slice of at most leafthr::kKeys keys into one leaf of byte
-// codes, one thread per leaf (leaf_thread.cuh): the thread decodes its leaf
-// serially, places the keys and rewrites the bytes from the first edit on in
-// place, 16 bytes at a time.  Slices this small are the common case of a
+// codes, one thread per leaf (leaf_thread.cuh): the thread sums its leaf
+// chunk by chunk up to the chunks where its keys land, places them and
+// rewrites the bytes from the first edit on in place, 16 bytes at a time.  Slices this small are the common case of a
 // batch that is small against the set (about one key per touched leaf), where
 // a warp per leaf leaves most lanes idle.  A leaf with a code of more than 4
 // bytes goes to the element-array splice (state kFallback); a result over LB
@@ -746,8 +746,6 @@ __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
       if (res == leafthr::kLongCode) {
         a.T_state[t] = kFallback;
         a.list_v1[atomicAdd(&a.st->n_v1, 1ull)] = t;
-      } else if (res == leafthr::kBadCount) {
-        atomicOr(&a.st->err, kErrState);
       } else {
         uint32_t c0 = 0;
         if (res == leafthr::kUnchanged) {
@@ -1255,7 +1253,7 @@ struct FinArgs {
 __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
   if (a.st->err) return;
   const uint64_t nT = a.st->nT;
-  ull mb = 0, dl = 0, np = 0;
+  ull mb = 0, dl = 0, np = 0, db = 0;  // db: change of the byte total, mod 2^64
   for (uint64_t t = gtid(); t < nT; t += gstride()) {
     const uint32_t state = a.T_state[t];
     const uint32_t oldc = a.T_oldcnt[t], newc = a.T_newcnt[t];
@@ -1275,6 +1273,7 @@ __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
     }
     dl += (ull)(a.is_delete ? oldc - newc : newc - oldc);
     const uint64_t nb = a.T_newbytes[t];
+    db += nb - (ull)a.T_oldused[t];
     if (state == kPending) {
       a.used[j] = (uint32_t)nb;
       a.cnt[j] = newc;
@@ -1290,9 +1289,11 @@ __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
   // one atomic per warp for the batch totals
   dl = warp_sum(dl);
   np = warp_sum(np);
+  db = warp_sum(db);
   if (lane_id() == 0) {
     if (dl) atomicAdd(&a.st->delta, dl);
     if (np) atomicAdd(&a.st->npend, np);
+    if (db) atomicAdd(&a.st->bytes_total, db);
   }
   if (a.merge_bytes) {
     mb = warp_sum(mb);
@@ -1402,12 +1403,20 @@ __global__ void __launch_bounds__(kT) k_win_sizes(const uint64_t* __restrict__ w
   for (uint64_t w = gtid(); w < nwin; w += gstride()) sizes[w] = wins[2 * w + 1];
 }
 
+// Element count of every source leaf; the leaves' bytes leave the total
+// (the encode adds the new ones).
 __global__ void __launch_bounds__(kT) k_src_counts(WinArgs w, const uint32_t* __restrict__ cnt,
-                                                   uint64_t nsrc, uint32_t* __restrict__ srccnt) {
+                                                   const uint32_t* __restrict__ used, uint64_t nsrc,
+                                                   uint32_t* __restrict__ srccnt, Status* st) {
+  ull gone = 0;
   for (uint64_t f = gtid(); f < nsrc; f += gstride()) {
     const uint64_t s = find_seg(w.leaf_off, w.nwin, f);
-    srccnt[f] = cnt[w.win_src[2 * s] + (f - w.leaf_off[s])];
+    const uint64_t j = w.win_src[2 * s] + (f - w.leaf_off[s]);
+    srccnt[f] = cnt[j];
+    gone += used[j];
   }
+  gone = warp_sum(gone);
+  if (lane_id() == 0 && gone) atomicAdd(&st->bytes_total, 0ull - gone);
 }
 
 __global__ void k_elem_offsets(WinArgs w, const uint64_t* __restrict__ srcoff, Status* st) {
@@ -1506,6 +1515,7 @@ __global__ void __launch_bounds__(kT) k_encode(EncodeArgs a) {
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   uint8_t* buf = smem + (size_t)warp * a.LB;
   const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
+  ull added = 0;  // lane 0: bytes of this warp's leaves
   for (uint64_t g = gw; g < a.ndst; g += nw) {
     const uint64_t s = find_seg(a.w.dst_off, a.w.nwin, g);
     const uint64_t wl = g - a.w.dst_off[s];
@@ -1532,11 +1542,13 @@ __global__ void __launch_bounds__(kT) k_encode(EncodeArgs a) {
       a.used[j] = got;
       a.cnt[j] = r;
       a.heads[j] = r ? a.E[b] : KEY_MAX;
+      added += got;
       if (got != nb) atomicOr(&a.st->err, kErrState);
       if (r == 0) atomicAdd(&a.st->nempty, 1ull);
     }
     __syncwarp();
   }
+  if (lane == 0 && added) atomicAdd(&a.st->bytes_total, added);
 }
 
 // Head index of empty leaves: the head of the next non-empty leaf, or
@@ -1736,45 +1748,42 @@ int ensure_bits(cpma* h, cudaStream_t st, Levels* lv) {
   uint64_t words = 0;
   *lv = levels_of(h->L, H, &words);
   if (words != h->bits_words) {
-    CPMA_TRY(ensure(h->s.bits, words * 4));
+    CPMA_TRY(ensure(h, h->s.bits, words * 4));
     CPMA_CUDA(cudaMemsetAsync(h->s.bits.p, 0, words * 4, st));
     h->bits_words = words;
   }
   return CPMA_OK;
 }
 
-struct Arrays {
-  uint8_t* data;
-  uint32_t* used;
-  uint32_t* cnt;
-  uint64_t* heads;
-};
-
-int alloc_arrays(uint64_t L, uint32_t LB, Arrays* a) {
-  *a = Arrays{nullptr, nullptr, nullptr, nullptr};
-  if (cudaMalloc(&a->data, L * LB) != cudaSuccess || cudaMalloc(&a->used, L * 4) != cudaSuccess ||
-      cudaMalloc(&a->cnt, L * 4) != cudaSuccess ||
-      cudaMalloc(&a->heads, (L + 1) * 8) != cudaSuccess) {
-    cudaGetLastError();
-    cudaFree(a->data); cudaFree(a->used); cudaFree(a->cnt); cudaFree(a->heads);
-    *a = Arrays{nullptr, nullptr, nullptr, nullptr};
-    return CPMA_ENOMEM;
-  }
-  return CPMA_OK;
+// The handle's live leaf arrays.
+Arrays live_arrays(const cpma* h) {
+  Arrays a;
+  a.data = h->data;
+  a.used = h->used;
+  a.cnt = h->cnt;
+  a.heads = h->heads;
+  a.cap_leaves = h->cap_leaves;
+  a.cap_bytes = h->cap_bytes;
+  return a;
 }
 
-void free_arrays(Arrays a) {
-  cudaFree(a.data); cudaFree(a.used); cudaFree(a.cnt); cudaFree(a.heads);
+void set_live(cpma* h, const Arrays& a) {
+  h->data = a.data;
+  h->used = a.used;
+  h->cnt = a.cnt;
+  h->heads = a.heads;
+  h->cap_leaves = a.cap_leaves;
+  h->cap_bytes = a.cap_bytes;
 }
 
 // Shared tail of every redistribution: costs over E, their prefix, cut points
 // and the encode into `dst`.  The window arrays and elem_off must be set;
 // nelem_dev points at the element count.
 int spread(cpma* h, cudaStream_t st, WinArgs w, uint64_t nelem_bound, const ull* nelem_dev,
-           uint64_t ndst, Arrays dst) {
-  CPMA_TRY(ensure(h->s.cost, nelem_bound + 1));
-  CPMA_TRY(ensure(h->s.C, (nelem_bound + 2) * 8));
-  CPMA_TRY(ensure(h->s.dstart, (ndst + 1) * 8));
+           uint64_t ndst, Arrays dst, uint32_t LBdst) {
+  CPMA_TRY(ensure(h, h->s.cost, nelem_bound + 1));
+  CPMA_TRY(ensure(h, h->s.C, (nelem_bound + 2) * 8));
+  CPMA_TRY(ensure(h, h->s.dstart, (ndst + 1) * 8));
   k_costs<<<grid_for(h, nelem_bound), kT, 0, st>>>(w, P<uint64_t>(h->s.E), nelem_dev,
                                                    P<uint8_t>(h->s.cost), (int)h->cfg.codec);
   h->launches++;
@@ -1793,10 +1802,10 @@ int spread(cpma* h, cudaStream_t st, WinArgs w, uint64_t nelem_bound, const ull*
   ea.used = dst.used;
   ea.cnt = dst.cnt;
   ea.heads = dst.heads;
-  ea.LB = h->cfg.leaf_bytes;
+  ea.LB = LBdst;
   ea.st = h->d_status;
   ea.raw = (int)h->cfg.codec;
-  const size_t smem = (size_t)(kT / 32) * h->cfg.leaf_bytes;
+  const size_t smem = (size_t)(kT / 32) * LBdst;
   k_encode<<<grid_for(h, ndst * 32), kT, smem, st>>>(ea);
   h->launches++;
   return check_cuda(cudaGetLastError());
@@ -1814,11 +1823,11 @@ WinArgs win_args(cpma* h, uint64_t nwin) {
 }
 
 int ensure_win(cpma* h, uint64_t nwin) {
-  CPMA_TRY(ensure(h->s.win_src, (nwin + 1) * 16));
-  CPMA_TRY(ensure(h->s.win_dst, (nwin + 1) * 16));
-  CPMA_TRY(ensure(h->s.win_leaf_off, (nwin + 2) * 8));
-  CPMA_TRY(ensure(h->s.win_dst_off, (nwin + 2) * 8));
-  CPMA_TRY(ensure(h->s.win_elem_off, (nwin + 2) * 8));
+  CPMA_TRY(ensure(h, h->s.win_src, (nwin + 1) * 16));
+  CPMA_TRY(ensure(h, h->s.win_dst, (nwin + 1) * 16));
+  CPMA_TRY(ensure(h, h->s.win_leaf_off, (nwin + 2) * 8));
+  CPMA_TRY(ensure(h, h->s.win_dst_off, (nwin + 2) * 8));
+  CPMA_TRY(ensure(h, h->s.win_elem_off, (nwin + 2) * 8));
   return CPMA_OK;
 }
 
@@ -1827,10 +1836,11 @@ int ensure_win(cpma* h, uint64_t nwin) {
 int pack(cpma* h, cudaStream_t st, uint64_t nwin, uint64_t nsrc, uint64_t nelem_bound,
          uint64_t nT) {
   WinArgs w = win_args(h, nwin);
-  CPMA_TRY(ensure(h->s.srccnt, (nsrc + 1) * 4));
-  CPMA_TRY(ensure(h->s.srcoff, (nsrc + 2) * 8));
-  CPMA_TRY(ensure(h->s.E, (nelem_bound + 1) * 8));
-  k_src_counts<<<grid_for(h, nsrc), kT, 0, st>>>(w, h->cnt, nsrc, P<uint32_t>(h->s.srccnt));
+  CPMA_TRY(ensure(h, h->s.srccnt, (nsrc + 1) * 4));
+  CPMA_TRY(ensure(h, h->s.srcoff, (nsrc + 2) * 8));
+  CPMA_TRY(ensure(h, h->s.E, (nelem_bound + 1) * 8));
+  k_src_counts<<<grid_for(h, nsrc), kT, 0, st>>>(w, h->cnt, h->used, nsrc, P<uint32_t>(h->s.srccnt),
+                                                  h->d_status);
   h->launches++;
   CPMA_TRY(scan_u32_to_u64(h, P<uint32_t>(h->s.srccnt), P<uint64_t>(h->s.srcoff), nsrc, nullptr,
                            st));
@@ -1849,7 +1859,7 @@ int pack(cpma* h, cudaStream_t st, uint64_t nwin, uint64_t nsrc, uint64_t nelem_
   ua.T_first_chunk = P<uint32_t>(h->s.T_first_chunk);
   ua.chunk_off = P<uint64_t>(h->s.chunk_off);
   ua.nT = nT;
-  ua.ovf = P<uint64_t>(h->s.ovf);
+  ua.ovf = P<uint64_t>(h->s.C);  // the overflow elements (C is written only after the pack)
   ua.E = P<uint64_t>(h->s.E);
   ua.st = h->d_status;
   ua.raw = (int)h->cfg.codec;
@@ -1859,14 +1869,14 @@ int pack(cpma* h, cudaStream_t st, uint64_t nwin, uint64_t nsrc, uint64_t nelem_
 }
 
 int redistribute(cpma* h, cudaStream_t st, uint64_t nwin, uint64_t nsrc, uint64_t ndst,
-                 uint64_t nelem_bound, uint64_t nT, Arrays dst) {
+                 uint64_t nelem_bound, uint64_t nT, Arrays dst, uint32_t LBdst) {
   CPMA_TRY(pack(h, st, nwin, nsrc, nelem_bound, nT));
-  return spread(h, st, win_args(h, nwin), nelem_bound, &h->d_status->nelem, ndst, dst);
+  return spread(h, st, win_args(h, nwin), nelem_bound, &h->d_status->nelem, ndst, dst, LBdst);
 }
 
 int fix_heads(cpma* h, cudaStream_t st) {
   const uint64_t nt = (h->L + kFHTile - 1) / kFHTile;
-  CPMA_TRY(ensure(h->s.fh, nt * sizeof(FHTile)));
+  CPMA_TRY(ensure(h, h->s.fh, nt * sizeof(FHTile)));
   FHTile* tiles = P<FHTile>(h->s.fh);
   k_fh_tiles<<<(unsigned)nt, kFH, 0, st>>>(h->used, h->heads, h->L, tiles);
   k_fh_carry<<<1, kFH, 0, st>>>(tiles, nt, h->heads, h->L, h->d_status);
@@ -1875,17 +1885,29 @@ int fix_heads(cpma* h, cudaStream_t st) {
   return check_cuda(cudaGetLastError());
 }
 
+// Leaf size for a structure of n keys (R13): the configured size, or with
+// leaf_growth > 0 the size that grows with log n,
+// min(2048, max(leaf_bytes, 16 ceil(leaf_growth bitlen(n) / 16))).
+uint32_t leaf_size_for(const cpma* h, uint64_t n) {
+  const uint32_t g = h->cfg.leaf_growth;
+  if (!g) return h->lb_min;
+  uint32_t bl = 0;
+  while (bl < 64 && (n >> bl)) bl++;
+  const uint64_t want = ((uint64_t)g * bl + 15) / 16 * 16;
+  return (uint32_t)std::min<uint64_t>(2048, std::max<uint64_t>(h->lb_min, want));
+}
+
 // R9 of the readings: grow by grow_num/grow_den (rounded up) while the root
 // upper bound fails, shrink by the inverse (rounded down) while the root
-// lower bound fails and more than one leaf remains.
-uint64_t resize_target(const cpma_config& c, uint64_t T, uint64_t L) {
+// lower bound fails and more than one leaf remains, for leaves of LB bytes.
+uint64_t resize_target(const cpma_config& c, uint64_t T, uint64_t L, uint32_t LB) {
   typedef unsigned __int128 u128;
   uint64_t Lp = L;
-  if ((u128)T * 1000 > (u128)c.tau_root * Lp * c.leaf_bytes) {
-    while ((u128)T * 1000 > (u128)c.tau_root * Lp * c.leaf_bytes)
+  if ((u128)T * 1000 > (u128)c.tau_root * Lp * LB) {
+    while ((u128)T * 1000 > (u128)c.tau_root * Lp * LB)
       Lp = (uint64_t)(((u128)Lp * c.grow_num + c.grow_den - 1) / c.grow_den);
   } else {
-    while (Lp > 1 && (u128)T * 1000 < (u128)c.rho_root * Lp * c.leaf_bytes) {
+    while (Lp > 1 && (u128)T * 1000 < (u128)c.rho_root * Lp * LB) {
       uint64_t nx = (uint64_t)((u128)Lp * c.grow_den / c.grow_num);
       Lp = nx < 1 ? 1 : nx;
     }
@@ -1893,22 +1915,40 @@ uint64_t resize_target(const cpma_config& c, uint64_t T, uint64_t L) {
   return Lp;
 }
 
+// The leaf count and size a resize gives for T bytes and n_after keys: the
+// leaf size for n_after, then R9 from the leaf count of the same capacity.
+void resize_plan(const cpma* h, uint64_t T, uint64_t n_after, uint64_t* Lp, uint32_t* LBp) {
+  const uint32_t LB = h->cfg.leaf_bytes, LB2 = leaf_size_for(h, n_after);
+  const uint64_t L0 = LB2 == LB ? h->L : std::max<uint64_t>(1, (h->L * LB + LB2 - 1) / LB2);
+  *LBp = LB2;
+  *Lp = resize_target(h->cfg, T, L0, LB2);
+}
+
+// Whole-array redistribution into L' leaves of LB' bytes (R9, R13).  The
+// destination is the live arrays when they have the capacity (the pack reads
+// every element before the encode writes), else the spare arrays reserved
+// before the update; nothing is allocated here.
 int do_resize(cpma* h, cudaStream_t st, uint64_t T, uint64_t n_after, uint64_t nT) {
-  const uint64_t Lp = resize_target(h->cfg, T, h->L);
-  Arrays na;
-  CPMA_TRY(alloc_arrays(Lp, h->cfg.leaf_bytes, &na));
-  int rc = ensure_win(h, 1);
-  if (rc != CPMA_OK) { free_arrays(na); return rc; }
+  uint64_t Lp = 0;
+  uint32_t LBp = 0;
+  resize_plan(h, T, n_after, &Lp, &LBp);
+  const bool in_place = Lp <= h->cap_leaves && Lp * LBp <= h->cap_bytes;
+  if (!in_place && (Lp > h->spare.cap_leaves || Lp * LBp > h->spare.cap_bytes))
+    return CPMA_EINTERNAL;  // the reservation missed this case
+  Arrays dst = in_place ? live_arrays(h) : h->spare;
   k_set_window<<<1, 1, 0, st>>>(P<uint64_t>(h->s.win_src), P<uint64_t>(h->s.win_dst),
                                 P<uint64_t>(h->s.win_leaf_off), P<uint64_t>(h->s.win_dst_off), 0,
                                 h->L, 0, Lp);
   h->launches++;
-  rc = redistribute(h, st, 1, h->L, Lp, n_after, nT, na);
-  if (rc != CPMA_OK) { free_arrays(na); return rc; }
-  rc = check_cuda(cudaStreamSynchronize(st));
-  if (rc != CPMA_OK) return rc;
-  free_arrays(Arrays{h->data, h->used, h->cnt, h->heads});
-  h->data = na.data; h->used = na.used; h->cnt = na.cnt; h->heads = na.heads;
+  CPMA_TRY(redistribute(h, st, 1, h->L, Lp, n_after, nT, dst, LBp));
+  CPMA_CUDA(cudaStreamSynchronize(st));
+  if (!in_place) {
+    Arrays old = live_arrays(h);
+    free_arrays(h, &old);
+    set_live(h, dst);
+    h->spare = Arrays{};
+  }
+  h->cfg.leaf_bytes = LBp;
   h->L = Lp;
   return CPMA_OK;
 }
@@ -2048,6 +2088,16 @@ void merge_attrs() {
   done = true;
 }
 
+// The thread-granular insert (or delete) over the touched leaves of a batch
+// of k keys (at most k of them).
+template <bool DEL>
+void launch_insert_thread(cpma* h, const MergeArgs& ma, uint64_t k, cudaStream_t st) {
+  const int g = (int)std::max<uint64_t>(
+      1, std::min<uint64_t>((k + kThrT - 1) / kThrT, (uint64_t)h->num_sms * 16));
+  k_insert_thread<DEL><<<g, kThrT, 0, st>>>(ma);
+  h->launches++;
+}
+
 // Every buffer the front segment of a batch of k keys touches, sized before
 // it runs (a graph capture must not allocate), plus the window bitsets of the
 // current tree.
@@ -2064,21 +2114,21 @@ int front_scratch(cpma* h, uint64_t k, bool tagged, cudaStream_t st) {
   if (!h->ev_fork) CPMA_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   if (!h->ev_join) CPMA_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   CPMA_TRY(sort_scratch(h, k, tagged));
-  CPMA_TRY(ensure(s.partials, (size_t)(2 * h->num_sms + 2) * 8));
-  CPMA_TRY(ensure(s.leaf_of, k * 4));
-  CPMA_TRY(ensure(s.flags, k * 8));
-  CPMA_TRY(ensure(s.flags_scan, (k + 1) * 8));
+  CPMA_TRY(ensure(h, s.partials, (size_t)(2 * h->num_sms + 2) * 8));
+  CPMA_TRY(ensure(h, s.leaf_of, k * 4));
+  CPMA_TRY(ensure(h, s.flags, k * 8));
+  CPMA_TRY(ensure(h, s.flags_scan, (k + 1) * 8));
   for (Buf* b : {&s.chunk_begin, &s.chunk_leaf, &s.chunk_tid, &s.chunk_cnt, &s.T_leaf, &s.T_begin,
                  &s.T_first_chunk, &s.T_oldcnt, &s.T_oldused, &s.T_newcnt, &s.T_state, &s.viol})
-    CPMA_TRY(ensure(*b, (k + 2) * 4));
-  CPMA_TRY(ensure(s.chunk_off, (k + 2) * 8));
-  CPMA_TRY(ensure(s.T_newbytes, (k + 2) * 8));
-  CPMA_TRY(ensure(s.list_lane, (k + 2) * 4));
-  CPMA_TRY(ensure(s.list_v1, (k + 2) * 4));
-  CPMA_TRY(ensure(s.list_gen, (k + 2) * 4));
-  CPMA_TRY(ensure(s.cand, (2 * k + 2) * 8));
-  CPMA_TRY(ensure(s.wins, (2 * k + 2) * 16));
-  CPMA_TRY(ensure(s.prefix, (h->L + 2) * 8));
+    CPMA_TRY(ensure(h, *b, (k + 2) * 4));
+  CPMA_TRY(ensure(h, s.chunk_off, (k + 2) * 8));
+  CPMA_TRY(ensure(h, s.T_newbytes, (k + 2) * 8));
+  CPMA_TRY(ensure(h, s.list_lane, (k + 2) * 4));
+  CPMA_TRY(ensure(h, s.list_v1, (k + 2) * 4));
+  CPMA_TRY(ensure(h, s.list_gen, (k + 2) * 4));
+  CPMA_TRY(ensure(h, s.cand, (2 * k + 2) * 8));
+  CPMA_TRY(ensure(h, s.wins, (2 * k + 2) * 16));
+  CPMA_TRY(ensure(h, s.prefix, (h->L + 2) * 8));
   Levels lv;
   return ensure_bits(h, st, &lv);
 }
@@ -2206,20 +2256,14 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
       CPMA_CUDA(cudaEventRecord(h->ev_join, h->side));
       ma.prof = prof_bytes(h, PH_MERGE);
       if (!ma.raw) {
-        const int tgrid = (int)std::max<uint64_t>(
-            1, std::min<uint64_t>((k + kThrT - 1) / kThrT, (uint64_t)h->num_sms * 16));
-        k_insert_thread<false><<<tgrid, kThrT, 0, st>>>(ma);
-        h->launches++;
+        launch_insert_thread<false>(h, ma, k, st);
       }
       ma.prof = nullptr;
       CPMA_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
     }
     if (is_delete && !ma.raw) {
       ma.prof = prof_bytes(h, PH_MERGE);
-      const int tgrid = (int)std::max<uint64_t>(
-          1, std::min<uint64_t>((k + kThrT - 1) / kThrT, (uint64_t)h->num_sms * 16));
-      k_insert_thread<true><<<tgrid, kThrT, 0, st>>>(ma);
-      h->launches++;
+      launch_insert_thread<true>(h, ma, k, st);
       ma.prof = nullptr;
     }
     prof_end(h, st);
@@ -2293,9 +2337,11 @@ constexpr int kSigPtrs = 33;
 
 struct FrontSig {
   const void* p[kSigPtrs];
-  uint64_t L;
+  uint64_t L, LB;
+  uint32_t poll;    // sort look-back poll limit and silent tile (tests)
+  int64_t silent;
   bool operator==(const FrontSig& o) const {
-    if (L != o.L) return false;
+    if (L != o.L || LB != o.LB || poll != o.poll || silent != o.silent) return false;
     for (int i = 0; i < kSigPtrs; i++)
       if (p[i] != o.p[i]) return false;
     return true;
@@ -2311,7 +2357,7 @@ FrontSig front_sig(const cpma* h) {
                    s.T_newbytes.p, s.T_state.p,   s.viol.p,          s.list_lane.p, s.list_v1.p,
                    s.list_gen.p,  s.cand.p,       s.wins.p,          s.bits.p,      h->data,
                    h->used,       h->cnt,         h->heads,          h->d_status},
-                  h->L};
+                  h->L, h->cfg.leaf_bytes, h->sort_poll_limit, h->sort_silent_tile};
 }
 
 struct GraphSlot {
@@ -2357,7 +2403,7 @@ __global__ void __launch_bounds__(kT) k_stage(const uint64_t* __restrict__ in, u
 int run_front_graph(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_delete,
                     cudaStream_t st, Front* f) {
   const uint64_t K = graph_bucket(k);
-  CPMA_TRY(ensure(h->s.stage, K * 8));
+  CPMA_TRY(ensure(h, h->s.stage, K * 8));
   CPMA_TRY(front_scratch(h, K, false, st));
   uint64_t* stage = P<uint64_t>(h->s.stage);
   k_stage<<<grid_for(h, K), kT, 0, st>>>(d_keys, k, stage, K);
@@ -2471,18 +2517,18 @@ int run_rebuild(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_
   prof_begin(h, PH_REDIST, st);
   // every element, in order, into E (one window over all leaves); E later
   // takes the merged set, up to n + k keys
-  CPMA_TRY(ensure(s.E, (N + 1) * 8));
+  CPMA_TRY(ensure(h, s.E, (N + 1) * 8));
   CPMA_TRY(ensure_win(h, 1));
   k_set_window<<<1, 1, 0, st>>>(P<uint64_t>(s.win_src), P<uint64_t>(s.win_dst),
                                 P<uint64_t>(s.win_leaf_off), P<uint64_t>(s.win_dst_off), 0, h->L,
                                 0, h->L);
   h->launches++;
   CPMA_TRY(pack(h, st, 1, h->L, n, 0));
-  CPMA_TRY(ensure(s.ovf, (N + 1) * 8));
-  CPMA_TRY(ensure(s.cost, N + 1));
-  CPMA_TRY(ensure(s.flags_scan, (N + 2) * 8));
-  CPMA_TRY(ensure(s.srccnt, N + 1));
-  uint64_t* M = P<uint64_t>(s.ovf);
+  CPMA_TRY(ensure(h, s.C, (N + 2) * 8));
+  CPMA_TRY(ensure(h, s.cost, N + 1));
+  CPMA_TRY(ensure(h, s.flags_scan, (N + 2) * 8));
+  CPMA_TRY(ensure(h, s.srccnt, N + 1));
+  uint64_t* M = P<uint64_t>(s.C);  // dead once the result is in E
   uint8_t* fromB = P<uint8_t>(s.srccnt);
   uint8_t* keep = P<uint8_t>(s.cost);
   uint64_t* pos = P<uint64_t>(s.flags_scan);
@@ -2500,6 +2546,7 @@ int run_rebuild(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_
   CPMA_CUDA(cudaGetLastError());
   CPMA_TRY(sync_status(h, st));
   Status hs = *h->h_status;
+  if (hs.err & kErrSort) return CPMA_ETIMEOUT;
   if (hs.err & kErrUnsorted) return CPMA_EINVAL;
   if (hs.err) return CPMA_EINTERNAL;
   CPMA_TRY(build_from_sorted_unique(h, P<uint64_t>(s.E), hs.nelem, st));
@@ -2520,12 +2567,102 @@ int reserve(cpma* h, uint64_t max_batch, int tagged, cudaStream_t st) {
   if (h->graph_max_batch && !tagged) {
     const uint64_t K = graph_bucket(std::min(max_batch, h->graph_max_batch));
     if (K < (1ull << 31)) {
-      CPMA_TRY(ensure(h->s.stage, K * 8));
+      CPMA_TRY(ensure(h, h->s.stage, K * 8));
       CPMA_TRY(front_scratch(h, K, false, st));
     }
   }
   return CPMA_OK;
 }
+
+// Everything an update of k keys can allocate once it starts changing the
+// structure, reserved before it does, so that running out of memory (or out
+// of budget) leaves the set unchanged: the redistribution buffers for the
+// whole set (elements, costs, their prefix -- which also holds the overflow
+// elements of pending leaves -- and the source counts and offsets), the
+// window lists, the cut points, level bitsets and head fix-up tiles of the
+// largest tree a resize can give, and spare leaf arrays when the batch can
+// make the array outgrow the live ones.  A resize needs the root bound to
+// fail; the used bytes after the merge lie within t_known -+ t_slack (the
+// redistribution after the last merge) and 10 bytes per key (an inserted
+// key adds at most a 10-byte code, a deleted one removes at most one).
+int reserve_update(cpma* h, uint64_t k, int is_delete, cudaStream_t st) {
+  Scratch& s = h->s;
+  const uint64_t n = h->n, L = h->L;
+  const uint64_t n_hi = is_delete ? n : n + k, n_lo = is_delete ? (n > k ? n - k : 0) : n;
+  CPMA_TRY(ensure(h, s.E, (n_hi + 1) * 8, st));
+  CPMA_TRY(ensure(h, s.cost, n_hi + 1, st));
+  CPMA_TRY(ensure(h, s.C, (n_hi + 2) * 8, st));
+  const uint64_t dk = 10 * k;
+  const uint64_t t_hi = h->t_known + h->t_slack + (is_delete ? 0 : dk);
+  const uint64_t sub = h->t_slack + (is_delete ? dk : 0);
+  const uint64_t t_lo = h->t_known > sub ? h->t_known - sub : 0;
+  const Bounds B = bounds_of(h);
+  const unsigned H = ceil_log2(L);
+  const bool may_resize = node_violates(B, H, H, L, t_hi) || node_violates(B, H, H, L, t_lo);
+  uint64_t Lmax = L, bytes_max = L * h->cfg.leaf_bytes;
+  if (may_resize) {
+    // the most leaves and bytes over every key count the batch can leave
+    // (each leaf size between theirs) at the most bytes
+    uint32_t b_lo = 0, b_hi = 0;
+    while (b_lo < 64 && (n_lo >> b_lo)) b_lo++;
+    while (b_hi < 64 && (n_hi >> b_hi)) b_hi++;
+    for (uint32_t b = b_lo; b <= b_hi; b++) {
+      const uint64_t nn = b == b_lo ? n_lo : b == b_hi ? n_hi : (1ull << (b - 1));
+      uint64_t Lp = 0;
+      uint32_t LBp = 0;
+      resize_plan(h, t_hi, nn, &Lp, &LBp);
+      Lmax = std::max(Lmax, Lp);
+      bytes_max = std::max(bytes_max, Lp * LBp);
+    }
+  }
+  if (Lmax > h->cap_leaves || bytes_max > h->cap_bytes) {
+    if (h->spare.cap_leaves < Lmax || h->spare.cap_bytes < bytes_max) {
+      free_arrays(h, &h->spare);  // never in use between updates
+      CPMA_TRY(alloc_arrays(h, Lmax, bytes_max, &h->spare, st));
+    }
+  } else if (h->spare.data) {
+    free_arrays(h, &h->spare);
+  }
+  // leaf-count buffers for the larger of the two trees, so that the update
+  // after a resize finds them sized too
+  CPMA_TRY(ensure_win(h, std::min(k, Lmax) + 2));
+  CPMA_TRY(ensure(h, s.srccnt, (Lmax + 1) * 4, st));
+  CPMA_TRY(ensure(h, s.srcoff, (Lmax + 2) * 8, st));
+  CPMA_TRY(ensure(h, s.prefix, (Lmax + 2) * 8, st));
+  CPMA_TRY(ensure(h, s.dstart, (Lmax + 1) * 8, st));
+  uint64_t words = 0;
+  levels_of(Lmax, ceil_log2(Lmax), &words);
+  const void* bits_before = s.bits.p;
+  CPMA_TRY(ensure(h, s.bits, words * 4, st));
+  if (s.bits.p != bits_before) h->bits_words = 0;  // a new buffer: ensure_bits zeroes it
+  CPMA_TRY(ensure(h, s.fh, ((Lmax + kFHTile - 1) / kFHTile) * sizeof(FHTile), st));
+  return CPMA_OK;
+}
+
+// Every scratch buffer of the update path and the spare leaf arrays freed
+// (after the device is idle), and the graphs that bake their addresses in.
+void trim_update_scratch(cpma* h) {
+  cudaDeviceSynchronize();
+  graph_cache_free(h);
+  Scratch& s = h->s;
+  for (Buf* b : {&s.keysA, &s.keysB, &s.valsA, &s.valsB, &s.hist, &s.flags, &s.flags_scan,
+                 &s.leaf_of, &s.chunk_begin, &s.chunk_leaf, &s.chunk_tid, &s.chunk_cnt,
+                 &s.chunk_off, &s.T_leaf, &s.T_begin, &s.T_first_chunk, &s.T_oldcnt, &s.T_oldused,
+                 &s.T_newcnt, &s.T_newbytes, &s.T_state, &s.viol, &s.list_lane, &s.list_v1,
+                 &s.list_gen, &s.cand, &s.wins, &s.bits, &s.prefix, &s.E, &s.cost, &s.C,
+                 &s.srccnt, &s.srcoff, &s.dstart, &s.win_src, &s.win_dst, &s.win_leaf_off,
+                 &s.win_elem_off, &s.win_dst_off, &s.partials, &s.stage, &s.fh})
+    release(h, *b);
+  h->bits_words = 0;
+  free_arrays(h, &h->spare);
+}
+
+// Set while an update changes the structure: every allocation then fails.
+struct NoAlloc {
+  cpma* h;
+  explicit NoAlloc(cpma* hh) : h(hh) { h->no_alloc = true; }
+  ~NoAlloc() { h->no_alloc = false; }
+};
 
 int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_delete,
                uint64_t* d_delta, cudaStream_t st, const uint32_t* tags, uint64_t* tag_counts,
@@ -2541,13 +2678,28 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
       (unsigned __int128)1000 * k >= (unsigned __int128)h->cfg.rebuild_pm * h->n)
     return run_rebuild(h, d_keys, k, sorted, is_delete, d_delta, st);
   Scratch& s = h->s;
+  const bool graph = k <= h->graph_max_batch && !tags && graph_bucket(k) < (1ull << 31);
+  int rc = reserve_update(h, k, is_delete, st);
+  if (rc == CPMA_OK && graph) {
+    rc = ensure(h, s.stage, graph_bucket(k) * 8, st);
+    if (rc == CPMA_OK) rc = front_scratch(h, graph_bucket(k), false, st);
+  } else if (rc == CPMA_OK) {
+    rc = front_scratch(h, k, tags != nullptr, st);
+  }
+  if (rc == CPMA_ENOMEM) {
+    // refused before any change; give back the scratch grown so far, so
+    // that a smaller batch after this one starts from the structure alone
+    trim_update_scratch(h);
+    return rc;
+  }
+  CPMA_TRY(rc);
   Front f;
-  if (k <= h->graph_max_batch && !tags && graph_bucket(k) < (1ull << 31)) {
+  if (graph) {
     CPMA_TRY(run_front_graph(h, d_keys, k, sorted, is_delete, st, &f));
   } else {
-    CPMA_TRY(front_scratch(h, k, tags != nullptr, st));
     CPMA_TRY(run_front(h, d_keys, k, sorted, is_delete, st, tags, tag_counts, ntags, &f));
   }
+  const NoAlloc guard(h);  // from here on everything needed is reserved
   MergeArgs& ma = f.ma;
   FinArgs& fa = f.fa;
   const Levels& lv = f.lv;
@@ -2558,16 +2710,19 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   CPMA_TRY(sync_status(h, st));
   prof_begin(h, PH_COUNT, st);
   Status hs = *h->h_status;
+  if (hs.err & kErrSort) return CPMA_ETIMEOUT;
   if (hs.err & kErrUnsorted) return CPMA_EINVAL;
   if (hs.err) return CPMA_EINTERNAL;
+  const uint64_t t_merged = hs.bytes_total;  // exact: every leaf changed by the merge counted
+  uint64_t t_slack = 0;
   const uint64_t delta = hs.delta;
   const uint64_t n_after = is_delete ? h->n - delta : h->n + delta;
   if (hs.nempty || hs.empties) h->may_have_empty = true;
 
   // ---- pending leaves: materialise their merged elements ----
   if (hs.npend) {
-    CPMA_TRY(ensure(s.ovf, (hs.novf + 1) * 8));
-    ma.ovf = P<uint64_t>(s.ovf);
+    if (s.C.cap < (hs.novf + 1) * 8) return CPMA_EINTERNAL;  // reserved: novf <= n + k
+    ma.ovf = P<uint64_t>(s.C);
     ma.tag_counts = nullptr;
     k_merge<true><<<mgrid, mwarps * 32, msmem, st>>>(ma);
     h->launches++;
@@ -2604,7 +2759,9 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
     if (hs.err) return CPMA_EINTERNAL;
     prof_begin(h, PH_REDIST, st);
     if (hs.resize) {
+      const uint64_t L0 = h->L;
       CPMA_TRY(do_resize(h, st, hs.total_bytes, n_after, hs.nT));
+      t_slack = 9 * std::max(L0, h->L);
       resized = true;
     } else if (hs.nwin) {
       const uint64_t nwin = hs.nwin;
@@ -2618,8 +2775,9 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
       CPMA_TRY(scan_u64(h, P<uint64_t>(s.prefix), P<uint64_t>(s.win_leaf_off), nwin, nullptr, st));
       CPMA_CUDA(cudaMemcpyAsync(s.win_dst_off.p, s.win_leaf_off.p, (nwin + 1) * 8,
                                 cudaMemcpyDeviceToDevice, st));
-      Arrays cur{h->data, h->used, h->cnt, h->heads};
-      CPMA_TRY(redistribute(h, st, nwin, hs.win_leaves, hs.win_leaves, n_after, hs.nT, cur));
+      CPMA_TRY(redistribute(h, st, nwin, hs.win_leaves, hs.win_leaves, n_after, hs.nT,
+                            live_arrays(h), h->cfg.leaf_bytes));
+      t_slack = 9 * hs.win_leaves;
     }
   }
   prof_end(h, st);
@@ -2631,6 +2789,11 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   }
   if (h->may_have_empty) CPMA_TRY(fix_heads(h, st));
   h->n = n_after;
+  // the bytes a re-encode changes: a new head costs at most 7 more than the
+  // code it replaces, a former head at most 2 more as a code (and the
+  // reverse), per leaf of the larger side
+  h->t_known = t_merged;
+  h->t_slack = t_slack;
   if (d_delta)
     CPMA_CUDA(cudaMemcpyAsync(d_delta, &ds->delta, 8, cudaMemcpyDeviceToDevice, st));
   CPMA_CUDA(cudaGetLastError());
@@ -2643,11 +2806,11 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
 // a stream of S bytes, then one byte-balanced spread.
 int build_from_sorted_unique(cpma* h, const uint64_t* E, uint64_t n, cudaStream_t st) {
   typedef unsigned __int128 u128;
-  const uint32_t LB = h->cfg.leaf_bytes;
+  const uint32_t LB = leaf_size_for(h, n);
   Scratch& s = h->s;
   CPMA_TRY(ensure_win(h, 1));
-  CPMA_TRY(ensure(s.cost, n + 1));
-  CPMA_TRY(ensure(s.C, (n + 2) * 8));
+  CPMA_TRY(ensure(h, s.cost, n + 1));
+  CPMA_TRY(ensure(h, s.C, (n + 2) * 8));
   if (E != P<uint64_t>(s.E)) return CPMA_EINTERNAL;
   // costs and stream bytes (one window, no source leaves)
   k_set_window<<<1, 1, 0, st>>>(P<uint64_t>(s.win_src), P<uint64_t>(s.win_dst),
@@ -2670,12 +2833,12 @@ int build_from_sorted_unique(cpma* h, const uint64_t* E, uint64_t n, cudaStream_
   uint64_t L = (uint64_t)((num + den - 1) / den);
   if (L < 1) L = 1;
   Arrays na;
-  CPMA_TRY(alloc_arrays(L, LB, &na));
+  CPMA_TRY(alloc_arrays(h, L, L * LB, &na, st));
   k_set_window<<<1, 1, 0, st>>>(P<uint64_t>(s.win_src), P<uint64_t>(s.win_dst),
                                 P<uint64_t>(s.win_leaf_off), P<uint64_t>(s.win_dst_off), 0, 0, 0,
                                 L);
   h->launches++;
-  CPMA_TRY(ensure(s.dstart, (L + 1) * 8));
+  CPMA_TRY(ensure(h, s.dstart, (L + 1) * 8));
   k_starts<<<grid_for(h, L), kT, 0, st>>>(w, P<uint64_t>(s.C), L, P<uint64_t>(s.dstart));
   h->launches++;
   EncodeArgs ea;
@@ -2691,12 +2854,23 @@ int build_from_sorted_unique(cpma* h, const uint64_t* E, uint64_t n, cudaStream_
   ea.LB = LB;
   ea.st = h->d_status;
   ea.raw = (int)h->cfg.codec;
-  k_encode<<<grid_for(h, L * 32), kT, (size_t)(kT / 32) * LB, st>>>(ea);
-  h->launches++;
-  CPMA_CUDA(cudaGetLastError());
-  CPMA_CUDA(cudaStreamSynchronize(st));
-  if (h->data) free_arrays(Arrays{h->data, h->used, h->cnt, h->heads});
-  h->data = na.data; h->used = na.used; h->cnt = na.cnt; h->heads = na.heads;
+  // the byte total restarts with the new leaves (the encode adds them)
+  int rc = check_cuda(cudaMemsetAsync(&h->d_status->bytes_total, 0, 8, st));
+  if (rc == CPMA_OK) {
+    k_encode<<<grid_for(h, L * 32), kT, (size_t)(kT / 32) * LB, st>>>(ea);
+    h->launches++;
+    rc = check_cuda(cudaGetLastError());
+  }
+  if (rc == CPMA_OK) rc = check_cuda(cudaStreamSynchronize(st));
+  if (rc != CPMA_OK) {
+    free_arrays(h, &na);
+    return rc;
+  }
+  Arrays old = live_arrays(h);
+  free_arrays(h, &old);
+  free_arrays(h, &h->spare);
+  set_live(h, na);
+  h->cfg.leaf_bytes = LB;
   h->L = L;
   h->n = n;
   Levels lv;
@@ -2706,6 +2880,8 @@ int build_from_sorted_unique(cpma* h, const uint64_t* E, uint64_t n, cudaStream_
   CPMA_TRY(sync_status(h, st));
   if (h->h_status->err) return CPMA_EINTERNAL;
   h->may_have_empty = h->h_status->empties > 0;
+  h->t_known = h->h_status->bytes_total;
+  h->t_slack = 0;
   return CPMA_OK;
 }
 

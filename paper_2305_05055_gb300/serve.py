@@ -4,7 +4,13 @@ Clients send insert, delete and range-sum requests.  The loop runs in epochs:
 
 1. every request that has arrived is admitted, in arrival order, while the
    device memory it needs fits the budget (structure + library scratch +
-   admitted payloads); the rest wait for the next epoch;
+   admitted payloads); the rest wait for the next epoch.  The budget is also
+   the library's own memory cap (cpma_set_mem_budget): an update whose
+   reservation would exceed it is refused before it changes anything
+   (CPMA_ENOMEM), and the loop then defers that run and every request
+   admitted after it to the next epoch, which admits them again at the
+   front; a single update that does not fit even alone completes with the
+   result "ENOMEM";
 2. the admitted updates are cut into runs of consecutive requests of the same
    kind; each run is one tagged batch (the library credits every key it adds
    or removes to the request of its first occurrence), so each request's
@@ -113,7 +119,12 @@ class Server:
         self.s_upd = torch.cuda.Stream()
         self.s_read = torch.cuda.Stream()
         self.epochs: list[EpochLog] = []
-        self.stats = dict(epochs=0, admitted=0, deferred=0, max_epoch_requests=0)
+        self.stats = dict(epochs=0, admitted=0, deferred=0, deferred_runs=0, rejected=0,
+                          max_epoch_requests=0)
+        g.set_mem_budget(self.budget)
+        # most requests per run: halved when the library refuses a run for
+        # memory, doubled back after an epoch without refusal
+        self.run_cap = self.max_epoch
         # pinned staging for a run's keys and tags, reused: every run's copy
         # has completed before the next run is staged (each run ends with a
         # wait on the update stream)
@@ -147,7 +158,7 @@ class Server:
         for r in batch:
             if r.kind == "range":
                 continue
-            if runs and runs[-1][0] == r.kind:
+            if runs and runs[-1][0] == r.kind and len(runs[-1][1]) < self.run_cap:
                 runs[-1][1].append(r)
             else:
                 runs.append((r.kind, [r]))
@@ -195,28 +206,55 @@ class Server:
                         time.sleep(min(wait, 0.002))
                 continue
             self.stats["epochs"] += 1
-            self.stats["admitted"] += len(batch)
             self.stats["max_epoch_requests"] = max(self.stats["max_epoch_requests"], len(batch))
             log = EpochLog()
             runs = self._runs(batch)
-            prepared = self._prepare_run(runs[0][1]) if runs else None
+            prepared = None
+            if runs:  # sorted while the previous epoch's reads still run
+                try:
+                    prepared = self._prepare_run(runs[0][1])
+                except cp.CPMAError as e:
+                    if e.code != cp.CPMA_ENOMEM:
+                        raise
             # the structure changes only after the previous epoch's reads
             if reads_done is not None:
                 self.s_upd.wait_event(reads_done)
+            cut = len(batch)  # requests of the batch served in this epoch
             for ri, (kind, reqs) in enumerate(runs):
-                sk, st = prepared if ri == 0 else self._prepare_run(reqs)
-                fn = cp.cpma_insert_batch_tagged if kind == "insert" else cp.cpma_delete_batch_tagged
-                with torch.cuda.stream(self.s_upd):
-                    counts = torch.empty(len(reqs), dtype=torch.int64, device=self.dev)
-                    fn(self.g.handle, sk, st, len(reqs), counts=counts, sorted=True,
-                       stream=self.s_upd)
-                    res = counts.cpu()
+                try:
+                    sk, st = (prepared if ri == 0 and prepared is not None
+                              else self._prepare_run(reqs))
+                    fn = (cp.cpma_insert_batch_tagged if kind == "insert"
+                          else cp.cpma_delete_batch_tagged)
+                    with torch.cuda.stream(self.s_upd):
+                        counts = torch.empty(len(reqs), dtype=torch.int64, device=self.dev)
+                        fn(self.g.handle, sk, st, len(reqs), counts=counts, sorted=True,
+                           stream=self.s_upd)
+                        res = counts.cpu()
+                except cp.CPMAError as e:
+                    if e.code != cp.CPMA_ENOMEM:
+                        raise
+                    # refused before any change: this run and everything
+                    # admitted after it go back to the front of the queue
+                    cut = batch.index(reqs[0])
+                    if cut == 0 and len(reqs) == 1:
+                        reqs[0].result = "ENOMEM"   # too large even alone
+                        reqs[0].done = clock() - t0
+                        self.stats["rejected"] += 1
+                        cut = 1
+                    self.stats["deferred_runs"] += 1
+                    self.run_cap = max(1, len(reqs) // 2)
+                    waiting.extendleft(reversed(batch[cut:]))
+                    break
                 t = clock() - t0
                 for i, r in enumerate(reqs):
                     r.result = int(res[i])
                     r.done = t
                 log.runs.append((kind, [r.rid for r in reqs]))
-            reads = [r for r in batch if r.kind == "range"]
+            self.stats["admitted"] += cut
+            if cut == len(batch):
+                self.run_cap = min(self.max_epoch, 2 * self.run_cap)
+            reads = [r for r in batch[:cut] if r.kind == "range"]
             if reads:
                 upd_done = torch.cuda.Event()
                 upd_done.record(self.s_upd)

@@ -30,6 +30,7 @@ def T(a):
 
 def same_layout(g, o):
     assert g.leaves() == o.leaves()
+    assert g.leaf_bytes() == o.leaf_bytes()
     data, used, heads = g.layout()
     od, ou, oh = o.layout()
     gu = used.cpu().numpy().view(np.uint32)
@@ -40,7 +41,7 @@ def same_layout(g, o):
     assert np.array_equal(gh, oh), np.nonzero(gh != oh)[0][:10]
     gd = data.cpu().numpy()
     if not np.array_equal(gd, od):
-        LB = g.config.leaf_bytes
+        LB = g.leaf_bytes()
         bad = np.unique(np.nonzero(gd != od)[0] // LB)[:10]
         raise AssertionError("leaf bytes differ in leaves %s" % bad)
     assert g.size() == o.size()
@@ -143,6 +144,36 @@ def test_growing_factors_grow_and_shrink(num, den):
         Ls.append(g.leaves())
     same_queries(g, p, 880)
     assert max(Ls) > Ls[0] and Ls[-1] < max(Ls), Ls
+
+
+@pytest.mark.parametrize("growth", [16, 40])
+def test_leaf_size_growing_with_n(growth):
+    # R13 (Sec. 5: leaves of Theta(log n)): every build and resize sets the
+    # leaf size for the key count it will hold; layout parity after every
+    # batch while the set grows from 3000 to ~3e5 keys and back, and the leaf
+    # size must have moved both ways.
+    cfg = dict(leaf_bytes=256, leaf_growth=growth)
+    base = W.uniform_keys(41, 3000, bits=40)
+    g = cp.CPMA(T(base), **cfg)
+    o = oracle.SeqCPMA(base, **cfg)
+    p = oracle.PlainSet(base)
+    same_layout(g, o)
+    assert g.leaf_bytes() == o.leaf_bytes()
+    sizes = [g.leaf_bytes()]
+    for r in range(7):
+        keys = W.uniform_keys(950 + r, 4000 * 2 ** r, bits=40)
+        assert int(g.insert_batch(T(keys)).item()) == o.insert_batch(keys) == p.insert_batch(keys)
+        same_layout(g, o)
+        sizes.append(g.leaf_bytes())
+    same_queries(g, p, 960)
+    for r in range(5):
+        keys = W.sample_present(p.S, 970 + r, (len(p) * 3) // 4)
+        assert int(g.delete_batch(T(keys)).item()) == o.delete_batch(keys) == p.delete_batch(keys)
+        assert o.check() == 0
+        same_layout(g, o)
+        sizes.append(g.leaf_bytes())
+    same_queries(g, p, 980)
+    assert max(sizes) > sizes[0] and sizes[-1] < max(sizes), sizes
 
 
 def test_grow_from_empty_and_delete_everything():

@@ -252,6 +252,69 @@ def test_resize_leaf_counts_other_growing_factors():
         assert R(1536, 10, 512, 700, 300, num, den) == 10
 
 
+def test_leaf_size_grows_with_log_n():
+    # R13: LB(n) = min(2048, max(LB_min, 16 ceil(g bitlen(n) / 16))); g = 0
+    # keeps LB_min
+    S = oracle.leaf_size
+    assert S(10 ** 8, 512, 0) == 512 and S(0, 256, 0) == 256
+    assert S(0, 256, 16) == 256                  # bitlen 0
+    assert S(10 ** 6, 256, 16) == 320            # bitlen 20: 320
+    assert S(10 ** 8, 256, 16) == 432            # bitlen 27: 432
+    assert S(1 << 63, 256, 16) == 1024           # bitlen 64
+    assert S(10 ** 8, 256, 40) == 1088           # 27 * 40 = 1080 -> 1088
+    assert S(1 << 30, 256, 100) == 2048          # 3100 clipped
+    assert S(4095, 256, 24) == 288 and S(4096, 256, 24) == 320   # bitlen 12 / 13
+    assert S(600, 256, 24) == 256                # 240 < LB_min
+
+
+def test_scenario_grow_with_leaf_growth():
+    # The grow scenario below with g = 24: the build of 600 keys keeps 256-byte
+    # leaves (bitlen 10: 240 < 256); after the insert the array holds 2397
+    # keys (bitlen 12: LB' = 288).  The resize starts from the leaf count of
+    # equal capacity, ceil(6 * 256 / 288) = 6, and grows while 1000 * 2439 >
+    # 700 * L' * 288: 6 -> 8 -> 10 -> 12 (2,419,200) -> 15.  The cut points do
+    # not depend on LB, so the used bytes and heads are those of the 6/5 case.
+    o = oracle.SeqCPMA([4 * i for i in range(600)][::-1] + [8, 8, 12], leaf_bytes=256,
+                       leaf_growth=24, **CFG)
+    assert o.leaf_bytes() == 256 and o.leaves() == 6
+    ins = [4 * i + r for i in range(599) for r in (1, 2, 3)]
+    assert o.insert_batch(ins) == 1797
+    assert o.last_batch()["resized"] == 1
+    assert o.leaf_bytes() == 288 and o.leaves() == 15
+    assert o.bytes() == 15 * (288 + 16)
+    s = [0] + [2404 * w // 15 - 7 for w in range(1, 15)] + [2397]
+    data, used, head = o.layout()
+    assert data.size == 15 * 288
+    assert list(used) == [s[w + 1] - s[w] + 7 for w in range(15)]
+    elems = sorted([4 * i for i in range(600)] + ins)
+    assert list(head) == [elems[s[w]] for w in range(15)]
+    assert o.check() == 0
+
+
+def test_scenario_shrink_with_leaf_growth():
+    # g = 24, LB_min = 256.  Build from 4i, i < 5000: bitlen 13 -> LB = 320;
+    # stream S = 8 + 4999 = 5007 bytes, L = ceil(5,007,000 / (500*320 -
+    # 8000)) = 33.  Deleting 4i for 100 <= i < 4900 leaves 200 keys (bitlen 8:
+    # 192 -> LB' = 256): leaves 0 and 32 keep 100 keys each (107 bytes), the
+    # others empty; the walks pass the root (214 bytes against 300 permille
+    # of 33 * 320), so resize: start at ceil(33 * 320 / 256) = 42, shrink
+    # while 214,000 < 300 * L' * 256: 42 -> 35 -> 29 -> 24 -> 20 -> 16 -> 13
+    # -> 10 -> 8 -> 6 -> 5 -> 4 -> 3 -> 2 (153,600: stop).  Costs: head 8,
+    # then 1 per delta of 4 except 19600 - 396 = 19204 (3 bytes): S = 209;
+    # s_1 = min{i : C_i >= 104} = 97 (C_i = i + 7 up to i = 100), so leaf 0
+    # holds elements 0..96 (8 + 96 = 104 bytes) and leaf 1 the rest, from key
+    # 388 (8 + 2 + 3 + 99 = 112 bytes).
+    o = oracle.SeqCPMA([4 * i for i in range(5000)], leaf_bytes=256, leaf_growth=24, **CFG)
+    assert o.leaf_bytes() == 320 and o.leaves() == 33
+    assert o.delete_batch([4 * i for i in range(100, 4900)]) == 4800
+    assert o.last_batch()["resized"] == 1
+    assert o.leaf_bytes() == 256 and o.leaves() == 2
+    _, used, head = o.layout()
+    assert list(used) == [104, 112] and list(head) == [0, 388]
+    assert o.bytes() == 2 * (256 + 16)
+    assert o.check() == 0
+
+
 @pytest.mark.parametrize("num,den,Lp", [(6, 5, 15), (11, 10, 15), (3, 2, 14), (2, 1, 24)])
 def test_scenario_grow(num, den, Lp):
     # Insert 4i+1, 4i+2, 4i+3 for every i < 599: 1797 keys, every delta

@@ -42,6 +42,44 @@ def test_served_results_equal_one_at_a_time():
     stats = srv.run(trace)
     assert stats["epochs"] < len(trace)            # requests were coalesced
     assert max(len(e.runs) for e in srv.epochs) >= 1
+    check_serial(g, base, trace, srv)
+
+
+def test_tight_budget_defers_runs_and_keeps_results():
+    # All requests arrive at once, nearly all inserts, so the first epoch
+    # coalesces them into one large run.  The budget is the most memory a
+    # handle held while applying every insert in runs no larger than the
+    # largest single request (measured on a probe), plus 1 MiB: the large run is refused by
+    # the library (CPMA_ENOMEM, nothing changed), the loop defers it with a
+    # smaller run size, and every result still equals its serial replay.  The
+    # probe is built like the served handle, so both hold the same scratch.
+    base = W.uniform_keys(93, 100000, bits=40)
+    S = np.unique(base)
+    trace = serve.make_trace(300, rate=1e7, seed=94, present_keys=S, sorted_keys=S,
+                             max_insert=3000, max_delete=500, min_width=1, max_width=30000,
+                             p_insert=0.9, p_delete=0.05)
+    g = cp.CPMA(T(base), leaf_bytes=512)
+    ups = [r.keys for r in trace if r.kind != "range"]
+    biggest = max(k.size for k in ups)
+    allk = np.concatenate([r.keys for r in trace if r.kind == "insert"])
+    probe = cp.CPMA(T(base), leaf_bytes=512)
+    for i in range(0, allk.size, biggest):     # the loop's form: sorted, tagged runs
+        k = T(allk[i:i + biggest])
+        tg = torch.zeros(k.numel(), dtype=torch.int32, device="cuda")
+        sk, st = cp.cpma_sort_batch(probe.handle, k, tg)
+        cp.cpma_insert_batch_tagged(probe.handle, sk, st, 1, sorted=True)
+    probe.range_map(T(S[:400]), T(S[1:401]))
+    budget = probe.mem_peak() + (1 << 20)
+    del probe
+    srv = serve.Server(g, mem_budget_bytes=budget)
+    stats = srv.run(trace)
+    assert stats["deferred_runs"] > 0 and stats["rejected"] == 0, stats
+    assert g.mem_held() <= budget
+    check_serial(g, base, trace, srv)
+
+
+def check_serial(g, base, trace, srv):
+    """Every served result equals the request run alone in the loop's order."""
     by_id = {r.rid: r for r in trace}
     served = {r.rid: r.result for r in trace}
     # 1. the oracle, one request at a time in the served order
