@@ -15,13 +15,15 @@
 // the first scratch buffer.  No host round trip.  Batches of at most one tile
 // are sorted by a single block.
 //
-// Batches of up to 1.25M keys go most significant digit first instead: one
-// scatter pass by the highest varying digit (same tile ranking and
-// look-back), then each of its 256 buckets (k / 256 keys on average) is sorted
-// by the lower digits in the shared memory of one block.  Three reads and two
-// writes of the batch instead of six and five.  A bucket of more than 6144
-// keys (heavy repeats) sets a flag, and the digit passes, launched gated on
-// that flag, sort the input again from scratch.
+// Batches of up to 1.25M keys go most significant bits first instead: one
+// pass takes the OR and AND of the keys, which give the 8 highest bits that
+// vary; one pass counts them (256 buckets); one scatter pass (the same tile
+// ranking and look-back) moves the keys to their buckets, and each bucket is
+// then sorted by the bits below them in one block: in shared memory when it
+// holds at most 6144 keys (k / 256 on average), else (heavy repeats or skew)
+// by a block-level LSD radix sort through global memory.  Three reads and
+// two writes of the batch instead of six and five, with no pass that
+// depends on how the keys fall.
 #include <algorithm>
 
 #include "dev_common.cuh"
@@ -145,8 +147,83 @@ struct SortCtl {
   uint32_t done_blocks;    // histogram blocks finished
   uint32_t tile_ctr[9];    // next tile id per pass (8: the top-digit scatter)
   uint32_t top;            // highest varying digit
-  uint32_t fallback;       // a top-digit bucket exceeded kBTile: the digit passes run
+  // bucket path: OR / AND of every key, and the bucket field they give: the
+  // top 8 varying bits, bits [fshift, fshift + 8)
+  ull or_all, and_all;
+  uint32_t fshift;
+  uint32_t done_or;        // OR/AND blocks finished
 };
+
+__device__ __forceinline__ uint32_t bucket_of(uint64_t x, uint32_t fshift) {
+  return (uint32_t)(x >> fshift) & 255u;
+}
+
+// Bucket path, pass 1: OR and AND of the keys; the last block turns them into
+// the bucket field (the 8 highest bits that vary; fewer when fewer vary) and
+// npass (0 when every key is equal).
+__global__ void __launch_bounds__(kT) k_orand(const uint64_t* __restrict__ in, uint64_t k,
+                                              SortCtl* ctl) {
+  __shared__ ull s_or[kWarps], s_and[kWarps];
+  __shared__ bool last;
+  ull o = 0, a = ~0ull;
+  for (uint64_t i = (uint64_t)blockIdx.x * kT + threadIdx.x; i < k; i += (uint64_t)gridDim.x * kT) {
+    const uint64_t x = in[i];
+    o |= x;
+    a &= x;
+  }
+  const uint32_t olo = __reduce_or_sync(FULL, (uint32_t)o), ohi = __reduce_or_sync(FULL, (uint32_t)(o >> 32));
+  const uint32_t alo = __reduce_and_sync(FULL, (uint32_t)a), ahi = __reduce_and_sync(FULL, (uint32_t)(a >> 32));
+  if (lane_id() == 0) {
+    s_or[threadIdx.x >> 5] = ((ull)ohi << 32) | olo;
+    s_and[threadIdx.x >> 5] = ((ull)ahi << 32) | alo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ull bo = 0, ba = ~0ull;
+    for (int w = 0; w < kWarps; w++) { bo |= s_or[w]; ba &= s_and[w]; }
+    atomicOr(&ctl->or_all, bo);
+    atomicAnd(&ctl->and_all, ba);
+    __threadfence();
+    last = atomicAdd(&ctl->done_or, 1u) == gridDim.x - 1;
+    if (last) {
+      __threadfence();
+      const ull vary = *((volatile ull*)&ctl->or_all) ^ *((volatile ull*)&ctl->and_all);
+      const uint32_t hb = vary ? 64u - (uint32_t)__clzll((long long)vary) : 0u;
+      ctl->fshift = hb > 8u ? hb - 8u : 0u;
+      ctl->npass = vary ? 1u : 0u;
+    }
+  }
+}
+
+// Bucket path, pass 2: histogram of the bucket field; the last block writes
+// the buckets' exclusive offsets (hist[0], off[0]).
+__global__ void __launch_bounds__(kT) k_hist_field(const uint64_t* __restrict__ in, uint64_t k,
+                                                   SortCtl* ctl) {
+  __shared__ uint32_t hs[256];
+  __shared__ bool last;
+  __shared__ uint32_t wt[kWarps];
+  hs[threadIdx.x] = 0;  // kT == 256
+  __syncthreads();
+  const uint32_t fs = ctl->fshift;
+  for (uint64_t i = (uint64_t)blockIdx.x * kT + threadIdx.x; i < k; i += (uint64_t)gridDim.x * kT)
+    atomicAdd(&hs[bucket_of(in[i], fs)], 1u);
+  __syncthreads();
+  if (hs[threadIdx.x]) atomicAdd(&ctl->hist[0][threadIdx.x], hs[threadIdx.x]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&ctl->done_blocks, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const uint32_t d = threadIdx.x;
+  const uint32_t v = *((volatile uint32_t*)&ctl->hist[0][d]);
+  const uint32_t inc = warp_incl_scan(v);
+  if (lane_id() == 31) wt[d >> 5] = inc;
+  __syncthreads();
+  uint32_t wbase = 0;
+  for (unsigned q = 0; q < (d >> 5); q++) wbase += wt[q];
+  ctl->off[0][d] = wbase + inc - v;
+}
 
 __global__ void __launch_bounds__(kT) k_hist_all(const uint64_t* __restrict__ in, uint64_t k,
                                                  SortCtl* ctl) {
@@ -211,17 +288,17 @@ __global__ void k_copy_if_no_pass(const uint64_t* __restrict__ in, uint64_t* __r
 
 // One digit pass.  Buffers: the input, then A and B alternately, arranged so
 // that the last varying pass writes A.  With top != 0 it is instead the
-// stable scatter of the input by its highest varying digit into B (the
-// buckets k_bucket_sort finishes); with gate != 0 it runs only if a bucket
-// overflowed.  Blocks take tiles in order from a counter until none is left,
-// so the grid can be smaller than the tile count (a pass that does not run
-// costs one short launch).
+// stable scatter of the input by the bucket field (the 8 highest varying
+// bits) into B, the buckets k_bucket_sort finishes.  Blocks take tiles in
+// order from a counter until none is left, so the grid can be smaller than
+// the tile count (a pass over a digit that does not vary costs one short
+// launch).
 template <bool VALS>
 __global__ void __launch_bounds__(kT, 3) k_onesweep(const uint64_t* __restrict__ in,
                                                  const uint32_t* __restrict__ vin,
                                                  uint64_t* __restrict__ A, uint64_t* __restrict__ B,
                                                  uint32_t* __restrict__ VA, uint32_t* __restrict__ VB,
-                                                 uint64_t k, int p, int top, int gate, SortCtl* ctl,
+                                                 uint64_t k, int p, int top, SortCtl* ctl,
                                                  uint32_t* __restrict__ look, Status* st,
                                                  uint32_t spin_limit, uint32_t silent) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -233,16 +310,18 @@ __global__ void __launch_bounds__(kT, 3) k_onesweep(const uint64_t* __restrict__
   const uint32_t* vsrc;
   uint32_t* vdst;
   uint32_t* ctr;
+  int shift;
   if (top) {
     if (ctl->npass == 0) return;
-    p = (int)ctl->top;
+    p = 0;  // the bucket field's histogram and offsets are row 0
+    shift = (int)ctl->fshift;
     src = in;
     dst = B;
     vsrc = vin;
     vdst = VB;
     ctr = &ctl->tile_ctr[8];
   } else {
-    if (!ctl->varying[p] || (gate && !ctl->fallback)) return;
+    if (!ctl->varying[p]) return;
     const uint32_t r = ctl->rank[p], P = ctl->npass;
     // pass r writes B when P-1-r is odd, else A (so pass P-1 writes A) and
     // reads what pass r-1 wrote
@@ -251,8 +330,8 @@ __global__ void __launch_bounds__(kT, 3) k_onesweep(const uint64_t* __restrict__
     vsrc = (r == 0) ? vin : (((P - r) & 1u) ? VB : VA);
     vdst = ((P - 1u - r) & 1u) ? VB : VA;
     ctr = &ctl->tile_ctr[p];
+    shift = 8 * p;
   }
-  const int shift = 8 * p;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t ntiles = (uint32_t)((k + kTile - 1) / kTile);
   for (;;) {
@@ -324,67 +403,153 @@ __global__ void __launch_bounds__(kT, 3) k_onesweep(const uint64_t* __restrict__
   }
 }
 
-// Bucket b of the top-digit scatter (B[off .. off + count)), sorted stably by
-// every lower digit that varies inside it, in shared memory, into the same
-// positions of A.  A bucket of more than kBTile keys sets the fallback flag
-// instead (the digit passes then sort the whole batch again).
+// Bucket b of the field scatter (B[off .. off + n)), sorted stably by the
+// bits below the field, into the same positions of A.  A bucket of at most
+// kBTile keys is sorted in shared memory, digit by digit over the digits
+// that vary inside it.  A larger one (heavy repeats or skew) is sorted by a
+// block-level LSD radix sort through global memory: per varying digit, one
+// counting pass over the bucket, then its tiles in order, each ranked stably
+// in shared memory and scattered to the running digit offsets, alternating
+// between B and A (and copied to A if it ends in B).
 template <bool VALS>
-__global__ void __launch_bounds__(kBT, 2) k_bucket_sort(const uint64_t* __restrict__ B,
-                                                     const uint32_t* __restrict__ VB,
+__global__ void __launch_bounds__(kBT, 2) k_bucket_sort(uint64_t* __restrict__ B,
+                                                     uint32_t* __restrict__ VB,
                                                      uint64_t* __restrict__ A,
                                                      uint32_t* __restrict__ VA, SortCtl* ctl) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   TileSmemT<VALS, kBT, kBItems>& sm = *reinterpret_cast<TileSmemT<VALS, kBT, kBItems>*>(smem_raw);
   __shared__ ull s_or, s_and;
+  __shared__ uint32_t s_run[256];
+  __shared__ uint32_t s_wt[8];
   if (ctl->npass == 0) return;
-  const uint32_t top = ctl->top, b = blockIdx.x;
-  const uint32_t n = ctl->hist[top][b];
+  const uint32_t b = blockIdx.x;
+  const uint32_t n = ctl->hist[0][b];
   if (n == 0) return;
-  if (n > (uint32_t)kBTile) {
-    if (threadIdx.x == 0) atomicExch(&ctl->fallback, 1u);
-    return;
-  }
-  const uint64_t base = ctl->off[top][b];
+  const uint64_t base = ctl->off[0][b];
+  const uint32_t npd = (ctl->fshift + 7u) / 8u;  // digits below the field
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
-  // items per warp: the bucket spread over every warp, in element order
-  const uint32_t ipw = (n + 32u * (kBT / 32) - 1u) / (32u * (kBT / 32));
   if (threadIdx.x == 0) { s_or = 0; s_and = ~0ull; }
   __syncthreads();
-  uint64_t key[kBItems];
-  uint32_t val[kBItems];
-  ull o = 0, a = ~0ull;
+  if (n <= (uint32_t)kBTile) {
+    // items per warp: the bucket spread over every warp, in element order
+    const uint32_t ipw = (n + 32u * (kBT / 32) - 1u) / (32u * (kBT / 32));
+    uint64_t key[kBItems];
+    uint32_t val[kBItems];
+    ull o = 0, a = ~0ull;
 #pragma unroll
-  for (int j = 0; j < kBItems; j++) {
-    const uint32_t li = warp * 32 * ipw + j * 32 + lane;
-    const bool ok = (uint32_t)j < ipw && li < n;
-    key[j] = ok ? B[base + li] : 0ull;
-    if constexpr (VALS) val[j] = ok ? VB[base + li] : 0u;
-    else val[j] = 0u;
-    if (ok) { o |= key[j]; a &= key[j]; }
-  }
-  atomicOr(&s_or, o);
-  atomicAnd(&s_and, a);
-  __syncthreads();
-  const ull vary = s_or ^ s_and;
-  for (uint32_t p = 0; p < top; p++) {
-    if (((vary >> (8 * p)) & 255u) == 0) continue;
-    tile_rank<VALS, kBT, kBItems>(key, val, n, 8 * (int)p, sm, ipw);
+    for (int j = 0; j < kBItems; j++) {
+      const uint32_t li = warp * 32 * ipw + j * 32 + lane;
+      const bool ok = (uint32_t)j < ipw && li < n;
+      key[j] = ok ? B[base + li] : 0ull;
+      if constexpr (VALS) val[j] = ok ? VB[base + li] : 0u;
+      else val[j] = 0u;
+      if (ok) { o |= key[j]; a &= key[j]; }
+    }
+    atomicOr(&s_or, o);
+    atomicAnd(&s_and, a);
+    __syncthreads();
+    const ull vary = s_or ^ s_and;
+    for (uint32_t p = 0; p < npd; p++) {
+      if (((vary >> (8 * p)) & 255u) == 0) continue;
+      tile_rank<VALS, kBT, kBItems>(key, val, n, 8 * (int)p, sm, ipw);
+#pragma unroll
+      for (int j = 0; j < kBItems; j++) {
+        const uint32_t li = warp * 32 * ipw + j * 32 + lane;
+        if ((uint32_t)j < ipw && li < n) {
+          key[j] = sm.keys[li];
+          if constexpr (VALS) val[j] = sm.vals[li];
+        }
+      }
+      __syncthreads();
+    }
 #pragma unroll
     for (int j = 0; j < kBItems; j++) {
       const uint32_t li = warp * 32 * ipw + j * 32 + lane;
       if ((uint32_t)j < ipw && li < n) {
-        key[j] = sm.keys[li];
-        if constexpr (VALS) val[j] = sm.vals[li];
+        A[base + li] = key[j];
+        if constexpr (VALS) VA[base + li] = val[j];
       }
     }
+    return;
+  }
+  // ---- oversized bucket: block-level LSD through global memory ----
+  {
+    ull o = 0, a = ~0ull;
+    for (uint32_t i = threadIdx.x; i < n; i += kBT) {
+      const uint64_t x = B[base + i];
+      o |= x;
+      a &= x;
+    }
+    atomicOr(&s_or, o);
+    atomicAnd(&s_and, a);
+  }
+  __syncthreads();
+  const ull vary = s_or ^ s_and;
+  uint64_t* src = B + base;
+  uint64_t* dst = A + base;
+  uint32_t* vsrc = VALS ? VB + base : nullptr;
+  uint32_t* vdst = VALS ? VA + base : nullptr;
+  bool in_a = false;
+  for (uint32_t p = 0; p < npd; p++) {
+    if (((vary >> (8 * p)) & 255u) == 0) continue;
+    const int shift = 8 * (int)p;
+    // counting pass, then exclusive offsets of the digits
+    if (threadIdx.x < 256) s_run[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += kBT)
+      atomicAdd(&s_run[(uint32_t)(src[i] >> shift) & 255u], 1u);
+    __syncthreads();
+    uint32_t v = 0, inc = 0;
+    if (threadIdx.x < 256) {
+      v = s_run[threadIdx.x];
+      inc = warp_incl_scan(v);
+      if (lane == 31) s_wt[warp] = inc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {
+      uint32_t wbase = 0;
+      for (unsigned q = 0; q < warp; q++) wbase += s_wt[q];
+      s_run[threadIdx.x] = wbase + inc - v;
+    }
+    __syncthreads();
+    // the tiles in order: stable rank, scatter to the running offsets
+    for (uint32_t t0 = 0; t0 < n; t0 += (uint32_t)kBTile) {
+      const uint32_t nv = min((uint32_t)kBTile, n - t0);
+      const uint32_t ipw = (nv + 32u * (kBT / 32) - 1u) / (32u * (kBT / 32));
+      uint64_t key[kBItems];
+      uint32_t val[kBItems];
+#pragma unroll
+      for (int j = 0; j < kBItems; j++) {
+        const uint32_t li = warp * 32 * ipw + j * 32 + lane;
+        const bool ok = (uint32_t)j < ipw && li < nv;
+        key[j] = ok ? src[t0 + li] : 0ull;
+        if constexpr (VALS) val[j] = ok ? vsrc[t0 + li] : 0u;
+        else val[j] = 0u;
+      }
+      tile_rank<VALS, kBT, kBItems>(key, val, nv, shift, sm, ipw);
+      for (uint32_t i = threadIdx.x; i < nv; i += kBT) {
+        const uint64_t x = sm.keys[i];
+        const uint32_t d = (uint32_t)(x >> shift) & 255u;
+        const uint32_t o = s_run[d] + (i - sm.dstart[d]);
+        dst[o] = x;
+        if constexpr (VALS) vdst[o] = sm.vals[i];
+      }
+      __syncthreads();
+      if (threadIdx.x < 256) {
+        const uint32_t d = threadIdx.x;
+        s_run[d] += (d < 255 ? sm.dstart[d + 1] : nv) - sm.dstart[d];
+      }
+      __syncthreads();
+    }
+    uint64_t* t = src; src = dst; dst = t;
+    uint32_t* tv = vsrc; vsrc = vdst; vdst = tv;
+    in_a = !in_a;
     __syncthreads();
   }
-#pragma unroll
-  for (int j = 0; j < kBItems; j++) {
-    const uint32_t li = warp * 32 * ipw + j * 32 + lane;
-    if ((uint32_t)j < ipw && li < n) {
-      A[base + li] = key[j];
-      if constexpr (VALS) VA[base + li] = val[j];
+  if (!in_a) {
+    for (uint32_t i = threadIdx.x; i < n; i += kBT) {
+      A[base + i] = B[base + i];
+      if constexpr (VALS) VA[base + i] = VB[base + i];
     }
   }
 }
@@ -461,9 +626,9 @@ __global__ void k_unique_scatter(const uint64_t* __restrict__ in, uint64_t k,
 
 namespace {
 size_t ctl_bytes() { return (sizeof(SortCtl) + 255) & ~(size_t)255; }
-size_t look_bytes(uint64_t k) {  // eight digit passes and the top-digit scatter
+size_t look_bytes(uint64_t k) {  // one array per digit pass (the bucket path uses one)
   const uint64_t ntiles = (k + kTile - 1) / kTile;
-  return (size_t)9 * ntiles * 256 * 4;
+  return (size_t)8 * ntiles * 256 * 4;
 }
 template <bool VALS>
 int& sweep_blocks_per_sm() {
@@ -526,37 +691,42 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
   const uint32_t spin = h->sort_poll_limit ? h->sort_poll_limit : kSpinLimit;
   const uint32_t silent = h->sort_silent_tile >= 0 && h->sort_silent_tile < (int64_t)ntiles
                               ? (uint32_t)h->sort_silent_tile : 0xFFFFFFFFu;
-  // control block + 9 look-back arrays, zeroed in one memset
   SortCtl* ctl = reinterpret_cast<SortCtl*>(h->s.hist.p);
   uint32_t* look = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(h->s.hist.p) + ctl_bytes());
-  CPMA_CUDA(cudaMemsetAsync(h->s.hist.p, 0, ctl_bytes() + look_bytes(k), st));
   const int hgrid = (int)std::min<uint64_t>((uint64_t)h->num_sms * 2, (k + kT - 1) / kT);
-  k_hist_all<<<hgrid, kT, 0, st>>>(d_in, k, ctl);
-  h->launches++;
-  prof_add_bytes(h, PH_SORT, 8ull * k);  // the histogram read
   const unsigned sgrid = (unsigned)std::min<uint64_t>(
       ntiles, (uint64_t)h->num_sms * (uint64_t)sweep_blocks_per_sm<VALS>());
-  const bool buckets = k <= kBucketMax;
-  if (buckets) {
-    // scatter by the highest varying digit, then each of its 256 buckets
-    // sorted in shared memory; the digit passes below run only if a bucket
-    // overflowed
-    k_onesweep<VALS><<<sgrid, kT, smem, st>>>(d_in, v_in, A, B, VA, VB, k, 0, 1, 0, ctl,
-                                               look + (size_t)8 * ntiles * 256, h->d_status,
-                                               spin, silent);
+  if (k <= kBucketMax) {
+    // most significant bits first: OR / AND of the keys give the 8 highest
+    // bits that vary, their histogram, one scatter into 256 buckets by them,
+    // then every bucket sorted by the bits below in one block.  The control
+    // block and one look-back array are zeroed first (and_all starts at ~0).
+    CPMA_CUDA(cudaMemsetAsync(h->s.hist.p, 0, ctl_bytes() + (size_t)ntiles * 256 * 4, st));
+    CPMA_CUDA(cudaMemsetAsync(&ctl->and_all, 0xFF, sizeof(ull), st));
+    k_orand<<<hgrid, kT, 0, st>>>(d_in, k, ctl);
+    k_hist_field<<<hgrid, kT, 0, st>>>(d_in, k, ctl);
+    k_onesweep<VALS><<<sgrid, kT, smem, st>>>(d_in, v_in, A, B, VA, VB, k, 0, 1, ctl, look,
+                                               h->d_status, spin, silent);
     k_bucket_sort<VALS><<<256, kBT, sizeof(TileSmemT<VALS, kBT, kBItems>), st>>>(B, VB, A, VA,
                                                                                  ctl);
-    h->launches += 2;
-    prof_add_bytes(h, PH_SORT, (VALS ? 24ull : 16ull) * k * 2);
-  }
-  for (int p = 0; p < 8; p++) {
-    // digits that vary: the scatter reads and writes keys (and tags)
-    k_onesweep<VALS><<<sgrid, kT, smem, st>>>(d_in, v_in, A, B, VA, VB, k, p, 0, buckets ? 1 : 0,
-                                               ctl, look + (size_t)p * ntiles * 256, h->d_status,
-                                               spin, silent);
+    h->launches += 4;
+    // OR/AND and histogram reads, scatter and bucket read + write
+    prof_add_bytes(h, PH_SORT, 16ull * k + (VALS ? 24ull : 16ull) * k * 2);
+  } else {
+    // least significant digit first over the digits that vary
+    CPMA_CUDA(cudaMemsetAsync(h->s.hist.p, 0, ctl_bytes() + look_bytes(k), st));
+    k_hist_all<<<hgrid, kT, 0, st>>>(d_in, k, ctl);
     h->launches++;
+    prof_add_bytes(h, PH_SORT, 8ull * k);  // the histogram read
+    for (int p = 0; p < 8; p++) {
+      // digits that vary: the scatter reads and writes keys (and tags)
+      k_onesweep<VALS><<<sgrid, kT, smem, st>>>(d_in, v_in, A, B, VA, VB, k, p, 0, ctl,
+                                                 look + (size_t)p * ntiles * 256, h->d_status,
+                                                 spin, silent);
+      h->launches++;
+    }
+    prof_add_bytes(h, PH_SORT, (VALS ? 24ull : 16ull) * k * 5);  // typical: 5 varying digits
   }
-  if (!buckets) prof_add_bytes(h, PH_SORT, (VALS ? 24ull : 16ull) * k * 5);  // typical: 5 varying digits
   k_copy_if_no_pass<<<std::min<uint64_t>((uint64_t)h->num_sms * 4, (k + kT - 1) / kT), kT, 0, st>>>(
       d_in, A, v_in, VA, k, ctl);
   h->launches++;

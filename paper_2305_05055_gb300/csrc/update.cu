@@ -2717,7 +2717,10 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   uint64_t t_slack = 0;
   const uint64_t delta = hs.delta;
   const uint64_t n_after = is_delete ? h->n - delta : h->n + delta;
-  if (hs.nempty || hs.empties) h->may_have_empty = true;
+  // empty leaves: made by this batch's merges, or left when the last head
+  // fix-up ran (a window redistribution never empties a leaf: each gets
+  // about S/W >= rho_leaf LB > 10 bytes, more than one code)
+  h->may_have_empty = hs.nempty || hs.empties;
 
   // ---- pending leaves: materialise their merged elements ----
   if (hs.npend) {

@@ -1,10 +1,11 @@
 """GPU batch sort (cpma_sort_batch) against its plain definition: the keys in
 non-decreasing order, each tag travelling with its key, equal keys in input
 order (a stable sort: numpy's stable argsort).  The sizes and key shapes
-cover the single-tile sort, the top-digit buckets (batches of up to 1.25M
-keys), a bucket too large for one block (the digit passes take over), the
-digit passes alone (larger batches), and keys that vary in one digit only,
-in all eight, or not at all."""
+cover the single-tile sort, the buckets by the 8 highest varying bits
+(batches of up to 1.25M keys), buckets too large for one block's shared
+memory (sorted through global memory by that block), the digit passes
+(larger batches), 34-bit uniform and skewed keys, and keys that vary in one
+digit only, in all eight, in fewer than 8 bits, or not at all."""
 import numpy as np
 import pytest
 import torch
@@ -45,11 +46,28 @@ def test_sort_keys_only(handle):
 
 
 def test_sort_bucket_overflow(handle):
-    # 40% of the keys share one value: its top-digit bucket exceeds one block
+    # 40% of the keys share one value: its bucket far exceeds one block's
+    # shared memory (an oversized bucket with nothing to sort inside)
     k = 1_000_000
     keys = W.uniform_keys(11, k, bits=40)
     keys[W.permuted_indices(k, 400_000, 12)] = np.uint64(0x12_3456_789A)
     check(handle, keys)
+    # an oversized bucket whose keys differ: a narrow band of values takes
+    # a quarter of the batch (sorted through global memory, several digits)
+    band = W.uniform_keys(17, 250_000, bits=30) + np.uint64(0x55_0000_0000)
+    keys[:250_000] = band
+    check(handle, keys)
+
+
+@pytest.mark.parametrize("k", [20_000, 100_000, 1_000_000])
+def test_sort_34bit_uniform_and_zipf(handle, k):
+    check(handle, W.uniform_keys(41 + k, k, bits=34))
+    check(handle, W.zipf_keys(42 + k, k, bits=34))
+
+
+def test_sort_few_varying_bits(handle):
+    check(handle, W.uniform_keys(18, 50_000, bits=5) << np.uint64(20))   # fewer than 8 bits
+    check(handle, np.arange(70_000, dtype=np.uint64)[::-1].copy())       # dense, reversed
 
 
 def test_sort_one_varying_digit(handle):
