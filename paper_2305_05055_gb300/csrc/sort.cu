@@ -166,7 +166,17 @@ __global__ void __launch_bounds__(kT) k_orand(const uint64_t* __restrict__ in, u
   __shared__ ull s_or[kWarps], s_and[kWarps];
   __shared__ bool last;
   ull o = 0, a = ~0ull;
-  for (uint64_t i = (uint64_t)blockIdx.x * kT + threadIdx.x; i < k; i += (uint64_t)gridDim.x * kT) {
+  // eight keys per thread and step, loaded together
+  const uint64_t stride = (uint64_t)gridDim.x * kT;
+  uint64_t i = (uint64_t)blockIdx.x * kT + threadIdx.x;
+  for (; i + 7 * stride < k; i += 8 * stride) {
+    uint64_t x[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) x[j] = in[i + j * stride];
+#pragma unroll
+    for (int j = 0; j < 8; j++) { o |= x[j]; a &= x[j]; }
+  }
+  for (; i < k; i += stride) {
     const uint64_t x = in[i];
     o |= x;
     a &= x;
@@ -205,8 +215,16 @@ __global__ void __launch_bounds__(kT) k_hist_field(const uint64_t* __restrict__ 
   hs[threadIdx.x] = 0;  // kT == 256
   __syncthreads();
   const uint32_t fs = ctl->fshift;
-  for (uint64_t i = (uint64_t)blockIdx.x * kT + threadIdx.x; i < k; i += (uint64_t)gridDim.x * kT)
-    atomicAdd(&hs[bucket_of(in[i], fs)], 1u);
+  const uint64_t stride = (uint64_t)gridDim.x * kT;
+  uint64_t i = (uint64_t)blockIdx.x * kT + threadIdx.x;
+  for (; i + 7 * stride < k; i += 8 * stride) {  // eight keys per thread and step
+    uint64_t x[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) x[j] = in[i + j * stride];
+#pragma unroll
+    for (int j = 0; j < 8; j++) atomicAdd(&hs[bucket_of(x[j], fs)], 1u);
+  }
+  for (; i < k; i += stride) atomicAdd(&hs[bucket_of(in[i], fs)], 1u);
   __syncthreads();
   if (hs[threadIdx.x]) atomicAdd(&ctl->hist[0][threadIdx.x], hs[threadIdx.x]);
   __threadfence();
@@ -554,53 +572,40 @@ __global__ void __launch_bounds__(kBT, 2) k_bucket_sort(uint64_t* __restrict__ B
   }
 }
 
-// Whole batch in one tile: all varying digits in one block.
+// Batches of at most kTile keys: a stable rank sort spread over many
+// blocks.  Every block holds the whole batch in shared memory; P consecutive
+// threads share one key, each counting over a P-th of the batch the keys
+// below it and the equal keys before it, and the sum of their counts (a
+// shuffle reduction) is where the key (and its tag) goes.
+constexpr int kRankT = 256;
 template <bool VALS>
-__global__ void __launch_bounds__(kT) k_sort_small(const uint64_t* __restrict__ in,
-                                                   uint64_t* __restrict__ out,
-                                                   const uint32_t* __restrict__ vin,
-                                                   uint32_t* __restrict__ vout, uint32_t k) {
-  extern __shared__ __align__(16) uint8_t smem_raw[];
-  TileSmemT<VALS>& sm = *reinterpret_cast<TileSmemT<VALS>*>(smem_raw);
-  __shared__ ull s_or, s_and;
-  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) { s_or = 0; s_and = ~0ull; }
+__global__ void __launch_bounds__(kRankT) k_sort_rank(const uint64_t* __restrict__ in,
+                                                      uint64_t* __restrict__ out,
+                                                      const uint32_t* __restrict__ vin,
+                                                      uint32_t* __restrict__ vout, uint32_t k,
+                                                      uint32_t P) {
+  extern __shared__ __align__(16) uint64_t s_keys[];
+  for (uint32_t i = threadIdx.x; i < k; i += kRankT) s_keys[i] = in[i];
   __syncthreads();
-  uint64_t key[kItems];
-  uint32_t val[kItems];
-  ull o = 0, a = ~0ull;
-#pragma unroll
-  for (int j = 0; j < kItems; j++) {
-    const uint32_t li = warp * 32 * kItems + j * 32 + lane;
-    key[j] = li < k ? in[li] : 0ull;
-    if constexpr (VALS) val[j] = li < k ? vin[li] : 0u;
-    else val[j] = 0u;
-    if (li < k) { o |= key[j]; a &= key[j]; }
+  const uint32_t g = blockIdx.x * kRankT + threadIdx.x;
+  const uint32_t i = g / P, part = g % P;
+  const bool valid = i < k;
+  const uint64_t x = valid ? s_keys[i] : 0ull;
+  const uint32_t per = (k + P - 1) / P;
+  const uint32_t j0 = min(k, part * per), j1 = min(k, j0 + per);
+  uint32_t r = 0;
+  if (valid) {
+    // equal keys count only before i: two ranges with a fixed test
+    const uint32_t jm = min(max(i, j0), j1);
+#pragma unroll 8
+    for (uint32_t j = j0; j < jm; j++) r += s_keys[j] <= x;
+#pragma unroll 8
+    for (uint32_t j = jm; j < j1; j++) r += s_keys[j] < x;
   }
-  atomicOr(&s_or, o);
-  atomicAnd(&s_and, a);
-  __syncthreads();
-  const ull vary = s_or ^ s_and;
-  for (int p = 0; p < 8; p++) {
-    if (((vary >> (8 * p)) & 255u) == 0) continue;
-    tile_rank<VALS>(key, val, k, 8 * p, sm);
-#pragma unroll
-    for (int j = 0; j < kItems; j++) {
-      const uint32_t li = warp * 32 * kItems + j * 32 + lane;
-      if (li < k) {
-        key[j] = sm.keys[li];
-        if constexpr (VALS) val[j] = sm.vals[li];
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int j = 0; j < kItems; j++) {
-    const uint32_t li = warp * 32 * kItems + j * 32 + lane;
-    if (li < k) {
-      out[li] = key[j];
-      if constexpr (VALS) vout[li] = val[j];
-    }
+  for (uint32_t o = 1; o < P; o <<= 1) r += __shfl_xor_sync(FULL, r, o);
+  if (valid && part == 0) {
+    out[r] = x;
+    if constexpr (VALS) vout[r] = vin[i];
   }
 }
 
@@ -641,7 +646,6 @@ void sort_attrs() {
   if (done) return;
   const int smem = (int)sizeof(TileSmemT<VALS>);
   cudaFuncSetAttribute(k_onesweep<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_sort_small<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_bucket_sort<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sizeof(TileSmemT<VALS, kBT, kBItems>));
   int bps = 0;
@@ -678,7 +682,11 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
   const size_t smem = sizeof(TileSmemT<VALS>);
   if (k <= (uint64_t)kTile) {
     prof_add_bytes(h, PH_SORT, (VALS ? 24ull : 16ull) * k);
-    k_sort_small<VALS><<<1, kT, smem, st>>>(d_in, A, v_in, VA, (uint32_t)k);
+    // threads per key: a power of two keeping each thread's share at 256 keys
+    uint32_t P = 1;
+    while (P < 32 && k > 256ull * P) P <<= 1;
+    const uint32_t nb = (uint32_t)((k * P + kRankT - 1) / kRankT);
+    k_sort_rank<VALS><<<nb, kRankT, k * 8, st>>>(d_in, A, v_in, VA, (uint32_t)k, P);
     h->launches++;
     *out = A;
     if (vout) *vout = VA;
@@ -703,8 +711,11 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
     // block and one look-back array are zeroed first (and_all starts at ~0).
     CPMA_CUDA(cudaMemsetAsync(h->s.hist.p, 0, ctl_bytes() + (size_t)ntiles * 256 * 4, st));
     CPMA_CUDA(cudaMemsetAsync(&ctl->and_all, 0xFF, sizeof(ull), st));
-    k_orand<<<hgrid, kT, 0, st>>>(d_in, k, ctl);
-    k_hist_field<<<hgrid, kT, 0, st>>>(d_in, k, ctl);
+    // about eight keys per thread: one step of the unrolled loops
+    const int ogrid = (int)std::max<uint64_t>(
+        1, std::min<uint64_t>((uint64_t)h->num_sms * 8, (k + 8 * kT - 1) / (8 * kT)));
+    k_orand<<<ogrid, kT, 0, st>>>(d_in, k, ctl);
+    k_hist_field<<<ogrid, kT, 0, st>>>(d_in, k, ctl);
     k_onesweep<VALS><<<sgrid, kT, smem, st>>>(d_in, v_in, A, B, VA, VB, k, 0, 1, ctl, look,
                                                h->d_status, spin, silent);
     k_bucket_sort<VALS><<<256, kBT, sizeof(TileSmemT<VALS, kBT, kBItems>), st>>>(B, VB, A, VA,

@@ -190,6 +190,7 @@ struct MergeArgs {
   uint32_t* list_v1;     // touched leaves for k_merge_small (count st->n_v1)
   uint32_t* list_gen;    // work items for k_merge in count mode (st->n_gen)
   int raw;               // leaves hold 8-byte cells (codec 1), not byte codes
+  int small;             // a small batch: every slice goes to a warp per leaf
 };
 
 // Append to a work list, one atomic per warp (all lanes must call).
@@ -292,11 +293,15 @@ __host__ __device__ constexpr size_t lane_warp_bytes(int seg) {
 // kLaneSeg keys into leaves of at most 512 used bytes -> k_insert_lane (from
 // the list k_classify builds).
 constexpr uint32_t kThrKeys = leafthr::kKeys;
-__device__ __forceinline__ bool thread_class(uint32_t s, uint32_t uold) {
-  return s >= 1 && s <= kThrKeys && uold > 0;
+// A small batch touches few leaves, so its merge time is latency rather than
+// throughput: every slice then goes to a warp per leaf (one coalesced load of
+// the leaf instead of a thread's chain of dependent 16-byte loads).
+constexpr uint64_t kSmallBatch = 8192;
+__device__ __forceinline__ bool thread_class(uint32_t s, uint32_t uold, int small = 0) {
+  return !small && s >= 1 && s <= kThrKeys && uold > 0;
 }
-__device__ __forceinline__ bool lane_class(uint32_t s, uint32_t uold) {
-  return s > kThrKeys && s <= (uint32_t)kLaneSeg && uold > 0 && uold <= 512;
+__device__ __forceinline__ bool lane_class(uint32_t s, uint32_t uold, int small = 0) {
+  return s > (small ? 0u : kThrKeys) && s <= (uint32_t)kLaneSeg && uold > 0 && uold <= 512;
 }
 
 // Copy of the kept old bytes for the lane-granular insert: the lane's 4*NW
@@ -706,7 +711,7 @@ __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
     bool mine = false;
     if (idx < n) {
       const uint32_t uo = a.T_oldused[idx];
-      mine = thread_class(a.T_begin[idx + 1] - a.T_begin[idx], uo);
+      mine = thread_class(a.T_begin[idx + 1] - a.T_begin[idx], uo, a.small);
       if (mine) {
         bkt = min((uint32_t)kThrBuckets - 1u, (uo + 15u) >> 4);
         slot = atomicAdd(&s_hist[bkt], 1u);
@@ -807,8 +812,8 @@ __global__ void __launch_bounds__(kT) k_classify(MergeArgs a) {
       const uint32_t uold = a.T_oldused[t];
       if (small_slice(tb, te, uold)) {
         const bool ins = !a.is_delete && !a.raw;
-        cls = (!a.raw && thread_class(te - tb, uold)) ? 4u
-            : (ins && lane_class(te - tb, uold)) ? 0u : 1u;
+        cls = (!a.raw && thread_class(te - tb, uold, a.small)) ? 4u
+            : (ins && lane_class(te - tb, uold, a.small)) ? 0u : 1u;
       } else {
         cls = 2;
         fc0 = a.T_first_chunk[t];
@@ -2221,6 +2226,7 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   ma.list_v1 = P<uint32_t>(s.list_v1);
   ma.list_gen = P<uint32_t>(s.list_gen);
   ma.raw = (int)h->cfg.codec;
+  ma.small = k <= kSmallBatch ? 1 : 0;
   const size_t per = merge_warp_bytes(LB);
   const int mwarps = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));
   const size_t msmem = per * mwarps;
@@ -2255,13 +2261,13 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
       prof_end_side(h, h->side);
       CPMA_CUDA(cudaEventRecord(h->ev_join, h->side));
       ma.prof = prof_bytes(h, PH_MERGE);
-      if (!ma.raw) {
+      if (!ma.raw && !ma.small) {
         launch_insert_thread<false>(h, ma, k, st);
       }
       ma.prof = nullptr;
       CPMA_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
     }
-    if (is_delete && !ma.raw) {
+    if (is_delete && !ma.raw && !ma.small) {
       ma.prof = prof_bytes(h, PH_MERGE);
       launch_insert_thread<true>(h, ma, k, st);
       ma.prof = nullptr;
