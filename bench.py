@@ -593,6 +593,9 @@ def serving(a, g, S):
     sat_plain = max(p["one_at_a_time"]["requests_per_s"] for p in sweep)
     rate = 0.7 * sat_served
     head = point(rate, 90)
+    # a load both forms sustain: 70% of the one-call-per-request saturation
+    rate_plain = 0.7 * sat_plain
+    low = point(rate_plain, 91)
     return {"requests_per_point": a.serve_requests, "sweep": sweep,
             "saturation_requests_per_s": {"served": sat_served, "one_at_a_time": sat_plain},
             "offered_requests_per_s": rate, "at_offered": head,
@@ -602,7 +605,12 @@ def serving(a, g, S):
             "p99_speedup": head["one_at_a_time"]["p99_ms"] / head["served"]["p99_ms"],
             "throughput_ratio": head["served"]["requests_per_s"] /
                                 head["one_at_a_time"]["requests_per_s"],
-            "saturation_ratio": sat_served / sat_plain}
+            "saturation_ratio": sat_served / sat_plain,
+            "at_plain_offered": {"offered_requests_per_s": rate_plain,
+                                 "p50_ms": low["served"]["p50_ms"],
+                                 "p99_ms": low["served"]["p99_ms"],
+                                 "one_at_a_time_p50_ms": low["one_at_a_time"]["p50_ms"],
+                                 "one_at_a_time_p99_ms": low["one_at_a_time"]["p99_ms"]}}
 
 
 def pma_ablation(a, dev, lo, hi, timed):
@@ -705,7 +713,12 @@ def graph_workload(a, dev, timed):
 def skew(a, dev, T, timed):
     """Skewed updates: 5e7 keys uniform in [0, 2^34), then 100 rounds of 1e5
     zipfian (0.99, 2^34 universe, scattered ranks) inserts + 5e4 deletes of
-    present keys; device time per round and final bytes/key."""
+    present keys; device time per round and final bytes/key.  Those rounds
+    change the set by under a tenth, within the root bounds, so growth and
+    shrink at this scale are exercised after them: net-growing rounds of 1e6
+    fresh uniform keys of the same universe until the array has grown twice,
+    then net-shrinking rounds of 2e6 deletes of the initial keys until it
+    has shrunk twice."""
     import torch
     from paper_2305_05055_gb300 import cpma as cp
     from paper_2305_05055_gb300 import workloads as W
@@ -727,14 +740,50 @@ def skew(a, dev, T, timed):
         per.append(ms)
     prof = g.profile_read()
     g.profile(False)
+    L_rounds = g.leaves()
+    size_rounds, bpk_rounds = g.size(), g.bytes() / max(1, g.size())
+    # growth and shrink at this scale
+    resize = {"grow": [], "shrink": []}
+    Ls, r = g.leaves(), 0
+    while len(resize["grow"]) < 2 and r < 60:
+        # fresh keys of the same 2^34 universe (zipfian draws repeat their
+        # hot keys and barely grow the set)
+        zb = T(W.uniform_keys(4400 + r, 2 * 10 ** 6, bits=34))
+        ms, _ = timed(lambda: g.insert_batch(zb))
+        r += 1
+        if g.leaves() != Ls:
+            resize["grow"].append({"round": r, "ms": ms, "leaves": [Ls, g.leaves()],
+                                   "size": g.size()})
+            Ls = g.leaves()
+    grow_rounds = r
+    del dels
+    # then delete everything, 2e6 keys a round: the initial keys, then the
+    # grown ones, until the array has shrunk twice
+    S0 = np.sort(W.uniform_keys(4, n0, bits=34))
+    ns0 = (S0.size + 2 * 10 ** 6 - 1) // (2 * 10 ** 6)
+    chunk = lambda q: (S0[q * 2 * 10 ** 6:(q + 1) * 2 * 10 ** 6] if q < ns0 else
+                       W.uniform_keys(4400 + q - ns0, 2 * 10 ** 6, bits=34))
+    r = 0
+    while len(resize["shrink"]) < 2 and r < ns0 + grow_rounds:
+        db = T(chunk(r))
+        ms, _ = timed(lambda: g.delete_batch(db))
+        r += 1
+        if g.leaves() != Ls:
+            resize["shrink"].append({"round": r, "ms": ms, "leaves": [Ls, g.leaves()],
+                                     "size": g.size()})
+            Ls = g.leaves()
+    resize.update(grow_rounds=grow_rounds, shrink_rounds=r, leaves_end=g.leaves(),
+                  size_end=g.size(), bytes_per_key_end=g.bytes() / max(1, g.size()))
     per_s = sorted(per)
     return {"rounds": rounds, "insert_per_round": ki, "delete_per_round": kd,
             "round_ms_median": statistics.median(per), "round_ms_p99": per_s[int(0.99 * (len(per) - 1))],
             "round_ms_max": per_s[-1], "total_ms": sum(per),
             "keys_per_s": rounds * (ki + kd) / (sum(per) / 1e3),
-            "leaves_start": L0, "leaves_end": g.leaves(), "size_end": g.size(),
-            "bytes_per_key_start": b0 / n0, "bytes_per_key_end": g.bytes() / max(1, g.size()),
-            "phases_ms": {p: prof[p]["ms"] for p in prof if prof[p]["ms"] > 0}}
+            "leaves_start": L0, "leaves_after_rounds": L_rounds, "size_end": size_rounds,
+            "bytes_per_key_end": bpk_rounds,
+            "bytes_per_key_start": b0 / n0,
+            "phases_ms": {p: prof[p]["ms"] for p in prof if prof[p]["ms"] > 0},
+            "growth_and_shrink": resize}
 
 
 def flush_l2(dev):

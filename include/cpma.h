@@ -332,12 +332,15 @@ int cpma_export_layout(const cpma_t* h, uint8_t* d_data, uint32_t* d_used,
 
 /* Pre-size the scratch that an update of up to max_batch keys (tagged != 0:
  * with request tags) and a range_map of up to max_queries queries use, so
- * that those calls do not allocate.  Buffers whose size depends on the data
- * -- the overflow elements of leaves that outgrow leaf_bytes, the elements of
- * redistributed windows, a resized array -- still grow on first use.  With
- * graphs on (cpma_use_graphs) it also sizes the staging buffer of the padded
- * batch.  Errors: CPMA_EINVAL (null handle, max_batch >= 2^31), CPMA_ENOMEM.
- * Synchronises the device when an existing buffer has to grow. */
+ * that those calls do not allocate: the batch's sort, routing and merge
+ * buffers, the redistribution buffers for the whole set plus the batch, and
+ * spare leaf arrays for the resize the batch could cause (held until a
+ * resize uses them, or until 64 updates in a row could not have resized).
+ * Later updates that grow the set past these sizes reserve more before they
+ * change anything.  With graphs on (cpma_use_graphs) it also sizes the
+ * staging buffer of the padded batch.  Errors: CPMA_EINVAL (null handle,
+ * max_batch >= 2^31), CPMA_ENOMEM.  Synchronises the device when an existing
+ * buffer has to grow. */
 int cpma_reserve(cpma_t* h, uint64_t max_batch, uint64_t max_queries, int tagged,
                  cpma_stream_t stream);
 

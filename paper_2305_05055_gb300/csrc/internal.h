@@ -143,6 +143,7 @@ struct cpma {
   uint64_t* heads = nullptr;       // L + 1 entries; heads[L] = last non-empty leaf
   uint64_t cap_leaves = 0, cap_bytes = 0;  // capacity of the arrays above
   cpmaimpl::Arrays spare;          // arrays kept for a resize the next update may need
+  uint32_t spare_idle = 0;         // updates since a resize was last possible
   // memory: bytes held (structure, spare arrays, scratch, status), and a
   // flag that makes every allocation fail (set while an update is changing
   // the structure: everything it needs was reserved before)

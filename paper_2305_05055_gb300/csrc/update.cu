@@ -2566,9 +2566,13 @@ int run_rebuild(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_
   return check_cuda(cudaGetLastError());
 }
 
+int reserve_update(cpma* h, uint64_t k, int is_delete, cudaStream_t st, bool as_if_resizing);
+
 int reserve(cpma* h, uint64_t max_batch, int tagged, cudaStream_t st) {
   if (max_batch >= (1ull << 31)) return CPMA_EINVAL;
   if (max_batch == 0) return CPMA_OK;
+  // everything an insert of max_batch keys reserves, a growing resize included
+  CPMA_TRY(reserve_update(h, max_batch, 0, st, true));
   CPMA_TRY(front_scratch(h, max_batch, tagged != 0, st));
   if (h->graph_max_batch && !tagged) {
     const uint64_t K = graph_bucket(std::min(max_batch, h->graph_max_batch));
@@ -2591,20 +2595,24 @@ int reserve(cpma* h, uint64_t max_batch, int tagged, cudaStream_t st) {
 // fail; the used bytes after the merge lie within t_known -+ t_slack (the
 // redistribution after the last merge) and 10 bytes per key (an inserted
 // key adds at most a 10-byte code, a deleted one removes at most one).
-int reserve_update(cpma* h, uint64_t k, int is_delete, cudaStream_t st) {
+int reserve_update(cpma* h, uint64_t k, int is_delete, cudaStream_t st, bool as_if_resizing) {
   Scratch& s = h->s;
   const uint64_t n = h->n, L = h->L;
   const uint64_t n_hi = is_delete ? n : n + k, n_lo = is_delete ? (n > k ? n - k : 0) : n;
-  CPMA_TRY(ensure(h, s.E, (n_hi + 1) * 8, st));
-  CPMA_TRY(ensure(h, s.cost, n_hi + 1, st));
-  CPMA_TRY(ensure(h, s.C, (n_hi + 2) * 8, st));
+  // grown with an eighth to spare, so that a set growing batch by batch
+  // does not reallocate them at every step
+  const uint64_t n_res = n_hi + n_hi / 8;
+  if (s.E.cap < (n_hi + 1) * 8) CPMA_TRY(ensure(h, s.E, (n_res + 1) * 8, st));
+  if (s.cost.cap < n_hi + 1) CPMA_TRY(ensure(h, s.cost, n_res + 1, st));
+  if (s.C.cap < (n_hi + 2) * 8) CPMA_TRY(ensure(h, s.C, (n_res + 2) * 8, st));
   const uint64_t dk = 10 * k;
   const uint64_t t_hi = h->t_known + h->t_slack + (is_delete ? 0 : dk);
   const uint64_t sub = h->t_slack + (is_delete ? dk : 0);
   const uint64_t t_lo = h->t_known > sub ? h->t_known - sub : 0;
   const Bounds B = bounds_of(h);
   const unsigned H = ceil_log2(L);
-  const bool may_resize = node_violates(B, H, H, L, t_hi) || node_violates(B, H, H, L, t_lo);
+  const bool may_resize = as_if_resizing || node_violates(B, H, H, L, t_hi) ||
+                          node_violates(B, H, H, L, t_lo);
   uint64_t Lmax = L, bytes_max = L * h->cfg.leaf_bytes;
   if (may_resize) {
     // the most leaves and bytes over every key count the batch can leave
@@ -2616,17 +2624,24 @@ int reserve_update(cpma* h, uint64_t k, int is_delete, cudaStream_t st) {
       const uint64_t nn = b == b_lo ? n_lo : b == b_hi ? n_hi : (1ull << (b - 1));
       uint64_t Lp = 0;
       uint32_t LBp = 0;
-      resize_plan(h, t_hi, nn, &Lp, &LBp);
+      // (as_if_resizing: at least the bytes that would need one more grow)
+      const uint64_t tt = as_if_resizing ? std::max<uint64_t>(
+          t_hi, (uint64_t)((unsigned __int128)h->cfg.tau_root * L * h->cfg.leaf_bytes / 1000 + 1))
+                                         : t_hi;
+      resize_plan(h, tt, nn, &Lp, &LBp);
       Lmax = std::max(Lmax, Lp);
       bytes_max = std::max(bytes_max, Lp * LBp);
     }
   }
   if (Lmax > h->cap_leaves || bytes_max > h->cap_bytes) {
+    h->spare_idle = 0;
     if (h->spare.cap_leaves < Lmax || h->spare.cap_bytes < bytes_max) {
       free_arrays(h, &h->spare);  // never in use between updates
       CPMA_TRY(alloc_arrays(h, Lmax, bytes_max, &h->spare, st));
     }
-  } else if (h->spare.data) {
+  } else if (h->spare.data && ++h->spare_idle > 64) {
+    // kept while resizes stay likely; returned after 64 updates that could
+    // not have resized
     free_arrays(h, &h->spare);
   }
   // leaf-count buffers for the larger of the two trees, so that the update
@@ -2685,7 +2700,7 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
     return run_rebuild(h, d_keys, k, sorted, is_delete, d_delta, st);
   Scratch& s = h->s;
   const bool graph = k <= h->graph_max_batch && !tags && graph_bucket(k) < (1ull << 31);
-  int rc = reserve_update(h, k, is_delete, st);
+  int rc = reserve_update(h, k, is_delete, st, false);
   if (rc == CPMA_OK && graph) {
     rc = ensure(h, s.stage, graph_bucket(k) * 8, st);
     if (rc == CPMA_OK) rc = front_scratch(h, graph_bucket(k), false, st);

@@ -1,13 +1,18 @@
-"""Parity at the benchmark's full size, in the benchmark's launch
-configuration: a CPMA of 1e8 uniform 40-bit keys receives a 1e6-key insert
-batch and a 1e6-key delete batch (the headline step), and its answers are
-checked on samples the plain definition computes directly (numpy set
+"""Parity at large sizes.  At the benchmark's full size, in the benchmark's
+launch configuration: a CPMA of 1e8 uniform 40-bit keys receives a 1e6-key
+insert batch and a 1e6-key delete batch (the headline step), and its answers
+are checked on samples the plain definition computes directly (numpy set
 operations on the same seeded keys): counts, size, full sum, has on 2e4
-keys and range sums / counts / map_range_length on 2e3 rank-based ranges."""
+keys and range sums / counts / map_range_length on 2e3 rank-based ranges.
+At 1e7 keys the whole layout (every leaf byte, used count and head entry)
+is compared with the sequential CPMA after a uniform insert, a delete and a
+skewed insert of 1e5 keys each (Sec. 4: merge, counting, redistribution at
+the leaf count and fill of a large set)."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2305_05055_gb300 import cpma as cp
 from paper_2305_05055_gb300 import workloads as W
 from setops import member, sorted_unique
@@ -63,3 +68,34 @@ def test_headline_size_parity():
     assert np.array_equal(cp.to_u64(gc), wc) and np.array_equal(cp.to_u64(gs), ws)
     ls, lc = g.range_map_length(T(lo), T(cnt.astype(np.uint64)))
     assert np.array_equal(cp.to_u64(lc), wc) and np.array_equal(cp.to_u64(ls), ws)
+
+
+def same_layout(g, o):
+    assert g.leaves() == o.leaves() and g.leaf_bytes() == o.leaf_bytes()
+    data, used, heads = g.layout()
+    od, ou, oh = o.layout()
+    gu = used.cpu().numpy().view(np.uint32)
+    bad = np.nonzero(gu != ou)[0][:10]
+    assert bad.size == 0, ("used differs", bad, gu[bad], ou[bad])
+    assert np.array_equal(cp.to_u64(heads), oh)
+    assert np.array_equal(data.cpu().numpy(), od)
+    assert g.size() == o.size() and g.bytes() == o.bytes()
+
+
+def test_layout_parity_at_1e7_keys():
+    n, k = 10 ** 7, 10 ** 5
+    base = W.uniform_keys(61, n, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=512)
+    o = oracle.SeqCPMA(base, leaf_bytes=512)
+    del base
+    same_layout(g, o)
+    ins = W.uniform_keys(62, k, bits=40)
+    assert int(g.insert_batch(T(ins)).item()) == o.insert_batch(ins)
+    same_layout(g, o)
+    dele = W.sample_present(o.elements(), 63, k)
+    assert int(g.delete_batch(T(dele)).item()) == o.delete_batch(dele)
+    same_layout(g, o)
+    z = W.zipf_keys(64, k, bits=34)
+    assert int(g.insert_batch(T(z)).item()) == o.insert_batch(z)
+    same_layout(g, o)
+    assert o.check() == 0
