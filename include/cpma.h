@@ -64,9 +64,10 @@ enum {
   CPMA_ENOMEM = -2,    /* device or host allocation failed */
   CPMA_ECUDA = -3,     /* a CUDA call failed */
   CPMA_EINTERNAL = -4, /* a device-side consistency check failed */
-  CPMA_ETIMEOUT = -5,  /* a bounded device-side wait gave up (the batch sort's
-                          look-back: a tile whose predecessor never published
-                          its counts); the set is unchanged */
+  CPMA_ETIMEOUT = -5,  /* a bounded device-side wait gave up (the look-back
+                          of the batch sort or of the routing: a tile whose
+                          predecessor never published its counts); the set
+                          is unchanged */
 };
 
 /* Device memory callbacks (cpma_config.alloc / .free).  alloc returns
@@ -316,12 +317,12 @@ int cpma_mem_peak(const cpma_t* h, uint64_t* out);
 int cpma_set_mem_budget(cpma_t* h, uint64_t bytes);
 
 /* For tests of the bounded wait (no counterpart in the paper): poll_limit
- * replaces the number of polls after which a tile of the batch sort stops
- * waiting for its predecessor (0 restores the default, 2^22), and
- * silent_tile >= 0 makes that tile of every sort pass skip publishing its
- * counts, so the tiles after it wait until the limit; the update then
- * returns CPMA_ETIMEOUT with the set unchanged.  silent_tile < 0 turns it
- * off. */
+ * replaces the number of polls after which a tile of the batch sort or of
+ * the routing stops waiting for its predecessor (0 restores the default,
+ * 2^22), and silent_tile >= 0 makes that tile of every sort pass and of the
+ * routing skip publishing its counts, so the tiles after it wait until the
+ * limit; the update then returns CPMA_ETIMEOUT with the set unchanged.
+ * silent_tile < 0 turns it off. */
 int cpma_test_sort_stall(cpma_t* h, uint32_t poll_limit, int64_t silent_tile);
 
 /* Copy the layout into caller device buffers: d_data (L * leaf_bytes bytes),

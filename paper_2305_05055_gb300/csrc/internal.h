@@ -46,6 +46,7 @@ constexpr ull kErrUnsorted = 1;   // a batch promised sorted was not
 constexpr ull kErrFit = 2;        // a redistributed leaf did not fit
 constexpr ull kErrState = 4;      // inconsistent leaf state
 constexpr ull kErrSort = 8;       // a sort tile waited too long for its predecessor
+constexpr ull kErrRoute = 16;     // a routing tile waited too long for its predecessor
 
 constexpr uint32_t kChunk = 256;  // keys per merge work item
 constexpr int kMaxLevels = 48;

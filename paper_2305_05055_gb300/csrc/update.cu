@@ -57,110 +57,305 @@ __device__ __forceinline__ bool bsearch_sm(const uint64_t* a, uint32_t n, uint64
 // ---------------------------------------------------------------------------
 // 2. routing
 // ---------------------------------------------------------------------------
-// Leaf of x given that the count of heads <= x lies in [lo, lo + n]
-// (route_leaf restricted to that range).
-__device__ __forceinline__ uint32_t route_in(const uint64_t* __restrict__ heads, uint64_t L,
-                                             uint64_t lo, uint64_t n, uint64_t x) {
-  if (x == KEY_MAX) return (uint32_t)heads[L];
-  const uint64_t c = lo + (n ? upper_count(heads + lo, n, x) : 0);
-  return (uint32_t)(c ? c - 1 : 0);
-}
-
-// Route every key of the sorted batch; flag run starts (a new leaf) and
-// chunk starts.  A warp's keys are consecutive in sorted order, so they fall
-// in a short stretch of leaves: the warp first narrows the head range that
-// holds the counts of its smallest and largest key (including the key
-// before the warp, for the run flag of lane 0) with up to four rounds of 32
-// evenly spaced samples and two ballots, then each lane searches the
-// narrowed range.  The dependent-load chain drops from log2 L loads to about
-// four plus log2 of the stretch.  (An unsorted batch, which is flagged, can
-// only make the range empty: every index stays in [0, L).)
-__global__ void __launch_bounds__(kT) k_route_flags(const uint64_t* __restrict__ u, uint64_t k,
-                                                    const uint64_t* __restrict__ heads, uint64_t L,
-                                                    uint32_t* __restrict__ leaf_of,
-                                                    uint64_t* __restrict__ flags, Status* st) {
-  const unsigned lane = lane_id();
-  const uint64_t nthreads = gstride();
-  for (uint64_t base = gtid() - lane; base < k; base += nthreads) {
-    const uint64_t i = base + lane;
-    const bool valid = i < k;
-    const uint64_t x = valid ? u[i] : 0;
-    const unsigned vm = __ballot_sync(FULL, valid);
-    const int last = 31 - __clz(vm);
-    uint64_t px = __shfl_up_sync(FULL, x, 1);
-    if (lane == 0 && i > 0) px = u[i - 1];
-    const uint64_t xlo = __shfl_sync(FULL, (lane == 0 && i > 0) ? min(px, x) : x, 0);
-    const uint64_t xhi = __shfl_sync(FULL, x, last);
-    uint64_t lo = 0, n = L;
-    for (int it = 0; it < 4 && n > 64; it++) {
-      const uint64_t step = (n + 31) / 32;
-      const uint64_t ns = (n + step - 1) / step;  // samples inside the range
-      const uint64_t p = lo + lane * step;
-      const bool in = lane < ns;
-      const uint64_t hv = in ? __ldg(heads + p) : 0;
-      const unsigned mlo = __popc(__ballot_sync(FULL, in && hv <= xlo));
-      const unsigned mhi = __popc(__ballot_sync(FULL, in && hv <= xhi));
-      const uint64_t nlo = mlo ? lo + (uint64_t)(mlo - 1) * step + 1 : lo;
-      uint64_t nhi = mhi < ns ? lo + (uint64_t)mhi * step : lo + n;
-      if (nhi < nlo) nhi = nlo;  // unsorted batch
-      lo = nlo;
-      n = nhi - nlo;
-    }
-    const uint32_t leaf = valid ? route_in(heads, L, lo, n, x) : 0u;
-    uint32_t prev = __shfl_up_sync(FULL, leaf, 1);
-    if (lane == 0 && i > 0 && valid) prev = route_in(heads, L, lo, n, px);
-    if (valid) {
-      if (i > 0 && px > x) atomicOr(&st->err, kErrUnsorted);
-      const uint64_t run = (i == 0 || leaf != prev) ? 1u : 0u;
-      const uint64_t chunk = (run || (i % kChunk) == 0) ? 1u : 0u;
-      leaf_of[i] = leaf;
-      flags[i] = (run << 32) | chunk;
-    }
-  }
-}
-
 struct RouteOut {
   uint32_t *chunk_begin, *chunk_leaf, *chunk_tid;
   uint32_t *T_leaf, *T_begin, *T_first_chunk, *T_oldcnt, *T_oldused, *T_newcnt, *T_state;
   ull* T_newbytes;
 };
 
-__global__ void __launch_bounds__(kT) k_route_scatter(uint64_t k, const uint32_t* __restrict__ leaf_of,
-                                                      const uint64_t* __restrict__ flags,
-                                                      const uint64_t* __restrict__ fscan,
-                                                      const uint32_t* __restrict__ cnt,
-                                                      const uint32_t* __restrict__ used, RouteOut o,
-                                                      Status* st) {
-  for (uint64_t i = gtid(); i < k; i += gstride()) {
-    const uint64_t f = flags[i], ex = fscan[i];
-    const uint32_t run = (uint32_t)(f >> 32), ch = (uint32_t)(f & 1u);
-    const uint32_t runs_before = (uint32_t)(ex >> 32), chunks_before = (uint32_t)ex;
-    const uint32_t t = runs_before + run - 1;
-    const uint32_t leaf = leaf_of[i];
-    if (ch) {
-      o.chunk_begin[chunks_before] = (uint32_t)i;
-      o.chunk_leaf[chunks_before] = leaf;
-      o.chunk_tid[chunks_before] = t;
+// One-pass routing: the search, the run and chunk flags, their scan and the
+// touched-leaf and work-item entries in one kernel.  Blocks take tiles of
+// KPT * 256 consecutive sorted keys in order from a counter; thread t holds
+// keys [t KPT, (t + 1) KPT) of its tile.  The heads a tile can reach,
+// indices [c_lo, c_hi) with c_lo / c_hi the counts of entries <= the key
+// before the tile / the tile's last key (two warps, 32-ary search), are
+// copied to shared memory when there are at most kRHeads of them (else every
+// step-th of them, and the last few candidates are bisected in the global
+// array).  A thread bisects for its first key and gallops from there for
+// the next ones.  The tile's run and chunk counts are scanned in the block
+// and joined to the tiles before it by decoupled look-back: the whole block
+// reads 256 predecessors per step; each published value packs runs << 31 |
+// chunks with an aggregate / inclusive flag.  A predecessor that has not
+// published after spin_limit polls sets kErrRoute instead of waiting longer;
+// `silent` names a tile that never publishes (tests of that bound only).
+// The tile's entries are gathered in shared memory and written out
+// coalesced; every run starts a work item, so a touched leaf's key index
+// and leaf come from its first item.
+constexpr int kRT = 256;
+constexpr uint32_t kRHeads = 4096;             // staged heads per tile (32 KB)
+constexpr uint64_t kRFlagA = 1ull << 62;       // tile aggregate published
+constexpr uint64_t kRFlagP = 1ull << 63;       // inclusive prefix published
+constexpr uint64_t kRValue = kRFlagA - 1;      // runs << 31 | chunks
+
+// Count of entries <= x in the non-decreasing heads[0, L), by the whole
+// warp: 32 evenly spaced samples per round narrow the answer's range
+// [lo, lo + n] to at most step - 1 candidates.
+__device__ __forceinline__ uint64_t warp_upper_count(const uint64_t* __restrict__ heads,
+                                                     uint64_t L, uint64_t x) {
+  const unsigned lane = lane_id();
+  uint64_t lo = 0, n = L;
+  while (n) {
+    const uint64_t step = (n + 31) >> 5;
+    const uint64_t p = lo + (uint64_t)(lane + 1) * step - 1;
+    const bool le = p < lo + n && __ldg(heads + p) <= x;
+    const uint64_t nlo = lo + (uint64_t)__popc(__ballot_sync(FULL, le)) * step;
+    n = min(step - 1, lo + n - nlo);
+    lo = nlo;
+  }
+  return lo;
+}
+
+// First index in [a, b) whose entry is > x (b if none), given that the
+// entries before a are <= x and those from b on are > x.
+__device__ __forceinline__ uint32_t bisect_upper(const uint64_t* h, uint32_t a, uint32_t b,
+                                                 uint64_t x) {
+  while (a < b) {
+    const uint32_t mid = (a + b) >> 1;
+    if (h[mid] <= x) a = mid + 1;
+    else b = mid;
+  }
+  return a;
+}
+
+// The same over [a, n), probing a, a + 1, a + 3, ... first (the answer is
+// usually close to a).
+__device__ __forceinline__ uint32_t gallop_upper(const uint64_t* h, uint32_t a, uint32_t n,
+                                                 uint64_t x) {
+  uint32_t d = 1, b = n;
+  while (a < n) {
+    const uint32_t probe = a + d - 1;
+    if (probe >= n) break;
+    if (h[probe] > x) { b = probe; break; }
+    a = probe + 1;
+    d <<= 1;
+  }
+  return bisect_upper(h, a, b, x);
+}
+
+// Shared memory of a routing tile: the staged heads, then (once every key
+// has its leaf) the tile's work items -- first key, leaf, touched-leaf entry
+// -- and each touched leaf's first work item.
+template <int KPT>
+union RouteSmem {
+  uint64_t heads[kRHeads];
+  struct {
+    uint32_t c_begin[kRT * KPT], c_leaf[kRT * KPT], c_t[kRT * KPT], t_fc[kRT * KPT];
+  } e;
+};
+
+template <int KPT>
+__global__ void __launch_bounds__(kRT, 4) k_route(const uint64_t* __restrict__ u, uint64_t k,
+                                                  const uint64_t* __restrict__ heads, uint64_t L,
+                                                  const uint32_t* __restrict__ cnt,
+                                                  const uint32_t* __restrict__ used, RouteOut o,
+                                                  uint64_t* look_raw, Status* st,
+                                                  uint32_t spin_limit, uint32_t silent) {
+  constexpr uint32_t kTileKeys = (uint32_t)kRT * KPT;
+  constexpr int kW = kRT / 32;
+  static_assert(sizeof(RouteSmem<KPT>) <= 32 * 1024, "routing tile smem");
+  __shared__ RouteSmem<KPT> sm;
+  __shared__ uint64_t s_c[2];
+  __shared__ uint64_t s_wsum[kW];
+  __shared__ uint64_t s_lsum[kW];
+  __shared__ uint32_t s_wlast[kW];
+  __shared__ uint32_t s_tile, s_pmin, s_tmo;
+  uint32_t* ctr = reinterpret_cast<uint32_t*>(look_raw);
+  volatile uint64_t* look = look_raw + 1;
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint32_t ntiles = (uint32_t)((k + kTileKeys - 1) / kTileKeys);
+  const bool vec = (reinterpret_cast<uintptr_t>(u) & 15u) == 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(ctr, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= ntiles) return;
+    const uint64_t base = (uint64_t)tile * kTileKeys;
+    const uint32_t nvalid = (uint32_t)min((uint64_t)kTileKeys, k - base);
+    const uint32_t i0 = threadIdx.x * KPT;
+    uint64_t x[KPT];
+    bool loaded = false;
+    if constexpr (KPT % 2 == 0) {
+      if (vec && i0 + KPT <= nvalid) {
+#pragma unroll
+        for (int j = 0; j < KPT; j += 2) {
+          const uint4 v = *reinterpret_cast<const uint4*>(u + base + i0 + j);
+          x[j] = (uint64_t)v.x | ((uint64_t)v.y << 32);
+          x[j + 1] = (uint64_t)v.z | ((uint64_t)v.w << 32);
+        }
+        loaded = true;
+      }
     }
-    if (run) {
-      o.T_leaf[t] = leaf;
-      o.T_begin[t] = (uint32_t)i;
-      o.T_first_chunk[t] = chunks_before;
-      o.T_oldcnt[t] = cnt[leaf];
-      o.T_oldused[t] = used[leaf];
+    if (!loaded) {
+#pragma unroll
+      for (int j = 0; j < KPT; j++) x[j] = i0 + j < nvalid ? u[base + i0 + j] : KEY_MAX;
+    }
+    // the key before the tile and the tile's last key bound its heads
+    if (warp < 2) {
+      const uint64_t y = warp == 0 ? u[base ? base - 1 : 0] : u[base + nvalid - 1];
+      const uint64_t c = warp_upper_count(heads, L, y);
+      if (lane == 0) s_c[warp] = c;
+    }
+    __syncthreads();
+    const uint64_t c_lo = s_c[0];
+    const uint32_t nh = (uint32_t)(s_c[1] > c_lo ? s_c[1] - c_lo : 0);  // unsorted: empty
+    // every step-th of those heads in shared memory (all of them when they fit)
+    const uint32_t step = nh <= kRHeads ? 1u : (nh + kRHeads - 1) / kRHeads;
+    const uint32_t ns = nh / step;
+    for (uint32_t j = threadIdx.x; j < ns; j += kRT)
+      sm.heads[j] = __ldg(heads + c_lo + (uint64_t)(j + 1) * step - 1);
+    __syncthreads();
+    // leaf of every key: m samples <= x put the count of heads <= x in
+    // [m step, min(m step + step - 1, nh)], bisected in the global array
+    uint32_t leaf[KPT];
+    uint32_t m = 0;
+    bool unsorted = false;
+#pragma unroll
+    for (int j = 0; j < KPT; j++) {
+      if (j && x[j - 1] > x[j]) unsorted = true;
+      if (x[j] == KEY_MAX) {
+        leaf[j] = (uint32_t)__ldg(heads + L);
+        continue;
+      }
+      m = j == 0 ? bisect_upper(sm.heads, 0, ns, x[j]) : gallop_upper(sm.heads, m, ns, x[j]);
+      uint32_t a = m * step, b = min(a + step - 1u, nh);
+      while (a < b) {
+        const uint32_t mid = (a + b) >> 1;
+        if (__ldg(heads + c_lo + mid) <= x[j]) a = mid + 1;
+        else b = mid;
+      }
+      const uint64_t c = c_lo + a;
+      leaf[j] = (uint32_t)(c ? c - 1 : 0);
+    }
+    // predecessor of the thread's first key: the thread before it, the warp
+    // before it, or the key before the tile
+    uint32_t prev = __shfl_up_sync(FULL, leaf[KPT - 1], 1);
+    uint64_t px = __shfl_up_sync(FULL, x[KPT - 1], 1);
+    if (lane == 31) s_wlast[warp] = leaf[KPT - 1];
+    __syncthreads();  // also: every key has left the staged heads
+    if (lane == 0 && i0 < nvalid) {
+      if (warp) {
+        prev = s_wlast[warp - 1];
+        px = u[base + i0 - 1];
+      } else if (base) {
+        px = u[base - 1];
+        prev = px == KEY_MAX ? (uint32_t)__ldg(heads + L)
+                             : (uint32_t)(c_lo ? c_lo - 1 : 0);
+      }
+    }
+    uint32_t runs = 0, chunks = 0;
+    uint32_t rflags = 0, cflags = 0;
+#pragma unroll
+    for (int j = 0; j < KPT; j++) {
+      const uint64_t i = base + i0 + j;
+      if (i0 + j >= nvalid) break;
+      const uint32_t pl = j ? leaf[j - 1] : prev;
+      if (j == 0 && i > 0 && px > x[0]) unsorted = true;
+      const bool run = i == 0 || leaf[j] != pl;
+      const bool ch = run || (i % kChunk) == 0;
+      rflags |= (uint32_t)run << j;
+      cflags |= (uint32_t)ch << j;
+      runs += run;
+      chunks += ch;
+    }
+    if (unsorted) atomicOr(&st->err, kErrUnsorted);
+    // block exclusive scan of (runs, chunks) packed as runs << 32 | chunks
+    const uint64_t mine = ((uint64_t)runs << 32) | chunks;
+    const uint64_t incl = warp_incl_scan(mine);
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      uint64_t w = lane < kW ? s_wsum[lane] : 0ull;
+      w = warp_incl_scan(w);
+      if (lane < kW) s_wsum[lane] = w;
+    }
+    __syncthreads();
+    const uint64_t tot = s_wsum[kW - 1];
+    const uint32_t runs_tile = (uint32_t)(tot >> 32), chunks_tile = (uint32_t)tot;
+    const uint64_t agg = ((uint64_t)runs_tile << 31) | chunks_tile;
+    const bool publish = tile != silent;
+    // look-back: thread i polls tile tp - i
+    uint64_t excl = 0;
+    if (threadIdx.x == 0 && publish) look[tile] = (tile ? kRFlagA : kRFlagP) | agg;
+    if (tile > 0) {
+      int64_t tp = (int64_t)tile - 1;
+      for (;;) {
+        const int64_t q = tp - (int64_t)threadIdx.x;
+        uint64_t v = kRFlagA;  // past tile 0: counts nothing
+        if (q >= 0) {
+          uint32_t spins = 0;
+          v = look[q];
+          while (!(v & (kRFlagA | kRFlagP)) && spins < spin_limit) {
+            v = look[q];
+            spins++;
+          }
+        }
+        if (threadIdx.x == 0) { s_pmin = kRT; s_tmo = 0; }
+        __syncthreads();
+        if (!(v & (kRFlagA | kRFlagP))) s_tmo = 1;
+        if (q >= 0 && (v & kRFlagP)) atomicMin(&s_pmin, threadIdx.x);
+        __syncthreads();
+        const uint32_t stop = s_pmin;  // nearest predecessor with its inclusive prefix
+        const uint64_t add = warp_sum(q >= 0 && threadIdx.x <= stop ? (v & kRValue) : 0ull);
+        if (lane == 0) s_lsum[warp] = add;
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < kW; w++) excl += s_lsum[w];
+        const bool gave_up = s_tmo != 0;
+        if (gave_up || stop < (uint32_t)kRT || tp < kRT) {
+          if (gave_up && threadIdx.x == 0) atomicOr(&st->err, kErrRoute);
+          break;
+        }
+        tp -= kRT;
+        __syncthreads();  // s_pmin, s_tmo and s_lsum are reused
+      }
+      if (threadIdx.x == 0 && publish) {
+        __threadfence();
+        look[tile] = kRFlagP | (excl + agg);
+      }
+    }
+    const uint32_t g_runs = (uint32_t)(excl >> 31), g_chunks = (uint32_t)(excl & 0x7FFFFFFFull);
+    // this tile's work items and touched-leaf starts, in shared memory
+    const uint64_t before = (warp ? s_wsum[warp - 1] : 0ull) + incl - mine;
+    uint32_t r = (uint32_t)(before >> 32), c = (uint32_t)before;  // local indices
+#pragma unroll
+    for (int j = 0; j < KPT; j++) {
+      if (i0 + j >= nvalid) break;
+      const bool run = (rflags >> j) & 1u, ch = (cflags >> j) & 1u;
+      r += run;  // r - 1: the key's touched leaf, local
+      if (run) sm.e.t_fc[r - 1] = c;
+      if (ch) {
+        sm.e.c_begin[c] = (uint32_t)(base + i0 + j);
+        sm.e.c_leaf[c] = leaf[j];
+        sm.e.c_t[c] = g_runs + r - 1;
+        c++;
+      }
+    }
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < chunks_tile; q += kRT) {
+      o.chunk_begin[g_chunks + q] = sm.e.c_begin[q];
+      o.chunk_leaf[g_chunks + q] = sm.e.c_leaf[q];
+      o.chunk_tid[g_chunks + q] = sm.e.c_t[q];
+    }
+    for (uint32_t q = threadIdx.x; q < runs_tile; q += kRT) {
+      const uint32_t fc = sm.e.t_fc[q], lf = sm.e.c_leaf[fc], t = g_runs + q;
+      o.T_leaf[t] = lf;
+      o.T_begin[t] = sm.e.c_begin[fc];
+      o.T_first_chunk[t] = g_chunks + fc;
+      o.T_oldcnt[t] = cnt[lf];
+      o.T_oldused[t] = used[lf];
       o.T_newcnt[t] = 0;
       o.T_newbytes[t] = 0;
       o.T_state[t] = kUnchanged;
     }
-    if (i == k - 1) {
-      const uint64_t tot = fscan[k];
-      const uint32_t nT = (uint32_t)(tot >> 32), nC = (uint32_t)tot;
+    if (threadIdx.x == 0 && base + nvalid == k) {
+      const uint32_t nT = g_runs + runs_tile, nC = g_chunks + chunks_tile;
       st->nT = nT;
       st->nchunks = nC;
       o.T_begin[nT] = (uint32_t)k;
       o.T_first_chunk[nT] = nC;
       o.chunk_begin[nC] = (uint32_t)k;
     }
+    __syncthreads();  // the next tile reuses the shared arrays
   }
 }
 
@@ -1258,7 +1453,7 @@ struct FinArgs {
 __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
   if (a.st->err) return;
   const uint64_t nT = a.st->nT;
-  ull mb = 0, dl = 0, np = 0, db = 0;  // db: change of the byte total, mod 2^64
+  ull mb = 0, dl = 0, np = 0, db = 0, ov = 0;  // db: change of the byte total, mod 2^64
   for (uint64_t t = gtid(); t < nT; t += gstride()) {
     const uint32_t state = a.T_state[t];
     const uint32_t oldc = a.T_oldcnt[t], newc = a.T_newcnt[t];
@@ -1283,6 +1478,8 @@ __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
       a.used[j] = (uint32_t)nb;
       a.cnt[j] = newc;
       np++;
+      // its merged elements, counted per work item (the overflow total)
+      for (uint32_t c = a.T_first_chunk[t]; c < a.T_first_chunk[t + 1]; c++) ov += a.chunk_cnt[c];
     }
     if (node_violates(a.B, a.H, 0, 1, nb)) {
       const ull v = atomicAdd(&a.st->nviol, 1ull);
@@ -1295,10 +1492,12 @@ __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
   dl = warp_sum(dl);
   np = warp_sum(np);
   db = warp_sum(db);
+  ov = warp_sum(ov);
   if (lane_id() == 0) {
     if (dl) atomicAdd(&a.st->delta, dl);
     if (np) atomicAdd(&a.st->npend, np);
     if (db) atomicAdd(&a.st->bytes_total, db);
+    if (ov) atomicAdd(&a.st->novf, ov);
   }
   if (a.merge_bytes) {
     mb = warp_sum(mb);
@@ -1306,7 +1505,6 @@ __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
   }
 }
 
-__global__ void k_copy_total(const uint64_t* arr, const ull* n, ull* dst) { *dst = arr[*n]; }
 __global__ void k_put_u64(uint64_t* dst, uint64_t v) { *dst = v; }
 
 __global__ void __launch_bounds__(kT) k_check_tags(const uint32_t* __restrict__ tags, uint64_t k,
@@ -2081,6 +2279,7 @@ struct Front {
   unsigned H = 0;
   int mgrid = 0, mwarps = 0;
   size_t msmem = 0;
+  uint64_t k = 0;  // keys the front segment ran over (the work items are fewer)
 };
 
 void merge_attrs() {
@@ -2121,7 +2320,7 @@ int front_scratch(cpma* h, uint64_t k, bool tagged, cudaStream_t st) {
   CPMA_TRY(sort_scratch(h, k, tagged));
   CPMA_TRY(ensure(h, s.partials, (size_t)(2 * h->num_sms + 2) * 8));
   CPMA_TRY(ensure(h, s.leaf_of, k * 4));
-  CPMA_TRY(ensure(h, s.flags, k * 8));
+  CPMA_TRY(ensure(h, s.flags, (k + 2) * 8));  // also the routing look-back words
   CPMA_TRY(ensure(h, s.flags_scan, (k + 1) * 8));
   for (Buf* b : {&s.chunk_begin, &s.chunk_leaf, &s.chunk_tid, &s.chunk_cnt, &s.T_leaf, &s.T_begin,
                  &s.T_first_chunk, &s.T_oldcnt, &s.T_oldused, &s.T_newcnt, &s.T_state, &s.viol})
@@ -2171,13 +2370,6 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
 
   // ---- route ----
   prof_begin(h, PH_ROUTE, st);
-  // keys 8k, leaf ids 4k + 4k, flags 8k + 8k, flag scan 24k, T / chunk
-  // entries about 12 bytes per key on a uniform batch
-  prof_add_bytes(h, PH_ROUTE, 68ull * k);
-  k_route_flags<<<grid_for(h, k), kT, 0, st>>>(u, k, h->heads, h->L, P<uint32_t>(s.leaf_of),
-                                               P<uint64_t>(s.flags), ds);
-  h->launches++;
-  CPMA_TRY(scan_u64(h, P<uint64_t>(s.flags), P<uint64_t>(s.flags_scan), k, nullptr, st));
   RouteOut ro;
   ro.chunk_begin = P<uint32_t>(s.chunk_begin);
   ro.chunk_leaf = P<uint32_t>(s.chunk_leaf);
@@ -2190,10 +2382,32 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   ro.T_newcnt = P<uint32_t>(s.T_newcnt);
   ro.T_state = P<uint32_t>(s.T_state);
   ro.T_newbytes = P<ull>(s.T_newbytes);
-  k_route_scatter<<<grid_for(h, k), kT, 0, st>>>(k, P<uint32_t>(s.leaf_of), P<uint64_t>(s.flags),
-                                                 P<uint64_t>(s.flags_scan), h->cnt, h->used, ro,
-                                                 ds);
-  h->launches++;
+  {
+    // eight keys per thread once the batch fills two tiles per SM and is
+    // dense enough (a 2048-key tile then reaches about as many heads as
+    // shared memory holds); one key per thread otherwise
+    const bool wide = k >= (uint64_t)h->num_sms * 2 * 8 * kRT && 2 * k >= h->L;
+    const uint64_t tile_keys = (uint64_t)kRT * (wide ? 8 : 1);
+    const uint64_t ntiles = (k + tile_keys - 1) / tile_keys;
+    // the tile counter, then one look-back word per tile
+    uint64_t* look = P<uint64_t>(s.flags);
+    CPMA_CUDA(cudaMemsetAsync(look, 0, (ntiles + 1) * 8, st));
+    const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)h->num_sms * 4);
+    const uint32_t spin = h->sort_poll_limit ? h->sort_poll_limit : (1u << 22);
+    const uint32_t silent = h->sort_silent_tile >= 0 && h->sort_silent_tile < (int64_t)ntiles
+                                ? (uint32_t)h->sort_silent_tile : 0xFFFFFFFFu;
+    // keys, the heads searched, and per touched leaf its entries (36 bytes),
+    // old counts (8) and work item (12)
+    prof_add_bytes(h, PH_ROUTE, 8ull * k + 64ull * std::min<uint64_t>(k, h->L));
+    if (wide)
+      k_route<8><<<grid, kRT, 0, st>>>(u, k, h->heads, h->L, h->cnt, h->used, ro, look, ds, spin,
+                                       silent);
+    else
+      k_route<1><<<grid, kRT, 0, st>>>(u, k, h->heads, h->L, h->cnt, h->used, ro, look, ds, spin,
+                                       silent);
+    h->launches++;
+    CPMA_CUDA(cudaGetLastError());
+  }
 
   // ---- merge (count; in-place rewrites) ----
   MergeArgs ma;
@@ -2308,9 +2522,6 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   fa.st = ds;
   k_finalize<<<grid_for(h, k), kT, 0, st>>>(fa);
   h->launches++;
-  CPMA_TRY(scan_u32_to_u64(h, ma.chunk_cnt, P<uint64_t>(s.chunk_off), k + 1, &ds->nchunks, st));
-  k_copy_total<<<1, 1, 0, st>>>(P<uint64_t>(s.chunk_off), &ds->nchunks, &ds->novf);
-  h->launches++;
   CPMA_CUDA(cudaGetLastError());
   prof_end(h, st);
   f->ma = ma;
@@ -2320,6 +2531,7 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   f->mgrid = mgrid;
   f->mwarps = mwarps;
   f->msmem = msmem;
+  f->k = k;
   return CPMA_OK;
 }
 
@@ -2552,7 +2764,7 @@ int run_rebuild(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_
   CPMA_CUDA(cudaGetLastError());
   CPMA_TRY(sync_status(h, st));
   Status hs = *h->h_status;
-  if (hs.err & kErrSort) return CPMA_ETIMEOUT;
+  if (hs.err & (kErrSort | kErrRoute)) return CPMA_ETIMEOUT;
   if (hs.err & kErrUnsorted) return CPMA_EINVAL;
   if (hs.err) return CPMA_EINTERNAL;
   CPMA_TRY(build_from_sorted_unique(h, P<uint64_t>(s.E), hs.nelem, st));
@@ -2731,7 +2943,7 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   CPMA_TRY(sync_status(h, st));
   prof_begin(h, PH_COUNT, st);
   Status hs = *h->h_status;
-  if (hs.err & kErrSort) return CPMA_ETIMEOUT;
+  if (hs.err & (kErrSort | kErrRoute)) return CPMA_ETIMEOUT;
   if (hs.err & kErrUnsorted) return CPMA_EINVAL;
   if (hs.err) return CPMA_EINTERNAL;
   const uint64_t t_merged = hs.bytes_total;  // exact: every leaf changed by the merge counted
@@ -2746,6 +2958,9 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   // ---- pending leaves: materialise their merged elements ----
   if (hs.npend) {
     if (s.C.cap < (hs.novf + 1) * 8) return CPMA_EINTERNAL;  // reserved: novf <= n + k
+    // offsets of the work items' merged elements, only needed here
+    CPMA_TRY(scan_u32_to_u64(h, ma.chunk_cnt, P<uint64_t>(s.chunk_off), f.k + 1, &ds->nchunks,
+                             st));
     ma.ovf = P<uint64_t>(s.C);
     ma.tag_counts = nullptr;
     k_merge<true><<<mgrid, mwarps * 32, msmem, st>>>(ma);

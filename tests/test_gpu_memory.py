@@ -4,9 +4,9 @@ An update reserves every byte it can need before it changes anything, so a
 failed allocation -- from the caller's allocator or the memory budget --
 leaves the set exactly as it was, and so does a sort that gives up waiting
 (CPMA_ETIMEOUT).  Failures are made on the host: an allocator that refuses
-its N-th request, a budget just above what the handle holds, a sort tile
-told (through the test hook) never to publish its counts, with a short poll
-limit.  Nothing here faults or hangs the GPU: the wait is bounded and the
+its N-th request, a budget just above what the handle holds, a sort or
+routing tile told (through the test hook) never to publish its counts, with
+a short poll limit.  Nothing here faults or hangs the GPU: the wait is bounded and the
 kernels check the error flag before they change a leaf."""
 import ctypes as C
 
@@ -156,5 +156,37 @@ def test_sort_wait_gives_up_with_etimeout(silent):
     assert snapshot(g) == before
     cp.cpma_test_sort_stall(g.handle, 0, -1)
     rc, added = raw_update(g, keys)
+    assert rc == cp.CPMA_OK and added == o.insert_batch(keys)
+    same_as_oracle(g, o)
+
+
+def raw_sorted_update(g, keys, delete=False):
+    k = T(np.sort(np.asarray(keys, np.uint64)))
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    fn = cp.lib().cpma_delete_batch if delete else cp.lib().cpma_insert_batch
+    rc = fn(g.handle, C.c_void_p(k.data_ptr()), k.numel(), 1, C.c_void_p(out.data_ptr()),
+            C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    return rc, int(out.item())
+
+
+@pytest.mark.parametrize("silent", [0, 1, 5])
+def test_route_wait_gives_up_with_etimeout(silent):
+    # a batch given sorted skips the sort: the routing's look-back is the
+    # wait that runs out (20000 keys: 79 tiles of 256 keys)
+    base = W.uniform_keys(531, 50000, bits=40)
+    keys = W.uniform_keys(532, 20000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=512)
+    o = oracle.SeqCPMA(base, leaf_bytes=512)
+    before = snapshot(g)
+    cp.cpma_test_sort_stall(g.handle, 2000, silent)
+    rc, _ = raw_sorted_update(g, keys)
+    assert rc == cp.CPMA_ETIMEOUT
+    assert snapshot(g) == before
+    rc, _ = raw_sorted_update(g, keys, delete=True)
+    assert rc == cp.CPMA_ETIMEOUT
+    assert snapshot(g) == before
+    cp.cpma_test_sort_stall(g.handle, 0, -1)
+    rc, added = raw_sorted_update(g, keys)
     assert rc == cp.CPMA_OK and added == o.insert_batch(keys)
     same_as_oracle(g, o)
