@@ -433,13 +433,24 @@ template <bool VALS>
 __global__ void __launch_bounds__(kBT, 2) k_bucket_sort(uint64_t* __restrict__ B,
                                                      uint32_t* __restrict__ VB,
                                                      uint64_t* __restrict__ A,
-                                                     uint32_t* __restrict__ VA, SortCtl* ctl) {
+                                                     uint32_t* __restrict__ VA, SortCtl* ctl,
+                                                     const uint64_t* __restrict__ in,
+                                                     const uint32_t* __restrict__ vin,
+                                                     uint64_t k) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   TileSmemT<VALS, kBT, kBItems>& sm = *reinterpret_cast<TileSmemT<VALS, kBT, kBItems>*>(smem_raw);
   __shared__ ull s_or, s_and;
   __shared__ uint32_t s_run[256];
   __shared__ uint32_t s_wt[8];
-  if (ctl->npass == 0) return;
+  if (ctl->npass == 0) {
+    // every key equal: the batch as given is the result
+    for (uint64_t i = (uint64_t)blockIdx.x * kBT + threadIdx.x; i < k;
+         i += (uint64_t)gridDim.x * kBT) {
+      A[i] = in[i];
+      if constexpr (VALS) VA[i] = vin[i];
+    }
+    return;
+  }
   const uint32_t b = blockIdx.x;
   const uint32_t n = ctl->hist[0][b];
   if (n == 0) return;
@@ -572,7 +583,34 @@ __global__ void __launch_bounds__(kBT, 2) k_bucket_sort(uint64_t* __restrict__ B
   }
 }
 
-// Batches of at most kTile keys: a stable rank sort spread over many
+// Untagged batches of at most kTile keys: one block, a bitonic sorting
+// network over the batch padded with 2^64-1 to n (a power of two) in shared
+// memory, one compare-exchange of each pair per stage (equal keys are equal
+// values, so order among them does not matter).
+constexpr int kBitT = 1024;
+__global__ void __launch_bounds__(kBitT) k_sort_bitonic(const uint64_t* __restrict__ in,
+                                                        uint64_t* __restrict__ out, uint32_t k,
+                                                        uint32_t n) {
+  __shared__ uint64_t s[kTile];
+  for (uint32_t i = threadIdx.x; i < n; i += kBitT) s[i] = i < k ? in[i] : ~0ull;
+  __syncthreads();
+  for (uint32_t size = 2; size <= n; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride; stride >>= 1) {
+      for (uint32_t t = threadIdx.x; t < n / 2; t += kBitT) {
+        const uint32_t i = 2 * t - (t & (stride - 1)), j = i + stride;  // pair t of this stage
+        const uint64_t a = s[i], b = s[j];
+        if ((a > b) == ((i & size) == 0)) {  // ascending runs where bit `size` of i is 0
+          s[i] = b;
+          s[j] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < k; i += kBitT) out[i] = s[i];
+}
+
+// Tagged batches of at most kTile keys: a stable rank sort spread over many
 // blocks.  Every block holds the whole batch in shared memory; P consecutive
 // threads share one key, each counting over a P-th of the batch the keys
 // below it and the equal keys before it, and the sum of their counts (a
@@ -680,6 +718,15 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
   uint64_t* A = (uint64_t*)h->s.keysA.p;
   uint32_t* VA = VALS ? (uint32_t*)h->s.valsA.p : nullptr;
   const size_t smem = sizeof(TileSmemT<VALS>);
+  if (!VALS && k <= (uint64_t)kTile) {
+    prof_add_bytes(h, PH_SORT, 16ull * k);
+    uint32_t n = 2;
+    while (n < k) n <<= 1;
+    k_sort_bitonic<<<1, kBitT, 0, st>>>(d_in, A, (uint32_t)k, n);
+    h->launches++;
+    *out = A;
+    return check_cuda(cudaGetLastError());
+  }
   if (k <= (uint64_t)kTile) {
     prof_add_bytes(h, PH_SORT, (VALS ? 24ull : 16ull) * k);
     // threads per key: a power of two keeping each thread's share at 256 keys
@@ -719,7 +766,8 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
     k_onesweep<VALS><<<sgrid, kT, smem, st>>>(d_in, v_in, A, B, VA, VB, k, 0, 1, ctl, look,
                                                h->d_status, spin, silent);
     k_bucket_sort<VALS><<<256, kBT, sizeof(TileSmemT<VALS, kBT, kBItems>), st>>>(B, VB, A, VA,
-                                                                                 ctl);
+                                                                                 ctl, d_in, v_in,
+                                                                                 k);
     h->launches += 4;
     // OR/AND and histogram reads, scatter and bucket read + write
     prof_add_bytes(h, PH_SORT, 16ull * k + (VALS ? 24ull : 16ull) * k * 2);
@@ -737,10 +785,10 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
       h->launches++;
     }
     prof_add_bytes(h, PH_SORT, (VALS ? 24ull : 16ull) * k * 5);  // typical: 5 varying digits
+    k_copy_if_no_pass<<<std::min<uint64_t>((uint64_t)h->num_sms * 4, (k + kT - 1) / kT), kT, 0,
+                        st>>>(d_in, A, v_in, VA, k, ctl);
+    h->launches++;
   }
-  k_copy_if_no_pass<<<std::min<uint64_t>((uint64_t)h->num_sms * 4, (k + kT - 1) / kT), kT, 0, st>>>(
-      d_in, A, v_in, VA, k, ctl);
-  h->launches++;
   CPMA_CUDA(cudaGetLastError());
   const uint64_t* src = A;
   const uint32_t* vsrc = VA;

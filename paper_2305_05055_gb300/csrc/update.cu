@@ -66,13 +66,13 @@ struct RouteOut {
 // One-pass routing: the search, the run and chunk flags, their scan and the
 // touched-leaf and work-item entries in one kernel.  Blocks take tiles of
 // KPT * 256 consecutive sorted keys in order from a counter; thread t holds
-// keys [t KPT, (t + 1) KPT) of its tile.  The heads a tile can reach,
-// indices [c_lo, c_hi) with c_lo / c_hi the counts of entries <= the key
-// before the tile / the tile's last key (two warps, 32-ary search), are
-// copied to shared memory when there are at most kRHeads of them (else every
-// step-th of them, and the last few candidates are bisected in the global
-// array).  A thread bisects for its first key and gallops from there for
-// the next ones.  The tile's run and chunk counts are scanned in the block
+// keys [t KPT, (t + 1) KPT) of its tile.  The heads a tile can reach lie
+// between the sampled heads around the key before the tile and around its
+// last key (kRSamples evenly spaced heads, one load each, bisected in shared
+// memory); they are copied to shared memory when there are at most kRHeads
+// of them (else every step-th of them, and the last few candidates are
+// bisected in the global array).  A thread bisects for its first key and
+// gallops from there for the next ones.  The tile's run and chunk counts are scanned in the block
 // and joined to the tiles before it by decoupled look-back: the whole block
 // reads 256 predecessors per step; each published value packs runs << 31 |
 // chunks with an aggregate / inclusive flag.  A predecessor that has not
@@ -83,27 +83,10 @@ struct RouteOut {
 // and leaf come from its first item.
 constexpr int kRT = 256;
 constexpr uint32_t kRHeads = 4096;             // staged heads per tile (32 KB)
+constexpr uint64_t kRSamples = 1024;           // heads sampled to bound a tile's range
 constexpr uint64_t kRFlagA = 1ull << 62;       // tile aggregate published
 constexpr uint64_t kRFlagP = 1ull << 63;       // inclusive prefix published
 constexpr uint64_t kRValue = kRFlagA - 1;      // runs << 31 | chunks
-
-// Count of entries <= x in the non-decreasing heads[0, L), by the whole
-// warp: 32 evenly spaced samples per round narrow the answer's range
-// [lo, lo + n] to at most step - 1 candidates.
-__device__ __forceinline__ uint64_t warp_upper_count(const uint64_t* __restrict__ heads,
-                                                     uint64_t L, uint64_t x) {
-  const unsigned lane = lane_id();
-  uint64_t lo = 0, n = L;
-  while (n) {
-    const uint64_t step = (n + 31) >> 5;
-    const uint64_t p = lo + (uint64_t)(lane + 1) * step - 1;
-    const bool le = p < lo + n && __ldg(heads + p) <= x;
-    const uint64_t nlo = lo + (uint64_t)__popc(__ballot_sync(FULL, le)) * step;
-    n = min(step - 1, lo + n - nlo);
-    lo = nlo;
-  }
-  return lo;
-}
 
 // First index in [a, b) whose entry is > x (b if none), given that the
 // entries before a are <= x and those from b on are > x.
@@ -189,11 +172,19 @@ __global__ void __launch_bounds__(kRT, 4) k_route(const uint64_t* __restrict__ u
 #pragma unroll
       for (int j = 0; j < KPT; j++) x[j] = i0 + j < nvalid ? u[base + i0 + j] : KEY_MAX;
     }
-    // the key before the tile and the tile's last key bound its heads
-    if (warp < 2) {
-      const uint64_t y = warp == 0 ? u[base ? base - 1 : 0] : u[base + nvalid - 1];
-      const uint64_t c = warp_upper_count(heads, L, y);
-      if (lane == 0) s_c[warp] = c;
+    // the heads the tile can reach: kRSamples evenly spaced heads put the
+    // counts of the key before the tile and of its last key in two
+    // intervals, and the heads [c_lo, c_hi) from the start of the first to
+    // the end of the second are the only ones its keys can need
+    const uint64_t S1 = (L + kRSamples - 1) / kRSamples;
+    const uint32_t ns1 = (uint32_t)(L / S1);
+    for (uint32_t j = threadIdx.x; j < ns1; j += kRT)
+      sm.heads[j] = __ldg(heads + (uint64_t)(j + 1) * S1 - 1);
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      const uint64_t y = threadIdx.x == 0 ? u[base ? base - 1 : 0] : u[base + nvalid - 1];
+      const uint64_t m = bisect_upper(sm.heads, 0, ns1, y);
+      s_c[threadIdx.x] = threadIdx.x == 0 ? m * S1 : min((m + 1) * S1 - 1, L);
     }
     __syncthreads();
     const uint64_t c_lo = s_c[0];
@@ -204,8 +195,19 @@ __global__ void __launch_bounds__(kRT, 4) k_route(const uint64_t* __restrict__ u
     for (uint32_t j = threadIdx.x; j < ns; j += kRT)
       sm.heads[j] = __ldg(heads + c_lo + (uint64_t)(j + 1) * step - 1);
     __syncthreads();
-    // leaf of every key: m samples <= x put the count of heads <= x in
-    // [m step, min(m step + step - 1, nh)], bisected in the global array
+    // leaf of x: m staged heads <= x put the count of heads <= x in
+    // c_lo + [m step, min(m step + step - 1, nh)], bisected in the global
+    // array (nothing left to bisect when every head is staged)
+    auto leaf_of = [&](uint64_t y, uint32_t m) -> uint32_t {
+      uint32_t a = m * step, b = min(a + step - 1u, nh);
+      while (a < b) {
+        const uint32_t mid = (a + b) >> 1;
+        if (__ldg(heads + c_lo + mid) <= y) a = mid + 1;
+        else b = mid;
+      }
+      const uint64_t c = c_lo + a;
+      return (uint32_t)(c ? c - 1 : 0);
+    };
     uint32_t leaf[KPT];
     uint32_t m = 0;
     bool unsorted = false;
@@ -217,30 +219,22 @@ __global__ void __launch_bounds__(kRT, 4) k_route(const uint64_t* __restrict__ u
         continue;
       }
       m = j == 0 ? bisect_upper(sm.heads, 0, ns, x[j]) : gallop_upper(sm.heads, m, ns, x[j]);
-      uint32_t a = m * step, b = min(a + step - 1u, nh);
-      while (a < b) {
-        const uint32_t mid = (a + b) >> 1;
-        if (__ldg(heads + c_lo + mid) <= x[j]) a = mid + 1;
-        else b = mid;
-      }
-      const uint64_t c = c_lo + a;
-      leaf[j] = (uint32_t)(c ? c - 1 : 0);
+      leaf[j] = leaf_of(x[j], m);
     }
     // predecessor of the thread's first key: the thread before it, the warp
     // before it, or the key before the tile
     uint32_t prev = __shfl_up_sync(FULL, leaf[KPT - 1], 1);
     uint64_t px = __shfl_up_sync(FULL, x[KPT - 1], 1);
+    if (threadIdx.x == 0 && base) {
+      px = u[base - 1];
+      prev = px == KEY_MAX ? (uint32_t)__ldg(heads + L)
+                           : leaf_of(px, bisect_upper(sm.heads, 0, ns, px));
+    }
     if (lane == 31) s_wlast[warp] = leaf[KPT - 1];
     __syncthreads();  // also: every key has left the staged heads
-    if (lane == 0 && i0 < nvalid) {
-      if (warp) {
-        prev = s_wlast[warp - 1];
-        px = u[base + i0 - 1];
-      } else if (base) {
-        px = u[base - 1];
-        prev = px == KEY_MAX ? (uint32_t)__ldg(heads + L)
-                             : (uint32_t)(c_lo ? c_lo - 1 : 0);
-      }
+    if (lane == 0 && warp && i0 < nvalid) {
+      prev = s_wlast[warp - 1];
+      px = u[base + i0 - 1];
     }
     uint32_t runs = 0, chunks = 0;
     uint32_t rflags = 0, cflags = 0;
@@ -336,16 +330,31 @@ __global__ void __launch_bounds__(kRT, 4) k_route(const uint64_t* __restrict__ u
       o.chunk_leaf[g_chunks + q] = sm.e.c_leaf[q];
       o.chunk_tid[g_chunks + q] = sm.e.c_t[q];
     }
-    for (uint32_t q = threadIdx.x; q < runs_tile; q += kRT) {
-      const uint32_t fc = sm.e.t_fc[q], lf = sm.e.c_leaf[fc], t = g_runs + q;
-      o.T_leaf[t] = lf;
-      o.T_begin[t] = sm.e.c_begin[fc];
-      o.T_first_chunk[t] = g_chunks + fc;
-      o.T_oldcnt[t] = cnt[lf];
-      o.T_oldused[t] = used[lf];
-      o.T_newcnt[t] = 0;
-      o.T_newbytes[t] = 0;
-      o.T_state[t] = kUnchanged;
+    // touched leaves: every thread's (at most KPT) old counts are loaded
+    // together before any entry is stored
+    {
+      uint32_t lf[KPT], oc[KPT], ou[KPT];
+#pragma unroll
+      for (int j = 0; j < KPT; j++) {
+        const uint32_t q = threadIdx.x + (uint32_t)j * kRT;
+        lf[j] = q < runs_tile ? sm.e.c_leaf[sm.e.t_fc[q]] : 0u;
+        oc[j] = q < runs_tile ? cnt[lf[j]] : 0u;
+        ou[j] = q < runs_tile ? used[lf[j]] : 0u;
+      }
+#pragma unroll
+      for (int j = 0; j < KPT; j++) {
+        const uint32_t q = threadIdx.x + (uint32_t)j * kRT;
+        if (q >= runs_tile) break;
+        const uint32_t fc = sm.e.t_fc[q], t = g_runs + q;
+        o.T_leaf[t] = lf[j];
+        o.T_begin[t] = sm.e.c_begin[fc];
+        o.T_first_chunk[t] = g_chunks + fc;
+        o.T_oldcnt[t] = oc[j];
+        o.T_oldused[t] = ou[j];
+        o.T_newcnt[t] = 0;
+        o.T_newbytes[t] = 0;
+        o.T_state[t] = kUnchanged;
+      }
     }
     if (threadIdx.x == 0 && base + nvalid == k) {
       const uint32_t nT = g_runs + runs_tile, nC = g_chunks + chunks_tile;
@@ -386,6 +395,9 @@ struct MergeArgs {
   uint32_t* list_gen;    // work items for k_merge in count mode (st->n_gen)
   int raw;               // leaves hold 8-byte cells (codec 1), not byte codes
   int small;             // a small batch: every slice goes to a warp per leaf
+  Bounds B;              // density bounds and tree height, for the leaves the
+  unsigned H;            // thread-granular merge finalises itself
+  uint32_t* viol;        // touched leaves over their own bound (count st->nviol)
 };
 
 // Append to a work list, one atomic per warp (all lanes must call).
@@ -410,6 +422,9 @@ constexpr uint32_t kSmall = 32;
 // T-entry state set by the lane-granular insert when a leaf holds a code of
 // more than 4 bytes: the element-array splice takes it instead.
 constexpr uint32_t kFallback = 3;
+// T-entry state of a leaf the thread-granular merge rewrote in place and
+// also counted (batch totals, own-bound test): the finalize pass skips it.
+constexpr uint32_t kDone = 4;
 
 // Copy the bytes of the old leaf (global, uold bytes) that lie outside the E
 // edits into out[] (shared, zeroed), each shifted by the size change of the
@@ -928,6 +943,7 @@ __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
     __syncthreads();
     if (mine) s_tile[s_hist[bkt] + slot] = (uint32_t)idx;
     __syncthreads();
+    ull dl = 0, db = 0;  // db: change of the byte total, mod 2^64
     if (tid < s_hist[kThrBuckets]) {
       const uint32_t t = s_tile[tid];
       const uint32_t tb = a.T_begin[t], s = a.T_begin[t + 1] - tb;
@@ -970,15 +986,25 @@ __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
           a.used[j] = R.nb;
           a.cnt[j] = R.newc;
           a.heads[j] = R.newhead;
-          a.T_state[t] = kInPlace;
           a.T_newcnt[t] = R.newc;
           a.T_newbytes[t] = R.nb;
+          // the finalize pass's work for this leaf, done here
+          dl += DEL ? m - R.newc : R.newc - m;
+          db += (ull)R.nb - (ull)uold;
+          if (node_violates(a.B, a.H, 0, 1, R.nb)) a.viol[atomicAdd(&a.st->nviol, 1ull)] = j;
+          a.T_state[t] = kDone;
         }
         for (uint32_t cq = fc0; cq < fc1; cq++) a.chunk_cnt[cq] = cq == fc0 ? c0 : 0u;
         if (a.tag_counts)
           for (uint32_t q = 0; q < s; q++)
             if ((R.added >> q) & 1u) credit(a, tb + q);
       }
+    }
+    dl = warp_sum(dl);
+    db = warp_sum(db);
+    if (lane_id() == 0) {
+      if (dl) atomicAdd(&a.st->delta, dl);
+      if (db) atomicAdd(&a.st->bytes_total, db);
     }
     __syncthreads();
   }
@@ -1456,6 +1482,7 @@ __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
   ull mb = 0, dl = 0, np = 0, db = 0, ov = 0;  // db: change of the byte total, mod 2^64
   for (uint64_t t = gtid(); t < nT; t += gstride()) {
     const uint32_t state = a.T_state[t];
+    if (state == kDone) continue;  // finalised by the thread-granular merge
     const uint32_t oldc = a.T_oldcnt[t], newc = a.T_newcnt[t];
     const uint32_t j = a.T_leaf[t];
     if (a.merge_bytes && state != kUnchanged && a.T_begin[t + 1] - a.T_begin[t] > kSmall) {
@@ -2441,6 +2468,9 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   ma.list_gen = P<uint32_t>(s.list_gen);
   ma.raw = (int)h->cfg.codec;
   ma.small = k <= kSmallBatch ? 1 : 0;
+  ma.B = B;
+  ma.H = H;
+  ma.viol = P<uint32_t>(s.viol);
   const size_t per = merge_warp_bytes(LB);
   const int mwarps = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per));
   const size_t msmem = per * mwarps;
@@ -2539,7 +2569,9 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
 // ---- CUDA graphs for the front segment ----
 //
 // A batch of k keys is staged into a library buffer of K = graph_bucket(k)
-// keys, staged[j] = batch[floor(j k / K)]: every key appears once or twice,
+// keys (K = k when the previous graph-launched update had k keys too, so a
+// stream of equal batches is not padded), staged[j] = batch[floor(j k / K)]:
+// every key appears once or twice,
 // in the batch's own order (a sorted batch stays sorted), so the repeats are
 // spread evenly over the touched leaves instead of piling into one.  Repeats
 // are dropped by the merge (first occurrence wins), so the padded batch
@@ -2612,21 +2644,33 @@ uint64_t graph_bucket(uint64_t k) {
   return (k + step - 1) / step * step;
 }
 
+// staged[j] = batch[floor(j k / K)] with r = floor(2^32 k / K): (j r) >> 32 is
+// floor(j k / K) or one less (j < 2^31, so the error j (2^32 k / K - r) is
+// below 2^32), fixed by one comparison; no division on the device
 __global__ void __launch_bounds__(kT) k_stage(const uint64_t* __restrict__ in, uint64_t k,
-                                              uint64_t* __restrict__ out, uint64_t K) {
-  // j k < 2^31 * 2^31: no overflow
-  for (uint64_t j = gtid(); j < K; j += gstride()) out[j] = in[j * k / K];
+                                              uint64_t* __restrict__ out, uint64_t K, uint64_t r) {
+  for (uint64_t j = gtid(); j < K; j += gstride()) {
+    uint64_t i = (j * r) >> 32;
+    if ((i + 1) * K <= j * k) i++;
+    out[j] = in[i];
+  }
+}
+
+uint64_t graph_size(const cpma* h, uint64_t k) {
+  return k == h->graph_last_k ? k : graph_bucket(k);
 }
 
 int run_front_graph(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_delete,
                     cudaStream_t st, Front* f) {
-  const uint64_t K = graph_bucket(k);
-  CPMA_TRY(ensure(h, h->s.stage, K * 8));
-  CPMA_TRY(front_scratch(h, K, false, st));
+  const uint64_t K = graph_size(h, k);
+  CPMA_TRY(ensure(h, h->s.stage, graph_bucket(k) * 8));
+  CPMA_TRY(front_scratch(h, graph_bucket(k), false, st));
   uint64_t* stage = P<uint64_t>(h->s.stage);
-  k_stage<<<grid_for(h, K), kT, 0, st>>>(d_keys, k, stage, K);
+  const uint64_t r = (uint64_t)(((unsigned __int128)k << 32) / K);  // 2^32 when K == k
+  k_stage<<<grid_for(h, K), kT, 0, st>>>(d_keys, k, stage, K, r);
   h->launches++;
   CPMA_CUDA(cudaGetLastError());
+  h->graph_last_k = k;
   if (!h->graphs) h->graphs = new GraphCache();
   GraphCache& c = *static_cast<GraphCache*>(h->graphs);
   const FrontSig sig = front_sig(h);

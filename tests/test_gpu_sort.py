@@ -1,7 +1,8 @@
 """GPU batch sort (cpma_sort_batch) against its plain definition: the keys in
 non-decreasing order, each tag travelling with its key, equal keys in input
 order (a stable sort: numpy's stable argsort).  The sizes and key shapes
-cover the single-tile sort, the buckets by the 8 highest varying bits
+cover the single-tile sorts (a sorting network for untagged batches, a
+stable rank sort for tagged ones), the buckets by the 8 highest varying bits
 (batches of up to 1.25M keys), buckets too large for one block's shared
 memory (sorted through global memory by that block), the digit passes
 (larger batches), 34-bit uniform and skewed keys, and keys that vary in one
@@ -79,3 +80,14 @@ def test_sort_all_digits_and_equal_keys(handle):
     check(handle, W.full_range_keys(15, 300_000))
     check(handle, np.full(50_000, 0xABCDEF, dtype=np.uint64))
     check(handle, W.zipf_keys(16, 1_000_000))
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 255, 1000, 2048, 2049, 4096])
+def test_sort_small_keys_only(handle, k):
+    # untagged batches of at most 4096 keys: the one-block sorting network,
+    # padded to a power of two (repeats and the maximum key included)
+    keys = W.uniform_keys(61 + k, k, bits=40)
+    if k > 8:
+        keys[: k // 8] = keys[k // 2]
+        keys[-1] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    check(handle, keys, tagged=False)
