@@ -70,9 +70,9 @@ struct RouteOut {
 // between the sampled heads around the key before the tile and around its
 // last key (kRSamples evenly spaced heads, one load each, bisected in shared
 // memory); they are copied to shared memory when there are at most kRHeads
-// of them (else every step-th of them, and the last few candidates are
-// bisected in the global array).  A thread bisects for its first key and
-// gallops from there for the next ones.  The tile's run and chunk counts are scanned in the block
+// of them (else every step-th of them, and the last candidates are searched
+// in the global array, seven probes per round trip).  A thread bisects for
+// its first key and gallops from there for the next ones.  The tile's run and chunk counts are scanned in the block
 // and joined to the tiles before it by decoupled look-back: the whole block
 // reads 256 predecessors per step; each published value packs runs << 31 |
 // chunks with an aggregate / inclusive flag.  A predecessor that has not
@@ -98,6 +98,32 @@ __device__ __forceinline__ uint32_t bisect_upper(const uint64_t* h, uint32_t a, 
     else b = mid;
   }
   return a;
+}
+
+// The same in global memory with seven probes per round, loaded together
+// (one round trip narrows the range eightfold), then the last few entries.
+__device__ __forceinline__ uint32_t kary_upper(const uint64_t* __restrict__ g, uint32_t a,
+                                               uint32_t b, uint64_t x) {
+  while (b - a > 8) {
+    const uint64_t w = b - a;
+    uint64_t v[7];
+#pragma unroll
+    for (int i = 0; i < 7; i++) v[i] = __ldg(g + a + (uint64_t)(i + 1) * w / 8);
+    uint32_t c = 0;  // probes <= x (a prefix of them)
+#pragma unroll
+    for (int i = 0; i < 7; i++) c += v[i] <= x ? 1u : 0u;
+    const uint32_t na = c ? a + (uint32_t)((uint64_t)c * w / 8) + 1 : a;
+    const uint32_t nb = c < 7 ? a + (uint32_t)((uint64_t)(c + 1) * w / 8) : b;
+    a = na;
+    b = nb;
+  }
+  uint64_t v[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) v[i] = a + i < b ? __ldg(g + a + i) : ~0ull;
+  uint32_t c = 0;
+#pragma unroll
+  for (int i = 0; i < 8; i++) c += (a + i < b && v[i] <= x) ? 1u : 0u;
+  return a + c;
 }
 
 // The same over [a, n), probing a, a + 1, a + 3, ... first (the answer is
@@ -196,16 +222,11 @@ __global__ void __launch_bounds__(kRT, 4) k_route(const uint64_t* __restrict__ u
       sm.heads[j] = __ldg(heads + c_lo + (uint64_t)(j + 1) * step - 1);
     __syncthreads();
     // leaf of x: m staged heads <= x put the count of heads <= x in
-    // c_lo + [m step, min(m step + step - 1, nh)], bisected in the global
-    // array (nothing left to bisect when every head is staged)
+    // c_lo + [m step, min(m step + step - 1, nh)], searched in the global
+    // array (nothing left to search when every head is staged)
     auto leaf_of = [&](uint64_t y, uint32_t m) -> uint32_t {
-      uint32_t a = m * step, b = min(a + step - 1u, nh);
-      while (a < b) {
-        const uint32_t mid = (a + b) >> 1;
-        if (__ldg(heads + c_lo + mid) <= y) a = mid + 1;
-        else b = mid;
-      }
-      const uint64_t c = c_lo + a;
+      const uint32_t a = m * step, b = min(a + step - 1u, nh);
+      const uint64_t c = c_lo + (a < b ? kary_upper(heads + c_lo, a, b, y) : a);
       return (uint32_t)(c ? c - 1 : 0);
     };
     uint32_t leaf[KPT];
