@@ -496,6 +496,9 @@ __global__ void __launch_bounds__(kT) k_range(RangeArgs a) {
   if (a.prof && lane == 0 && nbytes) atomicAdd(a.prof, nbytes);
 }
 
+constexpr uint32_t kSumShift = 4;      // sort key of a leaf: used bytes / 16
+constexpr uint32_t kSumBuckets = 128;  // enough for 2048-byte leaves (a multiple of 32)
+
 __global__ void __launch_bounds__(kT) k_sum(const uint8_t* __restrict__ data,
                                             const uint32_t* __restrict__ used,
                                             const uint32_t* __restrict__ cnt, uint64_t L,
@@ -506,8 +509,49 @@ __global__ void __launch_bounds__(kT) k_sum(const uint8_t* __restrict__ data,
   const uint64_t j0 = L * gw / nw, j1 = L * (gw + 1) / nw;
   uint64_t s = 0, c = 0;
   ull nbytes = 0;
-  if (raw) warp_span_sum(data, used, cnt, LB, j0, j1, s, c, nbytes, raw);
-  else thread_span_sum(data, used, cnt, LB, j0, j1, s, c, nbytes);
+  if (raw) {
+    warp_span_sum(data, used, cnt, LB, j0, j1, s, c, nbytes, raw);
+  } else {
+    // The block's leaves in tiles of kT, each ordered by used bytes (a
+    // counting sort in shared memory), so the 32 leaves a warp decodes side
+    // by side take about the same number of steps.
+    __shared__ uint32_t s_hist[kSumBuckets];
+    __shared__ uint32_t s_order[kT];
+    const uint64_t b0 = L * blockIdx.x / gridDim.x, b1 = L * (blockIdx.x + 1) / gridDim.x;
+    for (uint64_t t0 = b0; t0 < b1; t0 += kT) {
+      for (uint32_t i = threadIdx.x; i < kSumBuckets; i += kT) s_hist[i] = 0;
+      __syncthreads();
+      const uint64_t j = t0 + threadIdx.x;
+      const uint32_t u = j < b1 ? min(used[j], LB) : 0u;
+      const uint32_t bkt = min(u >> kSumShift, kSumBuckets - 1);
+      const uint32_t slot = j < b1 ? atomicAdd(&s_hist[bkt], 1u) : 0u;
+      __syncthreads();
+      if (threadIdx.x < 32) {  // exclusive scan of the bucket counts
+        uint32_t run = 0;
+        for (uint32_t b = 0; b < kSumBuckets; b += 32) {
+          const uint32_t v = s_hist[b + lane];
+          const uint32_t inc = warp_incl_scan(v);
+          s_hist[b + lane] = run + inc - v;
+          run += __shfl_sync(FULL, inc, 31);
+        }
+      }
+      __syncthreads();
+      if (j < b1) s_order[s_hist[bkt] + slot] = threadIdx.x;
+      __syncthreads();
+      const uint32_t nt = (uint32_t)min((uint64_t)kT, b1 - t0);
+      if (threadIdx.x < nt) {
+        const uint64_t jj = t0 + s_order[threadIdx.x];
+        const uint32_t uu = min(used[jj], LB);
+        nbytes += 8;  // its used and element counts
+        if (uu) {
+          s += thread_leaf_sum(data + jj * LB, uu);
+          c += cnt[jj];
+          nbytes += uu;
+        }
+      }
+      __syncthreads();  // s_hist and s_order are reused
+    }
+  }
   s = warp_sum(s);
   c = warp_sum(c);
   nbytes = warp_sum(nbytes);
@@ -515,7 +559,7 @@ __global__ void __launch_bounds__(kT) k_sum(const uint8_t* __restrict__ data,
     atomicAdd((ull*)sum, (ull)s);
     if (count) atomicAdd((ull*)count, (ull)c);
   }
-  if (prof && lane == 0 && nbytes) atomicAdd(prof, nbytes + 8ull * (j1 - j0));
+  if (prof && lane == 0 && nbytes) atomicAdd(prof, nbytes + (raw ? 8ull * (j1 - j0) : 0ull));
 }
 
 int persistent_grid(const cpma* h) { return h->num_sms * 8; }

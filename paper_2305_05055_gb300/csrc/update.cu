@@ -2431,11 +2431,14 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   ro.T_state = P<uint32_t>(s.T_state);
   ro.T_newbytes = P<ull>(s.T_newbytes);
   {
-    // eight keys per thread once the batch fills two tiles per SM and is
-    // dense enough (a 2048-key tile then reaches about as many heads as
-    // shared memory holds); one key per thread otherwise
-    const bool wide = k >= (uint64_t)h->num_sms * 2 * 8 * kRT && 2 * k >= h->L;
-    const uint64_t tile_keys = (uint64_t)kRT * (wide ? 8 : 1);
+    // keys per thread: the most (8, 4, 2) that still gives two tiles per SM
+    // when the batch is dense against the leaves (a tile then reaches about
+    // as many heads as it has keys); one otherwise
+    int kpt = 1;
+    if (2 * k >= h->L)
+      for (int c = 8; c > 1 && kpt == 1; c >>= 1)
+        if (k >= (uint64_t)h->num_sms * 2 * kRT * c) kpt = c;
+    const uint64_t tile_keys = (uint64_t)kRT * kpt;
     const uint64_t ntiles = (k + tile_keys - 1) / tile_keys;
     // the tile counter, then one look-back word per tile
     uint64_t* look = P<uint64_t>(s.flags);
@@ -2447,12 +2450,24 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
     // keys, the heads searched, and per touched leaf its entries (36 bytes),
     // old counts (8) and work item (12)
     prof_add_bytes(h, PH_ROUTE, 8ull * k + 64ull * std::min<uint64_t>(k, h->L));
-    if (wide)
-      k_route<8><<<grid, kRT, 0, st>>>(u, k, h->heads, h->L, h->cnt, h->used, ro, look, ds, spin,
-                                       silent);
-    else
-      k_route<1><<<grid, kRT, 0, st>>>(u, k, h->heads, h->L, h->cnt, h->used, ro, look, ds, spin,
-                                       silent);
+    const uint64_t* H = h->heads;
+    switch (kpt) {
+      case 8:
+        k_route<8><<<grid, kRT, 0, st>>>(u, k, H, h->L, h->cnt, h->used, ro, look, ds, spin,
+                                         silent);
+        break;
+      case 4:
+        k_route<4><<<grid, kRT, 0, st>>>(u, k, H, h->L, h->cnt, h->used, ro, look, ds, spin,
+                                         silent);
+        break;
+      case 2:
+        k_route<2><<<grid, kRT, 0, st>>>(u, k, H, h->L, h->cnt, h->used, ro, look, ds, spin,
+                                         silent);
+        break;
+      default:
+        k_route<1><<<grid, kRT, 0, st>>>(u, k, H, h->L, h->cnt, h->used, ro, look, ds, spin,
+                                         silent);
+    }
     h->launches++;
     CPMA_CUDA(cudaGetLastError());
   }

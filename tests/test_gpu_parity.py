@@ -657,3 +657,40 @@ def test_insert_five_to_eight_keys_per_leaf(bits):
     assert counts.cpu().tolist() == want
     o.insert_batch(more)
     same_layout(g, o)
+
+
+@pytest.mark.parametrize("k", [160_000, 320_000, 640_000])
+def test_route_tile_sizes(k):
+    # batches dense against the leaves, large enough for routing tiles of
+    # 2, 4 and 8 keys per thread (512, 1024, 2048 keys per tile), inserted
+    # unsorted, pre-sorted (with repeats) and deleted, layout against the oracle
+    base = W.uniform_keys(141, 400_000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=512)
+    o = oracle.SeqCPMA(base, leaf_bytes=512)
+    ins = W.uniform_keys(142 + k, k, bits=40)
+    assert int(g.insert_batch(T(ins)).item()) == o.insert_batch(ins)
+    same_layout(g, o)
+    srt = np.sort(np.concatenate([W.uniform_keys(143 + k, k - k // 8, bits=40), ins[: k // 8]]))
+    assert int(g.insert_batch(T(srt), sorted=True).item()) == o.insert_batch(srt)
+    same_layout(g, o)
+    gone = W.sample_present(oracle.PlainSet(np.concatenate([base, ins, srt])).S, 144 + k, k)
+    assert int(g.delete_batch(T(gone)).item()) == o.delete_batch(gone)
+    same_layout(g, o)
+
+
+def test_route_sparse_tiles():
+    # small batches against many leaves: a 256-key tile reaches more heads
+    # than shared memory holds, so every step-th head is staged and the last
+    # candidates are searched in the global array (keys 0 and 2^64-1 too)
+    base = W.uniform_keys(151, 2_000_000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=256)
+    o = oracle.SeqCPMA(base, leaf_bytes=256)
+    assert g.leaves() > 4 * 4096
+    for r, k in enumerate([1, 37, 1000, 5000]):
+        ins = np.concatenate([W.uniform_keys(152 + r, k, bits=40),
+                              np.array([0, M64], np.uint64)])
+        assert int(g.insert_batch(T(ins)).item()) == o.insert_batch(ins)
+        same_layout(g, o)
+        gone = W.sample_present(np.unique(ins), 160 + r, max(1, k // 2))
+        assert int(g.delete_batch(T(gone)).item()) == o.delete_batch(gone)
+        same_layout(g, o)
