@@ -349,8 +349,8 @@ int cpma_reserve(cpma_t* h, uint64_t max_batch, uint64_t max_queries, int tagged
  * sort, route, the in-place merges and the finalize pass, everything before
  * the update's first host read -- as a CUDA graph (max_batch = 0: never; the
  * default).  A batch of k keys is staged into a library buffer of K keys, K =
- * k rounded up to four significant bits (at least 16, at most k * 9/8 for k
- * >= 16), entry j being key floor(j k / K): each key appears once or twice,
+ * k rounded up to five significant bits (at least 16, at most k * 17/16 for
+ * k >= 16), entry j being key floor(j k / K): each key appears once or twice,
  * in the batch's order.  Repeats of a key change nothing (Sec. 4 batches are
  * sets; App. A counts only keys actually added or removed), so one graph
  * serves every k of a bucket.  Graphs are captured on first use per (K,

@@ -166,7 +166,6 @@ struct cpma {
   std::atomic<uint64_t> launches{0};
   cpmaimpl::Prof prof;
   uint64_t graph_max_batch = 0;     // batches up to this size run their front segment as a graph
-  uint64_t graph_last_k = 0;        // batch size of the last graph-launched update
   void* graphs = nullptr;           // graph cache (update.cu)
   cudaStream_t cap_stream = nullptr;  // private stream graphs are captured on
   // side stream of the merge fork (k_insert_lane next to k_insert_thread) and

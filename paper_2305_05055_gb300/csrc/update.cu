@@ -2605,17 +2605,16 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
 // ---- CUDA graphs for the front segment ----
 //
 // A batch of k keys is staged into a library buffer of K = graph_bucket(k)
-// keys (K = k when the previous graph-launched update had k keys too, so a
-// stream of equal batches is not padded), staged[j] = batch[floor(j k / K)]:
-// every key appears once or twice,
-// in the batch's own order (a sorted batch stays sorted), so the repeats are
-// spread evenly over the touched leaves instead of piling into one.  Repeats
-// are dropped by the merge (first occurrence wins), so the padded batch
-// changes the set exactly as the original does, and one graph serves every k
-// of its bucket.  A graph bakes in the addresses of the structure's arrays, of the
-// scratch buffers the segment touches and the leaf count, so it is keyed by
-// (K, sorted, insert/delete, those addresses and L) and captured again when
-// any of them changed (a resize, a scratch buffer that had to grow).
+// keys (k rounded up to 5 significant bits: K <= 17k/16), staged[j] =
+// batch[floor(j k / K)]: every key appears once or twice, in the batch's own
+// order (a sorted batch stays sorted), so the repeats are spread evenly over
+// the touched leaves instead of piling into one.  Repeats are dropped by the
+// merge (first occurrence wins), so the padded batch changes the set exactly
+// as the original does, and one graph serves every k of its bucket.  A graph
+// bakes in the addresses of the structure's arrays, of the scratch buffers
+// the segment touches and the leaf count, so it is keyed by (K, sorted,
+// insert/delete, those addresses and L) and captured again when any of them
+// changed (a resize, a scratch buffer that had to grow).
 
 constexpr int kGraphSlots = 8;
 
@@ -2673,10 +2672,10 @@ struct GraphCache {
 };
 
 // k rounded up to 4 significant bits (at most 1/8 extra keys), at least 16
-uint64_t graph_bucket(uint64_t k) {
+uint64_t graph_bucket(uint64_t k) {  // k rounded up to 5 significant bits
   if (k <= 16) return 16;
   const unsigned e = 63u - (unsigned)__builtin_clzll(k);
-  const uint64_t step = 1ull << (e - 3);
+  const uint64_t step = 1ull << (e - 4);
   return (k + step - 1) / step * step;
 }
 
@@ -2692,21 +2691,17 @@ __global__ void __launch_bounds__(kT) k_stage(const uint64_t* __restrict__ in, u
   }
 }
 
-uint64_t graph_size(const cpma* h, uint64_t k) {
-  return k == h->graph_last_k ? k : graph_bucket(k);
-}
 
 int run_front_graph(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_delete,
                     cudaStream_t st, Front* f) {
-  const uint64_t K = graph_size(h, k);
-  CPMA_TRY(ensure(h, h->s.stage, graph_bucket(k) * 8));
-  CPMA_TRY(front_scratch(h, graph_bucket(k), false, st));
+  const uint64_t K = graph_bucket(k);
+  CPMA_TRY(ensure(h, h->s.stage, K * 8));
+  CPMA_TRY(front_scratch(h, K, false, st));
   uint64_t* stage = P<uint64_t>(h->s.stage);
   const uint64_t r = (uint64_t)(((unsigned __int128)k << 32) / K);  // 2^32 when K == k
   k_stage<<<grid_for(h, K), kT, 0, st>>>(d_keys, k, stage, K, r);
   h->launches++;
   CPMA_CUDA(cudaGetLastError());
-  h->graph_last_k = k;
   if (!h->graphs) h->graphs = new GraphCache();
   GraphCache& c = *static_cast<GraphCache*>(h->graphs);
   const FrontSig sig = front_sig(h);
