@@ -2775,11 +2775,12 @@ int run_front_graph(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int
 }  // namespace
 
 void graph_cache_free(cpma* h) {
-  if (!h->graphs) return;
-  GraphCache* c = static_cast<GraphCache*>(h->graphs);
-  for (GraphSlot& g : c->slot) g.release();
-  delete c;
-  h->graphs = nullptr;
+  if (h->graphs) {
+    GraphCache* c = static_cast<GraphCache*>(h->graphs);
+    for (GraphSlot& g : c->slot) g.release();
+    delete c;
+    h->graphs = nullptr;
+  }
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   h->cap_stream = nullptr;
   if (h->side) cudaStreamDestroy(h->side);
