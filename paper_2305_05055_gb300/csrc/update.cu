@@ -4,13 +4,15 @@
 //
 // Phases of one batch, all on the caller's stream:
 //  1. sort the batch (sort.cu);
-//  2. route: every sorted key goes to the last leaf whose head-index entry is
-//     <= key; runs of equal leaf ids are the touched leaves, further split
-//     every kChunk keys into merge work items (one scan over packed flags);
-//  3. merge (warp per work item): decode the leaf, merge (insert: union with
-//     the repeat-free slice; delete: difference), count the new bytes.  A
-//     single-item leaf whose result fits is rewritten in place; otherwise the
-//     leaf is "pending" and its merged elements go to an overflow buffer
+//  2. route (one kernel): every sorted key goes to the last leaf whose
+//     head-index entry is <= key; runs of equal leaf ids are the touched
+//     leaves, further split every kChunk keys into merge work items (their
+//     counts scanned across tiles by decoupled look-back);
+//  3. merge: decode the leaf, merge (insert: union with the repeat-free
+//     slice; delete: difference), count the new bytes -- one thread per leaf
+//     for slices of at most four keys, a warp per leaf or per work item
+//     otherwise.  A leaf whose result fits is rewritten in place; otherwise
+//     the leaf is "pending" and its merged elements go to an overflow buffer
 //     (Sec. 4: "copies all elements into separate memory");
 //  4. counting (Sec. 4 "Counting phase"): every changed leaf that violates
 //     its own bound walks up the implicit tree over a prefix sum of the byte
