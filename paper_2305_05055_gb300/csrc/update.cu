@@ -973,8 +973,9 @@ __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
       const uint32_t uold = a.T_oldused[t], j = a.T_leaf[t], m = a.T_oldcnt[t];
       const uint32_t fc0 = a.T_first_chunk[t], fc1 = a.T_first_chunk[t + 1];
       uint8_t* leafp = a.data + (size_t)j * a.LB;
-      // the old leaf, the slice and ~28 bytes of per-leaf metadata
-      nbytes += uold + 8u * s + 28u;
+      // algorithmic bytes of a touched leaf: the old leaf, the new one and
+      // 24 bytes of metadata (the new leaf added below once it is known)
+      nbytes += uold + 24u;
       uint64_t y[K];
 #pragma unroll
       for (uint32_t q = 0; q < K; q++) y[q] = q < s ? a.u[tb + q] : 0ull;
@@ -988,6 +989,7 @@ __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
       } else {
         uint32_t c0 = 0;
         if (res == leafthr::kUnchanged) {
+          nbytes += uold;
           a.T_state[t] = kUnchanged;
           a.T_newcnt[t] = m;
           a.T_newbytes[t] = uold;
@@ -1005,7 +1007,7 @@ __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
             leafthr::rewrite_leaf(leafp, a.LB, uold, S, R);
             leafthr::write_edits(leafp, y, S, R);
           }
-          nbytes += R.whi - R.wlo;
+          nbytes += R.nb;
           a.used[j] = R.nb;
           a.cnt[j] = R.newc;
           a.heads[j] = R.newhead;
