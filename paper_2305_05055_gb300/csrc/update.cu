@@ -1505,39 +1505,53 @@ __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
   if (a.st->err) return;
   const uint64_t nT = a.st->nT;
   ull mb = 0, dl = 0, np = 0, db = 0, ov = 0;  // db: change of the byte total, mod 2^64
-  for (uint64_t t = gtid(); t < nT; t += gstride()) {
-    const uint32_t state = a.T_state[t];
-    if (state == kDone) continue;  // finalised by the thread-granular merge
-    const uint32_t oldc = a.T_oldcnt[t], newc = a.T_newcnt[t];
-    const uint32_t j = a.T_leaf[t];
-    if (a.merge_bytes && state != kUnchanged && a.T_begin[t + 1] - a.T_begin[t] > kSmall) {
-      // leaves of the element-array / general merge: old leaf, slice,
-      // metadata, and the rewrite when in place
-      mb += a.T_oldused[t] + 8ull * (a.T_begin[t + 1] - a.T_begin[t]) + 24;
-      if (state == kInPlace) mb += (max(a.T_oldused[t], (uint32_t)a.T_newbytes[t]) + 15u) & ~15u;
+  // four entries per thread and step, their states loaded at once: most are
+  // already done (the thread-granular merge finalised them)
+  for (uint64_t t0 = gtid() * 4; t0 < nT; t0 += gstride() * 4) {
+    uint32_t sv[4];
+    if (t0 + 4 <= nT) {
+      const uint4 v = *reinterpret_cast<const uint4*>(a.T_state + t0);
+      sv[0] = v.x; sv[1] = v.y; sv[2] = v.z; sv[3] = v.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; i++) sv[i] = t0 + i < nT ? a.T_state[t0 + i] : kDone;
     }
-    if (newc == oldc) {
-      if (state == kPending) {
-        a.T_state[t] = kUnchanged;
-        for (uint32_t c = a.T_first_chunk[t]; c < a.T_first_chunk[t + 1]; c++) a.chunk_cnt[c] = 0;
+#pragma unroll 1
+    for (int i = 0; i < 4; i++) {
+      const uint64_t t = t0 + i;
+      const uint32_t state = sv[i];
+      if (state == kDone) continue;  // finalised by the thread-granular merge
+      const uint32_t oldc = a.T_oldcnt[t], newc = a.T_newcnt[t];
+      const uint32_t j = a.T_leaf[t];
+      if (a.merge_bytes && state != kUnchanged && a.T_begin[t + 1] - a.T_begin[t] > kSmall) {
+        // leaves of the element-array / general merge: old leaf, slice,
+        // metadata, and the rewrite when in place
+        mb += a.T_oldused[t] + 8ull * (a.T_begin[t + 1] - a.T_begin[t]) + 24;
+        if (state == kInPlace) mb += (max(a.T_oldused[t], (uint32_t)a.T_newbytes[t]) + 15u) & ~15u;
       }
-      continue;
-    }
-    dl += (ull)(a.is_delete ? oldc - newc : newc - oldc);
-    const uint64_t nb = a.T_newbytes[t];
-    db += nb - (ull)a.T_oldused[t];
-    if (state == kPending) {
-      a.used[j] = (uint32_t)nb;
-      a.cnt[j] = newc;
-      np++;
-      // its merged elements, counted per work item (the overflow total)
-      for (uint32_t c = a.T_first_chunk[t]; c < a.T_first_chunk[t + 1]; c++) ov += a.chunk_cnt[c];
-    }
-    if (node_violates(a.B, a.H, 0, 1, nb)) {
-      const ull v = atomicAdd(&a.st->nviol, 1ull);
-      a.viol[v] = j;
-    } else if (state == kPending) {
-      mark_node(a.bits, a.lv, 0, j, a.cand, a.st);
+      if (newc == oldc) {
+        if (state == kPending) {
+          a.T_state[t] = kUnchanged;
+          for (uint32_t c = a.T_first_chunk[t]; c < a.T_first_chunk[t + 1]; c++) a.chunk_cnt[c] = 0;
+        }
+        continue;
+      }
+      dl += (ull)(a.is_delete ? oldc - newc : newc - oldc);
+      const uint64_t nb = a.T_newbytes[t];
+      db += nb - (ull)a.T_oldused[t];
+      if (state == kPending) {
+        a.used[j] = (uint32_t)nb;
+        a.cnt[j] = newc;
+        np++;
+        // its merged elements, counted per work item (the overflow total)
+        for (uint32_t c = a.T_first_chunk[t]; c < a.T_first_chunk[t + 1]; c++) ov += a.chunk_cnt[c];
+      }
+      if (node_violates(a.B, a.H, 0, 1, nb)) {
+        const ull v = atomicAdd(&a.st->nviol, 1ull);
+        a.viol[v] = j;
+      } else if (state == kPending) {
+        mark_node(a.bits, a.lv, 0, j, a.cand, a.st);
+      }
     }
   }
   // one atomic per warp for the batch totals
