@@ -75,9 +75,9 @@ struct Scratch {
   Buf keysA, keysB;       // sort ping-pong (u64)
   Buf valsA, valsB;       // sort ping-pong of 32-bit tags
   Buf hist;               // sort control block and look-back arrays
-  Buf flags;              // route / unique flags (u64)
-  Buf flags_scan;         // scanned flags (u64)
-  Buf leaf_of;            // leaf per sorted key (u32)
+  Buf flags;              // routing: tile counter and look-back words (u64)
+  Buf flags_scan;         // build and rebuild: scanned flags (u64)
+  Buf leaf_of;            // build: unique flags (u32)
   Buf chunk_begin, chunk_leaf, chunk_tid, chunk_cnt, chunk_off;
   Buf T_leaf, T_begin, T_first_chunk, T_oldcnt, T_oldused, T_newcnt, T_newbytes, T_state;
   Buf viol, cand, wins;   // violating leaves, window candidates, windows

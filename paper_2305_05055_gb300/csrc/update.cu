@@ -2385,9 +2385,8 @@ int front_scratch(cpma* h, uint64_t k, bool tagged, cudaStream_t st) {
   if (!h->ev_join) CPMA_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   CPMA_TRY(sort_scratch(h, k, tagged));
   CPMA_TRY(ensure(h, s.partials, (size_t)(2 * h->num_sms + 2) * 8));
-  CPMA_TRY(ensure(h, s.leaf_of, k * 4));
-  CPMA_TRY(ensure(h, s.flags, (k + 2) * 8));  // also the routing look-back words
-  CPMA_TRY(ensure(h, s.flags_scan, (k + 1) * 8));
+  // the routing's tile counter and look-back words (tiles of >= 256 keys)
+  CPMA_TRY(ensure(h, s.flags, (k / 256 + 3) * 8));
   for (Buf* b : {&s.chunk_begin, &s.chunk_leaf, &s.chunk_tid, &s.chunk_cnt, &s.T_leaf, &s.T_begin,
                  &s.T_first_chunk, &s.T_oldcnt, &s.T_oldused, &s.T_newcnt, &s.T_state, &s.viol})
     CPMA_TRY(ensure(h, *b, (k + 2) * 4));
