@@ -35,7 +35,8 @@ struct Status {
   ull n_lane;      // touched leaves for the lane-granular insert
   ull n_v1;        // touched leaves for the element-array splice
   ull n_gen;       // work items for the general merge
-  ull pad[10];
+  ull n_pendl;     // pending leaves left by the thread- and lane-granular inserts
+  ull pad[9];
   ull empties;     // empty leaves in the structure (written by the head
                    // fix-up; not cleared at the start of a batch)
   ull bytes_total; // used bytes over all leaves, kept exact by the merge,
@@ -82,6 +83,7 @@ struct Scratch {
   Buf T_leaf, T_begin, T_first_chunk, T_oldcnt, T_oldused, T_newcnt, T_newbytes, T_state;
   Buf viol, cand, wins;   // violating leaves, window candidates, windows
   Buf list_lane, list_v1, list_gen;  // merge work lists
+  Buf list_pend;          // pending leaves of the thread- and lane-granular inserts
   Buf bits;               // per-level window bitsets (u32 words)
   Buf prefix;             // prefix sums of used bytes (u64, L+1)
   Buf E, cost, C;         // redistribution: elements, costs, cost prefix; C also holds

@@ -416,6 +416,7 @@ struct MergeArgs {
   uint32_t* list_lane;   // touched leaves for k_insert_lane (count st->n_lane)
   uint32_t* list_v1;     // touched leaves for k_merge_small (count st->n_v1)
   uint32_t* list_gen;    // work items for k_merge in count mode (st->n_gen)
+  uint32_t* list_pend;   // pending leaves of k_insert_thread / k_insert_lane (st->n_pendl)
   int raw;               // leaves hold 8-byte cells (codec 1), not byte codes
   int small;             // a small batch: every slice goes to a warp per leaf
   Bounds B;              // density bounds and tree height, for the leaves the
@@ -650,6 +651,7 @@ __global__ void __launch_bounds__(kT, SEG == 32 ? 4 : 3) k_insert_lane(MergeArgs
   int32_t* shc = reinterpret_cast<int32_t*>(en + KS);
   const uint64_t nL = a.st->n_lane;
   ull nbytes = 0;  // algorithmic bytes (lane 0 of each segment)
+  ull dl = 0, db = 0;  // keys added, byte total change (lane 0 of each segment)
   uint64_t r0, r1;
   warp_share(nL, (uint64_t)blockIdx.x * wpb + warp, (uint64_t)gridDim.x * wpb, r0, r1);
   for (uint64_t tbase = r0; tbase < r1; tbase += 32) {
@@ -843,6 +845,7 @@ __global__ void __launch_bounds__(kT, SEG == 32 ? 4 : 3) k_insert_lane(MergeArgs
         a.T_state[t] = kPending;
         a.T_newcnt[t] = newc;
         a.T_newbytes[t] = nb;
+        a.list_pend[atomicAdd(&a.st->n_pendl, 1ull)] = t;
       }
       for (uint32_t cq = fc0 + sl; cq < fc1; cq += SEG) a.chunk_cnt[cq] = (cq == fc0) ? newc : 0u;
       if (keep) credit(a, tb + sl);
@@ -893,16 +896,26 @@ __global__ void __launch_bounds__(kT, SEG == 32 ? 4 : 3) k_insert_lane(MergeArgs
       a.used[j] = nb;
       a.cnt[j] = newc;
       a.heads[j] = newhead;
-      a.T_state[t] = kInPlace;
       a.T_newcnt[t] = newc;
       a.T_newbytes[t] = nb;
+      // the finalize pass's work for this leaf, done here
+      dl += newc - m;
+      db += (ull)nb - (ull)uold;
+      if (node_violates(a.B, a.H, 0, 1, nb)) a.viol[atomicAdd(&a.st->nviol, 1ull)] = j;
+      a.T_state[t] = kDone;
     }
     for (uint32_t cq = fc0 + sl; cq < fc1; cq += SEG) a.chunk_cnt[cq] = 0;
     __syncwarp(seg);
     }
   }
   nbytes = warp_sum(sl == 0 ? nbytes : 0ull);
-  if (a.prof && lane == 0 && nbytes) atomicAdd(a.prof, nbytes);
+  dl = warp_sum(sl == 0 ? dl : 0ull);
+  db = warp_sum(sl == 0 ? db : 0ull);
+  if (lane == 0) {
+    if (a.prof && nbytes) atomicAdd(a.prof, nbytes);
+    if (dl) atomicAdd(&a.st->delta, dl);
+    if (db) atomicAdd(&a.st->bytes_total, db);
+  }
 }
 
 // Insert of a slice of at most leafthr::kKeys keys into one leaf of byte
@@ -997,6 +1010,7 @@ __global__ void __launch_bounds__(kThrT) k_insert_thread(MergeArgs a) {
           a.T_state[t] = kPending;
           a.T_newcnt[t] = R.newc;
           a.T_newbytes[t] = R.nb;
+          a.list_pend[atomicAdd(&a.st->n_pendl, 1ull)] = t;
           c0 = R.newc;
         } else {
           if (DEL) {
@@ -1491,6 +1505,8 @@ struct FinArgs {
   uint32_t* T_state;
   const ull* T_newbytes;
   uint32_t* chunk_cnt;
+  const uint32_t* chunk_tid;
+  const uint32_t *list_v1, *list_gen, *list_pend;
   uint32_t* viol;
   uint64_t* cand;
   uint32_t* bits;
@@ -1503,55 +1519,53 @@ struct FinArgs {
 
 __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
   if (a.st->err) return;
-  const uint64_t nT = a.st->nT;
   ull mb = 0, dl = 0, np = 0, db = 0, ov = 0;  // db: change of the byte total, mod 2^64
-  // four entries per thread and step, their states loaded at once: most are
-  // already done (the thread-granular merge finalised them)
-  for (uint64_t t0 = gtid() * 4; t0 < nT; t0 += gstride() * 4) {
-    uint32_t sv[4];
-    if (t0 + 4 <= nT) {
-      const uint4 v = *reinterpret_cast<const uint4*>(a.T_state + t0);
-      sv[0] = v.x; sv[1] = v.y; sv[2] = v.z; sv[3] = v.w;
+  // the touched leaves the thread- and lane-granular inserts did not finish
+  // themselves: the element-array splice's list, the general merge's leaves
+  // (each once, by its first work item) and the pending leaves they left
+  const uint64_t nv = a.st->n_v1, ng = a.st->n_gen, npl = a.st->n_pendl;
+  for (uint64_t i = gtid(); i < nv + ng + npl; i += gstride()) {
+    uint64_t t;
+    if (i < nv) {
+      t = a.list_v1[i];
+    } else if (i < nv + ng) {
+      const uint32_t c = a.list_gen[i - nv];
+      t = a.chunk_tid[c];
+      if (a.T_first_chunk[t] != c) continue;
     } else {
-#pragma unroll
-      for (int i = 0; i < 4; i++) sv[i] = t0 + i < nT ? a.T_state[t0 + i] : kDone;
+      t = a.list_pend[i - nv - ng];
     }
-#pragma unroll 1
-    for (int i = 0; i < 4; i++) {
-      const uint64_t t = t0 + i;
-      const uint32_t state = sv[i];
-      if (state == kDone) continue;  // finalised by the thread-granular merge
-      const uint32_t oldc = a.T_oldcnt[t], newc = a.T_newcnt[t];
-      const uint32_t j = a.T_leaf[t];
-      if (a.merge_bytes && state != kUnchanged && a.T_begin[t + 1] - a.T_begin[t] > kSmall) {
-        // leaves of the element-array / general merge: old leaf, slice,
-        // metadata, and the rewrite when in place
-        mb += a.T_oldused[t] + 8ull * (a.T_begin[t + 1] - a.T_begin[t]) + 24;
-        if (state == kInPlace) mb += (max(a.T_oldused[t], (uint32_t)a.T_newbytes[t]) + 15u) & ~15u;
-      }
-      if (newc == oldc) {
-        if (state == kPending) {
-          a.T_state[t] = kUnchanged;
-          for (uint32_t c = a.T_first_chunk[t]; c < a.T_first_chunk[t + 1]; c++) a.chunk_cnt[c] = 0;
-        }
-        continue;
-      }
-      dl += (ull)(a.is_delete ? oldc - newc : newc - oldc);
-      const uint64_t nb = a.T_newbytes[t];
-      db += nb - (ull)a.T_oldused[t];
+    const uint32_t state = a.T_state[t];
+    const uint32_t oldc = a.T_oldcnt[t], newc = a.T_newcnt[t];
+    const uint32_t j = a.T_leaf[t];
+    if (a.merge_bytes && state != kUnchanged && a.T_begin[t + 1] - a.T_begin[t] > kSmall) {
+      // leaves of the element-array / general merge: old leaf, slice,
+      // metadata, and the rewrite when in place
+      mb += a.T_oldused[t] + 8ull * (a.T_begin[t + 1] - a.T_begin[t]) + 24;
+      if (state == kInPlace) mb += (max(a.T_oldused[t], (uint32_t)a.T_newbytes[t]) + 15u) & ~15u;
+    }
+    if (newc == oldc) {
       if (state == kPending) {
-        a.used[j] = (uint32_t)nb;
-        a.cnt[j] = newc;
-        np++;
-        // its merged elements, counted per work item (the overflow total)
-        for (uint32_t c = a.T_first_chunk[t]; c < a.T_first_chunk[t + 1]; c++) ov += a.chunk_cnt[c];
+        a.T_state[t] = kUnchanged;
+        for (uint32_t c = a.T_first_chunk[t]; c < a.T_first_chunk[t + 1]; c++) a.chunk_cnt[c] = 0;
       }
-      if (node_violates(a.B, a.H, 0, 1, nb)) {
-        const ull v = atomicAdd(&a.st->nviol, 1ull);
-        a.viol[v] = j;
-      } else if (state == kPending) {
-        mark_node(a.bits, a.lv, 0, j, a.cand, a.st);
-      }
+      continue;
+    }
+    dl += (ull)(a.is_delete ? oldc - newc : newc - oldc);
+    const uint64_t nb = a.T_newbytes[t];
+    db += nb - (ull)a.T_oldused[t];
+    if (state == kPending) {
+      a.used[j] = (uint32_t)nb;
+      a.cnt[j] = newc;
+      np++;
+      // its merged elements, counted per work item (the overflow total)
+      for (uint32_t c = a.T_first_chunk[t]; c < a.T_first_chunk[t + 1]; c++) ov += a.chunk_cnt[c];
+    }
+    if (node_violates(a.B, a.H, 0, 1, nb)) {
+      const ull v = atomicAdd(&a.st->nviol, 1ull);
+      a.viol[v] = j;
+    } else if (state == kPending) {
+      mark_node(a.bits, a.lv, 0, j, a.cand, a.st);
     }
   }
   // one atomic per warp for the batch totals
@@ -2395,6 +2409,7 @@ int front_scratch(cpma* h, uint64_t k, bool tagged, cudaStream_t st) {
   CPMA_TRY(ensure(h, s.list_lane, (k + 2) * 4));
   CPMA_TRY(ensure(h, s.list_v1, (k + 2) * 4));
   CPMA_TRY(ensure(h, s.list_gen, (k + 2) * 4));
+  CPMA_TRY(ensure(h, s.list_pend, (k + 2) * 4));
   CPMA_TRY(ensure(h, s.cand, (2 * k + 2) * 8));
   CPMA_TRY(ensure(h, s.wins, (2 * k + 2) * 16));
   CPMA_TRY(ensure(h, s.prefix, (h->L + 2) * 8));
@@ -2519,6 +2534,7 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   ma.list_lane = P<uint32_t>(s.list_lane);
   ma.list_v1 = P<uint32_t>(s.list_v1);
   ma.list_gen = P<uint32_t>(s.list_gen);
+  ma.list_pend = P<uint32_t>(s.list_pend);
   ma.raw = (int)h->cfg.codec;
   ma.small = k <= kSmallBatch ? 1 : 0;
   ma.B = B;
@@ -2595,6 +2611,10 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   fa.T_state = ro.T_state;
   fa.T_newbytes = ro.T_newbytes;
   fa.chunk_cnt = ma.chunk_cnt;
+  fa.chunk_tid = ma.chunk_tid;
+  fa.list_v1 = ma.list_v1;
+  fa.list_gen = ma.list_gen;
+  fa.list_pend = ma.list_pend;
   fa.viol = P<uint32_t>(s.viol);
   fa.cand = P<uint64_t>(s.cand);
   fa.bits = P<uint32_t>(s.bits);
@@ -2635,7 +2655,7 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
 
 constexpr int kGraphSlots = 8;
 
-constexpr int kSigPtrs = 33;
+constexpr int kSigPtrs = 34;
 
 struct FrontSig {
   const void* p[kSigPtrs];
@@ -2657,7 +2677,7 @@ FrontSig front_sig(const cpma* h) {
                    s.chunk_leaf.p, s.chunk_tid.p, s.chunk_cnt.p,     s.chunk_off.p, s.T_leaf.p,
                    s.T_begin.p,   s.T_first_chunk.p, s.T_oldcnt.p,   s.T_oldused.p, s.T_newcnt.p,
                    s.T_newbytes.p, s.T_state.p,   s.viol.p,          s.list_lane.p, s.list_v1.p,
-                   s.list_gen.p,  s.cand.p,       s.wins.p,          s.bits.p,      h->data,
+                   s.list_gen.p,  s.list_pend.p,  s.cand.p,          s.wins.p,      s.bits.p,  h->data,
                    h->used,       h->cnt,         h->heads,          h->d_status},
                   h->L, h->cfg.leaf_bytes, h->sort_poll_limit, h->sort_silent_tile};
 }
@@ -2975,7 +2995,7 @@ void trim_update_scratch(cpma* h) {
                  &s.leaf_of, &s.chunk_begin, &s.chunk_leaf, &s.chunk_tid, &s.chunk_cnt,
                  &s.chunk_off, &s.T_leaf, &s.T_begin, &s.T_first_chunk, &s.T_oldcnt, &s.T_oldused,
                  &s.T_newcnt, &s.T_newbytes, &s.T_state, &s.viol, &s.list_lane, &s.list_v1,
-                 &s.list_gen, &s.cand, &s.wins, &s.bits, &s.prefix, &s.E, &s.cost, &s.C,
+                 &s.list_gen, &s.list_pend, &s.cand, &s.wins, &s.bits, &s.prefix, &s.E, &s.cost, &s.C,
                  &s.srccnt, &s.srcoff, &s.dstart, &s.win_src, &s.win_dst, &s.win_leaf_off,
                  &s.win_elem_off, &s.win_dst_off, &s.partials, &s.stage, &s.fh})
     release(h, *b);
