@@ -912,7 +912,9 @@ def sweep(a, g, dev, T, timed):
     insert + delete of another batch of the same size first, which leaves the
     same set.  Then the insert of the trial's batch and the delete of the
     same keys, each timed alone after an L2 flush.  Reported: medians, launch
-    by launch and with the front segment as a CUDA graph."""
+    by launch and with the front segment as a CUDA graph; inserts of up to
+    4096 keys take the point path in both, so for those sizes a third form
+    times the batch algorithm alone (point path off, graphs on)."""
     import torch
     from paper_2305_05055_gb300 import workloads as W
     rows = []
@@ -920,12 +922,15 @@ def sweep(a, g, dev, T, timed):
         res = {"batch": kk}
         batches = [T(W.uniform_keys(3 * 10 ** 7 + 100 * t + kk % 97, kk, bits=40))
                    for t in range(a.sweep_trials + 2)]
-        for mode in ("eager", "graph"):
+        modes = ("eager", "graph") + (("batch_graph",) if kk <= 4096 else ())
+        for mode in modes:
             ins_ms, del_ms, added = [], [], []
             for t in range(a.sweep_trials + 1):
                 c = g.clone()
                 c.reserve(kk)
-                c.use_graphs((1 << 31) - 1 if mode == "graph" else 0)
+                c.use_graphs((1 << 31) - 1 if mode != "eager" else 0)
+                if mode == "batch_graph":
+                    c.set_point_max(0)
                 w = batches[-1]
                 c.insert_batch(w)
                 c.delete_batch(w)
@@ -945,10 +950,8 @@ def sweep(a, g, dev, T, timed):
                          "insert_keys_per_s": kk / (mi / 1e3),
                          "delete_keys_per_s": kk / (md / 1e3),
                          "insert_ms_min": min(ins_ms), "delete_ms_min": min(del_ms)}
-        res["insert_keys_per_s"] = max(res["eager"]["insert_keys_per_s"],
-                                       res["graph"]["insert_keys_per_s"])
-        res["delete_keys_per_s"] = max(res["eager"]["delete_keys_per_s"],
-                                       res["graph"]["delete_keys_per_s"])
+        res["insert_keys_per_s"] = max(res[m]["insert_keys_per_s"] for m in modes)
+        res["delete_keys_per_s"] = max(res[m]["delete_keys_per_s"] for m in modes)
         rows.append(res)
         del batches
     return rows

@@ -365,6 +365,26 @@ int cpma_reserve(cpma_t* h, uint64_t max_batch, uint64_t max_queries, int tagged
  * route work.  Errors: CPMA_EINVAL (null handle). */
 int cpma_use_graphs(cpma_t* h, uint64_t max_batch);
 
+/* Point path (Sec. 4: a batch much smaller than the set is applied as point
+ * updates rather than by the batch merge).  An untagged insert of 1 ..
+ * max_keys keys (at most 4096; default 4096; 0 = never) into a non-empty set
+ * of byte-code leaves of at most 512 bytes is first sorted and routed by one
+ * block, and each touched leaf is checked by a warp: it takes its keys in
+ * place when it receives at most 32 of them, holds at most 512 used bytes
+ * and codes of at most 4 bytes, and the result fits in 512 bytes and keeps
+ * the leaf within its own density bound (Sec. 3 bounds at height 0).  If
+ * every touched leaf does, they are rewritten in place and the update is
+ * done (three kernels and one status read); otherwise nothing is written and
+ * the update runs the batch algorithm.  Counts, sets and layouts are the same
+ * either way: with no leaf pending and none over its bound the batch
+ * algorithm rewrites exactly those leaves, with the same bytes, and starts no
+ * redistribution.  Errors: CPMA_EINVAL (null handle). */
+int cpma_set_point_max(cpma_t* h, uint64_t max_keys);
+
+/* Updates that took the point path (calls) and those of them that the batch
+ * algorithm finished instead (batch) since the handle was created. */
+int cpma_point_stats(const cpma_t* h, uint64_t* calls, uint64_t* batch);
+
 /* Graph captures and graph launches of updates on this handle so far. */
 int cpma_graph_stats(const cpma_t* h, uint64_t* captures, uint64_t* launches);
 

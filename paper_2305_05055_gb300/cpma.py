@@ -89,6 +89,8 @@ def lib():
                 "cpma_range_extract": (I, [V, V, V, U64, V, V, U64, V]),
                 "cpma_use_graphs": (I, [V, U64]),
                 "cpma_graph_stats": (I, [V, P64, P64]),
+                "cpma_set_point_max": (I, [V, U64]),
+                "cpma_point_stats": (I, [V, P64, P64]),
                 "cpma_leaf_bytes": (I, [V, P64]),
                 "cpma_mem_held": (I, [V, P64]),
                 "cpma_mem_peak": (I, [V, P64]),
@@ -385,6 +387,17 @@ def cpma_graph_stats(h) -> dict:
     return {"captures": int(c.value), "launches": int(n.value)}
 
 
+def cpma_set_point_max(h, max_keys: int):
+    """Untagged inserts of <= max_keys keys try the point path first (0: never)."""
+    _check(lib().cpma_set_point_max(h, int(max_keys)), "cpma_set_point_max")
+
+
+def cpma_point_stats(h) -> dict:
+    c, b = C.c_uint64(), C.c_uint64()
+    _check(lib().cpma_point_stats(h, C.byref(c), C.byref(b)), "cpma_point_stats")
+    return {"calls": int(c.value), "batch": int(b.value)}
+
+
 PHASES = ("sort", "route", "merge", "count", "redistribute", "finish", "has",
           "range_prep", "range", "sum", "merge_other", "merge_lane")
 
@@ -512,6 +525,12 @@ class CPMA:
 
     def graph_stats(self) -> dict:
         return cpma_graph_stats(self._h)
+
+    def set_point_max(self, max_keys: int):
+        cpma_set_point_max(self._h, max_keys)
+
+    def point_stats(self) -> dict:
+        return cpma_point_stats(self._h)
 
     def profile(self, enable: bool = True, phases=None):
         """Reset and enable (or disable) per-phase profiling; `phases` limits

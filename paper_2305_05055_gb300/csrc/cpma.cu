@@ -274,7 +274,7 @@ void release_all(cpma* h) {
   for (Buf* b : {&s.keysA, &s.keysB, &s.valsA, &s.valsB, &s.hist, &s.flags, &s.flags_scan, &s.leaf_of,
                  &s.chunk_begin, &s.chunk_leaf, &s.chunk_tid, &s.chunk_cnt, &s.chunk_off,
                  &s.T_leaf, &s.T_begin, &s.T_first_chunk, &s.T_oldcnt, &s.T_oldused, &s.T_newcnt,
-                 &s.T_newbytes, &s.T_state, &s.viol, &s.list_lane, &s.list_v1, &s.list_gen, &s.list_pend, &s.cand,
+                 &s.T_newbytes, &s.T_state, &s.viol, &s.list_lane, &s.list_v1, &s.list_gen, &s.list_pend, &s.point_stage, &s.point_rec, &s.cand,
                  &s.wins, &s.bits, &s.prefix, &s.E, &s.cost, &s.C, &s.srccnt, &s.srcoff, &s.dstart,
                  &s.win_src, &s.win_dst, &s.win_leaf_off, &s.win_elem_off, &s.win_dst_off,
                  &s.partials, &s.partials_q, &s.q_first, &s.q_items, &s.q_off, &s.stage, &s.q_lo,
@@ -630,6 +630,19 @@ int cpma_reserve(cpma_t* h, uint64_t max_batch, uint64_t max_queries, int tagged
 int cpma_use_graphs(cpma_t* h, uint64_t max_batch) {
   if (!h) return CPMA_EINVAL;
   h->graph_max_batch = max_batch;
+  return CPMA_OK;
+}
+
+int cpma_set_point_max(cpma_t* h, uint64_t max_keys) {
+  if (!h) return CPMA_EINVAL;
+  h->point_max = max_keys;
+  return CPMA_OK;
+}
+
+int cpma_point_stats(const cpma_t* h, uint64_t* calls, uint64_t* batch) {
+  if (!h) return CPMA_EINVAL;
+  if (calls) *calls = h->point_calls;
+  if (batch) *batch = h->point_batch;
   return CPMA_OK;
 }
 

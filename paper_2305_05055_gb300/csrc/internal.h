@@ -36,7 +36,9 @@ struct Status {
   ull n_v1;        // touched leaves for the element-array splice
   ull n_gen;       // work items for the general merge
   ull n_pendl;     // pending leaves left by the thread- and lane-granular inserts
-  ull pad[9];
+  ull point_fb;    // point path: touched leaves that need the batch algorithm
+  ull point_done;  // point path: blocks finished (the last one finishes the pass)
+  ull pad[7];
   ull empties;     // empty leaves in the structure (written by the head
                    // fix-up; not cleared at the start of a batch)
   ull bytes_total; // used bytes over all leaves, kept exact by the merge,
@@ -84,6 +86,8 @@ struct Scratch {
   Buf viol, cand, wins;   // violating leaves, window candidates, windows
   Buf list_lane, list_v1, list_gen;  // merge work lists
   Buf list_pend;          // pending leaves of the thread- and lane-granular inserts
+  Buf point_stage;        // point path: 512-byte staging slot per key
+  Buf point_rec;          // point path: staged result per key
   Buf bits;               // per-level window bitsets (u32 words)
   Buf prefix;             // prefix sums of used bytes (u64, L+1)
   Buf E, cost, C;         // redistribution: elements, costs, cost prefix; C also holds
@@ -175,6 +179,11 @@ struct cpma {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   uint64_t graph_captures = 0, graph_launches = 0;
+  // untagged inserts of up to this many keys try the point path first (at
+  // most 4096; 0 = never); updates that took it, and those of them that the
+  // batch algorithm finished instead
+  uint64_t point_max = 4096;
+  uint64_t point_calls = 0, point_batch = 0;
 };
 
 namespace cpmaimpl {

@@ -422,6 +422,18 @@ struct MergeArgs {
   Bounds B;              // density bounds and tree height, for the leaves the
   unsigned H;            // thread-granular merge finalises itself
   uint32_t* viol;        // touched leaves over their own bound (count st->nviol)
+  uint8_t* pstage;       // point path: 512-byte staging slot per key (first key of a leaf)
+  struct PointRec* prec; // point path: the staged result per key (first key of a leaf)
+};
+
+// A touched leaf's result staged by the point path's plan pass: the new
+// head, used bytes and count, the rewritten byte range [lo, wend) held in
+// the staging slot, and the keys added and byte change.
+struct PointRec {
+  uint64_t head;
+  uint32_t leaf, nb, newc, lo, wend, added;
+  int32_t dbytes;
+  uint32_t pad;
 };
 
 // Append to a work list, one atomic per warp (all lanes must call).
@@ -608,6 +620,302 @@ __device__ __forceinline__ T seg_scan(unsigned seg, unsigned sl, T v) {
   return v;
 }
 
+// What the per-leaf body of the lane-granular insert does with a leaf:
+// kLaneBatch -- the batch merge (work-list bookkeeping, pending and fallback
+// leaves handed on); kLaneStage -- the point path's plan: the leaf is left
+// as it is, and a result that can go in place is written to the leaf's
+// staging slot instead (the rewritten 16-byte chunks at their leaf offsets)
+// with a PointRec, for k_point_commit.  kLaneStage returns kLeafInPlace,
+// kLeafSame (every key already present) or kLeafBatch (the leaf needs the
+// batch algorithm: a slice over SEG keys, an empty leaf or one over 512 used
+// bytes, a code over 4 bytes, a result over the leaf or over 512 bytes, or
+// one that violates the leaf's own density bound).
+constexpr int kLaneBatch = 0, kLaneStage = 1;
+constexpr uint32_t kLeafInPlace = 0, kLeafSame = 1, kLeafBatch = 2;
+
+// One leaf of the lane-granular insert, taken by the segment sg of SEG lanes
+// (lane sl in it, mask seg); wbase is the segment's shared scratch.  The
+// leaf's keys are u[tb, te); nbytes, dl and db accumulate the algorithmic
+// bytes, keys added and byte total change (lane 0 of the segment).
+template <int SEG, int MODE>
+__device__ __forceinline__ uint32_t lane_leaf(const MergeArgs& a, uint8_t* wbase, unsigned sg,
+                                              unsigned sl, unsigned seg, uint32_t t, uint32_t tb,
+                                              uint32_t te, uint32_t uold, uint32_t j, uint32_t m,
+                                              uint32_t fc0, uint32_t fc1, ull& nbytes, ull& dl,
+                                              ull& db) {
+  constexpr int NW = 512 / (4 * SEG);        // words per lane
+  constexpr uint32_t kLB = 4u * NW;          // bytes per lane
+  constexpr uint32_t KS = SEG;               // keys per slice
+  constexpr bool BATCH = MODE == kLaneBatch;
+  const unsigned lt_mask = (1u << sl) - 1u;
+  uint8_t* out = wbase;
+  uint64_t* kx = reinterpret_cast<uint64_t*>(wbase + kLaneOut);  // key
+  uint64_t* kp = kx + KS;                                         // predecessor value
+  uint64_t* ks = kp + KS;                                         // successor value
+  uint32_t* kr = reinterpret_cast<uint32_t*>(ks + KS);  // rank; bit 31 = present
+  uint32_t* kcs = kr + KS;                              // successor code start
+  uint32_t* kce = kcs + KS;                             // successor code end (excl.)
+  uint32_t* ktl = kce + KS;                             // owning lane
+  uint32_t* es = ktl + KS;
+  uint32_t* ee = es + KS;
+  uint32_t* en = ee + KS;
+  int32_t* shc = reinterpret_cast<int32_t*>(en + KS);
+  const uint32_t s = te - tb;
+  if (!BATCH && (s > KS || uold == 0 || uold > 512)) return kLeafBatch;
+  uint8_t* leafp = a.data + (size_t)j * a.LB;
+  // the old leaf, the slice and ~28 bytes of per-leaf metadata
+  if (BATCH) nbytes += uold + 8u * s + 28u;
+  // ---- bit-parallel summary of each lane's bytes ----
+  const uint32_t p0 = sl * kLB;
+  uint32_t w[NW];
+#pragma unroll
+  for (int q = 0; q < NW; q += 4) {
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (p0 + 4u * q < uold) v = *reinterpret_cast<const uint4*>(leafp + p0 + 4u * q);
+    w[q] = v.x; w[q + 1] = v.y; w[q + 2] = v.z; w[q + 3] = v.w;
+  }
+  // the slice's keys, loaded now so their latency overlaps the summary
+  uint64_t x = 0, xprev = 0;
+  if (sl < s) {
+    x = a.u[tb + sl];
+    if (sl > 0) xprev = a.u[tb + sl - 1];
+  }
+  const int b_lo = sl == 0 ? 8 : 0;
+  const int b_hi = (uold > p0) ? (int)min(kLB, uold - p0) : 0;
+  LaneCodesN<NW> lc;
+  lane_codes<false, NW>(w, b_lo, b_hi, lc);
+  bool bad = lc.bad;
+  uint32_t pv = __shfl_up_sync(seg, lc.tail, 1, SEG);
+  uint32_t ps = __shfl_up_sync(seg, lc.tail_sh, 1, SEG);
+  if (sl == 0) { pv = 0; ps = 0; }
+  uint32_t D = 0;
+  if (lc.term) {
+    if (ps / 7u + lc.first_len > 4u) bad = true;
+    D = lc.D - lc.first_own + pv + (lc.first_own << ps);
+  }
+  if (__any_sync(seg, bad)) {
+    if (BATCH && sl == 0) {
+      a.T_state[t] = kFallback;
+      a.list_v1[atomicAdd(&a.st->n_v1, 1ull)] = t;
+    }
+    return kLeafBatch;
+  }
+  const uint32_t c = __popc(lc.term);
+  const uint32_t B = seg_scan<SEG, uint32_t>(seg, sl, c) - c;                       // codes in earlier lanes
+  if (__shfl_sync(seg, B + c, SEG - 1, SEG) + 1u != m) {   // must match the stored count
+    if (sl == 0) atomicOr(&a.st->err, kErrState);
+    return kLeafBatch;
+  }
+  const uint64_t Dinc = seg_scan<SEG, uint64_t>(seg, sl, (uint64_t)D);
+  const uint64_t head = __shfl_sync(seg, (uint64_t)w[0] | ((uint64_t)w[1] << 32), 0, SEG);
+  const uint64_t V = head + (Dinc - D);                             // element before my codes
+  const uint64_t lastv = head + __shfl_sync(seg, Dinc, SEG - 1, SEG);  // the last element
+  // ---- keys: owning lane, or before the head / after the last element ----
+  const bool valid = sl < s && !(sl > 0 && xprev == x);
+  unsigned owners = 0;
+  for (uint32_t k = 0; k < s; k++) {
+    const uint64_t xk = __shfl_sync(seg, x, k, SEG);
+    const unsigned own = seg_ballot<SEG>(seg, sg, c > 0 && V < xk && xk <= V + D);
+    if (sl == k) ktl[k] = own ? (uint32_t)(__ffs(own) - 1) : 0xFFFFFFFFu;
+    owners |= own;
+  }
+  if (sl < s) {
+    kx[sl] = x;
+    if (x <= head) {            // before the head, or the head itself
+      kr[sl] = (x == head) ? 0x80000000u : 0u;
+      kp[sl] = 0; ks[sl] = head; kcs[sl] = 0; kce[sl] = 8;
+    } else if (x > lastv) {     // after the last element
+      kr[sl] = m;
+      kp[sl] = lastv; ks[sl] = 0; kcs[sl] = uold; kce[sl] = uold;
+    }
+  }
+  __syncwarp(seg);
+  // ---- each owning lane decodes its own codes (all owners at once) ----
+  // Walking its codes in order, the lane keeps the running value; a key
+  // takes the first code whose value reaches it: that code's element is
+  // its successor (rank 1 + codes before it), the value before is its
+  // predecessor, and the code's bytes are the ones an insert replaces.
+  if ((owners >> sl) & 1u) {
+    uint32_t kq = 0;
+    while (ktl[kq] != sl) kq++;  // this lane's keys are consecutive
+    uint32_t tm2 = lc.term, st = (sl == 0) ? 8u : 0u, rank = 1u + B;
+    uint64_t val = V;
+    bool firstc = true;
+    while (tm2 && kq < s && ktl[kq] == sl) {
+      const uint32_t tb8 = (uint32_t)__ffs(tm2) - 1u;
+      tm2 &= tm2 - 1u;
+      const uint32_t own = compact7(window32<NW>(lc.x, st)) & mask7(tb8 + 1u - st);
+      const uint32_t code = firstc ? pv + (own << ps) : own;
+      const uint32_t cs = kLB * sl + st - (firstc ? ps / 7u : 0u);
+      const uint64_t prev = val;
+      val += code;
+      while (kq < s && ktl[kq] == sl && kx[kq] <= val) {
+        kr[kq] = rank | (kx[kq] == val ? 0x80000000u : 0u);
+        kp[kq] = prev;
+        ks[kq] = val;
+        kcs[kq] = cs;
+        kce[kq] = kLB * sl + tb8 + 1u;
+        kq++;
+      }
+      rank++;
+      st = tb8 + 1u;
+      firstc = false;
+    }
+  }
+  __syncwarp(seg);
+  // ---- kept keys and their gaps ----
+  uint32_t r = 0;
+  bool keep = false;
+  if (sl < s) {
+    r = kr[sl];
+    keep = valid && !(r & 0x80000000u);
+  }
+  const unsigned kb = seg_ballot<SEG>(seg, sg, keep);
+  const uint32_t nn = __popc(kb);
+  uint64_t mx = 0, mp = 0, ms = 0;
+  uint32_t mcs = 0, mce = 0;
+  if (keep) { mx = kx[sl]; mp = kp[sl]; ms = ks[sl]; mcs = kcs[sl]; mce = kce[sl]; }
+  __syncwarp(seg);
+  if (keep) {
+    const uint32_t q = __popc(kb & lt_mask);
+    kx[q] = mx; kp[q] = mp; ks[q] = ms; kcs[q] = mcs; kce[q] = mce; kr[q] = r;
+  }
+  __syncwarp(seg);
+  if (nn == 0) {
+    if (BATCH) {
+      if (sl == 0) {
+        a.T_state[t] = kUnchanged;
+        a.T_newcnt[t] = m;
+        a.T_newbytes[t] = uold;
+      }
+      for (uint32_t cq = fc0 + sl; cq < fc1; cq += SEG) a.chunk_cnt[cq] = 0;
+      __syncwarp(seg);
+    }
+    return kLeafSame;
+  }
+  bool lead = false;
+  if (sl < nn) lead = sl == 0 || kr[sl - 1] != kr[sl];
+  const unsigned lb = seg_ballot<SEG>(seg, sg, lead);
+  const uint32_t E = __popc(lb);
+  uint32_t e_os = 0, e_oe = 0, e_nl = 0, gend = 0, g0 = 0;
+  if (lead) {
+    const unsigned after = lb & ~((2u << sl) - 1u);
+    gend = after ? (uint32_t)(__ffs(after) - 1) : nn;
+    g0 = kr[sl];
+    e_os = kcs[sl];
+    e_oe = kce[sl];
+    uint64_t prev = kx[sl];
+    uint32_t len = (g0 == 0) ? 8u : leb_len(kx[sl] - kp[sl]);
+    for (uint32_t q = sl + 1; q < gend; q++) { len += leb_len(kx[q] - prev); prev = kx[q]; }
+    if (g0 < m) len += leb_len(ks[sl] - prev);
+    e_nl = len;
+  }
+  const uint32_t eidx = __popc(lb & lt_mask);
+  const int32_t delta = lead ? (int32_t)e_nl - (int32_t)(e_oe - e_os) : 0;
+  const int32_t dinc = (int32_t)seg_scan<SEG, uint32_t>(seg, sl, (uint32_t)delta);
+  const int32_t total = (int32_t)__shfl_sync(seg, (uint32_t)dinc, SEG - 1, SEG);
+  if (lead) {
+    es[eidx] = e_os;
+    ee[eidx] = e_oe;
+    en[eidx] = (uint32_t)((int32_t)e_os + dinc - delta);
+    shc[eidx] = dinc;
+  }
+  const uint32_t nb = (uint32_t)((int32_t)uold + total);
+  const uint32_t newc = m + nn;
+  const uint64_t newhead = (kr[0] == 0) ? kx[0] : head;
+  __syncwarp(seg);
+  if (nb > a.LB) {
+    if (BATCH) {
+      if (sl == 0) {
+        a.T_state[t] = kPending;
+        a.T_newcnt[t] = newc;
+        a.T_newbytes[t] = nb;
+        a.list_pend[atomicAdd(&a.st->n_pendl, 1ull)] = t;
+      }
+      for (uint32_t cq = fc0 + sl; cq < fc1; cq += SEG) a.chunk_cnt[cq] = (cq == fc0) ? newc : 0u;
+      if (keep) credit(a, tb + sl);
+      __syncwarp(seg);
+    }
+    return kLeafBatch;
+  }
+  if (nb > 512) {  // fits the leaf but not this kernel's 512-byte buffer
+    if (BATCH && sl == 0) {
+      a.T_state[t] = kFallback;
+      a.list_v1[atomicAdd(&a.st->n_v1, 1ull)] = t;
+    }
+    __syncwarp(seg);
+    return kLeafBatch;
+  }
+  // outside the batch merge a leaf is only rewritten when it stays within its
+  // own bound (the batch merge writes it either way and starts a walk)
+  const bool viol = node_violates(a.B, a.H, 0, 1, nb);
+  if (!BATCH && viol) return kLeafBatch;
+  const uint32_t wend = (max(uold, nb) + 15u) & ~15u;
+  // lanes whose bytes lie wholly before the first edit keep them: they
+  // neither rebuild nor rewrite them
+  const bool touched = p0 + kLB > es[0];
+  if (touched)
+#pragma unroll
+    for (uint32_t q = 0; q < kLB; q += 16)
+      if (p0 + q < wend) *reinterpret_cast<uint4*>(out + p0 + q) = make_uint4(0u, 0u, 0u, 0u);
+  __syncwarp(seg);
+  if (touched) splice_copy_words<NW>(w, p0, uold, out, E, es, ee, shc);
+  __syncwarp(seg);
+  if (lead) {
+    uint8_t* o = out + en[eidx];
+    uint64_t prev = kx[sl];
+    if (g0 == 0) {
+#pragma unroll
+      for (int b = 0; b < 8; b++) o[b] = (uint8_t)(prev >> (8 * b));
+      o += 8;
+    } else {
+      o += leb_put(o, prev - kp[sl]);
+    }
+    for (uint32_t q = sl + 1; q < gend; q++) { o += leb_put(o, kx[q] - prev); prev = kx[q]; }
+    if (g0 < m) leb_put(o, ks[sl] - prev);
+  }
+  __syncwarp(seg);
+  uint8_t* dst = BATCH ? leafp : a.pstage + (size_t)tb * 512;
+  if (touched)
+#pragma unroll
+    for (uint32_t q = 0; q < kLB; q += 16)
+      if (p0 + q < wend)
+        *reinterpret_cast<uint4*>(dst + p0 + q) = *reinterpret_cast<const uint4*>(out + p0 + q);
+  if (!BATCH) {
+    if (sl == 0) {
+      PointRec R;
+      R.head = newhead;
+      R.leaf = j;
+      R.nb = nb;
+      R.newc = newc;
+      R.lo = es[0] & ~15u;
+      R.wend = wend;
+      R.added = nn;
+      R.dbytes = total;
+      a.prec[tb] = R;
+    }
+    __syncwarp(seg);
+    return kLeafInPlace;
+  }
+  if (sl == 0) nbytes += wend - min(wend, es[0] & ~15u);
+  if (keep) credit(a, tb + sl);
+  if (sl == 0) {
+    a.used[j] = nb;
+    a.cnt[j] = newc;
+    a.heads[j] = newhead;
+    // the finalize pass's work for this leaf, done here
+    dl += newc - m;
+    db += (ull)nb - (ull)uold;
+    a.T_newcnt[t] = newc;
+    a.T_newbytes[t] = nb;
+    if (viol) a.viol[atomicAdd(&a.st->nviol, 1ull)] = j;
+    a.T_state[t] = kDone;
+  }
+  for (uint32_t cq = fc0 + sl; cq < fc1; cq += SEG) a.chunk_cnt[cq] = 0;
+  __syncwarp(seg);
+  return kLeafInPlace;
+}
+
 // Insert of a small slice (at most SEG keys) into a leaf of at most 512 used
 // bytes, without decoding the whole leaf into an element array.  A segment
 // of SEG lanes takes one leaf (32 / SEG leaves per warp step), each lane
@@ -624,31 +932,15 @@ __device__ __forceinline__ T seg_scan(unsigned seg, unsigned sl, T v) {
 // shuffles and ballots) between those loads.
 template <int SEG>
 __global__ void __launch_bounds__(kT, SEG == 32 ? 4 : 3) k_insert_lane(MergeArgs a) {
-  constexpr int NW = 512 / (4 * SEG);        // words per lane
-  constexpr uint32_t kLB = 4u * NW;          // bytes per lane
   constexpr int SPW = 32 / SEG;              // segments (leaves) per warp step
-  constexpr uint32_t KS = SEG;               // keys per slice
   constexpr unsigned SEGBITS = SEG == 32 ? 0xFFFFFFFFu : ((1u << SEG) - 1u);
   extern __shared__ __align__(16) uint8_t smem[];
   if (a.st->err) return;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const unsigned sg = lane / SEG, sl = lane % SEG;
   const unsigned seg = SEGBITS << (sg * SEG);
-  const unsigned lt_mask = (1u << sl) - 1u;
   const unsigned wpb = blockDim.x >> 5;
   uint8_t* wbase = smem + (size_t)warp * lane_warp_bytes(SEG) + (size_t)sg * lane_seg_bytes(SEG);
-  uint8_t* out = wbase;
-  uint64_t* kx = reinterpret_cast<uint64_t*>(wbase + kLaneOut);  // key
-  uint64_t* kp = kx + KS;                                         // predecessor value
-  uint64_t* ks = kp + KS;                                         // successor value
-  uint32_t* kr = reinterpret_cast<uint32_t*>(ks + KS);  // rank; bit 31 = present
-  uint32_t* kcs = kr + KS;                              // successor code start
-  uint32_t* kce = kcs + KS;                             // successor code end (excl.)
-  uint32_t* ktl = kce + KS;                             // owning lane
-  uint32_t* es = ktl + KS;
-  uint32_t* ee = es + KS;
-  uint32_t* en = ee + KS;
-  int32_t* shc = reinterpret_cast<int32_t*>(en + KS);
   const uint64_t nL = a.st->n_lane;
   ull nbytes = 0;  // algorithmic bytes (lane 0 of each segment)
   ull dl = 0, db = 0;  // keys added, byte total change (lane 0 of each segment)
@@ -666,246 +958,21 @@ __global__ void __launch_bounds__(kT, SEG == 32 ? 4 : 3) k_insert_lane(MergeArgs
     }
     unsigned todo = __ballot_sync(FULL, have);
     while (todo) {
-    // segment sg takes the sg-th remaining leaf of this step
-    unsigned tm = todo;
-    for (unsigned q = 0; q < sg; q++) tm &= tm - 1u;
-    const bool mine = tm != 0;
-    const unsigned src = mine ? (unsigned)(__ffs(tm) - 1) : 0u;
-    const uint32_t t = __shfl_sync(FULL, ti, src);
-    const uint32_t tb = __shfl_sync(FULL, i_tb, src), te = __shfl_sync(FULL, i_te, src);
-    const uint32_t uold = __shfl_sync(FULL, i_uold, src), j = __shfl_sync(FULL, i_j, src);
-    const uint32_t m = __shfl_sync(FULL, i_m, src);
-    const uint32_t fc0 = __shfl_sync(FULL, i_fc0, src), fc1 = __shfl_sync(FULL, i_fc1, src);
+      // segment sg takes the sg-th remaining leaf of this step
+      unsigned tm = todo;
+      for (unsigned q = 0; q < sg; q++) tm &= tm - 1u;
+      const bool mine = tm != 0;
+      const unsigned src = mine ? (unsigned)(__ffs(tm) - 1) : 0u;
+      const uint32_t t = __shfl_sync(FULL, ti, src);
+      const uint32_t tb = __shfl_sync(FULL, i_tb, src), te = __shfl_sync(FULL, i_te, src);
+      const uint32_t uold = __shfl_sync(FULL, i_uold, src), j = __shfl_sync(FULL, i_j, src);
+      const uint32_t m = __shfl_sync(FULL, i_m, src);
+      const uint32_t fc0 = __shfl_sync(FULL, i_fc0, src), fc1 = __shfl_sync(FULL, i_fc1, src);
 #pragma unroll
-    for (int q = 0; q < SPW; q++) todo &= todo - 1u;
-    if (!mine) continue;
-    const uint32_t s = te - tb;
-    uint8_t* leafp = a.data + (size_t)j * a.LB;
-    // the old leaf, the slice and ~28 bytes of per-leaf metadata
-    nbytes += uold + 8u * s + 28u;
-    // ---- bit-parallel summary of each lane's bytes ----
-    const uint32_t p0 = sl * kLB;
-    uint32_t w[NW];
-#pragma unroll
-    for (int q = 0; q < NW; q += 4) {
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (p0 + 4u * q < uold) v = *reinterpret_cast<const uint4*>(leafp + p0 + 4u * q);
-      w[q] = v.x; w[q + 1] = v.y; w[q + 2] = v.z; w[q + 3] = v.w;
-    }
-    // the slice's keys, loaded now so their latency overlaps the summary
-    uint64_t x = 0, xprev = 0;
-    if (sl < s) {
-      x = a.u[tb + sl];
-      if (sl > 0) xprev = a.u[tb + sl - 1];
-    }
-    const int b_lo = sl == 0 ? 8 : 0;
-    const int b_hi = (uold > p0) ? (int)min(kLB, uold - p0) : 0;
-    LaneCodesN<NW> lc;
-    lane_codes<false, NW>(w, b_lo, b_hi, lc);
-    bool bad = lc.bad;
-    uint32_t pv = __shfl_up_sync(seg, lc.tail, 1, SEG);
-    uint32_t ps = __shfl_up_sync(seg, lc.tail_sh, 1, SEG);
-    if (sl == 0) { pv = 0; ps = 0; }
-    uint32_t D = 0;
-    if (lc.term) {
-      if (ps / 7u + lc.first_len > 4u) bad = true;
-      D = lc.D - lc.first_own + pv + (lc.first_own << ps);
-    }
-    if (__any_sync(seg, bad)) {
-      if (sl == 0) {
-        a.T_state[t] = kFallback;
-        a.list_v1[atomicAdd(&a.st->n_v1, 1ull)] = t;
-      }
-      continue;
-    }
-    const uint32_t c = __popc(lc.term);
-    const uint32_t B = seg_scan<SEG, uint32_t>(seg, sl, c) - c;                       // codes in earlier lanes
-    if (__shfl_sync(seg, B + c, SEG - 1, SEG) + 1u != m) {   // must match the stored count
-      if (sl == 0) atomicOr(&a.st->err, kErrState);
-      continue;
-    }
-    const uint64_t Dinc = seg_scan<SEG, uint64_t>(seg, sl, (uint64_t)D);
-    const uint64_t head = __shfl_sync(seg, (uint64_t)w[0] | ((uint64_t)w[1] << 32), 0, SEG);
-    const uint64_t V = head + (Dinc - D);                             // element before my codes
-    const uint64_t lastv = head + __shfl_sync(seg, Dinc, SEG - 1, SEG);  // the last element
-    // ---- keys: owning lane, or before the head / after the last element ----
-    const bool valid = sl < s && !(sl > 0 && xprev == x);
-    unsigned owners = 0;
-    for (uint32_t k = 0; k < s; k++) {
-      const uint64_t xk = __shfl_sync(seg, x, k, SEG);
-      const unsigned own = seg_ballot<SEG>(seg, sg, c > 0 && V < xk && xk <= V + D);
-      if (sl == k) ktl[k] = own ? (uint32_t)(__ffs(own) - 1) : 0xFFFFFFFFu;
-      owners |= own;
-    }
-    if (sl < s) {
-      kx[sl] = x;
-      if (x <= head) {            // before the head, or the head itself
-        kr[sl] = (x == head) ? 0x80000000u : 0u;
-        kp[sl] = 0; ks[sl] = head; kcs[sl] = 0; kce[sl] = 8;
-      } else if (x > lastv) {     // after the last element
-        kr[sl] = m;
-        kp[sl] = lastv; ks[sl] = 0; kcs[sl] = uold; kce[sl] = uold;
-      }
-    }
-    __syncwarp(seg);
-    // ---- each owning lane decodes its own codes (all owners at once) ----
-    // Walking its codes in order, the lane keeps the running value; a key
-    // takes the first code whose value reaches it: that code's element is
-    // its successor (rank 1 + codes before it), the value before is its
-    // predecessor, and the code's bytes are the ones an insert replaces.
-    if ((owners >> sl) & 1u) {
-      uint32_t kq = 0;
-      while (ktl[kq] != sl) kq++;  // this lane's keys are consecutive
-      uint32_t tm2 = lc.term, st = (sl == 0) ? 8u : 0u, rank = 1u + B;
-      uint64_t val = V;
-      bool firstc = true;
-      while (tm2 && kq < s && ktl[kq] == sl) {
-        const uint32_t tb8 = (uint32_t)__ffs(tm2) - 1u;
-        tm2 &= tm2 - 1u;
-        const uint32_t own = compact7(window32<NW>(lc.x, st)) & mask7(tb8 + 1u - st);
-        const uint32_t code = firstc ? pv + (own << ps) : own;
-        const uint32_t cs = kLB * sl + st - (firstc ? ps / 7u : 0u);
-        const uint64_t prev = val;
-        val += code;
-        while (kq < s && ktl[kq] == sl && kx[kq] <= val) {
-          kr[kq] = rank | (kx[kq] == val ? 0x80000000u : 0u);
-          kp[kq] = prev;
-          ks[kq] = val;
-          kcs[kq] = cs;
-          kce[kq] = kLB * sl + tb8 + 1u;
-          kq++;
-        }
-        rank++;
-        st = tb8 + 1u;
-        firstc = false;
-      }
-    }
-    __syncwarp(seg);
-    // ---- kept keys and their gaps ----
-    uint32_t r = 0;
-    bool keep = false;
-    if (sl < s) {
-      r = kr[sl];
-      keep = valid && !(r & 0x80000000u);
-    }
-    const unsigned kb = seg_ballot<SEG>(seg, sg, keep);
-    const uint32_t nn = __popc(kb);
-    uint64_t mx = 0, mp = 0, ms = 0;
-    uint32_t mcs = 0, mce = 0;
-    if (keep) { mx = kx[sl]; mp = kp[sl]; ms = ks[sl]; mcs = kcs[sl]; mce = kce[sl]; }
-    __syncwarp(seg);
-    if (keep) {
-      const uint32_t q = __popc(kb & lt_mask);
-      kx[q] = mx; kp[q] = mp; ks[q] = ms; kcs[q] = mcs; kce[q] = mce; kr[q] = r;
-    }
-    __syncwarp(seg);
-    if (nn == 0) {
-      if (sl == 0) {
-        a.T_state[t] = kUnchanged;
-        a.T_newcnt[t] = m;
-        a.T_newbytes[t] = uold;
-      }
-      for (uint32_t cq = fc0 + sl; cq < fc1; cq += SEG) a.chunk_cnt[cq] = 0;
-      __syncwarp(seg);
-      continue;
-    }
-    bool lead = false;
-    if (sl < nn) lead = sl == 0 || kr[sl - 1] != kr[sl];
-    const unsigned lb = seg_ballot<SEG>(seg, sg, lead);
-    const uint32_t E = __popc(lb);
-    uint32_t e_os = 0, e_oe = 0, e_nl = 0, gend = 0, g0 = 0;
-    if (lead) {
-      const unsigned after = lb & ~((2u << sl) - 1u);
-      gend = after ? (uint32_t)(__ffs(after) - 1) : nn;
-      g0 = kr[sl];
-      e_os = kcs[sl];
-      e_oe = kce[sl];
-      uint64_t prev = kx[sl];
-      uint32_t len = (g0 == 0) ? 8u : leb_len(kx[sl] - kp[sl]);
-      for (uint32_t q = sl + 1; q < gend; q++) { len += leb_len(kx[q] - prev); prev = kx[q]; }
-      if (g0 < m) len += leb_len(ks[sl] - prev);
-      e_nl = len;
-    }
-    const uint32_t eidx = __popc(lb & lt_mask);
-    const int32_t delta = lead ? (int32_t)e_nl - (int32_t)(e_oe - e_os) : 0;
-    const int32_t dinc = (int32_t)seg_scan<SEG, uint32_t>(seg, sl, (uint32_t)delta);
-    const int32_t total = (int32_t)__shfl_sync(seg, (uint32_t)dinc, SEG - 1, SEG);
-    if (lead) {
-      es[eidx] = e_os;
-      ee[eidx] = e_oe;
-      en[eidx] = (uint32_t)((int32_t)e_os + dinc - delta);
-      shc[eidx] = dinc;
-    }
-    const uint32_t nb = (uint32_t)((int32_t)uold + total);
-    const uint32_t newc = m + nn;
-    const uint64_t newhead = (kr[0] == 0) ? kx[0] : head;
-    __syncwarp(seg);
-    if (nb > a.LB) {
-      if (sl == 0) {
-        a.T_state[t] = kPending;
-        a.T_newcnt[t] = newc;
-        a.T_newbytes[t] = nb;
-        a.list_pend[atomicAdd(&a.st->n_pendl, 1ull)] = t;
-      }
-      for (uint32_t cq = fc0 + sl; cq < fc1; cq += SEG) a.chunk_cnt[cq] = (cq == fc0) ? newc : 0u;
-      if (keep) credit(a, tb + sl);
-      __syncwarp(seg);
-      continue;
-    }
-    if (nb > 512) {  // fits the leaf but not this kernel's 512-byte buffer
-      if (sl == 0) {
-        a.T_state[t] = kFallback;
-        a.list_v1[atomicAdd(&a.st->n_v1, 1ull)] = t;
-      }
-      __syncwarp(seg);
-      continue;
-    }
-    const uint32_t wend = (max(uold, nb) + 15u) & ~15u;
-    // lanes whose bytes lie wholly before the first edit keep them: they
-    // neither rebuild nor rewrite them
-    const bool touched = p0 + kLB > es[0];
-    if (touched)
-#pragma unroll
-      for (uint32_t q = 0; q < kLB; q += 16)
-        if (p0 + q < wend) *reinterpret_cast<uint4*>(out + p0 + q) = make_uint4(0u, 0u, 0u, 0u);
-    __syncwarp(seg);
-    if (touched) splice_copy_words<NW>(w, p0, uold, out, E, es, ee, shc);
-    __syncwarp(seg);
-    if (lead) {
-      uint8_t* o = out + en[eidx];
-      uint64_t prev = kx[sl];
-      if (g0 == 0) {
-#pragma unroll
-        for (int b = 0; b < 8; b++) o[b] = (uint8_t)(prev >> (8 * b));
-        o += 8;
-      } else {
-        o += leb_put(o, prev - kp[sl]);
-      }
-      for (uint32_t q = sl + 1; q < gend; q++) { o += leb_put(o, kx[q] - prev); prev = kx[q]; }
-      if (g0 < m) leb_put(o, ks[sl] - prev);
-    }
-    __syncwarp(seg);
-    if (touched)
-#pragma unroll
-      for (uint32_t q = 0; q < kLB; q += 16)
-        if (p0 + q < wend)
-          *reinterpret_cast<uint4*>(leafp + p0 + q) = *reinterpret_cast<const uint4*>(out + p0 + q);
-    if (sl == 0) nbytes += wend - min(wend, es[0] & ~15u);
-    if (keep) credit(a, tb + sl);
-    if (sl == 0) {
-      a.used[j] = nb;
-      a.cnt[j] = newc;
-      a.heads[j] = newhead;
-      a.T_newcnt[t] = newc;
-      a.T_newbytes[t] = nb;
-      // the finalize pass's work for this leaf, done here
-      dl += newc - m;
-      db += (ull)nb - (ull)uold;
-      if (node_violates(a.B, a.H, 0, 1, nb)) a.viol[atomicAdd(&a.st->nviol, 1ull)] = j;
-      a.T_state[t] = kDone;
-    }
-    for (uint32_t cq = fc0 + sl; cq < fc1; cq += SEG) a.chunk_cnt[cq] = 0;
-    __syncwarp(seg);
+      for (int q = 0; q < SPW; q++) todo &= todo - 1u;
+      if (!mine) continue;
+      lane_leaf<SEG, kLaneBatch>(a, wbase, sg, sl, seg, t, tb, te, uold, j, m, fc0, fc1, nbytes,
+                                 dl, db);
     }
   }
   nbytes = warp_sum(sl == 0 ? nbytes : 0ull);
@@ -915,6 +982,208 @@ __global__ void __launch_bounds__(kT, SEG == 32 ? 4 : 3) k_insert_lane(MergeArgs
     if (a.prof && nbytes) atomicAdd(a.prof, nbytes);
     if (dl) atomicAdd(&a.st->delta, dl);
     if (db) atomicAdd(&a.st->bytes_total, db);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Point path (Sec. 4: a batch much smaller than the set is applied as point
+// updates instead of by the batch algorithm).  An untagged insert of at most
+// kPointMax keys is sorted and routed in one kernel (k_point_sort_route); a
+// plan pass then takes each touched leaf with a warp and decides whether the
+// leaf's keys go in place: the lane-granular insert's conditions (at most 32
+// keys, a non-empty leaf of at most 512 used bytes, codes of at most four
+// bytes, a result of at most 512 bytes) and, in addition, that the leaf stays
+// within its own density bound.  When every touched leaf does, an apply pass
+// rewrites them (the same bytes the batch merge writes); otherwise nothing is
+// written and the update runs the batch algorithm.  With no pending leaf and
+// no leaf over its bound the batch algorithm's counting phase starts no walk,
+// so both give the same structure.
+constexpr uint32_t kPointMax = 4096;    // keys (the whole batch in one block's shared memory)
+constexpr int kPRT = 256;
+
+// A warp per key: its stable rank (the lanes count over the batch, held in
+// shared memory by every block, the keys below it and the equal keys before
+// it) -- or, for a batch given sorted, rank = index (the plan pass checks the
+// order) -- and its leaf by route_leaf's rule (the last leaf whose head is <= x,
+// else leaf 0; 2^64-1 to the leaf heads[L] names), searched 32-ary in the
+// head array: 31 probes per round trip, loaded together, narrow the range
+// 32-fold, so 10^6 leaves take four.  Writes the key to u[rank] and its
+// leaf to leaf_of[rank].  Clears the status words the point path uses.
+__global__ void __launch_bounds__(kPRT) k_point_sort_route(const uint64_t* __restrict__ in,
+                                                          uint32_t k, int sorted,
+                                                          uint64_t* __restrict__ u,
+                                                          uint32_t* __restrict__ leaf_of,
+                                                          const uint64_t* __restrict__ heads,
+                                                          uint64_t L, Status* st) {
+  extern __shared__ __align__(16) uint64_t s_keys[];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->err = 0;
+    st->point_fb = 0;
+    st->point_done = 0;
+    st->delta = 0;
+  }
+  for (uint32_t i = threadIdx.x; i < k; i += kPRT) s_keys[i] = in[i];
+  __syncthreads();
+  const unsigned lane = lane_id();
+  const uint32_t i = blockIdx.x * (kPRT / 32) + (threadIdx.x >> 5);
+  if (i >= k) return;
+  const uint64_t x = s_keys[i];
+  uint32_t r = i;
+  if (!sorted) {
+    uint32_t c = 0;
+    for (uint32_t j = lane; j < k; j += 32) {
+      const uint64_t y = s_keys[j];
+      c += (y < x || (y == x && j < i)) ? 1u : 0u;
+    }
+    r = warp_sum(c);
+  }
+  uint64_t a = 0;  // heads before a are <= x; from b on they are > x
+  if (x == KEY_MAX) {
+    a = __ldg(heads + L) + 1;
+  } else {
+    uint64_t b = L;
+    while (b - a > 32) {
+      const uint64_t w = b - a;
+      const uint64_t p = a + (uint64_t)(lane + 1) * w / 32;  // lanes 0..30
+      const unsigned le = __ballot_sync(FULL, lane < 31 && __ldg(heads + p) <= x);
+      const uint32_t c = (uint32_t)__popc(le);  // the probes <= x are a prefix
+      const uint64_t na = c ? a + (uint64_t)c * w / 32 + 1 : a;
+      const uint64_t nb = c < 31 ? a + (uint64_t)(c + 1) * w / 32 : b;
+      a = na;
+      b = nb;
+    }
+    a += (uint32_t)__popc(__ballot_sync(FULL, a + lane < b && __ldg(heads + a + lane) <= x));
+  }
+  if (lane == 0) {
+    u[r] = x;
+    leaf_of[r] = (uint32_t)(a ? a - 1 : 0);
+  }
+}
+
+// Commit the staged result of the leaf whose first key is i: the rewritten
+// bytes, used bytes, count and head (a warp; lane 0 adds to dl and db).
+__device__ __forceinline__ void point_commit(const MergeArgs& a, uint32_t i, ull& dl, ull& db) {
+  const PointRec R = a.prec[i];
+  uint8_t* leafp = a.data + (size_t)R.leaf * a.LB;
+  const uint8_t* src = a.pstage + (size_t)i * 512;
+  const uint32_t q = R.lo + 16u * lane_id();
+  if (q < R.wend)
+    *reinterpret_cast<uint4*>(leafp + q) = *reinterpret_cast<const uint4*>(src + q);
+  if (lane_id() == 0) {
+    a.used[R.leaf] = R.nb;
+    a.cnt[R.leaf] = R.newc;
+    a.heads[R.leaf] = R.head;
+    dl += R.added;
+    db += (ull)(long long)R.dbytes;
+  }
+}
+
+// Is sorted key i the first of its leaf, and which leaf ([tb, te) its keys;
+// te = tb when more than 32 of the keys share the leaf)?  A warp.
+__device__ __forceinline__ bool point_first(const uint32_t* __restrict__ leaf_of, uint32_t k,
+                                            uint32_t i, uint32_t& j, uint32_t& te) {
+  j = leaf_of[i];
+  if (i > 0 && leaf_of[i - 1] == j) return false;
+  // the leaf's keys end at the first of the next 32 in another leaf
+  const uint32_t q = i + 1 + lane_id();
+  const unsigned other = __ballot_sync(FULL, q >= k || leaf_of[q] != j);
+  te = other ? i + (uint32_t)__ffs(other) : i;
+  return true;
+}
+
+// The point path's plan pass, a warp per sorted key: the order of the keys
+// is checked, and the warp of the first key of each leaf stages the leaf's
+// result (kLaneStage) or counts the leaf in st->point_fb.  With COMMIT (few
+// keys) the block that finishes last -- every block's stagings and counts
+// are then visible -- commits every staged leaf itself when there is no
+// error and no leaf for the batch algorithm, and writes the keys added to
+// d_delta.
+template <bool COMMIT>
+__global__ void __launch_bounds__(kT, 4) k_point_plan(MergeArgs a,
+                                                      const uint32_t* __restrict__ leaf_of,
+                                                      uint32_t k, uint64_t* d_delta) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ bool s_last;
+  __shared__ ull s_dl[kT / 32], s_db[kT / 32];
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const unsigned wpb = blockDim.x >> 5;
+  uint8_t* wbase = smem + (size_t)warp * lane_warp_bytes(kLaneSeg);
+  ull nbytes = 0, dl = 0, db = 0;
+  ull nfb = 0;
+  for (uint32_t i = blockIdx.x * wpb + warp; i < k; i += gridDim.x * wpb) {
+    if (lane == 0 && i > 0 && a.u[i - 1] > a.u[i]) atomicOr(&a.st->err, kErrUnsorted);
+    uint32_t j, te;
+    if (!point_first(leaf_of, k, i, j, te)) continue;
+    // the slice must be in order before the leaf is planned
+    const bool down = lane + 1 < te - i && a.u[i + lane] > a.u[i + lane + 1];
+    if (te == i || __any_sync(FULL, down)) {
+      nfb++;
+      continue;
+    }
+    const uint32_t r = lane_leaf<kLaneSeg, kLaneStage>(a, wbase, 0u, lane, FULL, 0u, i, te,
+                                                       a.used[j], j, a.cnt[j], 0u, 0u, nbytes,
+                                                       dl, db);
+    nfb += r == kLeafBatch ? 1u : 0u;
+    if (lane == 0 && r == kLeafSame) a.prec[i].leaf = 0xFFFFFFFFu;  // nothing to commit
+  }
+  if (lane == 0 && nfb) atomicAdd(&a.st->point_fb, nfb);
+  if (!COMMIT) return;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&a.st->point_done, 1ull) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const volatile Status* vs = a.st;
+  if (vs->err || vs->point_fb) return;
+  dl = db = 0;
+  for (uint32_t i = warp; i < k; i += wpb) {
+    uint32_t j, te;
+    if (point_first(leaf_of, k, i, j, te) && a.prec[i].leaf != 0xFFFFFFFFu)
+      point_commit(a, i, dl, db);
+  }
+  if (lane == 0) { s_dl[warp] = dl; s_db[warp] = db; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ull tdl = 0, tdb = 0;
+    for (unsigned w = 0; w < wpb; w++) { tdl += s_dl[w]; tdb += s_db[w]; }
+    a.st->delta = tdl;
+    if (tdb) atomicAdd(&a.st->bytes_total, tdb);
+    if (d_delta) *d_delta = tdl;
+  }
+}
+
+// The point path's commit pass for larger batches: when there is no error
+// and no leaf for the batch algorithm, a warp per sorted key commits the
+// leaf the key is the first of; the block that finishes last writes the
+// keys added to d_delta.
+__global__ void __launch_bounds__(kT) k_point_commit(MergeArgs a,
+                                                     const uint32_t* __restrict__ leaf_of,
+                                                     uint32_t k, uint64_t* d_delta) {
+  __shared__ bool s_last;
+  if (a.st->err || a.st->point_fb) return;
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const unsigned wpb = blockDim.x >> 5;
+  ull dl = 0, db = 0;
+  for (uint32_t i = blockIdx.x * wpb + warp; i < k; i += gridDim.x * wpb) {
+    uint32_t j, te;
+    if (point_first(leaf_of, k, i, j, te) && a.prec[i].leaf != 0xFFFFFFFFu)
+      point_commit(a, i, dl, db);
+  }
+  dl = warp_sum(dl);
+  db = warp_sum(db);
+  if (lane == 0) {
+    if (dl) atomicAdd(&a.st->delta, dl);
+    if (db) atomicAdd(&a.st->bytes_total, db);
+  }
+  if (!d_delta) return;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&a.st->point_done, 1ull) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    *d_delta = *reinterpret_cast<const volatile ull*>(&a.st->delta);
   }
 }
 
@@ -2809,6 +3078,82 @@ int run_front_graph(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int
   return CPMA_OK;
 }
 
+// May an update take the point path?  Untagged inserts of 1 .. point_max
+// keys into a non-empty set of byte-code leaves of at most 512 bytes (the
+// lane-granular insert's buffer), unless a test of the bounded waits is set
+// up (those waits are in the batch algorithm's sort and routing).
+bool point_ok(const cpma* h, uint64_t k, int is_delete, const uint32_t* tags) {
+  return !is_delete && !tags && k >= 1 && k <= std::min<uint64_t>(h->point_max, kPointMax) &&
+         h->cfg.codec == 0 && h->cfg.leaf_bytes <= 512 && h->n > 0 && h->L > 0 &&
+         h->sort_poll_limit == 0 && h->sort_silent_tile < 0;
+}
+
+// Scratch of the point path for batches of up to k keys: the sort buffer,
+// one leaf word, one 512-byte staging slot and one staged record per key.
+int point_scratch(cpma* h, uint64_t k, cudaStream_t st) {
+  k = std::min<uint64_t>(std::max<uint64_t>(k, 2), kPointMax);
+  CPMA_TRY(ensure(h, h->s.keysA, k * 8, st));
+  CPMA_TRY(ensure(h, h->s.T_leaf, (k + 2) * 4, st));
+  CPMA_TRY(ensure(h, h->s.point_stage, k * 512, st));
+  return ensure(h, h->s.point_rec, k * sizeof(PointRec), st);
+}
+
+// The point path: sort and route, stage a warp per touched leaf, commit when
+// no leaf needs the batch algorithm (in the staging kernel's last block for
+// up to kPointFew keys, else in a commit kernel), then read the status.  On
+// return *fb tells whether some leaf needs the batch algorithm (nothing has
+// been written then).  point_scratch sized the buffers it uses.
+constexpr uint64_t kPointFew = 32;
+int run_point(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, uint64_t* d_delta,
+              cudaStream_t st, bool* fb) {
+  Status* ds = h->d_status;
+  Scratch& s = h->s;
+  uint64_t* u = P<uint64_t>(s.keysA);
+  uint32_t* leaf_of = P<uint32_t>(s.T_leaf);
+  const unsigned grid = (unsigned)((k + kPRT / 32 - 1) / (kPRT / 32));  // a warp per key
+  prof_begin(h, PH_ROUTE, st);
+  prof_add_bytes(h, PH_ROUTE, 20ull * k);
+  k_point_sort_route<<<grid, kPRT, k * 8, st>>>(d_keys, (uint32_t)k, sorted, u, leaf_of, h->heads,
+                                                h->L, ds);
+  prof_end(h, st);
+  MergeArgs ma;
+  memset(&ma, 0, sizeof(ma));
+  ma.u = u;
+  ma.data = h->data;
+  ma.used = h->used;
+  ma.cnt = h->cnt;
+  ma.heads = h->heads;
+  ma.LB = h->cfg.leaf_bytes;
+  ma.st = ds;
+  ma.small = 1;
+  ma.B = bounds_of(h);
+  ma.H = ceil_log2(h->L);
+  ma.pstage = P<uint8_t>(s.point_stage);
+  ma.prec = P<PointRec>(s.point_rec);
+  const size_t smem = lane_warp_bytes(kLaneSeg) * (kT / 32);
+  prof_begin(h, PH_MERGE_LANE, st);
+  if (k <= kPointFew) {
+    k_point_plan<true><<<grid, kT, smem, st>>>(ma, leaf_of, (uint32_t)k, d_delta);
+    h->launches += 2;
+  } else {
+    k_point_plan<false><<<grid, kT, smem, st>>>(ma, leaf_of, (uint32_t)k, nullptr);
+    k_point_commit<<<grid, kT, 0, st>>>(ma, leaf_of, (uint32_t)k, d_delta);
+    h->launches += 3;
+  }
+  prof_end(h, st);
+  CPMA_CUDA(cudaGetLastError());
+  CPMA_TRY(sync_status(h, st));
+  const Status& hs = *h->h_status;
+  if (hs.err & kErrUnsorted) return CPMA_EINVAL;
+  if (hs.err) return CPMA_EINTERNAL;
+  *fb = hs.point_fb != 0;
+  if (!*fb) {
+    h->n += hs.delta;
+    h->t_known = hs.bytes_total;
+  }
+  return CPMA_OK;
+}
+
 }  // namespace
 
 void graph_cache_free(cpma* h) {
@@ -2899,6 +3244,7 @@ int reserve(cpma* h, uint64_t max_batch, int tagged, cudaStream_t st) {
   // everything an insert of max_batch keys reserves, a growing resize included
   CPMA_TRY(reserve_update(h, max_batch, 0, st, true));
   CPMA_TRY(front_scratch(h, max_batch, tagged != 0, st));
+  if (!tagged && h->point_max) CPMA_TRY(point_scratch(h, std::min(max_batch, h->point_max), st));
   if (h->graph_max_batch && !tagged) {
     const uint64_t K = graph_bucket(std::min(max_batch, h->graph_max_batch));
     if (K < (1ull << 31)) {
@@ -2995,7 +3341,7 @@ void trim_update_scratch(cpma* h) {
                  &s.leaf_of, &s.chunk_begin, &s.chunk_leaf, &s.chunk_tid, &s.chunk_cnt,
                  &s.chunk_off, &s.T_leaf, &s.T_begin, &s.T_first_chunk, &s.T_oldcnt, &s.T_oldused,
                  &s.T_newcnt, &s.T_newbytes, &s.T_state, &s.viol, &s.list_lane, &s.list_v1,
-                 &s.list_gen, &s.list_pend, &s.cand, &s.wins, &s.bits, &s.prefix, &s.E, &s.cost, &s.C,
+                 &s.list_gen, &s.list_pend, &s.point_stage, &s.point_rec, &s.cand, &s.wins, &s.bits, &s.prefix, &s.E, &s.cost, &s.C,
                  &s.srccnt, &s.srcoff, &s.dstart, &s.win_src, &s.win_dst, &s.win_leaf_off,
                  &s.win_elem_off, &s.win_dst_off, &s.partials, &s.stage, &s.fh})
     release(h, *b);
@@ -3039,6 +3385,16 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
     return rc;
   }
   CPMA_TRY(rc);
+  if (point_ok(h, k, is_delete, tags)) {
+    // the point path; the batch algorithm below only when some touched leaf
+    // cannot take its keys in place (nothing has been written then)
+    CPMA_TRY(point_scratch(h, k, st));
+    bool fb = false;
+    CPMA_TRY(run_point(h, d_keys, k, sorted, d_delta, st, &fb));
+    h->point_calls++;
+    if (!fb) return CPMA_OK;
+    h->point_batch++;
+  }
   Front f;
   if (graph) {
     CPMA_TRY(run_front_graph(h, d_keys, k, sorted, is_delete, st, &f));

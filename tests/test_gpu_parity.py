@@ -280,14 +280,18 @@ def test_many_uneven_ranges_one_launch():
     assert np.array_equal(cp.to_u64(s), ws)
 
 
+@pytest.mark.parametrize("point", [True, False])
 @pytest.mark.parametrize("LB", [256, 512, 1024])
-def test_small_batches_hit_every_splice_case(LB):
+def test_small_batches_hit_every_splice_case(LB, point):
     """Many batches of 1..40 keys: keys just below / equal to / just above
     existing keys and heads, runs in one gap, keys past the last element,
-    repeats and deletes of neighbours -- the splice paths' edge cases."""
+    repeats and deletes of neighbours -- the splice paths' edge cases, with
+    inserts taking the point path when it applies and with it off."""
     rng = np.random.default_rng(LB + 7)
     base = np.unique(W.uniform_keys(81, 6000, bits=30))
     g = cp.CPMA(T(base), leaf_bytes=LB)
+    if not point:
+        g.set_point_max(0)
     o = oracle.SeqCPMA(base, leaf_bytes=LB)
     p = oracle.PlainSet(base)
     for r in range(60):
@@ -326,6 +330,7 @@ def test_graph_updates_match_oracle(LB):
     a new capture) and with several batch sizes sharing one bucket."""
     base = W.uniform_keys(31, 6000, bits=40)
     g = cp.CPMA(T(base), leaf_bytes=LB)
+    g.set_point_max(0)  # small inserts take the batch algorithm (its graphs)
     g.use_graphs(1 << 20)
     g.reserve(4500)
     o = oracle.SeqCPMA(base, leaf_bytes=LB)
@@ -357,6 +362,7 @@ def test_graphs_replay_within_a_bucket():
     captured graph until the leaf arrays are replaced."""
     base = W.uniform_keys(41, 200000, bits=40)
     g = cp.CPMA(T(base), leaf_bytes=512)
+    g.set_point_max(0)
     g.use_graphs(1 << 20)
     g.reserve(1100)
     p = oracle.PlainSet(base)
@@ -611,6 +617,7 @@ def test_profiling_with_graph_replays():
     base = W.uniform_keys(91, 100000, bits=40)
     g = cp.CPMA(T(base), leaf_bytes=512)
     o = oracle.SeqCPMA(base, leaf_bytes=512)
+    g.set_point_max(0)
     g.use_graphs(1 << 20)
     g.reserve(3000)
     g.profile(True)
@@ -684,6 +691,7 @@ def test_route_sparse_tiles():
     # candidates are searched in the global array (keys 0 and 2^64-1 too)
     base = W.uniform_keys(151, 2_000_000, bits=40)
     g = cp.CPMA(T(base), leaf_bytes=256)
+    g.set_point_max(0)  # the batch algorithm's routing
     o = oracle.SeqCPMA(base, leaf_bytes=256)
     assert g.leaves() > 4 * 4096
     for r, k in enumerate([1, 37, 1000, 5000]):
