@@ -366,19 +366,23 @@ int cpma_reserve(cpma_t* h, uint64_t max_batch, uint64_t max_queries, int tagged
 int cpma_use_graphs(cpma_t* h, uint64_t max_batch);
 
 /* Point path (Sec. 4: a batch much smaller than the set is applied as point
- * updates rather than by the batch merge).  An untagged insert of 1 ..
- * max_keys keys (at most 4096; default 4096; 0 = never) into a non-empty set
- * of byte-code leaves of at most 512 bytes is first sorted and routed by one
- * block, and each touched leaf is checked by a warp: it takes its keys in
- * place when it receives at most 32 of them, holds at most 512 used bytes
- * and codes of at most 4 bytes, and the result fits in 512 bytes and keeps
- * the leaf within its own density bound (Sec. 3 bounds at height 0).  If
- * every touched leaf does, they are rewritten in place and the update is
- * done (three kernels and one status read); otherwise nothing is written and
- * the update runs the batch algorithm.  Counts, sets and layouts are the same
- * either way: with no leaf pending and none over its bound the batch
- * algorithm rewrites exactly those leaves, with the same bytes, and starts no
- * redistribution.  Errors: CPMA_EINVAL (null handle). */
+ * updates rather than by the batch merge).  An untagged insert or delete of
+ * 1 .. max_keys keys (at most 4096; default 4096; 0 = never) on a non-empty
+ * set of byte-code leaves of at most 512 bytes is first sorted and routed
+ * (a warp per key), and each touched leaf is checked by a warp: it changes
+ * in place when it receives at most 32 keys (4 for a delete), holds codes of
+ * at most 4 bytes and, for an insert, at most 512 used bytes before and
+ * after, is not emptied by a delete, and stays within its own density bound
+ * (Sec. 3 bounds at height 0).  The results are staged; if every touched
+ * leaf qualifies they are committed and the update is done (two or three
+ * kernels and one status read); otherwise nothing is written and the update
+ * runs the batch algorithm.  Counts, sets and layouts are the same either
+ * way: with no leaf pending, emptied or outside its bound the batch
+ * algorithm rewrites exactly those leaves, with the same bytes, and starts
+ * no redistribution.  The point path's scratch (about 550 bytes per key,
+ * held like the rest) is reserved by cpma_reserve for max_batch keys; when it
+ * cannot be had within the memory budget the update takes the batch
+ * algorithm instead.  Errors: CPMA_EINVAL (null handle). */
 int cpma_set_point_max(cpma_t* h, uint64_t max_keys);
 
 /* Updates that took the point path (calls) and those of them that the batch

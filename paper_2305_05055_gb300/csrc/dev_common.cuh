@@ -67,28 +67,6 @@ __device__ __forceinline__ uint64_t lower_bound(P a, uint64_t n, uint64_t x) {
   return lo;
 }
 
-// Bitonic sorting network over s[0..n) in shared memory (n a power of two),
-// ascending, by the NT threads of the block: one compare-exchange of each
-// pair per stage, the block synchronised after every stage (equal keys are
-// equal values, so their order does not matter).  The caller synchronises
-// the block after filling s.
-template <int NT>
-__device__ __forceinline__ void bitonic_smem(uint64_t* s, uint32_t n) {
-  for (uint32_t size = 2; size <= n; size <<= 1) {
-    for (uint32_t stride = size >> 1; stride; stride >>= 1) {
-      for (uint32_t t = threadIdx.x; t < n / 2; t += NT) {
-        const uint32_t i = 2 * t - (t & (stride - 1)), j = i + stride;  // pair t of this stage
-        const uint64_t a = s[i], b = s[j];
-        if ((a > b) == ((i & size) == 0)) {  // ascending runs where bit `size` of i is 0
-          s[i] = b;
-          s[j] = a;
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
 // Number of entries <= x in the sorted array a[0..n), n >= 1 (branch-free).
 __device__ __forceinline__ uint64_t upper_count(const uint64_t* __restrict__ a, uint64_t n,
                                                 uint64_t x) {

@@ -585,7 +585,8 @@ __global__ void __launch_bounds__(kBT, 2) k_bucket_sort(uint64_t* __restrict__ B
 
 // Untagged batches of at most kTile keys: one block, a bitonic sorting
 // network over the batch padded with 2^64-1 to n (a power of two) in shared
-// memory.
+// memory, one compare-exchange of each pair per stage (equal keys are equal
+// values, so order among them does not matter).
 constexpr int kBitT = 1024;
 __global__ void __launch_bounds__(kBitT) k_sort_bitonic(const uint64_t* __restrict__ in,
                                                         uint64_t* __restrict__ out, uint32_t k,
@@ -593,7 +594,19 @@ __global__ void __launch_bounds__(kBitT) k_sort_bitonic(const uint64_t* __restri
   __shared__ uint64_t s[kTile];
   for (uint32_t i = threadIdx.x; i < n; i += kBitT) s[i] = i < k ? in[i] : ~0ull;
   __syncthreads();
-  bitonic_smem<kBitT>(s, n);
+  for (uint32_t size = 2; size <= n; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride; stride >>= 1) {
+      for (uint32_t t = threadIdx.x; t < n / 2; t += kBitT) {
+        const uint32_t i = 2 * t - (t & (stride - 1)), j = i + stride;  // pair t of this stage
+        const uint64_t a = s[i], b = s[j];
+        if ((a > b) == ((i & size) == 0)) {  // ascending runs where bit `size` of i is 0
+          s[i] = b;
+          s[j] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
   for (uint32_t i = threadIdx.x; i < k; i += kBitT) out[i] = s[i];
 }
 

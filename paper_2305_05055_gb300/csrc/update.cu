@@ -1091,14 +1091,67 @@ __device__ __forceinline__ bool point_first(const uint32_t* __restrict__ leaf_of
   return true;
 }
 
+// Delete of the slice u[i, i + s) (s <= leafthr::kKeys) from leaf j by the
+// thread-granular delete, staged: the warp copies the leaf to the staging
+// slot of key i, then lane 0 plans the delete and rewrites the slot in
+// place.  The leaf goes in place unless it holds a code over 4 bytes, would
+// be emptied (the head fix-up is the batch algorithm's) or would leave its
+// own bound.  wbase holds lane 0's scratch.
+__device__ __forceinline__ uint32_t point_stage_delete(const MergeArgs& a, uint8_t* wbase,
+                                                       uint32_t i, uint32_t s, uint32_t j) {
+  constexpr uint32_t K = leafthr::kKeys;
+  const unsigned lane = lane_id();
+  const uint32_t uold = a.used[j], m = a.cnt[j];
+  if (s > K || uold == 0) return kLeafBatch;
+  uint8_t* slot = a.pstage + (size_t)i * 512;
+  const uint8_t* leafp = a.data + (size_t)j * a.LB;
+  if (16u * lane < a.LB)
+    *reinterpret_cast<uint4*>(slot + 16u * lane) =
+        *reinterpret_cast<const uint4*>(leafp + 16u * lane);
+  __syncwarp();
+  uint32_t verdict = kLeafBatch;
+  if (lane == 0) {
+    uint64_t* rval = reinterpret_cast<uint64_t*>(wbase);
+    uint32_t* w32 = reinterpret_cast<uint32_t*>(wbase + 8 * K);
+    const leafthr::Scratch S{w32, rval, w32 + K, w32 + 2 * K,
+                             reinterpret_cast<int32_t*>(w32 + 3 * K), w32 + 4 * K, 1u};
+    uint64_t y[K];
+#pragma unroll
+    for (uint32_t q = 0; q < K; q++) y[q] = q < s ? a.u[i + q] : 0ull;
+    leafthr::Result R;
+    R.E = 0;
+    const uint32_t res = leafthr::plan_delete(slot, a.LB, uold, m, y, s, S, R);
+    if (res == leafthr::kUnchanged) {
+      verdict = kLeafSame;
+    } else if (res == leafthr::kWritten && R.newc > 0 &&
+               !node_violates(a.B, a.H, 0, 1, R.nb)) {
+      leafthr::rewrite_forward(slot, a.LB, uold, S, R);
+      leafthr::write_delete_edits(slot, S, R);
+      PointRec rec;
+      rec.head = R.newhead;
+      rec.leaf = j;
+      rec.nb = R.nb;
+      rec.newc = R.newc;
+      rec.lo = R.wlo;
+      rec.wend = R.whi;
+      rec.added = m - R.newc;
+      rec.dbytes = (int32_t)R.nb - (int32_t)uold;
+      a.prec[i] = rec;
+      verdict = kLeafInPlace;
+    }
+  }
+  return __shfl_sync(FULL, verdict, 0);
+}
+
 // The point path's plan pass, a warp per sorted key: the order of the keys
 // is checked, and the warp of the first key of each leaf stages the leaf's
-// result (kLaneStage) or counts the leaf in st->point_fb.  With COMMIT (few
+// result (an insert by kLaneStage, a delete by point_stage_delete) or counts
+// the leaf in st->point_fb.  With COMMIT (few
 // keys) the block that finishes last -- every block's stagings and counts
 // are then visible -- commits every staged leaf itself when there is no
 // error and no leaf for the batch algorithm, and writes the keys added to
 // d_delta.
-template <bool COMMIT>
+template <bool COMMIT, bool DEL>
 __global__ void __launch_bounds__(kT, 4) k_point_plan(MergeArgs a,
                                                       const uint32_t* __restrict__ leaf_of,
                                                       uint32_t k, uint64_t* d_delta) {
@@ -1120,9 +1173,10 @@ __global__ void __launch_bounds__(kT, 4) k_point_plan(MergeArgs a,
       nfb++;
       continue;
     }
-    const uint32_t r = lane_leaf<kLaneSeg, kLaneStage>(a, wbase, 0u, lane, FULL, 0u, i, te,
-                                                       a.used[j], j, a.cnt[j], 0u, 0u, nbytes,
-                                                       dl, db);
+    const uint32_t r =
+        DEL ? point_stage_delete(a, wbase, i, te - i, j)
+            : lane_leaf<kLaneSeg, kLaneStage>(a, wbase, 0u, lane, FULL, 0u, i, te, a.used[j], j,
+                                              a.cnt[j], 0u, 0u, nbytes, dl, db);
     nfb += r == kLeafBatch ? 1u : 0u;
     if (lane == 0 && r == kLeafSame) a.prec[i].leaf = 0xFFFFFFFFu;  // nothing to commit
   }
@@ -3078,12 +3132,13 @@ int run_front_graph(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int
   return CPMA_OK;
 }
 
-// May an update take the point path?  Untagged inserts of 1 .. point_max
-// keys into a non-empty set of byte-code leaves of at most 512 bytes (the
-// lane-granular insert's buffer), unless a test of the bounded waits is set
-// up (those waits are in the batch algorithm's sort and routing).
-bool point_ok(const cpma* h, uint64_t k, int is_delete, const uint32_t* tags) {
-  return !is_delete && !tags && k >= 1 && k <= std::min<uint64_t>(h->point_max, kPointMax) &&
+// May an update take the point path?  Untagged updates of 1 .. point_max
+// keys on a non-empty set of byte-code leaves of at most 512 bytes (the
+// lane-granular insert's buffer, the staging slot), unless a test of the
+// bounded waits is set up (those waits are in the batch algorithm's sort and
+// routing).
+bool point_ok(const cpma* h, uint64_t k, const uint32_t* tags) {
+  return !tags && k >= 1 && k <= std::min<uint64_t>(h->point_max, kPointMax) &&
          h->cfg.codec == 0 && h->cfg.leaf_bytes <= 512 && h->n > 0 && h->L > 0 &&
          h->sort_poll_limit == 0 && h->sort_silent_tile < 0;
 }
@@ -3104,8 +3159,8 @@ int point_scratch(cpma* h, uint64_t k, cudaStream_t st) {
 // return *fb tells whether some leaf needs the batch algorithm (nothing has
 // been written then).  point_scratch sized the buffers it uses.
 constexpr uint64_t kPointFew = 32;
-int run_point(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, uint64_t* d_delta,
-              cudaStream_t st, bool* fb) {
+int run_point(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_delete,
+              uint64_t* d_delta, cudaStream_t st, bool* fb) {
   Status* ds = h->d_status;
   Scratch& s = h->s;
   uint64_t* u = P<uint64_t>(s.keysA);
@@ -3133,10 +3188,12 @@ int run_point(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, uint64_t*
   const size_t smem = lane_warp_bytes(kLaneSeg) * (kT / 32);
   prof_begin(h, PH_MERGE_LANE, st);
   if (k <= kPointFew) {
-    k_point_plan<true><<<grid, kT, smem, st>>>(ma, leaf_of, (uint32_t)k, d_delta);
+    if (is_delete) k_point_plan<true, true><<<grid, kT, smem, st>>>(ma, leaf_of, (uint32_t)k, d_delta);
+    else k_point_plan<true, false><<<grid, kT, smem, st>>>(ma, leaf_of, (uint32_t)k, d_delta);
     h->launches += 2;
   } else {
-    k_point_plan<false><<<grid, kT, smem, st>>>(ma, leaf_of, (uint32_t)k, nullptr);
+    if (is_delete) k_point_plan<false, true><<<grid, kT, smem, st>>>(ma, leaf_of, (uint32_t)k, nullptr);
+    else k_point_plan<false, false><<<grid, kT, smem, st>>>(ma, leaf_of, (uint32_t)k, nullptr);
     k_point_commit<<<grid, kT, 0, st>>>(ma, leaf_of, (uint32_t)k, d_delta);
     h->launches += 3;
   }
@@ -3148,7 +3205,7 @@ int run_point(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, uint64_t*
   if (hs.err) return CPMA_EINTERNAL;
   *fb = hs.point_fb != 0;
   if (!*fb) {
-    h->n += hs.delta;
+    h->n = is_delete ? h->n - hs.delta : h->n + hs.delta;
     h->t_known = hs.bytes_total;
   }
   return CPMA_OK;
@@ -3385,12 +3442,14 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
     return rc;
   }
   CPMA_TRY(rc);
-  if (point_ok(h, k, is_delete, tags)) {
-    // the point path; the batch algorithm below only when some touched leaf
-    // cannot take its keys in place (nothing has been written then)
-    CPMA_TRY(point_scratch(h, k, st));
+  // the point path; the batch algorithm below when its scratch cannot be
+  // had within the memory budget, or when some touched leaf cannot change
+  // in place (nothing has been written then)
+  const int prc = point_ok(h, k, tags) ? point_scratch(h, k, st) : CPMA_ENOMEM;
+  if (prc != CPMA_OK && prc != CPMA_ENOMEM) return prc;
+  if (prc == CPMA_OK) {
     bool fb = false;
-    CPMA_TRY(run_point(h, d_keys, k, sorted, d_delta, st, &fb));
+    CPMA_TRY(run_point(h, d_keys, k, sorted, is_delete, d_delta, st, &fb));
     h->point_calls++;
     if (!fb) return CPMA_OK;
     h->point_batch++;

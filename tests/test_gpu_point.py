@@ -1,10 +1,11 @@
 """GPU parity of the point path (Sec. 4: a batch much smaller than the set is
-applied as point updates).  Inserts of up to 4096 keys whose touched leaves
-all take their keys in place, and batches that some leaf cannot take (more
-than 32 keys in one leaf, a leaf pushed over its own bound or past 512
-bytes) and that the batch algorithm then finishes, give the same counts, set
-and byte layout as the sequential oracle.  The point path is checked to have
-run, both ways, and turning it off changes nothing."""
+applied as point updates).  Inserts and deletes of up to 4096 keys whose
+touched leaves all change in place, and batches that some leaf cannot take
+(more than 32 keys -- 4 for a delete -- in one leaf, a leaf pushed over its
+own bound or past 512 bytes, a leaf emptied) and that the batch algorithm
+then finishes, give the same counts, set and byte layout as the sequential
+oracle.  The point path is checked to have run, both ways, and turning it
+off changes nothing."""
 import numpy as np
 import pytest
 import torch
@@ -81,9 +82,10 @@ def test_point_path_matches_oracle(LB):
     heads = lambda: cp.to_u64(g.layout()[2])
     n_ins = 0
     for r, keys in batches(LB, p, heads, 42):
-        if r % 7 == 3:  # deletes keep the leaves uneven (batch algorithm)
+        if r % 7 == 3:  # deletes keep the leaves uneven
             gone = W.sample_present(p.S, 700 + r, 300)
             assert int(g.delete_batch(T(gone)).item()) == o.delete_batch(gone) == p.delete_batch(gone)
+            n_ins += 1
         elif r % 5 == 4:
             srt = np.sort(keys)
             assert int(g.insert_batch(T(srt), sorted=True).item()) == o.insert_batch(srt) == p.insert_batch(srt)
@@ -95,6 +97,55 @@ def test_point_path_matches_oracle(LB):
     st = g.point_stats()
     assert st["calls"] == n_ins, st
     assert 0 < st["batch"] < st["calls"], st   # both outcomes taken
+
+
+@pytest.mark.parametrize("LB", [256, 512])
+def test_point_deletes_match_oracle(LB):
+    """Small deletes: present and absent keys, leaf heads (a new head), the
+    last element, repeats, whole runs of neighbours (a leaf emptied or
+    pushed under its bound: the batch algorithm), with inserts between."""
+    rng = np.random.default_rng(LB + 3)
+    base = W.uniform_keys(651 + LB, 50000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=LB)
+    o = oracle.SeqCPMA(base, leaf_bytes=LB)
+    p = oracle.PlainSet(base)
+    sizes = [1, 3, 30, 300, 1000, 4096]
+    n_del = 0
+    for r in range(36):
+        S = p.S
+        k = sizes[r % len(sizes)]
+        kind = r % 5
+        if kind == 0:
+            keys = W.sample_present(S, 660 + r, k)
+        elif kind == 1:
+            keys = np.concatenate([W.sample_present(S, 660 + r, k // 2 + 1),
+                                   W.uniform_keys(670 + r, k // 2 + 1, bits=40)])
+        elif kind == 2:
+            hd = cp.to_u64(g.layout()[2])
+            keys = np.concatenate([hd[rng.integers(0, hd.size, size=k)], S[-1:]])
+        elif kind == 3:
+            keys = W.sample_present(S, 660 + r, k)
+            keys = np.concatenate([keys, keys[: k // 2 + 1]])
+        else:
+            at = int(rng.integers(0, S.size - 200))
+            keys = S[at: at + int(rng.integers(2, 120))]  # a run of neighbours
+        keys = np.asarray(keys, dtype=np.uint64)
+        if r % 4 == 3:
+            srt = np.sort(keys)
+            got = int(g.delete_batch(T(srt), sorted=True).item())
+        else:
+            got = int(g.delete_batch(T(keys)).item())
+        assert got == o.delete_batch(keys) == p.delete_batch(keys)
+        n_del += keys.size <= 4096
+        same_layout(g, o)
+        if r % 6 == 5:
+            ins = W.uniform_keys(680 + r, 2000, bits=40)
+            assert int(g.insert_batch(T(ins)).item()) == o.insert_batch(ins) == p.insert_batch(ins)
+            n_del += 1
+            same_layout(g, o)
+    st = g.point_stats()
+    assert st["calls"] == n_del, st
+    assert 0 < st["batch"] < st["calls"], st
 
 
 def test_point_path_fills_a_leaf_past_its_bound():
@@ -123,10 +174,13 @@ def test_point_path_off_changes_nothing():
     for r, keys in batches(5, p, heads, 14):
         na, nb = int(a.insert_batch(T(keys)).item()), int(b.insert_batch(T(keys)).item())
         assert na == nb == p.insert_batch(keys)
+        gone = W.sample_present(p.S, 690 + r, keys.size)
+        na, nb = int(a.delete_batch(T(gone)).item()), int(b.delete_batch(T(gone)).item())
+        assert na == nb == p.delete_batch(gone)
         for x, y in zip(a.layout(), b.layout()):
             assert torch.equal(x, y)
     assert b.point_stats() == {"calls": 0, "batch": 0}
-    assert a.point_stats()["calls"] == 14
+    assert a.point_stats()["calls"] == 28
 
 
 def test_point_path_extreme_keys_and_limits():
