@@ -999,6 +999,16 @@ __global__ void __launch_bounds__(kT, SEG == 32 ? 4 : 3) k_insert_lane(MergeArgs
 // no leaf over its bound the batch algorithm's counting phase starts no walk,
 // so both give the same structure.
 constexpr uint32_t kPointMax = 4096;    // keys (the whole batch in one block's shared memory)
+
+// Programmatic dependent launch between the point path's kernels: a kernel
+// launched with programmatic stream serialisation may be scheduled while the
+// kernel before it still runs; pdl_wait() returns once that kernel has
+// completed and its memory operations are visible (at once when there is no
+// such dependency), and pdl_launch() lets the next kernel be scheduled.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 constexpr int kPRT = 256;
 
 // A warp per key: its stable rank (the lanes count over the batch, held in
@@ -1016,6 +1026,7 @@ __global__ void __launch_bounds__(kPRT) k_point_sort_route(const uint64_t* __res
                                                           const uint64_t* __restrict__ heads,
                                                           uint64_t L, Status* st) {
   extern __shared__ __align__(16) uint64_t s_keys[];
+  pdl_launch();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->err = 0;
     st->point_fb = 0;
@@ -1158,6 +1169,8 @@ __global__ void __launch_bounds__(kT, 4) k_point_plan(MergeArgs a,
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ bool s_last;
   __shared__ ull s_dl[kT / 32], s_db[kT / 32];
+  pdl_wait();
+  pdl_launch();
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const unsigned wpb = blockDim.x >> 5;
   uint8_t* wbase = smem + (size_t)warp * lane_warp_bytes(kLaneSeg);
@@ -1215,6 +1228,7 @@ __global__ void __launch_bounds__(kT) k_point_commit(MergeArgs a,
                                                      const uint32_t* __restrict__ leaf_of,
                                                      uint32_t k, uint64_t* d_delta) {
   __shared__ bool s_last;
+  pdl_wait();
   if (a.st->err || a.st->point_fb) return;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const unsigned wpb = blockDim.x >> 5;
@@ -3143,6 +3157,23 @@ bool point_ok(const cpma* h, uint64_t k, const uint32_t* tags) {
          h->sort_poll_limit == 0 && h->sort_silent_tile < 0;
 }
 
+// Launch with programmatic stream serialisation (see pdl_wait).
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*kern)(Params...), unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<Params>(args)...);
+}
+
 // Scratch of the point path for batches of up to k keys: the sort buffer,
 // one leaf word, one 512-byte staging slot and one staged record per key.
 int point_scratch(cpma* h, uint64_t k, cudaStream_t st) {
@@ -3187,14 +3218,20 @@ int run_point(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   ma.prec = P<PointRec>(s.point_rec);
   const size_t smem = lane_warp_bytes(kLaneSeg) * (kT / 32);
   prof_begin(h, PH_MERGE_LANE, st);
+  const uint32_t k32 = (uint32_t)k;
+  uint64_t* none = nullptr;
   if (k <= kPointFew) {
-    if (is_delete) k_point_plan<true, true><<<grid, kT, smem, st>>>(ma, leaf_of, (uint32_t)k, d_delta);
-    else k_point_plan<true, false><<<grid, kT, smem, st>>>(ma, leaf_of, (uint32_t)k, d_delta);
+    CPMA_CUDA(is_delete
+                  ? launch_pdl(k_point_plan<true, true>, grid, kT, smem, st, ma, leaf_of, k32, d_delta)
+                  : launch_pdl(k_point_plan<true, false>, grid, kT, smem, st, ma, leaf_of, k32,
+                               d_delta));
     h->launches += 2;
   } else {
-    if (is_delete) k_point_plan<false, true><<<grid, kT, smem, st>>>(ma, leaf_of, (uint32_t)k, nullptr);
-    else k_point_plan<false, false><<<grid, kT, smem, st>>>(ma, leaf_of, (uint32_t)k, nullptr);
-    k_point_commit<<<grid, kT, 0, st>>>(ma, leaf_of, (uint32_t)k, d_delta);
+    CPMA_CUDA(is_delete
+                  ? launch_pdl(k_point_plan<false, true>, grid, kT, smem, st, ma, leaf_of, k32, none)
+                  : launch_pdl(k_point_plan<false, false>, grid, kT, smem, st, ma, leaf_of, k32,
+                               none));
+    CPMA_CUDA(launch_pdl(k_point_commit, grid, kT, 0, st, ma, leaf_of, k32, d_delta));
     h->launches += 3;
   }
   prof_end(h, st);
