@@ -11,6 +11,37 @@ namespace cpmaimpl {
 
 typedef unsigned long long ull;
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation (launch_pdl) may be scheduled while the kernel before it in
+// the stream still runs.  pdl_wait() returns once that kernel has completed
+// and its memory operations are visible (at once when the launch carried no
+// such dependency), so a kernel calls it before reading anything its
+// predecessor wrote -- and every kernel so launched calls it, so that its
+// own completion implies its predecessors'.  pdl_launch() lets the next
+// kernel be scheduled.
+#if defined(__CUDACC__)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*kern)(Params...), unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<Params>(args)...);
+}
+#endif
+
 // Device-side control block of one batch.  The host reads it back once or
 // twice per update to size the later phases.
 struct Status {

@@ -165,6 +165,8 @@ __global__ void __launch_bounds__(kT) k_orand(const uint64_t* __restrict__ in, u
                                               SortCtl* ctl) {
   __shared__ ull s_or[kWarps], s_and[kWarps];
   __shared__ bool last;
+  pdl_wait();
+  pdl_launch();
   ull o = 0, a = ~0ull;
   // eight keys per thread and step, loaded together
   const uint64_t stride = (uint64_t)gridDim.x * kT;
@@ -212,6 +214,8 @@ __global__ void __launch_bounds__(kT) k_hist_field(const uint64_t* __restrict__ 
   __shared__ uint32_t hs[256];
   __shared__ bool last;
   __shared__ uint32_t wt[kWarps];
+  pdl_wait();
+  pdl_launch();
   hs[threadIdx.x] = 0;  // kT == 256
   __syncthreads();
   const uint32_t fs = ctl->fshift;
@@ -247,6 +251,8 @@ __global__ void __launch_bounds__(kT) k_hist_all(const uint64_t* __restrict__ in
                                                  SortCtl* ctl) {
   __shared__ uint32_t hs[8][256];
   __shared__ bool last;
+  pdl_wait();
+  pdl_launch();
   for (int i = threadIdx.x; i < 8 * 256; i += kT) (&hs[0][0])[i] = 0;
   __syncthreads();
   for (uint64_t i = (uint64_t)blockIdx.x * kT + threadIdx.x; i < k; i += (uint64_t)gridDim.x * kT) {
@@ -296,6 +302,8 @@ __global__ void __launch_bounds__(kT) k_hist_all(const uint64_t* __restrict__ in
 __global__ void k_copy_if_no_pass(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                                   const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout,
                                   uint64_t k, const SortCtl* ctl) {
+  pdl_wait();
+  pdl_launch();
   if (ctl->npass != 0) return;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k;
        i += (uint64_t)gridDim.x * blockDim.x) {
@@ -323,6 +331,8 @@ __global__ void __launch_bounds__(kT, 3) k_onesweep(const uint64_t* __restrict__
   TileSmemT<VALS>& sm = *reinterpret_cast<TileSmemT<VALS>*>(smem_raw);
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_excl[256];
+  pdl_wait();
+  pdl_launch();
   const uint64_t* src;
   uint64_t* dst;
   const uint32_t* vsrc;
@@ -442,6 +452,8 @@ __global__ void __launch_bounds__(kBT, 2) k_bucket_sort(uint64_t* __restrict__ B
   __shared__ ull s_or, s_and;
   __shared__ uint32_t s_run[256];
   __shared__ uint32_t s_wt[8];
+  pdl_wait();
+  pdl_launch();
   if (ctl->npass == 0) {
     // every key equal: the batch as given is the result
     for (uint64_t i = (uint64_t)blockIdx.x * kBT + threadIdx.x; i < k;
@@ -761,13 +773,14 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
     // about eight keys per thread: one step of the unrolled loops
     const int ogrid = (int)std::max<uint64_t>(
         1, std::min<uint64_t>((uint64_t)h->num_sms * 8, (k + 8 * kT - 1) / (8 * kT)));
+    // each kernel after the first may be scheduled while the one before it
+    // finishes (programmatic dependent launch; each waits for it first)
     k_orand<<<ogrid, kT, 0, st>>>(d_in, k, ctl);
-    k_hist_field<<<ogrid, kT, 0, st>>>(d_in, k, ctl);
-    k_onesweep<VALS><<<sgrid, kT, smem, st>>>(d_in, v_in, A, B, VA, VB, k, 0, 1, ctl, look,
-                                               h->d_status, spin, silent);
-    k_bucket_sort<VALS><<<256, kBT, sizeof(TileSmemT<VALS, kBT, kBItems>), st>>>(B, VB, A, VA,
-                                                                                 ctl, d_in, v_in,
-                                                                                 k);
+    CPMA_CUDA(launch_pdl(k_hist_field, ogrid, kT, 0, st, d_in, k, ctl));
+    CPMA_CUDA(launch_pdl(k_onesweep<VALS>, sgrid, kT, smem, st, d_in, v_in, A, B, VA, VB, k, 0, 1,
+                         ctl, look, h->d_status, spin, silent));
+    CPMA_CUDA(launch_pdl(k_bucket_sort<VALS>, 256, kBT, sizeof(TileSmemT<VALS, kBT, kBItems>), st,
+                         B, VB, A, VA, ctl, d_in, v_in, k));
     h->launches += 4;
     // OR/AND and histogram reads, scatter and bucket read + write
     prof_add_bytes(h, PH_SORT, 16ull * k + (VALS ? 24ull : 16ull) * k * 2);
@@ -779,14 +792,14 @@ int sort_impl(cpma* h, const uint64_t* d_in, const uint32_t* v_in, uint64_t k, c
     prof_add_bytes(h, PH_SORT, 8ull * k);  // the histogram read
     for (int p = 0; p < 8; p++) {
       // digits that vary: the scatter reads and writes keys (and tags)
-      k_onesweep<VALS><<<sgrid, kT, smem, st>>>(d_in, v_in, A, B, VA, VB, k, p, 0, ctl,
-                                                 look + (size_t)p * ntiles * 256, h->d_status,
-                                                 spin, silent);
+      CPMA_CUDA(launch_pdl(k_onesweep<VALS>, sgrid, kT, smem, st, d_in, v_in, A, B, VA, VB, k, p,
+                           0, ctl, look + (size_t)p * ntiles * 256, h->d_status, spin, silent));
       h->launches++;
     }
     prof_add_bytes(h, PH_SORT, (VALS ? 24ull : 16ull) * k * 5);  // typical: 5 varying digits
-    k_copy_if_no_pass<<<std::min<uint64_t>((uint64_t)h->num_sms * 4, (k + kT - 1) / kT), kT, 0,
-                        st>>>(d_in, A, v_in, VA, k, ctl);
+    CPMA_CUDA(launch_pdl(k_copy_if_no_pass,
+                         (unsigned)std::min<uint64_t>((uint64_t)h->num_sms * 4, (k + kT - 1) / kT),
+                         kT, 0, st, d_in, A, v_in, VA, k, ctl));
     h->launches++;
   }
   CPMA_CUDA(cudaGetLastError());

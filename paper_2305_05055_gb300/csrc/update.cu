@@ -170,6 +170,8 @@ __global__ void __launch_bounds__(kRT, 4) k_route(const uint64_t* __restrict__ u
   __shared__ uint64_t s_lsum[kW];
   __shared__ uint32_t s_wlast[kW];
   __shared__ uint32_t s_tile, s_pmin, s_tmo;
+  pdl_wait();
+  pdl_launch();
   uint32_t* ctr = reinterpret_cast<uint32_t*>(look_raw);
   volatile uint64_t* look = look_raw + 1;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
@@ -1000,15 +1002,6 @@ __global__ void __launch_bounds__(kT, SEG == 32 ? 4 : 3) k_insert_lane(MergeArgs
 // so both give the same structure.
 constexpr uint32_t kPointMax = 4096;    // keys (the whole batch in one block's shared memory)
 
-// Programmatic dependent launch between the point path's kernels: a kernel
-// launched with programmatic stream serialisation may be scheduled while the
-// kernel before it still runs; pdl_wait() returns once that kernel has
-// completed and its memory operations are visible (at once when there is no
-// such dependency), and pdl_launch() lets the next kernel be scheduled.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_launch() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
 constexpr int kPRT = 256;
 
 // A warp per key: its stable rank (the lanes count over the batch, held in
@@ -1444,6 +1437,8 @@ __global__ void __launch_bounds__(kT) k_classify(MergeArgs a) {
 // pending for the general merge.
 __global__ void __launch_bounds__(kT, 3) k_merge_small(MergeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
+  pdl_wait();
+  pdl_launch();
   if (a.st->err) return;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const unsigned wpb = blockDim.x >> 5;
@@ -1632,6 +1627,8 @@ __global__ void __launch_bounds__(kT, 3) k_merge_small(MergeArgs a) {
 template <bool WRITE>
 __global__ void __launch_bounds__(kT, 2) k_merge(MergeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
+  pdl_wait();
+  pdl_launch();
   if (a.st->err) return;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const unsigned wpb = blockDim.x >> 5;
@@ -1855,6 +1852,8 @@ struct FinArgs {
 };
 
 __global__ void __launch_bounds__(kT) k_finalize(FinArgs a) {
+  pdl_wait();
+  pdl_launch();
   if (a.st->err) return;
   ull mb = 0, dl = 0, np = 0, db = 0, ov = 0;  // db: change of the byte total, mod 2^64
   // the touched leaves the thread- and lane-granular inserts did not finish
@@ -2766,6 +2765,19 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
               Front* f) {
   Status* ds = h->d_status;
   CPMA_CUDA(cudaMemsetAsync(ds, 0, offsetof(Status, empties), st));
+  // routing tiles: keys per thread, the most (8, 4, 2) that still gives two
+  // tiles per SM when the batch is dense against the leaves (a tile then
+  // reaches about as many heads as it has keys), one otherwise.  The tile
+  // counter and look-back words are cleared now, so that the routing kernel
+  // directly follows the sort's last kernel.
+  int kpt = 1;
+  if (2 * k >= h->L)
+    for (int c = 8; c > 1 && kpt == 1; c >>= 1)
+      if (k >= (uint64_t)h->num_sms * 2 * kRT * c) kpt = c;
+  const uint64_t tile_keys = (uint64_t)kRT * kpt;
+  const uint64_t ntiles = (k + tile_keys - 1) / tile_keys;
+  uint64_t* look = P<uint64_t>(h->s.flags);
+  CPMA_CUDA(cudaMemsetAsync(look, 0, (ntiles + 1) * 8, st));
   const uint64_t* u = d_keys;
   const uint32_t* ut = tags;
   if (tags) {
@@ -2800,18 +2812,6 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   ro.T_state = P<uint32_t>(s.T_state);
   ro.T_newbytes = P<ull>(s.T_newbytes);
   {
-    // keys per thread: the most (8, 4, 2) that still gives two tiles per SM
-    // when the batch is dense against the leaves (a tile then reaches about
-    // as many heads as it has keys); one otherwise
-    int kpt = 1;
-    if (2 * k >= h->L)
-      for (int c = 8; c > 1 && kpt == 1; c >>= 1)
-        if (k >= (uint64_t)h->num_sms * 2 * kRT * c) kpt = c;
-    const uint64_t tile_keys = (uint64_t)kRT * kpt;
-    const uint64_t ntiles = (k + tile_keys - 1) / tile_keys;
-    // the tile counter, then one look-back word per tile
-    uint64_t* look = P<uint64_t>(s.flags);
-    CPMA_CUDA(cudaMemsetAsync(look, 0, (ntiles + 1) * 8, st));
     const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)h->num_sms * 4);
     const uint32_t spin = h->sort_poll_limit ? h->sort_poll_limit : (1u << 22);
     const uint32_t silent = h->sort_silent_tile >= 0 && h->sort_silent_tile < (int64_t)ntiles
@@ -2820,22 +2820,24 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
     // old counts (8) and work item (12)
     prof_add_bytes(h, PH_ROUTE, 8ull * k + 64ull * std::min<uint64_t>(k, h->L));
     const uint64_t* H = h->heads;
+    // scheduled while the sort's last kernel finishes (it waits for it first)
+    const uint64_t L = h->L;
     switch (kpt) {
       case 8:
-        k_route<8><<<grid, kRT, 0, st>>>(u, k, H, h->L, h->cnt, h->used, ro, look, ds, spin,
-                                         silent);
+        CPMA_CUDA(launch_pdl(k_route<8>, grid, kRT, 0, st, u, k, H, L, h->cnt, h->used, ro, look,
+                             ds, spin, silent));
         break;
       case 4:
-        k_route<4><<<grid, kRT, 0, st>>>(u, k, H, h->L, h->cnt, h->used, ro, look, ds, spin,
-                                         silent);
+        CPMA_CUDA(launch_pdl(k_route<4>, grid, kRT, 0, st, u, k, H, L, h->cnt, h->used, ro, look,
+                             ds, spin, silent));
         break;
       case 2:
-        k_route<2><<<grid, kRT, 0, st>>>(u, k, H, h->L, h->cnt, h->used, ro, look, ds, spin,
-                                         silent);
+        CPMA_CUDA(launch_pdl(k_route<2>, grid, kRT, 0, st, u, k, H, L, h->cnt, h->used, ro, look,
+                             ds, spin, silent));
         break;
       default:
-        k_route<1><<<grid, kRT, 0, st>>>(u, k, H, h->L, h->cnt, h->used, ro, look, ds, spin,
-                                         silent);
+        CPMA_CUDA(launch_pdl(k_route<1>, grid, kRT, 0, st, u, k, H, L, h->cnt, h->used, ro, look,
+                             ds, spin, silent));
     }
     h->launches++;
     CPMA_CUDA(cudaGetLastError());
@@ -2929,7 +2931,7 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
     h->launches++;
     ma.prof = nullptr;
   }
-  k_merge<false><<<mgrid, mwarps * 32, msmem, st>>>(ma);
+  CPMA_CUDA(launch_pdl(k_merge<false>, (unsigned)mgrid, (unsigned)(mwarps * 32), msmem, st, ma));
   h->launches++;
   CPMA_CUDA(cudaGetLastError());
   prof_end(h, st);
@@ -2960,7 +2962,7 @@ int run_front(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   fa.H = H;
   fa.is_delete = is_delete;
   fa.st = ds;
-  k_finalize<<<grid_for(h, k), kT, 0, st>>>(fa);
+  CPMA_CUDA(launch_pdl(k_finalize, (unsigned)grid_for(h, k), kT, 0, st, fa));
   h->launches++;
   CPMA_CUDA(cudaGetLastError());
   prof_end(h, st);
@@ -3155,23 +3157,6 @@ bool point_ok(const cpma* h, uint64_t k, const uint32_t* tags) {
   return !tags && k >= 1 && k <= std::min<uint64_t>(h->point_max, kPointMax) &&
          h->cfg.codec == 0 && h->cfg.leaf_bytes <= 512 && h->n > 0 && h->L > 0 &&
          h->sort_poll_limit == 0 && h->sort_silent_tile < 0;
-}
-
-// Launch with programmatic stream serialisation (see pdl_wait).
-template <typename... Params, typename... Args>
-cudaError_t launch_pdl(void (*kern)(Params...), unsigned grid, unsigned block, size_t smem,
-                       cudaStream_t st, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, static_cast<Params>(args)...);
 }
 
 // Scratch of the point path for batches of up to k keys: the sort buffer,
