@@ -85,9 +85,13 @@ void release(cpma* h, Buf& b) {
   b.cap = 0;
 }
 
+// The leaf bytes get kLeafPad bytes of padding: a thread rewriting a chunk
+// reads whole 4-byte words, which may reach up to 3 bytes past the last leaf.
+constexpr uint64_t kLeafPad = 16;
+
 int alloc_arrays(cpma* h, uint64_t leaves, uint64_t data_bytes, Arrays* a, cudaStream_t st) {
   *a = Arrays{};
-  int rc = dev_alloc(h, (void**)&a->data, data_bytes, st);
+  int rc = dev_alloc(h, (void**)&a->data, data_bytes + kLeafPad, st);
   if (rc == CPMA_OK) rc = dev_alloc(h, (void**)&a->used, leaves * 4, st);
   if (rc == CPMA_OK) rc = dev_alloc(h, (void**)&a->cnt, leaves * 4, st);
   if (rc == CPMA_OK) rc = dev_alloc(h, (void**)&a->heads, (leaves + 1) * 8, st);
@@ -98,7 +102,7 @@ int alloc_arrays(cpma* h, uint64_t leaves, uint64_t data_bytes, Arrays* a, cudaS
 }
 
 void free_arrays(cpma* h, Arrays* a) {
-  dev_free(h, a->data, a->cap_bytes, nullptr);
+  if (a->data) dev_free(h, a->data, a->cap_bytes + kLeafPad, nullptr);
   dev_free(h, a->used, a->cap_leaves * 4, nullptr);
   dev_free(h, a->cnt, a->cap_leaves * 4, nullptr);
   dev_free(h, a->heads, (a->cap_leaves + 1) * 8, nullptr);

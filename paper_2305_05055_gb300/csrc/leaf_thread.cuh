@@ -440,6 +440,21 @@ LT_HD void tail_segment(const Scratch& S, uint32_t E, uint32_t uold, int32_t& dl
 // after it, shifted together.  A destination chunk wholly inside the
 // segment after the last edit is exactly this, with src = o - sa.
 LT_HD void chunk_tail(const uint8_t* leafp, int32_t src, uint32_t (&r)[4]) {
+#if defined(__CUDA_ARCH__)
+  // five 4-byte words from the 4-byte boundary at or below src, then the
+  // byte shift inside a word (no word selects).  The fifth word is needed
+  // only for an unaligned src; its bytes past src + 16 (the leaf's zero
+  // bytes, the next leaf, or the padding after the last leaf) are shifted
+  // out.
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(leafp + (src & ~3));
+  const uint32_t s8 = 8u * (uint32_t)(src & 3);
+  uint32_t W[5];
+#pragma unroll
+  for (int i = 0; i < 4; i++) W[i] = w[i];
+  W[4] = s8 ? w[4] : 0u;
+#pragma unroll
+  for (int i = 0; i < 4; i++) r[i] = fshr(W[i], W[i + 1], s8);
+#else
   const int32_t A = src & ~15;
   const uint32_t d = (uint32_t)(src - A);
   uint32_t W[8];
@@ -462,6 +477,7 @@ LT_HD void chunk_tail(const uint8_t* leafp, int32_t src, uint32_t (&r)[4]) {
   for (int i = 0; i < 5; i++) V[i] = (q & 2u) ? X[i + 2] : X[i];
 #pragma unroll
   for (int i = 0; i < 4; i++) r[i] = fshr(V[i], V[i + 1], s8);
+#endif
 }
 
 // Pass B by one thread: the chunks R.wlo .. R.whi of the leaf from the end
