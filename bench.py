@@ -780,15 +780,19 @@ def skew(a, dev, T, timed):
     g = cp.CPMA(T(base), leaf_bytes=a.leaf_bytes)
     del base
     L0, b0 = g.leaves(), g.bytes()
-    ins = T(W.zipf_keys(44, rounds * ki, bits=34))
-    dels = T(S[W.permuted_indices(S.size, rounds * kd, 45)])
+    nprof = 10  # rounds after the timed ones, profiled for the phase split
+    ins = T(W.zipf_keys(44, (rounds + nprof) * ki, bits=34))
+    dels = T(S[W.permuted_indices(S.size, (rounds + nprof) * kd, 45)])
     del S
     per = []
-    g.profile(True)
-    for r in range(rounds):
+    for r in range(rounds):  # timed without the profiler's event records
         ms, _ = timed(lambda: (g.insert_batch(ins[r * ki:(r + 1) * ki]),
                                g.delete_batch(dels[r * kd:(r + 1) * kd])))
         per.append(ms)
+    g.profile(True)
+    for r in range(rounds, rounds + nprof):
+        g.insert_batch(ins[r * ki:(r + 1) * ki])
+        g.delete_batch(dels[r * kd:(r + 1) * kd])
     prof = g.profile_read()
     g.profile(False)
     L_rounds = g.leaves()
@@ -833,7 +837,9 @@ def skew(a, dev, T, timed):
             "leaves_start": L0, "leaves_after_rounds": L_rounds, "size_end": size_rounds,
             "bytes_per_key_end": bpk_rounds,
             "bytes_per_key_start": b0 / n0,
-            "phases_ms": {p: prof[p]["ms"] for p in prof if prof[p]["ms"] > 0},
+            "phases_ms_per_round": {p: prof[p]["ms"] / nprof for p in prof if prof[p]["ms"] > 0},
+            "phases_note": "from %d profiled rounds after the timed ones (the profiler's event "
+                           "records are not in the timed rounds); merge_lane overlaps merge" % nprof,
             "growth_and_shrink": resize}
 
 
