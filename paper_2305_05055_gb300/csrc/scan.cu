@@ -71,6 +71,8 @@ __device__ __forceinline__ void block_tiles(uint64_t n, uint64_t& t0, uint64_t& 
 template <typename Tin>
 __global__ void __launch_bounds__(kT) k_reduce(const Tin* __restrict__ in, uint64_t n_host,
                                                const ull* n_dev, uint64_t* partials) {
+  pdl_wait();
+  pdl_launch();
   const uint64_t n = n_dev ? *n_dev : n_host;
   uint64_t tb0, tb1;
   block_tiles(n, tb0, tb1);
@@ -100,6 +102,8 @@ __global__ void __launch_bounds__(kT) k_reduce(const Tin* __restrict__ in, uint6
 
 // One block: exclusive scan of G partials in place, partials[G] = total.
 __global__ void __launch_bounds__(1024) k_partials(uint64_t* partials, int G) {
+  pdl_wait();
+  pdl_launch();
   __shared__ uint64_t wt[32];
   __shared__ uint64_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -131,6 +135,8 @@ template <typename Tin, bool SINGLE = false>
 __global__ void __launch_bounds__(kT) k_down(const Tin* __restrict__ in, uint64_t* __restrict__ out,
                                              uint64_t n_host, const ull* n_dev,
                                              const uint64_t* __restrict__ partials) {
+  pdl_wait();
+  pdl_launch();
   __shared__ uint64_t tile[kTile];
   __shared__ uint64_t warp_tot[kT / 32];
   __shared__ uint64_t tile_total;
@@ -172,7 +178,7 @@ int scan_impl(cpma* h, const Tin* in, uint64_t* out, uint64_t n_host, const ull*
               cudaStream_t st, Buf* partials = nullptr) {
   uint64_t tiles = (n_host + kTile - 1) / kTile;
   if (tiles <= kSingleTiles) {
-    k_down<Tin, true><<<1, kT, 0, st>>>(in, out, n_host, n_dev, nullptr);
+    CPMA_CUDA(launch_pdl(k_down<Tin, true>, 1, kT, 0, st, in, out, n_host, n_dev, nullptr));
     h->launches++;
     return check_cuda(cudaGetLastError());
   }
@@ -180,9 +186,10 @@ int scan_impl(cpma* h, const Tin* in, uint64_t* out, uint64_t n_host, const ull*
   Buf& pb = partials ? *partials : h->s.partials;
   CPMA_TRY(ensure(h, pb, (size_t)(G + 1) * 8));
   uint64_t* part = (uint64_t*)pb.p;
-  k_reduce<Tin><<<G, kT, 0, st>>>(in, n_host, n_dev, part);
-  k_partials<<<1, 1024, 0, st>>>(part, G);
-  k_down<Tin><<<G, kT, 0, st>>>(in, out, n_host, n_dev, part);
+  // each kernel may be scheduled while the one before it finishes
+  CPMA_CUDA(launch_pdl(k_reduce<Tin>, (unsigned)G, kT, 0, st, in, n_host, n_dev, part));
+  CPMA_CUDA(launch_pdl(k_partials, 1, 1024, 0, st, part, G));
+  CPMA_CUDA(launch_pdl(k_down<Tin>, (unsigned)G, kT, 0, st, in, out, n_host, n_dev, part));
   h->launches += 3;
   return check_cuda(cudaGetLastError());
 }
@@ -213,15 +220,16 @@ int scan_u64_given_partials(cpma* h, const uint64_t* in, uint64_t* out, uint64_t
                             uint64_t* partials, uint64_t partials_cap, cudaStream_t st) {
   uint64_t tiles = (n_host + kTile - 1) / kTile;
   if (tiles <= kSingleTiles) {
-    k_down<uint64_t, true><<<1, kT, 0, st>>>(in, out, n_host, nullptr, nullptr);
+    CPMA_CUDA(launch_pdl(k_down<uint64_t, true>, 1, kT, 0, st, in, out, n_host, nullptr, nullptr));
     h->launches++;
     return check_cuda(cudaGetLastError());
   }
   int G = (int)std::min<uint64_t>((uint64_t)2 * h->num_sms, std::max<uint64_t>(tiles, 1));
   if ((uint64_t)G + 1 > partials_cap) return CPMA_EINVAL;
-  k_reduce<uint64_t><<<G, kT, 0, st>>>(in, n_host, nullptr, partials);
-  k_partials<<<1, 1024, 0, st>>>(partials, G);
-  k_down<uint64_t><<<G, kT, 0, st>>>(in, out, n_host, nullptr, partials);
+  CPMA_CUDA(launch_pdl(k_reduce<uint64_t>, (unsigned)G, kT, 0, st, in, n_host, nullptr, partials));
+  CPMA_CUDA(launch_pdl(k_partials, 1, 1024, 0, st, partials, G));
+  CPMA_CUDA(launch_pdl(k_down<uint64_t>, (unsigned)G, kT, 0, st, in, out, n_host, nullptr,
+                       partials));
   h->launches += 3;
   return check_cuda(cudaGetLastError());
 }

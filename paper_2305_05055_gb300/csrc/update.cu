@@ -1943,6 +1943,8 @@ struct WalkArgs {
 };
 
 __global__ void __launch_bounds__(kT) k_walk(WalkArgs a) {
+  pdl_wait();
+  pdl_launch();
   if (gtid() == 0) a.st->total_bytes = a.P[a.L];
   const uint64_t nv = a.st->nviol;
   for (uint64_t v = gtid(); v < nv; v += gstride()) {
@@ -1964,6 +1966,8 @@ __global__ void __launch_bounds__(kT) k_maximal(const uint64_t* __restrict__ can
                                                 const uint32_t* __restrict__ bits, Levels lv,
                                                 unsigned H, uint64_t L, uint64_t* wins,
                                                 Status* st) {
+  pdl_wait();
+  pdl_launch();
   if (st->resize) return;
   const uint64_t nc = st->ncand;
   for (uint64_t c = gtid(); c < nc; c += gstride()) {
@@ -1987,6 +1991,8 @@ __global__ void __launch_bounds__(kT) k_maximal(const uint64_t* __restrict__ can
 
 __global__ void __launch_bounds__(kT) k_clear_bits(const uint64_t* __restrict__ cand,
                                                    uint32_t* bits, Levels lv, Status* st) {
+  pdl_wait();
+  pdl_launch();
   const uint64_t nc = st->ncand;
   for (uint64_t c = gtid(); c < nc; c += gstride()) {
     const uint64_t v = cand[c];
@@ -2019,6 +2025,8 @@ __device__ __forceinline__ uint64_t find_seg(const uint64_t* off, uint64_t nseg,
 
 __global__ void __launch_bounds__(kT) k_win_sizes(const uint64_t* __restrict__ wins, uint64_t nwin,
                                                   uint64_t* __restrict__ sizes) {
+  pdl_wait();
+  pdl_launch();
   for (uint64_t w = gtid(); w < nwin; w += gstride()) sizes[w] = wins[2 * w + 1];
 }
 
@@ -2027,6 +2035,8 @@ __global__ void __launch_bounds__(kT) k_win_sizes(const uint64_t* __restrict__ w
 __global__ void __launch_bounds__(kT) k_src_counts(WinArgs w, const uint32_t* __restrict__ cnt,
                                                    const uint32_t* __restrict__ used, uint64_t nsrc,
                                                    uint32_t* __restrict__ srccnt, Status* st) {
+  pdl_wait();
+  pdl_launch();
   ull gone = 0;
   for (uint64_t f = gtid(); f < nsrc; f += gstride()) {
     const uint64_t s = find_seg(w.leaf_off, w.nwin, f);
@@ -2039,6 +2049,8 @@ __global__ void __launch_bounds__(kT) k_src_counts(WinArgs w, const uint32_t* __
 }
 
 __global__ void k_elem_offsets(WinArgs w, const uint64_t* __restrict__ srcoff, Status* st) {
+  pdl_wait();
+  pdl_launch();
   for (uint64_t s = gtid(); s <= w.nwin; s += gstride()) w.elem_off[s] = srcoff[w.leaf_off[s]];
   if (gtid() == 0) st->nelem = srcoff[w.leaf_off[w.nwin]];
 }
@@ -2064,6 +2076,8 @@ struct UnpackArgs {
 };
 
 __global__ void __launch_bounds__(kT) k_unpack(UnpackArgs a) {
+  pdl_wait();
+  pdl_launch();
   const unsigned lane = lane_id();
   const uint64_t gw = gtid() >> 5, nw = gstride() >> 5;
   for (uint64_t f = gw; f < a.nsrc; f += nw) {
@@ -2093,6 +2107,8 @@ __global__ void __launch_bounds__(kT) k_unpack(UnpackArgs a) {
 __global__ void __launch_bounds__(kT) k_costs(WinArgs w, const uint64_t* __restrict__ E,
                                               const ull* nelem, uint8_t* __restrict__ cost,
                                               int raw) {
+  pdl_wait();
+  pdl_launch();
   const uint64_t n = *nelem;
   for (uint64_t i = gtid(); i < n; i += gstride()) {
     const uint64_t s = find_seg(w.elem_off, w.nwin, i);
@@ -2102,6 +2118,8 @@ __global__ void __launch_bounds__(kT) k_costs(WinArgs w, const uint64_t* __restr
 
 __global__ void __launch_bounds__(kT) k_starts(WinArgs w, const uint64_t* __restrict__ C,
                                                uint64_t ndst, uint64_t* __restrict__ dstart) {
+  pdl_wait();
+  pdl_launch();
   typedef unsigned __int128 u128;
   for (uint64_t g = gtid(); g < ndst; g += gstride()) {
     const uint64_t s = find_seg(w.dst_off, w.nwin, g);
@@ -2130,6 +2148,8 @@ struct EncodeArgs {
 };
 
 __global__ void __launch_bounds__(kT) k_encode(EncodeArgs a) {
+  pdl_wait();
+  pdl_launch();
   extern __shared__ __align__(16) uint8_t smem[];
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   uint8_t* buf = smem + (size_t)warp * a.LB;
@@ -2191,6 +2211,8 @@ struct FHTile {
 __global__ void __launch_bounds__(kFH) k_fh_tiles(const uint32_t* __restrict__ used,
                                                   const uint64_t* __restrict__ heads, uint64_t L,
                                                   FHTile* __restrict__ tiles) {
+  pdl_wait();
+  pdl_launch();
   __shared__ int first_t;
   __shared__ unsigned int ne_s;
   __shared__ ull last_s;
@@ -2226,6 +2248,8 @@ __global__ void __launch_bounds__(kFH) k_fh_tiles(const uint32_t* __restrict__ u
 __global__ void __launch_bounds__(kFH) k_fh_carry(FHTile* __restrict__ tiles, uint64_t nt,
                                                   uint64_t* __restrict__ heads, uint64_t L,
                                                   Status* st) {
+  pdl_wait();
+  pdl_launch();
   __shared__ uint64_t cv[kFH];
   __shared__ uint32_t cok[kFH];
   __shared__ ull ne_s, last_s;
@@ -2274,6 +2298,8 @@ __global__ void __launch_bounds__(kFH) k_fh_carry(FHTile* __restrict__ tiles, ui
 __global__ void __launch_bounds__(kFH) k_fh_fill(const uint32_t* __restrict__ used,
                                                  uint64_t* __restrict__ heads, uint64_t L,
                                                  const FHTile* __restrict__ tiles) {
+  pdl_wait();
+  pdl_launch();
   __shared__ uint64_t wv[kFH / 32], wc[kFH / 32];
   __shared__ uint32_t wok[kFH / 32], wcok[kFH / 32];
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
@@ -2323,6 +2349,8 @@ __global__ void __launch_bounds__(kFH) k_fh_fill(const uint32_t* __restrict__ us
 __global__ void k_set_window(uint64_t* win_src, uint64_t* win_dst, uint64_t* leaf_off,
                              uint64_t* dst_off, uint64_t sa, uint64_t sW, uint64_t da,
                              uint64_t dW) {
+  pdl_wait();
+  pdl_launch();
   win_src[0] = sa; win_src[1] = sW;
   win_dst[0] = da; win_dst[1] = dW;
   leaf_off[0] = 0; leaf_off[1] = sW;
@@ -2403,13 +2431,13 @@ int spread(cpma* h, cudaStream_t st, WinArgs w, uint64_t nelem_bound, const ull*
   CPMA_TRY(ensure(h, h->s.cost, nelem_bound + 1));
   CPMA_TRY(ensure(h, h->s.C, (nelem_bound + 2) * 8));
   CPMA_TRY(ensure(h, h->s.dstart, (ndst + 1) * 8));
-  k_costs<<<grid_for(h, nelem_bound), kT, 0, st>>>(w, P<uint64_t>(h->s.E), nelem_dev,
-                                                   P<uint8_t>(h->s.cost), (int)h->cfg.codec);
+  CPMA_CUDA(launch_pdl(k_costs, (unsigned)(grid_for(h, nelem_bound)), kT, 0, st, w,
+                       P<uint64_t>(h->s.E), nelem_dev, P<uint8_t>(h->s.cost), (int)h->cfg.codec));
   h->launches++;
   CPMA_TRY(scan_u8_to_u64(h, P<uint8_t>(h->s.cost), P<uint64_t>(h->s.C), nelem_bound, nelem_dev,
                           st));
-  k_starts<<<grid_for(h, ndst), kT, 0, st>>>(w, P<uint64_t>(h->s.C), ndst,
-                                             P<uint64_t>(h->s.dstart));
+  CPMA_CUDA(launch_pdl(k_starts, (unsigned)(grid_for(h, ndst)), kT, 0, st, w, P<uint64_t>(h->s.C),
+                       ndst, P<uint64_t>(h->s.dstart)));
   h->launches++;
   EncodeArgs ea;
   ea.w = w;
@@ -2425,7 +2453,7 @@ int spread(cpma* h, cudaStream_t st, WinArgs w, uint64_t nelem_bound, const ull*
   ea.st = h->d_status;
   ea.raw = (int)h->cfg.codec;
   const size_t smem = (size_t)(kT / 32) * LBdst;
-  k_encode<<<grid_for(h, ndst * 32), kT, smem, st>>>(ea);
+  CPMA_CUDA(launch_pdl(k_encode, (unsigned)(grid_for(h, ndst * 32)), kT, smem, st, ea));
   h->launches++;
   return check_cuda(cudaGetLastError());
 }
@@ -2458,12 +2486,13 @@ int pack(cpma* h, cudaStream_t st, uint64_t nwin, uint64_t nsrc, uint64_t nelem_
   CPMA_TRY(ensure(h, h->s.srccnt, (nsrc + 1) * 4));
   CPMA_TRY(ensure(h, h->s.srcoff, (nsrc + 2) * 8));
   CPMA_TRY(ensure(h, h->s.E, (nelem_bound + 1) * 8));
-  k_src_counts<<<grid_for(h, nsrc), kT, 0, st>>>(w, h->cnt, h->used, nsrc, P<uint32_t>(h->s.srccnt),
-                                                  h->d_status);
+  CPMA_CUDA(launch_pdl(k_src_counts, (unsigned)(grid_for(h, nsrc)), kT, 0, st, w, h->cnt, h->used,
+                       nsrc, P<uint32_t>(h->s.srccnt), h->d_status));
   h->launches++;
   CPMA_TRY(scan_u32_to_u64(h, P<uint32_t>(h->s.srccnt), P<uint64_t>(h->s.srcoff), nsrc, nullptr,
                            st));
-  k_elem_offsets<<<1, kT, 0, st>>>(w, P<uint64_t>(h->s.srcoff), h->d_status);
+  CPMA_CUDA(launch_pdl(k_elem_offsets, (unsigned)(1), kT, 0, st, w, P<uint64_t>(h->s.srcoff),
+                       h->d_status));
   h->launches++;
   UnpackArgs ua;
   ua.w = w;
@@ -2482,7 +2511,7 @@ int pack(cpma* h, cudaStream_t st, uint64_t nwin, uint64_t nsrc, uint64_t nelem_
   ua.E = P<uint64_t>(h->s.E);
   ua.st = h->d_status;
   ua.raw = (int)h->cfg.codec;
-  k_unpack<<<grid_for(h, nsrc * 32), kT, 0, st>>>(ua);
+  CPMA_CUDA(launch_pdl(k_unpack, (unsigned)(grid_for(h, nsrc * 32)), kT, 0, st, ua));
   h->launches++;
   return check_cuda(cudaGetLastError());
 }
@@ -2497,9 +2526,12 @@ int fix_heads(cpma* h, cudaStream_t st) {
   const uint64_t nt = (h->L + kFHTile - 1) / kFHTile;
   CPMA_TRY(ensure(h, h->s.fh, nt * sizeof(FHTile)));
   FHTile* tiles = P<FHTile>(h->s.fh);
-  k_fh_tiles<<<(unsigned)nt, kFH, 0, st>>>(h->used, h->heads, h->L, tiles);
-  k_fh_carry<<<1, kFH, 0, st>>>(tiles, nt, h->heads, h->L, h->d_status);
-  k_fh_fill<<<(unsigned)nt, kFH, 0, st>>>(h->used, h->heads, h->L, tiles);
+  CPMA_CUDA(launch_pdl(k_fh_tiles, (unsigned)((unsigned)nt), kFH, 0, st, h->used, h->heads, h->L,
+                       tiles));
+  CPMA_CUDA(launch_pdl(k_fh_carry, (unsigned)(1), kFH, 0, st, tiles, nt, h->heads, h->L,
+                       h->d_status));
+  CPMA_CUDA(launch_pdl(k_fh_fill, (unsigned)((unsigned)nt), kFH, 0, st, h->used, h->heads, h->L,
+                       tiles));
   h->launches += 3;
   return check_cuda(cudaGetLastError());
 }
@@ -2555,9 +2587,9 @@ int do_resize(cpma* h, cudaStream_t st, uint64_t T, uint64_t n_after, uint64_t n
   if (!in_place && (Lp > h->spare.cap_leaves || Lp * LBp > h->spare.cap_bytes))
     return CPMA_EINTERNAL;  // the reservation missed this case
   Arrays dst = in_place ? live_arrays(h) : h->spare;
-  k_set_window<<<1, 1, 0, st>>>(P<uint64_t>(h->s.win_src), P<uint64_t>(h->s.win_dst),
-                                P<uint64_t>(h->s.win_leaf_off), P<uint64_t>(h->s.win_dst_off), 0,
-                                h->L, 0, Lp);
+  CPMA_CUDA(launch_pdl(k_set_window, (unsigned)(1), 1, 0, st, P<uint64_t>(h->s.win_src),
+                       P<uint64_t>(h->s.win_dst), P<uint64_t>(h->s.win_leaf_off),
+                       P<uint64_t>(h->s.win_dst_off), 0, h->L, 0, Lp));
   h->launches++;
   CPMA_TRY(redistribute(h, st, 1, h->L, Lp, n_after, nT, dst, LBp));
   CPMA_CUDA(cudaStreamSynchronize(st));
@@ -2609,6 +2641,8 @@ __global__ void __launch_bounds__(kT) k_merge_path(const uint64_t* __restrict__ 
                                                    const uint64_t* __restrict__ B, uint64_t k,
                                                    uint64_t* __restrict__ M,
                                                    uint8_t* __restrict__ fromB) {
+  pdl_wait();
+  pdl_launch();
   __shared__ uint64_t sA[kMergeTile + 1], sB[kMergeTile + 1];
   __shared__ uint64_t split[2];
   const uint64_t N = n + k;
@@ -2663,6 +2697,8 @@ __global__ void __launch_bounds__(kT) k_rebuild_flags(const uint64_t* __restrict
                                                       const uint8_t* __restrict__ fromB,
                                                       uint64_t N, int is_delete,
                                                       uint8_t* __restrict__ keep) {
+  pdl_wait();
+  pdl_launch();
   for (uint64_t i = gtid(); i < N; i += gstride()) {
     const uint64_t x = M[i];
     bool kp;
@@ -2678,6 +2714,8 @@ __global__ void __launch_bounds__(kT) k_rebuild_scatter(const uint64_t* __restri
                                                         uint64_t N, uint64_t n_old,
                                                         int is_delete,
                                                         uint64_t* __restrict__ E, Status* st) {
+  pdl_wait();
+  pdl_launch();
   for (uint64_t i = gtid(); i < N; i += gstride())
     if (keep[i]) E[pos[i]] = M[i];
   if (gtid() == 0) {
@@ -3206,16 +3244,16 @@ int run_point(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   const uint32_t k32 = (uint32_t)k;
   uint64_t* none = nullptr;
   if (k <= kPointFew) {
-    CPMA_CUDA(is_delete
-                  ? launch_pdl(k_point_plan<true, true>, grid, kT, smem, st, ma, leaf_of, k32, d_delta)
-                  : launch_pdl(k_point_plan<true, false>, grid, kT, smem, st, ma, leaf_of, k32,
-                               d_delta));
+    CPMA_CUDA(is_delete ? launch_pdl(k_point_plan<true, true>, grid, kT, smem, st, ma, leaf_of,
+                                     k32, d_delta)
+                        : launch_pdl(k_point_plan<true, false>, grid, kT, smem, st, ma, leaf_of,
+                                     k32, d_delta));
     h->launches += 2;
   } else {
-    CPMA_CUDA(is_delete
-                  ? launch_pdl(k_point_plan<false, true>, grid, kT, smem, st, ma, leaf_of, k32, none)
-                  : launch_pdl(k_point_plan<false, false>, grid, kT, smem, st, ma, leaf_of, k32,
-                               none));
+    CPMA_CUDA(is_delete ? launch_pdl(k_point_plan<false, true>, grid, kT, smem, st, ma, leaf_of,
+                                     k32, none)
+                        : launch_pdl(k_point_plan<false, false>, grid, kT, smem, st, ma, leaf_of,
+                                     k32, none));
     CPMA_CUDA(launch_pdl(k_point_commit, grid, kT, 0, st, ma, leaf_of, k32, d_delta));
     h->launches += 3;
   }
@@ -3291,12 +3329,14 @@ int run_rebuild(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_
   // merge and store phases across blocks
   const uint64_t mg = std::max<uint64_t>(1, (N + kMergeTile - 1) / kMergeTile);
   if (mg >= (1ull << 31)) return CPMA_EINVAL;
-  k_merge_path<<<(unsigned)mg, kT, 0, st>>>(P<uint64_t>(s.E), n, u, k, M, fromB);
-  k_rebuild_flags<<<grid_for(h, N), kT, 0, st>>>(M, fromB, N, is_delete, keep);
+  CPMA_CUDA(launch_pdl(k_merge_path, (unsigned)((unsigned)mg), kT, 0, st, P<uint64_t>(s.E), n, u, k,
+                       M, fromB));
+  CPMA_CUDA(launch_pdl(k_rebuild_flags, (unsigned)(grid_for(h, N)), kT, 0, st, M, fromB, N,
+                       is_delete, keep));
   h->launches += 2;
   CPMA_TRY(scan_u8_to_u64(h, keep, pos, N, nullptr, st));
-  k_rebuild_scatter<<<grid_for(h, N), kT, 0, st>>>(M, keep, pos, N, n, is_delete,
-                                                   P<uint64_t>(s.E), ds);
+  CPMA_CUDA(launch_pdl(k_rebuild_scatter, (unsigned)(grid_for(h, N)), kT, 0, st, M, keep, pos, N, n,
+                       is_delete, P<uint64_t>(s.E), ds));
   h->launches++;
   CPMA_CUDA(cudaGetLastError());
   CPMA_TRY(sync_status(h, st));
@@ -3420,7 +3460,8 @@ void trim_update_scratch(cpma* h) {
                  &s.leaf_of, &s.chunk_begin, &s.chunk_leaf, &s.chunk_tid, &s.chunk_cnt,
                  &s.chunk_off, &s.T_leaf, &s.T_begin, &s.T_first_chunk, &s.T_oldcnt, &s.T_oldused,
                  &s.T_newcnt, &s.T_newbytes, &s.T_state, &s.viol, &s.list_lane, &s.list_v1,
-                 &s.list_gen, &s.list_pend, &s.point_stage, &s.point_rec, &s.cand, &s.wins, &s.bits, &s.prefix, &s.E, &s.cost, &s.C,
+                 &s.list_gen, &s.list_pend, &s.point_stage, &s.point_rec, &s.cand, &s.wins,
+                 &s.bits, &s.prefix, &s.E, &s.cost, &s.C,
                  &s.srccnt, &s.srcoff, &s.dstart, &s.win_src, &s.win_dst, &s.win_leaf_off,
                  &s.win_elem_off, &s.win_dst_off, &s.partials, &s.stage, &s.fh})
     release(h, *b);
@@ -3513,7 +3554,7 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
                              st));
     ma.ovf = P<uint64_t>(s.C);
     ma.tag_counts = nullptr;
-    k_merge<true><<<mgrid, mwarps * 32, msmem, st>>>(ma);
+    CPMA_CUDA(launch_pdl(k_merge<true>, (unsigned)(mgrid), mwarps * 32, msmem, st, ma));
     h->launches++;
     CPMA_CUDA(cudaGetLastError());
   }
@@ -3533,13 +3574,14 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
       wa.B = B;
       wa.H = H;
       wa.st = ds;
-      k_walk<<<grid_for(h, hs.nviol), kT, 0, st>>>(wa);
+      CPMA_CUDA(launch_pdl(k_walk, (unsigned)(grid_for(h, hs.nviol)), kT, 0, st, wa));
       h->launches++;
     }
     const uint64_t ncand_bound = hs.nviol + hs.npend + 1;
-    k_maximal<<<grid_for(h, ncand_bound), kT, 0, st>>>(fa.cand, fa.bits, lv, H, h->L,
-                                                       P<uint64_t>(s.wins), ds);
-    k_clear_bits<<<grid_for(h, ncand_bound), kT, 0, st>>>(fa.cand, fa.bits, lv, ds);
+    CPMA_CUDA(launch_pdl(k_maximal, (unsigned)(grid_for(h, ncand_bound)), kT, 0, st, fa.cand,
+                         fa.bits, lv, H, h->L, P<uint64_t>(s.wins), ds));
+    CPMA_CUDA(launch_pdl(k_clear_bits, (unsigned)(grid_for(h, ncand_bound)), kT, 0, st, fa.cand,
+                         fa.bits, lv, ds));
     h->launches += 2;
     CPMA_CUDA(cudaGetLastError());
     prof_end(h, st);
@@ -3558,8 +3600,8 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
       // windows in place: destination = source
       CPMA_CUDA(cudaMemcpyAsync(s.win_src.p, s.wins.p, nwin * 16, cudaMemcpyDeviceToDevice, st));
       CPMA_CUDA(cudaMemcpyAsync(s.win_dst.p, s.wins.p, nwin * 16, cudaMemcpyDeviceToDevice, st));
-      k_win_sizes<<<grid_for(h, nwin), kT, 0, st>>>(P<uint64_t>(s.wins), nwin,
-                                                    P<uint64_t>(s.prefix));
+      CPMA_CUDA(launch_pdl(k_win_sizes, (unsigned)(grid_for(h, nwin)), kT, 0, st,
+                           P<uint64_t>(s.wins), nwin, P<uint64_t>(s.prefix)));
       h->launches++;
       CPMA_TRY(scan_u64(h, P<uint64_t>(s.prefix), P<uint64_t>(s.win_leaf_off), nwin, nullptr, st));
       CPMA_CUDA(cudaMemcpyAsync(s.win_dst_off.p, s.win_leaf_off.p, (nwin + 1) * 8,
@@ -3602,16 +3644,16 @@ int build_from_sorted_unique(cpma* h, const uint64_t* E, uint64_t n, cudaStream_
   CPMA_TRY(ensure(h, s.C, (n + 2) * 8));
   if (E != P<uint64_t>(s.E)) return CPMA_EINTERNAL;
   // costs and stream bytes (one window, no source leaves)
-  k_set_window<<<1, 1, 0, st>>>(P<uint64_t>(s.win_src), P<uint64_t>(s.win_dst),
-                                P<uint64_t>(s.win_leaf_off), P<uint64_t>(s.win_dst_off), 0, 0, 0,
-                                1);
+  CPMA_CUDA(launch_pdl(k_set_window, (unsigned)(1), 1, 0, st, P<uint64_t>(s.win_src),
+                       P<uint64_t>(s.win_dst), P<uint64_t>(s.win_leaf_off),
+                       P<uint64_t>(s.win_dst_off), 0, 0, 0, 1));
   h->launches++;
   uint64_t eo[2] = {0, n};
   CPMA_CUDA(cudaMemcpyAsync(s.win_elem_off.p, eo, 16, cudaMemcpyHostToDevice, st));
   CPMA_CUDA(cudaMemcpyAsync(&h->d_status->nelem, &n, 8, cudaMemcpyHostToDevice, st));
   WinArgs w = win_args(h, 1);
-  k_costs<<<grid_for(h, n), kT, 0, st>>>(w, E, &h->d_status->nelem, P<uint8_t>(s.cost),
-                                         (int)h->cfg.codec);
+  CPMA_CUDA(launch_pdl(k_costs, (unsigned)(grid_for(h, n)), kT, 0, st, w, E, &h->d_status->nelem,
+                       P<uint8_t>(s.cost), (int)h->cfg.codec));
   h->launches++;
   CPMA_TRY(scan_u8_to_u64(h, P<uint8_t>(s.cost), P<uint64_t>(s.C), n, nullptr, st));
   CPMA_CUDA(cudaMemcpyAsync(&h->d_status->stream_bytes, P<uint64_t>(s.C) + n, 8,
@@ -3623,12 +3665,13 @@ int build_from_sorted_unique(cpma* h, const uint64_t* E, uint64_t n, cudaStream_
   if (L < 1) L = 1;
   Arrays na;
   CPMA_TRY(alloc_arrays(h, L, L * LB, &na, st));
-  k_set_window<<<1, 1, 0, st>>>(P<uint64_t>(s.win_src), P<uint64_t>(s.win_dst),
-                                P<uint64_t>(s.win_leaf_off), P<uint64_t>(s.win_dst_off), 0, 0, 0,
-                                L);
+  CPMA_CUDA(launch_pdl(k_set_window, (unsigned)(1), 1, 0, st, P<uint64_t>(s.win_src),
+                       P<uint64_t>(s.win_dst), P<uint64_t>(s.win_leaf_off),
+                       P<uint64_t>(s.win_dst_off), 0, 0, 0, L));
   h->launches++;
   CPMA_TRY(ensure(h, s.dstart, (L + 1) * 8));
-  k_starts<<<grid_for(h, L), kT, 0, st>>>(w, P<uint64_t>(s.C), L, P<uint64_t>(s.dstart));
+  CPMA_CUDA(launch_pdl(k_starts, (unsigned)(grid_for(h, L)), kT, 0, st, w, P<uint64_t>(s.C), L,
+                       P<uint64_t>(s.dstart)));
   h->launches++;
   EncodeArgs ea;
   ea.w = w;
@@ -3646,7 +3689,8 @@ int build_from_sorted_unique(cpma* h, const uint64_t* E, uint64_t n, cudaStream_
   // the byte total restarts with the new leaves (the encode adds them)
   int rc = check_cuda(cudaMemsetAsync(&h->d_status->bytes_total, 0, 8, st));
   if (rc == CPMA_OK) {
-    k_encode<<<grid_for(h, L * 32), kT, (size_t)(kT / 32) * LB, st>>>(ea);
+    CPMA_CUDA(launch_pdl(k_encode, (unsigned)(grid_for(h, L * 32)), kT, (size_t)(kT / 32) * LB, st,
+                         ea));
     h->launches++;
     rc = check_cuda(cudaGetLastError());
   }
