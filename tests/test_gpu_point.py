@@ -215,3 +215,27 @@ def test_point_path_rejects_an_unsorted_batch_unchanged():
         assert e.value.code == cp.CPMA_EINVAL
         assert all(torch.equal(a, b.cpu()) for a, b in zip(before, g.layout()))
     assert g.size() == len(oracle.PlainSet(base))
+
+
+def test_point_path_with_profiling_and_graphs():
+    """Profiling and graph mode on: small updates still take the point path,
+    their phases are recorded (routing and the warp-per-leaf phase), and the
+    layout stays the oracle's."""
+    base = W.uniform_keys(661, 30000, bits=40)
+    g = cp.CPMA(T(base), leaf_bytes=512)
+    o = oracle.SeqCPMA(base, leaf_bytes=512)
+    g.use_graphs(1 << 20)
+    g.reserve(5000)
+    g.profile(True)
+    for r, k in enumerate([1, 40, 1000, 4096]):
+        keys = W.uniform_keys(662 + r, k, bits=40)
+        assert int(g.insert_batch(T(keys)).item()) == o.insert_batch(keys)
+        gone = W.sample_present(np.unique(keys), 670 + r, max(1, k // 3))
+        assert int(g.delete_batch(T(gone)).item()) == o.delete_batch(gone)
+        same_layout(g, o)
+    prof = g.profile_read()
+    g.profile(False)
+    assert g.point_stats()["calls"] == 8
+    assert g.graph_stats()["launches"] == 0  # no batch went to the batch algorithm
+    for ph in ("route", "merge_lane"):
+        assert prof[ph]["calls"] == 8 and prof[ph]["ms"] > 0, (ph, prof[ph])
