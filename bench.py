@@ -602,7 +602,8 @@ def measure_extra(a, g, ins_batches, dev, st, hbm_peak, peak_kind, T):
         c = g.clone()
         # keys the timed steps inserted and the deletes above left in place
         present = torch.cat(list(ins_batches[min(5, len(ins_batches) - 1):]))
-        out["small_updates"] = latency.measure(c, present, sizes=(1, 100, 1000, 4096), trials=15)
+        out["small_updates"] = latency.measure(c, present, sizes=(1, 100, 1000, 4096, 16384),
+                                               trials=15)
         del c, present
     if not a.no_skew:
         out["skew"] = skew(a, dev, T, timed)

@@ -366,10 +366,12 @@ int cpma_reserve(cpma_t* h, uint64_t max_batch, uint64_t max_queries, int tagged
 int cpma_use_graphs(cpma_t* h, uint64_t max_batch);
 
 /* Point path (Sec. 4: a batch much smaller than the set is applied as point
- * updates rather than by the batch merge).  An untagged insert or delete of
- * 1 .. max_keys keys (at most 4096; default 4096; 0 = never) on a non-empty
- * set of byte-code leaves of at most 512 bytes is first sorted and routed
- * (a warp per key), and each touched leaf is checked by a warp: it changes
+ * updates rather than by the batch merge).  An untagged insert of 1 ..
+ * max_keys keys (at most 16384; default 16384; 0 = never), or delete of at
+ * most min(max_keys, 4096) keys, on a non-empty set of byte-code leaves of
+ * at most 512 bytes is first sorted
+ * (up to 4096 keys by ranks in the routing kernel, more by the batch sort)
+ * and routed (a warp per key), and each touched leaf is checked by a warp: it changes
  * in place when it receives at most 32 keys (4 for a delete), holds codes of
  * at most 4 bytes and, for an insert, at most 512 used bytes before and
  * after, is not emptied by a delete, and stays within its own density bound

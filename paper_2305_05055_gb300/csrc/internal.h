@@ -210,10 +210,10 @@ struct cpma {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   uint64_t graph_captures = 0, graph_launches = 0;
-  // untagged inserts of up to this many keys try the point path first (at
-  // most 4096; 0 = never); updates that took it, and those of them that the
+  // untagged updates of up to this many keys try the point path first (at
+  // most 16384; 0 = never); updates that took it, and those of them that the
   // batch algorithm finished instead
-  uint64_t point_max = 4096;
+  uint64_t point_max = 16384;
   uint64_t point_calls = 0, point_batch = 0;
 };
 

@@ -990,7 +990,8 @@ __global__ void __launch_bounds__(kT, SEG == 32 ? 4 : 3) k_insert_lane(MergeArgs
 // ---------------------------------------------------------------------------
 // Point path (Sec. 4: a batch much smaller than the set is applied as point
 // updates instead of by the batch algorithm).  An untagged insert of at most
-// kPointMax keys is sorted and routed in one kernel (k_point_sort_route); a
+// kPointMax keys is sorted and routed (k_point_sort_route; the batch sort
+// first above kPointRankMax keys); a
 // plan pass then takes each touched leaf with a warp and decides whether the
 // leaf's keys go in place: the lane-granular insert's conditions (at most 32
 // keys, a non-empty leaf of at most 512 used bytes, codes of at most four
@@ -1000,7 +1001,12 @@ __global__ void __launch_bounds__(kT, SEG == 32 ? 4 : 3) k_insert_lane(MergeArgs
 // written and the update runs the batch algorithm.  With no pending leaf and
 // no leaf over its bound the batch algorithm's counting phase starts no walk,
 // so both give the same structure.
-constexpr uint32_t kPointMax = 4096;    // keys (the whole batch in one block's shared memory)
+constexpr uint32_t kPointMax = 16384;     // keys of an insert
+constexpr uint32_t kPointDelMax = 4096;   // keys of a delete (its leaves are planned by one
+                                          // lane each: larger deletes are faster batched)
+constexpr uint32_t kPointRankMax = 4096;  // ranked in k_point_sort_route (the batch in one
+                                          // block's shared memory); larger batches are
+                                          // sorted first by the batch sort
 
 constexpr int kPRT = 256;
 
@@ -1026,12 +1032,14 @@ __global__ void __launch_bounds__(kPRT) k_point_sort_route(const uint64_t* __res
     st->point_done = 0;
     st->delta = 0;
   }
-  for (uint32_t i = threadIdx.x; i < k; i += kPRT) s_keys[i] = in[i];
-  __syncthreads();
+  if (!sorted) {  // (a sorted batch is only read at each warp's own key)
+    for (uint32_t i = threadIdx.x; i < k; i += kPRT) s_keys[i] = in[i];
+    __syncthreads();
+  }
   const unsigned lane = lane_id();
   const uint32_t i = blockIdx.x * (kPRT / 32) + (threadIdx.x >> 5);
   if (i >= k) return;
-  const uint64_t x = s_keys[i];
+  const uint64_t x = sorted ? in[i] : s_keys[i];
   uint32_t r = i;
   if (!sorted) {
     uint32_t c = 0;
@@ -3191,8 +3199,9 @@ int run_front_graph(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int
 // lane-granular insert's buffer, the staging slot), unless a test of the
 // bounded waits is set up (those waits are in the batch algorithm's sort and
 // routing).
-bool point_ok(const cpma* h, uint64_t k, const uint32_t* tags) {
-  return !tags && k >= 1 && k <= std::min<uint64_t>(h->point_max, kPointMax) &&
+bool point_ok(const cpma* h, uint64_t k, int is_delete, const uint32_t* tags) {
+  return !tags && k >= 1 &&
+         k <= std::min<uint64_t>(h->point_max, is_delete ? kPointDelMax : kPointMax) &&
          h->cfg.codec == 0 && h->cfg.leaf_bytes <= 512 && h->n > 0 && h->L > 0 &&
          h->sort_poll_limit == 0 && h->sort_silent_tile < 0;
 }
@@ -3201,6 +3210,7 @@ bool point_ok(const cpma* h, uint64_t k, const uint32_t* tags) {
 // one leaf word, one 512-byte staging slot and one staged record per key.
 int point_scratch(cpma* h, uint64_t k, cudaStream_t st) {
   k = std::min<uint64_t>(std::max<uint64_t>(k, 2), kPointMax);
+  if (k > kPointRankMax) CPMA_TRY(sort_scratch(h, k, false));
   CPMA_TRY(ensure(h, h->s.keysA, k * 8, st));
   CPMA_TRY(ensure(h, h->s.T_leaf, (k + 2) * 4, st));
   CPMA_TRY(ensure(h, h->s.point_stage, k * 512, st));
@@ -3219,11 +3229,21 @@ int run_point(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_de
   Scratch& s = h->s;
   uint64_t* u = P<uint64_t>(s.keysA);
   uint32_t* leaf_of = P<uint32_t>(s.T_leaf);
+  if (!sorted && k > kPointRankMax) {
+    // the batch sort (into one of its scratch buffers); the routing kernel
+    // then copies the keys to u (a no-op when they are already there)
+    prof_begin(h, PH_SORT, st);
+    const uint64_t* srt = nullptr;
+    CPMA_TRY(sort_keys(h, d_keys, k, &srt, st));
+    prof_end(h, st);
+    d_keys = srt;
+    sorted = 1;
+  }
   const unsigned grid = (unsigned)((k + kPRT / 32 - 1) / (kPRT / 32));  // a warp per key
   prof_begin(h, PH_ROUTE, st);
   prof_add_bytes(h, PH_ROUTE, 20ull * k);
-  k_point_sort_route<<<grid, kPRT, k * 8, st>>>(d_keys, (uint32_t)k, sorted, u, leaf_of, h->heads,
-                                                h->L, ds);
+  k_point_sort_route<<<grid, kPRT, sorted ? 0 : k * 8, st>>>(d_keys, (uint32_t)k, sorted, u,
+                                                             leaf_of, h->heads, h->L, ds);
   prof_end(h, st);
   MergeArgs ma;
   memset(&ma, 0, sizeof(ma));
@@ -3508,7 +3528,7 @@ int run_update(cpma* h, const uint64_t* d_keys, uint64_t k, int sorted, int is_d
   // the point path; the batch algorithm below when its scratch cannot be
   // had within the memory budget, or when some touched leaf cannot change
   // in place (nothing has been written then)
-  const int prc = point_ok(h, k, tags) ? point_scratch(h, k, st) : CPMA_ENOMEM;
+  const int prc = point_ok(h, k, is_delete, tags) ? point_scratch(h, k, st) : CPMA_ENOMEM;
   if (prc != CPMA_OK && prc != CPMA_ENOMEM) return prc;
   if (prc == CPMA_OK) {
     bool fb = false;

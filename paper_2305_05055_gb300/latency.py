@@ -7,7 +7,9 @@ read included; medians over the trials.
 
     python -m paper_2305_05055_gb300.latency --n 1e8 --sizes 1,1000,4096
 
-With --profile the timed calls of the point path run between
+Deletes of more than 4096 keys take the batch algorithm in both columns
+(the library's point path stops there for deletes).  With --profile the
+timed calls of the point path run between
 cudaProfilerStart and cudaProfilerStop (for `ncu --profile-from-start off`).
 """
 import argparse
@@ -20,6 +22,9 @@ import torch
 
 from . import cpma as cp
 from . import workloads as W
+
+
+POINT_MAX = 16384  # the library's largest point-path batch
 
 
 def _keys(dev, a):
@@ -41,7 +46,7 @@ def measure(g, present, sizes=(1, 10, 100, 1000, 4096), trials=35, warm=5, seed=
     ins, dele = cp.lib().cpma_insert_batch, cp.lib().cpma_delete_batch
     calls0 = g.point_stats()
     for point in (True, False):
-        g.set_point_max(4096 if point else 0)
+        g.set_point_max(POINT_MAX if point else 0)
         for k in sizes:
             ib = [_keys(dev, W.uniform_keys(seed + 1000 * k + t, k, bits=40))
                   for t in range(warm + trials)]
@@ -74,7 +79,7 @@ def measure(g, present, sizes=(1, 10, 100, 1000, 4096), trials=35, warm=5, seed=
                     st.synchronize()
                 row[name + "_us"] = statistics.median(ev)
             out.setdefault("point" if point else "batch", {})[str(k)] = row
-    g.set_point_max(4096)
+    g.set_point_max(POINT_MAX)
     calls1 = g.point_stats()
     out["point_calls"] = calls1["calls"] - calls0["calls"]
     out["point_fell_back"] = calls1["batch"] - calls0["batch"]
@@ -86,7 +91,7 @@ def measure(g, present, sizes=(1, 10, 100, 1000, 4096), trials=35, warm=5, seed=
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--n", type=float, default=1e8)
-    ap.add_argument("--sizes", default="1,10,100,1000,4096")
+    ap.add_argument("--sizes", default="1,10,100,1000,4096,16384")
     ap.add_argument("--trials", type=int, default=35)
     ap.add_argument("--leaf-bytes", type=int, default=512)
     ap.add_argument("--profile", action="store_true")

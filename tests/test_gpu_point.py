@@ -1,5 +1,5 @@
 """GPU parity of the point path (Sec. 4: a batch much smaller than the set is
-applied as point updates).  Inserts and deletes of up to 4096 keys whose
+applied as point updates).  Inserts and deletes of up to 16384 keys whose
 touched leaves all change in place, and batches that some leaf cannot take
 (more than 32 keys -- 4 for a delete -- in one leaf, a leaf pushed over its
 own bound or past 512 bytes, a leaf emptied) and that the batch algorithm
@@ -50,7 +50,7 @@ def batches(seed, p, heads, n_rounds):
     heads (new heads), keys past the last element, repeats, and runs of 20
     to 40 keys into one gap (over 32 keys: the batch algorithm's)."""
     rng = np.random.default_rng(seed)
-    sizes = [1, 2, 7, 33, 100, 1000, 4096]
+    sizes = [1, 2, 7, 33, 100, 1000, 4096, 9000]
     for r in range(n_rounds):
         S = p.S
         k = sizes[r % len(sizes)]
@@ -89,10 +89,10 @@ def test_point_path_matches_oracle(LB):
         elif r % 5 == 4:
             srt = np.sort(keys)
             assert int(g.insert_batch(T(srt), sorted=True).item()) == o.insert_batch(srt) == p.insert_batch(srt)
-            n_ins += keys.size <= 4096
+            n_ins += keys.size <= 16384
         else:
             assert int(g.insert_batch(T(keys)).item()) == o.insert_batch(keys) == p.insert_batch(keys)
-            n_ins += keys.size <= 4096
+            n_ins += keys.size <= 16384
         same_layout(g, o)
     st = g.point_stats()
     assert st["calls"] == n_ins, st
@@ -101,9 +101,10 @@ def test_point_path_matches_oracle(LB):
 
 @pytest.mark.parametrize("LB", [256, 512])
 def test_point_deletes_match_oracle(LB):
-    """Small deletes: present and absent keys, leaf heads (a new head), the
-    last element, repeats, whole runs of neighbours (a leaf emptied or
-    pushed under its bound: the batch algorithm), with inserts between."""
+    """Small deletes (the point path takes up to 4096 keys): present and
+    absent keys, leaf heads (a new head), the last element, repeats, whole
+    runs of neighbours (a leaf emptied or pushed under its bound: the batch
+    algorithm), with inserts between."""
     rng = np.random.default_rng(LB + 3)
     base = W.uniform_keys(651 + LB, 50000, bits=40)
     g = cp.CPMA(T(base), leaf_bytes=LB)
@@ -171,44 +172,49 @@ def test_point_path_off_changes_nothing():
     b.set_point_max(0)
     p = oracle.PlainSet(base)
     heads = lambda: cp.to_u64(a.layout()[2])
+    calls = 0
     for r, keys in batches(5, p, heads, 14):
         na, nb = int(a.insert_batch(T(keys)).item()), int(b.insert_batch(T(keys)).item())
         assert na == nb == p.insert_batch(keys)
         gone = W.sample_present(p.S, 690 + r, keys.size)
         na, nb = int(a.delete_batch(T(gone)).item()), int(b.delete_batch(T(gone)).item())
         assert na == nb == p.delete_batch(gone)
+        calls += (keys.size <= 16384) + (gone.size <= 4096)
         for x, y in zip(a.layout(), b.layout()):
             assert torch.equal(x, y)
     assert b.point_stats() == {"calls": 0, "batch": 0}
-    assert a.point_stats()["calls"] == 28
+    assert a.point_stats()["calls"] == calls
 
 
 def test_point_path_extreme_keys_and_limits():
-    """Keys 0 and 2^64-1 (routed by the head array's last entry), a batch of
-    exactly 4096 keys (the largest the point path takes) and 4097 (the batch
-    algorithm's), and the point limit lowered below a batch's size."""
+    """Keys 0 and 2^64-1 (routed by the head array's last entry), batches of
+    4096 keys (the largest ranked in the routing kernel), 4097 and 16384
+    (sorted by the batch sort first; 16384 is the largest the point path
+    takes) and 16385 (the batch algorithm's), and the point limit lowered
+    below a batch's size."""
     base = np.concatenate([W.uniform_keys(631, 20000, bits=64), np.array([5, M64 - 5], np.uint64)])
     g = cp.CPMA(T(base), leaf_bytes=256)
     o = oracle.SeqCPMA(base, leaf_bytes=256)
     p = oracle.PlainSet(base)
     for keys in ([0], [M64], [M64, 0, M64 - 1, 1], W.uniform_keys(632, 4096, bits=64),
-                 W.uniform_keys(633, 4097, bits=64)):
+                 W.uniform_keys(633, 4097, bits=64), W.uniform_keys(635, 16384, bits=64),
+                 W.uniform_keys(636, 16385, bits=64)):
         keys = np.asarray(keys, dtype=np.uint64)
         assert int(g.insert_batch(T(keys)).item()) == o.insert_batch(keys) == p.insert_batch(keys)
         same_layout(g, o)
-    assert g.point_stats()["calls"] == 4
+    assert g.point_stats()["calls"] == 6
     g.set_point_max(10)
     keys = W.uniform_keys(634, 11, bits=64)
     assert int(g.insert_batch(T(keys)).item()) == o.insert_batch(keys)
     same_layout(g, o)
-    assert g.point_stats()["calls"] == 4
+    assert g.point_stats()["calls"] == 6
 
 
 def test_point_path_rejects_an_unsorted_batch_unchanged():
     base = W.uniform_keys(641, 20000, bits=40)
     g = cp.CPMA(T(base), leaf_bytes=512)
     before = [t.cpu().clone() for t in g.layout()]
-    for k in (2, 100, 4096):
+    for k in (2, 100, 4096, 9000):
         keys = np.sort(W.uniform_keys(642 + k, k, bits=40))[::-1].copy()  # descending
         with pytest.raises(cp.CPMAError) as e:
             g.insert_batch(T(keys), sorted=True)
