@@ -369,22 +369,22 @@ int cpma_use_graphs(cpma_t* h, uint64_t max_batch);
  * updates rather than by the batch merge).  An untagged insert of 1 ..
  * max_keys keys (at most 16384; default 16384; 0 = never), or delete of at
  * most min(max_keys, 4096) keys, on a non-empty set of byte-code leaves of
- * at most 512 bytes is first sorted
- * (up to 4096 keys by ranks in the routing kernel, more by the batch sort)
- * and routed (a warp per key), and each touched leaf is checked by a warp: it changes
- * in place when it receives at most 32 keys (4 for a delete), holds codes of
- * at most 4 bytes and, for an insert, at most 512 used bytes before and
- * after, is not emptied by a delete, and stays within its own density bound
- * (Sec. 3 bounds at height 0).  The results are staged; if every touched
- * leaf qualifies they are committed and the update is done (two or three
- * kernels and one status read); otherwise nothing is written and the update
- * runs the batch algorithm.  Counts, sets and layouts are the same either
- * way: with no leaf pending, emptied or outside its bound the batch
- * algorithm rewrites exactly those leaves, with the same bytes, and starts
- * no redistribution.  The point path's scratch (about 550 bytes per key,
- * held like the rest) is reserved by cpma_reserve for max_batch keys; when it
- * cannot be had within the memory budget the update takes the batch
- * algorithm instead.  Errors: CPMA_EINVAL (null handle). */
+ * at most 512 bytes is first sorted (up to 4096 keys by ranks in the
+ * routing kernel, more by the batch sort) and routed (a warp per key), and
+ * each touched leaf is checked by a warp: it changes in place when it
+ * receives at most 32 keys (4 for a delete), holds codes of at most 4 bytes
+ * and, for an insert, at most 512 used bytes before and after, is not
+ * emptied by a delete, and stays within its own density bound (Sec. 3
+ * bounds at height 0).  The results are staged; if every touched leaf
+ * qualifies they are committed and the update is done (two or three kernels
+ * after the sort, and one status read); otherwise nothing is written and
+ * the update runs the batch algorithm.  Counts, sets and layouts are the
+ * same either way: with no leaf pending, emptied or outside its bound the
+ * batch algorithm rewrites exactly those leaves, with the same bytes, and
+ * starts no redistribution.  The point path's scratch (about 550 bytes per
+ * key, held like the rest) is reserved by cpma_reserve for max_batch keys;
+ * when it cannot be had within the memory budget the update takes the
+ * batch algorithm instead.  Errors: CPMA_EINVAL (null handle). */
 int cpma_set_point_max(cpma_t* h, uint64_t max_keys);
 
 /* Updates that took the point path (calls) and those of them that the batch
